@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: FSE / EPI seconds at 27,525,120 isochromats on one GB300,
+grouped vs plain GPU forms, signal rel-L2 against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrsim|reference]
+
+One step = one grouped FP32 simulation of the 2-D FSE workload (512 x 512 x
+105 isochromats, ETL 16, 256 phase encodes, 3 ms sinc pulses at 1 us) on a
+phantom resident in HBM: combined-transition precompute, the fused
+isochromat pass, the group-signal pass and the signal read-back.  Grouping
+(classification + group build + layout) is prepared once per phantom and is
+reported separately (`prep_s`), and again inside the end-to-end figure,
+which runs the whole public API from pinned host buffers every step.
+
+Also reported on the same GPU: grouped EPI, plain (per-isochromat) FSE and
+EPI, plain+cache FSE, per-kernel device times, the roofline of the dominant
+kernel, and the FP64 oracle timed on this host's cores on a sample.
+
+`--impl reference` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded isochromat sample of the same workload and prints the
+same JSON line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FSE/EPI seconds @27.5M isochromats, grouped vs plain GPU, rel-L2≤1e-4 vs FP64"
+WORKLOAD = ("fse_27m: 2-D FSE, 512x512 in-plane x 105 z-subvoxels = 27,525,120 isochromats, "
+            "8-ellipse phantom (seed 1002), 3 ms Hamming-sinc 90x/180y at 1 us, ETL 16, "
+            "256 phase encodes in 16 shots, 256 samples at 4 us, ESP 8 ms, TR 3 s")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    try:
+                        rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                    except ValueError:
+                        pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        power = [r[2] for r in rows]
+        thr = 0.5 * max(power)
+        load = [r for r in rows if r[2] >= thr] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
+
+
+def golden_check(name, sig, ph_digest, seq_digest):
+    path = os.path.join(GOLDEN, f"{name}_27m_oracle.npz")
+    if not os.path.exists(path):
+        return None
+    import oracle
+    d = np.load(path)
+    if str(d["phantom_digest"]) != ph_digest or str(d["sequence_digest"]) != seq_digest:
+        return {"error": "stored oracle signal was made from different inputs"}
+    return float(oracle.rel_l2(sig, d["signal"]))
+
+
+def cpu_baseline(ph, seq, stride, threads=0):
+    """FP64 oracle on every `stride`-th isochromat; time extrapolated to K
+    (run time is linear in K: isochromats are independent)."""
+    import oracle
+    sub = ph.subset(np.arange(0, ph.K, stride))
+    t0 = time.perf_counter()
+    oracle.simulate(sub, seq, memo=True, adc_recurrence=True, n_threads=threads, want_M=False)
+    wall = time.perf_counter() - t0
+    cores = threads if threads > 0 else os.cpu_count()
+    return wall * ph.K / sub.K, wall, sub.K, cores
+
+
+# algorithmic FP32 work of the fused kernel per isochromat and event (flops,
+# FMA = 2, each of sin / cos / exp counted as 1):
+#   advance, Eqs. 4-5: phase x.kx + y.ky + z.kz + dB0.tau = 7, sin + cos + 2 exp = 4,
+#     transverse rotate-and-decay 8, longitudinal recovery 3          -> 22
+#   with-RF update step M <- A M + b M0 (3 rows x (1 mul + 3 FMA))     -> 21
+#   with-ADC block sum: phase 7, sin + cos + exp 3, transverse 8, add 2 -> 20
+FLOPS_RF, FLOPS_ADC, FLOPS_END = 43, 20, 22
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mrsim", choices=["mrsim", "reference"])
+    ap.add_argument("--plain-fse", default="on", choices=["on", "off"],
+                    help="time one plain (per-isochromat) FSE run (~tens of seconds)")
+    ap.add_argument("--cpu-stride", type=int, default=128)
+    a = ap.parse_args()
+    a.warmup = max(3, a.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from mrsim_inputs import configs, phantom_digest, sequence_digest
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        reference_arm(a, configs)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_03960_gb300 import mrsim
+
+    ph = configs.full_phantom()
+    fse = configs.fse_sequence()
+    epi = configs.epi_sequence()
+    stream = torch.cuda.current_stream()
+    ctx = mrsim.Context(local, stream.cuda_stream)
+    pk, pk_kind = peaks()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def maxr(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- resident phantom, prepared sequences and groups (once per phantom) ----
+    t0 = time.perf_counter()
+    hp = ctx.phantom(ph)
+    torch.cuda.synchronize()
+    t_upload = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs_f = ctx.sequence(fse)
+    hg_f = ctx.group(hp, hs_f)
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    hs_e = ctx.sequence(epi)
+    hg_e = ctx.group(hp, hs_e)
+    groups = {n: mrsim.mrsim_group_info(hg_f, t)[0] for n, t in (("gx", mrsim.G_X), ("gz", mrsim.G_Z))}
+
+    ns_f, ns_e = fse.n_samples, epi.n_samples
+    sig_f = torch.zeros(2 * ns_f, dtype=torch.float64, device="cuda")
+    sig_e = torch.zeros(2 * ns_e, dtype=torch.float64, device="cuda")
+
+    def step(hs, hg, sig, mode=mrsim.GROUPED):
+        mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+
+    # ---- headline: grouped FSE ----
+    for _ in range(a.warmup):
+        step(hs_f, hg_f, sig_f)
+    mrsim.mrsim_profile_reset(ctx.h)
+    mrsim.mrsim_profile_enable(ctx.h, True)
+    n_launch0 = mrsim.mrsim_launch_count(ctx.h)
+    barrier()
+    with Clocks(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            step(hs_f, hg_f, sig_f)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = mrsim.mrsim_launch_count(ctx.h) - n_launch0
+    prof = mrsim.mrsim_profile_get(ctx.h)
+    mrsim.mrsim_profile_enable(ctx.h, False)
+    clocks = clk.summary()
+    fse_s = maxr(ms_total / a.steps / 1e3)
+    fse_sig = sig_f.cpu().numpy().view(np.complex128)
+
+    # ---- grouped EPI ----
+    for _ in range(a.warmup):
+        step(hs_e, hg_e, sig_e)
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(hs_e, hg_e, sig_e)
+    e1.record(stream)
+    barrier()
+    epi_s = maxr(e0.elapsed_time(e1) / a.steps / 1e3)
+    epi_sig = sig_e.cpu().numpy().view(np.complex128)
+
+    # ---- plain forms on the same GPU ----
+    def timed_once(fn):
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        return maxr(e0.elapsed_time(e1) / 1e3)
+
+    step(hs_e, None, sig_e, mrsim.PLAIN)  # warm the plain kernels
+    epi_plain_s = timed_once(lambda: step(hs_e, None, sig_e, mrsim.PLAIN))
+    epi_plain_sig = sig_e.cpu().numpy().view(np.complex128).copy()
+    fse_plain_s = fse_plain_sig = None
+    fse_cache_s = None
+    if a.plain_fse == "on":
+        fse_cache_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN_CACHE))
+        fse_plain_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN))
+        fse_plain_sig = sig_f.cpu().numpy().view(np.complex128).copy()
+
+    # ---- end to end through the public API from pinned host buffers ----
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).pin_memory()
+           for k, v in dict(x=ph.x, y=ph.y, z=ph.z, T1=ph.T1, T2=ph.T2, dB0=ph.dB0,
+                            M0=ph.M0).items()}
+    out_pin = torch.zeros(2 * ns_f, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 4 for t in pin.values()) + sum(v.nbytes for v in fse.arrays().values())
+    d2h = out_pin.numel() * 8
+
+    def e2e_step():
+        p = mrsim.mrsim_phantom(ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0",
+                                                                  "M0")])
+        s = ctx.sequence(fse)
+        g = mrsim.mrsim_group(ctx.h, p, s)
+        mrsim.mrsim_run(ctx.h, p, s, g, mrsim.GROUPED, mrsim.FP32, out_pin, None, 0)
+        mrsim.mrsim_free_groups(g)
+        ctx.free("seq", s)
+        mrsim.mrsim_free_phantom(p)
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(a.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_s = maxr(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / a.steps)
+
+    # ---- roofline of the dominant kernel (fused isochromat pass) ----
+    name = max(prof, key=lambda n: prof[n][1])
+    n_l, ms_l = prof[name]
+    avg_s = ms_l / n_l / 1e3
+    roof = None
+    if name.startswith("fused_grouped"):
+        n_rf, n_adc = fse.meta["n_rf"], fse.meta["n_adc"]
+        flops = ph.K * (n_rf * FLOPS_RF + n_adc * FLOPS_ADC + FLOPS_END)
+        peak = 2 * 128 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / avg_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz from "
+                               f"MEASURED_PEAKS.json ({pk_kind})",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": round(avg_s * 1e3, 4),
+                "launches": n_l}
+
+    # ---- parity against the stored oracle signals ----
+    pd, sd_f, sd_e = phantom_digest(ph), sequence_digest(fse), sequence_digest(epi)
+    parity = {"fse_grouped_rel_l2": golden_check("fse", fse_sig, pd, sd_f),
+              "epi_grouped_rel_l2": golden_check("epi", epi_sig, pd, sd_e),
+              "epi_plain_rel_l2": golden_check("epi", epi_plain_sig, pd, sd_e)}
+    if fse_plain_sig is not None:
+        parity["fse_plain_rel_l2"] = golden_check("fse", fse_plain_sig, pd, sd_f)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, wall, n, cores = cpu_baseline(ph, fse, a.cpu_stride)
+        cpu = {"value": round(v, 2), "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle on every {a.cpu_stride}th isochromat ({n} of {ph.K}) of "
+                         f"the FSE workload, {wall:.2f} s wall, extrapolated x{ph.K / n:.1f} "
+                         "(linear in K)"}
+
+    steps_fse = ph.K * (sum(int(r) for r, b1, b2 in zip(fse.repeat, fse.b1re, fse.b1im)
+                            if b1 != 0 or b2 != 0) + ns_f)
+    out = {
+        "metric": METRIC, "value": round(fse_s, 6), "unit": "s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(fse_s * 1e3, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "K": ph.K, "mode": "grouped", "precision": "fp32",
+                   "l2": "inputs larger than L2 (27.5M isochromats x 40 B resident)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fse_grouped_s": round(fse_s, 6), "epi_grouped_s": round(epi_s, 6),
+        "fse_plain_s": None if fse_plain_s is None else round(fse_plain_s, 4),
+        "fse_plain_cache_s": None if fse_cache_s is None else round(fse_cache_s, 4),
+        "epi_plain_s": round(epi_plain_s, 5),
+        "speedup_grouped_vs_plain": {
+            "fse": None if fse_plain_s is None else round(fse_plain_s / fse_s, 1),
+            "epi": round(epi_plain_s / epi_s, 1)},
+        "isochromat_steps_per_s_equiv": round(steps_fse / fse_s, 1),
+        "prep_s": round(prep_s, 4), "phantom_upload_s": round(t_upload, 4), "groups": groups,
+        "parity": parity,
+        "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(a, configs):
+    """The FP64 CPU oracle as it stands, on this host's cores, on a bounded
+    sample of the FSE workload each step; value extrapolated to K."""
+    ph = configs.full_phantom()
+    fse = configs.fse_sequence()
+    stride = 1024
+    vals = []
+    walls = []
+    for i in range(a.warmup + a.steps):
+        v, wall, n, cores = cpu_baseline(ph, fse, stride)
+        if i >= a.warmup:
+            vals.append(v)
+            walls.append(wall)
+    value = statistics.mean(vals)
+    sample = (f"FP64 oracle on every {stride}th isochromat ({n} of {ph.K}) per step, "
+              f"extrapolated x{ph.K / n:.1f} (linear in K)")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "s",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": round(statistics.mean(walls) * 1e3, 2), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "K": ph.K, "mode": "oracle (ungrouped, FP64)"},
+           "cpu_baseline": {"value": round(value, 3), "unit": "s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * mrsim — GB300 (sm_103a) Bloch-equation MR simulator with grouped
+ * isochromats.  C ABI.
+ *
+ * Method: H. Takeshima, "Fast Magnetic Resonance Simulation Using Combined
+ * Update with Grouped Isochromats" (arXiv 2508.03960).
+ *
+ * Problem (Sec. 2.1, Eq. 1): K static isochromats k with position r(k),
+ * T1(k), T2(k), off-resonance dB0(k) and equilibrium magnetization M0(k)
+ * evolve under a piecewise-constant field B(t) = (b1(k) B1re, b1(k) B1im,
+ * G(t).r(k) + dB0(k)/gamma_bar).  The received signal at every ADC sample is
+ * A(t) = sum_k (Mx + i My)(k, t)  (Eq. 6, one receive coil, S = 1).
+ *
+ * Units everywhere: seconds, tesla, T/m, metres, Hz (dB0), dimensionless b1.
+ * gamma = 2 pi * 42.577478518e6 rad/s/T.  T1 or T2 = +inf means no
+ * relaxation.  Sign conventions: rotation by theta = -gamma |B| dt about
+ * B/|B| (Eq. A2) followed by relaxation (Eq. A1); free precession multiplies
+ * M_xy by exp(-i gamma int Bz dt) (Eq. 4).
+ *
+ * Conventions shared by all calls
+ *  - Status: every int-returning call returns MRSIM_OK (0) or an MRSIM_E*
+ *    code; the message of the last failure is in mrsim_last_error(ctx).
+ *  - Ownership: the caller owns every array it passes; the library copies
+ *    what it keeps (phantoms go to device memory), so input arrays may be
+ *    freed as soon as a call returns.  Handles (mrsim_ctx, mrsim_phantom,
+ *    mrsim_seq, mrsim_groups) are owned by the library and released with the
+ *    matching mrsim_free_* / mrsim_destroy call.  Output arrays are
+ *    caller-allocated.
+ *  - Threading: one context per host thread.  All device work of a context
+ *    runs on its CUDA stream; every call that produces results is
+ *    synchronous at return.
+ *  - Pointers: unless a flag says MRSIM_PTR_DEVICE / MRSIM_OUT_DEVICE,
+ *    arrays are host memory.
+ */
+#ifndef MRSIM_H
+#define MRSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MRSIM_OK 0
+#define MRSIM_EINVAL 1       /* bad argument: NaN, T <= 0, K <= 0, dt <= 0, repeat < 1, ... */
+#define MRSIM_EUNSUPPORTED 2 /* RF and ADC active in the same segment (Sec. 2.1) */
+#define MRSIM_ENOMEM 3       /* device or host allocation failed */
+#define MRSIM_ECUDA 4        /* a CUDA runtime call or kernel failed */
+#define MRSIM_ETIMEOUT 5     /* a bounded device wait ran out (batched launcher) */
+#define MRSIM_ESTATE 6       /* handles do not belong together (e.g. groups of another phantom) */
+
+/* subsequence types (Fig. 1) */
+#define MRSIM_SUB_RF 0
+#define MRSIM_SUB_ADC 1
+#define MRSIM_SUB_RELAX 2
+
+/* gradient types (Sec. 2.4); MRSIM_G_GENERAL falls back to the conventional method */
+#define MRSIM_G_NONE 0
+#define MRSIM_G_X 1
+#define MRSIM_G_Y 2
+#define MRSIM_G_Z 3
+#define MRSIM_G_GENERAL 4
+
+/* run modes */
+#define MRSIM_PLAIN 0       /* every isochromat stepped individually (Eq. 3, Eq. 6) */
+#define MRSIM_PLAIN_CACHE 1 /* per-isochromat combined transitions reused (Eq. 7, dynamic caching) */
+#define MRSIM_GROUPED 2     /* grouped isochromats (Sec. 2.3, Eqs. 8-10) */
+#define MRSIM_SURROGATE 3   /* GROUPED with learned with-RF transitions where trained */
+
+/* precision of the per-isochromat arithmetic (FP64 is always used to compose
+ * combined transitions and to reduce the signal across isochromats) */
+#define MRSIM_FP32 0
+#define MRSIM_FP64 1
+
+/* flags */
+#define MRSIM_PTR_DEVICE 1u /* mrsim_phantom: input arrays are device pointers */
+#define MRSIM_OUT_DEVICE 2u /* mrsim_run: signal and M_final are device pointers */
+
+typedef struct mrsim_ctx mrsim_ctx;
+typedef struct mrsim_phantom_t mrsim_phantom_t;
+typedef struct mrsim_seq mrsim_seq;
+typedef struct mrsim_groups mrsim_groups;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * run on (not owned), or NULL for a context-owned stream.
+ * Errors: MRSIM_EINVAL (ctx NULL or bad device), MRSIM_ECUDA. */
+int mrsim_create(mrsim_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and its stream (if owned).  NULL is a no-op. */
+void mrsim_destroy(mrsim_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char *mrsim_last_error(const mrsim_ctx *ctx);
+
+/* Upload a phantom of K isochromats (Sec. 2.1).  Each array has K float32
+ * entries: position x, y, z (m), T1_s, T2_s (s, > 0, +inf allowed), dB0_hz,
+ * M0.  b1_scale: relative RF amplitude per isochromat, NULL => 1.  M_init:
+ * initial magnetization as [3][K] (Mx block, My block, Mz block), NULL =>
+ * thermal equilibrium (0, 0, M0).  flags: MRSIM_PTR_DEVICE if the arrays are
+ * device pointers on the context's device.  The data are copied.
+ * Errors: MRSIM_EINVAL (K <= 0, NULL array, NaN, T <= 0), MRSIM_ENOMEM,
+ * MRSIM_ECUDA. */
+int mrsim_phantom(mrsim_ctx *ctx, int64_t K, const float *x, const float *y, const float *z,
+                  const float *T1_s, const float *T2_s, const float *dB0_hz, const float *M0,
+                  const float *b1_scale, const float *M_init, unsigned flags,
+                  mrsim_phantom_t **out);
+
+/* Describe a pulse sequence as n_seg run-length segments (Sec. 2.1: B(t) is
+ * piecewise constant).  Segment j holds repeat[j] >= 1 sub-steps of dt_s[j]
+ * > 0 seconds with constant RF b1_re_T + i b1_im_T (tesla), gradient
+ * (gx, gy, gz) (T/m) and adc[j] (1 => one sample at the end of every
+ * sub-step).  The call splits the sequence into maximal with-RF (B1 != 0),
+ * with-ADC and relaxation subsequences (Fig. 1) and types each by which
+ * gradient axes are nonzero anywhere in it (Sec. 2.4; a component is zero
+ * when it equals 0.0f).  Host arrays; copied.
+ * Errors: MRSIM_EINVAL (n_seg <= 0, dt <= 0, repeat < 1, non-finite value),
+ * MRSIM_EUNSUPPORTED (RF and ADC in one segment, "not considered" in
+ * Sec. 2.1), MRSIM_ENOMEM. */
+int mrsim_sequence(mrsim_ctx *ctx, int64_t n_seg, const double *dt_s, const int32_t *repeat,
+                   const float *b1_re_T, const float *b1_im_T, const float *gx_Tpm,
+                   const float *gy_Tpm, const float *gz_Tpm, const uint8_t *adc,
+                   mrsim_seq **out);
+
+/* Subsequence table of a sequence.  n_subseq receives the count; each output
+ * array (host, n_subseq entries) may be NULL.  type: MRSIM_SUB_*; gtype:
+ * MRSIM_G_*; seg_begin/seg_end: half-open segment range; n_samples_total:
+ * ADC samples of the whole sequence.  Errors: MRSIM_EINVAL (seq NULL). */
+int mrsim_seq_info(const mrsim_seq *seq, int64_t *n_subseq, uint8_t *type, uint8_t *gtype,
+                   int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples_total);
+
+/* Build the groups the sequence needs (Sec. 2.4, Fig. 2): for every known
+ * gradient type used by a with-RF or with-ADC subsequence, isochromats with
+ * bit-equal keys share a group.  Keys: Gx-only (x, T1, T2, dB0[, b1]),
+ * Gy-only (y, ...), Gz-only (z, ...), no-grads (T1, T2, dB0[, b1]); -0 and
+ * +0 compare equal; b1 joins the key when the phantom has one.  Groups are
+ * numbered by first occurrence in isochromat index order.  Also lays the
+ * isochromats out in device memory sorted by (with-ADC group, with-RF group).
+ * Runs on the device; done once per (phantom, sequence shape).
+ * Errors: MRSIM_EINVAL, MRSIM_ENOMEM, MRSIM_ECUDA. */
+int mrsim_group(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
+                mrsim_groups **out);
+
+/* Group count and (optionally) the group id of every isochromat, in the
+ * phantom's original order, for gradient type gtype (MRSIM_G_NONE..Z).
+ * gid: host int32[K] or NULL.  Errors: MRSIM_EINVAL (type not built). */
+int mrsim_group_info(const mrsim_groups *groups, int gtype, int64_t *n_groups, int32_t *gid);
+
+/* Simulate the sequence on the phantom and return the received signal.
+ * groups: required for MRSIM_GROUPED / MRSIM_SURROGATE (NULL => error),
+ * ignored otherwise.  mode: MRSIM_PLAIN, MRSIM_PLAIN_CACHE, MRSIM_GROUPED,
+ * MRSIM_SURROGATE.  precision: MRSIM_FP32 or MRSIM_FP64 for the
+ * per-isochromat arithmetic.  signal: [2 * n_samples_total] doubles,
+ * interleaved (re, im), in time order.  M_final: [3][K] float32 final
+ * magnetization in the phantom's order, or NULL.  out_flags:
+ * MRSIM_OUT_DEVICE if signal / M_final are device pointers.
+ * Errors: MRSIM_EINVAL, MRSIM_ESTATE (groups built for another phantom or
+ * without a needed type), MRSIM_ENOMEM, MRSIM_ECUDA. */
+int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
+              const mrsim_groups *groups, int mode, int precision, double *signal,
+              float *M_final, unsigned out_flags);
+
+/* Run n_jobs independent (phantom, sequence) jobs of uneven sizes in one
+ * persistent, CUDA-graph-captured launch chain (grouped FP32 steps, FP64
+ * signal sums).  groups[i] must come from mrsim_group(ph[i], seq[i]).
+ * signals[i]: host [2 * n_samples_total(seq[i])] doubles.
+ * Errors: MRSIM_EINVAL, MRSIM_ESTATE, MRSIM_ENOMEM, MRSIM_ECUDA,
+ * MRSIM_ETIMEOUT (a bounded device wait gave up). */
+int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph,
+                    const mrsim_seq *const *seq, const mrsim_groups *const *groups,
+                    double *const *signals);
+
+/* Per-kernel timing.  With profiling on, every kernel launch of the context
+ * is bracketed by CUDA events on the context stream.  mrsim_profile_get
+ * returns, for entry i (0-based, in first-launch order), the kernel name
+ * (copied into name[cap], NUL-terminated), the number of launches and their
+ * summed device time in ms; it returns MRSIM_EINVAL past the last entry.
+ * mrsim_profile_reset clears the counters. */
+int mrsim_profile_enable(mrsim_ctx *ctx, int on);
+int mrsim_profile_reset(mrsim_ctx *ctx);
+int mrsim_profile_get(mrsim_ctx *ctx, int i, char *name, int cap, int64_t *launches,
+                      double *ms_total);
+
+/* Kernels launched by this context since creation (all modes). */
+int64_t mrsim_launch_count(const mrsim_ctx *ctx);
+
+void mrsim_free_phantom(mrsim_phantom_t *ph);
+void mrsim_free_seq(mrsim_seq *seq);
+void mrsim_free_groups(mrsim_groups *groups);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRSIM_H */

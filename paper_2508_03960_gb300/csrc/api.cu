@@ -1,0 +1,864 @@
+// C ABI of libmrsim (declared in include/mrsim.h) and the host planner that
+// turns a classified sequence into kernel launches.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace mrsim {
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(MRSIM_ENOMEM, std::string("out of device memory in ") + what);
+    }
+    fail(MRSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+DBuf dalloc(size_t bytes) {
+    DBuf d;
+    if (bytes == 0) return d;
+    cudaError_t e = cudaMalloc(&d.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        d.p = nullptr;
+        fail(MRSIM_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    d.bytes = bytes;
+    return d;
+}
+
+void *scratch(mrsim_ctx *c, int slot, size_t bytes) {
+    DBuf &b = c->scratch[slot];
+    if (b.bytes < bytes) {
+        MRSIM_CUDA(cudaStreamSynchronize(c->stream));
+        b.reset();
+        b = dalloc(std::max<size_t>(bytes, 256));
+    }
+    return b.p;
+}
+
+void upload(mrsim_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return;
+    MRSIM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+}
+
+void sync(mrsim_ctx *c) {
+    MRSIM_CUDA(cudaGetLastError());
+    MRSIM_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+}
+
+KScope::KScope(mrsim_ctx *ctx, const char *name) : c(ctx) {
+    ++c->launches;
+    if (!c->prof_on) return;
+    for (size_t i = 0; i < c->prof_names.size(); ++i)
+        if (c->prof_names[i] == name) { id = (int)i; break; }
+    if (id < 0) {
+        id = (int)c->prof_names.size();
+        c->prof_names.push_back(name);
+        c->prof_count.push_back(0);
+        c->prof_ms.push_back(0.0);
+    }
+    for (cudaEvent_t *e : {&a, &b}) {
+        if (!c->ev_pool.empty()) {
+            *e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            *e = nullptr;
+        }
+    }
+    if (a) cudaEventRecord(a, c->stream);
+}
+
+KScope::~KScope() {
+    if (id < 0 || !a || !b) return;
+    cudaEventRecord(b, c->stream);
+    c->prof_pending.push_back({id, a, b});
+}
+
+void prof_flush(mrsim_ctx *c) {
+    for (auto &p : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            c->prof_ms[p.id] += ms;
+            c->prof_count[p.id] += 1;
+        }
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->prof_pending.clear();
+}
+
+namespace {
+
+std::atomic<uint64_t> g_uid{1};
+
+inline AdvF make_adv_f(const double mom[3], double tau) {
+    auto sp = [](double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    AdvF a;
+    sp(kGammaBar * mom[0], a.kx_hi, a.kx_lo);
+    sp(kGammaBar * mom[1], a.ky_hi, a.ky_lo);
+    sp(kGammaBar * mom[2], a.kz_hi, a.kz_lo);
+    sp(tau, a.tau_hi, a.tau_lo);
+    return a;
+}
+inline AdvD make_adv_d(const double mom[3], double tau) {
+    return AdvD{kGammaBar * mom[0], kGammaBar * mom[1], kGammaBar * mom[2], tau};
+}
+
+template <typename R>
+struct AdvOf;
+template <>
+struct AdvOf<float> {
+    using T = AdvF;
+    static AdvF make(const double m[3], double t) { return make_adv_f(m, t); }
+};
+template <>
+struct AdvOf<double> {
+    using T = AdvD;
+    static AdvD make(const double m[3], double t) { return make_adv_d(m, t); }
+};
+
+uint64_t seg_hash(const mrsim_seq *s, int64_t j, uint64_t h) {
+    auto mixin = [&](const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mixin(&s->dt[j], 8);
+    mixin(&s->rep[j], 4);
+    mixin(&s->b1re[j], 4);
+    mixin(&s->b1im[j], 4);
+    mixin(&s->gx[j], 4);
+    mixin(&s->gy[j], 4);
+    mixin(&s->gz[j], 4);
+    return h;
+}
+
+bool same_seg(const mrsim_seq *s, int64_t a, int64_t b) {
+    return s->dt[a] == s->dt[b] && s->rep[a] == s->rep[b] && s->b1re[a] == s->b1re[b] &&
+           s->b1im[a] == s->b1im[b] && s->gx[a] == s->gx[b] && s->gy[a] == s->gy[b] &&
+           s->gz[a] == s->gz[b];
+}
+
+__global__ void k_validate(int64_t K, const float *x, const float *y, const float *z,
+                           const float *T1, const float *T2, const float *dB0, const float *M0,
+                           const float *b1, const float *Mi, int *err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        bool bad = !isfinite(x[k]) || !isfinite(y[k]) || !isfinite(z[k]) || !isfinite(dB0[k]) ||
+                   !isfinite(M0[k]) || !(T1[k] > 0.0f) || !(T2[k] > 0.0f) ||
+                   (b1 && !isfinite(b1[k]));
+        if (Mi) bad |= !isfinite(Mi[k]) || !isfinite(Mi[K + k]) || !isfinite(Mi[2 * K + k]);
+        if (bad) atomicOr(err, 1);
+    }
+}
+
+void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
+    const int64_t n = s->n_seg;
+    // split into maximal runs of one class (Fig. 1)
+    auto cls = [&](int64_t j) {
+        bool rf = s->b1re[j] != 0.0f || s->b1im[j] != 0.0f;
+        if (rf && s->adc[j]) fail(MRSIM_EUNSUPPORTED, "RF and ADC active in segment " + std::to_string(j));
+        return rf ? SUB_RF : (s->adc[j] ? SUB_ADC : SUB_RELAX);
+    };
+    for (int64_t j = 0; j < n; ++j) {
+        if (!(std::isfinite(s->dt[j]) && s->dt[j] > 0.0) || s->rep[j] < 1 ||
+            !std::isfinite(s->b1re[j]) || !std::isfinite(s->b1im[j]) ||
+            !std::isfinite(s->gx[j]) || !std::isfinite(s->gy[j]) || !std::isfinite(s->gz[j]))
+            fail(MRSIM_EINVAL, "invalid segment " + std::to_string(j));
+        int t = cls(j);
+        if (j == 0 || t != s->sub.back().type) {
+            Subseq q;
+            q.type = t;
+            q.seg_begin = j;
+            s->sub.push_back(q);
+        }
+        s->sub.back().seg_end = j + 1;
+    }
+    int64_t smp = 0;
+    std::unordered_map<uint64_t, std::vector<int>> by_hash;
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        Subseq &q = s->sub[i];
+        bool ax = false, ay = false, az = false;
+        uint64_t h = 1469598103934665603ull;
+        for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
+            ax |= s->gx[j] != 0.0f;
+            ay |= s->gy[j] != 0.0f;
+            az |= s->gz[j] != 0.0f;
+            const double d = s->dt[j] * s->rep[j];
+            q.dur += d;
+            q.mom[0] += (double)s->gx[j] * d;
+            q.mom[1] += (double)s->gy[j] * d;
+            q.mom[2] += (double)s->gz[j] * d;
+            if (s->adc[j]) q.n_samples += s->rep[j];
+            if (q.type == SUB_RF) h = seg_hash(s, j, h);
+        }
+        const int cnt = (int)ax + (int)ay + (int)az;
+        q.gtype = cnt == 0 ? G_NONE : cnt > 1 ? G_GENERAL : ax ? G_X : ay ? G_Y : G_Z;
+        q.sample0 = smp;
+        smp += q.n_samples;
+        if (q.type == SUB_RF) {
+            const int64_t len = q.seg_end - q.seg_begin;
+            int found = -1;
+            for (int cid : by_hash[h]) {
+                const Subseq &r = s->sub[s->content_first[cid]];
+                if (r.seg_end - r.seg_begin != len) continue;
+                bool eq = true;
+                for (int64_t d = 0; d < len && eq; ++d)
+                    eq = same_seg(s, r.seg_begin + d, q.seg_begin + d);
+                if (eq) { found = cid; break; }
+            }
+            if (found < 0) {
+                found = s->n_content++;
+                s->content_first.push_back((int64_t)i);
+                s->content_count.push_back(0);
+                by_hash[h].push_back(found);
+            }
+            q.content = found;
+            s->content_count[found]++;
+        }
+    }
+    s->n_samples = smp;
+    // device waveforms of every distinct with-RF content
+    mrsim_seq *dev = s;
+    s->rf_f.resize(s->n_content);
+    s->rf_d.resize(s->n_content);
+    dev->rf_off.resize(s->n_content);
+    s->content_steps.assign(s->n_content, 0);
+    for (int cid = 0; cid < s->n_content; ++cid) {
+        const Subseq &q = s->sub[s->content_first[cid]];
+        const int64_t len = q.seg_end - q.seg_begin;
+        std::vector<RFSegF> f(len);
+        std::vector<RFSegD> d(len);
+        std::vector<int64_t> off(len + 1, 0);
+        for (int64_t t = 0; t < len; ++t) {
+            const int64_t j = q.seg_begin + t;
+            const double dt = s->dt[j];
+            d[t] = RFSegD{kGamma * s->b1re[j] * dt, kGamma * s->b1im[j] * dt, kGamma * s->gx[j] * dt,
+                          kGamma * s->gy[j] * dt, kGamma * s->gz[j] * dt, kTwoPi * dt, dt,
+                          (long long)s->rep[j]};
+            f[t] = RFSegF{(float)d[t].are, (float)d[t].aim, (float)d[t].cx, (float)d[t].cy,
+                          (float)d[t].cz, (float)d[t].cdw, (float)dt, s->rep[j]};
+            off[t + 1] = off[t] + s->rep[j];
+        }
+        s->content_steps[cid] = off[len];
+        s->rf_f[cid] = dalloc(len * sizeof(RFSegF));
+        s->rf_d[cid] = dalloc(len * sizeof(RFSegD));
+        dev->rf_off[cid] = dalloc((len + 1) * sizeof(int64_t));
+        upload(c, s->rf_f[cid].p, f.data(), len * sizeof(RFSegF));
+        upload(c, s->rf_d[cid].p, d.data(), len * sizeof(RFSegD));
+        upload(c, dev->rf_off[cid].p, off.data(), (len + 1) * sizeof(int64_t));
+    }
+    // ADC segments and per-sample window-relative (tau, k)
+    std::vector<ADCSegF> af;
+    std::vector<ADCSegD> ad;
+    std::vector<GSampleF> gf(std::max<int64_t>(smp, 1));
+    std::vector<GSampleD> gd(std::max<int64_t>(smp, 1));
+    dev->adc_off.assign(s->sub.size(), -1);
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        const Subseq &q = s->sub[i];
+        if (q.type != SUB_ADC) continue;
+        dev->adc_off[i] = (int64_t)af.size();
+        double tau = 0.0, m[3] = {0, 0, 0};
+        int64_t si = q.sample0;
+        const int ax = q.gtype == G_X ? 0 : q.gtype == G_Y ? 1 : q.gtype == G_Z ? 2 : -1;
+        for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
+            const double dt = s->dt[j];
+            const double g[3] = {(double)s->gx[j], (double)s->gy[j], (double)s->gz[j]};
+            ADCSegD sd{kGammaBar * g[0] * dt, kGammaBar * g[1] * dt, kGammaBar * g[2] * dt, dt,
+                       (long long)s->rep[j]};
+            ad.push_back(sd);
+            ADCSegF sf;
+            auto sp = [](double v, float &hi, float &lo) { hi = (float)v; lo = (float)(v - (double)hi); };
+            sp(sd.kx, sf.kx_hi, sf.kx_lo);
+            sp(sd.ky, sf.ky_hi, sf.ky_lo);
+            sp(sd.kz, sf.kz_hi, sf.kz_lo);
+            sf.dt = (float)dt;
+            sf.rep = s->rep[j];
+            af.push_back(sf);
+            if (s->adc[j]) {
+                for (int32_t r = 0; r < s->rep[j]; ++r, ++si) {
+                    const double ts = tau + (r + 1) * dt;
+                    const double ks = ax >= 0 ? kGammaBar * (m[ax] + g[ax] * (r + 1) * dt) : 0.0;
+                    gd[si] = GSampleD{ts, ks};
+                    GSampleF f;
+                    sp(ts, f.tau_hi, f.tau_lo);
+                    sp(ks, f.k_hi, f.k_lo);
+                    gf[si] = f;
+                }
+            }
+            tau += dt * s->rep[j];
+            for (int a = 0; a < 3; ++a) m[a] += g[a] * dt * s->rep[j];
+        }
+    }
+    if (!af.empty()) {
+        dev->adc_f = dalloc(af.size() * sizeof(ADCSegF));
+        dev->adc_d = dalloc(ad.size() * sizeof(ADCSegD));
+        upload(c, dev->adc_f.p, af.data(), af.size() * sizeof(ADCSegF));
+        upload(c, dev->adc_d.p, ad.data(), ad.size() * sizeof(ADCSegD));
+    }
+    dev->gs_f = dalloc(gf.size() * sizeof(GSampleF));
+    dev->gs_d = dalloc(gd.size() * sizeof(GSampleD));
+    upload(c, dev->gs_f.p, gf.data(), gf.size() * sizeof(GSampleF));
+    upload(c, dev->gs_d.p, gd.data(), gd.size() * sizeof(GSampleD));
+    sync(c);
+}
+
+PlainState plain_state(const mrsim_phantom_t *ph, void *Mx, void *My, void *Mz) {
+    return PlainState{ph->K, ph->x.as<float>(), ph->y.as<float>(), ph->z.as<float>(),
+                      ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
+                      ph->M0.as<float>(), ph->has_b1 ? ph->b1.as<float>() : nullptr, Mx, My, Mz};
+}
+
+PlainState sorted_state(const mrsim_groups *g, void *Mx, void *My, void *Mz) {
+    return PlainState{g->K, g->x.as<float>(), g->y.as<float>(), g->z.as<float>(),
+                      g->T1.as<float>(), g->T2.as<float>(), g->dB0.as<float>(),
+                      g->M0.as<float>(), g->has_b1 ? g->b1.as<float>() : nullptr, Mx, My, Mz};
+}
+
+// ---------------------------------------------------------------- plain ----
+template <typename R>
+void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool use_cache,
+               double *d_signal, R *M) {
+    const int64_t K = ph->K;
+    const mrsim_seq &dev = *s;
+    PlainState st = plain_state(ph, M, M + K, M + 2 * K);
+    launch_init_state<R>(c, st, ph->has_M_init ? ph->M_init.as<float>() : nullptr);
+    std::vector<DBuf> cache(s->n_content);
+    double mom[3] = {0, 0, 0}, tau = 0.0;
+    using A = typename AdvOf<R>::T;
+    const bool f64 = sizeof(R) == 8;
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        const Subseq &q = s->sub[i];
+        const A adv = AdvOf<R>::make(mom, tau);
+        if (q.type == SUB_RELAX) {
+            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+            tau += q.dur;
+            continue;
+        }
+        if (q.type == SUB_RF) {
+            const int cid = q.content;
+            const void *segs = f64 ? s->rf_d[cid].p : s->rf_f[cid].p;
+            const int nseg = (int)(q.seg_end - q.seg_begin);
+            if (use_cache && s->content_count[cid] > 1) {
+                if (!cache[cid].p) {
+                    cache[cid] = dalloc(12 * (size_t)K * sizeof(R));
+                    launch_plain_rf_affine<R>(c, st, segs, nseg, cache[cid].as<R>());
+                }
+                launch_apply_affine<R>(c, st, cache[cid].as<R>(), &adv);
+            } else {
+                launch_plain_rf<R>(c, st, segs, nseg, &adv, 2);
+            }
+            mom[0] = mom[1] = mom[2] = 0.0;
+            tau = 0.0;
+        } else {
+            const void *segs = f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[i])
+                                   : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[i]);
+            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &adv,
+                                d_signal + 2 * q.sample0);
+            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+            tau += q.dur;
+        }
+    }
+    const A adv = AdvOf<R>::make(mom, tau);
+    launch_advance<R>(c, st, &adv);
+    sync(c);
+}
+
+// -------------------------------------------------------------- grouped ----
+template <typename R>
+void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
+                 const mrsim_groups *g, double *d_signal, R *M) {
+    const int64_t K = ph->K;
+    const mrsim_seq &dev = *s;
+    const bool f64 = sizeof(R) == 8;
+    using A = typename AdvOf<R>::T;
+    // 1) combined transitions for every (content, gradient type) of a known with-RF
+    std::map<std::pair<int, int>, int64_t> row_of;
+    int64_t rows = 0;
+    for (const Subseq &q : s->sub) {
+        if (q.type != SUB_RF || q.gtype == G_GENERAL) continue;
+        auto key = std::make_pair(q.content, q.gtype);
+        if (!row_of.count(key)) {
+            row_of[key] = rows;
+            rows += g->n_groups[q.gtype];
+        }
+    }
+    R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(rows, 1) * 12 * sizeof(R));
+    for (auto &kv : row_of) {
+        const int cid = kv.first.first, gt = kv.first.second;
+        const Subseq &q = s->sub[s->content_first[cid]];
+        PrecompArgs pa{f64 ? s->rf_d[cid].p : s->rf_f[cid].p, dev.rf_off[cid].as<int64_t>(),
+                       (int)(q.seg_end - q.seg_begin), s->content_steps[cid], gt,
+                       g->n_groups[gt], g->tab[gt].d_par64.as<double>(), T_tab + kv.second * 12};
+        launch_precompute<R>(c, pa);
+    }
+    // 2) block-sum storage per known with-ADC window
+    std::vector<GWin> wins;
+    std::vector<int64_t> win_off(s->sub.size(), -1);
+    int64_t ablk_n = 0;
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        const Subseq &q = s->sub[i];
+        if (q.type != SUB_ADC || q.gtype == G_GENERAL || q.n_samples == 0) continue;
+        win_off[i] = ablk_n;
+        wins.push_back(GWin{q.gtype, (int)g->n_groups[q.gtype], ablk_n, q.sample0,
+                            (int)q.n_samples, 0});
+        ablk_n += g->n_groups[q.gtype];
+    }
+    double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double));
+    MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double),
+                               c->stream));
+    // 3) spans of known-type events; unknown types fall back to plain kernels
+    PlainState st = sorted_state(g, M, M + K, M + 2 * K);
+    bool init_eq = !g->has_M_init;
+    if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+    FusedArgs<R> fa{};
+    fa.K = K;
+    fa.x = g->x.as<float>(); fa.y = g->y.as<float>(); fa.z = g->z.as<float>();
+    fa.T1 = g->T1.as<float>(); fa.T2 = g->T2.as<float>(); fa.dB0 = g->dB0.as<float>();
+    fa.M0 = g->M0.as<float>();
+    for (int t = 0; t < 4; ++t) fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
+    fa.gtype_p = g->primary;
+    fa.gtype_r = g->secondary >= 0 ? g->secondary : g->primary;
+    fa.Mx = M; fa.My = M + K; fa.Mz = M + 2 * K;
+    fa.T_tab = T_tab;
+    fa.Ablk = Ablk;
+    std::vector<FEvent<R>> ev;
+    double mom[3] = {0, 0, 0}, tau = 0.0;
+    auto flush = [&]() {
+        FEvent<R> e{};
+        e.kind = EV_END;
+        e.adv = AdvOf<R>::make(mom, tau);
+        ev.push_back(e);
+        // one event buffer for all spans: uploads are ordered after earlier launches
+        void *b = scratch(c, 11, ev.size() * sizeof(FEvent<R>));
+        upload(c, b, ev.data(), ev.size() * sizeof(FEvent<R>));
+        fa.ev = (const FEvent<R> *)b;
+        fa.n_ev = (int)ev.size();
+        fa.init_eq = init_eq ? 1 : 0;
+        launch_fused<R>(c, fa, 4);
+        ev.clear();
+        init_eq = false;
+        mom[0] = mom[1] = mom[2] = 0.0;
+        tau = 0.0;
+    };
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        const Subseq &q = s->sub[i];
+        if (q.type == SUB_RELAX) {
+            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+            tau += q.dur;
+        } else if (q.type == SUB_RF && q.gtype != G_GENERAL) {
+            FEvent<R> e{};
+            e.kind = EV_RF;
+            e.gtype = q.gtype;
+            e.row = row_of.at(std::make_pair(q.content, q.gtype));
+            e.adv = AdvOf<R>::make(mom, tau);
+            ev.push_back(e);
+            mom[0] = mom[1] = mom[2] = 0.0;
+            tau = 0.0;
+        } else if (q.type == SUB_ADC && q.gtype != G_GENERAL) {
+            if (q.n_samples > 0) {
+                FEvent<R> e{};
+                e.kind = EV_ADC;
+                e.gtype = q.gtype;
+                e.win = win_off[i];
+                e.adv = AdvOf<R>::make(mom, tau);
+                ev.push_back(e);
+            }
+            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+            tau += q.dur;
+        } else if (q.type == SUB_RF) {
+            flush();  // state now at the pulse start
+            const double z0[3] = {0.0, 0.0, 0.0};
+            const A zero = AdvOf<R>::make(z0, 0.0);
+            launch_plain_rf<R>(c, st, f64 ? s->rf_d[q.content].p : s->rf_f[q.content].p,
+                               (int)(q.seg_end - q.seg_begin), &zero, 2);
+        } else {
+            flush();  // state now at the window start
+            const double z0[3] = {0.0, 0.0, 0.0};
+            const A zero = AdvOf<R>::make(z0, 0.0);
+            const void *segs = f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[i])
+                                   : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[i]);
+            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &zero,
+                                d_signal + 2 * q.sample0);
+            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+            tau += q.dur;
+        }
+    }
+    flush();
+    // 4) every sample from the block sums (Eqs. 8, 10)
+    if (!wins.empty()) {
+        int64_t base_blocks = 0;
+        int64_t max_g = 1;
+        for (const GWin &w : wins) {
+            base_blocks += (w.n_samples + 255) / 256;
+            max_g = std::max<int64_t>(max_g, w.n_groups);
+        }
+        const int64_t want = 4LL * c->sm_count;
+        int64_t split = std::max<int64_t>(1, (want + base_blocks - 1) / base_blocks);
+        split = std::min<int64_t>(split, (max_g + 255) / 256);
+        std::vector<int4> blk;
+        for (size_t wi = 0; wi < wins.size(); ++wi) {
+            const GWin &w = wins[wi];
+            const int64_t gs = std::max<int64_t>(256, ((w.n_groups + split - 1) / split + 255) / 256 * 256);
+            for (int64_t s0 = 0; s0 < w.n_samples; s0 += 256)
+                for (int64_t g0 = 0; g0 < w.n_groups; g0 += gs)
+                    blk.push_back(make_int4((int)wi, (int)(w.sample0 + s0), (int)g0,
+                                            (int)std::min<int64_t>(w.n_groups, g0 + gs)));
+        }
+        GWin *dw = (GWin *)scratch(c, 12, wins.size() * sizeof(GWin));
+        int4 *db = (int4 *)scratch(c, 13, blk.size() * sizeof(int4));
+        upload(c, dw, wins.data(), wins.size() * sizeof(GWin));
+        upload(c, db, blk.data(), blk.size() * sizeof(int4));
+        GSigTables<R> tab{};
+        for (int t = 0; t < 4; ++t) {
+            if (!g->built[t]) continue;
+            tab.pos[t] = f64 ? (const R *)g->tab[t].d_pos64.p : (const R *)g->tab[t].d_pos.p;
+            tab.dB0[t] = f64 ? (const R *)g->tab[t].d_dB064.p : (const R *)g->tab[t].d_dB0.p;
+            tab.rT2[t] = f64 ? (const R *)g->tab[t].d_rT264.p : (const R *)g->tab[t].d_rT2.p;
+        }
+        launch_group_signal<R>(c, dw, db, (int)blk.size(),
+                               f64 ? dev.gs_d.p : dev.gs_f.p, tab, Ablk, d_signal);
+        sync(c);
+    } else {
+        sync(c);
+    }
+}
+
+int set_err(mrsim_ctx *c, int code, const std::string &m) {
+    if (c) c->err = m;
+    return code;
+}
+
+template <class F>
+int guard(mrsim_ctx *c, F &&f) {
+    try {
+        f();
+        if (c) c->err.clear();
+        return MRSIM_OK;
+    } catch (const Error &e) {
+        return set_err(c, e.code, e.msg);
+    } catch (const std::bad_alloc &) {
+        return set_err(c, MRSIM_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return set_err(c, MRSIM_EINVAL, e.what());
+    }
+}
+
+int most_frequent(const int cnt[5]) {
+    int best = -1, bc = 0;
+    for (int t = 0; t < 4; ++t)
+        if (cnt[t] > bc) { bc = cnt[t]; best = t; }
+    return best;
+}
+
+}  // namespace
+}  // namespace mrsim
+
+using namespace mrsim;
+
+extern "C" {
+
+int mrsim_create(mrsim_ctx **ctx, int device, void *cuda_stream) {
+    if (!ctx) return MRSIM_EINVAL;
+    *ctx = nullptr;
+    mrsim_ctx *c = nullptr;
+    try {
+        c = new mrsim_ctx();
+    } catch (...) {
+        return MRSIM_ENOMEM;
+    }
+    int rc = guard(c, [&] {
+        int n = 0;
+        MRSIM_CUDA(cudaGetDeviceCount(&n));
+        if (device < 0 || device >= n) fail(MRSIM_EINVAL, "no CUDA device " + std::to_string(device));
+        c->device = device;
+        MRSIM_CUDA(cudaSetDevice(device));
+        MRSIM_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+        } else {
+            MRSIM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        c->dev_err = dalloc(64);
+        MRSIM_CUDA(cudaMemsetAsync(c->dev_err.p, 0, 64, c->stream));
+    });
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    *ctx = c;
+    return MRSIM_OK;
+}
+
+void mrsim_destroy(mrsim_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    prof_flush(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &b : c->scratch) b.reset();
+    c->dev_err.reset();
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *mrsim_last_error(const mrsim_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+int mrsim_phantom(mrsim_ctx *c, int64_t K, const float *x, const float *y, const float *z,
+                  const float *T1, const float *T2, const float *dB0, const float *M0,
+                  const float *b1, const float *M_init, unsigned flags, mrsim_phantom_t **out) {
+    if (!c || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    auto p = std::unique_ptr<mrsim_phantom_t>(new (std::nothrow) mrsim_phantom_t());
+    if (!p) return set_err(c, MRSIM_ENOMEM, "host allocation failed");
+    int rc = guard(c, [&] {
+        if (K <= 0 || K > 0x7fffffffLL) fail(MRSIM_EINVAL, "K must be in [1, 2^31 - 1]");
+        if (!x || !y || !z || !T1 || !T2 || !dB0 || !M0) fail(MRSIM_EINVAL, "NULL phantom array");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        p->ctx = c;
+        p->K = K;
+        p->uid = g_uid++;
+        const cudaMemcpyKind kind = (flags & MRSIM_PTR_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice;
+        auto put = [&](DBuf &d, const float *src, int64_t n) {
+            d = dalloc(n * sizeof(float));
+            MRSIM_CUDA(cudaMemcpyAsync(d.p, src, n * sizeof(float), kind, c->stream));
+        };
+        put(p->x, x, K); put(p->y, y, K); put(p->z, z, K);
+        put(p->T1, T1, K); put(p->T2, T2, K); put(p->dB0, dB0, K); put(p->M0, M0, K);
+        if (b1) { put(p->b1, b1, K); p->has_b1 = true; }
+        if (M_init) { put(p->M_init, M_init, 3 * K); p->has_M_init = true; }
+        int *err = c->dev_err.as<int>();
+        MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+        {
+            KScope ks(c, "validate_phantom");
+            const int blocks = (int)std::min<int64_t>((K + 255) / 256, (int64_t)c->sm_count * 16);
+            k_validate<<<blocks, 256, 0, c->stream>>>(
+                K, p->x.as<float>(), p->y.as<float>(), p->z.as<float>(), p->T1.as<float>(),
+                p->T2.as<float>(), p->dB0.as<float>(), p->M0.as<float>(),
+                p->has_b1 ? p->b1.as<float>() : nullptr,
+                p->has_M_init ? p->M_init.as<float>() : nullptr, err);
+        }
+        int h = 0;
+        MRSIM_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (h) fail(MRSIM_EINVAL, "phantom has a non-finite value or T1/T2 <= 0");
+    });
+    if (rc == MRSIM_OK) *out = p.release();
+    return rc;
+}
+
+int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t *rep,
+                   const float *b1re, const float *b1im, const float *gx, const float *gy,
+                   const float *gz, const uint8_t *adc, mrsim_seq **out) {
+    if (!c || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    auto s = std::unique_ptr<mrsim_seq>(new (std::nothrow) mrsim_seq());
+    if (!s) return set_err(c, MRSIM_ENOMEM, "host allocation failed");
+    int rc = guard(c, [&] {
+        if (n_seg <= 0) fail(MRSIM_EINVAL, "n_seg must be positive");
+        if (!dt || !rep || !b1re || !b1im || !gx || !gy || !gz || !adc)
+            fail(MRSIM_EINVAL, "NULL sequence array");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        s->ctx = c;
+        s->n_seg = n_seg;
+        s->dt.assign(dt, dt + n_seg);
+        s->rep.assign(rep, rep + n_seg);
+        s->b1re.assign(b1re, b1re + n_seg);
+        s->b1im.assign(b1im, b1im + n_seg);
+        s->gx.assign(gx, gx + n_seg);
+        s->gy.assign(gy, gy + n_seg);
+        s->gz.assign(gz, gz + n_seg);
+        s->adc.assign(adc, adc + n_seg);
+        build_sequence(c, s.get());
+    });
+    if (rc == MRSIM_OK) *out = s.release();
+    return rc;
+}
+
+int mrsim_seq_info(const mrsim_seq *s, int64_t *n_subseq, uint8_t *type, uint8_t *gtype,
+                   int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples_total) {
+    if (!s) return MRSIM_EINVAL;
+    if (n_subseq) *n_subseq = (int64_t)s->sub.size();
+    if (n_samples_total) *n_samples_total = s->n_samples;
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        if (type) type[i] = (uint8_t)s->sub[i].type;
+        if (gtype) gtype[i] = (uint8_t)s->sub[i].gtype;
+        if (seg_begin) seg_begin[i] = s->sub[i].seg_begin;
+        if (seg_end) seg_end[i] = s->sub[i].seg_end;
+    }
+    return MRSIM_OK;
+}
+
+int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrsim_groups **out) {
+    if (!c || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    auto g = std::unique_ptr<mrsim_groups>(new (std::nothrow) mrsim_groups());
+    if (!g) return set_err(c, MRSIM_ENOMEM, "host allocation failed");
+    int rc = guard(c, [&] {
+        if (!ph || !s) fail(MRSIM_EINVAL, "NULL phantom or sequence");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        g->ctx = c;
+        g->phantom_uid = ph->uid;
+        g->K = ph->K;
+        int cnt_rf[5] = {0, 0, 0, 0, 0}, cnt_adc[5] = {0, 0, 0, 0, 0};
+        for (const Subseq &q : s->sub) {
+            if (q.type == SUB_RF) cnt_rf[q.gtype]++;
+            if (q.type == SUB_ADC) cnt_adc[q.gtype]++;
+        }
+        const int rf_t = most_frequent(cnt_rf), adc_t = most_frequent(cnt_adc);
+        g->primary = adc_t >= 0 ? adc_t : (rf_t >= 0 ? rf_t : G_NONE);
+        g->secondary = (rf_t >= 0 && rf_t != g->primary) ? rf_t : -1;
+        bool need[4] = {false, false, false, false};
+        for (int t = 0; t < 4; ++t) need[t] = cnt_rf[t] > 0 || cnt_adc[t] > 0;
+        need[g->primary] = true;
+        for (int t = 0; t < 4; ++t) {
+            if (!need[t]) continue;
+            build_group_type(c, ph, t, g->gid_orig[t], g->n_groups[t], g->tab[t]);
+            g->built[t] = true;
+        }
+        build_layout(c, ph, g.get());
+    });
+    if (rc == MRSIM_OK) *out = g.release();
+    return rc;
+}
+
+int mrsim_group_info(const mrsim_groups *g, int gtype, int64_t *n_groups, int32_t *gid) {
+    if (!g || gtype < 0 || gtype > 3 || !g->built[gtype]) return MRSIM_EINVAL;
+    if (n_groups) *n_groups = g->n_groups[gtype];
+    if (gid) {
+        if (cudaMemcpyAsync(gid, g->gid_orig[gtype].p, g->K * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, g->ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(g->ctx->stream) != cudaSuccess)
+            return MRSIM_ECUDA;
+    }
+    return MRSIM_OK;
+}
+
+int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
+              const mrsim_groups *g, int mode, int precision, double *signal, float *M_final,
+              unsigned out_flags) {
+    if (!c) return MRSIM_EINVAL;
+    return guard(c, [&] {
+        if (!ph || !s || !signal) fail(MRSIM_EINVAL, "NULL phantom, sequence or signal");
+        if (precision != MRSIM_FP32 && precision != MRSIM_FP64) fail(MRSIM_EINVAL, "bad precision");
+        if (mode < MRSIM_PLAIN || mode > MRSIM_SURROGATE) fail(MRSIM_EINVAL, "bad mode");
+        const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
+        if (grouped) {
+            if (!g) fail(MRSIM_EINVAL, "grouped mode needs groups");
+            if (g->phantom_uid != ph->uid) fail(MRSIM_ESTATE, "groups belong to another phantom");
+            for (const Subseq &q : s->sub)
+                if ((q.type == SUB_RF || q.type == SUB_ADC) && q.gtype != G_GENERAL &&
+                    !g->built[q.gtype])
+                    fail(MRSIM_ESTATE, "groups lack a gradient type the sequence uses");
+        }
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        const int64_t K = ph->K, ns = s->n_samples;
+        const bool dev_out = (out_flags & MRSIM_OUT_DEVICE) != 0;
+        double *d_sig = dev_out ? signal
+                                : (double *)scratch(c, 8, std::max<int64_t>(ns, 1) * 2 * sizeof(double));
+        MRSIM_CUDA(cudaMemsetAsync(d_sig, 0, std::max<int64_t>(ns, 1) * 2 * sizeof(double), c->stream));
+        const size_t esz = precision == MRSIM_FP64 ? 8 : 4;
+        void *Mst = scratch(c, 9, 3 * K * esz);
+        if (grouped) {
+            if (precision == MRSIM_FP64) run_grouped<double>(c, ph, s, g, d_sig, (double *)Mst);
+            else run_grouped<float>(c, ph, s, g, d_sig, (float *)Mst);
+        } else {
+            const bool cache = mode == MRSIM_PLAIN_CACHE;
+            if (precision == MRSIM_FP64) run_plain<double>(c, ph, s, cache, d_sig, (double *)Mst);
+            else run_plain<float>(c, ph, s, cache, d_sig, (float *)Mst);
+        }
+        if (M_final) {
+            float *d_out = dev_out ? M_final : (float *)scratch(c, 10, 3 * K * sizeof(float));
+            launch_gather_out(c, K, Mst, (char *)Mst + K * esz, (char *)Mst + 2 * K * esz,
+                              esz == 8, grouped ? g->perm.as<int32_t>() : nullptr, d_out);
+            if (!dev_out)
+                MRSIM_CUDA(cudaMemcpyAsync(M_final, d_out, 3 * K * sizeof(float),
+                                           cudaMemcpyDeviceToHost, c->stream));
+            sync(c);
+        }
+        if (!dev_out && ns > 0)
+            MRSIM_CUDA(cudaMemcpyAsync(signal, d_sig, ns * 2 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+    });
+}
+
+int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
+                    const mrsim_seq *const *s, const mrsim_groups *const *g,
+                    double *const *signals) {
+    if (!c) return MRSIM_EINVAL;
+    return guard(c, [&] {
+        if (n_jobs <= 0 || !ph || !s || !g || !signals) fail(MRSIM_EINVAL, "bad batch arguments");
+        for (int i = 0; i < n_jobs; ++i) {
+            if (!ph[i] || !s[i] || !g[i] || !signals[i]) fail(MRSIM_EINVAL, "NULL batch entry");
+            if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
+        }
+        fail(MRSIM_EUNSUPPORTED, "batched launcher not available in this build");
+    });
+}
+
+int mrsim_profile_enable(mrsim_ctx *c, int on) {
+    if (!c) return MRSIM_EINVAL;
+    c->prof_on = on != 0;
+    return MRSIM_OK;
+}
+
+int mrsim_profile_reset(mrsim_ctx *c) {
+    if (!c) return MRSIM_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    prof_flush(c);
+    std::fill(c->prof_count.begin(), c->prof_count.end(), 0);
+    std::fill(c->prof_ms.begin(), c->prof_ms.end(), 0.0);
+    return MRSIM_OK;
+}
+
+int mrsim_profile_get(mrsim_ctx *c, int i, char *name, int cap, int64_t *launches, double *ms) {
+    if (!c || i < 0 || i >= (int)c->prof_names.size()) return MRSIM_EINVAL;
+    if (name && cap > 0) {
+        std::snprintf(name, (size_t)cap, "%s", c->prof_names[i].c_str());
+    }
+    if (launches) *launches = c->prof_count[i];
+    if (ms) *ms = c->prof_ms[i];
+    return MRSIM_OK;
+}
+
+int64_t mrsim_launch_count(const mrsim_ctx *c) { return c ? c->launches : 0; }
+
+void mrsim_free_phantom(mrsim_phantom_t *ph) {
+    if (!ph) return;
+    if (ph->ctx) cudaSetDevice(ph->ctx->device);
+    delete ph;
+}
+
+void mrsim_free_seq(mrsim_seq *s) {
+    if (!s) return;
+    if (s->ctx) cudaSetDevice(s->ctx->device);
+    delete s;
+}
+
+void mrsim_free_groups(mrsim_groups *g) {
+    if (!g) return;
+    if (g->ctx) cudaSetDevice(g->ctx->device);
+    delete g;
+}
+
+}  // extern "C"

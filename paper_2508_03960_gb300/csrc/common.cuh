@@ -1,0 +1,233 @@
+// Plain-data records shared by the host planner and the kernels, and the
+// per-isochromat math used by every kernel (Eqs. 4-5, Eq. A1-A2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrsim {
+
+// 1H gyromagnetic ratio / 2 pi (Hz/T); gamma = 2 pi * kGammaBar rad/s/T.
+constexpr double kGammaBar = 42.577478518e6;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kGamma = kTwoPi * kGammaBar;
+constexpr double kLog2e = 1.4426950408889634073599246810019;
+
+enum SubType : int { SUB_RF = 0, SUB_ADC = 1, SUB_RELAX = 2 };
+enum GType : int { G_NONE = 0, G_X = 1, G_Y = 2, G_Z = 3, G_GENERAL = 4 };
+enum EvKind : int { EV_RF = 0, EV_ADC = 1, EV_END = 2 };
+
+// Free-precession parameters of an advance from the state time t_w to a
+// later time t (Eqs. 4-5): k = gamma_bar * int_{t_w}^{t} G dt (cycles/m per
+// axis) and tau = t - t_w (s).  The FP32 form keeps every double as an
+// unevaluated sum hi + lo of two floats so that phases of hundreds of turns
+// keep ~1e-7-turn accuracy after reduction modulo one turn.
+struct AdvF {
+    float kx_hi, kx_lo, ky_hi, ky_lo, kz_hi, kz_lo, tau_hi, tau_lo;
+};
+struct AdvD {
+    double kx, ky, kz, tau;
+};
+
+// One RF segment: rotation-vector coefficients per sub-step.
+//   phi = -(b1 * are, b1 * aim, cx x + cy y + cz z + cdw dB0)   (radians)
+// with are = gamma B1re dt, cx = gamma gx dt (rad/m), cdw = 2 pi dt (rad/Hz).
+struct RFSegF {
+    float are, aim, cx, cy, cz, cdw, dt;
+    int rep;
+};
+struct RFSegD {
+    double are, aim, cx, cy, cz, cdw, dt;
+    long long rep;
+};
+
+// One ADC segment of a window: per-sub-step moment k = gamma_bar G dt
+// (cycles/m, split), the sub-step length and the number of samples.
+struct ADCSegF {
+    float kx_hi, kx_lo, ky_hi, ky_lo, kz_hi, kz_lo, dt;
+    int rep;
+};
+struct ADCSegD {
+    double kx, ky, kz, dt;
+    long long rep;
+};
+
+// Event of the fused grouped kernel.  RF: advance, then M <- A M + b M0 with
+// the combined transition row `row` of the RF table.  ADC: advance into a
+// register copy and add M_xy into the block sum of window `win` (Eq. 9).
+// END: advance and store the state.
+template <typename R>
+struct FEvent;
+template <>
+struct FEvent<float> {
+    int kind, gtype;
+    long long row;  // RF: first row of the table of this (content, gtype)
+    long long win;  // ADC: offset of this window's block sums (complex entries)
+    AdvF adv;
+};
+template <>
+struct FEvent<double> {
+    int kind, gtype;
+    long long row;
+    long long win;
+    AdvD adv;
+};
+
+// A with-ADC window for the grouped signal kernel (Eqs. 8, 10).
+struct GWin {
+    int gtype;
+    int n_groups;
+    long long ablk;      // offset of the block sums (complex entries)
+    long long sample0;   // first sample (global index)
+    int n_samples;
+    int pad;
+};
+// per-sample time and moment since the window start on the group's axis
+struct GSampleF {
+    float tau_hi, tau_lo, k_hi, k_lo;
+};
+struct GSampleD {
+    double tau, k;
+};
+
+// ------------------------------------------------------------------------
+// device helpers
+// ------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+// fractional part (turns) of a * (hi + lo), a float32 value times a
+// double-length constant: the product a*hi is split exactly with one FMA.
+__device__ __forceinline__ float turns_prod(float a, float hi, float lo) {
+    float p = a * hi;
+    float e = fmaf(a, hi, -p);  // a*hi = p + e exactly
+    float r = p - rintf(p);     // exact for |p| < 2^22
+    return r + fmaf(a, lo, e);
+}
+
+__device__ __forceinline__ float adv_turns(const AdvF &a, float x, float y, float z, float dB0) {
+    return turns_prod(x, a.kx_hi, a.kx_lo) + turns_prod(y, a.ky_hi, a.ky_lo) +
+           turns_prod(z, a.kz_hi, a.kz_lo) + turns_prod(dB0, a.tau_hi, a.tau_lo);
+}
+__device__ __forceinline__ double adv_turns(const AdvD &a, double x, double y, double z,
+                                            double dB0) {
+    double v = x * a.kx + y * a.ky + z * a.kz + dB0 * a.tau;
+    return v - rint(v);
+}
+
+__device__ __forceinline__ float adv_tau(const AdvF &a) { return a.tau_hi + a.tau_lo; }
+__device__ __forceinline__ double adv_tau(const AdvD &a) { return a.tau; }
+
+// exp(-phase) as (cos, sin) of 2 pi * turns
+__device__ __forceinline__ void phasor(float turns, float &c, float &s) {
+    sincospif(2.0f * turns, &s, &c);
+}
+__device__ __forceinline__ void phasor(double turns, double &c, double &s) {
+    sincospi(2.0 * turns, &s, &c);
+}
+
+// exp(-tau / T) with r = log2(e) / T precomputed (r = 0 for T = inf)
+__device__ __forceinline__ float decay(float tau, float r) { return exp2f(-tau * r); }
+__device__ __forceinline__ double decay(double tau, double r) { return exp2(-tau * r); }
+
+// Free precession and relaxation over an advance (Eqs. 4-5):
+//   M_xy <- M_xy exp(-tau/T2) exp(-i 2 pi turns),  Mz <- M0 + (Mz - M0) exp(-tau/T1)
+template <typename R, typename A>
+__device__ __forceinline__ void advance(R &mx, R &my, R &mz, R M0, R x, R y, R z, R dB0, R rT1,
+                                        R rT2, const A &adv) {
+    R c, s;
+    phasor(adv_turns(adv, x, y, z, dB0), c, s);
+    R tau = (R)adv_tau(adv);
+    R E2 = decay(tau, rT2), E1 = decay(tau, rT1);
+    R nx = E2 * (mx * c + my * s);
+    R ny = E2 * (my * c - mx * s);
+    mx = nx;
+    my = ny;
+    mz = M0 + (mz - M0) * E1;
+}
+
+// Transverse part only (for ADC block sums).
+template <typename R, typename A>
+__device__ __forceinline__ void advance_xy(R mx, R my, R x, R y, R z, R dB0, R rT2, const A &adv,
+                                           R &ox, R &oy) {
+    R c, s;
+    phasor(adv_turns(adv, x, y, z, dB0), c, s);
+    R E2 = decay((R)adv_tau(adv), rT2);
+    ox = E2 * (mx * c + my * s);
+    oy = E2 * (my * c - mx * s);
+}
+
+// Rotation coefficients for the vector form of Eq. A2:
+//   R v = v + s (phi x v) + c2 (phi x (phi x v)),  theta^2 = |phi|^2,
+//   s = sin(theta)/theta, c2 = (1 - cos(theta))/theta^2.
+// Both are even in theta: for theta^2 <= 1/4 they come from their Maclaurin
+// series in theta^2 (truncation < 3e-11 in FP32, < 1e-22 in FP64); above that
+// from sin / cos of theta/2.
+__device__ __forceinline__ void rot_coeffs(float th2, float &s, float &c2) {
+    if (th2 <= 0.25f) {
+        s = fmaf(th2, fmaf(th2, fmaf(th2, fmaf(th2, 1.0f / 362880.0f, -1.0f / 5040.0f),
+                                     1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+        c2 = fmaf(th2, fmaf(th2, fmaf(th2, fmaf(th2, 1.0f / 3628800.0f, -1.0f / 40320.0f),
+                                      1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
+    } else {
+        float th = sqrtf(th2), sh, ch;
+        sincosf(0.5f * th, &sh, &ch);
+        s = 2.0f * sh * ch / th;
+        c2 = 2.0f * sh * sh / th2;
+    }
+}
+__device__ __forceinline__ void rot_coeffs(double th2, double &s, double &c2) {
+    if (th2 <= 0.25) {
+        // sum_{n=0}^{8} (-1)^n th2^n / (2n+1)!  and  / (2n+2)!, Horner from n = 8
+        s = 1.0 / 355687428096000.0;              //  1/17!
+        s = fma(th2, s, -1.0 / 1307674368000.0);  // -1/15!
+        s = fma(th2, s, 1.0 / 6227020800.0);      //  1/13!
+        s = fma(th2, s, -1.0 / 39916800.0);       // -1/11!
+        s = fma(th2, s, 1.0 / 362880.0);          //  1/9!
+        s = fma(th2, s, -1.0 / 5040.0);           // -1/7!
+        s = fma(th2, s, 1.0 / 120.0);             //  1/5!
+        s = fma(th2, s, -1.0 / 6.0);              // -1/3!
+        s = fma(th2, s, 1.0);
+        c2 = 1.0 / 6402373705728000.0;            //  1/18!
+        c2 = fma(th2, c2, -1.0 / 20922789888000.0);  // -1/16!
+        c2 = fma(th2, c2, 1.0 / 87178291200.0);      //  1/14!
+        c2 = fma(th2, c2, -1.0 / 479001600.0);       // -1/12!
+        c2 = fma(th2, c2, 1.0 / 3628800.0);          //  1/10!
+        c2 = fma(th2, c2, -1.0 / 40320.0);           // -1/8!
+        c2 = fma(th2, c2, 1.0 / 720.0);              //  1/6!
+        c2 = fma(th2, c2, -1.0 / 24.0);              // -1/4!
+        c2 = fma(th2, c2, 0.5);                      //  1/2!
+    } else {
+        double th = sqrt(th2), sh, ch;
+        sincos(0.5 * th, &sh, &ch);
+        s = 2.0 * sh * ch / th;
+        c2 = 2.0 * sh * sh / th2;
+    }
+}
+
+// One RF sub-step on a magnetization vector: M <- D R M (App. A).
+// em1 = expm1(-dt/T1), em2 = expm1(-dt/T2) so that relaxation adds small
+// increments instead of multiplying by factors close to one.
+template <typename R>
+__device__ __forceinline__ void rf_step(R &mx, R &my, R &mz, R M0, R px, R py, R pz, R em1,
+                                        R em2) {
+    R th2 = px * px + py * py + pz * pz;
+    R s, c2;
+    rot_coeffs(th2, s, c2);
+    // q = phi x M ; M += s q + c2 (phi x q)
+    R qx = py * mz - pz * my;
+    R qy = pz * mx - px * mz;
+    R qz = px * my - py * mx;
+    R wx = py * qz - pz * qy;
+    R wy = pz * qx - px * qz;
+    R wz = px * qy - py * qx;
+    mx += s * qx + c2 * wx;
+    my += s * qy + c2 * wy;
+    mz += s * qz + c2 * wz;
+    mx += mx * em2;
+    my += my * em2;
+    mz -= (M0 - mz) * em1;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace mrsim

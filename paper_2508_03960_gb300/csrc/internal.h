@@ -1,0 +1,232 @@
+// Host-side objects behind the C ABI handles, device buffers and the launch
+// scope that counts kernels and (optionally) times them with CUDA events.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "common.cuh"
+
+namespace mrsim {
+
+// Owned device allocation.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) { reset(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Error carrying a status code and message; thrown inside the library,
+// caught at every ABI entry point.
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what);
+#define MRSIM_CUDA(call) ::mrsim::cuda_check((call), #call)
+
+}  // namespace mrsim
+
+struct mrsim_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int64_t launches = 0;
+    // profiling
+    bool prof_on = false;
+    std::vector<std::string> prof_names;
+    std::vector<int64_t> prof_count;
+    std::vector<double> prof_ms;
+    struct Pending { int id; cudaEvent_t a, b; };
+    std::vector<Pending> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    // growable scratch areas reused across calls
+    mrsim::DBuf scratch[16];
+    // error word written by kernels with bounded waits / bounds checks
+    mrsim::DBuf dev_err;
+    // pinned host staging for uploads of per-run plans
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+};
+
+struct mrsim_phantom_t {
+    mrsim_ctx *ctx = nullptr;
+    int64_t K = 0;
+    uint64_t uid = 0;
+    mrsim::DBuf x, y, z, T1, T2, dB0, M0, b1, M_init;  // b1 / M_init may be empty
+    bool has_b1 = false, has_M_init = false;
+};
+
+namespace mrsim {
+
+struct Subseq {
+    int type = SUB_RELAX, gtype = G_NONE;
+    int64_t seg_begin = 0, seg_end = 0;
+    int64_t n_samples = 0, sample0 = 0;
+    int content = -1;       // with-RF: content id (exact equality of segments)
+    double dur = 0.0;       // seconds
+    double mom[3] = {0, 0, 0};  // int G dt over the subsequence (T s / m)
+};
+
+struct GroupTable {
+    int64_t n = 0;
+    std::vector<double> pos, T1, T2, dB0, b1;  // host copies
+    DBuf d_par64;                    // [5][n] doubles: pos, T1, T2, dB0, b1 (precompute)
+    DBuf d_pos, d_dB0, d_rT2;        // float copies for the group-signal kernel
+    DBuf d_pos64, d_dB064, d_rT264;  // double copies for the group-signal kernel
+};
+
+}  // namespace mrsim
+
+struct mrsim_seq {
+    mrsim_ctx *ctx = nullptr;
+    int64_t n_seg = 0;
+    std::vector<double> dt;
+    std::vector<int32_t> rep;
+    std::vector<float> b1re, b1im, gx, gy, gz;
+    std::vector<uint8_t> adc;
+    std::vector<mrsim::Subseq> sub;
+    int64_t n_samples = 0;
+    int n_content = 0;
+    std::vector<int64_t> content_first;  // first subsequence of each content
+    std::vector<int64_t> content_count;
+    std::vector<int64_t> content_steps;  // sub-steps per content
+    // device RF waveforms per content and their sub-step offsets [n_seg + 1]
+    std::vector<mrsim::DBuf> rf_f, rf_d, rf_off;
+    // ADC segments of every window (concatenated) and each subsequence's first one
+    mrsim::DBuf adc_f, adc_d;
+    std::vector<int64_t> adc_off;
+    // per-sample (tau, k) since the start of its window, on the window's axis
+    mrsim::DBuf gs_f, gs_d;
+};
+
+struct mrsim_groups {
+    mrsim_ctx *ctx = nullptr;
+    uint64_t phantom_uid = 0;
+    int64_t K = 0;
+    bool built[4] = {false, false, false, false};
+    int64_t n_groups[4] = {0, 0, 0, 0};
+    mrsim::DBuf gid_orig[4];    // int32 [K], phantom order
+    mrsim::DBuf gid_sorted[4];  // int32 [K], layout order
+    mrsim::GroupTable tab[4];
+    int primary = -1, secondary = -1;  // layout keys (gradient types)
+    int64_t n_cells = 0;
+    mrsim::DBuf perm;  // int32 [K]: layout position -> phantom index
+    mrsim::DBuf x, y, z, T1, T2, dB0, M0, b1, M_init;  // layout order
+    bool has_b1 = false, has_M_init = false;
+};
+
+namespace mrsim {
+
+// Counts a kernel launch and brackets it with events when profiling is on.
+struct KScope {
+    mrsim_ctx *c;
+    int id = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KScope(mrsim_ctx *ctx, const char *name);
+    ~KScope();
+};
+
+// after a synchronize: fold pending event pairs into the per-kernel totals
+void prof_flush(mrsim_ctx *c);
+
+// scratch area `slot` of at least `bytes` bytes (grows, contents undefined)
+void *scratch(mrsim_ctx *c, int slot, size_t bytes);
+DBuf dalloc(size_t bytes);
+void upload(mrsim_ctx *c, void *dst, const void *src, size_t bytes);
+void sync(mrsim_ctx *c);
+
+// ---- group builder (k_group.cu) ----
+void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
+                      int64_t &n_groups, GroupTable &tab);
+void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
+
+// ---- plain path (k_plain.cu) ----
+struct PlainState {
+    int64_t K;
+    const float *x, *y, *z, *T1, *T2, *dB0, *M0, *b1;  // b1 may be null
+    void *Mx, *My, *Mz;  // R arrays
+};
+template <typename R>
+void launch_init_state(mrsim_ctx *c, const PlainState &s, const float *M_init);
+template <typename R>
+void launch_plain_rf(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
+                     const void *adv, int ni);
+template <typename R>
+void launch_plain_adc(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
+                      int64_t n_samples, const void *adv, double *signal);
+template <typename R>
+void launch_advance(mrsim_ctx *c, const PlainState &s, const void *adv);
+template <typename R>
+void launch_plain_rf_affine(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
+                            R *cache);
+template <typename R>
+void launch_apply_affine(mrsim_ctx *c, const PlainState &s, const R *cache, const void *adv);
+void launch_gather_out(mrsim_ctx *c, int64_t K, const void *Mx, const void *My, const void *Mz,
+                       bool fp64, const int32_t *perm, float *out);
+
+// ---- grouped path (k_grouped.cu) ----
+struct PrecompArgs {
+    const void *segs;        // RFSegF / RFSegD of one with-RF content
+    const int64_t *seg_off;  // [n_seg + 1] first sub-step of each segment
+    int n_seg;
+    int64_t n_steps;
+    int gtype;
+    int64_t n_groups;
+    const double *par;       // [5][n_groups]: pos, T1, T2, dB0, b1
+    void *out;               // R [n_groups][12]
+};
+template <typename R>
+void launch_precompute(mrsim_ctx *c, const PrecompArgs &a);
+
+template <typename R>
+struct FusedArgs {
+    int64_t K;
+    const float *x, *y, *z, *T1, *T2, *dB0, *M0;
+    const int32_t *gid[4];   // layout-order gids per gradient type (null if not built)
+    int gtype_p, gtype_r;    // ADC-sorted type, preferred RF type (-1: none)
+    R *Mx, *My, *Mz;
+    int init_eq;
+    const FEvent<R> *ev;
+    int n_ev;
+    const R *T_tab;
+    double *Ablk;            // complex block sums (interleaved re, im)
+};
+template <typename R>
+void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni);
+
+template <typename R>
+struct GSigTables {
+    const R *pos[4], *dB0[4], *rT2[4];
+};
+template <typename R>
+void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int n_blk,
+                         const void *d_samples, const GSigTables<R> &tab, const double *Ablk,
+                         double *signal);
+
+}  // namespace mrsim

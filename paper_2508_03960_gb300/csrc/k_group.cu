@@ -1,0 +1,475 @@
+// Group builder (Sec. 2.4, Fig. 2): isochromats whose grouping keys are bit
+// equal share a group; groups are numbered by first occurrence in isochromat
+// index order.  Device hash table keyed by the key words; each slot keeps the
+// smallest member index (the representative); representatives are ranked by a
+// prefix sum over "is representative" flags, which yields the first-occurrence
+// numbering directly.
+//
+// The same primitive groups (with-ADC gid, with-RF gid) pairs into cells to
+// lay the isochromats out sorted by (ADC group, RF group): contiguous runs of
+// one ADC group make the block sums of Eq. 9 a segmented reduction, and runs
+// of one RF group make the combined-transition lookups warp-uniform.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "internal.h"
+
+namespace mrsim {
+
+namespace {
+
+constexpr int kErrNaN = 1;
+constexpr int kErrTableFull = 2;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xbf58476d1ce4e5b9ull;
+    z ^= z >> 27;
+    z *= 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return z;
+}
+
+// Grouping key of one gradient type: (r_axis, T1, T2, dB0, b1) as float32
+// bit patterns, -0 folded to +0.  No-grads uses 0 for the position word; a
+// phantom without b1 uses 1.0f for it.
+struct PhantomKey {
+    static constexpr int W = 5;
+    const float *pos, *T1, *T2, *dB0, *b1;
+    __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
+        float v[W] = {pos ? pos[k] : 0.0f, T1[k], T2[k], dB0[k], b1 ? b1[k] : 1.0f};
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            ok &= !isnan(v[i]);
+            if (v[i] == 0.0f) v[i] = 0.0f;
+            w[i] = __float_as_uint(v[i]);
+        }
+        return ok;
+    }
+};
+
+// (gid_a, gid_b) pair key for the layout cells.
+struct PairKey {
+    static constexpr int W = 2;
+    const int32_t *a, *b;
+    __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
+        w[0] = (uint32_t)a[k];
+        w[1] = b ? (uint32_t)b[k] : 0u;
+        return true;
+    }
+};
+
+template <class KF>
+__global__ void k_hash_insert(int64_t K, KF kf, int32_t *owner, int32_t *minidx,
+                              int32_t *slot_of, uint32_t mask, int *err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w[KF::W];
+        if (!kf.words(k, w)) {
+            atomicOr(err, kErrNaN);
+            slot_of[k] = 0;
+            continue;
+        }
+        uint64_t h = 0x9e3779b97f4a7c15ull;
+#pragma unroll
+        for (int i = 0; i < KF::W; ++i) h = mix64(h ^ (uint64_t)w[i] ^ ((uint64_t)i << 40));
+        uint32_t s = (uint32_t)h & mask;
+        // bounded linear probing: at most mask + 1 slots are visited
+        for (uint32_t probes = 0;; ++probes) {
+            if (probes > mask) {
+                atomicOr(err, kErrTableFull);
+                slot_of[k] = 0;
+                break;
+            }
+            int32_t o = __ldcg(&owner[s]);
+            if (o < 0) {
+                int32_t prev = atomicCAS(&owner[s], -1, (int32_t)k);
+                if (prev < 0) {
+                    atomicMin(&minidx[s], (int32_t)k);
+                    slot_of[k] = (int32_t)s;
+                    break;
+                }
+                o = prev;
+            }
+            uint32_t w2[KF::W];
+            kf.words(o, w2);
+            bool eq = true;
+#pragma unroll
+            for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
+            if (eq) {
+                if ((int32_t)k < __ldcg(&minidx[s])) atomicMin(&minidx[s], (int32_t)k);
+                slot_of[k] = (int32_t)s;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+    }
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_rep_flag(int64_t K, const int32_t *slot_of, const int32_t *minidx,
+                           int32_t *flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = (minidx[slot_of[k]] == (int32_t)k) ? 1 : 0;
+}
+
+__global__ void k_assign(int64_t K, const int32_t *slot_of, const int32_t *minidx,
+                         const int32_t *rank, int32_t *gid) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        gid[k] = rank[minidx[slot_of[k]]];
+}
+
+// ---- exclusive prefix sum of int32 flags (three passes) ----
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t &total) {
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    int64_t off = 0;
+    total = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < wid) off += warp_tot[w];
+        total += warp_tot[w];
+    }
+    __syncthreads();
+    return off + x - v;
+}
+
+__global__ void k_scan_tiles(const int32_t *in, int64_t n, int64_t *tile_sum) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile;
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + threadIdx.x * kScanItems + i;
+        if (idx < n) s += in[idx];
+    }
+    int64_t tot;
+    block_exclusive_scan(s, tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tile_sums(int64_t *tile_sum, int64_t nt) {
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nt; base += kScanThreads) {
+        int64_t idx = base + threadIdx.x;
+        int64_t v = idx < nt ? tile_sum[idx] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan(v, tot);
+        if (idx < nt) tile_sum[idx] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_apply(const int32_t *in, int64_t n, const int64_t *tile_off,
+                             int32_t *out) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile;
+    int32_t v[kScanItems];
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + threadIdx.x * kScanItems + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(s, tot) + tile_off[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + threadIdx.x * kScanItems + i;
+        if (idx < n) out[idx] = (int32_t)ex;
+        ex += v[i];
+    }
+}
+
+// per-group parameters from the representatives
+__global__ void k_group_table(int64_t K, const int32_t *flag, const int32_t *rank,
+                              const float *pos, const float *T1, const float *T2,
+                              const float *dB0, const float *b1, double *o_pos, double *o_T1,
+                              double *o_T2, double *o_dB0, double *o_b1) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        int32_t g = rank[k];
+        o_pos[g] = pos ? (double)pos[k] : 0.0;
+        o_T1[g] = T1[k];
+        o_T2[g] = T2[k];
+        o_dB0[g] = dB0[k];
+        o_b1[g] = b1 ? (double)b1[k] : 1.0;
+    }
+}
+
+__global__ void k_cell_table(int64_t K, const int32_t *flag, const int32_t *rank,
+                             const int32_t *ga, const int32_t *gb, int32_t *oa, int32_t *ob) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        int32_t g = rank[k];
+        oa[g] = ga[k];
+        ob[g] = gb ? gb[k] : 0;
+    }
+}
+
+// warp-aggregated atomic add of 1 per element on counter[key]; returns the
+// element's slot (old value + rank among same-key lanes)
+__device__ __forceinline__ int32_t warp_agg_inc(int32_t *counter, int32_t key, bool active) {
+    unsigned am = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    unsigned peers = __match_any_sync(am, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(&counter[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void k_count(int64_t K, const int32_t *key, int32_t *count) {
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < K;
+         k0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = k0 + threadIdx.x;
+        bool act = k < K;
+        warp_agg_inc(count, act ? key[k] : 0, act);
+    }
+}
+
+__global__ void k_scatter(int64_t K, const int32_t *cell, const int32_t *cell_off,
+                          int32_t *cursor, int32_t *perm) {
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < K;
+         k0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = k0 + threadIdx.x;
+        bool act = k < K;
+        int32_t c = act ? cell[k] : 0;
+        int32_t r = warp_agg_inc(cursor, c, act);
+        if (act) perm[cell_off[c] + r] = (int32_t)k;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int64_t K, const int32_t *perm, const T *in, T *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+int grid_for(mrsim_ctx *c, int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)c->sm_count * 16;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Hash-group K elements; writes rank-of-representative gid[K] and returns the
+// group count.  flag/rank stay in scratch slots 2/3 for table extraction.
+template <class KF>
+int64_t hash_group(mrsim_ctx *c, int64_t K, const KF &kf, int32_t *gid, int32_t **flag_out,
+                   int32_t **rank_out) {
+    uint64_t C = 1024;
+    while (C < (uint64_t)(2 * K)) C <<= 1;
+    if (C > (1ull << 31)) fail(MRSIM_EINVAL, "too many isochromats for the group hash table");
+    int32_t *owner = (int32_t *)scratch(c, 0, C * sizeof(int32_t));
+    int32_t *minidx = (int32_t *)scratch(c, 1, C * sizeof(int32_t));
+    int32_t *flag = (int32_t *)scratch(c, 2, K * sizeof(int32_t));
+    int32_t *rank = (int32_t *)scratch(c, 3, K * sizeof(int32_t));
+    int32_t *slot_of = (int32_t *)scratch(c, 4, K * sizeof(int32_t));
+    int64_t nt = (K + kScanTile - 1) / kScanTile;
+    int64_t *tsum = (int64_t *)scratch(c, 5, nt * sizeof(int64_t));
+    int *err = c->dev_err.as<int>();
+    MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+    MRSIM_CUDA(cudaMemsetAsync(owner, 0xff, C * sizeof(int32_t), c->stream));
+    {
+        KScope ks(c, "group_fill");
+        k_fill_i32<<<grid_for(c, C), 256, 0, c->stream>>>(minidx, C, 0x7fffffff);
+    }
+    {
+        KScope ks(c, "group_hash_insert");
+        k_hash_insert<<<grid_for(c, K), 256, 0, c->stream>>>(K, kf, owner, minidx, slot_of,
+                                                            (uint32_t)(C - 1), err);
+    }
+    {
+        KScope ks(c, "group_rep_flag");
+        k_rep_flag<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, flag);
+    }
+    {
+        KScope ks(c, "scan_tiles");
+        k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum);
+    }
+    {
+        KScope ks(c, "scan_tile_sums");
+        k_scan_tile_sums<<<1, kScanThreads, 0, c->stream>>>(tsum, nt);
+    }
+    {
+        KScope ks(c, "scan_apply");
+        k_scan_apply<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum, rank);
+    }
+    {
+        KScope ks(c, "group_assign");
+        k_assign<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, rank, gid);
+    }
+    int h_err = 0;
+    int32_t last[2] = {0, 0};
+    MRSIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MRSIM_CUDA(cudaMemcpyAsync(&last[0], rank + (K - 1), sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c->stream));
+    MRSIM_CUDA(cudaMemcpyAsync(&last[1], flag + (K - 1), sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c->stream));
+    sync(c);
+    if (h_err & kErrNaN) fail(MRSIM_EINVAL, "NaN in a grouping key");
+    if (h_err & kErrTableFull) fail(MRSIM_ECUDA, "group hash table overflow");
+    *flag_out = flag;
+    *rank_out = rank;
+    return (int64_t)last[0] + last[1];
+}
+
+}  // namespace
+
+void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
+                      int64_t &n_groups, GroupTable &tab) {
+    const int64_t K = ph->K;
+    const float *pos = gtype == G_X ? ph->x.as<float>()
+                     : gtype == G_Y ? ph->y.as<float>()
+                     : gtype == G_Z ? ph->z.as<float>()
+                                    : nullptr;
+    PhantomKey kf{pos, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
+                  ph->has_b1 ? ph->b1.as<float>() : nullptr};
+    gid = dalloc(K * sizeof(int32_t));
+    int32_t *flag, *rank;
+    n_groups = hash_group(c, K, kf, gid.as<int32_t>(), &flag, &rank);
+    const int64_t G = n_groups;
+    DBuf t = dalloc(5 * G * sizeof(double));
+    double *tp = t.as<double>();
+    {
+        KScope ks(c, "group_table");
+        k_group_table<<<grid_for(c, K), 256, 0, c->stream>>>(
+            K, flag, rank, pos, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
+            ph->has_b1 ? ph->b1.as<float>() : nullptr, tp, tp + G, tp + 2 * G, tp + 3 * G,
+            tp + 4 * G);
+    }
+    std::vector<double> h(5 * G);
+    MRSIM_CUDA(cudaMemcpyAsync(h.data(), tp, 5 * G * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    sync(c);
+    tab.n = G;
+    tab.pos.assign(h.begin(), h.begin() + G);
+    tab.T1.assign(h.begin() + G, h.begin() + 2 * G);
+    tab.T2.assign(h.begin() + 2 * G, h.begin() + 3 * G);
+    tab.dB0.assign(h.begin() + 3 * G, h.begin() + 4 * G);
+    tab.b1.assign(h.begin() + 4 * G, h.begin() + 5 * G);
+    // device copies used by the precompute and group-signal kernels
+    std::vector<float> fpos(G), fdB0(G), frT2(G);
+    std::vector<double> rT2d(G);
+    for (int64_t g = 0; g < G; ++g) {
+        fpos[g] = (float)tab.pos[g];
+        fdB0[g] = (float)tab.dB0[g];
+        rT2d[g] = std::isinf(tab.T2[g]) ? 0.0 : kLog2e / tab.T2[g];
+        frT2[g] = (float)rT2d[g];
+    }
+    auto up = [&](DBuf &d, const void *src, size_t bytes) {
+        d = dalloc(bytes);
+        upload(c, d.p, src, bytes);
+    };
+    up(tab.d_pos, fpos.data(), G * 4);
+    up(tab.d_dB0, fdB0.data(), G * 4);
+    up(tab.d_rT2, frT2.data(), G * 4);
+    up(tab.d_pos64, tab.pos.data(), G * 8);
+    up(tab.d_dB064, tab.dB0.data(), G * 8);
+    up(tab.d_rT264, rT2d.data(), G * 8);
+    // FP64 parameter block (pos, T1, T2, dB0, b1) for the precompute kernel
+    tab.d_par64 = std::move(t);
+}
+
+void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
+    const int64_t K = ph->K;
+    const int p = g->primary, s = g->secondary;
+    PairKey kf{g->gid_orig[p].as<int32_t>(), s >= 0 ? g->gid_orig[s].as<int32_t>() : nullptr};
+    DBuf cell = dalloc(K * sizeof(int32_t));
+    int32_t *flag, *rank;
+    const int64_t nc = hash_group(c, K, kf, cell.as<int32_t>(), &flag, &rank);
+    g->n_cells = nc;
+    DBuf ca = dalloc(nc * sizeof(int32_t)), cb = dalloc(nc * sizeof(int32_t));
+    DBuf cnt = dalloc(nc * sizeof(int32_t));
+    {
+        KScope ks(c, "layout_cell_table");
+        k_cell_table<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, kf.a, kf.b,
+                                                            ca.as<int32_t>(), cb.as<int32_t>());
+    }
+    MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
+    {
+        KScope ks(c, "layout_count");
+        k_count<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), cnt.as<int32_t>());
+    }
+    std::vector<int32_t> ha(nc), hb(nc), hc(nc);
+    MRSIM_CUDA(cudaMemcpyAsync(ha.data(), ca.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    MRSIM_CUDA(cudaMemcpyAsync(hb.data(), cb.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    MRSIM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    std::vector<int32_t> order(nc);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int32_t u, int32_t v) {
+        return ha[u] != ha[v] ? ha[u] < ha[v] : hb[u] < hb[v];
+    });
+    std::vector<int32_t> off(nc);
+    int64_t run = 0;
+    for (int64_t i = 0; i < nc; ++i) {
+        off[order[i]] = (int32_t)run;
+        run += hc[order[i]];
+    }
+    DBuf doff = dalloc(nc * sizeof(int32_t));
+    upload(c, doff.p, off.data(), nc * 4);
+    MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
+    g->perm = dalloc(K * sizeof(int32_t));
+    {
+        KScope ks(c, "layout_scatter");
+        k_scatter<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), doff.as<int32_t>(),
+                                                         cnt.as<int32_t>(), g->perm.as<int32_t>());
+    }
+    const int32_t *perm = g->perm.as<int32_t>();
+    auto gather_f = [&](DBuf &dst, const DBuf &src) {
+        dst = dalloc(K * sizeof(float));
+        KScope ks(c, "layout_gather");
+        k_gather<float><<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, src.as<float>(),
+                                                               dst.as<float>());
+    };
+    gather_f(g->x, ph->x);
+    gather_f(g->y, ph->y);
+    gather_f(g->z, ph->z);
+    gather_f(g->T1, ph->T1);
+    gather_f(g->T2, ph->T2);
+    gather_f(g->dB0, ph->dB0);
+    gather_f(g->M0, ph->M0);
+    g->has_b1 = ph->has_b1;
+    if (ph->has_b1) gather_f(g->b1, ph->b1);
+    g->has_M_init = ph->has_M_init;
+    if (ph->has_M_init) {
+        g->M_init = dalloc(3 * K * sizeof(float));
+        for (int r = 0; r < 3; ++r) {
+            KScope ks(c, "layout_gather");
+            k_gather<float><<<grid_for(c, K), 256, 0, c->stream>>>(
+                K, perm, ph->M_init.as<float>() + r * K, g->M_init.as<float>() + r * K);
+        }
+    }
+    for (int t = 0; t < 4; ++t) {
+        if (!g->built[t]) continue;
+        g->gid_sorted[t] = dalloc(K * sizeof(int32_t));
+        KScope ks(c, "layout_gather");
+        k_gather<int32_t><<<grid_for(c, K), 256, 0, c->stream>>>(
+            K, perm, g->gid_orig[t].as<int32_t>(), g->gid_sorted[t].as<int32_t>());
+    }
+    sync(c);
+}
+
+}  // namespace mrsim

@@ -1,0 +1,435 @@
+// Grouped-isochromat kernels (Sec. 2.3).
+//
+//  k_precompute   preparation step once per group (Sec. 2.3): the combined
+//                 transition T_g = U_{N-1} ... U_0 (Eq. 7) of one with-RF
+//                 content for every group.  One CTA per group; its threads
+//                 compose contiguous chunks of sub-steps and the chunk
+//                 products are combined by an ordered tree (composition is
+//                 associative, not commutative).  Each step's U - I is formed
+//                 in the run precision (FP32: vector-form rotation, expm1
+//                 relaxation, no loss near identity) and accumulated into an
+//                 FP64 product: T <- T + (U - I) T.
+//  k_fused        the update step of every with-RF subsequence and step 1 of
+//                 every with-ADC subsequence (Eq. 9) of a span of the
+//                 sequence, with each isochromat's M kept in registers from
+//                 the first event to the last.  Between events M is advanced
+//                 in closed form (Eqs. 4-5; relaxation subsequences and ADC
+//                 windows cost nothing extra because those equations compose).
+//                 Isochromats are laid out sorted by their with-ADC group, so
+//                 Eq. 9 becomes a segmented warp reduction plus shared-memory
+//                 accumulation and one FP64 atomic per (CTA, group, window).
+//  k_group_signal step 2 of the with-ADC method (Eqs. 8, 10): every sample is
+//                 the sum over groups of the block sum times the group's
+//                 relaxation and phase since the window start.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace mrsim {
+
+namespace {
+
+constexpr int kPreThreads = 128;
+constexpr int kThreads = 256;
+
+template <typename R>
+struct SegT;
+template <>
+struct SegT<float> { using RF = RFSegF; };
+template <>
+struct SegT<double> { using RF = RFSegD; };
+
+__device__ __forceinline__ void compose(double (&C)[12], const double (&B)[12],
+                                        const double (&A)[12]) {
+    // C = B o A for row-major 3x4 affines (A applied first)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double v = B[4 * r] * A[c] + B[4 * r + 1] * A[4 + c] + B[4 * r + 2] * A[8 + c];
+            if (c == 3) v += B[4 * r + 3];
+            C[4 * r + c] = v;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kPreThreads) k_precompute(const typename SegT<R>::RF *segs,
+                                                            const int64_t *seg_off, int n_seg,
+                                                            int64_t n_steps, int gtype,
+                                                            const double *par, int64_t G,
+                                                            R *out) {
+    using RFS = typename SegT<R>::RF;
+    __shared__ double P[kPreThreads][12];
+    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+        const R pos = (R)par[g], T1 = (R)par[G + g], T2 = (R)par[2 * G + g];
+        const R dB0 = (R)par[3 * G + g], b1 = (R)par[4 * G + g];
+        const R iT1 = isinf((double)T1) ? (R)0 : (R)1 / T1;
+        const R iT2 = isinf((double)T2) ? (R)0 : (R)1 / T2;
+        // this thread's contiguous chunk of sub-steps
+        const int64_t s0 = n_steps * threadIdx.x / kPreThreads;
+        const int64_t s1 = n_steps * (threadIdx.x + 1) / kPreThreads;
+        double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+        if (s1 > s0) {
+            // segment holding step s0 (binary search on the prefix offsets)
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (seg_off[mid] <= s0) lo = mid; else hi = mid - 1;
+            }
+            int j = lo;
+            int64_t st = s0;
+            R dt_prev = (R)-1, em1 = 0, em2 = 0;
+            while (st < s1) {
+                const RFS sg = segs[j];
+                const int64_t seg_end = seg_off[j + 1];
+                const int64_t n_here = min(seg_end, s1) - st;
+                if ((R)sg.dt != dt_prev) {
+                    dt_prev = (R)sg.dt;
+                    em1 = expm1(-dt_prev * iT1);
+                    em2 = expm1(-dt_prev * iT2);
+                }
+                const R cA = gtype == G_X ? (R)sg.cx : gtype == G_Y ? (R)sg.cy
+                           : gtype == G_Z ? (R)sg.cz : (R)0;
+                const R px = -b1 * (R)sg.are, py = -b1 * (R)sg.aim;
+                const R pz = -(cA * pos + (R)sg.cdw * dB0);
+                const R th2 = px * px + py * py + pz * pz;
+                R s, c2;
+                rot_coeffs(th2, s, c2);
+                // U - I = r (1 + d_i) + d_i delta_ij with r = R - I = s[phi]x + c2[phi]x^2
+                const R r00 = -c2 * (py * py + pz * pz), r11 = -c2 * (px * px + pz * pz);
+                const R r22 = -c2 * (px * px + py * py);
+                const R r01 = -s * pz + c2 * px * py, r10 = s * pz + c2 * px * py;
+                const R r02 = s * py + c2 * px * pz, r20 = -s * py + c2 * px * pz;
+                const R r12 = -s * px + c2 * py * pz, r21 = s * px + c2 * py * pz;
+                const R f2 = (R)1 + em2, f1 = (R)1 + em1;
+                const double D[9] = {(double)(r00 * f2 + em2), (double)(r01 * f2), (double)(r02 * f2),
+                                     (double)(r10 * f2), (double)(r11 * f2 + em2), (double)(r12 * f2),
+                                     (double)(r20 * f1), (double)(r21 * f1), (double)(r22 * f1 + em1)};
+                const double bz = -(double)em1;
+                for (int64_t q = 0; q < n_here; ++q) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double v0 = T[c], v1 = T[4 + c], v2 = T[8 + c];
+                        T[c] = v0 + (D[0] * v0 + D[1] * v1 + D[2] * v2);
+                        T[4 + c] = v1 + (D[3] * v0 + D[4] * v1 + D[5] * v2);
+                        T[8 + c] = v2 + (D[6] * v0 + D[7] * v1 + D[8] * v2);
+                    }
+                    T[11] += bz;
+                }
+                st += n_here;
+                ++j;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 12; ++e) P[threadIdx.x][e] = T[e];
+        __syncthreads();
+        // ordered tree: P[t] <- P[t + h] o P[t]
+        for (int h = 1; h < kPreThreads; h <<= 1) {
+            if ((threadIdx.x % (2 * h)) == 0) {
+                double A[12], B[12], C[12];
+#pragma unroll
+                for (int e = 0; e < 12; ++e) {
+                    A[e] = P[threadIdx.x][e];
+                    B[e] = P[threadIdx.x + h][e];
+                }
+                compose(C, B, A);
+#pragma unroll
+                for (int e = 0; e < 12; ++e) P[threadIdx.x][e] = C[e];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < 12) out[g * 12 + threadIdx.x] = (R)P[0][threadIdx.x];
+        __syncthreads();
+    }
+}
+
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> { using T = float4; };
+template <>
+struct Vec4<double> { using T = double2; };
+
+template <typename R>
+__device__ __forceinline__ void load_row(const R *p, R (&T)[12]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+        float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+        T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
+        T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
+        T[8] = c.x; T[9] = c.y; T[10] = c.z; T[11] = c.w;
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double2 v = __ldg(q + i);
+            T[2 * i] = v.x;
+            T[2 * i + 1] = v.y;
+        }
+    }
+}
+
+template <typename R, int NI>
+__global__ void __launch_bounds__(kThreads) k_fused(FusedArgs<R> a) {
+    __shared__ R acc_re[kThreads * NI], acc_im[kThreads * NI];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t chunk = (int64_t)kThreads * NI;
+    const int64_t base = blockIdx.x * chunk;
+    const int64_t last = min(base + chunk, a.K) - 1;
+    const int32_t *gp = a.gtype_p >= 0 ? a.gid[a.gtype_p] : nullptr;
+    const int32_t *gr = a.gtype_r >= 0 ? a.gid[a.gtype_r] : nullptr;
+    const int32_t g_first = gp ? gp[base] : 0;
+    const int S = gp ? (int)(gp[last] - g_first + 1) : 0;
+
+    R mx[NI], my[NI], mz[NI], M0[NI], x[NI], y[NI], z[NI], dB0[NI], r1[NI], r2[NI];
+    int32_t gP[NI], gR[NI];
+    bool ok[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int64_t k = base + (int64_t)i * kThreads + tid;
+        ok[i] = k < a.K;
+        if (ok[i]) {
+            x[i] = a.x[k]; y[i] = a.y[k]; z[i] = a.z[k]; dB0[i] = a.dB0[k]; M0[i] = a.M0[k];
+            const float T1 = a.T1[k], T2 = a.T2[k];
+            r1[i] = isinf(T1) ? (R)0 : (R)kLog2e / (R)T1;
+            r2[i] = isinf(T2) ? (R)0 : (R)kLog2e / (R)T2;
+            if (a.init_eq) {
+                mx[i] = 0; my[i] = 0; mz[i] = M0[i];
+            } else {
+                mx[i] = a.Mx[k]; my[i] = a.My[k]; mz[i] = a.Mz[k];
+            }
+            gP[i] = gp ? gp[k] : 0;
+            gR[i] = gr ? gr[k] : 0;
+        } else {
+            x[i] = y[i] = z[i] = dB0[i] = M0[i] = r1[i] = r2[i] = 0;
+            mx[i] = my[i] = mz[i] = 0;
+            gP[i] = 0x7fffffff;  // sorts after every real group
+            gR[i] = 0;
+        }
+    }
+    for (int t = tid; t < S; t += kThreads) acc_re[t] = acc_im[t] = 0;
+    // a warp whose isochromats all share one with-ADC group reduces with plain shuffles
+    const int32_t w0 = __shfl_sync(0xffffffffu, gP[0], 0);
+    bool uni = true;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) uni &= (!ok[i] || gP[i] == w0);
+    const bool warp_uni = __all_sync(0xffffffffu, uni) && w0 != 0x7fffffff;
+    __syncthreads();
+
+    for (int e = 0; e < a.n_ev; ++e) {
+        const FEvent<R> ev = a.ev[e];
+        if (ev.kind == EV_RF) {
+            const int32_t *g = ev.gtype == a.gtype_r ? nullptr : a.gid[ev.gtype];
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+                advance<R>(mx[i], my[i], mz[i], M0[i], x[i], y[i], z[i], dB0[i], r1[i], r2[i],
+                           ev.adv);
+                const int64_t k = base + (int64_t)i * kThreads + tid;
+                const int32_t gi = g ? (ok[i] ? g[k] : 0) : gR[i];
+                R T[12];
+                load_row(a.T_tab + (ev.row + gi) * 12, T);
+                const R nx = T[0] * mx[i] + T[1] * my[i] + T[2] * mz[i] + T[3] * M0[i];
+                const R ny = T[4] * mx[i] + T[5] * my[i] + T[6] * mz[i] + T[7] * M0[i];
+                const R nz = T[8] * mx[i] + T[9] * my[i] + T[10] * mz[i] + T[11] * M0[i];
+                mx[i] = nx;
+                my[i] = ny;
+                mz[i] = nz;
+            }
+        } else if (ev.kind == EV_ADC) {
+            R vr[NI], vi[NI];
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+                advance_xy<R>(mx[i], my[i], x[i], y[i], z[i], dB0[i], r2[i], ev.adv, vr[i], vi[i]);
+                if (!ok[i]) vr[i] = vi[i] = 0;
+            }
+            if (ev.gtype == a.gtype_p) {
+                if (warp_uni) {
+                    R sr = 0, si = 0;
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) { sr += vr[i]; si += vi[i]; }
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) {
+                        sr += __shfl_xor_sync(0xffffffffu, sr, d);
+                        si += __shfl_xor_sync(0xffffffffu, si, d);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&acc_re[w0 - g_first], sr);
+                        atomicAdd(&acc_im[w0 - g_first], si);
+                    }
+                } else {
+                    // segmented inclusive scan over lanes (keys sorted along lanes):
+                    // the last lane of each run holds the run's sum
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        R sr = vr[i], si = vi[i];
+                        const int32_t key = gP[i];
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const R orr = __shfl_up_sync(0xffffffffu, sr, d);
+                            const R oii = __shfl_up_sync(0xffffffffu, si, d);
+                            const int32_t ok2 = __shfl_up_sync(0xffffffffu, key, d);
+                            if (lane >= d && ok2 == key) { sr += orr; si += oii; }
+                        }
+                        const int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
+                        if ((lane == 31 || nk != key) && ok[i]) {
+                            atomicAdd(&acc_re[key - g_first], sr);
+                            atomicAdd(&acc_im[key - g_first], si);
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int t = tid; t < S; t += kThreads) {
+                    const R sr = acc_re[t], si = acc_im[t];
+                    if (sr != (R)0 || si != (R)0) {
+                        atomicAdd(&a.Ablk[2 * (ev.win + g_first + t)], (double)sr);
+                        atomicAdd(&a.Ablk[2 * (ev.win + g_first + t) + 1], (double)si);
+                        acc_re[t] = 0;
+                        acc_im[t] = 0;
+                    }
+                }
+                __syncthreads();
+            } else {
+                // window of a type the layout is not sorted by: per-isochromat FP64 atomics
+                const int32_t *g = a.gid[ev.gtype];
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    const int64_t k = base + (int64_t)i * kThreads + tid;
+                    if (ok[i]) {
+                        atomicAdd(&a.Ablk[2 * (ev.win + g[k])], (double)vr[i]);
+                        atomicAdd(&a.Ablk[2 * (ev.win + g[k]) + 1], (double)vi[i]);
+                    }
+                }
+            }
+        } else {  // EV_END: advance to the span end and store the state
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+                advance<R>(mx[i], my[i], mz[i], M0[i], x[i], y[i], z[i], dB0[i], r1[i], r2[i],
+                           ev.adv);
+                const int64_t k = base + (int64_t)i * kThreads + tid;
+                if (ok[i]) {
+                    a.Mx[k] = mx[i];
+                    a.My[k] = my[i];
+                    a.Mz[k] = mz[i];
+                }
+            }
+        }
+    }
+}
+
+template <typename R>
+struct GS;
+template <>
+struct GS<float> { using S = GSampleF; };
+template <>
+struct GS<double> { using S = GSampleD; };
+
+__device__ __forceinline__ float gs_turns(const GSampleF &s, float pos, float dB0) {
+    return turns_prod(pos, s.k_hi, s.k_lo) + turns_prod(dB0, s.tau_hi, s.tau_lo);
+}
+__device__ __forceinline__ double gs_turns(const GSampleD &s, double pos, double dB0) {
+    double v = pos * s.k + dB0 * s.tau;
+    return v - rint(v);
+}
+__device__ __forceinline__ float gs_tau(const GSampleF &s) { return s.tau_hi + s.tau_lo; }
+__device__ __forceinline__ double gs_tau(const GSampleD &s) { return s.tau; }
+
+constexpr int kGTile = 256;
+
+// block b covers samples [blk.y, blk.y + blockDim) of window blk.x and the
+// groups [blk.z, blk.w); partial sums go to the signal with FP64 atomics
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_group_signal(const GWin *wins, const int4 *blk,
+                                                           const typename GS<R>::S *smp,
+                                                           GSigTables<R> tab,
+                                                           const double *Ablk, double *signal) {
+    __shared__ R s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
+    const int4 b = blk[blockIdx.x];
+    const GWin w = wins[b.x];
+    const int64_t s_idx = (int64_t)b.y + threadIdx.x;
+    const bool act = s_idx < w.sample0 + w.n_samples;
+    typename GS<R>::S sm{};
+    if (act) sm = smp[s_idx];
+    const R tau = act ? (R)gs_tau(sm) : (R)0;
+    const R *pos = tab.pos[w.gtype], *dB0 = tab.dB0[w.gtype], *rT2 = tab.rT2[w.gtype];
+    double accr = 0, acci = 0;
+    for (int g0 = b.z; g0 < b.w; g0 += kGTile) {
+        const int n = min(kGTile, b.w - g0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            s_pos[t] = pos[g0 + t];
+            s_dB0[t] = dB0[g0 + t];
+            s_rT2[t] = rT2[g0 + t];
+            s_ar[t] = (R)Ablk[2 * (w.ablk + g0 + t)];
+            s_ai[t] = (R)Ablk[2 * (w.ablk + g0 + t) + 1];
+        }
+        __syncthreads();
+        R pr = 0, pi = 0;
+        if (act) {
+            for (int t = 0; t < n; ++t) {
+                R c, s;
+                phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, s);
+                const R e = decay(tau, s_rT2[t]);
+                const R ar = s_ar[t], ai = s_ai[t];
+                pr += e * (c * ar + s * ai);
+                pi += e * (c * ai - s * ar);
+            }
+        }
+        accr += (double)pr;
+        acci += (double)pi;
+    }
+    if (act) {
+        atomicAdd(&signal[2 * s_idx], accr);
+        atomicAdd(&signal[2 * s_idx + 1], acci);
+    }
+}
+
+}  // namespace
+
+template <typename R>
+void launch_precompute(mrsim_ctx *c, const PrecompArgs &a) {
+    using RFS = typename SegT<R>::RF;
+    if (a.n_groups <= 0) return;
+    KScope ks(c, sizeof(R) == 4 ? "precompute_f32" : "precompute_f64");
+    const unsigned grid = (unsigned)std::min<int64_t>(a.n_groups, 1 << 20);
+    k_precompute<R><<<grid, kPreThreads, 0, c->stream>>>(
+        (const RFS *)a.segs, a.seg_off, a.n_seg, a.n_steps, a.gtype, a.par, a.n_groups, (R *)a.out);
+}
+
+template <typename R>
+void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
+    KScope ks(c, sizeof(R) == 4 ? "fused_grouped_f32" : "fused_grouped_f64");
+    if (ni >= 4) {
+        const unsigned nb = (unsigned)((a.K + kThreads * 4 - 1) / (kThreads * 4));
+        k_fused<R, 4><<<nb, kThreads, 0, c->stream>>>(a);
+    } else if (ni == 2) {
+        const unsigned nb = (unsigned)((a.K + kThreads * 2 - 1) / (kThreads * 2));
+        k_fused<R, 2><<<nb, kThreads, 0, c->stream>>>(a);
+    } else {
+        const unsigned nb = (unsigned)((a.K + kThreads - 1) / kThreads);
+        k_fused<R, 1><<<nb, kThreads, 0, c->stream>>>(a);
+    }
+}
+
+template <typename R>
+void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int n_blk,
+                         const void *d_samples, const GSigTables<R> &tab, const double *Ablk,
+                         double *signal) {
+    if (n_blk <= 0) return;
+    KScope ks(c, sizeof(R) == 4 ? "group_signal_f32" : "group_signal_f64");
+    k_group_signal<R><<<n_blk, kThreads, 0, c->stream>>>(
+        d_win, d_blk, (const typename GS<R>::S *)d_samples, tab, Ablk, signal);
+}
+
+template void launch_precompute<float>(mrsim_ctx *, const PrecompArgs &);
+template void launch_precompute<double>(mrsim_ctx *, const PrecompArgs &);
+template void launch_fused<float>(mrsim_ctx *, const FusedArgs<float> &, int);
+template void launch_fused<double>(mrsim_ctx *, const FusedArgs<double> &, int);
+template void launch_group_signal<float>(mrsim_ctx *, const GWin *, const int4 *, int,
+                                         const void *, const GSigTables<float> &,
+                                         const double *, double *);
+template void launch_group_signal<double>(mrsim_ctx *, const GWin *, const int4 *, int,
+                                          const void *, const GSigTables<double> &,
+                                          const double *, double *);
+
+}  // namespace mrsim

@@ -1,0 +1,291 @@
+"""Python binding of libmrsim (C ABI in include/mrsim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  The functions carry the C names (mrsim_create, mrsim_phantom,
+mrsim_sequence, mrsim_group, mrsim_run, ...); the small ``Context`` class
+below wraps them with numpy / torch arrays for tests and the benchmark.
+
+The library must be built (``paper_2508_03960_gb300.build``); importing this
+module on a machine without it raises instead of falling back to anything.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence as Seq
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmrsim.so")
+
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(7)
+SUB_RF, SUB_ADC, SUB_RELAX = 0, 1, 2
+G_NONE, G_X, G_Y, G_Z, G_GENERAL = 0, 1, 2, 3, 4
+PLAIN, PLAIN_CACHE, GROUPED, SURROGATE = 0, 1, 2, 3
+FP32, FP64 = 0, 1
+PTR_DEVICE, OUT_DEVICE = 1, 2
+
+# every entry point declared in include/mrsim.h
+EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
+           "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
+           "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
+           "mrsim_profile_get", "mrsim_launch_count", "mrsim_free_phantom", "mrsim_free_seq",
+           "mrsim_free_groups"]
+
+
+class MrsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mrsim error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libmrsim is not built ({path} missing); run "
+                          "python -m paper_2508_03960_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I, I64, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "mrsim_create": (I, [PP, I, P]),
+        "mrsim_destroy": (None, [P]),
+        "mrsim_last_error": (ctypes.c_char_p, [P]),
+        "mrsim_phantom": (I, [P, I64] + [P] * 9 + [U, PP]),
+        "mrsim_sequence": (I, [P, I64] + [P] * 8 + [PP]),
+        "mrsim_seq_info": (I, [P] * 7),
+        "mrsim_group": (I, [P, P, P, PP]),
+        "mrsim_group_info": (I, [P, I, P, P]),
+        "mrsim_run": (I, [P, P, P, P, I, I, P, P, U]),
+        "mrsim_run_batch": (I, [P, I, P, P, P, P]),
+        "mrsim_profile_enable": (I, [P, I]),
+        "mrsim_profile_reset": (I, [P]),
+        "mrsim_profile_get": (I, [P, I, P, I, P, P]),
+        "mrsim_launch_count": (I64, [P]),
+        "mrsim_free_phantom": (None, [P]),
+        "mrsim_free_seq": (None, [P]),
+        "mrsim_free_groups": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+# ------------------------------------------------------------------ C names --
+def mrsim_create(device: int = 0, stream: Optional[int] = None) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().mrsim_create(ctypes.byref(h), device, stream)
+    if rc:
+        raise MrsimError(rc, "mrsim_create failed")
+    return h.value
+
+
+def mrsim_destroy(ctx: int) -> None:
+    lib().mrsim_destroy(ctx)
+
+
+def mrsim_last_error(ctx: int) -> str:
+    return (lib().mrsim_last_error(ctx) or b"").decode()
+
+
+def _check(ctx, rc, what):
+    if rc:
+        raise MrsimError(rc, f"{what}: {mrsim_last_error(ctx)}")
+
+
+def mrsim_phantom(ctx, K, x, y, z, T1, T2, dB0, M0, b1=None, M_init=None, flags=0) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().mrsim_phantom(ctx, int(K), *[_ptr(a) for a in (x, y, z, T1, T2, dB0, M0, b1,
+                                                              M_init)],
+                             flags, ctypes.byref(h))
+    _check(ctx, rc, "mrsim_phantom")
+    return h.value
+
+
+def mrsim_sequence(ctx, n_seg, dt, repeat, b1re, b1im, gx, gy, gz, adc) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().mrsim_sequence(ctx, int(n_seg), *[_ptr(a) for a in (dt, repeat, b1re, b1im, gx,
+                                                                    gy, gz, adc)],
+                              ctypes.byref(h))
+    _check(ctx, rc, "mrsim_sequence")
+    return h.value
+
+
+def mrsim_seq_info(seq):
+    n = ctypes.c_int64()
+    ns = ctypes.c_int64()
+    rc = lib().mrsim_seq_info(seq, ctypes.byref(n), None, None, None, None, ctypes.byref(ns))
+    if rc:
+        raise MrsimError(rc, "mrsim_seq_info")
+    N = n.value
+    out = dict(type=np.zeros(N, np.uint8), gtype=np.zeros(N, np.uint8),
+               seg_begin=np.zeros(N, np.int64), seg_end=np.zeros(N, np.int64))
+    rc = lib().mrsim_seq_info(seq, ctypes.byref(n), *[_ptr(out[k]) for k in
+                                                      ("type", "gtype", "seg_begin", "seg_end")],
+                              ctypes.byref(ns))
+    if rc:
+        raise MrsimError(rc, "mrsim_seq_info")
+    out["n_samples_total"] = ns.value
+    return out
+
+
+def mrsim_group(ctx, ph, seq) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().mrsim_group(ctx, ph, seq, ctypes.byref(h))
+    _check(ctx, rc, "mrsim_group")
+    return h.value
+
+
+def mrsim_group_info(groups, gtype, K=None):
+    n = ctypes.c_int64()
+    gid = None if K is None else np.empty(K, np.int32)
+    rc = lib().mrsim_group_info(groups, gtype, ctypes.byref(n), _ptr(gid))
+    if rc:
+        raise MrsimError(rc, "mrsim_group_info")
+    return n.value, gid
+
+
+def mrsim_run(ctx, ph, seq, groups, mode, precision, signal, M_final=None, out_flags=0):
+    rc = lib().mrsim_run(ctx, ph, seq, groups, mode, precision, _ptr(signal), _ptr(M_final),
+                         out_flags)
+    _check(ctx, rc, "mrsim_run")
+
+
+def mrsim_run_batch(ctx, phs, seqs, groups, signals):
+    n = len(phs)
+    A = ctypes.c_void_p * n
+    rc = lib().mrsim_run_batch(ctx, n, A(*phs), A(*seqs), A(*groups),
+                               A(*[_ptr(s) for s in signals]))
+    _check(ctx, rc, "mrsim_run_batch")
+
+
+def mrsim_profile_enable(ctx, on=True):
+    lib().mrsim_profile_enable(ctx, int(on))
+
+
+def mrsim_profile_reset(ctx):
+    lib().mrsim_profile_reset(ctx)
+
+
+def mrsim_profile_get(ctx):
+    """All per-kernel entries: {name: (launches, ms_total)}."""
+    out = {}
+    buf = ctypes.create_string_buffer(128)
+    i = 0
+    while True:
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        rc = lib().mrsim_profile_get(ctx, i, buf, 128, ctypes.byref(n), ctypes.byref(ms))
+        if rc:
+            break
+        out[buf.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
+
+
+def mrsim_launch_count(ctx) -> int:
+    return int(lib().mrsim_launch_count(ctx))
+
+
+def mrsim_free_phantom(ph):
+    lib().mrsim_free_phantom(ph)
+
+
+def mrsim_free_seq(seq):
+    lib().mrsim_free_seq(seq)
+
+
+def mrsim_free_groups(groups):
+    lib().mrsim_free_groups(groups)
+
+
+# -------------------------------------------------------------- helpers -----
+class Context:
+    """Owns one mrsim context and the handles created through it."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.h = mrsim_create(device, stream)
+        self._handles = []
+
+    def close(self):
+        for kind, h in reversed(self._handles):
+            {"ph": mrsim_free_phantom, "seq": mrsim_free_seq, "grp": mrsim_free_groups}[kind](h)
+        self._handles = []
+        if self.h:
+            mrsim_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def phantom(self, p, device_ptrs: bool = False) -> int:
+        """Upload an ``mrsim_inputs.Phantom`` (numpy) or a dict of torch
+        device tensors (device_ptrs=True)."""
+        if device_ptrs:
+            a = p
+            K = a["x"].numel()
+            M_init = a.get("M_init")
+            h = mrsim_phantom(self.h, K, a["x"], a["y"], a["z"], a["T1"], a["T2"], a["dB0"],
+                              a["M0"], a.get("b1"), M_init, PTR_DEVICE)
+        else:
+            keep = [_f32(p.x), _f32(p.y), _f32(p.z), _f32(p.T1), _f32(p.T2), _f32(p.dB0),
+                    _f32(p.M0), _f32(p.b1),
+                    None if p.M_init is None else np.ascontiguousarray(p.M_init, np.float32)]
+            h = mrsim_phantom(self.h, p.K, *keep)
+        self._handles.append(("ph", h))
+        return h
+
+    def sequence(self, s) -> int:
+        keep = [np.ascontiguousarray(s.dt, np.float64), np.ascontiguousarray(s.repeat, np.int32),
+                _f32(s.b1re), _f32(s.b1im), _f32(s.gx), _f32(s.gy), _f32(s.gz),
+                np.ascontiguousarray(s.adc, np.uint8)]
+        h = mrsim_sequence(self.h, s.n_seg, *keep)
+        self._handles.append(("seq", h))
+        return h
+
+    def group(self, ph: int, seq: int) -> int:
+        h = mrsim_group(self.h, ph, seq)
+        self._handles.append(("grp", h))
+        return h
+
+    def run(self, ph, seq, groups=None, mode=GROUPED, precision=FP32, n_samples=None,
+            K=None, want_M=False):
+        if n_samples is None:
+            n_samples = mrsim_seq_info(seq)["n_samples_total"]
+        sig = np.zeros(2 * max(n_samples, 1), np.float64)
+        M = np.zeros((3, K), np.float32) if want_M else None
+        mrsim_run(self.h, ph, seq, groups if groups else None, mode, precision, sig, M)
+        return sig[: 2 * n_samples].view(np.complex128).copy(), M
+
+    def free(self, kind: str, h: int):
+        self._handles = [(k, x) for (k, x) in self._handles if x != h]
+        {"ph": mrsim_free_phantom, "seq": mrsim_free_seq, "grp": mrsim_free_groups}[kind](h)

@@ -1,0 +1,292 @@
+"""GPU library vs FP64 oracle, through the C ABI.
+
+Tolerances (signal rel-L2 over all complex samples, M_final max abs error
+relative to max M0):
+  FP64 per-isochromat arithmetic  signal 1e-10 (same formulas, different
+                                  rounding order and closed-form shortcuts);
+                                  M_final 1e-7, because the ABI returns M_final
+                                  as float32 (half an ulp of |M| <= 1 is 6e-8)
+  FP32 per-isochromat arithmetic  1e-4 for both (the target for FP32 paths)
+Classification and group ids are compared bit-exactly.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from mrsim_inputs import Phantom, SeqBuilder, Sequence, configs
+from mrsim_inputs.sequence import epi_2d, fse_2d, gre_2d, spin_echo_2d
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-10}  # by precision (FP32, FP64)
+
+
+@pytest.fixture(scope="module")
+def ctx(mrsim):
+    c = mrsim.Context(0)
+    yield c
+    c.close()
+
+
+def run_both(mrsim, ctx, ph, seq, mode, precision, want_M=True):
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs) if mode in (mrsim.GROUPED, mrsim.SURROGATE) else None
+    sig, M = ctx.run(hp, hs, hg, mode, precision, K=ph.K, want_M=want_M)
+    ctx.free("grp", hg) if hg else None
+    ctx.free("seq", hs)
+    ctx.free("ph", hp)
+    return sig, M
+
+
+def check(sig, M, ref, Mref, precision, M0max=1.0):
+    e = oracle.rel_l2(sig, ref)
+    assert e <= TOL[precision], f"signal rel-L2 {e:.3e}"
+    if M is not None:
+        em = float(np.max(np.abs(M - Mref))) / M0max
+        tolM = 1e-7 if precision == 1 else 1e-4
+        assert em <= tolM, f"M_final max error {em:.3e}"
+    return e
+
+
+SE = None
+
+
+def se():
+    global SE
+    if SE is None:
+        ph, seq = configs.se_32()
+        SE = (ph, seq, *oracle.simulate(ph, seq, memo=True, adc_recurrence=True))
+    return SE
+
+
+@pytest.mark.parametrize("mode", ["plain", "plain_cache", "grouped"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_spin_echo_32x32x4_all_modes(mrsim, ctx, mode, precision):
+    ph, seq, ref, Mref = se()
+    m = {"plain": mrsim.PLAIN, "plain_cache": mrsim.PLAIN_CACHE, "grouped": mrsim.GROUPED}[mode]
+    sig, M = run_both(mrsim, ctx, ph, seq, m, precision)
+    check(sig, M, ref, Mref, precision)
+
+
+def test_classification_bit_exact(mrsim, ctx):
+    for seq in (configs.se_32()[1], fse_2d(n_ro=32, n_pe=32, etl=8, n_shots=1),
+                epi_2d(n_ro=32, n_lines=16), gre_2d(n_ro=16, n_pe=4)):
+        hs = ctx.sequence(seq)
+        info = mrsim.mrsim_seq_info(hs)
+        ctx.free("seq", hs)
+        q = oracle.classify(seq)
+        for k in ("type", "gtype", "seg_begin", "seg_end"):
+            assert np.array_equal(info[k], q[k].astype(info[k].dtype)), k
+        assert info["n_samples_total"] == int(q["n_samples"].sum())
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 4), (16, 24, 3), (64, 64, 8)])
+def test_group_ids_bit_exact(mrsim, ctx, shape):
+    ph = configs.small_phantom(*shape)
+    seq = fse_2d(n_ro=16, n_pe=16, etl=4, n_shots=1)
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    for gt in (mrsim.G_X, mrsim.G_Z):
+        n, gid = mrsim.mrsim_group_info(hg, gt, ph.K)
+        ref, nref = oracle.group(ph, gt)
+        assert n == nref
+        assert np.array_equal(gid, ref)
+    with pytest.raises(mrsim.MrsimError):
+        mrsim.mrsim_group_info(hg, mrsim.G_Y, ph.K)  # not needed by this sequence
+    ctx.free("grp", hg)
+    ctx.free("seq", hs)
+    ctx.free("ph", hp)
+
+
+def test_group_ids_with_b1_and_negative_zero(mrsim, ctx):
+    ph = configs.small_phantom(16, 16, 2)
+    rng = np.random.default_rng(3)
+    ph.b1 = rng.choice(np.array([0.9, 1.0, 1.1], np.float32), ph.K)
+    ph.x = ph.x.copy()
+    ph.x[ph.x == 0] = -0.0
+    ph.x[:5] = 0.0
+    seq = spin_echo_2d(n_ro=8, n_pe=8, n_tr=2)
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    for gt in (mrsim.G_X, mrsim.G_Z):
+        n, gid = mrsim.mrsim_group_info(hg, gt, ph.K)
+        ref, nref = oracle.group(ph, gt)
+        assert n == nref and np.array_equal(gid, ref)
+    ref, Mref = oracle.simulate(ph, seq)
+    sig, M = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP64, K=ph.K, want_M=True)
+    check(sig, M, ref, Mref, 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fse_small_grouped_and_plain(mrsim, ctx, precision):
+    ph = configs.small_phantom(24, 20, 5)
+    seq = fse_2d(n_ro=32, n_pe=32, etl=8, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=0.5, n_shots=2)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        sig, M = run_both(mrsim, ctx, ph, seq, mode, precision)
+        check(sig, M, ref, Mref, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_epi_small_grouped_and_plain(mrsim, ctx, precision):
+    ph = configs.small_phantom(24, 20, 5)
+    seq = epi_2d(n_ro=32, n_lines=24, rf_dur=2e-3, rf_dt=5e-6)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        sig, M = run_both(mrsim, ctx, ph, seq, mode, precision)
+        check(sig, M, ref, Mref, precision)
+
+
+@pytest.mark.parametrize("K", [1, 7, 255, 1023, 1025, 3001])
+def test_ragged_and_tiny_phantoms(mrsim, ctx, K):
+    rng = np.random.default_rng(K)
+    full = configs.small_phantom(32, 32, 4)
+    idx = np.sort(rng.choice(full.K, size=K, replace=False))
+    ph = full.subset(idx)
+    seq = spin_echo_2d(n_ro=16, n_pe=16, n_tr=3)
+    ref, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        for prec in (0, 1):
+            sig, M = run_both(mrsim, ctx, ph, seq, mode, prec)
+            check(sig, M, ref, Mref, prec)
+
+
+def general_type_sequence():
+    """Unclassifiable with-RF (Gx + Gz during RF) and with-ADC (Gx + Gy)
+    subsequences between known ones: the conventional fallback path."""
+    b = SeqBuilder()
+    b.rf_sinc(90, "x", 1e-3, 10e-6, 4.0, 0.01)              # Gz-only
+    b.add(1e-3, 1, g=(2e-3, 1e-3, -3e-3))
+    for j in range(50):                                       # RF with Gx and Gz
+        b.add(10e-6, 1, b1=(2e-6, 0.5e-6), g=(1e-3, 0, 2e-3))
+    b.add(2e-3, 1, g=(0, 1e-3, 0))
+    b.add(10e-6, 16, g=(5e-3, 2e-3, 0), adc=True)            # ADC with Gx and Gy
+    b.add(1e-3, 1)
+    b.add(10e-6, 16, g=(5e-3, 0, 0), adc=True)               # Gx-only
+    b.add(1e-3, 1, g=(0, 0, 1e-3))
+    b.rf_hard(30, "y", 100e-6, 10e-6)                         # no-grads RF
+    b.add(10e-6, 8, adc=True)                                 # no-grads ADC
+    b.add(5e-3, 1)
+    return b.build()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_general_type_fallback_and_no_grads(mrsim, ctx, precision):
+    ph = configs.small_phantom(16, 16, 3)
+    seq = general_type_sequence()
+    q = oracle.classify(seq)
+    assert 4 in set(q["gtype"][q["type"] != oracle.RELAX])  # has GENERAL subsequences
+    ref, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN, mrsim.PLAIN_CACHE):
+        sig, M = run_both(mrsim, ctx, ph, seq, mode, precision)
+        check(sig, M, ref, Mref, precision)
+
+
+def test_initial_state_b1_scale_and_infinite_relaxation(mrsim, ctx):
+    ph = configs.small_phantom(16, 16, 2)
+    rng = np.random.default_rng(11)
+    ph.M_init = rng.uniform(-0.5, 0.5, (3, ph.K)).astype(np.float32)
+    ph.b1 = rng.uniform(0.9, 1.1, ph.K).astype(np.float32)
+    ph.T1 = np.where(ph.labels == 1, np.inf, ph.T1).astype(np.float32)
+    ph.T2 = np.where(ph.labels == 2, np.inf, ph.T2).astype(np.float32)
+    seq = spin_echo_2d(n_ro=16, n_pe=16, n_tr=2)
+    ref, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN, mrsim.PLAIN_CACHE):
+        for prec in (0, 1):
+            sig, M = run_both(mrsim, ctx, ph, seq, mode, prec)
+            check(sig, M, ref, Mref, prec)
+
+
+def test_sequence_without_adc_and_without_rf(mrsim, ctx):
+    ph = configs.small_phantom(8, 8, 2)
+    b = SeqBuilder()
+    b.rf_hard(45, "x", 100e-6, 10e-6)
+    b.add(3e-3, 1, g=(1e-3, 2e-3, 0))
+    seq = b.build()
+    _, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        hp = ctx.phantom(ph)
+        hs = ctx.sequence(seq)
+        hg = ctx.group(hp, hs) if mode == mrsim.GROUPED else None
+        sig, M = ctx.run(hp, hs, hg, mode, mrsim.FP64, K=ph.K, want_M=True)
+        assert sig.size == 0
+        assert np.max(np.abs(M - Mref)) < 1e-7
+    b = SeqBuilder()
+    b.add(2e-3, 1, g=(1e-3, 0, 0))
+    b.add(10e-6, 10, g=(2e-3, 0, 0), adc=True)
+    seq = b.build()
+    ref, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        sig, M = run_both(mrsim, ctx, ph, seq, mode, 1)
+        assert np.allclose(sig, 0) and np.allclose(ref, 0)
+        assert np.max(np.abs(M - Mref)) < 1e-7
+
+
+def test_errors_are_reported(mrsim, ctx):
+    ph = configs.small_phantom(8, 8, 2)
+    bad = Phantom(**{**ph.__dict__})
+    bad.T2 = ph.T2.copy()
+    bad.T2[3] = np.nan
+    with pytest.raises(mrsim.MrsimError) as e:
+        ctx.phantom(bad)
+    assert e.value.code == mrsim.EINVAL
+    bad.T2[3] = 0.0
+    with pytest.raises(mrsim.MrsimError) as e:
+        ctx.phantom(bad)
+    assert e.value.code == mrsim.EINVAL
+    b = SeqBuilder()
+    b.add(1e-6, 1, b1=(1e-6, 0), adc=True)
+    with pytest.raises(mrsim.MrsimError) as e:
+        ctx.sequence(b.build())
+    assert e.value.code == mrsim.EUNSUPPORTED
+    b = SeqBuilder()
+    b.add(1e-6, 1)
+    s = b.build()
+    s.repeat[0] = 0
+    with pytest.raises(mrsim.MrsimError) as e:
+        ctx.sequence(s)
+    assert e.value.code == mrsim.EINVAL
+    # groups built for another phantom
+    seq = spin_echo_2d(n_ro=8, n_pe=8, n_tr=1)
+    h1, h2 = ctx.phantom(ph), ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    g1 = ctx.group(h1, hs)
+    sig = np.zeros(2 * 8)
+    with pytest.raises(mrsim.MrsimError) as e:
+        mrsim.mrsim_run(ctx.h, h2, hs, g1, mrsim.GROUPED, mrsim.FP32, sig)
+    assert e.value.code == mrsim.ESTATE
+    with pytest.raises(mrsim.MrsimError) as e:
+        mrsim.mrsim_run(ctx.h, h2, hs, None, mrsim.GROUPED, mrsim.FP32, sig)
+    assert e.value.code == mrsim.EINVAL
+
+
+def test_device_pointer_inputs_and_outputs(mrsim, ctx):
+    import torch
+    ph, seq, ref, Mref = se()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+           for k, v in dict(x=ph.x, y=ph.y, z=ph.z, T1=ph.T1, T2=ph.T2, dB0=ph.dB0,
+                            M0=ph.M0).items()}
+    hp = ctx.phantom(dev, device_ptrs=True)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    sig = torch.zeros(2 * seq.n_samples, dtype=torch.float64, device="cuda")
+    M = torch.zeros(3 * ph.K, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    mrsim.mrsim_run(ctx.h, hp, hs, hg, mrsim.GROUPED, mrsim.FP32, sig, M, mrsim.OUT_DEVICE)
+    s = sig.cpu().numpy().view(np.complex128)
+    check(s, M.cpu().numpy().reshape(3, -1), ref, Mref, 0)
+
+
+def test_repeated_runs_are_consistent(mrsim, ctx):
+    ph, seq, ref, _ = se()
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    a, _ = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32)
+    b, _ = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32)
+    assert oracle.rel_l2(a, ref) <= 1e-4 and oracle.rel_l2(b, a) <= 1e-6
