@@ -185,6 +185,51 @@ int mrsim_profile_get(mrsim_ctx *ctx, int i, char *name, int cap, int64_t *launc
 /* Kernels launched by this context since creation (all modes). */
 int64_t mrsim_launch_count(const mrsim_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free grouped with-ADC signal.  The paper has no counterpart to
+ * this call; it exists for host programs that cannot allocate device memory
+ * once they are running: programs whose device memory is reserved up front by
+ * another allocator (a framework's caching pool or a fixed arena holding
+ * nearly all of HBM, where a new cudaMalloc fails or forces the pool to give
+ * memory back), and acquisition / reconstruction loops that forbid
+ * cudaMalloc / cudaFree after start-up because those calls can block until
+ * the device is idle.
+ *
+ * It computes the signal of one with-ADC window of a known gradient type by
+ * the grouped three-step method's first two steps: block sums of the
+ * transverse magnetization per group (Eq. 9), then every sample from the
+ * block sums (Eqs. 8 and 10).  Its only scratch, the complex block sums, is a
+ * static device array of MRSIM_NOALLOC_MAX_GROUPS entries (1 MiB) that every
+ * GPU which loads the library keeps until the process exits; nothing is
+ * allocated by the call.
+ *
+ * All pointers are device pointers on the current CUDA device, owned by the
+ * caller.  K >= 1 isochromats: d_mx, d_my (float32 [K]) transverse
+ * magnetization at the window start; d_gid (int32 [K]) group of each
+ * isochromat in [0, n_groups), any order.  Per group (float32 [n_groups]):
+ * d_gpos position on the window's gradient axis (m; 0 for a no-grads window),
+ * d_gdB0 (Hz), d_gT2 (s, +inf allowed).  Per sample (double [n_samples]):
+ * d_tau time since the window start (s), d_kmom gamma_bar times the gradient
+ * moment on the window's axis since the window start (cycles/m).  d_signal
+ * (double [2 * n_samples], interleaved re, im) is overwritten.  stream: a
+ * cudaStream_t, or NULL for the legacy default stream.  Synchronous at
+ * return.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array with that device current; make that first call before any stream
+ * capture.  Every call shares the array, which keeps the last call's
+ * contents (each call clears what it uses first); calls that overlap on the
+ * GPU (other streams, other host threads) race on it.
+ * Errors: MRSIM_EINVAL (K < 1, n_samples < 0, a NULL pointer, n_groups
+ * outside [1, MRSIM_NOALLOC_MAX_GROUPS], or a group id outside [0,
+ * n_groups): such isochromats are skipped), MRSIM_ECUDA. */
+#define MRSIM_NOALLOC_MAX_GROUPS 65536
+int mrsim_adc_grouped_noalloc(int64_t K, const float *d_mx, const float *d_my,
+                              const int32_t *d_gid, int32_t n_groups, const float *d_gpos,
+                              const float *d_gdB0, const float *d_gT2, int64_t n_samples,
+                              const double *d_tau, const double *d_kmom, double *d_signal,
+                              void *stream);
+
 void mrsim_free_phantom(mrsim_phantom_t *ph);
 void mrsim_free_seq(mrsim_seq *seq);
 void mrsim_free_groups(mrsim_groups *groups);

@@ -31,8 +31,9 @@ PTR_DEVICE, OUT_DEVICE = 1, 2
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
            "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
-           "mrsim_profile_get", "mrsim_launch_count", "mrsim_free_phantom", "mrsim_free_seq",
-           "mrsim_free_groups"]
+           "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
+           "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
+NOALLOC_MAX_GROUPS = 65536
 
 
 class MrsimError(RuntimeError):
@@ -63,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_profile_reset": (I, [P]),
         "mrsim_profile_get": (I, [P, I, P, I, P, P]),
         "mrsim_launch_count": (I64, [P]),
+        "mrsim_adc_grouped_noalloc": (I, [I64, P, P, P, ctypes.c_int32, P, P, P, I64, P, P, P, P]),
         "mrsim_free_phantom": (None, [P]),
         "mrsim_free_seq": (None, [P]),
         "mrsim_free_groups": (None, [P]),
@@ -211,6 +213,16 @@ def mrsim_profile_get(ctx):
 
 def mrsim_launch_count(ctx) -> int:
     return int(lib().mrsim_launch_count(ctx))
+
+
+def mrsim_adc_grouped_noalloc(K, mx, my, gid, n_groups, gpos, gdB0, gT2, n_samples, tau, kmom,
+                              signal, stream=None) -> int:
+    """Allocation-free grouped with-ADC window signal (device tensors in,
+    device signal out).  Returns the status code (0 on success)."""
+    return int(lib().mrsim_adc_grouped_noalloc(int(K), _ptr(mx), _ptr(my), _ptr(gid),
+                                               int(n_groups), _ptr(gpos), _ptr(gdB0), _ptr(gT2),
+                                               int(n_samples), _ptr(tau), _ptr(kmom),
+                                               _ptr(signal), stream))
 
 
 def mrsim_free_phantom(ph):
