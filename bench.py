@@ -147,6 +147,10 @@ def main():
     ap.add_argument("--plain-fse", default="on", choices=["on", "off"],
                     help="time one plain (per-isochromat) FSE run (~tens of seconds)")
     ap.add_argument("--cpu-stride", type=int, default=128)
+    ap.add_argument("--case", default="fse_27m", choices=["fse_27m", "fse_6m"],
+                    help="fse_6m: the same sequences on a 256x256x105 phantom (profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the grouped FSE/EPI steps (for profiler launch lists)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
 
@@ -170,7 +174,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2508_03960_gb300 import mrsim
 
-    ph = configs.full_phantom()
+    ph = configs.full_phantom() if a.case == "fse_27m" else configs.small_phantom(256, 256, 105)
     fse = configs.fse_sequence()
     epi = configs.epi_sequence()
     stream = torch.cuda.current_stream()
@@ -202,6 +206,11 @@ def main():
     hs_e = ctx.sequence(epi)
     hg_e = ctx.group(hp, hs_e)
     groups = {n: mrsim.mrsim_group_info(hg_f, t)[0] for n, t in (("gx", mrsim.G_X), ("gz", mrsim.G_Z))}
+
+    # autotuner: launch parameters picked by timing the grouped FSE run itself
+    t0 = time.perf_counter()
+    tuned = mrsim.mrsim_autotune(ctx.h, hp, hs_f, hg_f, mrsim.GROUPED, mrsim.FP32, 2)
+    autotune_s = time.perf_counter() - t0
 
     ns_f, ns_e = fse.n_samples, epi.n_samples
     sig_f = torch.zeros(2 * ns_f, dtype=torch.float64, device="cuda")
@@ -243,6 +252,13 @@ def main():
     barrier()
     epi_s = maxr(e0.elapsed_time(e1) / a.steps / 1e3)
     epi_sig = sig_e.cpu().numpy().view(np.complex128)
+    if a.quick:
+        if rank == 0:
+            print(json.dumps({"case": a.case, "K": ph.K, "fse_grouped_s": fse_s,
+                              "epi_grouped_s": epi_s, "autotune": tuned,
+                              "kernels": {k: v for k, v in prof.items()}}))
+        ctx.close()
+        return
 
     # ---- plain forms on the same GPU ----
     def timed_once(fn):
@@ -253,6 +269,11 @@ def main():
         barrier()
         return maxr(e0.elapsed_time(e1) / 1e3)
 
+    # plain kernels: tuned on the plain EPI run (the FSE run uses the same kernels)
+    fused_ni = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_FUSED_NI)
+    tuned_plain = mrsim.mrsim_autotune(ctx.h, hp, hs_e, None, mrsim.PLAIN, mrsim.FP32, 1)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, fused_ni)
+    tuned.update({k: v for k, v in tuned_plain.items() if k != mrsim.TUNE_FUSED_NI})
     step(hs_e, None, sig_e, mrsim.PLAIN)  # warm the plain kernels
     epi_plain_s = timed_once(lambda: step(hs_e, None, sig_e, mrsim.PLAIN))
     epi_plain_sig = sig_e.cpu().numpy().view(np.complex128).copy()
@@ -343,6 +364,10 @@ def main():
             "epi": round(epi_plain_s / epi_s, 1)},
         "isochromat_steps_per_s_equiv": round(steps_fse / fse_s, 1),
         "prep_s": round(prep_s, 4), "phantom_upload_s": round(t_upload, 4), "groups": groups,
+        "autotune": {"fused_isochromats_per_thread": tuned[mrsim.TUNE_FUSED_NI],
+                     "plain_rf_isochromats_per_thread": tuned[mrsim.TUNE_PLAIN_RF_NI],
+                     "plain_adc_ctas_per_sm": tuned[mrsim.TUNE_ADC_CTAS_PER_SM],
+                     "seconds": round(autotune_s, 2)},
         "parity": parity,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         "roofline": roof, "cpu_baseline": cpu,

@@ -171,6 +171,29 @@ int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);
 
+/* Launch parameters (one value per context).
+ *   MRSIM_TUNE_FUSED_NI        isochromats per thread held in registers by the
+ *                              grouped fused kernel: 1, 2 or 4 (default 4)
+ *   MRSIM_TUNE_PLAIN_RF_NI     isochromats per thread of the plain with-RF step
+ *                              kernel: 1 or 2 (default 2)
+ *   MRSIM_TUNE_ADC_CTAS_PER_SM CTAs per SM of the persistent plain with-ADC
+ *                              kernel: 1, 2, 4 or 8 (default 2)
+ * mrsim_set_tuning returns MRSIM_EINVAL for another parameter or value. */
+#define MRSIM_TUNE_FUSED_NI 0
+#define MRSIM_TUNE_PLAIN_RF_NI 1
+#define MRSIM_TUNE_ADC_CTAS_PER_SM 2
+int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
+int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
+
+/* Autotuner: for the given problem and mode, time every allowed value of each
+ * launch parameter the mode uses (one warm-up run plus `reps` timed runs of
+ * mrsim_run per value, CUDA events on the context stream, one parameter at a
+ * time) and keep the fastest in the context.  Results are identical for
+ * every choice up to floating-point summation order.
+ * Errors: as mrsim_run. */
+int mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
+                   const mrsim_groups *groups, int mode, int precision, int reps);
+
 /* Per-kernel timing.  With profiling on, every kernel launch of the context
  * is bracketed by CUDA events on the context stream.  mrsim_profile_get
  * returns, for entry i (0-based, in first-launch order), the kernel name

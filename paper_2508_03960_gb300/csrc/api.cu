@@ -319,6 +319,10 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
     sync(c);
 }
 
+// element stride between the Mx, My and Mz planes of the state buffer: a
+// multiple of 64 so that every plane starts 256-byte aligned (vector loads)
+inline int64_t plane_stride(int64_t K) { return (K + 63) / 64 * 64; }
+
 PlainState plain_state(const mrsim_phantom_t *ph, void *Mx, void *My, void *Mz) {
     return PlainState{ph->K, ph->x.as<float>(), ph->y.as<float>(), ph->z.as<float>(),
                       ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
@@ -337,7 +341,8 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
                double *d_signal, R *M) {
     const int64_t K = ph->K;
     const mrsim_seq &dev = *s;
-    PlainState st = plain_state(ph, M, M + K, M + 2 * K);
+    const int64_t Kp = plane_stride(K);
+    PlainState st = plain_state(ph, M, M + Kp, M + 2 * Kp);
     launch_init_state<R>(c, st, ph->has_M_init ? ph->M_init.as<float>() : nullptr);
     std::vector<DBuf> cache(s->n_content);
     double mom[3] = {0, 0, 0}, tau = 0.0;
@@ -362,7 +367,7 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
                 }
                 launch_apply_affine<R>(c, st, cache[cid].as<R>(), &adv);
             } else {
-                launch_plain_rf<R>(c, st, segs, nseg, &adv, 2);
+                launch_plain_rf<R>(c, st, segs, nseg, &adv, c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
             }
             mom[0] = mom[1] = mom[2] = 0.0;
             tau = 0.0;
@@ -370,7 +375,7 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
             const void *segs = f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[i])
                                    : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[i]);
             launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &adv,
-                                d_signal + 2 * q.sample0);
+                                d_signal + 2 * q.sample0, c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
             for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
             tau += q.dur;
         }
@@ -399,6 +404,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             rows += g->n_groups[q.gtype];
         }
     }
+    if (rows * 12 > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "combined-transition table too large");
     R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(rows, 1) * 12 * sizeof(R));
     for (auto &kv : row_of) {
         const int cid = kv.first.first, gt = kv.first.second;
@@ -420,40 +426,48 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                             (int)q.n_samples, 0});
         ablk_n += g->n_groups[q.gtype];
     }
+    if (ablk_n > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many block sums");
     double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double));
     MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double),
                                c->stream));
-    // 3) spans of known-type events; unknown types fall back to plain kernels
-    PlainState st = sorted_state(g, M, M + K, M + 2 * K);
-    bool init_eq = !g->has_M_init;
-    if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
-    FusedArgs<R> fa{};
-    fa.K = K;
-    fa.x = g->x.as<float>(); fa.y = g->y.as<float>(); fa.z = g->z.as<float>();
-    fa.T1 = g->T1.as<float>(); fa.T2 = g->T2.as<float>(); fa.dB0 = g->dB0.as<float>();
-    fa.M0 = g->M0.as<float>();
-    for (int t = 0; t < 4; ++t) fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
-    fa.gtype_p = g->primary;
-    fa.gtype_r = g->secondary >= 0 ? g->secondary : g->primary;
-    fa.Mx = M; fa.My = M + K; fa.Mz = M + 2 * K;
-    fa.T_tab = T_tab;
-    fa.Ablk = Ablk;
+    // 3) spans of known-type events; unknown types fall back to plain kernels.
+    //    All events of the run go into one list; each span is a slice of it.
+    const int64_t Kp = plane_stride(K);
+    PlainState st = sorted_state(g, M, M + Kp, M + 2 * Kp);
+    const int p = g->primary;  // layout / group-factor gradient type
+    const int64_t Gp = g->n_groups[p];
     std::vector<FEvent<R>> ev;
+    std::vector<EvAdv> adv;
+    struct Span { int64_t b, e; int fallback; };
+    std::vector<Span> spans;
+    int64_t span_begin = 0;
     double mom[3] = {0, 0, 0}, tau = 0.0;
-    auto flush = [&]() {
+    auto make = [&](int kind, int gtype) {
         FEvent<R> e{};
-        e.kind = EV_END;
-        e.adv = AdvOf<R>::make(mom, tau);
-        ev.push_back(e);
-        // one event buffer for all spans: uploads are ordered after earlier launches
-        void *b = scratch(c, 11, ev.size() * sizeof(FEvent<R>));
-        upload(c, b, ev.data(), ev.size() * sizeof(FEvent<R>));
-        fa.ev = (const FEvent<R> *)b;
-        fa.n_ev = (int)ev.size();
-        fa.init_eq = init_eq ? 1 : 0;
-        launch_fused<R>(c, fa, 4);
-        ev.clear();
-        init_eq = false;
+        const int64_t prow = (int64_t)ev.size() * Gp;
+        if (prow > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many events x groups");
+        e.prow = (int)prow;
+        double k[3];
+        for (int a = 0; a < 3; ++a) k[a] = kGammaBar * mom[a];
+        int mask = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (a == p - 1 || k[a] == 0.0) continue;
+            mask |= 1 << a;
+            if constexpr (sizeof(R) == 4) {
+                e.k_hi[a] = (float)k[a];
+                e.k_lo[a] = (float)(k[a] - (double)e.k_hi[a]);
+            } else {
+                e.k[a] = k[a];
+            }
+        }
+        e.op = ev_op(kind, mask, gtype);
+        adv.push_back(EvAdv{p >= 1 ? k[p - 1] : 0.0, tau});
+        return e;
+    };
+    auto close_span = [&](int fallback) {
+        ev.push_back(make(EV_END, G_NONE));
+        spans.push_back(Span{span_begin, (int64_t)ev.size(), fallback});
+        span_begin = (int64_t)ev.size();
         mom[0] = mom[1] = mom[2] = 0.0;
         tau = 0.0;
     };
@@ -463,44 +477,71 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
             tau += q.dur;
         } else if (q.type == SUB_RF && q.gtype != G_GENERAL) {
-            FEvent<R> e{};
-            e.kind = EV_RF;
-            e.gtype = q.gtype;
-            e.row = row_of.at(std::make_pair(q.content, q.gtype));
-            e.adv = AdvOf<R>::make(mom, tau);
+            FEvent<R> e = make(EV_RF, q.gtype);
+            e.row = (int)row_of.at(std::make_pair(q.content, q.gtype));
             ev.push_back(e);
             mom[0] = mom[1] = mom[2] = 0.0;
             tau = 0.0;
         } else if (q.type == SUB_ADC && q.gtype != G_GENERAL) {
             if (q.n_samples > 0) {
-                FEvent<R> e{};
-                e.kind = EV_ADC;
-                e.gtype = q.gtype;
-                e.win = win_off[i];
-                e.adv = AdvOf<R>::make(mom, tau);
+                FEvent<R> e = make(EV_ADC, q.gtype);
+                e.win = (int)win_off[i];
                 ev.push_back(e);
             }
             for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
             tau += q.dur;
-        } else if (q.type == SUB_RF) {
-            flush();  // state now at the pulse start
-            const double z0[3] = {0.0, 0.0, 0.0};
-            const A zero = AdvOf<R>::make(z0, 0.0);
-            launch_plain_rf<R>(c, st, f64 ? s->rf_d[q.content].p : s->rf_f[q.content].p,
-                               (int)(q.seg_end - q.seg_begin), &zero, 2);
         } else {
-            flush();  // state now at the window start
-            const double z0[3] = {0.0, 0.0, 0.0};
-            const A zero = AdvOf<R>::make(z0, 0.0);
-            const void *segs = f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[i])
-                                   : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[i]);
-            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &zero,
-                                d_signal + 2 * q.sample0);
-            for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
-            tau += q.dur;
+            close_span((int)i);  // state now at the start of the unclassified subsequence
+            if (q.type == SUB_ADC) {
+                for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
+                tau += q.dur;
+            }
         }
     }
-    flush();
+    close_span(-1);
+    const int n_ev = (int)ev.size();
+    EvAdv *d_adv = (EvAdv *)scratch(c, 14, n_ev * sizeof(EvAdv));
+    void *d_P = scratch(c, 15, (size_t)n_ev * std::max<int64_t>(Gp, 1) * 4 * sizeof(R));
+    FEvent<R> *d_ev = (FEvent<R> *)scratch(c, 11, n_ev * sizeof(FEvent<R>));
+    upload(c, d_adv, adv.data(), n_ev * sizeof(EvAdv));
+    upload(c, d_ev, ev.data(), n_ev * sizeof(FEvent<R>));
+    launch_event_table<R>(c, d_adv, n_ev, Gp, g->tab[p].d_par64.as<double>(), d_P);
+    bool init_eq = !g->has_M_init;
+    if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+    FusedArgs<R> fa{};
+    fa.K = K;
+    fa.x = g->x.as<float>(); fa.y = g->y.as<float>(); fa.z = g->z.as<float>();
+    fa.T1 = g->T1.as<float>(); fa.T2 = g->T2.as<float>(); fa.dB0 = g->dB0.as<float>();
+    fa.M0 = g->M0.as<float>();
+    for (int t = 0; t < 4; ++t) fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
+    fa.gtype_p = p;
+    fa.gtype_r = g->secondary >= 0 ? g->secondary : p;
+    fa.Mx = M; fa.My = M + Kp; fa.Mz = M + 2 * Kp;
+    fa.T_tab = T_tab;
+    fa.P_raw = d_P;
+    fa.Ablk = Ablk;
+    const double z0[3] = {0.0, 0.0, 0.0};
+    const A zero = AdvOf<R>::make(z0, 0.0);
+    for (const Span &sp : spans) {
+        fa.ev = d_ev + sp.b;
+        fa.n_ev = (int)(sp.e - sp.b);
+        fa.init_eq = init_eq ? 1 : 0;
+        launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
+        init_eq = false;
+        if (sp.fallback < 0) continue;
+        const Subseq &q = s->sub[sp.fallback];
+        if (q.type == SUB_RF) {
+            launch_plain_rf<R>(c, st, f64 ? s->rf_d[q.content].p : s->rf_f[q.content].p,
+                               (int)(q.seg_end - q.seg_begin), &zero,
+                               c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
+        } else {
+            const void *segs =
+                f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[sp.fallback])
+                    : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[sp.fallback]);
+            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &zero,
+                                d_signal + 2 * q.sample0, c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+        }
+    }
     // 4) every sample from the block sums (Eqs. 8, 10)
     if (!wins.empty()) {
         int64_t base_blocks = 0;
@@ -777,7 +818,8 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                                 : (double *)scratch(c, 8, std::max<int64_t>(ns, 1) * 2 * sizeof(double));
         MRSIM_CUDA(cudaMemsetAsync(d_sig, 0, std::max<int64_t>(ns, 1) * 2 * sizeof(double), c->stream));
         const size_t esz = precision == MRSIM_FP64 ? 8 : 4;
-        void *Mst = scratch(c, 9, 3 * K * esz);
+        const int64_t Kp = plane_stride(K);
+        void *Mst = scratch(c, 9, 3 * Kp * esz);
         if (grouped) {
             if (precision == MRSIM_FP64) run_grouped<double>(c, ph, s, g, d_sig, (double *)Mst);
             else run_grouped<float>(c, ph, s, g, d_sig, (float *)Mst);
@@ -788,7 +830,7 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         }
         if (M_final) {
             float *d_out = dev_out ? M_final : (float *)scratch(c, 10, 3 * K * sizeof(float));
-            launch_gather_out(c, K, Mst, (char *)Mst + K * esz, (char *)Mst + 2 * K * esz,
+            launch_gather_out(c, K, Mst, (char *)Mst + Kp * esz, (char *)Mst + 2 * Kp * esz,
                               esz == 8, grouped ? g->perm.as<int32_t>() : nullptr, d_out);
             if (!dev_out)
                 MRSIM_CUDA(cudaMemcpyAsync(M_final, d_out, 3 * K * sizeof(float),
@@ -813,6 +855,68 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
             if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
         }
         fail(MRSIM_EUNSUPPORTED, "batched launcher not available in this build");
+    });
+}
+
+int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
+    if (!c) return MRSIM_EINVAL;
+    static const int allowed[3][4] = {{1, 2, 4, 0}, {1, 2, 0, 0}, {1, 2, 4, 8}};
+    if (param < 0 || param > 2) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
+    bool ok = false;
+    for (int v : allowed[param]) ok |= v != 0 && v == value;
+    if (!ok) return set_err(c, MRSIM_EINVAL, "value not allowed for this tuning parameter");
+    c->tune[param] = value;
+    return MRSIM_OK;
+}
+
+int mrsim_get_tuning(const mrsim_ctx *c, int param, int *value) {
+    if (!c || !value || param < 0 || param > 2) return MRSIM_EINVAL;
+    *value = c->tune[param];
+    return MRSIM_OK;
+}
+
+int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
+                   const mrsim_groups *g, int mode, int precision, int reps) {
+    if (!c) return MRSIM_EINVAL;
+    return guard(c, [&] {
+        if (!ph || !s) fail(MRSIM_EINVAL, "NULL phantom or sequence");
+        if (reps < 1) reps = 1;
+        const int64_t ns = std::max<int64_t>(s->n_samples, 1);
+        DBuf sig = dalloc(ns * 2 * sizeof(double));
+        cudaEvent_t e0, e1;
+        MRSIM_CUDA(cudaEventCreate(&e0));
+        MRSIM_CUDA(cudaEventCreate(&e1));
+        // one parameter at a time, in the order they matter for the mode
+        const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
+        std::vector<std::pair<int, std::vector<int>>> plan;
+        if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
+        plan.push_back({MRSIM_TUNE_PLAIN_RF_NI, {1, 2}});
+        plan.push_back({MRSIM_TUNE_ADC_CTAS_PER_SM, {1, 2, 4, 8}});
+        for (auto &pv : plan) {
+            float best = 1e30f;
+            int best_v = c->tune[pv.first];
+            for (int v : pv.second) {
+                c->tune[pv.first] = v;
+                // a warm-up run, then the timed repetitions
+                int rc = mrsim_run(c, ph, s, g, mode, precision, sig.as<double>(), nullptr,
+                                   MRSIM_OUT_DEVICE);
+                if (rc) fail(rc, c->err);
+                MRSIM_CUDA(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < reps; ++r) {
+                    rc = mrsim_run(c, ph, s, g, mode, precision, sig.as<double>(), nullptr,
+                                   MRSIM_OUT_DEVICE);
+                    if (rc) fail(rc, c->err);
+                }
+                MRSIM_CUDA(cudaEventRecord(e1, c->stream));
+                MRSIM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                MRSIM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; best_v = v; }
+            }
+            c->tune[pv.first] = best_v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
     });
 }
 

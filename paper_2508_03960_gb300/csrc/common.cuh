@@ -52,25 +52,43 @@ struct ADCSegD {
     long long rep;
 };
 
-// Event of the fused grouped kernel.  RF: advance, then M <- A M + b M0 with
-// the combined transition row `row` of the RF table.  ADC: advance into a
-// register copy and add M_xy into the block sum of window `win` (Eq. 9).
-// END: advance and store the state.
+// Event of the fused grouped kernel.  Every event first advances M from the
+// state time in closed form (Eqs. 4-5).  The advance factors as
+//   M_xy <- P(e, g) Q(e, k) M_xy,  Mz <- M0 + (Mz - M0) E1(e, g)
+// with the group factor P = E2 exp(-i 2 pi (pos_p k_p + dB0 tau)) and E1 of
+// the isochromat's primary (with-ADC) group g, which shares pos_p, dB0, T1
+// and T2, taken from a per-(event, group) table, and the per-isochromat
+// factor Q = exp(-i 2 pi sum_a r_a k_a) over the other axes whose moment is
+// nonzero (bit a of `mask`).  RF: then M <- A M + b M0 with combined
+// transition row `row` (+ the isochromat's RF group).  ADC: add Q M_xy into
+// the block sum of window `win` (Eq. 9; P is applied once per group).  END:
+// store the state.
 template <typename R>
 struct FEvent;
+// 48-byte records; op = kind | mask << 2 | gtype << 5
 template <>
 struct FEvent<float> {
-    int kind, gtype;
-    long long row;  // RF: first row of the table of this (content, gtype)
-    long long win;  // ADC: offset of this window's block sums (complex entries)
-    AdvF adv;
+    int op;
+    int row;   // RF: first row of the combined-transition table of (content, gtype)
+    int prow;  // first row of this event's group-factor table
+    int win;   // ADC: offset of this window's block sums (complex entries)
+    float k_hi[4], k_lo[4];  // gamma_bar * moment per axis (cycles/m), split; [3] unused
 };
 template <>
 struct FEvent<double> {
-    int kind, gtype;
-    long long row;
-    long long win;
-    AdvD adv;
+    int op, row, prow, win;
+    double k[4];
+};
+__host__ __device__ constexpr int ev_op(int kind, int mask, int gtype) {
+    return kind | (mask << 2) | (gtype << 5);
+}
+__host__ __device__ constexpr int ev_kind(int op) { return op & 3; }
+__host__ __device__ constexpr int ev_mask(int op) { return (op >> 2) & 7; }
+__host__ __device__ constexpr int ev_gtype(int op) { return (op >> 5) & 7; }
+// per-event inputs of the group-factor table
+struct EvAdv {
+    double kp;   // gamma_bar * moment on the primary axis (cycles/m)
+    double tau;  // time since the state time (s)
 };
 
 // A with-ADC window for the grouped signal kernel (Eqs. 8, 10).

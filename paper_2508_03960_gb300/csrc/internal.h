@@ -72,6 +72,8 @@ struct mrsim_ctx {
     // pinned host staging for uploads of per-run plans
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
+    // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
+    int tune[4] = {4, 2, 2, 0};  // MRSIM_TUNE_FUSED_NI, _PLAIN_RF_NI, _ADC_CTAS_PER_SM, unused
 };
 
 struct mrsim_phantom_t {
@@ -179,7 +181,7 @@ void launch_plain_rf(mrsim_ctx *c, const PlainState &s, const void *segs, int n_
                      const void *adv, int ni);
 template <typename R>
 void launch_plain_adc(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
-                      int64_t n_samples, const void *adv, double *signal);
+                      int64_t n_samples, const void *adv, double *signal, int ctas_per_sm = 2);
 template <typename R>
 void launch_advance(mrsim_ctx *c, const PlainState &s, const void *adv);
 template <typename R>
@@ -215,10 +217,14 @@ struct FusedArgs {
     const FEvent<R> *ev;
     int n_ev;
     const R *T_tab;
+    const void *P_raw;       // per-(event, primary group) advance factors, 4 R each
     double *Ablk;            // complex block sums (interleaved re, im)
 };
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni);
+template <typename R>
+void launch_event_table(mrsim_ctx *c, const EvAdv *d_adv, int n_ev, int64_t G, const double *par,
+                        void *out);
 
 template <typename R>
 struct GSigTables {

@@ -22,6 +22,7 @@
 //                 the sum over groups of the block sum times the group's
 //                 relaxation and phase since the window start.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 
@@ -170,151 +171,323 @@ __device__ __forceinline__ void load_row(const R *p, R (&T)[12]) {
     }
 }
 
+// ---- per-(event, primary group) advance factors ----
+template <typename R>
+struct R4 { R x, y, z, w; };
+
+// P(e, g) = E2 exp(-i 2 pi (pos_g kp_e + dB0_g tau_e)), E1 = exp(-tau_e / T1_g).
+// The phase is reduced modulo one turn in FP64, the rest is evaluated in R.
+template <typename R>
+__global__ void k_event_table(const EvAdv *adv, int n_ev, int64_t G, const double *par,
+                              R4<R> *out) {
+    const int64_t n = (int64_t)n_ev * G;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / G, g = i - e * G;
+        const EvAdv ea = adv[e];
+        const double pos = par[g], T1 = par[G + g], T2 = par[2 * G + g], dB0 = par[3 * G + g];
+        double ph = pos * ea.kp + dB0 * ea.tau;
+        ph -= rint(ph);
+        R c, s;
+        phasor((R)ph, c, s);
+        const R E2 = isinf(T2) ? (R)1 : (R)exp(-ea.tau / T2);
+        const R E1 = isinf(T1) ? (R)1 : (R)exp(-ea.tau / T1);
+        out[i] = R4<R>{E2 * c, -E2 * s, E1, (R)0};
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R4<R> load4(const R4<R> *p) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        return R4<R>{v.x, v.y, v.z, v.w};
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        return R4<R>{a.x, a.y, b.x, b.y};
+    }
+}
+
+constexpr int kBatch = 8;             // with-ADC windows per shared-memory flush
+constexpr int kAccBytes = 32 * 1024;  // block-sum staging per CTA
+
+template <int MASK>
+__device__ __forceinline__ float iso_turns_m(const FEvent<float> &ev, float x, float y, float z) {
+    float t = 0.0f;
+    if constexpr ((MASK & 1) != 0) t += turns_prod(x, ev.k_hi[0], ev.k_lo[0]);
+    if constexpr ((MASK & 2) != 0) t += turns_prod(y, ev.k_hi[1], ev.k_lo[1]);
+    if constexpr ((MASK & 4) != 0) t += turns_prod(z, ev.k_hi[2], ev.k_lo[2]);
+    return t;
+}
+template <int MASK>
+__device__ __forceinline__ double iso_turns_m(const FEvent<double> &ev, double x, double y,
+                                              double z) {
+    double t = 0.0;
+    if constexpr ((MASK & 1) != 0) t += x * ev.k[0];
+    if constexpr ((MASK & 2) != 0) t += y * ev.k[1];
+    if constexpr ((MASK & 4) != 0) t += z * ev.k[2];
+    return t - rint(t);
+}
+
+// Per-isochromat registers of the fused kernel.  Padding isochromats (past
+// K) carry zero magnetization and M0 and valid table rows, so every event
+// leaves them at zero and the event loop needs no validity tests.
 template <typename R, int NI>
-__global__ void __launch_bounds__(kThreads) k_fused(FusedArgs<R> a) {
-    __shared__ R acc_re[kThreads * NI], acc_im[kThreads * NI];
+struct Iso {
+    R mx[NI], my[NI], mz[NI], M0[NI], x[NI], y[NI], z[NI];
+    int pofs[NI];  // primary group (row offset in a group-factor table)
+    int tofs[NI];  // 12 * RF group (offset in a combined-transition table)
+};
+
+// advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1
+template <typename R, int NI, int MASK>
+__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt) {
+    const R4<R> *Pe = Pt + ev.prow;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const R4<R> P = load4(Pe + s.pofs[i]);
+        R fr = P.x, fi = P.y;
+        if constexpr (MASK != 0) {
+            R c, sn;
+            phasor(iso_turns_m<MASK>(ev, s.x[i], s.y[i], s.z[i]), c, sn);
+            const R tr = fr * c + fi * sn;  // P * exp(-i psi)
+            fi = fi * c - fr * sn;
+            fr = tr;
+        }
+        const R nx = fr * s.mx[i] - fi * s.my[i];
+        s.my[i] = fr * s.my[i] + fi * s.mx[i];
+        s.mx[i] = nx;
+        s.mz[i] = s.M0[i] + (s.mz[i] - s.M0[i]) * P.z;
+    }
+}
+
+// transverse magnetization of every isochromat times Q (ADC block-sum terms)
+template <typename R, int NI, int MASK>
+__device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R> &ev, R (&vr)[NI],
+                                             R (&vi)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        vr[i] = s.mx[i];
+        vi[i] = s.my[i];
+        if constexpr (MASK != 0) {
+            R c, sn;
+            phasor(iso_turns_m<MASK>(ev, s.x[i], s.y[i], s.z[i]), c, sn);
+            const R tr = vr[i] * c + vi[i] * sn;
+            vi[i] = vi[i] * c - vr[i] * sn;
+            vr[i] = tr;
+        }
+    }
+}
+
+constexpr int kEvChunk = 128;  // events staged in shared memory at a time
+
+template <typename R, int NI>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
+    k_fused(FusedArgs<R> a) {
+    __shared__ __align__(16) unsigned char acc_raw[kAccBytes];
+    __shared__ __align__(16) FEvent<R> sev[kEvChunk];
+    __shared__ int batch_prow[kBatch], batch_win[kBatch];
+    R *acc = reinterpret_cast<R *>(acc_raw);  // [batch][slot][re, im]
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t chunk = (int64_t)kThreads * NI;
     const int64_t base = blockIdx.x * chunk;
     const int64_t last = min(base + chunk, a.K) - 1;
-    const int32_t *gp = a.gtype_p >= 0 ? a.gid[a.gtype_p] : nullptr;
-    const int32_t *gr = a.gtype_r >= 0 ? a.gid[a.gtype_r] : nullptr;
-    const int32_t g_first = gp ? gp[base] : 0;
-    const int S = gp ? (int)(gp[last] - g_first + 1) : 0;
+    const int32_t *gp = a.gid[a.gtype_p];
+    const int32_t *gr = a.gid[a.gtype_r];
+    const R4<R> *Pt = reinterpret_cast<const R4<R> *>(a.P_raw);
+    const R *Tt = a.T_tab;
+    double *Ablk = a.Ablk;
+    const int32_t g_first = gp[base];
+    const int32_t g_last = gp[last];
+    const int S = (int)(g_last - g_first + 1);  // primary groups in this chunk
+    // windows staged per flush: as many as fit, at most kBatch
+    const int B = max(1, min(kBatch, (int)(kAccBytes / (S * 2 * (int)sizeof(R)))));
+    const bool stage = S * 2 * (int)sizeof(R) <= kAccBytes;
 
-    R mx[NI], my[NI], mz[NI], M0[NI], x[NI], y[NI], z[NI], dB0[NI], r1[NI], r2[NI];
-    int32_t gP[NI], gR[NI];
-    bool ok[NI];
+    // isochromat i of this thread: base + i * kThreads + tid (coalesced per i)
+    Iso<R, NI> s;
+    int32_t key[NI];  // primary group, or a value sorting last for padding
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         const int64_t k = base + (int64_t)i * kThreads + tid;
-        ok[i] = k < a.K;
-        if (ok[i]) {
-            x[i] = a.x[k]; y[i] = a.y[k]; z[i] = a.z[k]; dB0[i] = a.dB0[k]; M0[i] = a.M0[k];
-            const float T1 = a.T1[k], T2 = a.T2[k];
-            r1[i] = isinf(T1) ? (R)0 : (R)kLog2e / (R)T1;
-            r2[i] = isinf(T2) ? (R)0 : (R)kLog2e / (R)T2;
+        if (k < a.K) {
+            s.x[i] = a.x[k]; s.y[i] = a.y[k]; s.z[i] = a.z[k]; s.M0[i] = a.M0[k];
             if (a.init_eq) {
-                mx[i] = 0; my[i] = 0; mz[i] = M0[i];
+                s.mx[i] = 0; s.my[i] = 0; s.mz[i] = s.M0[i];
             } else {
-                mx[i] = a.Mx[k]; my[i] = a.My[k]; mz[i] = a.Mz[k];
+                s.mx[i] = a.Mx[k]; s.my[i] = a.My[k]; s.mz[i] = a.Mz[k];
             }
-            gP[i] = gp ? gp[k] : 0;
-            gR[i] = gr ? gr[k] : 0;
+            key[i] = gp[k];
+            s.tofs[i] = 12 * gr[k];
         } else {
-            x[i] = y[i] = z[i] = dB0[i] = M0[i] = r1[i] = r2[i] = 0;
-            mx[i] = my[i] = mz[i] = 0;
-            gP[i] = 0x7fffffff;  // sorts after every real group
-            gR[i] = 0;
+            s.x[i] = s.y[i] = s.z[i] = s.M0[i] = 0;
+            s.mx[i] = s.my[i] = s.mz[i] = 0;
+            key[i] = 0x7fffffff;
+            s.tofs[i] = 0;
         }
+        s.pofs[i] = min(key[i], g_last);
     }
-    for (int t = tid; t < S; t += kThreads) acc_re[t] = acc_im[t] = 0;
-    // a warp whose isochromats all share one with-ADC group reduces with plain shuffles
-    const int32_t w0 = __shfl_sync(0xffffffffu, gP[0], 0);
+    if (stage)
+        for (int t = tid; t < B * S * 2; t += kThreads) acc[t] = 0;
+    // a warp whose isochromats all share one primary group reduces with plain shuffles
+    const int32_t w0 = __shfl_sync(0xffffffffu, key[0], 0);
     bool uni = true;
 #pragma unroll
-    for (int i = 0; i < NI; ++i) uni &= (!ok[i] || gP[i] == w0);
+    for (int i = 0; i < NI; ++i) uni &= (key[i] == w0 || key[i] == 0x7fffffff);
     const bool warp_uni = __all_sync(0xffffffffu, uni) && w0 != 0x7fffffff;
-    __syncthreads();
 
-    for (int e = 0; e < a.n_ev; ++e) {
-        const FEvent<R> ev = a.ev[e];
-        if (ev.kind == EV_RF) {
-            const int32_t *g = ev.gtype == a.gtype_r ? nullptr : a.gid[ev.gtype];
+    int nb = 0;  // windows staged (uniform)
+    auto flush = [&]() {
+        __syncthreads();
+        for (int t = tid; t < nb * S; t += kThreads) {
+            const int b = t / S, slot = t - b * S;
+            const R sr = acc[2 * t], si = acc[2 * t + 1];
+            if (sr != (R)0 || si != (R)0) {
+                const R4<R> P = load4(Pt + batch_prow[b] + g_first + slot);
+                const int64_t o = 2 * ((int64_t)batch_win[b] + g_first + slot);
+                atomicAdd(&Ablk[o], (double)(P.x * sr - P.y * si));
+                atomicAdd(&Ablk[o + 1], (double)(P.x * si + P.y * sr));
+                acc[2 * t] = 0;
+                acc[2 * t + 1] = 0;
+            }
+        }
+        __syncthreads();
+        nb = 0;
+    };
+
+    auto rf_apply = [&](const FEvent<R> &ev, int gtype) {
+        const int32_t *g = gtype == a.gtype_r ? nullptr : a.gid[gtype];
+        const R *Te = Tt + (int64_t)ev.row * 12;
 #pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                advance<R>(mx[i], my[i], mz[i], M0[i], x[i], y[i], z[i], dB0[i], r1[i], r2[i],
-                           ev.adv);
+        for (int i = 0; i < NI; ++i) {
+            int off = s.tofs[i];
+            if (g) {
                 const int64_t k = base + (int64_t)i * kThreads + tid;
-                const int32_t gi = g ? (ok[i] ? g[k] : 0) : gR[i];
-                R T[12];
-                load_row(a.T_tab + (ev.row + gi) * 12, T);
-                const R nx = T[0] * mx[i] + T[1] * my[i] + T[2] * mz[i] + T[3] * M0[i];
-                const R ny = T[4] * mx[i] + T[5] * my[i] + T[6] * mz[i] + T[7] * M0[i];
-                const R nz = T[8] * mx[i] + T[9] * my[i] + T[10] * mz[i] + T[11] * M0[i];
-                mx[i] = nx;
-                my[i] = ny;
-                mz[i] = nz;
+                off = k < a.K ? 12 * g[k] : 0;
             }
-        } else if (ev.kind == EV_ADC) {
-            R vr[NI], vi[NI];
+            R T[12];
+            load_row(Te + off, T);
+            const R nx = T[0] * s.mx[i] + T[1] * s.my[i] + T[2] * s.mz[i] + T[3] * s.M0[i];
+            const R ny = T[4] * s.mx[i] + T[5] * s.my[i] + T[6] * s.mz[i] + T[7] * s.M0[i];
+            const R nz = T[8] * s.mx[i] + T[9] * s.my[i] + T[10] * s.mz[i] + T[11] * s.M0[i];
+            s.mx[i] = nx;
+            s.my[i] = ny;
+            s.mz[i] = nz;
+        }
+    };
+
+    auto adc_reduce = [&](const FEvent<R> &ev, int gtype, R (&vr)[NI], R (&vi)[NI]) {
+        if (gtype == a.gtype_p && stage) {
+            R *accb = acc + 2 * nb * S;
+            if (warp_uni) {
+                R sr = 0, si = 0;
 #pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                advance_xy<R>(mx[i], my[i], x[i], y[i], z[i], dB0[i], r2[i], ev.adv, vr[i], vi[i]);
-                if (!ok[i]) vr[i] = vi[i] = 0;
-            }
-            if (ev.gtype == a.gtype_p) {
-                if (warp_uni) {
-                    R sr = 0, si = 0;
+                for (int i = 0; i < NI; ++i) { sr += vr[i]; si += vi[i]; }
 #pragma unroll
-                    for (int i = 0; i < NI; ++i) { sr += vr[i]; si += vi[i]; }
-#pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) {
-                        sr += __shfl_xor_sync(0xffffffffu, sr, d);
-                        si += __shfl_xor_sync(0xffffffffu, si, d);
-                    }
-                    if (lane == 0) {
-                        atomicAdd(&acc_re[w0 - g_first], sr);
-                        atomicAdd(&acc_im[w0 - g_first], si);
-                    }
-                } else {
-                    // segmented inclusive scan over lanes (keys sorted along lanes):
-                    // the last lane of each run holds the run's sum
-#pragma unroll
-                    for (int i = 0; i < NI; ++i) {
-                        R sr = vr[i], si = vi[i];
-                        const int32_t key = gP[i];
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const R orr = __shfl_up_sync(0xffffffffu, sr, d);
-                            const R oii = __shfl_up_sync(0xffffffffu, si, d);
-                            const int32_t ok2 = __shfl_up_sync(0xffffffffu, key, d);
-                            if (lane >= d && ok2 == key) { sr += orr; si += oii; }
-                        }
-                        const int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
-                        if ((lane == 31 || nk != key) && ok[i]) {
-                            atomicAdd(&acc_re[key - g_first], sr);
-                            atomicAdd(&acc_im[key - g_first], si);
-                        }
-                    }
+                for (int d = 16; d > 0; d >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, d);
+                    si += __shfl_xor_sync(0xffffffffu, si, d);
                 }
-                __syncthreads();
-                for (int t = tid; t < S; t += kThreads) {
-                    const R sr = acc_re[t], si = acc_im[t];
-                    if (sr != (R)0 || si != (R)0) {
-                        atomicAdd(&a.Ablk[2 * (ev.win + g_first + t)], (double)sr);
-                        atomicAdd(&a.Ablk[2 * (ev.win + g_first + t) + 1], (double)si);
-                        acc_re[t] = 0;
-                        acc_im[t] = 0;
-                    }
+                if (lane == 0) {
+                    atomicAdd(&accb[2 * (w0 - g_first)], sr);
+                    atomicAdd(&accb[2 * (w0 - g_first) + 1], si);
                 }
-                __syncthreads();
             } else {
-                // window of a type the layout is not sorted by: per-isochromat FP64 atomics
-                const int32_t *g = a.gid[ev.gtype];
+                // keys are sorted along the lanes for each i: a segmented
+                // inclusive scan leaves each run's sum in the run's last lane
 #pragma unroll
                 for (int i = 0; i < NI; ++i) {
-                    const int64_t k = base + (int64_t)i * kThreads + tid;
-                    if (ok[i]) {
-                        atomicAdd(&a.Ablk[2 * (ev.win + g[k])], (double)vr[i]);
-                        atomicAdd(&a.Ablk[2 * (ev.win + g[k]) + 1], (double)vi[i]);
+                    R sr = vr[i], si = vi[i];
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const R orr = __shfl_up_sync(0xffffffffu, sr, d);
+                        const R oii = __shfl_up_sync(0xffffffffu, si, d);
+                        const int32_t ok2 = __shfl_up_sync(0xffffffffu, key[i], d);
+                        if (lane >= d && ok2 == key[i]) { sr += orr; si += oii; }
+                    }
+                    const int32_t nk = __shfl_down_sync(0xffffffffu, key[i], 1);
+                    if ((lane == 31 || nk != key[i]) && key[i] != 0x7fffffff) {
+                        atomicAdd(&accb[2 * (key[i] - g_first)], sr);
+                        atomicAdd(&accb[2 * (key[i] - g_first) + 1], si);
                     }
                 }
             }
-        } else {  // EV_END: advance to the span end and store the state
+            if (tid == 0) {
+                batch_prow[nb] = ev.prow;
+                batch_win[nb] = ev.win;
+            }
+            ++nb;
+            if (nb == B) flush();
+        } else {
+            // a window whose groups are not the layout's: P per isochromat, FP64 atomics
+            const int32_t *g = a.gid[gtype];
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
-                advance<R>(mx[i], my[i], mz[i], M0[i], x[i], y[i], z[i], dB0[i], r1[i], r2[i],
-                           ev.adv);
                 const int64_t k = base + (int64_t)i * kThreads + tid;
-                if (ok[i]) {
-                    a.Mx[k] = mx[i];
-                    a.My[k] = my[i];
-                    a.Mz[k] = mz[i];
+                if (k < a.K) {
+                    const R4<R> P = load4(Pt + ev.prow + s.pofs[i]);
+                    const int64_t o = 2 * ((int64_t)ev.win + g[k]);
+                    atomicAdd(&Ablk[o], (double)(P.x * vr[i] - P.y * vi[i]));
+                    atomicAdd(&Ablk[o + 1], (double)(P.x * vi[i] + P.y * vr[i]));
                 }
             }
         }
+    };
+
+#define MRSIM_ADV_CASE(M)                       \
+    case M:                                     \
+        ev_advance<R, NI, M>(s, ev, Pt);        \
+        break;
+#define MRSIM_ADC_CASE(M)                       \
+    case M:                                     \
+        ev_adc_terms<R, NI, M>(s, ev, vr, vi);  \
+        break;
+
+    for (int e0 = 0; e0 < a.n_ev; e0 += kEvChunk) {
+        const int ne = min(kEvChunk, a.n_ev - e0);
+        __syncthreads();
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(a.ev + e0);
+            int4 *dst = reinterpret_cast<int4 *>(sev);
+            const int nw = ne * (int)(sizeof(FEvent<R>) / sizeof(int4));
+            for (int t = tid; t < nw; t += kThreads) dst[t] = src[t];
+        }
+        __syncthreads();
+        for (int e = 0; e < ne; ++e) {
+            const FEvent<R> &ev = sev[e];
+            const int op = ev.op;
+            const int kind = ev_kind(op), mask = ev_mask(op), gtype = ev_gtype(op);
+            if (kind != EV_ADC) {
+                switch (mask) {
+                    MRSIM_ADV_CASE(0) MRSIM_ADV_CASE(1) MRSIM_ADV_CASE(2) MRSIM_ADV_CASE(3)
+                    MRSIM_ADV_CASE(4) MRSIM_ADV_CASE(5) MRSIM_ADV_CASE(6) MRSIM_ADV_CASE(7)
+                }
+                if (kind == EV_RF) {
+                    rf_apply(ev, gtype);
+                } else {  // EV_END: store the state
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const int64_t k = base + (int64_t)i * kThreads + tid;
+                        if (k < a.K) {
+                            a.Mx[k] = s.mx[i];
+                            a.My[k] = s.my[i];
+                            a.Mz[k] = s.mz[i];
+                        }
+                    }
+                }
+            } else {
+                R vr[NI], vi[NI];
+                switch (mask) {
+                    MRSIM_ADC_CASE(0) MRSIM_ADC_CASE(1) MRSIM_ADC_CASE(2) MRSIM_ADC_CASE(3)
+                    MRSIM_ADC_CASE(4) MRSIM_ADC_CASE(5) MRSIM_ADC_CASE(6) MRSIM_ADC_CASE(7)
+                }
+                adc_reduce(ev, gtype, vr, vi);
+            }
+        }
     }
+#undef MRSIM_ADV_CASE
+#undef MRSIM_ADC_CASE
+    if (nb > 0) flush();
 }
 
 template <typename R>
@@ -412,6 +585,17 @@ void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
 }
 
 template <typename R>
+void launch_event_table(mrsim_ctx *c, const EvAdv *d_adv, int n_ev, int64_t G, const double *par,
+                        void *out) {
+    if (n_ev <= 0 || G <= 0) return;
+    KScope ks(c, sizeof(R) == 4 ? "event_table_f32" : "event_table_f64");
+    const int64_t n = (int64_t)n_ev * G;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                                          (int64_t)c->sm_count * 16));
+    k_event_table<R><<<grid, 256, 0, c->stream>>>(d_adv, n_ev, G, par, (R4<R> *)out);
+}
+
+template <typename R>
 void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int n_blk,
                          const void *d_samples, const GSigTables<R> &tab, const double *Ablk,
                          double *signal) {
@@ -423,6 +607,10 @@ void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int
 
 template void launch_precompute<float>(mrsim_ctx *, const PrecompArgs &);
 template void launch_precompute<double>(mrsim_ctx *, const PrecompArgs &);
+template void launch_event_table<float>(mrsim_ctx *, const EvAdv *, int, int64_t,
+                                        const double *, void *);
+template void launch_event_table<double>(mrsim_ctx *, const EvAdv *, int, int64_t,
+                                         const double *, void *);
 template void launch_fused<float>(mrsim_ctx *, const FusedArgs<float> &, int);
 template void launch_fused<double>(mrsim_ctx *, const FusedArgs<double> &, int);
 template void launch_group_signal<float>(mrsim_ctx *, const GWin *, const int4 *, int,

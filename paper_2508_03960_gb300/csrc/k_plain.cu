@@ -400,14 +400,15 @@ void launch_plain_rf(mrsim_ctx *c, const PlainState &s, const void *segs, int n_
 
 template <typename R>
 void launch_plain_adc(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
-                      int64_t n_samples, const void *adv, double *signal) {
+                      int64_t n_samples, const void *adv, double *signal, int ctas_per_sm) {
     using ADS = typename Seg<R>::ADC;
     using A = typename Seg<R>::Adv;
     const A a = *(const A *)adv;
     constexpr int NI = 8;
     const int64_t chunk = (int64_t)kThreads * NI;
     const int64_t n_chunks = (s.K + chunk - 1) / chunk;
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(n_chunks, 2 * c->sm_count)),
+    dim3 grid((unsigned)std::max<int64_t>(
+                  1, std::min<int64_t>(n_chunks, (int64_t)std::max(1, ctas_per_sm) * c->sm_count)),
               (unsigned)((n_samples + kAdcBlockSamples - 1) / kAdcBlockSamples));
     KScope ks(c, sizeof(R) == 4 ? "plain_adc_f32" : "plain_adc_f64");
     k_plain_adc<R, NI><<<grid, kThreads, 0, c->stream>>>(s, (const ADS *)segs, n_seg, n_samples,
@@ -454,7 +455,7 @@ void launch_gather_out(mrsim_ctx *c, int64_t K, const void *Mx, const void *My, 
     template void launch_plain_rf<R>(mrsim_ctx *, const PlainState &, const void *, int,     \
                                      const void *, int);                                     \
     template void launch_plain_adc<R>(mrsim_ctx *, const PlainState &, const void *, int,    \
-                                      int64_t, const void *, double *);                      \
+                                      int64_t, const void *, double *, int);                 \
     template void launch_advance<R>(mrsim_ctx *, const PlainState &, const void *);          \
     template void launch_plain_rf_affine<R>(mrsim_ctx *, const PlainState &, const void *,   \
                                             int, R *);                                       \

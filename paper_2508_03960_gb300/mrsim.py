@@ -26,12 +26,14 @@ G_NONE, G_X, G_Y, G_Z, G_GENERAL = 0, 1, 2, 3, 4
 PLAIN, PLAIN_CACHE, GROUPED, SURROGATE = 0, 1, 2, 3
 FP32, FP64 = 0, 1
 PTR_DEVICE, OUT_DEVICE = 1, 2
+TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM = 0, 1, 2
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
            "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
+           "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
 
@@ -65,6 +67,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_profile_get": (I, [P, I, P, I, P, P]),
         "mrsim_launch_count": (I64, [P]),
         "mrsim_adc_grouped_noalloc": (I, [I64, P, P, P, ctypes.c_int32, P, P, P, I64, P, P, P, P]),
+        "mrsim_set_tuning": (I, [P, I, I]),
+        "mrsim_get_tuning": (I, [P, I, P]),
+        "mrsim_autotune": (I, [P, P, P, P, I, I, I]),
         "mrsim_free_phantom": (None, [P]),
         "mrsim_free_seq": (None, [P]),
         "mrsim_free_groups": (None, [P]),
@@ -213,6 +218,25 @@ def mrsim_profile_get(ctx):
 
 def mrsim_launch_count(ctx) -> int:
     return int(lib().mrsim_launch_count(ctx))
+
+
+def mrsim_set_tuning(ctx, param, value):
+    _check(ctx, lib().mrsim_set_tuning(ctx, param, value), "mrsim_set_tuning")
+
+
+def mrsim_get_tuning(ctx, param) -> int:
+    v = ctypes.c_int()
+    rc = lib().mrsim_get_tuning(ctx, param, ctypes.byref(v))
+    if rc:
+        raise MrsimError(rc, "mrsim_get_tuning")
+    return v.value
+
+
+def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):
+    _check(ctx, lib().mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps),
+           "mrsim_autotune")
+    return {p: mrsim_get_tuning(ctx, p) for p in (TUNE_FUSED_NI, TUNE_PLAIN_RF_NI,
+                                                   TUNE_ADC_CTAS_PER_SM)}
 
 
 def mrsim_adc_grouped_noalloc(K, mx, my, gid, n_groups, gpos, gdB0, gT2, n_samples, tau, kmom,
