@@ -106,6 +106,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
+def fused_traffic(K):
+    """DRAM bytes per k_fused launch from the committed ncu summary, scaled by
+    K; None once the kernel source differs from the profiled one."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fused_grouped_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in ("k_grouped.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_03960_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("source_sha256"):
+        return None
+    return int(rec["dram_bytes_per_isochromat"] * K)
+
+
 def golden_check(name, sig, ph_digest, seq_digest):
     path = os.path.join(GOLDEN, f"{name}_27m_oracle.npz")
     if not os.path.exists(path):
@@ -323,7 +341,7 @@ def main():
         peak = 2 * 128 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = flops / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": fused_traffic(ph.K),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz from "
                                f"MEASURED_PEAKS.json ({pk_kind})",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": round(avg_s * 1e3, 4),
