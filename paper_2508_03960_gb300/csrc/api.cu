@@ -102,6 +102,9 @@ namespace {
 
 std::atomic<uint64_t> g_uid{1};
 
+// isochromats per fused-kernel chunk at the context's tuning
+inline int64_t kFusedChunk(const mrsim_ctx *c) { return 256LL * c->tune[MRSIM_TUNE_FUSED_NI]; }
+
 inline AdvF make_adv_f(const double mom[3], double tau) {
     auto sp = [](double v, float &hi, float &lo) {
         hi = (float)v;
@@ -386,65 +389,58 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
 }
 
 // -------------------------------------------------------------- grouped ----
+// Host-side plan of one grouped simulation: combined-transition tables, block
+// sums of every known with-ADC window, the event list of every span, the
+// fallback subsequence after each span and the group-signal blocks.
 template <typename R>
-void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
-                 const mrsim_groups *g, double *d_signal, R *M) {
-    const int64_t K = ph->K;
-    const mrsim_seq &dev = *s;
-    const bool f64 = sizeof(R) == 8;
-    using A = typename AdvOf<R>::T;
-    // 1) combined transitions for every (content, gradient type) of a known with-RF
-    std::map<std::pair<int, int>, int64_t> row_of;
+struct GPlan {
+    int p = 0;          // primary (layout / group-factor) gradient type
+    int64_t Gp = 0;     // its group count
+    std::vector<std::pair<std::pair<int, int>, int64_t>> tabs;  // ((content, gtype), row)
     int64_t rows = 0;
-    for (const Subseq &q : s->sub) {
-        if (q.type != SUB_RF || q.gtype == G_GENERAL) continue;
-        auto key = std::make_pair(q.content, q.gtype);
-        if (!row_of.count(key)) {
-            row_of[key] = rows;
-            rows += g->n_groups[q.gtype];
-        }
-    }
-    if (rows * 12 > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "combined-transition table too large");
-    R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(rows, 1) * 12 * sizeof(R));
-    for (auto &kv : row_of) {
-        const int cid = kv.first.first, gt = kv.first.second;
-        const Subseq &q = s->sub[s->content_first[cid]];
-        PrecompArgs pa{f64 ? s->rf_d[cid].p : s->rf_f[cid].p, dev.rf_off[cid].as<int64_t>(),
-                       (int)(q.seg_end - q.seg_begin), s->content_steps[cid], gt,
-                       g->n_groups[gt], g->tab[gt].d_par64.as<double>(), T_tab + kv.second * 12};
-        launch_precompute<R>(c, pa);
-    }
-    // 2) block-sum storage per known with-ADC window
     std::vector<GWin> wins;
-    std::vector<int64_t> win_off(s->sub.size(), -1);
     int64_t ablk_n = 0;
-    for (size_t i = 0; i < s->sub.size(); ++i) {
-        const Subseq &q = s->sub[i];
-        if (q.type != SUB_ADC || q.gtype == G_GENERAL || q.n_samples == 0) continue;
-        win_off[i] = ablk_n;
-        wins.push_back(GWin{q.gtype, (int)g->n_groups[q.gtype], ablk_n, q.sample0,
-                            (int)q.n_samples, 0});
-        ablk_n += g->n_groups[q.gtype];
-    }
-    if (ablk_n > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many block sums");
-    double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double));
-    MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(ablk_n, 1) * 2 * sizeof(double),
-                               c->stream));
-    // 3) spans of known-type events; unknown types fall back to plain kernels.
-    //    All events of the run go into one list; each span is a slice of it.
-    const int64_t Kp = plane_stride(K);
-    PlainState st = sorted_state(g, M, M + Kp, M + 2 * Kp);
-    const int p = g->primary;  // layout / group-factor gradient type
-    const int64_t Gp = g->n_groups[p];
     std::vector<FEvent<R>> ev;
     std::vector<EvAdv> adv;
     struct Span { int64_t b, e; int fallback; };
     std::vector<Span> spans;
+    std::vector<int4> blk;  // group-signal blocks (window, first sample, g0, g1)
+};
+
+template <typename R>
+void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan<R> &P) {
+    // 1) combined transitions for every (content, gradient type) of a known with-RF
+    std::map<std::pair<int, int>, int64_t> row_of;
+    for (const Subseq &q : s->sub) {
+        if (q.type != SUB_RF || q.gtype == G_GENERAL) continue;
+        auto key = std::make_pair(q.content, q.gtype);
+        if (!row_of.count(key)) {
+            row_of[key] = P.rows;
+            P.tabs.push_back({key, P.rows});
+            P.rows += g->n_groups[q.gtype];
+        }
+    }
+    if (P.rows * 12 > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "combined-transition table too large");
+    // 2) block-sum storage per known with-ADC window
+    std::vector<int64_t> win_off(s->sub.size(), -1);
+    for (size_t i = 0; i < s->sub.size(); ++i) {
+        const Subseq &q = s->sub[i];
+        if (q.type != SUB_ADC || q.gtype == G_GENERAL || q.n_samples == 0) continue;
+        win_off[i] = P.ablk_n;
+        P.wins.push_back(GWin{q.gtype, (int)g->n_groups[q.gtype], P.ablk_n, q.sample0,
+                              (int)q.n_samples, 0});
+        P.ablk_n += g->n_groups[q.gtype];
+    }
+    if (P.ablk_n > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many block sums");
+    // 3) spans of known-type events; unknown types close the span (plain fallback)
+    P.p = g->primary;
+    P.Gp = g->n_groups[P.p];
+    const int p = P.p;
     int64_t span_begin = 0;
     double mom[3] = {0, 0, 0}, tau = 0.0;
     auto make = [&](int kind, int gtype) {
         FEvent<R> e{};
-        const int64_t prow = (int64_t)ev.size() * Gp;
+        const int64_t prow = (int64_t)P.ev.size() * P.Gp;
         if (prow > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many events x groups");
         e.prow = (int)prow;
         double k[3];
@@ -461,13 +457,13 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             }
         }
         e.op = ev_op(kind, mask, gtype);
-        adv.push_back(EvAdv{p >= 1 ? k[p - 1] : 0.0, tau});
+        P.adv.push_back(EvAdv{p >= 1 ? k[p - 1] : 0.0, tau});
         return e;
     };
     auto close_span = [&](int fallback) {
-        ev.push_back(make(EV_END, G_NONE));
-        spans.push_back(Span{span_begin, (int64_t)ev.size(), fallback});
-        span_begin = (int64_t)ev.size();
+        P.ev.push_back(make(EV_END, G_NONE));
+        P.spans.push_back({span_begin, (int64_t)P.ev.size(), fallback});
+        span_begin = (int64_t)P.ev.size();
         mom[0] = mom[1] = mom[2] = 0.0;
         tau = 0.0;
     };
@@ -479,14 +475,14 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         } else if (q.type == SUB_RF && q.gtype != G_GENERAL) {
             FEvent<R> e = make(EV_RF, q.gtype);
             e.row = (int)row_of.at(std::make_pair(q.content, q.gtype));
-            ev.push_back(e);
+            P.ev.push_back(e);
             mom[0] = mom[1] = mom[2] = 0.0;
             tau = 0.0;
         } else if (q.type == SUB_ADC && q.gtype != G_GENERAL) {
             if (q.n_samples > 0) {
                 FEvent<R> e = make(EV_ADC, q.gtype);
                 e.win = (int)win_off[i];
-                ev.push_back(e);
+                P.ev.push_back(e);
             }
             for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
             tau += q.dur;
@@ -499,35 +495,105 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         }
     }
     close_span(-1);
-    const int n_ev = (int)ev.size();
-    EvAdv *d_adv = (EvAdv *)scratch(c, 14, n_ev * sizeof(EvAdv));
-    void *d_P = scratch(c, 15, (size_t)n_ev * std::max<int64_t>(Gp, 1) * 4 * sizeof(R));
-    FEvent<R> *d_ev = (FEvent<R> *)scratch(c, 11, n_ev * sizeof(FEvent<R>));
-    upload(c, d_adv, adv.data(), n_ev * sizeof(EvAdv));
-    upload(c, d_ev, ev.data(), n_ev * sizeof(FEvent<R>));
-    launch_event_table<R>(c, d_adv, n_ev, Gp, g->tab[p].d_par64.as<double>(), d_P);
-    bool init_eq = !g->has_M_init;
-    if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+    // 4) group-signal blocks: 256 samples x a slice of the groups
+    if (!P.wins.empty()) {
+        int64_t base_blocks = 0, max_g = 1;
+        for (const GWin &w : P.wins) {
+            base_blocks += (w.n_samples + 255) / 256;
+            max_g = std::max<int64_t>(max_g, w.n_groups);
+        }
+        const int64_t want = 4LL * c->sm_count;
+        int64_t split = std::max<int64_t>(1, (want + base_blocks - 1) / base_blocks);
+        split = std::min<int64_t>(split, (max_g + 255) / 256);
+        for (size_t wi = 0; wi < P.wins.size(); ++wi) {
+            const GWin &w = P.wins[wi];
+            const int64_t gs =
+                std::max<int64_t>(256, ((w.n_groups + split - 1) / split + 255) / 256 * 256);
+            for (int64_t s0 = 0; s0 < w.n_samples; s0 += 256)
+                for (int64_t g0 = 0; g0 < w.n_groups; g0 += gs)
+                    P.blk.push_back(make_int4((int)wi, (int)(w.sample0 + s0), (int)g0,
+                                              (int)std::min<int64_t>(w.n_groups, g0 + gs)));
+        }
+    }
+}
+
+template <typename R>
+PrecompArgs precomp_args(const mrsim_seq *s, const mrsim_groups *g, int cid, int gt, R *out) {
+    const Subseq &q = s->sub[s->content_first[cid]];
+    const bool f64 = sizeof(R) == 8;
+    return PrecompArgs{f64 ? s->rf_d[cid].p : s->rf_f[cid].p, s->rf_off[cid].as<int64_t>(),
+                       (int)(q.seg_end - q.seg_begin), s->content_steps[cid], gt,
+                       g->n_groups[gt], g->tab[gt].d_par64.as<double>(), out};
+}
+
+template <typename R>
+GSigTables<R> sig_tables(const mrsim_groups *g) {
+    const bool f64 = sizeof(R) == 8;
+    GSigTables<R> tab{};
+    for (int t = 0; t < 4; ++t) {
+        if (!g->built[t]) continue;
+        tab.pos[t] = f64 ? (const R *)g->tab[t].d_pos64.p : (const R *)g->tab[t].d_pos.p;
+        tab.dB0[t] = f64 ? (const R *)g->tab[t].d_dB064.p : (const R *)g->tab[t].d_dB0.p;
+        tab.rT2[t] = f64 ? (const R *)g->tab[t].d_rT264.p : (const R *)g->tab[t].d_rT2.p;
+    }
+    return tab;
+}
+
+template <typename R>
+FusedArgs<R> fused_args(const mrsim_groups *g, int p, R *Mx, R *My, R *Mz, const R *T_tab,
+                        const void *P_raw, double *Ablk) {
     FusedArgs<R> fa{};
-    fa.K = K;
+    fa.K = g->K;
     fa.x = g->x.as<float>(); fa.y = g->y.as<float>(); fa.z = g->z.as<float>();
     fa.T1 = g->T1.as<float>(); fa.T2 = g->T2.as<float>(); fa.dB0 = g->dB0.as<float>();
     fa.M0 = g->M0.as<float>();
     for (int t = 0; t < 4; ++t) fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
     fa.gtype_p = p;
     fa.gtype_r = g->secondary >= 0 ? g->secondary : p;
-    fa.Mx = M; fa.My = M + Kp; fa.Mz = M + 2 * Kp;
+    fa.Mx = Mx; fa.My = My; fa.Mz = Mz;
     fa.T_tab = T_tab;
-    fa.P_raw = d_P;
+    fa.P_raw = P_raw;
     fa.Ablk = Ablk;
+    fa.init_eq = g->has_M_init ? 0 : 1;
+    return fa;
+}
+
+template <typename R>
+void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
+                 const mrsim_groups *g, double *d_signal, R *M) {
+    const int64_t K = ph->K;
+    const bool f64 = sizeof(R) == 8;
+    using A = typename AdvOf<R>::T;
+    GPlan<R> P;
+    plan_grouped<R>(c, s, g, P);
+    R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(P.rows, 1) * 12 * sizeof(R));
+    for (auto &t : P.tabs)
+        launch_precompute<R>(c, precomp_args<R>(s, g, t.first.first, t.first.second,
+                                                 T_tab + t.second * 12));
+    double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double));
+    MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double),
+                               c->stream));
+    const int64_t Kp = plane_stride(K);
+    PlainState st = sorted_state(g, M, M + Kp, M + 2 * Kp);
+    const int n_ev = (int)P.ev.size();
+    EvAdv *d_adv = (EvAdv *)scratch(c, 14, n_ev * sizeof(EvAdv));
+    void *d_P = scratch(c, 15, (size_t)n_ev * std::max<int64_t>(P.Gp, 1) * 4 * sizeof(R));
+    FEvent<R> *d_ev = (FEvent<R> *)scratch(c, 11, n_ev * sizeof(FEvent<R>));
+    upload(c, d_adv, P.adv.data(), n_ev * sizeof(EvAdv));
+    upload(c, d_ev, P.ev.data(), n_ev * sizeof(FEvent<R>));
+    const int prim = P.p;
+    launch_event_table<R>(c, d_adv, n_ev, P.Gp, g->tab[prim].d_par64.as<double>(), d_P);
+    if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+    FusedArgs<R> fa = fused_args<R>(g, P.p, M, M + Kp, M + 2 * Kp, T_tab, d_P, Ablk);
     const double z0[3] = {0.0, 0.0, 0.0};
     const A zero = AdvOf<R>::make(z0, 0.0);
-    for (const Span &sp : spans) {
+    bool first = true;
+    for (const auto &sp : P.spans) {
         fa.ev = d_ev + sp.b;
         fa.n_ev = (int)(sp.e - sp.b);
-        fa.init_eq = init_eq ? 1 : 0;
+        fa.init_eq = (first && !g->has_M_init) ? 1 : 0;
         launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
-        init_eq = false;
+        first = false;
         if (sp.fallback < 0) continue;
         const Subseq &q = s->sub[sp.fallback];
         if (q.type == SUB_RF) {
@@ -536,49 +602,192 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                                c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
         } else {
             const void *segs =
-                f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[sp.fallback])
-                    : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[sp.fallback]);
+                f64 ? (const void *)(s->adc_d.as<ADCSegD>() + s->adc_off[sp.fallback])
+                    : (const void *)(s->adc_f.as<ADCSegF>() + s->adc_off[sp.fallback]);
             launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &zero,
                                 d_signal + 2 * q.sample0, c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
         }
     }
-    // 4) every sample from the block sums (Eqs. 8, 10)
-    if (!wins.empty()) {
-        int64_t base_blocks = 0;
-        int64_t max_g = 1;
-        for (const GWin &w : wins) {
-            base_blocks += (w.n_samples + 255) / 256;
-            max_g = std::max<int64_t>(max_g, w.n_groups);
-        }
-        const int64_t want = 4LL * c->sm_count;
-        int64_t split = std::max<int64_t>(1, (want + base_blocks - 1) / base_blocks);
-        split = std::min<int64_t>(split, (max_g + 255) / 256);
-        std::vector<int4> blk;
-        for (size_t wi = 0; wi < wins.size(); ++wi) {
-            const GWin &w = wins[wi];
-            const int64_t gs = std::max<int64_t>(256, ((w.n_groups + split - 1) / split + 255) / 256 * 256);
-            for (int64_t s0 = 0; s0 < w.n_samples; s0 += 256)
-                for (int64_t g0 = 0; g0 < w.n_groups; g0 += gs)
-                    blk.push_back(make_int4((int)wi, (int)(w.sample0 + s0), (int)g0,
-                                            (int)std::min<int64_t>(w.n_groups, g0 + gs)));
-        }
-        GWin *dw = (GWin *)scratch(c, 12, wins.size() * sizeof(GWin));
-        int4 *db = (int4 *)scratch(c, 13, blk.size() * sizeof(int4));
-        upload(c, dw, wins.data(), wins.size() * sizeof(GWin));
-        upload(c, db, blk.data(), blk.size() * sizeof(int4));
-        GSigTables<R> tab{};
-        for (int t = 0; t < 4; ++t) {
-            if (!g->built[t]) continue;
-            tab.pos[t] = f64 ? (const R *)g->tab[t].d_pos64.p : (const R *)g->tab[t].d_pos.p;
-            tab.dB0[t] = f64 ? (const R *)g->tab[t].d_dB064.p : (const R *)g->tab[t].d_dB0.p;
-            tab.rT2[t] = f64 ? (const R *)g->tab[t].d_rT264.p : (const R *)g->tab[t].d_rT2.p;
-        }
-        launch_group_signal<R>(c, dw, db, (int)blk.size(),
-                               f64 ? dev.gs_d.p : dev.gs_f.p, tab, Ablk, d_signal);
-        sync(c);
-    } else {
-        sync(c);
+    // every sample from the block sums (Eqs. 8, 10)
+    if (!P.blk.empty()) {
+        GWin *dw = (GWin *)scratch(c, 12, P.wins.size() * sizeof(GWin));
+        int4 *db = (int4 *)scratch(c, 13, P.blk.size() * sizeof(int4));
+        upload(c, dw, P.wins.data(), P.wins.size() * sizeof(GWin));
+        upload(c, db, P.blk.data(), P.blk.size() * sizeof(int4));
+        launch_group_signal<R>(c, dw, db, (int)P.blk.size(),
+                               f64 ? s->gs_d.p : s->gs_f.p, sig_tables<R>(g), Ablk, d_signal);
     }
+    sync(c);
+}
+
+// --------------------------------------------------------------- batch ----
+// All jobs' device work in four launches (batched transition precompute,
+// batched group-factor tables, the persistent fused kernel over every job's
+// chunks, batched group signal), captured once into a CUDA graph and reused
+// while the same jobs are run again.
+struct BatchCache {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<DBuf> bufs;
+    std::vector<double *> d_sig;
+    std::vector<int64_t> n_samples;
+    ~BatchCache() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+std::map<const mrsim_ctx *, std::unique_ptr<BatchCache>> &batch_caches() {
+    static std::map<const mrsim_ctx *, std::unique_ptr<BatchCache>> m;
+    return m;
+}
+
+void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsim_seq *const *s,
+               const mrsim_groups *const *g, double *const *signals) {
+    using R = float;
+    std::vector<uint64_t> key;
+    for (int i = 0; i < n; ++i) {
+        key.push_back(ph[i]->uid);
+        key.push_back(s[i]->uid);
+        key.push_back(g[i]->uid);
+    }
+    key.push_back((uint64_t)c->tune[MRSIM_TUNE_FUSED_NI]);
+    auto &slot = batch_caches()[c];
+    if (!slot || slot->key != key) {
+        auto bc = std::make_unique<BatchCache>();
+        bc->key = key;
+        std::vector<GPlan<R>> plans(n);
+        for (int i = 0; i < n; ++i) {
+            plan_grouped<R>(c, s[i], g[i], plans[i]);
+            if (plans[i].spans.size() != 1)
+                fail(MRSIM_EUNSUPPORTED, "batched jobs need known gradient types only");
+        }
+        // sizes and per-job offsets inside shared device buffers
+        int64_t rows = 0, ablk = 0, nev = 0, ptab = 0, nsig = 0, blks = 0, nblk = 0;
+        std::vector<int64_t> o_rows(n), o_ablk(n), o_ev(n), o_p(n), o_sig(n), o_blk(n);
+        for (int i = 0; i < n; ++i) {
+            o_rows[i] = rows; rows += plans[i].rows;
+            o_ablk[i] = ablk; ablk += plans[i].ablk_n;
+            o_ev[i] = nev; nev += (int64_t)plans[i].ev.size();
+            o_p[i] = ptab; ptab += (int64_t)plans[i].ev.size() * plans[i].Gp;
+            o_sig[i] = nsig; nsig += s[i]->n_samples;
+            o_blk[i] = blks; blks += (g[i]->K + kFusedChunk(c) - 1) / kFusedChunk(c);
+            nblk += (int64_t)plans[i].blk.size();
+        }
+        auto alloc = [&](size_t bytes) {
+            bc->bufs.push_back(dalloc(std::max<size_t>(bytes, 256)));
+            return bc->bufs.back().p;
+        };
+        R *T = (R *)alloc(rows * 12 * sizeof(R));
+        double *Ab = (double *)alloc(ablk * 2 * sizeof(double));
+        FEvent<R> *ev = (FEvent<R> *)alloc(nev * sizeof(FEvent<R>));
+        EvAdv *adv = (EvAdv *)alloc(nev * sizeof(EvAdv));
+        void *Pt = alloc(ptab * 4 * sizeof(R));
+        double *sig = (double *)alloc(std::max<int64_t>(nsig, 1) * 2 * sizeof(double));
+        // descriptors
+        std::vector<PrecompArgs> pre;
+        std::vector<int64_t> pre_off{0};
+        std::vector<EvTabJob> et;
+        std::vector<int64_t> et_off{0};
+        std::vector<FusedArgs<R>> fj;
+        std::vector<int64_t> fj_off{0};
+        std::vector<GSigJob<R>> gj;
+        std::vector<int4> gblk;
+        std::vector<int> gblk_job;
+        std::vector<GWin> allwin;
+        for (int i = 0; i < n; ++i) {
+            GPlan<R> &P = plans[i];
+            for (auto &t : P.tabs) {
+                pre.push_back(precomp_args<R>(s[i], g[i], t.first.first, t.first.second,
+                                              T + (o_rows[i] + t.second) * 12));
+                pre_off.push_back(pre_off.back() + g[i]->n_groups[t.first.second]);
+            }
+            const int prim = P.p;
+            et.push_back(EvTabJob{adv + o_ev[i], P.Gp, g[i]->tab[prim].d_par64.as<double>(),
+                                  (R *)Pt + o_p[i] * 4});
+            et_off.push_back(et_off.back() + (int64_t)P.ev.size() * P.Gp);
+            FusedArgs<R> fa = fused_args<R>(g[i], P.p, nullptr, nullptr, nullptr,
+                                            T + o_rows[i] * 12, (R *)Pt + o_p[i] * 4,
+                                            Ab + 2 * o_ablk[i]);
+            fa.ev = ev + o_ev[i];
+            fa.n_ev = (int)P.ev.size();
+            fa.init_eq = 1;
+            if (g[i]->has_M_init) fail(MRSIM_EUNSUPPORTED, "batched jobs start from equilibrium");
+            fj.push_back(fa);
+            fj_off.push_back(fj_off.back() + (g[i]->K + kFusedChunk(c) - 1) / kFusedChunk(c));
+            const int64_t w0 = (int64_t)allwin.size();
+            for (GWin w : P.wins) allwin.push_back(w);
+            gj.push_back(GSigJob<R>{nullptr, s[i]->gs_f.p, sig_tables<R>(g[i]),
+                                    Ab + 2 * o_ablk[i], sig + 2 * o_sig[i]});
+            gj.back().wins = (const GWin *)(intptr_t)w0;  // fixed up after upload
+            for (int4 b : P.blk) {
+                gblk.push_back(b);
+                gblk_job.push_back(i);
+            }
+            upload(c, ev + o_ev[i], P.ev.data(), P.ev.size() * sizeof(FEvent<R>));
+            upload(c, adv + o_ev[i], P.adv.data(), P.adv.size() * sizeof(EvAdv));
+            bc->d_sig.push_back(sig + 2 * o_sig[i]);
+            bc->n_samples.push_back(s[i]->n_samples);
+        }
+        GWin *d_win = (GWin *)alloc(std::max<size_t>(allwin.size(), 1) * sizeof(GWin));
+        upload(c, d_win, allwin.data(), allwin.size() * sizeof(GWin));
+        for (auto &j : gj) j.wins = d_win + (intptr_t)j.wins;
+        auto up = [&](const void *src, size_t bytes) {
+            void *d = alloc(bytes);
+            upload(c, d, src, bytes);
+            return d;
+        };
+        auto *d_pre = (PrecompArgs *)up(pre.data(), pre.size() * sizeof(PrecompArgs));
+        auto *d_pre_off = (int64_t *)up(pre_off.data(), pre_off.size() * sizeof(int64_t));
+        auto *d_et = (EvTabJob *)up(et.data(), et.size() * sizeof(EvTabJob));
+        auto *d_et_off = (int64_t *)up(et_off.data(), et_off.size() * sizeof(int64_t));
+        auto *d_fj = (FusedArgs<R> *)up(fj.data(), fj.size() * sizeof(FusedArgs<R>));
+        auto *d_fj_off = (int64_t *)up(fj_off.data(), fj_off.size() * sizeof(int64_t));
+        auto *d_gj = (GSigJob<R> *)up(gj.data(), gj.size() * sizeof(GSigJob<R>));
+        auto *d_gblk = (int4 *)up(gblk.data(), std::max<size_t>(gblk.size(), 1) * sizeof(int4));
+        auto *d_gbj = (int *)up(gblk_job.data(), std::max<size_t>(gblk_job.size(), 1) * sizeof(int));
+        auto *d_cnt = (unsigned long long *)alloc(sizeof(unsigned long long));
+        sync(c);
+        // capture the four launches
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        cudaGraph_t graph = nullptr;
+        MRSIM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t cap = cudaSuccess;
+        try {
+            cap = cudaMemsetAsync(Ab, 0, std::max<int64_t>(ablk, 1) * 2 * sizeof(double), c->stream);
+            if (cap == cudaSuccess)
+                cap = cudaMemsetAsync(sig, 0, std::max<int64_t>(nsig, 1) * 2 * sizeof(double),
+                                      c->stream);
+            if (cap == cudaSuccess) cap = cudaMemsetAsync(d_cnt, 0, sizeof(*d_cnt), c->stream);
+            launch_precompute_batch<R>(c, d_pre, d_pre_off, (int)pre.size(), pre_off.back());
+            launch_event_table_batch<R>(c, d_et, d_et_off, n, et_off.back());
+            launch_fused_batch<R>(c, d_fj, d_fj_off, n, d_cnt, c->tune[MRSIM_TUNE_FUSED_NI]);
+            launch_group_signal_batch<R>(c, d_gj, d_gblk, d_gbj, (int)gblk.size());
+        } catch (...) {
+            cudaStreamEndCapture(c->stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            c->prof_on = prof;
+            throw;
+        }
+        const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+        c->prof_on = prof;
+        MRSIM_CUDA(cap);
+        MRSIM_CUDA(end);
+        const cudaError_t inst = cudaGraphInstantiate(&bc->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        MRSIM_CUDA(inst);
+        slot = std::move(bc);
+    }
+    {
+        KScope ks(c, "batch_graph");
+        MRSIM_CUDA(cudaGraphLaunch(slot->exec, c->stream));
+    }
+    for (int i = 0; i < n; ++i)
+        if (slot->n_samples[i] > 0)
+            MRSIM_CUDA(cudaMemcpyAsync(signals[i], slot->d_sig[i],
+                                       slot->n_samples[i] * 2 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
 }
 
 int set_err(mrsim_ctx *c, int code, const std::string &m) {
@@ -657,6 +866,7 @@ void mrsim_destroy(mrsim_ctx *c) {
     for (auto &b : c->scratch) b.reset();
     c->dev_err.reset();
     if (c->pinned) cudaFreeHost(c->pinned);
+    batch_caches().erase(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -720,6 +930,7 @@ int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t 
             fail(MRSIM_EINVAL, "NULL sequence array");
         MRSIM_CUDA(cudaSetDevice(c->device));
         s->ctx = c;
+        s->uid = g_uid++;
         s->n_seg = n_seg;
         s->dt.assign(dt, dt + n_seg);
         s->rep.assign(rep, rep + n_seg);
@@ -758,6 +969,7 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
         if (!ph || !s) fail(MRSIM_EINVAL, "NULL phantom or sequence");
         MRSIM_CUDA(cudaSetDevice(c->device));
         g->ctx = c;
+        g->uid = g_uid++;
         g->phantom_uid = ph->uid;
         g->K = ph->K;
         int cnt_rf[5] = {0, 0, 0, 0, 0}, cnt_adc[5] = {0, 0, 0, 0, 0};
@@ -853,8 +1065,13 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
         for (int i = 0; i < n_jobs; ++i) {
             if (!ph[i] || !s[i] || !g[i] || !signals[i]) fail(MRSIM_EINVAL, "NULL batch entry");
             if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
+            for (const Subseq &q : s[i]->sub)
+                if ((q.type == SUB_RF || q.type == SUB_ADC) && q.gtype != G_GENERAL &&
+                    !g[i]->built[q.gtype])
+                    fail(MRSIM_ESTATE, "groups lack a gradient type the sequence uses");
         }
-        fail(MRSIM_EUNSUPPORTED, "batched launcher not available in this build");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        run_batch(c, n_jobs, ph, s, g, signals);
     });
 }
 

@@ -107,6 +107,7 @@ struct GroupTable {
 
 struct mrsim_seq {
     mrsim_ctx *ctx = nullptr;
+    uint64_t uid = 0;
     int64_t n_seg = 0;
     std::vector<double> dt;
     std::vector<int32_t> rep;
@@ -129,6 +130,7 @@ struct mrsim_seq {
 
 struct mrsim_groups {
     mrsim_ctx *ctx = nullptr;
+    uint64_t uid = 0;
     uint64_t phantom_uid = 0;
     int64_t K = 0;
     bool built[4] = {false, false, false, false};
@@ -230,6 +232,34 @@ template <typename R>
 struct GSigTables {
     const R *pos[4], *dB0[4], *rT2[4];
 };
+// batched forms (one launch for many jobs)
+struct EvTabJob {
+    const EvAdv *adv;
+    int64_t G;
+    const double *par;
+    void *out;
+};
+template <typename R>
+struct GSigJob {
+    const GWin *wins;
+    const void *samples;
+    GSigTables<R> tab;
+    const double *Ablk;
+    double *signal;
+};
+template <typename R>
+void launch_precompute_batch(mrsim_ctx *c, const PrecompArgs *d_tabs, const int64_t *d_off,
+                             int n_tab, int64_t total);
+template <typename R>
+void launch_event_table_batch(mrsim_ctx *c, const EvTabJob *d_jobs, const int64_t *d_off,
+                              int n_jobs, int64_t total);
+template <typename R>
+void launch_fused_batch(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
+                        int n_jobs, unsigned long long *d_counter, int ni);
+template <typename R>
+void launch_group_signal_batch(mrsim_ctx *c, const GSigJob<R> *d_jobs, const int4 *d_blk,
+                               const int *d_blk_job, int n_blk);
+
 template <typename R>
 void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int n_blk,
                          const void *d_samples, const GSigTables<R> &tab, const double *Ablk,

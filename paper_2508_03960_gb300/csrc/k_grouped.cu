@@ -54,15 +54,19 @@ __device__ __forceinline__ void compose(double (&C)[12], const double (&B)[12],
     }
 }
 
+// Combined transition of group g of one table (all threads of the CTA).
 template <typename R>
-__global__ void __launch_bounds__(kPreThreads) k_precompute(const typename SegT<R>::RF *segs,
-                                                            const int64_t *seg_off, int n_seg,
-                                                            int64_t n_steps, int gtype,
-                                                            const double *par, int64_t G,
-                                                            R *out) {
+__device__ void precompute_group(const PrecompArgs &a, int64_t g, double (*P)[12]) {
     using RFS = typename SegT<R>::RF;
-    __shared__ double P[kPreThreads][12];
-    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    const RFS *segs = (const RFS *)a.segs;
+    const int64_t *seg_off = a.seg_off;
+    const int n_seg = a.n_seg;
+    const int64_t n_steps = a.n_steps;
+    const int gtype = a.gtype;
+    const double *par = a.par;
+    const int64_t G = a.n_groups;
+    R *out = (R *)a.out;
+    {
         const R pos = (R)par[g], T1 = (R)par[G + g], T2 = (R)par[2 * G + g];
         const R dB0 = (R)par[3 * G + g], b1 = (R)par[4 * G + g];
         const R iT1 = isinf((double)T1) ? (R)0 : (R)1 / T1;
@@ -146,6 +150,28 @@ __global__ void __launch_bounds__(kPreThreads) k_precompute(const typename SegT<
 }
 
 template <typename R>
+__global__ void __launch_bounds__(kPreThreads) k_precompute(PrecompArgs a) {
+    __shared__ double P[kPreThreads][12];
+    for (int64_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) precompute_group<R>(a, g, P);
+}
+
+// many tables in one launch: block b serves group b - off[t] of table t
+template <typename R>
+__global__ void __launch_bounds__(kPreThreads) k_precompute_batch(const PrecompArgs *tabs,
+                                                                  const int64_t *off, int n_tab,
+                                                                  int64_t total) {
+    __shared__ double P[kPreThreads][12];
+    for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        int lo = 0, hi = n_tab - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        precompute_group<R>(tabs[lo], b - off[lo], P);
+    }
+}
+
+template <typename R>
 struct Vec4;
 template <>
 struct Vec4<float> { using T = float4; };
@@ -193,6 +219,33 @@ __global__ void k_event_table(const EvAdv *adv, int n_ev, int64_t G, const doubl
         const R E2 = isinf(T2) ? (R)1 : (R)exp(-ea.tau / T2);
         const R E1 = isinf(T1) ? (R)1 : (R)exp(-ea.tau / T1);
         out[i] = R4<R>{E2 * c, -E2 * s, E1, (R)0};
+    }
+}
+
+// group-factor tables of many jobs: items of job j are [off[j], off[j+1])
+template <typename R>
+__global__ void k_event_table_batch(const EvTabJob *jobs, const int64_t *off, int n_jobs,
+                                    int64_t total) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const EvTabJob jb = jobs[lo];
+        const int64_t r = i - off[lo];
+        const int64_t e = r / jb.G, g = r - e * jb.G;
+        const EvAdv ea = jb.adv[e];
+        const double pos = jb.par[g], T1 = jb.par[jb.G + g], T2 = jb.par[2 * jb.G + g];
+        const double dB0 = jb.par[3 * jb.G + g];
+        double ph = pos * ea.kp + dB0 * ea.tau;
+        ph -= rint(ph);
+        R c, sn;
+        phasor((R)ph, c, sn);
+        const R E2 = isinf(T2) ? (R)1 : (R)exp(-ea.tau / T2);
+        const R E1 = isinf(T1) ? (R)1 : (R)exp(-ea.tau / T1);
+        ((R4<R> *)jb.out)[r] = R4<R>{E2 * c, -E2 * sn, E1, (R)0};
     }
 }
 
@@ -281,16 +334,24 @@ __device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R
 
 constexpr int kEvChunk = 128;  // events staged in shared memory at a time
 
+template <typename R>
+struct FusedSmem {
+    __align__(16) unsigned char acc_raw[kAccBytes];  // staged block sums [batch][slot][re, im]
+    __align__(16) FEvent<R> sev[kEvChunk];           // staged events
+    int batch_prow[kBatch], batch_win[kBatch];
+};
+
+// One chunk of kThreads * NI isochromats (chunk index blk) through all events
+// of a span.  All threads of the CTA take part (shared memory, barriers).
 template <typename R, int NI>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
-    k_fused(FusedArgs<R> a) {
-    __shared__ __align__(16) unsigned char acc_raw[kAccBytes];
-    __shared__ __align__(16) FEvent<R> sev[kEvChunk];
-    __shared__ int batch_prow[kBatch], batch_win[kBatch];
-    R *acc = reinterpret_cast<R *>(acc_raw);  // [batch][slot][re, im]
+__device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
+                                            FusedSmem<R> &sm) {
+    FEvent<R> *sev = sm.sev;
+    int *batch_prow = sm.batch_prow, *batch_win = sm.batch_win;
+    R *acc = reinterpret_cast<R *>(sm.acc_raw);  // [batch][slot][re, im]
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t chunk = (int64_t)kThreads * NI;
-    const int64_t base = blockIdx.x * chunk;
+    const int64_t base = blk * chunk;
     const int64_t last = min(base + chunk, a.K) - 1;
     const int32_t *gp = a.gid[a.gtype_p];
     const int32_t *gr = a.gid[a.gtype_r];
@@ -464,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) :
                 }
                 if (kind == EV_RF) {
                     rf_apply(ev, gtype);
-                } else {  // EV_END: store the state
+                } else if (a.Mx) {  // EV_END: store the state
 #pragma unroll
                     for (int i = 0; i < NI; ++i) {
                         const int64_t k = base + (int64_t)i * kThreads + tid;
@@ -488,6 +549,44 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) :
 #undef MRSIM_ADV_CASE
 #undef MRSIM_ADC_CASE
     if (nb > 0) flush();
+    __syncthreads();
+}
+
+template <typename R, int NI>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
+    k_fused(FusedArgs<R> a) {
+    __shared__ FusedSmem<R> sm;
+    fused_chunk<R, NI>(a, blockIdx.x, sm);
+}
+
+// Persistent form for a batch of jobs: every CTA takes the next (job, chunk)
+// work item from a device counter until all chunks of all jobs are done, so
+// jobs of very different sizes share the GPU without a tail of idle SMs.
+template <typename R, int NI>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
+    k_fused_batch(const FusedArgs<R> *jobs, const int64_t *blk_off, int n_jobs,
+                  unsigned long long *counter) {
+    __shared__ FusedSmem<R> sm;
+    __shared__ FusedArgs<R> ja;
+    __shared__ long long item, jblk;
+    const int64_t total = blk_off[n_jobs];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            item = (long long)atomicAdd(counter, 1ull);
+            if (item < total) {
+                int lo = 0, hi = n_jobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (blk_off[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                ja = jobs[lo];
+                jblk = item - blk_off[lo];
+            }
+        }
+        __syncthreads();
+        if (item >= total) break;
+        fused_chunk<R, NI>(ja, jblk, sm);
+    }
 }
 
 template <typename R>
@@ -512,12 +611,11 @@ constexpr int kGTile = 256;
 // block b covers samples [blk.y, blk.y + blockDim) of window blk.x and the
 // groups [blk.z, blk.w); partial sums go to the signal with FP64 atomics
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_group_signal(const GWin *wins, const int4 *blk,
-                                                           const typename GS<R>::S *smp,
-                                                           GSigTables<R> tab,
-                                                           const double *Ablk, double *signal) {
+__device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 b,
+                                                   const typename GS<R>::S *smp,
+                                                   const GSigTables<R> &tab, const double *Ablk,
+                                                   double *signal) {
     __shared__ R s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
-    const int4 b = blk[blockIdx.x];
     const GWin w = wins[b.x];
     const int64_t s_idx = (int64_t)b.y + threadIdx.x;
     const bool act = s_idx < w.sample0 + w.n_samples;
@@ -555,6 +653,24 @@ __global__ void __launch_bounds__(kThreads) k_group_signal(const GWin *wins, con
         atomicAdd(&signal[2 * s_idx], accr);
         atomicAdd(&signal[2 * s_idx + 1], acci);
     }
+    __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_group_signal(const GWin *wins, const int4 *blk,
+                                                           const typename GS<R>::S *smp,
+                                                           GSigTables<R> tab,
+                                                           const double *Ablk, double *signal) {
+    group_signal_block<R>(wins, blk[blockIdx.x], smp, tab, Ablk, signal);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_group_signal_batch(const GSigJob<R> *jobs,
+                                                                 const int4 *blk,
+                                                                 const int *blk_job) {
+    const GSigJob<R> &j = jobs[blk_job[blockIdx.x]];
+    group_signal_block<R>(j.wins, blk[blockIdx.x], (const typename GS<R>::S *)j.samples, j.tab,
+                          j.Ablk, j.signal);
 }
 
 }  // namespace
@@ -565,8 +681,55 @@ void launch_precompute(mrsim_ctx *c, const PrecompArgs &a) {
     if (a.n_groups <= 0) return;
     KScope ks(c, sizeof(R) == 4 ? "precompute_f32" : "precompute_f64");
     const unsigned grid = (unsigned)std::min<int64_t>(a.n_groups, 1 << 20);
-    k_precompute<R><<<grid, kPreThreads, 0, c->stream>>>(
-        (const RFS *)a.segs, a.seg_off, a.n_seg, a.n_steps, a.gtype, a.par, a.n_groups, (R *)a.out);
+    (void)sizeof(RFS);
+    k_precompute<R><<<grid, kPreThreads, 0, c->stream>>>(a);
+}
+
+template <typename R>
+void launch_precompute_batch(mrsim_ctx *c, const PrecompArgs *d_tabs, const int64_t *d_off,
+                             int n_tab, int64_t total) {
+    if (total <= 0) return;
+    KScope ks(c, "precompute_batch");
+    const unsigned grid = (unsigned)std::min<int64_t>(total, 1 << 20);
+    k_precompute_batch<R><<<grid, kPreThreads, 0, c->stream>>>(d_tabs, d_off, n_tab, total);
+}
+
+template <typename R>
+void launch_event_table_batch(mrsim_ctx *c, const EvTabJob *d_jobs, const int64_t *d_off,
+                              int n_jobs, int64_t total) {
+    if (total <= 0) return;
+    KScope ks(c, "event_table_batch");
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((total + 255) / 256, (int64_t)c->sm_count * 16));
+    k_event_table_batch<R><<<grid, 256, 0, c->stream>>>(d_jobs, d_off, n_jobs, total);
+}
+
+template <typename R>
+void launch_fused_batch(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
+                        int n_jobs, unsigned long long *d_counter, int ni) {
+    KScope ks(c, "fused_batch");
+    int per_sm = 1;
+    if (ni >= 4) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 4>, kThreads, 0);
+        k_fused_batch<R, 4><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
+            d_jobs, d_blk_off, n_jobs, d_counter);
+    } else if (ni == 2) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 2>, kThreads, 0);
+        k_fused_batch<R, 2><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
+            d_jobs, d_blk_off, n_jobs, d_counter);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 1>, kThreads, 0);
+        k_fused_batch<R, 1><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
+            d_jobs, d_blk_off, n_jobs, d_counter);
+    }
+}
+
+template <typename R>
+void launch_group_signal_batch(mrsim_ctx *c, const GSigJob<R> *d_jobs, const int4 *d_blk,
+                               const int *d_blk_job, int n_blk) {
+    if (n_blk <= 0) return;
+    KScope ks(c, "group_signal_batch");
+    k_group_signal_batch<R><<<n_blk, kThreads, 0, c->stream>>>(d_jobs, d_blk, d_blk_job);
 }
 
 template <typename R>
@@ -612,6 +775,14 @@ template void launch_event_table<float>(mrsim_ctx *, const EvAdv *, int, int64_t
 template void launch_event_table<double>(mrsim_ctx *, const EvAdv *, int, int64_t,
                                          const double *, void *);
 template void launch_fused<float>(mrsim_ctx *, const FusedArgs<float> &, int);
+template void launch_precompute_batch<float>(mrsim_ctx *, const PrecompArgs *, const int64_t *,
+                                             int, int64_t);
+template void launch_event_table_batch<float>(mrsim_ctx *, const EvTabJob *, const int64_t *,
+                                              int, int64_t);
+template void launch_fused_batch<float>(mrsim_ctx *, const FusedArgs<float> *, const int64_t *,
+                                        int, unsigned long long *, int);
+template void launch_group_signal_batch<float>(mrsim_ctx *, const GSigJob<float> *,
+                                               const int4 *, const int *, int);
 template void launch_fused<double>(mrsim_ctx *, const FusedArgs<double> &, int);
 template void launch_group_signal<float>(mrsim_ctx *, const GWin *, const int4 *, int,
                                          const void *, const GSigTables<float> &,
