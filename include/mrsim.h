@@ -171,6 +171,54 @@ int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);
 
+/* ------------------------------------------------------------------------
+ * Learned with-RF transitions (MRSIM_SURROGATE mode).
+ *
+ * A small network (5 -> 128 -> 128 -> 12, GELU, BF16 weights, FP32
+ * accumulation; the 128x128 layer on tensor cores) per slice-selective
+ * (Gz-only) with-RF pulse maps a group's (z, dB0, b1, T1, T2) to the pulse's
+ * combined transition [A | b] (Eq. 7), replacing the per-group preparation
+ * step of the grouped method (Sec. 2.3).  It is trained on the device by the
+ * library's own forward / backward / Adam kernels on exact transitions of
+ * random parameter draws (computed by the FP64 preparation kernel), and
+ * validated on new draws: the parameter box is cut into 64 x 8 x 4 cells in
+ * (z, dB0, b1); a cell is served by the network only if the largest error of
+ * any transition entry among its validation samples is <= `bound`; groups in
+ * other cells, or outside the box, fall back to exact integration. */
+typedef struct mrsim_surrogate mrsim_surrogate;
+
+/* Train one network per distinct slice-selective with-RF pulse of `seq`.
+ * lo/hi: [5] training box for z (m), dB0 (Hz), b1, T1 (s), T2 (s) (T1, T2
+ * drawn log-uniformly, the others uniformly).  n_train draws per pulse,
+ * `epochs` passes in minibatches of `batch` (Adam, learning rate `lr`
+ * decayed by a cosine to lr/100), `seed` for the counter-based draws, `bound` the per-entry error
+ * bound of the fallback gate.  Errors: MRSIM_EINVAL (bad arguments, no
+ * slice-selective pulse), MRSIM_ENOMEM, MRSIM_ECUDA. */
+int mrsim_surrogate_train(mrsim_ctx *ctx, const mrsim_seq *seq, const double *lo,
+                          const double *hi, int64_t n_train, int epochs, int batch, double lr,
+                          uint64_t seed, double bound, mrsim_surrogate **out);
+
+/* out[8]: networks, mean final training loss (MSE per entry), largest
+ * validation error, fraction of cells served by the network, fraction of
+ * validation samples in served cells, largest validation error in served
+ * cells, and for the context's runs since mrsim_surrogate_use: groups served
+ * by the network, groups integrated exactly.  ctx may be NULL. */
+int mrsim_surrogate_stats(const mrsim_surrogate *sur, const mrsim_ctx *ctx, double *out);
+
+/* Make `sur` the network used by this context's MRSIM_SURROGATE runs (NULL:
+ * none, every pulse is integrated exactly).  The handle must outlive its use. */
+int mrsim_surrogate_use(mrsim_ctx *ctx, const mrsim_surrogate *sur);
+
+/* One forward and backward pass of the network with the given parameters
+ * (host float[18828], layout W1[128][5], b1[128], W2[128][128], b2[128],
+ * W3[12][128], b3[12]) on n host samples x[n][5] with targets t[n][12]:
+ * returns y[n][12], the gradient of the loss sum((y - t)^2) / (12 n) and
+ * the loss (any output may be NULL).  The same kernels as training. */
+int mrsim_surrogate_eval(mrsim_ctx *ctx, const float *params, int64_t n, const float *x,
+                         const float *t, float *y, float *grad, double *loss);
+
+void mrsim_free_surrogate(mrsim_surrogate *sur);
+
 /* Launch parameters (one value per context).
  *   MRSIM_TUNE_FUSED_NI        isochromats per thread held in registers by the
  *                              grouped fused kernel: 1, 2 or 4 (default 4)

@@ -405,6 +405,7 @@ struct GPlan {
     struct Span { int64_t b, e; int fallback; };
     std::vector<Span> spans;
     std::vector<int4> blk;  // group-signal blocks (window, first sample, g0, g1)
+    bool direct = false;    // factor table too large: advance fully per isochromat
 };
 
 template <typename R>
@@ -446,14 +447,14 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         double k[3];
         for (int a = 0; a < 3; ++a) k[a] = kGammaBar * mom[a];
         int mask = 0;
-        for (int a = 0; a < 3; ++a) {
-            if (a == p - 1 || k[a] == 0.0) continue;
-            mask |= 1 << a;
+        const double kt[4] = {k[0], k[1], k[2], tau};
+        for (int a = 0; a < 4; ++a) {
+            if (a < 3 && a != p - 1 && k[a] != 0.0) mask |= 1 << a;
             if constexpr (sizeof(R) == 4) {
-                e.k_hi[a] = (float)k[a];
-                e.k_lo[a] = (float)(k[a] - (double)e.k_hi[a]);
+                e.k_hi[a] = (float)kt[a];
+                e.k_lo[a] = (float)(kt[a] - (double)e.k_hi[a]);
             } else {
-                e.k[a] = k[a];
+                e.k[a] = kt[a];
             }
         }
         e.op = ev_op(kind, mask, gtype);
@@ -495,6 +496,11 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         }
     }
     close_span(-1);
+    // the factor table has n_events x G_primary entries: with nearly one group
+    // per isochromat it would outgrow the state itself, so advance directly
+    P.direct = (int64_t)P.ev.size() * P.Gp > (int64_t)1 << 26 || P.Gp * 4 > g->K;
+    if (P.direct)
+        for (auto &e : P.ev) e.prow = 0;
     // 4) group-signal blocks: 256 samples x a slice of the groups
     if (!P.wins.empty()) {
         int64_t base_blocks = 0, max_g = 1;
@@ -560,16 +566,23 @@ FusedArgs<R> fused_args(const mrsim_groups *g, int p, R *Mx, R *My, R *Mz, const
 
 template <typename R>
 void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
-                 const mrsim_groups *g, double *d_signal, R *M) {
+                 const mrsim_groups *g, double *d_signal, R *M, bool use_sur = false) {
     const int64_t K = ph->K;
     const bool f64 = sizeof(R) == 8;
     using A = typename AdvOf<R>::T;
     GPlan<R> P;
     plan_grouped<R>(c, s, g, P);
     R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(P.rows, 1) * 12 * sizeof(R));
-    for (auto &t : P.tabs)
+    for (auto &t : P.tabs) {
+        if constexpr (sizeof(R) == 4) {
+            // learned transitions for the slice-selective pulses the network serves
+            if (use_sur &&
+                sur_table(c, s, g, t.first.first, t.first.second, T_tab + t.second * 12))
+                continue;
+        }
         launch_precompute<R>(c, precomp_args<R>(s, g, t.first.first, t.first.second,
                                                  T_tab + t.second * 12));
+    }
     double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double));
     MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double),
                                c->stream));
@@ -577,14 +590,17 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     PlainState st = sorted_state(g, M, M + Kp, M + 2 * Kp);
     const int n_ev = (int)P.ev.size();
     EvAdv *d_adv = (EvAdv *)scratch(c, 14, n_ev * sizeof(EvAdv));
-    void *d_P = scratch(c, 15, (size_t)n_ev * std::max<int64_t>(P.Gp, 1) * 4 * sizeof(R));
+    void *d_P = scratch(c, 15, (P.direct ? 1 : (size_t)n_ev * std::max<int64_t>(P.Gp, 1)) * 4 *
+                                   sizeof(R));
     FEvent<R> *d_ev = (FEvent<R> *)scratch(c, 11, n_ev * sizeof(FEvent<R>));
     upload(c, d_adv, P.adv.data(), n_ev * sizeof(EvAdv));
     upload(c, d_ev, P.ev.data(), n_ev * sizeof(FEvent<R>));
     const int prim = P.p;
-    launch_event_table<R>(c, d_adv, n_ev, P.Gp, g->tab[prim].d_par64.as<double>(), d_P);
+    if (!P.direct)
+        launch_event_table<R>(c, d_adv, n_ev, P.Gp, g->tab[prim].d_par64.as<double>(), d_P);
     if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
     FusedArgs<R> fa = fused_args<R>(g, P.p, M, M + Kp, M + 2 * Kp, T_tab, d_P, Ablk);
+    fa.direct = P.direct ? 1 : 0;
     const double z0[3] = {0.0, 0.0, 0.0};
     const A zero = AdvOf<R>::make(z0, 0.0);
     bool first = true;
@@ -660,6 +676,8 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
             plan_grouped<R>(c, s[i], g[i], plans[i]);
             if (plans[i].spans.size() != 1)
                 fail(MRSIM_EUNSUPPORTED, "batched jobs need known gradient types only");
+            if (plans[i].direct)
+                fail(MRSIM_EUNSUPPORTED, "batched jobs need few groups per isochromat");
         }
         // sizes and per-job offsets inside shared device buffers
         int64_t rows = 0, ablk = 0, nev = 0, ptab = 0, nsig = 0, blks = 0, nblk = 0;
@@ -1033,8 +1051,12 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         const int64_t Kp = plane_stride(K);
         void *Mst = scratch(c, 9, 3 * Kp * esz);
         if (grouped) {
-            if (precision == MRSIM_FP64) run_grouped<double>(c, ph, s, g, d_sig, (double *)Mst);
-            else run_grouped<float>(c, ph, s, g, d_sig, (float *)Mst);
+            if (precision == MRSIM_FP64) {
+                if (mode == MRSIM_SURROGATE) fail(MRSIM_EINVAL, "the surrogate runs in FP32");
+                run_grouped<double>(c, ph, s, g, d_sig, (double *)Mst);
+            } else {
+                run_grouped<float>(c, ph, s, g, d_sig, (float *)Mst, mode == MRSIM_SURROGATE);
+            }
         } else {
             const bool cache = mode == MRSIM_PLAIN_CACHE;
             if (precision == MRSIM_FP64) run_plain<double>(c, ph, s, cache, d_sig, (double *)Mst);

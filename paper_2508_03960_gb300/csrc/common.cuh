@@ -72,12 +72,14 @@ struct FEvent<float> {
     int row;   // RF: first row of the combined-transition table of (content, gtype)
     int prow;  // first row of this event's group-factor table
     int win;   // ADC: offset of this window's block sums (complex entries)
-    float k_hi[4], k_lo[4];  // gamma_bar * moment per axis (cycles/m), split; [3] unused
+    // gamma_bar * moment per axis (cycles/m) and, in [3], the elapsed time (s),
+    // split hi + lo; every axis is filled, `mask` marks the per-isochromat ones
+    float k_hi[4], k_lo[4];
 };
 template <>
 struct FEvent<double> {
     int op, row, prow, win;
-    double k[4];
+    double k[4];  // moments per axis, elapsed time in [3]
 };
 __host__ __device__ constexpr int ev_op(int kind, int mask, int gtype) {
     return kind | (mask << 2) | (gtype << 5);

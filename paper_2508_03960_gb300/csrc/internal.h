@@ -72,6 +72,9 @@ struct mrsim_ctx {
     // pinned host staging for uploads of per-run plans
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
+    // active surrogate for MRSIM_SURROGATE runs and the counts of its last use
+    const struct mrsim_surrogate *sur = nullptr;
+    int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
     int tune[4] = {4, 2, 2, 0};  // MRSIM_TUNE_FUSED_NI, _PLAIN_RF_NI, _ADC_CTAS_PER_SM, unused
 };
@@ -165,6 +168,37 @@ DBuf dalloc(size_t bytes);
 void upload(mrsim_ctx *c, void *dst, const void *src, size_t bytes);
 void sync(mrsim_ctx *c);
 
+// ---- learned with-RF transitions (k_surrogate.cu, surrogate.cu) ----
+struct SurDomain {
+    double lo[5], hi[5];  // z (m), dB0 (Hz), b1, T1 (s), T2 (s)
+};
+struct SurPulse {
+    double mz;   // int Gz dt over the pulse (T s / m)
+    double dur;  // pulse duration (s)
+};
+constexpr int kCellsZ = 64, kCellsB0 = 8, kCellsB1 = 4;
+constexpr int kCells = kCellsZ * kCellsB0 * kCellsB1;
+void sur_sample(mrsim_ctx *c, const SurDomain &d, uint64_t seed, int64_t n, double *par, float *X);
+void sur_core(mrsim_ctx *c, const SurPulse &p, const double *par, int64_t n, const double *T,
+              float *C);
+void sur_bf16_copies(mrsim_ctx *c, const float *P, void *W2b, void *W2Tb);
+void sur_train_step(mrsim_ctx *c, const float *P, const void *W2b, const void *W2Tb,
+                    const float *X, const float *T, int64_t n, float *grad, double *loss,
+                    float *Yout);
+void sur_adam(mrsim_ctx *c, float *P, float *grad, float *m, float *v, int step, float lr,
+              void *W2b, void *W2Tb);
+void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t n,
+                    const float *Y, const float *T, unsigned int *cell_err);
+void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
+               const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
+               float *out, int32_t *fb, int32_t *fb_n);
+int sur_n_params();
+// run-time use by the grouped planner: fills rows [0, G) of `out` for with-RF
+// content `cid` of `s` from the context's active network, then integrates the
+// fallback groups exactly; returns false if no network serves this content
+bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid, int gtype,
+               float *out);
+
 // ---- group builder (k_group.cu) ----
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab);
@@ -204,6 +238,8 @@ struct PrecompArgs {
     int64_t n_groups;
     const double *par;       // [5][n_groups]: pos, T1, T2, dB0, b1
     void *out;               // R [n_groups][12]
+    const int32_t *gidx = nullptr;    // optional: only the groups gidx[0 .. *gcount)
+    const int32_t *gcount = nullptr;
 };
 template <typename R>
 void launch_precompute(mrsim_ctx *c, const PrecompArgs &a);
@@ -221,6 +257,7 @@ struct FusedArgs {
     const R *T_tab;
     const void *P_raw;       // per-(event, primary group) advance factors, 4 R each
     double *Ablk;            // complex block sums (interleaved re, im)
+    int direct;              // 1: no factor table, the whole advance per isochromat
 };
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni);

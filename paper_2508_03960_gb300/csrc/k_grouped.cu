@@ -152,7 +152,12 @@ __device__ void precompute_group(const PrecompArgs &a, int64_t g, double (*P)[12
 template <typename R>
 __global__ void __launch_bounds__(kPreThreads) k_precompute(PrecompArgs a) {
     __shared__ double P[kPreThreads][12];
-    for (int64_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) precompute_group<R>(a, g, P);
+    if (a.gidx) {  // only the listed groups
+        const int64_t n = *a.gcount;
+        for (int64_t b = blockIdx.x; b < n; b += gridDim.x) precompute_group<R>(a, a.gidx[b], P);
+    } else {
+        for (int64_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) precompute_group<R>(a, g, P);
+    }
 }
 
 // many tables in one launch: block b serves group b - off[t] of table t
@@ -288,9 +293,63 @@ __device__ __forceinline__ double iso_turns_m(const FEvent<double> &ev, double x
 template <typename R, int NI>
 struct Iso {
     R mx[NI], my[NI], mz[NI], M0[NI], x[NI], y[NI], z[NI];
+    R dB0[NI], r1[NI], r2[NI];  // direct mode only: dB0, log2(e)/T1, log2(e)/T2
     int pofs[NI];  // primary group (row offset in a group-factor table)
     int tofs[NI];  // 12 * RF group (offset in a combined-transition table)
 };
+
+// whole advance of one isochromat from the event record (direct mode):
+// phase of all three axes and dB0 tau, E2 and E1 from its own T2, T1
+__device__ __forceinline__ void direct_factor(const FEvent<float> &ev, float x, float y, float z,
+                                              float dB0, float r1, float r2, float &fr, float &fi,
+                                              float &E1) {
+    const float t = turns_prod(x, ev.k_hi[0], ev.k_lo[0]) + turns_prod(y, ev.k_hi[1], ev.k_lo[1]) +
+                    turns_prod(z, ev.k_hi[2], ev.k_lo[2]) + turns_prod(dB0, ev.k_hi[3], ev.k_lo[3]);
+    float c, sn;
+    phasor(t, c, sn);
+    const float tau = ev.k_hi[3] + ev.k_lo[3];
+    const float E2 = decay(tau, r2);
+    E1 = decay(tau, r1);
+    fr = E2 * c;
+    fi = -E2 * sn;
+}
+__device__ __forceinline__ void direct_factor(const FEvent<double> &ev, double x, double y,
+                                              double z, double dB0, double r1, double r2,
+                                              double &fr, double &fi, double &E1) {
+    double t = x * ev.k[0] + y * ev.k[1] + z * ev.k[2] + dB0 * ev.k[3];
+    t -= rint(t);
+    double c, sn;
+    phasor(t, c, sn);
+    const double E2 = decay(ev.k[3], r2);
+    E1 = decay(ev.k[3], r1);
+    fr = E2 * c;
+    fi = -E2 * sn;
+}
+
+template <typename R, int NI>
+__device__ __forceinline__ void ev_advance_direct(Iso<R, NI> &s, const FEvent<R> &ev) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        R fr, fi, E1;
+        direct_factor(ev, s.x[i], s.y[i], s.z[i], s.dB0[i], s.r1[i], s.r2[i], fr, fi, E1);
+        const R nx = fr * s.mx[i] - fi * s.my[i];
+        s.my[i] = fr * s.my[i] + fi * s.mx[i];
+        s.mx[i] = nx;
+        s.mz[i] = s.M0[i] + (s.mz[i] - s.M0[i]) * E1;
+    }
+}
+
+template <typename R, int NI>
+__device__ __forceinline__ void ev_adc_direct(const Iso<R, NI> &s, const FEvent<R> &ev,
+                                              R (&vr)[NI], R (&vi)[NI]) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        R fr, fi, E1;
+        direct_factor(ev, s.x[i], s.y[i], s.z[i], s.dB0[i], s.r1[i], s.r2[i], fr, fi, E1);
+        vr[i] = fr * s.mx[i] - fi * s.my[i];
+        vi[i] = fr * s.my[i] + fi * s.mx[i];
+    }
+}
 
 // advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1
 template <typename R, int NI, int MASK>
@@ -343,7 +402,7 @@ struct FusedSmem {
 
 // One chunk of kThreads * NI isochromats (chunk index blk) through all events
 // of a span.  All threads of the CTA take part (shared memory, barriers).
-template <typename R, int NI>
+template <typename R, int NI, bool DIRECT>
 __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                                             FusedSmem<R> &sm) {
     FEvent<R> *sev = sm.sev;
@@ -380,11 +439,18 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             }
             key[i] = gp[k];
             s.tofs[i] = 12 * gr[k];
+            if constexpr (DIRECT) {
+                s.dB0[i] = a.dB0[k];
+                const float T1 = a.T1[k], T2 = a.T2[k];
+                s.r1[i] = isinf(T1) ? (R)0 : (R)kLog2e / (R)T1;
+                s.r2[i] = isinf(T2) ? (R)0 : (R)kLog2e / (R)T2;
+            }
         } else {
             s.x[i] = s.y[i] = s.z[i] = s.M0[i] = 0;
             s.mx[i] = s.my[i] = s.mz[i] = 0;
             key[i] = 0x7fffffff;
             s.tofs[i] = 0;
+            if constexpr (DIRECT) s.dB0[i] = s.r1[i] = s.r2[i] = 0;
         }
         s.pofs[i] = min(key[i], g_last);
     }
@@ -404,7 +470,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             const int b = t / S, slot = t - b * S;
             const R sr = acc[2 * t], si = acc[2 * t + 1];
             if (sr != (R)0 || si != (R)0) {
-                const R4<R> P = load4(Pt + batch_prow[b] + g_first + slot);
+                R4<R> P{(R)1, (R)0, (R)1, (R)0};
+                if constexpr (!DIRECT) P = load4(Pt + batch_prow[b] + g_first + slot);
                 const int64_t o = 2 * ((int64_t)batch_win[b] + g_first + slot);
                 atomicAdd(&Ablk[o], (double)(P.x * sr - P.y * si));
                 atomicAdd(&Ablk[o + 1], (double)(P.x * si + P.y * sr));
@@ -486,7 +553,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             for (int i = 0; i < NI; ++i) {
                 const int64_t k = base + (int64_t)i * kThreads + tid;
                 if (k < a.K) {
-                    const R4<R> P = load4(Pt + ev.prow + s.pofs[i]);
+                    R4<R> P{(R)1, (R)0, (R)1, (R)0};
+                    if constexpr (!DIRECT) P = load4(Pt + ev.prow + s.pofs[i]);
                     const int64_t o = 2 * ((int64_t)ev.win + g[k]);
                     atomicAdd(&Ablk[o], (double)(P.x * vr[i] - P.y * vi[i]));
                     atomicAdd(&Ablk[o + 1], (double)(P.x * vi[i] + P.y * vr[i]));
@@ -519,9 +587,13 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             const int op = ev.op;
             const int kind = ev_kind(op), mask = ev_mask(op), gtype = ev_gtype(op);
             if (kind != EV_ADC) {
-                switch (mask) {
-                    MRSIM_ADV_CASE(0) MRSIM_ADV_CASE(1) MRSIM_ADV_CASE(2) MRSIM_ADV_CASE(3)
-                    MRSIM_ADV_CASE(4) MRSIM_ADV_CASE(5) MRSIM_ADV_CASE(6) MRSIM_ADV_CASE(7)
+                if constexpr (DIRECT) {
+                    ev_advance_direct<R, NI>(s, ev);
+                } else {
+                    switch (mask) {
+                        MRSIM_ADV_CASE(0) MRSIM_ADV_CASE(1) MRSIM_ADV_CASE(2) MRSIM_ADV_CASE(3)
+                        MRSIM_ADV_CASE(4) MRSIM_ADV_CASE(5) MRSIM_ADV_CASE(6) MRSIM_ADV_CASE(7)
+                    }
                 }
                 if (kind == EV_RF) {
                     rf_apply(ev, gtype);
@@ -538,9 +610,13 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 }
             } else {
                 R vr[NI], vi[NI];
-                switch (mask) {
-                    MRSIM_ADC_CASE(0) MRSIM_ADC_CASE(1) MRSIM_ADC_CASE(2) MRSIM_ADC_CASE(3)
-                    MRSIM_ADC_CASE(4) MRSIM_ADC_CASE(5) MRSIM_ADC_CASE(6) MRSIM_ADC_CASE(7)
+                if constexpr (DIRECT) {
+                    ev_adc_direct<R, NI>(s, ev, vr, vi);
+                } else {
+                    switch (mask) {
+                        MRSIM_ADC_CASE(0) MRSIM_ADC_CASE(1) MRSIM_ADC_CASE(2) MRSIM_ADC_CASE(3)
+                        MRSIM_ADC_CASE(4) MRSIM_ADC_CASE(5) MRSIM_ADC_CASE(6) MRSIM_ADC_CASE(7)
+                    }
                 }
                 adc_reduce(ev, gtype, vr, vi);
             }
@@ -552,11 +628,11 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     __syncthreads();
 }
 
-template <typename R, int NI>
+template <typename R, int NI, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
     k_fused(FusedArgs<R> a) {
     __shared__ FusedSmem<R> sm;
-    fused_chunk<R, NI>(a, blockIdx.x, sm);
+    fused_chunk<R, NI, DIRECT>(a, blockIdx.x, sm);
 }
 
 // Persistent form for a batch of jobs: every CTA takes the next (job, chunk)
@@ -585,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) :
         }
         __syncthreads();
         if (item >= total) break;
-        fused_chunk<R, NI>(ja, jblk, sm);
+        fused_chunk<R, NI, false>(ja, jblk, sm);
     }
 }
 
@@ -732,19 +808,25 @@ void launch_group_signal_batch(mrsim_ctx *c, const GSigJob<R> *d_jobs, const int
     k_group_signal_batch<R><<<n_blk, kThreads, 0, c->stream>>>(d_jobs, d_blk, d_blk_job);
 }
 
+template <typename R, bool DIRECT>
+void launch_fused_v(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
+    if (ni >= 4) {
+        const unsigned nb = (unsigned)((a.K + kThreads * 4 - 1) / (kThreads * 4));
+        k_fused<R, 4, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
+    } else if (ni == 2) {
+        const unsigned nb = (unsigned)((a.K + kThreads * 2 - 1) / (kThreads * 2));
+        k_fused<R, 2, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
+    } else {
+        const unsigned nb = (unsigned)((a.K + kThreads - 1) / kThreads);
+        k_fused<R, 1, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
+    }
+}
+
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
     KScope ks(c, sizeof(R) == 4 ? "fused_grouped_f32" : "fused_grouped_f64");
-    if (ni >= 4) {
-        const unsigned nb = (unsigned)((a.K + kThreads * 4 - 1) / (kThreads * 4));
-        k_fused<R, 4><<<nb, kThreads, 0, c->stream>>>(a);
-    } else if (ni == 2) {
-        const unsigned nb = (unsigned)((a.K + kThreads * 2 - 1) / (kThreads * 2));
-        k_fused<R, 2><<<nb, kThreads, 0, c->stream>>>(a);
-    } else {
-        const unsigned nb = (unsigned)((a.K + kThreads - 1) / kThreads);
-        k_fused<R, 1><<<nb, kThreads, 0, c->stream>>>(a);
-    }
+    if (a.direct) launch_fused_v<R, true>(c, a, ni);
+    else launch_fused_v<R, false>(c, a, ni);
 }
 
 template <typename R>

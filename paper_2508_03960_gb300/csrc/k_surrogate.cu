@@ -1,0 +1,591 @@
+// Learned with-RF transitions: a 5 -> 128 -> 128 -> 12 MLP (GELU) per
+// slice-selective pulse maps an isochromat group's (z, dB0, b1, T1, T2) to the
+// pulse's combined transition [A | b] (Eq. 7).  Everything here is device
+// work of the library: training data from the exact FP64 precompute kernel,
+// forward / backward / Adam training kernels, inference into the transition
+// table, and a validated error grid that sends groups back to exact
+// integration where the network's error exceeds the bound.
+//
+// Precision: the 128 x 128 hidden layer holds 16,384 of the 18,828 weights;
+// they are stored in BF16 (FP32 master copies for training) and that layer and
+// its two backward products run on the tensor cores (mma.sync m16n8k16, BF16
+// inputs, FP32 accumulation).  Its input activations enter as an unevaluated
+// sum of two BF16 numbers (hi + lo, two MMAs), so they keep ~16 bits.  The
+// 5-wide input layer and the 12-wide output layer are not contraction-shaped;
+// they run on FP32 lanes with FP32 weights.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace mrsim {
+
+namespace {
+
+constexpr int kTS = 64;       // samples per tile
+constexpr int kNT = 128;      // threads per tile CTA (4 warps x 16 samples)
+constexpr int kH = 128;       // hidden width
+constexpr int kIn = 5;
+constexpr int kOut = 12;
+constexpr int kLdH = kH + 8;  // bf16 row stride of [samples][hidden] tiles
+constexpr int kLdT = kTS + 8; // bf16 row stride of [hidden][samples] tiles
+constexpr int kLdW = kH + 8;  // bf16 row stride of W2 and W2^T
+
+// flat parameter layout (FP32 master, gradients, Adam moments)
+constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
+              oW3 = ob2 + kH, ob3 = oW3 + kOut * kH, kNParams = ob3 + kOut;
+static_assert(kNParams == 18828, "parameter count");
+
+__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float a) {
+    return 0.5f * (1.0f + erff(a * 0.70710678118654752f)) +
+           a * expf(-0.5f * a * a) * 0.39894228040143268f;
+}
+
+// D += A B for one 16x8x16 tile: A 16x16 row-major, B 16x8 column-major, BF16
+// inputs, FP32 accumulators (warp-wide).
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// A fragment of rows r0..r0+15, columns k0..k0+15 of a row-major bf16 array
+__device__ __forceinline__ void load_a(uint32_t (&a)[4], const __nv_bfloat16 *M, int ld, int r0,
+                                       int k0) {
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    const uint32_t *p0 = reinterpret_cast<const uint32_t *>(M + (r0 + g) * ld + k0 + 2 * t);
+    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(M + (r0 + g + 8) * ld + k0 + 2 * t);
+    a[0] = p0[0];
+    a[1] = p1[0];
+    a[2] = p0[4];
+    a[3] = p1[4];
+}
+// B fragment (k0..k0+15) x (n0..n0+7) of a matrix whose column n is stored as
+// row n of the bf16 array Mt (so Mt[n][k] = B[k][n])
+__device__ __forceinline__ void load_b(uint32_t (&b)[2], const __nv_bfloat16 *Mt, int ld, int n0,
+                                       int k0) {
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(Mt + (n0 + g) * ld + k0 + 2 * t);
+    b[0] = p[0];
+    b[1] = p[4];
+}
+
+struct SurSmem {
+    __nv_bfloat16 W2b[kH * kLdW];   // W2[o][i]
+    __nv_bfloat16 W2Tb[kH * kLdW];  // W2[o][i] at [i][o]
+    __nv_bfloat16 H1b[kTS * kLdH];  // h1[s][i], high part
+    union {                          // the forward and backward phases never overlap
+        __nv_bfloat16 H1lo[kTS * kLdH];  // h1[s][i] - high part, rounded (forward)
+        __nv_bfloat16 dA2b[kTS * kLdH];  // da2[s][o] (backward)
+    };
+    __nv_bfloat16 H1Tb[kH * kLdT];  // h1[s][i] at [i][s]
+    __nv_bfloat16 dA2Tb[kH * kLdT];
+    float F[kTS * kH];  // a2, then h2; later da1
+    float G[kTS * kH];  // gelu'(a2), then da2
+    float W1[kH * kIn], b1[kH], b2[kH], W3[kOut * kH], b3[16];
+    float X[kTS * kIn], T[kTS * kOut], dY[kTS * kOut];
+    float red[kNT / 32];
+};
+
+// weights into shared memory (W2 in BF16; the rest FP32)
+__device__ void load_weights(SurSmem &sm, const float *P, const __nv_bfloat16 *W2b_g,
+                             const __nv_bfloat16 *W2Tb_g, bool need_T) {
+    const int tid = threadIdx.x;
+    for (int j = tid; j < kH * kH / 8; j += kNT) {
+        const int r = (j * 8) / kH, c = (j * 8) % kH;
+        *reinterpret_cast<int4 *>(&sm.W2b[r * kLdW + c]) = reinterpret_cast<const int4 *>(W2b_g)[j];
+        if (need_T)
+            *reinterpret_cast<int4 *>(&sm.W2Tb[r * kLdW + c]) =
+                reinterpret_cast<const int4 *>(W2Tb_g)[j];
+    }
+    for (int j = tid; j < kH * kIn; j += kNT) sm.W1[j] = P[oW1 + j];
+    for (int j = tid; j < kH; j += kNT) {
+        sm.b1[j] = P[ob1 + j];
+        sm.b2[j] = P[ob2 + j];
+    }
+    for (int j = tid; j < kOut * kH; j += kNT) sm.W3[j] = P[oW3 + j];
+    if (tid < kOut) sm.b3[tid] = P[ob3 + tid];
+}
+
+// Forward pass of one tile: h1 (bf16, both layouts), a2 -> F = h2 and
+// G = gelu'(a2); outputs y [kTS][12] written to `y` (shared or global).
+__device__ void tile_forward(SurSmem &sm, int ns, bool keep_grad) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // layer 1 (FP32): a1 = W1 x + b1, h1 = gelu(a1) rounded to bf16
+    for (int j = tid; j < kTS * kH; j += kNT) {
+        const int s = j / kH, i = j % kH;
+        float a = sm.b1[i];
+#pragma unroll
+        for (int c = 0; c < kIn; ++c) a = fmaf(sm.W1[i * kIn + c], sm.X[s * kIn + c], a);
+        const float h = s < ns ? gelu(a) : 0.0f;
+        const __nv_bfloat16 hb = __float2bfloat16_rn(h);
+        sm.H1b[s * kLdH + i] = hb;
+        sm.H1lo[s * kLdH + i] = __float2bfloat16_rn(h - __bfloat162float(hb));
+        sm.H1Tb[i * kLdT + s] = hb;
+    }
+    __syncthreads();
+    // layer 2 on tensor cores: a2[s][o] = sum_i h1[s][i] W2[o][i] + b2[o]
+    {
+        const int g = (tid & 31) >> 2, t = tid & 3, r0 = warp * 16;
+        float acc[16][4];
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const float bl = sm.b2[nt * 8 + 2 * t], bh = sm.b2[nt * 8 + 2 * t + 1];
+            acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+        }
+#pragma unroll
+        for (int ks = 0; ks < kH / 16; ++ks) {
+            uint32_t a[4], al[4];
+            load_a(a, sm.H1b, kLdH, r0, ks * 16);
+            load_a(al, sm.H1lo, kLdH, r0, ks * 16);
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                uint32_t b[2];
+                load_b(b, sm.W2b, kLdW, nt * 8, ks * 16);
+                mma16816(acc[nt], a, b);
+                mma16816(acc[nt], al, b);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const int c = nt * 8 + 2 * t;
+            sm.F[(r0 + g) * kH + c] = acc[nt][0];
+            sm.F[(r0 + g) * kH + c + 1] = acc[nt][1];
+            sm.F[(r0 + g + 8) * kH + c] = acc[nt][2];
+            sm.F[(r0 + g + 8) * kH + c + 1] = acc[nt][3];
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < kTS * kH; j += kNT) {
+        const float a = sm.F[j];
+        if (keep_grad) sm.G[j] = gelu_grad(a);
+        sm.F[j] = gelu(a);
+    }
+    __syncthreads();
+}
+
+// output layer for sample s, output r
+__device__ __forceinline__ float out_layer(const SurSmem &sm, int s, int r) {
+    float y = sm.b3[r];
+    for (int o = 0; o < kH; ++o) y = fmaf(sm.W3[r * kH + o], sm.F[s * kH + o], y);
+    return y;
+}
+
+__device__ double block_sum(SurSmem &sm, float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double tot = 0;
+    for (int w = 0; w < kNT / 32; ++w) tot += sm.red[w];
+    __syncthreads();
+    return tot;
+}
+
+// One training tile: forward, loss, backward; gradients added into `grad`.
+// inv_n = 1 / (12 * samples in the whole minibatch).
+__global__ void __launch_bounds__(kNT) k_sur_train(const float *P, const __nv_bfloat16 *W2b_g,
+                                                   const __nv_bfloat16 *W2Tb_g, const float *X,
+                                                   const float *Tgt, int64_t n, float inv_n,
+                                                   float *grad, double *loss, float *Yout) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    SurSmem &sm = *reinterpret_cast<SurSmem *>(raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t s0 = blockIdx.x * (int64_t)kTS;
+    const int ns = (int)min((int64_t)kTS, n - s0);
+    load_weights(sm, P, W2b_g, W2Tb_g, true);
+    for (int j = tid; j < kTS * kIn; j += kNT) sm.X[j] = j < ns * kIn ? X[s0 * kIn + j] : 0.0f;
+    for (int j = tid; j < kTS * kOut; j += kNT) sm.T[j] = j < ns * kOut ? Tgt[s0 * kOut + j] : 0.0f;
+    __syncthreads();
+    tile_forward(sm, ns, true);
+    // output layer, residual and dL/dy
+    float lsum = 0.0f;
+    for (int j = tid; j < kTS * kOut; j += kNT) {
+        const int s = j / kOut, r = j % kOut;
+        float d = 0.0f;
+        if (s < ns) {
+            const float y = out_layer(sm, s, r);
+            if (Yout) Yout[(s0 + s) * kOut + r] = y;
+            const float res = y - sm.T[j];
+            lsum += res * res;
+            d = 2.0f * res * inv_n;
+        }
+        sm.dY[j] = d;
+    }
+    const double ls = block_sum(sm, lsum);
+    if (tid == 0 && loss) atomicAdd(loss, ls);
+    __syncthreads();
+    // dW3[r][o] = sum_s dY[s][r] h2[s][o]; db3[r] = sum_s dY[s][r]
+    for (int j = tid; j < kOut * kH; j += kNT) {
+        const int r = j / kH, o = j % kH;
+        float acc = 0.0f;
+        for (int s = 0; s < ns; ++s) acc = fmaf(sm.dY[s * kOut + r], sm.F[s * kH + o], acc);
+        atomicAdd(&grad[oW3 + j], acc);
+    }
+    if (tid < kOut) {
+        float acc = 0.0f;
+        for (int s = 0; s < ns; ++s) acc += sm.dY[s * kOut + tid];
+        atomicAdd(&grad[ob3 + tid], acc);
+    }
+    // da2[s][o] = (sum_r dY[s][r] W3[r][o]) gelu'(a2[s][o])
+    for (int j = tid; j < kTS * kH; j += kNT) {
+        const int s = j / kH, o = j % kH;
+        float d = 0.0f;
+#pragma unroll
+        for (int r = 0; r < kOut; ++r) d = fmaf(sm.dY[s * kOut + r], sm.W3[r * kH + o], d);
+        d *= sm.G[j];
+        sm.G[j] = d;
+        const __nv_bfloat16 db = __float2bfloat16_rn(d);
+        sm.dA2b[s * kLdH + o] = db;
+        sm.dA2Tb[o * kLdT + s] = db;
+    }
+    __syncthreads();
+    if (tid < kH) {
+        float acc = 0.0f;
+        for (int s = 0; s < ns; ++s) acc += sm.G[s * kH + tid];
+        atomicAdd(&grad[ob2 + tid], acc);
+    }
+    // dh1 = da2 W2 (tensor cores), then da1 = dh1 gelu'(a1) into F
+    {
+        const int g = (tid & 31) >> 2, t = tid & 3, r0 = warp * 16;
+        float acc[16][4];
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < kH / 16; ++ks) {
+            uint32_t a[4];
+            load_a(a, sm.dA2b, kLdH, r0, ks * 16);
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                uint32_t b[2];
+                load_b(b, sm.W2Tb, kLdW, nt * 8, ks * 16);  // B[k=o][n=i] = W2[o][i]
+                mma16816(acc[nt], a, b);
+            }
+        }
+        __syncthreads();  // every warp is done reading F (h2) before it becomes da1
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = r0 + g + (q >= 2 ? 8 : 0), i = nt * 8 + 2 * t + (q & 1);
+                float a1 = sm.b1[i];
+#pragma unroll
+                for (int c = 0; c < kIn; ++c) a1 = fmaf(sm.W1[i * kIn + c], sm.X[s * kIn + c], a1);
+                sm.F[s * kH + i] = s < ns ? acc[nt][q] * gelu_grad(a1) : 0.0f;
+            }
+        }
+    }
+    __syncthreads();
+    // dW1[i][c] = sum_s da1[s][i] x[s][c]; db1[i] = sum_s da1[s][i]
+    for (int j = tid; j < kH * kIn; j += kNT) {
+        const int i = j / kIn, c = j % kIn;
+        float acc = 0.0f;
+        for (int s = 0; s < ns; ++s) acc = fmaf(sm.F[s * kH + i], sm.X[s * kIn + c], acc);
+        atomicAdd(&grad[oW1 + j], acc);
+    }
+    if (tid < kH) {
+        float acc = 0.0f;
+        for (int s = 0; s < ns; ++s) acc += sm.F[s * kH + tid];
+        atomicAdd(&grad[ob1 + tid], acc);
+    }
+    // dW2[o][i] = sum_s da2[s][o] h1[s][i] (tensor cores; K = samples)
+    {
+        const int g = (tid & 31) >> 2, t = tid & 3;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int o0 = warp * 32 + mt * 16;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float acc[8][4];
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+                for (int ks = 0; ks < kTS / 16; ++ks) {
+                    uint32_t a[4];
+                    load_a(a, sm.dA2Tb, kLdT, o0, ks * 16);  // A[m=o][k=s]
+#pragma unroll
+                    for (int nt = 0; nt < 8; ++nt) {
+                        uint32_t b[2];
+                        load_b(b, sm.H1Tb, kLdT, (half * 8 + nt) * 8, ks * 16);  // B[k=s][n=i]
+                        mma16816(acc[nt], a, b);
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const int i = (half * 8 + nt) * 8 + 2 * t;
+                    atomicAdd(&grad[oW2 + (o0 + g) * kH + i], acc[nt][0]);
+                    atomicAdd(&grad[oW2 + (o0 + g) * kH + i + 1], acc[nt][1]);
+                    atomicAdd(&grad[oW2 + (o0 + g + 8) * kH + i], acc[nt][2]);
+                    atomicAdd(&grad[oW2 + (o0 + g + 8) * kH + i + 1], acc[nt][3]);
+                }
+            }
+        }
+    }
+}
+
+// Adam (bias-corrected); zeroes the gradient and refreshes the BF16 copies
+__global__ void k_sur_adam(float *P, float *grad, float *m, float *v, int step, float lr,
+                           __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kNParams; j += gridDim.x * blockDim.x) {
+        const float g = grad[j];
+        const float mj = b1 * m[j] + (1.0f - b1) * g;
+        const float vj = b2 * v[j] + (1.0f - b2) * g * g;
+        m[j] = mj;
+        v[j] = vj;
+        const float p = P[j] - lr * (mj / c1) / (sqrtf(vj / c2) + eps);
+        P[j] = p;
+        grad[j] = 0.0f;
+        if (j >= oW2 && j < ob2) {
+            const int o = (j - oW2) / kH, i = (j - oW2) % kH;
+            const __nv_bfloat16 pb = __float2bfloat16_rn(p);
+            W2b[o * kH + i] = pb;
+            W2Tb[i * kH + o] = pb;
+        }
+    }
+}
+
+__global__ void k_sur_bf16_copies(const float *P, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kH * kH; j += gridDim.x * blockDim.x) {
+        const int o = j / kH, i = j % kH;
+        const __nv_bfloat16 pb = __float2bfloat16_rn(P[oW2 + j]);
+        W2b[o * kH + i] = pb;
+        W2Tb[i * kH + o] = pb;
+    }
+}
+
+// ---------------------------------------------------------------- data ----
+// splitmix64 (S. Vigna): a counter-based generator, value i of stream seed
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+__device__ __forceinline__ double u01(uint64_t seed, uint64_t i) {
+    return (double)(splitmix64(seed * 0xd1342543de82ef95ull + i) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Features of one group/sample, normalised to about [-1, 1] over the domain.
+__device__ __forceinline__ void features(const SurDomain &d, double z, double dB0, double b1,
+                                         double T1, double T2, float *f) {
+    f[0] = (float)((z - d.lo[0]) / (d.hi[0] - d.lo[0]) * 2.0 - 1.0);
+    f[1] = (float)((dB0 - d.lo[1]) / (d.hi[1] - d.lo[1]) * 2.0 - 1.0);
+    f[2] = (float)((b1 - d.lo[2]) / (d.hi[2] - d.lo[2]) * 2.0 - 1.0);
+    f[3] = (float)((log(T1) - log(d.lo[3])) / (log(d.hi[3]) - log(d.lo[3])) * 2.0 - 1.0);
+    f[4] = (float)((log(T2) - log(d.lo[4])) / (log(d.hi[4]) - log(d.lo[4])) * 2.0 - 1.0);
+}
+
+// Draw n samples uniformly in (z, dB0, b1) and log-uniformly in (T1, T2);
+// write the precompute parameter block [5][n] (pos, T1, T2, dB0, b1) and the
+// network features [n][5].
+__global__ void k_sur_sample(SurDomain d, uint64_t seed, int64_t n, double *par, float *X) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double z = d.lo[0] + (d.hi[0] - d.lo[0]) * u01(seed, 5 * k);
+        const double dB0 = d.lo[1] + (d.hi[1] - d.lo[1]) * u01(seed, 5 * k + 1);
+        const double b1 = d.lo[2] + (d.hi[2] - d.lo[2]) * u01(seed, 5 * k + 2);
+        const double T1 = exp(log(d.lo[3]) + (log(d.hi[3]) - log(d.lo[3])) * u01(seed, 5 * k + 3));
+        const double T2 = exp(log(d.lo[4]) + (log(d.hi[4]) - log(d.lo[4])) * u01(seed, 5 * k + 4));
+        par[k] = z;
+        par[n + k] = T1;
+        par[2 * n + k] = T2;
+        par[3 * n + k] = dB0;
+        par[4 * n + k] = b1;
+        features(d, z, dB0, b1, T1, T2, X + 5 * k);
+    }
+}
+
+// P(phi) multiplies M_xy by exp(-i phi) (free precession, Eq. 4).  Returns
+// P(phi) [A P(phi) | b] for a row-major 3x4 affine [A | b].
+__device__ __forceinline__ void precess_affine(double (&T)[12], double phi) {
+    double s, c;
+    sincos(phi, &s, &c);
+    for (int r = 0; r < 3; ++r) {  // A <- A P: columns 0, 1 mix
+        const double a0 = T[4 * r], a1 = T[4 * r + 1];
+        T[4 * r] = c * a0 - s * a1;
+        T[4 * r + 1] = s * a0 + c * a1;
+    }
+    for (int col = 0; col < 4; ++col) {  // P [A | b]: rows 0, 1 mix
+        const double r0 = T[col], r1 = T[4 + col];
+        T[col] = c * r0 + s * r1;
+        T[4 + col] = -s * r0 + c * r1;
+    }
+}
+
+// half of the precession angle th = 2 pi (gamma_bar z int Gz dt + dB0 T_pulse)
+// of an isochromat at (z, dB0) during the pulse.  The half turn count is
+// reduced modulo one, so the result is continuous in z and dB0 (reducing th
+// first and halving would jump by pi where th wraps).
+__device__ __forceinline__ double pulse_half_angle(const SurPulse &p, double z, double dB0) {
+    double half_turns = 0.5 * (kGammaBar * z * p.mz + dB0 * p.dur);
+    half_turns -= rint(half_turns);
+    return kTwoPi * half_turns;
+}
+
+// Exact transitions -> network targets: the core C = P(-th/2) [A P(-th/2) | b]
+// removes the precession the slice gradient and dB0 impose during the pulse
+// (for an isochromat the pulse does not reach, T = P(th) and C = I), which
+// leaves a function of z that varies on the scale of the slice profile.
+__global__ void k_sur_core(SurPulse pulse, const double *par, int64_t n, const double *T,
+                           float *C) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double t[12];
+        for (int e = 0; e < 12; ++e) t[e] = T[k * 12 + e];
+        precess_affine(t, -pulse_half_angle(pulse, par[k], par[3 * n + k]));
+        for (int e = 0; e < 12; ++e) C[k * 12 + e] = (float)t[e];
+    }
+}
+
+__device__ __forceinline__ int cell_of(const SurDomain &d, double z, double dB0, double b1) {
+    const double u[3] = {(z - d.lo[0]) / (d.hi[0] - d.lo[0]), (dB0 - d.lo[1]) / (d.hi[1] - d.lo[1]),
+                         (b1 - d.lo[2]) / (d.hi[2] - d.lo[2])};
+    const int nb[3] = {kCellsZ, kCellsB0, kCellsB1};
+    int c = 0;
+    for (int a = 0; a < 3; ++a) {
+        int q = (int)floor(u[a] * nb[a]);
+        q = q < 0 ? 0 : (q >= nb[a] ? nb[a] - 1 : q);
+        c = c * nb[a] + q;
+    }
+    return c;
+}
+
+// validation: largest |error| of any transition entry per (z, dB0, b1) cell
+__global__ void k_sur_cell_error(SurDomain d, const double *par, int64_t n, const float *Y,
+                                 const float *Tgt, unsigned int *cell_err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        float e = 0.0f;
+        for (int r = 0; r < kOut; ++r) e = fmaxf(e, fabsf(Y[k * kOut + r] - Tgt[k * kOut + r]));
+        const int c = cell_of(d, par[k], par[3 * n + k], par[4 * n + k]);
+        atomicMax(&cell_err[c], __float_as_uint(e));
+    }
+}
+
+// Inference for the groups of one gradient type: features from the group
+// table, transition rows into `out`, and the groups that must be integrated
+// exactly (outside the domain, or in a cell whose validated error exceeds the
+// bound) appended to `fb` / `fb_n`.
+__global__ void __launch_bounds__(kNT) k_sur_infer(const float *P, const __nv_bfloat16 *W2b_g,
+                                                   SurDomain d, SurPulse pulse,
+                                                   const unsigned char *cell_ok,
+                                                   const double *par, int64_t G, float *out,
+                                                   int32_t *fb, int32_t *fb_n) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    SurSmem &sm = *reinterpret_cast<SurSmem *>(raw);
+    const int tid = threadIdx.x;
+    load_weights(sm, P, W2b_g, nullptr, false);
+    for (int64_t s0 = blockIdx.x * (int64_t)kTS; s0 < G; s0 += (int64_t)gridDim.x * kTS) {
+        const int ns = (int)min((int64_t)kTS, G - s0);
+        __syncthreads();
+        if (tid < kTS) {
+            float f[5] = {0, 0, 0, 0, 0};
+            if (tid < ns) {
+                const int64_t g = s0 + tid;
+                const double z = par[g], T1 = par[G + g], T2 = par[2 * G + g];
+                const double dB0 = par[3 * G + g], b1 = par[4 * G + g];
+                features(d, z, dB0, b1, T1, T2, f);
+                bool inside = z >= d.lo[0] && z <= d.hi[0] && dB0 >= d.lo[1] && dB0 <= d.hi[1] &&
+                              b1 >= d.lo[2] && b1 <= d.hi[2] && T1 >= d.lo[3] && T1 <= d.hi[3] &&
+                              T2 >= d.lo[4] && T2 <= d.hi[4];
+                if (!inside || !cell_ok[cell_of(d, z, dB0, b1)]) fb[atomicAdd(fb_n, 1)] = (int32_t)g;
+            }
+#pragma unroll
+            for (int c = 0; c < 5; ++c) sm.X[tid * kIn + c] = f[c];
+        }
+        __syncthreads();
+        tile_forward(sm, ns, false);
+        for (int j = tid; j < ns * kOut; j += kNT) {
+            const int s = j / kOut, r = j % kOut;
+            sm.T[j] = out_layer(sm, s, r);  // the core C
+        }
+        __syncthreads();
+        if (tid < ns) {  // T = P(th/2) [C_A P(th/2) | C_b]
+            const int64_t g = s0 + tid;
+            double t[12];
+            for (int e = 0; e < 12; ++e) t[e] = sm.T[tid * kOut + e];
+            precess_affine(t, pulse_half_angle(pulse, par[g], par[3 * G + g]));
+            for (int e = 0; e < 12; ++e) out[g * kOut + e] = (float)t[e];
+        }
+    }
+}
+
+static_assert(sizeof(SurSmem) <= 227 * 1024, "tile exceeds the per-CTA shared memory");
+size_t sur_smem() { return sizeof(SurSmem); }
+
+}  // namespace
+
+void sur_sample(mrsim_ctx *c, const SurDomain &d, uint64_t seed, int64_t n, double *par, float *X) {
+    KScope ks(c, "sur_sample");
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
+    k_sur_sample<<<std::max(grid, 1), 256, 0, c->stream>>>(d, seed, n, par, X);
+}
+
+void sur_core(mrsim_ctx *c, const SurPulse &p, const double *par, int64_t n, const double *T,
+              float *C) {
+    KScope ks(c, "sur_core");
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
+    k_sur_core<<<std::max(grid, 1), 256, 0, c->stream>>>(p, par, n, T, C);
+}
+
+void sur_bf16_copies(mrsim_ctx *c, const float *P, void *W2b, void *W2Tb) {
+    KScope ks(c, "sur_bf16");
+    k_sur_bf16_copies<<<64, 256, 0, c->stream>>>(P, (__nv_bfloat16 *)W2b, (__nv_bfloat16 *)W2Tb);
+}
+
+void sur_train_step(mrsim_ctx *c, const float *P, const void *W2b, const void *W2Tb,
+                    const float *X, const float *T, int64_t n, float *grad, double *loss,
+                    float *Yout) {
+    static bool attr = false;
+    if (!attr) {
+        MRSIM_CUDA(cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sur_smem()));
+        MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sur_smem()));
+        attr = true;
+    }
+    KScope ks(c, "sur_train");
+    const unsigned grid = (unsigned)((n + kTS - 1) / kTS);
+    k_sur_train<<<grid, kNT, sur_smem(), c->stream>>>(
+        P, (const __nv_bfloat16 *)W2b, (const __nv_bfloat16 *)W2Tb, X, T, n,
+        1.0f / (12.0f * (float)n), grad, loss, Yout);
+}
+
+void sur_adam(mrsim_ctx *c, float *P, float *grad, float *m, float *v, int step, float lr,
+              void *W2b, void *W2Tb) {
+    KScope ks(c, "sur_adam");
+    k_sur_adam<<<(kNParams + 255) / 256, 256, 0, c->stream>>>(
+        P, grad, m, v, step, lr, (__nv_bfloat16 *)W2b, (__nv_bfloat16 *)W2Tb);
+}
+
+void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t n,
+                    const float *Y, const float *T, unsigned int *cell_err) {
+    KScope ks(c, "sur_cell_error");
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
+    k_sur_cell_error<<<std::max(grid, 1), 256, 0, c->stream>>>(d, par, n, Y, T, cell_err);
+}
+
+void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
+               const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
+               float *out, int32_t *fb, int32_t *fb_n) {
+    static bool attr = false;
+    if (!attr) {
+        MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sur_smem()));
+        attr = true;
+    }
+    if (G <= 0) return;
+    KScope ks(c, "sur_infer");
+    const unsigned grid = (unsigned)std::min<int64_t>((G + kTS - 1) / kTS, (int64_t)c->sm_count * 2);
+    k_sur_infer<<<grid, kNT, sur_smem(), c->stream>>>(P, (const __nv_bfloat16 *)W2b, d, pulse,
+                                                      cell_ok, par, G, out, fb, fb_n);
+}
+
+int sur_n_params() { return kNParams; }
+
+}  // namespace mrsim

@@ -34,6 +34,8 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
+           "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
+           "mrsim_surrogate_eval", "mrsim_free_surrogate",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
 
@@ -70,6 +72,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_set_tuning": (I, [P, I, I]),
         "mrsim_get_tuning": (I, [P, I, P]),
         "mrsim_autotune": (I, [P, P, P, P, I, I, I]),
+        "mrsim_surrogate_train": (I, [P, P, P, P, I64, I, I, ctypes.c_double, ctypes.c_uint64,
+                                      ctypes.c_double, PP]),
+        "mrsim_surrogate_stats": (I, [P, P, P]),
+        "mrsim_surrogate_use": (I, [P, P]),
+        "mrsim_surrogate_eval": (I, [P, P, I64, P, P, P, P, P]),
+        "mrsim_free_surrogate": (None, [P]),
         "mrsim_free_phantom": (None, [P]),
         "mrsim_free_seq": (None, [P]),
         "mrsim_free_groups": (None, [P]),
@@ -237,6 +245,53 @@ def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):
            "mrsim_autotune")
     return {p: mrsim_get_tuning(ctx, p) for p in (TUNE_FUSED_NI, TUNE_PLAIN_RF_NI,
                                                    TUNE_ADC_CTAS_PER_SM)}
+
+
+def mrsim_surrogate_train(ctx, seq, lo, hi, n_train=1 << 22, epochs=20, batch=16384, lr=3e-3,
+                          seed=1005, bound=1e-3) -> int:
+    h = ctypes.c_void_p()
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    rc = lib().mrsim_surrogate_train(ctx, seq, _ptr(lo), _ptr(hi), int(n_train), int(epochs),
+                                     int(batch), float(lr), int(seed), float(bound),
+                                     ctypes.byref(h))
+    _check(ctx, rc, "mrsim_surrogate_train")
+    return h.value
+
+
+SURROGATE_STATS = ["networks", "train_loss", "val_max_err", "cells_served", "val_served",
+                   "val_served_max_err", "groups_served", "groups_exact"]
+
+
+def mrsim_surrogate_stats(sur, ctx=None) -> dict:
+    out = np.zeros(8)
+    rc = lib().mrsim_surrogate_stats(sur, ctx, _ptr(out))
+    if rc:
+        raise MrsimError(rc, "mrsim_surrogate_stats")
+    return dict(zip(SURROGATE_STATS, out.tolist()))
+
+
+def mrsim_surrogate_use(ctx, sur):
+    _check(ctx, lib().mrsim_surrogate_use(ctx, sur), "mrsim_surrogate_use")
+
+
+def mrsim_surrogate_eval(ctx, params, x, t):
+    """GPU forward + backward of the network: returns (y, grad, loss)."""
+    params = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    n = x.shape[0]
+    y = np.zeros((n, 12), np.float32)
+    g = np.zeros(params.size, np.float32)
+    L = ctypes.c_double()
+    rc = lib().mrsim_surrogate_eval(ctx, _ptr(params), n, _ptr(x), _ptr(t), _ptr(y), _ptr(g),
+                                    ctypes.byref(L))
+    _check(ctx, rc, "mrsim_surrogate_eval")
+    return y, g, L.value
+
+
+def mrsim_free_surrogate(sur):
+    lib().mrsim_free_surrogate(sur)
 
 
 def mrsim_adc_grouped_noalloc(K, mx, my, gid, n_groups, gpos, gdB0, gT2, n_samples, tau, kmom,
