@@ -175,6 +175,65 @@ def batch_workload(ctx, mrsim, torch, steps, warmup):
             "launches_per_batched_step": 4}
 
 
+SUR_LO = [-0.010, -80.0, 0.8, 0.3, 0.04]  # z (m), dB0 (Hz), b1, T1 (s), T2 (s)
+SUR_HI = [0.010, 80.0, 1.2, 1.5, 0.2]
+
+
+def surrogate_workload(ctx, mrsim, torch):
+    """Learned with-RF transitions: train on 4M draws of the FSE pulses with
+    2 ms sinc at 10 us, then simulate that FSE on a 27.5M-isochromat phantom
+    with per-isochromat dB0 ~ N(0, 20 Hz) and b1 ~ U[0.8, 1.2] (so nearly
+    every isochromat is its own group), exact preparation vs the network."""
+    from mrsim_inputs import configs
+    from mrsim_inputs.phantom import continuous_phantom
+    _, seq = configs.surrogate_fse()
+    hs = ctx.sequence(seq)
+    t0 = time.perf_counter()
+    sur = mrsim.mrsim_surrogate_train(ctx.h, hs, SUR_LO, SUR_HI, n_train=1 << 22, epochs=150,
+                                      batch=8192, lr=1e-2, seed=1005, bound=1e-3)
+    train_s = time.perf_counter() - t0
+    st = mrsim.mrsim_surrogate_stats(sur)
+    ph = continuous_phantom(512, 512, 105, 8, seed=1005)
+    hp = ctx.phantom(ph)
+    t0 = time.perf_counter()
+    hg = ctx.group(hp, hs)
+    group_s = time.perf_counter() - t0
+    sig = torch.zeros(2 * seq.n_samples, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(mode, reps=2):
+        mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3, sig.cpu().numpy().view(np.complex128).copy()
+
+    t_exact, s_exact = timed(mrsim.GROUPED)
+    mrsim.mrsim_surrogate_use(ctx.h, sur)
+    t_sur, s_sur = timed(mrsim.SURROGATE)
+    run = mrsim.mrsim_surrogate_stats(sur, ctx.h)
+    mrsim.mrsim_surrogate_use(ctx.h, None)
+    n_served, n_exact = run["groups_served"], run["groups_exact"]
+    out = {"K": ph.K, "groups_z": mrsim.mrsim_group_info(hg, mrsim.G_Z)[0],
+           "train": {"samples_per_pulse": 1 << 22, "epochs": 150, "seconds": round(train_s, 2),
+                     "final_mse_per_entry": st["train_loss"],
+                     "validation_max_error": st["val_max_err"],
+                     "cells_served": st["cells_served"],
+                     "served_max_error": st["val_served_max_err"], "bound": 1e-3},
+           "grouping_s": round(group_s, 3), "exact_s": round(t_exact, 4),
+           "surrogate_s": round(t_sur, 4), "speedup": round(t_exact / t_sur, 3),
+           "groups_served_fraction": round(n_served / max(n_served + n_exact, 1), 4),
+           "signal_rel_l2_vs_exact": float(np.linalg.norm(s_sur - s_exact) / np.linalg.norm(s_exact))}
+    ctx.free("grp", hg)
+    ctx.free("ph", hp)
+    mrsim.mrsim_free_surrogate(sur)
+    return out
+
+
 def golden_check(name, sig, ph_digest, seq_digest):
     path = os.path.join(GOLDEN, f"{name}_27m_oracle.npz")
     if not os.path.exists(path):
@@ -383,6 +442,8 @@ def main():
 
     # ---- batched workload: 64 uneven jobs in one graph launch ----
     batch = batch_workload(ctx, mrsim, torch, a.steps, a.warmup)
+    # ---- learned with-RF transitions ----
+    surrogate = surrogate_workload(ctx, mrsim, torch)
 
     # ---- roofline of the dominant kernel (fused isochromat pass) ----
     name = max(prof, key=lambda n: prof[n][1])
@@ -442,6 +503,7 @@ def main():
                      "seconds": round(autotune_s, 2)},
         "parity": parity,
         "batch64": batch,
+        "surrogate": surrogate,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),
