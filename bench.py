@@ -500,6 +500,8 @@ def main():
         "autotune": {"fused_isochromats_per_thread": tuned[mrsim.TUNE_FUSED_NI],
                      "plain_rf_isochromats_per_thread": tuned[mrsim.TUNE_PLAIN_RF_NI],
                      "plain_adc_ctas_per_sm": tuned[mrsim.TUNE_ADC_CTAS_PER_SM],
+                     "precompute_lanes": tuned[mrsim.TUNE_PRECOMP_LANES],
+                     "precompute_fp32_block_steps": tuned[mrsim.TUNE_PRECOMP_STEPS],
                      "seconds": round(autotune_s, 2)},
         "parity": parity,
         "batch64": batch,

@@ -226,10 +226,24 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              kernel: 1 or 2 (default 2)
  *   MRSIM_TUNE_ADC_CTAS_PER_SM CTAs per SM of the persistent plain with-ADC
  *                              kernel: 1, 2, 4 or 8 (default 2)
+ *   MRSIM_TUNE_PRECOMP_LANES   threads composing one group's combined
+ *                              transition: 4, 8, 16, 32 (one warp or less,
+ *                              shuffle tree) or 128 (a CTA, shared-memory
+ *                              tree); 0 (default) picks by pulse length
+ *   MRSIM_TUNE_PRECOMP_STEPS   FP32 runs: sub-steps composed in FP32 registers
+ *                              (difference form) before each fold into the
+ *                              FP64 combined transition: 1, 2, 4 or 8
+ *                              (default).  For 200-step sinc pulses the
+ *                              composed entries stay within 2e-7 of FP64
+ *                              composition at 8 and within 1e-7 at 4 or less
+ *                              (an FP32 result is itself rounded to 6e-8);
+ *                              FP64 runs compose every sub-step in FP64
  * mrsim_set_tuning returns MRSIM_EINVAL for another parameter or value. */
 #define MRSIM_TUNE_FUSED_NI 0
 #define MRSIM_TUNE_PLAIN_RF_NI 1
 #define MRSIM_TUNE_ADC_CTAS_PER_SM 2
+#define MRSIM_TUNE_PRECOMP_LANES 3
+#define MRSIM_TUNE_PRECOMP_STEPS 4
 int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
 int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
 

@@ -667,6 +667,7 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         key.push_back(g[i]->uid);
     }
     key.push_back((uint64_t)c->tune[MRSIM_TUNE_FUSED_NI]);
+    key.push_back((uint64_t)c->tune[MRSIM_TUNE_PRECOMP_STEPS]);
     auto &slot = batch_caches()[c];
     if (!slot || slot->key != key) {
         auto bc = std::make_unique<BatchCache>();
@@ -717,6 +718,7 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
             for (auto &t : P.tabs) {
                 pre.push_back(precomp_args<R>(s[i], g[i], t.first.first, t.first.second,
                                               T + (o_rows[i] + t.second) * 12));
+                pre.back().kb = c->tune[MRSIM_TUNE_PRECOMP_STEPS];
                 pre_off.push_back(pre_off.back() + g[i]->n_groups[t.first.second]);
             }
             const int prim = P.p;
@@ -1099,17 +1101,19 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
 
 int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
-    static const int allowed[3][4] = {{1, 2, 4, 0}, {1, 2, 0, 0}, {1, 2, 4, 8}};
-    if (param < 0 || param > 2) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
+    static const int allowed[5][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
+                                      {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
+                                      {1, 2, 4, 8, -1, -1}};
+    if (param < 0 || param > 4) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
-    for (int v : allowed[param]) ok |= v != 0 && v == value;
+    for (int v : allowed[param]) ok |= v >= 0 && v == value;
     if (!ok) return set_err(c, MRSIM_EINVAL, "value not allowed for this tuning parameter");
     c->tune[param] = value;
     return MRSIM_OK;
 }
 
 int mrsim_get_tuning(const mrsim_ctx *c, int param, int *value) {
-    if (!c || !value || param < 0 || param > 2) return MRSIM_EINVAL;
+    if (!c || !value || param < 0 || param > 4) return MRSIM_EINVAL;
     *value = c->tune[param];
     return MRSIM_OK;
 }
@@ -1129,6 +1133,8 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
         std::vector<std::pair<int, std::vector<int>>> plan;
         if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
+        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8}});
+        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 4, 8, 16, 32, 128}});
         plan.push_back({MRSIM_TUNE_PLAIN_RF_NI, {1, 2}});
         plan.push_back({MRSIM_TUNE_ADC_CTAS_PER_SM, {1, 2, 4, 8}});
         for (auto &pv : plan) {

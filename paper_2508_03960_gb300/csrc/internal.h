@@ -76,7 +76,7 @@ struct mrsim_ctx {
     const struct mrsim_surrogate *sur = nullptr;
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
-    int tune[4] = {4, 2, 2, 0};  // MRSIM_TUNE_FUSED_NI, _PLAIN_RF_NI, _ADC_CTAS_PER_SM, unused
+    int tune[5] = {4, 2, 2, 0, 8};  // indexed by the MRSIM_TUNE_* parameters
 };
 
 struct mrsim_phantom_t {
@@ -189,9 +189,13 @@ void sur_adam(mrsim_ctx *c, float *P, float *grad, float *m, float *v, int step,
               void *W2b, void *W2Tb);
 void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t n,
                     const float *Y, const float *T, unsigned int *cell_err);
+// Gate + network inference for the G groups of one table.  cell_ok == nullptr
+// serves every group (validation); otherwise groups outside the domain or in a
+// rejected cell go to the fallback list.  idx [2G]: fallback list, then served
+// list; cnt [2] (zeroed by the caller): fallback count, served count.
 void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
                const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
-               float *out, int32_t *fb, int32_t *fb_n);
+               float *out, int32_t *idx, int32_t *cnt);
 int sur_n_params();
 // run-time use by the grouped planner: fills rows [0, G) of `out` for with-RF
 // content `cid` of `s` from the context's active network, then integrates the
@@ -240,6 +244,7 @@ struct PrecompArgs {
     void *out;               // R [n_groups][12]
     const int32_t *gidx = nullptr;    // optional: only the groups gidx[0 .. *gcount)
     const int32_t *gcount = nullptr;
+    int kb = 8;                       // FP32 tables: sub-steps per FP32 register block
 };
 template <typename R>
 void launch_precompute(mrsim_ctx *c, const PrecompArgs &a);

@@ -370,20 +370,44 @@ __device__ __forceinline__ double u01(uint64_t seed, uint64_t i) {
     return (double)(splitmix64(seed * 0xd1342543de82ef95ull + i) >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// Features of one group/sample, normalised to about [-1, 1] over the domain.
-__device__ __forceinline__ void features(const SurDomain &d, double z, double dB0, double b1,
+// Affine maps of the domain: network features (about [-1, 1]) and validation
+// cells, fixed per domain so that training, validation and inference agree.
+struct FeatCoef {
+    float a[5], c[5];         // f = a v + c, v = z, dB0, b1, log T1, log T2
+    double lo[5], hi[5];      // the domain (inclusive)
+    double cell_scale[3];     // cells per unit of z, dB0, b1
+};
+
+FeatCoef feat_coef(const SurDomain &d) {
+    FeatCoef k;
+    for (int i = 0; i < 5; ++i) {
+        const bool lg = i >= 3;
+        const double lo = lg ? std::log(d.lo[i]) : d.lo[i], hi = lg ? std::log(d.hi[i]) : d.hi[i];
+        k.a[i] = (float)(2.0 / (hi - lo));
+        k.c[i] = (float)(-1.0 - 2.0 * lo / (hi - lo));
+        k.lo[i] = d.lo[i];
+        k.hi[i] = d.hi[i];
+    }
+    const int nb[3] = {kCellsZ, kCellsB0, kCellsB1};
+    for (int i = 0; i < 3; ++i) k.cell_scale[i] = nb[i] / (d.hi[i] - d.lo[i]);
+    return k;
+}
+
+// Features of one group/sample.
+__device__ __forceinline__ void features(const FeatCoef &k, double z, double dB0, double b1,
                                          double T1, double T2, float *f) {
-    f[0] = (float)((z - d.lo[0]) / (d.hi[0] - d.lo[0]) * 2.0 - 1.0);
-    f[1] = (float)((dB0 - d.lo[1]) / (d.hi[1] - d.lo[1]) * 2.0 - 1.0);
-    f[2] = (float)((b1 - d.lo[2]) / (d.hi[2] - d.lo[2]) * 2.0 - 1.0);
-    f[3] = (float)((log(T1) - log(d.lo[3])) / (log(d.hi[3]) - log(d.lo[3])) * 2.0 - 1.0);
-    f[4] = (float)((log(T2) - log(d.lo[4])) / (log(d.hi[4]) - log(d.lo[4])) * 2.0 - 1.0);
+    f[0] = fmaf(k.a[0], (float)z, k.c[0]);
+    f[1] = fmaf(k.a[1], (float)dB0, k.c[1]);
+    f[2] = fmaf(k.a[2], (float)b1, k.c[2]);
+    f[3] = fmaf(k.a[3], logf((float)T1), k.c[3]);
+    f[4] = fmaf(k.a[4], logf((float)T2), k.c[4]);
 }
 
 // Draw n samples uniformly in (z, dB0, b1) and log-uniformly in (T1, T2);
 // write the precompute parameter block [5][n] (pos, T1, T2, dB0, b1) and the
 // network features [n][5].
-__global__ void k_sur_sample(SurDomain d, uint64_t seed, int64_t n, double *par, float *X) {
+__global__ void k_sur_sample(SurDomain d, FeatCoef fc, uint64_t seed, int64_t n, double *par,
+                             float *X) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const double z = d.lo[0] + (d.hi[0] - d.lo[0]) * u01(seed, 5 * k);
@@ -396,7 +420,7 @@ __global__ void k_sur_sample(SurDomain d, uint64_t seed, int64_t n, double *par,
         par[2 * n + k] = T2;
         par[3 * n + k] = dB0;
         par[4 * n + k] = b1;
-        features(d, z, dB0, b1, T1, T2, X + 5 * k);
+        features(fc, z, dB0, b1, T1, T2, X + 5 * k);
     }
 }
 
@@ -442,13 +466,13 @@ __global__ void k_sur_core(SurPulse pulse, const double *par, int64_t n, const d
     }
 }
 
-__device__ __forceinline__ int cell_of(const SurDomain &d, double z, double dB0, double b1) {
-    const double u[3] = {(z - d.lo[0]) / (d.hi[0] - d.lo[0]), (dB0 - d.lo[1]) / (d.hi[1] - d.lo[1]),
-                         (b1 - d.lo[2]) / (d.hi[2] - d.lo[2])};
+__device__ __forceinline__ int cell_of(const FeatCoef &k, double z, double dB0, double b1) {
+    const double v[3] = {z, dB0, b1};
     const int nb[3] = {kCellsZ, kCellsB0, kCellsB1};
     int c = 0;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int q = (int)floor(u[a] * nb[a]);
+        int q = (int)floor((v[a] - k.lo[a]) * k.cell_scale[a]);
         q = q < 0 ? 0 : (q >= nb[a] ? nb[a] - 1 : q);
         c = c * nb[a] + q;
     }
@@ -456,62 +480,213 @@ __device__ __forceinline__ int cell_of(const SurDomain &d, double z, double dB0,
 }
 
 // validation: largest |error| of any transition entry per (z, dB0, b1) cell
-__global__ void k_sur_cell_error(SurDomain d, const double *par, int64_t n, const float *Y,
+__global__ void k_sur_cell_error(FeatCoef fc, const double *par, int64_t n, const float *Y,
                                  const float *Tgt, unsigned int *cell_err) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         float e = 0.0f;
         for (int r = 0; r < kOut; ++r) e = fmaxf(e, fabsf(Y[k * kOut + r] - Tgt[k * kOut + r]));
-        const int c = cell_of(d, par[k], par[3 * n + k], par[4 * n + k]);
+        const int c = cell_of(fc, par[k], par[3 * n + k], par[4 * n + k]);
         atomicMax(&cell_err[c], __float_as_uint(e));
     }
 }
 
-// Inference for the groups of one gradient type: features from the group
-// table, transition rows into `out`, and the groups that must be integrated
-// exactly (outside the domain, or in a cell whose validated error exceeds the
-// bound) appended to `fb` / `fb_n`.
-__global__ void __launch_bounds__(kNT) k_sur_infer(const float *P, const __nv_bfloat16 *W2b_g,
-                                                   SurDomain d, SurPulse pulse,
-                                                   const unsigned char *cell_ok,
-                                                   const double *par, int64_t G, float *out,
-                                                   int32_t *fb, int32_t *fb_n) {
+// Gate of the groups of one gradient type: a group is served by the network
+// when it lies inside the training domain and in a cell whose validated error
+// is within the bound (every group when cell_ok is null); otherwise it is
+// listed for exact integration.  Both
+// lists are appended with one atomic per warp (order within a list is free:
+// every group is computed on its own).
+__global__ void k_sur_gate(FeatCoef fc, const unsigned char *cell_ok, const double *par,
+                           int64_t G, int32_t *srv, int32_t *fb, int32_t *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_up = (G + 31) / 32 * 32;  // whole warps take part in the ballots
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_up;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        bool served = false;
+        const bool live = g < G;
+        if (live && !cell_ok) {
+            served = true;
+        } else if (live) {
+            const double z = par[g], T1 = par[G + g], T2 = par[2 * G + g];
+            const double dB0 = par[3 * G + g], b1 = par[4 * G + g];
+            const bool inside = z >= fc.lo[0] && z <= fc.hi[0] && dB0 >= fc.lo[1] &&
+                                dB0 <= fc.hi[1] && b1 >= fc.lo[2] && b1 <= fc.hi[2] &&
+                                T1 >= fc.lo[3] && T1 <= fc.hi[3] && T2 >= fc.lo[4] &&
+                                T2 <= fc.hi[4];
+            served = inside && cell_ok[cell_of(fc, z, dB0, b1)];
+        }
+        const unsigned ms = __ballot_sync(0xffffffffu, live && served);
+        const unsigned mf = __ballot_sync(0xffffffffu, live && !served);
+        int bs = 0, bf = 0;
+        if (lane == 0) {
+            if (ms) bs = atomicAdd(&cnt[1], __popc(ms));
+            if (mf) bf = atomicAdd(&cnt[0], __popc(mf));
+        }
+        bs = __shfl_sync(0xffffffffu, bs, 0);
+        bf = __shfl_sync(0xffffffffu, bf, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (live && served) srv[bs + __popc(ms & below)] = (int32_t)g;
+        if (live && !served) fb[bf + __popc(mf & below)] = (int32_t)g;
+    }
+}
+
+// Network inference, one warp per tile of 16 served groups, activations in
+// registers.  Layer 1 is evaluated directly into the m16n8k16 A fragments
+// (thread (g, t) of the warp owns rows g and g + 8, columns 2t, 2t + 1,
+// 2t + 8, 2t + 9 of each 16-column slice) as hi + lo BF16 pairs; layer 2 runs
+// on the tensor cores with W2 in shared memory; GELU and the FP32 output
+// layer work on the accumulator fragments, whose partial sums over a row's
+// columns are combined across the four threads of a quad.  The rows of the
+// transition are then rebuilt from the core (T = P(th/2) [C_A P(th/2) | C_b])
+// and stored.
+constexpr int kInfWarps = 4;
+struct InferSmem {
+    __nv_bfloat16 W2b[kH * kLdW];
+    float W1[kH * kIn], b1[kH], b2[kH], W3[kOut * kH], b3[16];
+    float stage[kInfWarps][16][kOut + 1];
+};
+
+__global__ void __launch_bounds__(kInfWarps * 32, 3)
+    k_sur_infer(const float *P, const __nv_bfloat16 *W2b_g, FeatCoef fc, SurPulse pulse,
+                const double *par, int64_t G, const int32_t *srv, const int32_t *cnt,
+                float *out) {
     extern __shared__ __align__(16) unsigned char raw[];
-    SurSmem &sm = *reinterpret_cast<SurSmem *>(raw);
-    const int tid = threadIdx.x;
-    load_weights(sm, P, W2b_g, nullptr, false);
-    for (int64_t s0 = blockIdx.x * (int64_t)kTS; s0 < G; s0 += (int64_t)gridDim.x * kTS) {
-        const int ns = (int)min((int64_t)kTS, G - s0);
-        __syncthreads();
-        if (tid < kTS) {
-            float f[5] = {0, 0, 0, 0, 0};
-            if (tid < ns) {
-                const int64_t g = s0 + tid;
-                const double z = par[g], T1 = par[G + g], T2 = par[2 * G + g];
-                const double dB0 = par[3 * G + g], b1 = par[4 * G + g];
-                features(d, z, dB0, b1, T1, T2, f);
-                bool inside = z >= d.lo[0] && z <= d.hi[0] && dB0 >= d.lo[1] && dB0 <= d.hi[1] &&
-                              b1 >= d.lo[2] && b1 <= d.hi[2] && T1 >= d.lo[3] && T1 <= d.hi[3] &&
-                              T2 >= d.lo[4] && T2 <= d.hi[4];
-                if (!inside || !cell_ok[cell_of(d, z, dB0, b1)]) fb[atomicAdd(fb_n, 1)] = (int32_t)g;
+    InferSmem &sm = *reinterpret_cast<InferSmem *>(raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    for (int j = tid; j < kH * kH / 8; j += kInfWarps * 32) {
+        const int r = (j * 8) / kH, c = (j * 8) % kH;
+        *reinterpret_cast<int4 *>(&sm.W2b[r * kLdW + c]) = reinterpret_cast<const int4 *>(W2b_g)[j];
+    }
+    for (int j = tid; j < kH * kIn; j += kInfWarps * 32) sm.W1[j] = P[oW1 + j];
+    for (int j = tid; j < kH; j += kInfWarps * 32) {
+        sm.b1[j] = P[ob1 + j];
+        sm.b2[j] = P[ob2 + j];
+    }
+    for (int j = tid; j < kOut * kH; j += kInfWarps * 32) sm.W3[j] = P[oW3 + j];
+    if (tid < kOut) sm.b3[tid] = P[ob3 + tid];
+    __syncthreads();
+    const int64_t n = *cnt;
+    float (*stage)[kOut + 1] = sm.stage[warp];
+    for (int64_t tile = blockIdx.x * (int64_t)kInfWarps + warp; tile * 16 < n;
+         tile += (int64_t)gridDim.x * kInfWarps) {
+        // features of the tile's groups (lanes 0-15) and their precession angle
+        const int64_t s0 = tile * 16;
+        const int ns = (int)min((int64_t)16, n - s0);
+        float f[kIn] = {0, 0, 0, 0, 0};
+        float half_turns = 0.0f;
+        int64_t grp = -1;
+        if (lane < ns) {
+            grp = srv[s0 + lane];
+            const double z = par[grp], T1 = par[G + grp], T2 = par[2 * G + grp];
+            const double dB0 = par[3 * G + grp], b1 = par[4 * G + grp];
+            features(fc, z, dB0, b1, T1, T2, f);
+            double h = 0.5 * (kGammaBar * z * pulse.mz + dB0 * pulse.dur);
+            half_turns = (float)(h - rint(h));
+        }
+        float xg[kIn], xg8[kIn];
+#pragma unroll
+        for (int c = 0; c < kIn; ++c) {
+            xg[c] = __shfl_sync(0xffffffffu, f[c], g);
+            xg8[c] = __shfl_sync(0xffffffffu, f[c], g + 8);
+        }
+        float acc[16][4];
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const float bl = sm.b2[nt * 8 + 2 * t], bh = sm.b2[nt * 8 + 2 * t + 1];
+            acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+        }
+#pragma unroll 1
+        for (int ks = 0; ks < kH / 16; ++ks) {
+            // h1 at rows g, g + 8 and columns ks*16 + {2t, 2t+1, 2t+8, 2t+9}
+            float h[2][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int col = ks * 16 + 2 * t + (q & 1) + (q >> 1) * 8;
+                float a0 = sm.b1[col], a1 = a0;
+#pragma unroll
+                for (int c = 0; c < kIn; ++c) {
+                    const float w = sm.W1[col * kIn + c];
+                    a0 = fmaf(w, xg[c], a0);
+                    a1 = fmaf(w, xg8[c], a1);
+                }
+                h[0][q] = gelu(a0);
+                h[1][q] = gelu(a1);
+            }
+            uint32_t ahi[4], alo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // fragment register q: row g (q even) or g + 8 (q odd), columns
+                // 2t, 2t + 1 (q < 2) or 2t + 8, 2t + 9 (q >= 2)
+                const int row = q & 1, pair = q >> 1;
+                const float v0 = h[row][2 * pair], v1 = h[row][2 * pair + 1];
+                const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 lb = __floats2bfloat162_rn(v0 - __low2float(hb),
+                                                                v1 - __high2float(hb));
+                ahi[q] = *reinterpret_cast<const uint32_t *>(&hb);
+                alo[q] = *reinterpret_cast<const uint32_t *>(&lb);
             }
 #pragma unroll
-            for (int c = 0; c < 5; ++c) sm.X[tid * kIn + c] = f[c];
+            for (int nt = 0; nt < 16; ++nt) {
+                uint32_t b[2];
+                load_b(b, sm.W2b, kLdW, nt * 8, ks * 16);
+                mma16816(acc[nt], ahi, b);
+                mma16816(acc[nt], alo, b);
+            }
         }
-        __syncthreads();
-        tile_forward(sm, ns, false);
-        for (int j = tid; j < ns * kOut; j += kNT) {
-            const int s = j / kOut, r = j % kOut;
-            sm.T[j] = out_layer(sm, s, r);  // the core C
+        // h2 = gelu(a2); output layer partial sums over this thread's columns
+        float part[2][kOut];
+#pragma unroll
+        for (int r = 0; r < kOut; ++r) part[0][r] = part[1][r] = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const float h00 = gelu(acc[nt][0]), h01 = gelu(acc[nt][1]);
+            const float h10 = gelu(acc[nt][2]), h11 = gelu(acc[nt][3]);
+#pragma unroll
+            for (int r = 0; r < kOut; ++r) {
+                const float2 w = *reinterpret_cast<const float2 *>(&sm.W3[r * kH + nt * 8 + 2 * t]);
+                part[0][r] = fmaf(w.x, h00, fmaf(w.y, h01, part[0][r]));
+                part[1][r] = fmaf(w.x, h10, fmaf(w.y, h11, part[1][r]));
+            }
         }
-        __syncthreads();
-        if (tid < ns) {  // T = P(th/2) [C_A P(th/2) | C_b]
-            const int64_t g = s0 + tid;
-            double t[12];
-            for (int e = 0; e < 12; ++e) t[e] = sm.T[tid * kOut + e];
-            precess_affine(t, pulse_half_angle(pulse, par[g], par[3 * G + g]));
-            for (int e = 0; e < 12; ++e) out[g * kOut + e] = (float)t[e];
+#pragma unroll
+        for (int r = 0; r < kOut; ++r) {
+#pragma unroll
+            for (int m = 1; m < 4; m <<= 1) {
+                part[0][r] += __shfl_xor_sync(0xffffffffu, part[0][r], m);
+                part[1][r] += __shfl_xor_sync(0xffffffffu, part[1][r], m);
+            }
+            if ((r & 3) == t) {
+                stage[g][r] = part[0][r] + sm.b3[r];
+                stage[g + 8][r] = part[1][r] + sm.b3[r];
+            }
         }
+        __syncwarp();
+        if (lane < ns) {  // T = P(th/2) [C_A P(th/2) | C_b]
+            float T[kOut];
+#pragma unroll
+            for (int e = 0; e < kOut; ++e) T[e] = stage[lane][e];
+            float sn, cs;
+            sincospif(2.0f * half_turns, &sn, &cs);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float a0 = T[4 * r], a1 = T[4 * r + 1];
+                T[4 * r] = cs * a0 - sn * a1;
+                T[4 * r + 1] = sn * a0 + cs * a1;
+            }
+#pragma unroll
+            for (int col = 0; col < 4; ++col) {
+                const float r0 = T[col], r1 = T[4 + col];
+                T[col] = cs * r0 + sn * r1;
+                T[4 + col] = -sn * r0 + cs * r1;
+            }
+            float4 *o = reinterpret_cast<float4 *>(out + grp * kOut);
+            o[0] = make_float4(T[0], T[1], T[2], T[3]);
+            o[1] = make_float4(T[4], T[5], T[6], T[7]);
+            o[2] = make_float4(T[8], T[9], T[10], T[11]);
+        }
+        __syncwarp();
     }
 }
 
@@ -523,7 +698,7 @@ size_t sur_smem() { return sizeof(SurSmem); }
 void sur_sample(mrsim_ctx *c, const SurDomain &d, uint64_t seed, int64_t n, double *par, float *X) {
     KScope ks(c, "sur_sample");
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
-    k_sur_sample<<<std::max(grid, 1), 256, 0, c->stream>>>(d, seed, n, par, X);
+    k_sur_sample<<<std::max(grid, 1), 256, 0, c->stream>>>(d, feat_coef(d), seed, n, par, X);
 }
 
 void sur_core(mrsim_ctx *c, const SurPulse &p, const double *par, int64_t n, const double *T,
@@ -545,8 +720,6 @@ void sur_train_step(mrsim_ctx *c, const float *P, const void *W2b, const void *W
     if (!attr) {
         MRSIM_CUDA(cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sur_smem()));
-        MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sur_smem()));
         attr = true;
     }
     KScope ks(c, "sur_train");
@@ -567,23 +740,37 @@ void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t
                     const float *Y, const float *T, unsigned int *cell_err) {
     KScope ks(c, "sur_cell_error");
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
-    k_sur_cell_error<<<std::max(grid, 1), 256, 0, c->stream>>>(d, par, n, Y, T, cell_err);
+    k_sur_cell_error<<<std::max(grid, 1), 256, 0, c->stream>>>(feat_coef(d), par, n, Y, T,
+                                                                cell_err);
 }
 
 void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
                const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
-               float *out, int32_t *fb, int32_t *fb_n) {
+               float *out, int32_t *idx, int32_t *cnt) {
     static bool attr = false;
     if (!attr) {
         MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sur_smem()));
+                                        (int)sizeof(InferSmem)));
         attr = true;
     }
     if (G <= 0) return;
+    const FeatCoef fc = feat_coef(d);
+    int32_t *fb = idx, *srv = idx + G;
+    {
+        KScope ks(c, "sur_gate");
+        const unsigned grid = (unsigned)std::min<int64_t>((G + 255) / 256, (int64_t)c->sm_count * 16);
+        k_sur_gate<<<grid, 256, 0, c->stream>>>(fc, cell_ok, par, G, srv, fb, cnt);
+    }
     KScope ks(c, "sur_infer");
-    const unsigned grid = (unsigned)std::min<int64_t>((G + kTS - 1) / kTS, (int64_t)c->sm_count * 2);
-    k_sur_infer<<<grid, kNT, sur_smem(), c->stream>>>(P, (const __nv_bfloat16 *)W2b, d, pulse,
-                                                      cell_ok, par, G, out, fb, fb_n);
+    int occ = 0;
+    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sur_infer, kInfWarps * 32,
+                                                             sizeof(InferSmem)));
+    const int64_t tiles = (G + 15) / 16;
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((tiles + kInfWarps - 1) / kInfWarps,
+                             (int64_t)c->sm_count * std::max(occ, 1)));
+    k_sur_infer<<<grid, kInfWarps * 32, sizeof(InferSmem), c->stream>>>(
+        P, (const __nv_bfloat16 *)W2b, fc, pulse, par, G, srv, cnt + 1, out);
 }
 
 int sur_n_params() { return kNParams; }

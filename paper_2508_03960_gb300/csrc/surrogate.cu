@@ -71,9 +71,9 @@ bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid,
         if (same_content(n, s, cid)) { net = &n; break; }
     if (!net) return false;
     const int64_t G = g->n_groups[G_Z];
-    int32_t *fb = (int32_t *)scratch(c, 4, std::max<int64_t>(G, 1) * sizeof(int32_t));
-    int32_t *fb_n = (int32_t *)scratch(c, 3, 64);
-    MRSIM_CUDA(cudaMemsetAsync(fb_n, 0, sizeof(int32_t), c->stream));
+    int32_t *fb = (int32_t *)scratch(c, 4, std::max<int64_t>(2 * G, 1) * sizeof(int32_t));
+    int32_t *fb_n = (int32_t *)scratch(c, 3, 64);  // [fallback count, served count]
+    MRSIM_CUDA(cudaMemsetAsync(fb_n, 0, 2 * sizeof(int32_t), c->stream));
     const double *par = g->tab[G_Z].d_par64.as<double>();
     sur_infer(c, net->P.as<float>(), net->W2b.p, S->dom, net->pulse,
               net->cell_ok.as<unsigned char>(), par, G, out, fb, fb_n);
@@ -201,14 +201,11 @@ int mrsim_surrogate_train(mrsim_ctx *c, const mrsim_seq *s, const double *lo, co
             launch_precompute<double>(c, exact_args(s, cid, n_val, par.as<double>(), Td.as<double>()));
             // validation compares full transitions (the quantity the gate bounds)
             sur_core(c, SurPulse{0.0, 0.0}, par.as<double>(), n_val, Td.as<double>(), T.as<float>());
-            std::vector<unsigned char> ok_all(kCells, 1);
-            DBuf ok = dalloc(kCells);
-            upload(c, ok.p, ok_all.data(), kCells);
-            DBuf fb = dalloc(n_val * sizeof(int32_t));
-            DBuf fb_n = dalloc(sizeof(int32_t));
-            MRSIM_CUDA(cudaMemsetAsync(fb_n.p, 0, sizeof(int32_t), c->stream));
-            sur_infer(c, net.P.as<float>(), net.W2b.p, S->dom, net.pulse, ok.as<unsigned char>(),
-                      par.as<double>(), n_val, Y.as<float>(), fb.as<int32_t>(), fb_n.as<int32_t>());
+            DBuf idx = dalloc(2 * n_val * sizeof(int32_t));
+            DBuf cnt = dalloc(2 * sizeof(int32_t));
+            MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), c->stream));
+            sur_infer(c, net.P.as<float>(), net.W2b.p, S->dom, net.pulse, nullptr,
+                      par.as<double>(), n_val, Y.as<float>(), idx.as<int32_t>(), cnt.as<int32_t>());
             MRSIM_CUDA(cudaMemsetAsync(cell_err.p, 0, kCells * sizeof(unsigned int), c->stream));
             sur_cell_error(c, S->dom, par.as<double>(), n_val, Y.as<float>(), T.as<float>(),
                            cell_err.as<unsigned int>());

@@ -26,7 +26,8 @@ G_NONE, G_X, G_Y, G_Z, G_GENERAL = 0, 1, 2, 3, 4
 PLAIN, PLAIN_CACHE, GROUPED, SURROGATE = 0, 1, 2, 3
 FP32, FP64 = 0, 1
 PTR_DEVICE, OUT_DEVICE = 1, 2
-TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM = 0, 1, 2
+TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1, 2, 3
+TUNE_PRECOMP_STEPS = 4
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
@@ -244,7 +245,8 @@ def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):
     _check(ctx, lib().mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps),
            "mrsim_autotune")
     return {p: mrsim_get_tuning(ctx, p) for p in (TUNE_FUSED_NI, TUNE_PLAIN_RF_NI,
-                                                   TUNE_ADC_CTAS_PER_SM)}
+                                                   TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES,
+                                                   TUNE_PRECOMP_STEPS)}
 
 
 def mrsim_surrogate_train(ctx, seq, lo, hi, n_train=1 << 22, epochs=20, batch=16384, lr=3e-3,

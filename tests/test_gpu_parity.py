@@ -290,3 +290,53 @@ def test_repeated_runs_are_consistent(mrsim, ctx):
     a, _ = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32)
     b, _ = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32)
     assert oracle.rel_l2(a, ref) <= 1e-4 and oracle.rel_l2(b, a) <= 1e-6
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32, 128])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_precompute_lane_counts(mrsim, ctx, lanes, precision):
+    """Every lane count of the combined-transition step (shuffle tree inside a
+    warp, or shared-memory tree over a CTA) gives the oracle's signal; the
+    phantom makes almost every isochromat its own group, with a ragged count
+    of groups per warp."""
+    from mrsim_inputs.phantom import continuous_phantom
+    ph = continuous_phantom(13, 11, 3, 2, seed=77)
+    seq = fse_2d(n_ro=16, n_pe=8, etl=4, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=0.5, n_shots=2)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_LANES, lanes)
+    try:
+        sig, M = run_both(mrsim, ctx, ph, seq, mrsim.GROUPED, precision)
+    finally:
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_LANES, 0)
+    check(sig, M, ref, Mref, precision, M0max=float(np.max(ph.M0)))
+
+
+@pytest.mark.parametrize("steps", [1, 2, 4, 8])
+def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
+    """FP32 runs compose a few sub-steps in FP32 registers before each fold into
+    the FP64 combined transition; every allowed block length keeps the FP32
+    target, and an FP64 run ignores the setting."""
+    from mrsim_inputs.phantom import continuous_phantom
+    ph = continuous_phantom(13, 11, 3, 2, seed=78)
+    seq = fse_2d(n_ro=16, n_pe=8, etl=4, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=0.5, n_shots=2)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS, steps)
+    try:
+        for precision in (0, 1):
+            sig, M = run_both(mrsim, ctx, ph, seq, mrsim.GROUPED, precision)
+            check(sig, M, ref, Mref, precision, M0max=float(np.max(ph.M0)))
+    finally:
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS, 8)
+
+
+def test_tuning_parameters_are_validated(mrsim, ctx):
+    for param, bad in ((mrsim.TUNE_FUSED_NI, 3), (mrsim.TUNE_PRECOMP_LANES, 64),
+                       (mrsim.TUNE_PRECOMP_STEPS, 16), (5, 1), (-1, 1)):
+        with pytest.raises(mrsim.MrsimError):
+            mrsim.mrsim_set_tuning(ctx.h, param, bad)
+    before = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS, 8)
+    assert mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS) == 8
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS, before)
