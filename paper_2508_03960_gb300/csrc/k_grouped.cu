@@ -454,12 +454,17 @@ __device__ __forceinline__ void ev_adc_direct(const Iso<R, NI> &s, const FEvent<
 }
 
 // advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1
+// (tu: the thread's isochromats share one primary group, so one factor load
+// serves all of them)
 template <typename R, int NI, int MASK>
-__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt) {
+__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt,
+                                           bool tu) {
     const R4<R> *Pe = Pt + ev.prow;
+    const R4<R> P0 = load4(Pe + s.pofs[0]);
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const R4<R> P = load4(Pe + s.pofs[i]);
+        R4<R> P = P0;
+        if (i > 0 && !tu) P = load4(Pe + s.pofs[i]);
         R fr = P.x, fi = P.y;
         if constexpr (MASK != 0) {
             R c, sn;
@@ -500,6 +505,8 @@ struct FusedSmem {
     __align__(16) unsigned char acc_raw[kAccBytes];  // staged block sums [batch][slot][re, im]
     __align__(16) FEvent<R> sev[kEvChunk];           // staged events
     int batch_prow[kBatch], batch_win[kBatch];
+    R wpart[kBatch][kThreads / 32][2];  // sums of warps whose isochromats share one group
+    int wslot[kThreads / 32];           // that group's slot, or -1
 };
 
 // One chunk of kThreads * NI isochromats (chunk index blk) through all events
@@ -526,12 +533,14 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     const int B = max(1, min(kBatch, (int)(kAccBytes / (S * 2 * (int)sizeof(R)))));
     const bool stage = S * 2 * (int)sizeof(R) <= kAccBytes;
 
-    // isochromat i of this thread: base + i * kThreads + tid (coalesced per i)
+    // isochromat i of this thread: base + tid * NI + i.  Consecutive
+    // isochromats of the sorted layout mostly share their groups, so a thread
+    // usually needs one group-factor and one transition row per event.
     Iso<R, NI> s;
     int32_t key[NI];  // primary group, or a value sorting last for padding
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const int64_t k = base + (int64_t)i * kThreads + tid;
+        const int64_t k = base + (int64_t)tid * NI + i;
         if (k < a.K) {
             s.x[i] = a.x[k]; s.y[i] = a.y[k]; s.z[i] = a.z[k]; s.M0[i] = a.M0[k];
             if (a.init_eq) {
@@ -556,6 +565,12 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
         }
         s.pofs[i] = min(key[i], g_last);
     }
+    bool tu_p = true, tu_r = true;  // the thread's isochromats share their groups
+#pragma unroll
+    for (int i = 1; i < NI; ++i) {
+        tu_p &= s.pofs[i] == s.pofs[0];
+        tu_r &= s.tofs[i] == s.tofs[0];
+    }
     if (stage)
         for (int t = tid; t < B * S * 2; t += kThreads) acc[t] = 0;
     // a warp whose isochromats all share one primary group reduces with plain shuffles
@@ -564,13 +579,22 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
 #pragma unroll
     for (int i = 0; i < NI; ++i) uni &= (key[i] == w0 || key[i] == 0x7fffffff);
     const bool warp_uni = __all_sync(0xffffffffu, uni) && w0 != 0x7fffffff;
+    const int warp = tid >> 5;
+    if (lane == 0) sm.wslot[warp] = (warp_uni && stage) ? w0 - g_first : -1;
 
     int nb = 0;  // windows staged (uniform)
     auto flush = [&]() {
         __syncthreads();
         for (int t = tid; t < nb * S; t += kThreads) {
             const int b = t / S, slot = t - b * S;
-            const R sr = acc[2 * t], si = acc[2 * t + 1];
+            R sr = acc[2 * t], si = acc[2 * t + 1];
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                if (sm.wslot[w] == slot) {
+                    sr += sm.wpart[b][w][0];
+                    si += sm.wpart[b][w][1];
+                }
+            }
             if (sr != (R)0 || si != (R)0) {
                 R4<R> P{(R)1, (R)0, (R)1, (R)0};
                 if constexpr (!DIRECT) P = load4(Pt + batch_prow[b] + g_first + slot);
@@ -588,15 +612,23 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     auto rf_apply = [&](const FEvent<R> &ev, int gtype) {
         const int32_t *g = gtype == a.gtype_r ? nullptr : a.gid[gtype];
         const R *Te = Tt + (int64_t)ev.row * 12;
+        const bool one_row = tu_r && !g;
+        R T0[12];
+        if (one_row) load_row(Te + s.tofs[0], T0);
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
-            int off = s.tofs[i];
-            if (g) {
-                const int64_t k = base + (int64_t)i * kThreads + tid;
-                off = k < a.K ? 12 * g[k] : 0;
-            }
             R T[12];
-            load_row(Te + off, T);
+            if (one_row) {
+#pragma unroll
+                for (int e = 0; e < 12; ++e) T[e] = T0[e];
+            } else {
+                int off = s.tofs[i];
+                if (g) {
+                    const int64_t k = base + (int64_t)tid * NI + i;
+                    off = k < a.K ? 12 * g[k] : 0;
+                }
+                load_row(Te + off, T);
+            }
             const R nx = T[0] * s.mx[i] + T[1] * s.my[i] + T[2] * s.mz[i] + T[3] * s.M0[i];
             const R ny = T[4] * s.mx[i] + T[5] * s.my[i] + T[6] * s.mz[i] + T[7] * s.M0[i];
             const R nz = T[8] * s.mx[i] + T[9] * s.my[i] + T[10] * s.mz[i] + T[11] * s.M0[i];
@@ -618,9 +650,9 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                     sr += __shfl_xor_sync(0xffffffffu, sr, d);
                     si += __shfl_xor_sync(0xffffffffu, si, d);
                 }
-                if (lane == 0) {
-                    atomicAdd(&accb[2 * (w0 - g_first)], sr);
-                    atomicAdd(&accb[2 * (w0 - g_first) + 1], si);
+                if (lane == 0) {  // no contention: summed over warps at the flush
+                    sm.wpart[nb][warp][0] = sr;
+                    sm.wpart[nb][warp][1] = si;
                 }
             } else {
                 // keys are sorted along the lanes for each i: a segmented
@@ -653,7 +685,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             const int32_t *g = a.gid[gtype];
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
-                const int64_t k = base + (int64_t)i * kThreads + tid;
+                const int64_t k = base + (int64_t)tid * NI + i;
                 if (k < a.K) {
                     R4<R> P{(R)1, (R)0, (R)1, (R)0};
                     if constexpr (!DIRECT) P = load4(Pt + ev.prow + s.pofs[i]);
@@ -667,7 +699,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
 
 #define MRSIM_ADV_CASE(M)                       \
     case M:                                     \
-        ev_advance<R, NI, M>(s, ev, Pt);        \
+        ev_advance<R, NI, M>(s, ev, Pt, tu_p);  \
         break;
 #define MRSIM_ADC_CASE(M)                       \
     case M:                                     \
@@ -702,7 +734,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 } else if (a.Mx) {  // EV_END: store the state
 #pragma unroll
                     for (int i = 0; i < NI; ++i) {
-                        const int64_t k = base + (int64_t)i * kThreads + tid;
+                        const int64_t k = base + (int64_t)tid * NI + i;
                         if (k < a.K) {
                             a.Mx[k] = s.mx[i];
                             a.My[k] = s.my[i];
