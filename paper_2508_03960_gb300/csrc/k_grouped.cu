@@ -368,7 +368,7 @@ __device__ __forceinline__ R4<R> load4(const R4<R> *p) {
     }
 }
 
-constexpr int kBatch = 8;             // with-ADC windows per shared-memory flush
+constexpr int kBatch = 32;            // with-ADC windows per shared-memory flush
 constexpr int kAccBytes = 32 * 1024;  // block-sum staging per CTA
 
 template <int MASK>
@@ -454,17 +454,12 @@ __device__ __forceinline__ void ev_adc_direct(const Iso<R, NI> &s, const FEvent<
 }
 
 // advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1
-// (tu: the thread's isochromats share one primary group, so one factor load
-// serves all of them)
 template <typename R, int NI, int MASK>
-__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt,
-                                           bool tu) {
+__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt) {
     const R4<R> *Pe = Pt + ev.prow;
-    const R4<R> P0 = load4(Pe + s.pofs[0]);
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        R4<R> P = P0;
-        if (i > 0 && !tu) P = load4(Pe + s.pofs[i]);
+        const R4<R> P = load4(Pe + s.pofs[i]);
         R fr = P.x, fi = P.y;
         if constexpr (MASK != 0) {
             R c, sn;
@@ -533,14 +528,20 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     const int B = max(1, min(kBatch, (int)(kAccBytes / (S * 2 * (int)sizeof(R)))));
     const bool stage = S * 2 * (int)sizeof(R) <= kAccBytes;
 
-    // isochromat i of this thread: base + tid * NI + i.  Consecutive
-    // isochromats of the sorted layout mostly share their groups, so a thread
-    // usually needs one group-factor and one transition row per event.
+    // isochromat i of this thread.  With group tables (groups of several
+    // isochromats) a thread holds NI consecutive isochromats of the sorted
+    // layout (measured faster: the table rows a warp reads are fewer and the
+    // warp-level reductions see longer runs).  In direct mode (about one group
+    // per isochromat) every isochromat reads its own transition row, and the
+    // mapping base + i * kThreads + tid keeps those reads coalesced.
+    auto iso_k = [&](int i) -> int64_t {
+        return DIRECT ? base + (int64_t)i * kThreads + tid : base + (int64_t)tid * NI + i;
+    };
     Iso<R, NI> s;
     int32_t key[NI];  // primary group, or a value sorting last for padding
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const int64_t k = base + (int64_t)tid * NI + i;
+        const int64_t k = iso_k(i);
         if (k < a.K) {
             s.x[i] = a.x[k]; s.y[i] = a.y[k]; s.z[i] = a.z[k]; s.M0[i] = a.M0[k];
             if (a.init_eq) {
@@ -565,12 +566,6 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
         }
         s.pofs[i] = min(key[i], g_last);
     }
-    bool tu_p = true, tu_r = true;  // the thread's isochromats share their groups
-#pragma unroll
-    for (int i = 1; i < NI; ++i) {
-        tu_p &= s.pofs[i] == s.pofs[0];
-        tu_r &= s.tofs[i] == s.tofs[0];
-    }
     if (stage)
         for (int t = tid; t < B * S * 2; t += kThreads) acc[t] = 0;
     // a warp whose isochromats all share one primary group reduces with plain shuffles
@@ -581,6 +576,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     const bool warp_uni = __all_sync(0xffffffffu, uni) && w0 != 0x7fffffff;
     const int warp = tid >> 5;
     if (lane == 0) sm.wslot[warp] = (warp_uni && stage) ? w0 - g_first : -1;
+    // (the flush visits the per-warp partials only if some warp stores them)
+    const bool any_uni = __syncthreads_or(warp_uni && stage) != 0;
 
     int nb = 0;  // windows staged (uniform)
     auto flush = [&]() {
@@ -588,19 +585,27 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
         for (int t = tid; t < nb * S; t += kThreads) {
             const int b = t / S, slot = t - b * S;
             R sr = acc[2 * t], si = acc[2 * t + 1];
+            if (any_uni) {
 #pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) {
-                if (sm.wslot[w] == slot) {
-                    sr += sm.wpart[b][w][0];
-                    si += sm.wpart[b][w][1];
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    if (sm.wslot[w] == slot) {
+                        sr += sm.wpart[b][w][0];
+                        si += sm.wpart[b][w][1];
+                    }
                 }
             }
             if (sr != (R)0 || si != (R)0) {
                 R4<R> P{(R)1, (R)0, (R)1, (R)0};
                 if constexpr (!DIRECT) P = load4(Pt + batch_prow[b] + g_first + slot);
                 const int64_t o = 2 * ((int64_t)batch_win[b] + g_first + slot);
-                atomicAdd(&Ablk[o], (double)(P.x * sr - P.y * si));
-                atomicAdd(&Ablk[o + 1], (double)(P.x * si + P.y * sr));
+                const double vr = (double)(P.x * sr - P.y * si), vi = (double)(P.x * si + P.y * sr);
+                if (slot != 0 && slot != S - 1) {
+                    // a group strictly inside the chunk has no other contributor
+                    *reinterpret_cast<double2 *>(&Ablk[o]) = make_double2(vr, vi);
+                } else {
+                    atomicAdd(&Ablk[o], vr);
+                    atomicAdd(&Ablk[o + 1], vi);
+                }
                 acc[2 * t] = 0;
                 acc[2 * t + 1] = 0;
             }
@@ -612,23 +617,15 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     auto rf_apply = [&](const FEvent<R> &ev, int gtype) {
         const int32_t *g = gtype == a.gtype_r ? nullptr : a.gid[gtype];
         const R *Te = Tt + (int64_t)ev.row * 12;
-        const bool one_row = tu_r && !g;
-        R T0[12];
-        if (one_row) load_row(Te + s.tofs[0], T0);
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
-            R T[12];
-            if (one_row) {
-#pragma unroll
-                for (int e = 0; e < 12; ++e) T[e] = T0[e];
-            } else {
-                int off = s.tofs[i];
-                if (g) {
-                    const int64_t k = base + (int64_t)tid * NI + i;
-                    off = k < a.K ? 12 * g[k] : 0;
-                }
-                load_row(Te + off, T);
+            int off = s.tofs[i];
+            if (g) {
+                const int64_t k = iso_k(i);
+                off = k < a.K ? 12 * g[k] : 0;
             }
+            R T[12];
+            load_row(Te + off, T);
             const R nx = T[0] * s.mx[i] + T[1] * s.my[i] + T[2] * s.mz[i] + T[3] * s.M0[i];
             const R ny = T[4] * s.mx[i] + T[5] * s.my[i] + T[6] * s.mz[i] + T[7] * s.M0[i];
             const R nz = T[8] * s.mx[i] + T[9] * s.my[i] + T[10] * s.mz[i] + T[11] * s.M0[i];
@@ -685,7 +682,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             const int32_t *g = a.gid[gtype];
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
-                const int64_t k = base + (int64_t)tid * NI + i;
+                const int64_t k = iso_k(i);
                 if (k < a.K) {
                     R4<R> P{(R)1, (R)0, (R)1, (R)0};
                     if constexpr (!DIRECT) P = load4(Pt + ev.prow + s.pofs[i]);
@@ -699,7 +696,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
 
 #define MRSIM_ADV_CASE(M)                       \
     case M:                                     \
-        ev_advance<R, NI, M>(s, ev, Pt, tu_p);  \
+        ev_advance<R, NI, M>(s, ev, Pt);        \
         break;
 #define MRSIM_ADC_CASE(M)                       \
     case M:                                     \
@@ -734,7 +731,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 } else if (a.Mx) {  // EV_END: store the state
 #pragma unroll
                     for (int i = 0; i < NI; ++i) {
-                        const int64_t k = base + (int64_t)tid * NI + i;
+                        const int64_t k = iso_k(i);
                         if (k < a.K) {
                             a.Mx[k] = s.mx[i];
                             a.My[k] = s.my[i];
@@ -826,9 +823,18 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
                                                    const GSigTables<R> &tab, const double *Ablk,
                                                    double *signal) {
     __shared__ R s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
+    __shared__ double s_red[2][kThreads];
     const GWin w = wins[b.x];
-    const int64_t s_idx = (int64_t)b.y + threadIdx.x;
-    const bool act = s_idx < w.sample0 + w.n_samples;
+    // samples of this block: [b.y, b.y + nsb).  A window shorter than the
+    // block gets several group lanes per sample (lane sl takes groups sl,
+    // sl + LPS, ...), combined in shared memory before the FP64 atomics.
+    const int nsb = (int)min((long long)kThreads, w.sample0 + w.n_samples - (long long)b.y);
+    int SPB = 32;
+    while (SPB < nsb) SPB <<= 1;
+    const int LPS = kThreads / SPB;
+    const int si = threadIdx.x & (SPB - 1), sl = threadIdx.x / SPB;
+    const int64_t s_idx = (int64_t)b.y + si;
+    const bool act = si < nsb;
     typename GS<R>::S sm{};
     if (act) sm = smp[s_idx];
     const R tau = act ? (R)gs_tau(sm) : (R)0;
@@ -847,7 +853,7 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
         __syncthreads();
         R pr = 0, pi = 0;
         if (act) {
-            for (int t = 0; t < n; ++t) {
+            for (int t = sl; t < n; t += LPS) {
                 R c, s;
                 phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, s);
                 const R e = decay(tau, s_rT2[t]);
@@ -859,7 +865,18 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
         accr += (double)pr;
         acci += (double)pi;
     }
-    if (act) {
+    if (LPS > 1) {
+        s_red[0][threadIdx.x] = accr;
+        s_red[1][threadIdx.x] = acci;
+        __syncthreads();
+        if (sl == 0) {
+            for (int l = 1; l < LPS; ++l) {
+                accr += s_red[0][l * SPB + si];
+                acci += s_red[1][l * SPB + si];
+            }
+        }
+    }
+    if (act && sl == 0) {
         atomicAdd(&signal[2 * s_idx], accr);
         atomicAdd(&signal[2 * s_idx + 1], acci);
     }
