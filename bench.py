@@ -210,11 +210,19 @@ def surrogate_workload(ctx, mrsim, torch):
             mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps / 1e3, sig.cpu().numpy().view(np.complex128).copy()
+        t = e0.elapsed_time(e1) / reps / 1e3
+        # per-kernel split of one more run (CUDA events around each launch)
+        mrsim.mrsim_profile_reset(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, True)
+        mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+        torch.cuda.synchronize()
+        prof = {k: round(v[1], 3) for k, v in mrsim.mrsim_profile_get(ctx.h).items() if v[0]}
+        mrsim.mrsim_profile_enable(ctx.h, False)
+        return t, sig.cpu().numpy().view(np.complex128).copy(), prof
 
-    t_exact, s_exact = timed(mrsim.GROUPED)
+    t_exact, s_exact, k_exact = timed(mrsim.GROUPED)
     mrsim.mrsim_surrogate_use(ctx.h, sur)
-    t_sur, s_sur = timed(mrsim.SURROGATE)
+    t_sur, s_sur, k_sur = timed(mrsim.SURROGATE)
     run = mrsim.mrsim_surrogate_stats(sur, ctx.h)
     mrsim.mrsim_surrogate_use(ctx.h, None)
     n_served, n_exact = run["groups_served"], run["groups_exact"]
@@ -226,6 +234,11 @@ def surrogate_workload(ctx, mrsim, torch):
                      "served_max_error": st["val_served_max_err"], "bound": 1e-3},
            "grouping_s": round(group_s, 3), "exact_s": round(t_exact, 4),
            "surrogate_s": round(t_sur, 4), "speedup": round(t_exact / t_sur, 3),
+           "kernels_ms_exact": k_exact, "kernels_ms_surrogate": k_sur,
+           "preparation_ms": {"exact": k_exact.get("precompute_f32", 0.0),
+                              "surrogate": round(sum(k_sur.get(n, 0.0) for n in
+                                                     ("precompute_f32", "sur_gate",
+                                                      "sur_infer")), 3)},
            "groups_served_fraction": round(n_served / max(n_served + n_exact, 1), 4),
            "signal_rel_l2_vs_exact": float(np.linalg.norm(s_sur - s_exact) / np.linalg.norm(s_exact))}
     ctx.free("grp", hg)

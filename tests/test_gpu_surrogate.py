@@ -128,16 +128,26 @@ def test_surrogate_gain_over_exact_preparation(mrsim, ctx, trained):
         for _ in range(3):
             mrsim.mrsim_run(ctx.h, hp, hs2, hg, mode, mrsim.FP32, sig)
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / 3, sig.view(np.complex128).copy()
+        t = (time.perf_counter() - t0) / 3
+        # preparation-step kernels of one more run (CUDA events per launch)
+        mrsim.mrsim_profile_reset(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, True)
+        mrsim.mrsim_run(ctx.h, hp, hs2, hg, mode, mrsim.FP32, sig)
+        prof = mrsim.mrsim_profile_get(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, False)
+        prep = sum(v[1] for k, v in prof.items() if k in ("precompute_f32", "sur_gate", "sur_infer"))
+        return t, prep, sig.view(np.complex128).copy()
 
-    t_exact, s_exact = timed(mrsim.GROUPED)
+    t_exact, p_exact, s_exact = timed(mrsim.GROUPED)
     mrsim.mrsim_surrogate_use(ctx.h, sur)
-    t_sur, s_sur = timed(mrsim.SURROGATE)
+    t_sur, p_sur, s_sur = timed(mrsim.SURROGATE)
     st = mrsim.mrsim_surrogate_stats(sur, ctx.h)
     mrsim.mrsim_surrogate_use(ctx.h, None)
     served = st["groups_served"] / (st["groups_served"] + st["groups_exact"])
-    # the preparation step shrinks with the served fraction
     assert served > 0.1
-    print(f"exact {t_exact * 1e3:.1f} ms, surrogate {t_sur * 1e3:.1f} ms, served {served:.3f}")
+    print(f"exact {t_exact * 1e3:.1f} ms (preparation {p_exact:.1f} ms), surrogate "
+          f"{t_sur * 1e3:.1f} ms (preparation {p_sur:.1f} ms), served {served:.3f}")
+    # the preparation step shrinks with the served fraction, and so does the run
+    assert p_sur < p_exact, (p_sur, p_exact, served)
     assert t_sur < t_exact, (t_sur, t_exact, served)
     assert oracle.rel_l2(s_sur, s_exact) <= 1e-2
