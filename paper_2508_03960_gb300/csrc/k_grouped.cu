@@ -353,9 +353,12 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                     atomicAdd(&Ablk[o], vr);
                     atomicAdd(&Ablk[o + 1], vi);
                 }
-                acc[2 * t] = 0;
-                acc[2 * t + 1] = 0;
             }
+            // cleared even when the slot's total is zero: the staged partial
+            // of the non-uniform warps can cancel the per-warp sums exactly,
+            // and a value left here would be added into a later window
+            acc[2 * t] = 0;
+            acc[2 * t + 1] = 0;
         }
         __syncthreads();
         nb = 0;
