@@ -1,6 +1,7 @@
 // C ABI of libmrsim (declared in include/mrsim.h) and the host planner that
 // turns a classified sequence into kernel launches.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -406,6 +407,11 @@ struct GPlan {
     std::vector<Span> spans;
     std::vector<int4> blk;  // group-signal blocks (window, first sample, g0, g1)
     bool direct = false;    // factor table too large: advance fully per isochromat
+    std::vector<std::array<double, 3>> kd;  // per event: gamma_bar * moment per axis
+    bool ax = false;        // per-isochromat phasors from axis tables (FP32 only)
+    std::vector<AxItem> ax_items;
+    int64_t ax_n = 0;       // table entries of all events
+    int ax_max = 0;         // longest table
 };
 
 template <typename R>
@@ -459,6 +465,7 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         }
         e.op = ev_op(kind, mask, gtype);
         P.adv.push_back(EvAdv{p >= 1 ? k[p - 1] : 0.0, tau});
+        P.kd.push_back({k[0], k[1], k[2]});
         return e;
     };
     auto close_span = [&](int fallback) {
@@ -501,6 +508,25 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
     P.direct = (int64_t)P.ev.size() * P.Gp > (int64_t)1 << 26 || P.Gp * 4 > g->K;
     if (P.direct)
         for (auto &e : P.ev) e.prow = 0;
+    // FP32 factor-table runs take the per-isochromat phasor of every axis in an
+    // event's mask from a table over that axis' distinct positions
+    if constexpr (sizeof(R) == 4) {
+        if (!P.direct && g->ax_ok) {
+            for (size_t i = 0; i < P.ev.size(); ++i) {
+                const int mask = ev_mask(P.ev[i].op);
+                for (int a = 0; a < 3; ++a) {
+                    P.ev[i].q[a] = 0;
+                    if (!(mask & (1 << a))) continue;
+                    P.ev[i].q[a] = (int)P.ax_n;
+                    P.ax_items.push_back(AxItem{P.kd[i][a], g->ax_val[a].as<float>(),
+                                                (int)g->n_ax[a], 0, P.ax_n});
+                    P.ax_n += g->n_ax[a];
+                    P.ax_max = std::max<int>(P.ax_max, (int)g->n_ax[a]);
+                }
+            }
+            P.ax = P.ax_n <= ((int64_t)1 << 24);
+        }
+    }
     // 4) group-signal blocks: 256 samples x a slice of the groups
     if (!P.wins.empty()) {
         int64_t base_blocks = 0, max_g = 1;
@@ -601,6 +627,22 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
     FusedArgs<R> fa = fused_args<R>(g, P.p, M, M + Kp, M + 2 * Kp, T_tab, d_P, Ablk);
     fa.direct = P.direct ? 1 : 0;
+    if (P.ax) {
+        fa.ax = 1;
+        fa.aidx = g->ax_idx.as<int32_t>();
+        int n = 0;
+        for (int a = 0; a < 3; ++a) {
+            fa.ax_sh[a] = 0;
+            if (a != P.p - 1) fa.ax_sh[a] = 16 * n++;
+        }
+        if (!P.ax_items.empty()) {
+            float2 *qtab = (float2 *)scratch(c, 16, P.ax_n * sizeof(float2));
+            AxItem *d_items = (AxItem *)scratch(c, 17, P.ax_items.size() * sizeof(AxItem));
+            upload(c, d_items, P.ax_items.data(), P.ax_items.size() * sizeof(AxItem));
+            launch_axis_phase(c, d_items, (int)P.ax_items.size(), P.ax_max, qtab);
+            fa.qtab = qtab;
+        }
+    }
     const double z0[3] = {0.0, 0.0, 0.0};
     const A zero = AdvOf<R>::make(z0, 0.0);
     bool first = true;
@@ -868,6 +910,7 @@ int mrsim_create(mrsim_ctx **ctx, int device, void *cuda_stream) {
         }
         c->dev_err = dalloc(64);
         MRSIM_CUDA(cudaMemsetAsync(c->dev_err.p, 0, 64, c->stream));
+        prepare_fused(c);
     });
     if (rc) {
         delete c;
@@ -1009,6 +1052,7 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
             g->built[t] = true;
         }
         build_layout(c, ph, g.get());
+        build_axis_index(c, g.get());
     });
     if (rc == MRSIM_OK) *out = g.release();
     return rc;

@@ -65,7 +65,7 @@ struct ADCSegD {
 // store the state.
 template <typename R>
 struct FEvent;
-// 48-byte records; op = kind | mask << 2 | gtype << 5
+// 64-byte records (FP32), 48-byte (FP64); op = kind | mask << 2 | gtype << 5
 template <>
 struct FEvent<float> {
     int op;
@@ -75,6 +75,9 @@ struct FEvent<float> {
     // gamma_bar * moment per axis (cycles/m) and, in [3], the elapsed time (s),
     // split hi + lo; every axis is filled, `mask` marks the per-isochromat ones
     float k_hi[4], k_lo[4];
+    // axis-table runs: first entry of this event's phasor table exp(-i 2 pi v k_a)
+    // over the distinct positions v of axis a (only for the axes in `mask`)
+    int q[4];
 };
 template <>
 struct FEvent<double> {

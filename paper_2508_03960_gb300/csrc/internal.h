@@ -66,7 +66,7 @@ struct mrsim_ctx {
     std::vector<Pending> prof_pending;
     std::vector<cudaEvent_t> ev_pool;
     // growable scratch areas reused across calls
-    mrsim::DBuf scratch[16];
+    mrsim::DBuf scratch[18];
     // error word written by kernels with bounded waits / bounds checks
     mrsim::DBuf dev_err;
     // pinned host staging for uploads of per-run plans
@@ -143,6 +143,15 @@ struct mrsim_groups {
     mrsim::GroupTable tab[4];
     int primary = -1, secondary = -1;  // layout keys (gradient types)
     int64_t n_cells = 0;
+    // distinct positions of the two axes other than the primary one, numbered
+    // by first occurrence in layout order; ax_idx packs both indices per
+    // isochromat (lower axis in bits 0-15, higher axis in bits 16-31).
+    // ax_ok is false if there is no primary axis or an axis has more than
+    // kMaxAxisValues distinct positions.
+    bool ax_ok = false;
+    int64_t n_ax[3] = {0, 0, 0};
+    mrsim::DBuf ax_val[3];  // float [n_ax[a]]
+    mrsim::DBuf ax_idx;     // int32 [K], layout order
     mrsim::DBuf perm;  // int32 [K]: layout position -> phantom index
     mrsim::DBuf x, y, z, T1, T2, dB0, M0, b1, M_init;  // layout order
     bool has_b1 = false, has_M_init = false;
@@ -207,6 +216,8 @@ bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid,
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab);
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
+constexpr int64_t kMaxAxisValues = 65535;
+void build_axis_index(mrsim_ctx *c, mrsim_groups *g);
 
 // ---- plain path (k_plain.cu) ----
 struct PlainState {
@@ -263,7 +274,25 @@ struct FusedArgs {
     const void *P_raw;       // per-(event, primary group) advance factors, 4 R each
     double *Ablk;            // complex block sums (interleaved re, im)
     int direct;              // 1: no factor table, the whole advance per isochromat
+    // axis tables (FP32 factor-table runs): per-isochromat phasors are read
+    // from qtab at the event's offsets instead of being evaluated
+    int ax;                  // 1: use them
+    const int32_t *aidx;     // packed axis indices [K] (layout order)
+    const float2 *qtab;      // phasor tables of all events
+    int ax_sh[3];            // bit position of each axis' index in aidx
 };
+// one axis table: out[j] = exp(-i 2 pi val[j] k) for j < n (cos, sin)
+struct AxItem {
+    double k;      // gamma_bar * moment on the axis (cycles/m)
+    const float *val;
+    int n;
+    int pad;
+    int64_t off;   // first entry in the table array
+};
+void launch_axis_phase(mrsim_ctx *c, const AxItem *d_items, int n_items, int max_n,
+                       float2 *out);
+// shared-memory limits of the fused kernels on the context's device
+void prepare_fused(mrsim_ctx *c);
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni);
 template <typename R>

@@ -50,6 +50,19 @@ struct PhantomKey {
     }
 };
 
+// One position axis alone (float32 bit pattern, -0 folded to +0): numbers the
+// distinct positions of that axis for the per-axis phasor tables.
+struct AxisKey {
+    static constexpr int W = 1;
+    const float *pos;
+    __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
+        float v = pos[k];
+        if (v == 0.0f) v = 0.0f;
+        w[0] = __float_as_uint(v);
+        return !isnan(v);
+    }
+};
+
 // (gid_a, gid_b) pair key for the layout cells.
 struct PairKey {
     static constexpr int W = 2;
@@ -223,6 +236,20 @@ __global__ void k_cell_table(int64_t K, const int32_t *flag, const int32_t *rank
         oa[g] = ga[k];
         ob[g] = gb ? gb[k] : 0;
     }
+}
+
+// distinct values of one axis from its representatives
+__global__ void k_axis_values(int64_t K, const int32_t *flag, const int32_t *rank,
+                              const float *pos, float *val) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        if (flag[k]) val[rank[k]] = pos[k] == 0.0f ? 0.0f : pos[k];
+}
+
+__global__ void k_pack_axis(int64_t K, const int32_t *lo, const int32_t *hi, int32_t *out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (int32_t)((uint32_t)lo[k] | ((uint32_t)hi[k] << 16));
 }
 
 // warp-aggregated atomic add of 1 per element on counter[key]; returns the
@@ -470,6 +497,42 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
             K, perm, g->gid_orig[t].as<int32_t>(), g->gid_sorted[t].as<int32_t>());
     }
     sync(c);
+}
+
+// Distinct positions of the two non-primary axes (layout order) and the
+// packed per-isochromat indices into them.  Leaves g->ax_ok false when the
+// layout has no primary axis or an axis has too many distinct positions.
+void build_axis_index(mrsim_ctx *c, mrsim_groups *g) {
+    g->ax_ok = false;
+    const int p = g->primary;
+    if (p < G_X || p > G_Z) return;
+    const int64_t K = g->K;
+    const float *pos[3] = {g->x.as<float>(), g->y.as<float>(), g->z.as<float>()};
+    int ax[2], n = 0;
+    for (int a = 0; a < 3; ++a)
+        if (a != p - 1) ax[n++] = a;
+    DBuf idx[2];
+    for (int i = 0; i < 2; ++i) {
+        const int a = ax[i];
+        idx[i] = dalloc(K * sizeof(int32_t));
+        int32_t *flag, *rank;
+        const int64_t nv = hash_group(c, K, AxisKey{pos[a]}, idx[i].as<int32_t>(), &flag, &rank);
+        if (nv > kMaxAxisValues) return;
+        g->n_ax[a] = nv;
+        g->ax_val[a] = dalloc(nv * sizeof(float));
+        KScope ks(c, "axis_values");
+        k_axis_values<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, pos[a],
+                                                             g->ax_val[a].as<float>());
+    }
+    g->ax_idx = dalloc(K * sizeof(int32_t));
+    {
+        KScope ks(c, "axis_pack");
+        k_pack_axis<<<grid_for(c, K), 256, 0, c->stream>>>(K, idx[0].as<int32_t>(),
+                                                           idx[1].as<int32_t>(),
+                                                           g->ax_idx.as<int32_t>());
+    }
+    sync(c);
+    g->ax_ok = true;
 }
 
 }  // namespace mrsim

@@ -115,8 +115,15 @@ __device__ __forceinline__ R4<R> load4(const R4<R> *p) {
     }
 }
 
-constexpr int kBatch = 32;            // with-ADC windows per shared-memory flush
+constexpr int kBatch = 16;            // with-ADC windows per shared-memory flush
 constexpr int kAccBytes = 32 * 1024;  // block-sum staging per CTA
+
+// how the fused kernel advances an isochromat between events
+enum FusedMode : int {
+    FM_FACTOR = 0,  // group-factor table, per-isochromat phasor evaluated
+    FM_AXIS = 1,    // group-factor table, per-isochromat phasor from axis tables
+    FM_DIRECT = 2,  // every factor from the isochromat's own parameters
+};
 
 template <int MASK>
 __device__ __forceinline__ float iso_turns_m(const FEvent<float> &ev, float x, float y, float z) {
@@ -136,6 +143,31 @@ __device__ __forceinline__ double iso_turns_m(const FEvent<double> &ev, double x
     return t - rint(t);
 }
 
+// (cos, sin) of 2 pi sum_{a in MASK} r_a k_a from the event's axis tables:
+// entry j of axis a's table holds the phasor of that axis' j-th distinct
+// position; the factors of two axes multiply as unit complex numbers.
+template <int MASK>
+__device__ __forceinline__ void axis_phasor(const FEvent<float> &ev, const float2 *qtab,
+                                            const int (&sh)[3], int aidx, float &c, float &s) {
+    c = 1.0f;
+    s = 0.0f;
+    bool first = true;  // resolved at compile time after unrolling
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((MASK & (1 << a)) == 0) continue;
+        const float2 q = __ldg(qtab + ev.q[a] + ((aidx >> sh[a]) & 0xffff));
+        if (first) {
+            c = q.x;
+            s = q.y;
+            first = false;
+        } else {
+            const float nc = c * q.x - s * q.y;
+            s = s * q.x + c * q.y;
+            c = nc;
+        }
+    }
+}
+
 // Per-isochromat registers of the fused kernel.  Padding isochromats (past
 // K) carry zero magnetization and M0 and valid table rows, so every event
 // leaves them at zero and the event loop needs no validity tests.
@@ -145,6 +177,7 @@ struct Iso {
     R dB0[NI], r1[NI], r2[NI];  // direct mode only: dB0, log2(e)/T1, log2(e)/T2
     int pofs[NI];  // primary group (row offset in a group-factor table)
     int tofs[NI];  // 12 * RF group (offset in a combined-transition table)
+    int aidx[NI];  // axis mode only: packed axis indices
 };
 
 // whole advance of one isochromat from the event record (direct mode):
@@ -200,17 +233,32 @@ __device__ __forceinline__ void ev_adc_direct(const Iso<R, NI> &s, const FEvent<
     }
 }
 
-// advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1
-template <typename R, int NI, int MASK>
-__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt) {
+// per-isochromat phasor Q of the axes in MASK (factor-table modes)
+template <typename R, int NI, int MASK, int MODE>
+__device__ __forceinline__ void iso_q(const Iso<R, NI> &s, int i, const FEvent<R> &ev,
+                                      const float2 *qtab, const int (&sh)[3], R &c, R &sn) {
+    if constexpr (MODE == FM_AXIS) {
+        axis_phasor<MASK>(ev, qtab, sh, s.aidx[i], c, sn);
+    } else {
+        phasor(iso_turns_m<MASK>(ev, s.x[i], s.y[i], s.z[i]), c, sn);
+    }
+}
+
+// advance of every isochromat (Eqs. 4-5): M_xy <- P Q M_xy, Mz relaxes with E1.
+// A thread's isochromats are consecutive in the layout and mostly share their
+// primary group, so the factor row is re-read only where the group changes.
+template <typename R, int NI, int MASK, int MODE>
+__device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, const R4<R> *Pt,
+                                           const float2 *qtab, const int (&sh)[3]) {
     const R4<R> *Pe = Pt + ev.prow;
+    R4<R> P = load4(Pe + s.pofs[0]);
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const R4<R> P = load4(Pe + s.pofs[i]);
+        if (i > 0 && s.pofs[i] != s.pofs[i - 1]) P = load4(Pe + s.pofs[i]);
         R fr = P.x, fi = P.y;
         if constexpr (MASK != 0) {
             R c, sn;
-            phasor(iso_turns_m<MASK>(ev, s.x[i], s.y[i], s.z[i]), c, sn);
+            iso_q<R, NI, MASK, MODE>(s, i, ev, qtab, sh, c, sn);
             const R tr = fr * c + fi * sn;  // P * exp(-i psi)
             fi = fi * c - fr * sn;
             fr = tr;
@@ -223,8 +271,9 @@ __device__ __forceinline__ void ev_advance(Iso<R, NI> &s, const FEvent<R> &ev, c
 }
 
 // transverse magnetization of every isochromat times Q (ADC block-sum terms)
-template <typename R, int NI, int MASK>
-__device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R> &ev, R (&vr)[NI],
+template <typename R, int NI, int MASK, int MODE>
+__device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R> &ev,
+                                             const float2 *qtab, const int (&sh)[3], R (&vr)[NI],
                                              R (&vi)[NI]) {
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
@@ -232,7 +281,7 @@ __device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R
         vi[i] = s.my[i];
         if constexpr (MASK != 0) {
             R c, sn;
-            phasor(iso_turns_m<MASK>(ev, s.x[i], s.y[i], s.z[i]), c, sn);
+            iso_q<R, NI, MASK, MODE>(s, i, ev, qtab, sh, c, sn);
             const R tr = vr[i] * c + vi[i] * sn;
             vi[i] = vi[i] * c - vr[i] * sn;
             vr[i] = tr;
@@ -242,20 +291,25 @@ __device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R
 
 constexpr int kEvChunk = 128;  // events staged in shared memory at a time
 
+// Shared memory of one fused CTA (dynamic: larger than the static limit).
 template <typename R>
 struct FusedSmem {
     __align__(16) unsigned char acc_raw[kAccBytes];  // staged block sums [batch][slot][re, im]
     __align__(16) FEvent<R> sev[kEvChunk];           // staged events
+    // per-thread partial sums of warps whose isochromats share one group,
+    // [window][thread] (row padded by one entry: conflict-free column reads)
+    __align__(16) R tpart[kBatch][kThreads + 1][2];
+    R wpart[kBatch][kThreads / 32][2];  // their per-warp sums
     int batch_prow[kBatch], batch_win[kBatch];
-    R wpart[kBatch][kThreads / 32][2];  // sums of warps whose isochromats share one group
-    int wslot[kThreads / 32];           // that group's slot, or -1
+    int wslot[kThreads / 32];  // that group's slot, or -1
 };
 
 // One chunk of kThreads * NI isochromats (chunk index blk) through all events
 // of a span.  All threads of the CTA take part (shared memory, barriers).
-template <typename R, int NI, bool DIRECT>
+template <typename R, int NI, int MODE>
 __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                                             FusedSmem<R> &sm) {
+    constexpr bool DIRECT = MODE == FM_DIRECT;
     FEvent<R> *sev = sm.sev;
     int *batch_prow = sm.batch_prow, *batch_win = sm.batch_win;
     R *acc = reinterpret_cast<R *>(sm.acc_raw);  // [batch][slot][re, im]
@@ -267,6 +321,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     const int32_t *gr = a.gid[a.gtype_r];
     const R4<R> *Pt = reinterpret_cast<const R4<R> *>(a.P_raw);
     const R *Tt = a.T_tab;
+    const float2 *qtab = a.qtab;
+    const int sh[3] = {a.ax_sh[0], a.ax_sh[1], a.ax_sh[2]};
     double *Ablk = a.Ablk;
     const int32_t g_first = gp[base];
     const int32_t g_last = gp[last];
@@ -290,7 +346,12 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     for (int i = 0; i < NI; ++i) {
         const int64_t k = iso_k(i);
         if (k < a.K) {
-            s.x[i] = a.x[k]; s.y[i] = a.y[k]; s.z[i] = a.z[k]; s.M0[i] = a.M0[k];
+            if constexpr (MODE == FM_AXIS) {
+                s.aidx[i] = a.aidx[k];
+            } else {
+                s.x[i] = a.x[k]; s.y[i] = a.y[k]; s.z[i] = a.z[k];
+            }
+            s.M0[i] = a.M0[k];
             if (a.init_eq) {
                 s.mx[i] = 0; s.my[i] = 0; s.mz[i] = s.M0[i];
             } else {
@@ -306,6 +367,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             }
         } else {
             s.x[i] = s.y[i] = s.z[i] = s.M0[i] = 0;
+            s.aidx[i] = 0;
             s.mx[i] = s.my[i] = s.mz[i] = 0;
             key[i] = 0x7fffffff;
             s.tofs[i] = 0;
@@ -315,7 +377,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     }
     if (stage)
         for (int t = tid; t < B * S * 2; t += kThreads) acc[t] = 0;
-    // a warp whose isochromats all share one primary group reduces with plain shuffles
+    // a warp whose isochromats all share one primary group stages per-thread
+    // partial sums and reduces them at the flush
     const int32_t w0 = __shfl_sync(0xffffffffu, key[0], 0);
     bool uni = true;
 #pragma unroll
@@ -328,6 +391,27 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
 
     int nb = 0;  // windows staged (uniform)
     auto flush = [&]() {
+        if (warp_uni && stage) {
+            // column sums of this warp's staged partials: lane (h, b) adds
+            // the 16 threads of half h for window b, then the halves combine
+            __syncwarp();
+            const int b = lane & (kBatch - 1), h = lane >> 4;
+            R sr = 0, si = 0;
+            if (b < nb) {
+                const R(*col)[2] = &sm.tpart[b][warp * 32 + h * 16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    sr += col[j][0];
+                    si += col[j][1];
+                }
+            }
+            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
+            si += __shfl_xor_sync(0xffffffffu, si, 16);
+            if (h == 0 && b < nb) {
+                sm.wpart[b][warp][0] = sr;
+                sm.wpart[b][warp][1] = si;
+            }
+        }
         __syncthreads();
         for (int t = tid; t < nb * S; t += kThreads) {
             const int b = t / S, slot = t - b * S;
@@ -367,6 +451,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     auto rf_apply = [&](const FEvent<R> &ev, int gtype) {
         const int32_t *g = gtype == a.gtype_r ? nullptr : a.gid[gtype];
         const R *Te = Tt + (int64_t)ev.row * 12;
+        R T[12];
+        int prev = -1;
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
             int off = s.tofs[i];
@@ -374,8 +460,9 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 const int64_t k = iso_k(i);
                 off = k < a.K ? 12 * g[k] : 0;
             }
-            R T[12];
-            load_row(Te + off, T);
+            // consecutive isochromats of a thread mostly share their RF group
+            if (DIRECT || i == 0 || off != prev) load_row(Te + off, T);
+            prev = off;
             const R nx = T[0] * s.mx[i] + T[1] * s.my[i] + T[2] * s.mz[i] + T[3] * s.M0[i];
             const R ny = T[4] * s.mx[i] + T[5] * s.my[i] + T[6] * s.mz[i] + T[7] * s.M0[i];
             const R nz = T[8] * s.mx[i] + T[9] * s.my[i] + T[10] * s.mz[i] + T[11] * s.M0[i];
@@ -392,15 +479,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 R sr = 0, si = 0;
 #pragma unroll
                 for (int i = 0; i < NI; ++i) { sr += vr[i]; si += vi[i]; }
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, d);
-                    si += __shfl_xor_sync(0xffffffffu, si, d);
-                }
-                if (lane == 0) {  // no contention: summed over warps at the flush
-                    sm.wpart[nb][warp][0] = sr;
-                    sm.wpart[nb][warp][1] = si;
-                }
+                sm.tpart[nb][tid][0] = sr;
+                sm.tpart[nb][tid][1] = si;
             } else {
                 // keys are sorted along the lanes for each i: a segmented
                 // inclusive scan leaves each run's sum in the run's last lane
@@ -444,13 +524,13 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
         }
     };
 
-#define MRSIM_ADV_CASE(M)                       \
-    case M:                                     \
-        ev_advance<R, NI, M>(s, ev, Pt);        \
+#define MRSIM_ADV_CASE(M)                                   \
+    case M:                                                 \
+        ev_advance<R, NI, M, MODE>(s, ev, Pt, qtab, sh);    \
         break;
-#define MRSIM_ADC_CASE(M)                       \
-    case M:                                     \
-        ev_adc_terms<R, NI, M>(s, ev, vr, vi);  \
+#define MRSIM_ADC_CASE(M)                                      \
+    case M:                                                    \
+        ev_adc_terms<R, NI, M, MODE>(s, ev, qtab, sh, vr, vi); \
         break;
 
     for (int e0 = 0; e0 < a.n_ev; e0 += kEvChunk) {
@@ -509,11 +589,11 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     __syncthreads();
 }
 
-template <typename R, int NI, bool DIRECT>
+template <typename R, int NI, int MODE>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
     k_fused(FusedArgs<R> a) {
-    __shared__ FusedSmem<R> sm;
-    fused_chunk<R, NI, DIRECT>(a, blockIdx.x, sm);
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    fused_chunk<R, NI, MODE>(a, blockIdx.x, *reinterpret_cast<FusedSmem<R> *>(fused_smem));
 }
 
 // Persistent form for a batch of jobs: every CTA takes the next (job, chunk)
@@ -523,7 +603,8 @@ template <typename R, int NI>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
     k_fused_batch(const FusedArgs<R> *jobs, const int64_t *blk_off, int n_jobs,
                   unsigned long long *counter) {
-    __shared__ FusedSmem<R> sm;
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    FusedSmem<R> &sm = *reinterpret_cast<FusedSmem<R> *>(fused_smem);
     __shared__ FusedArgs<R> ja;
     __shared__ long long item, jblk;
     const int64_t total = blk_off[n_jobs];
@@ -542,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) :
         }
         __syncthreads();
         if (item >= total) break;
-        fused_chunk<R, NI, false>(ja, jblk, sm);
+        fused_chunk<R, NI, FM_FACTOR>(ja, jblk, sm);
     }
 }
 
@@ -662,24 +743,32 @@ void launch_event_table_batch(mrsim_ctx *c, const EvTabJob *d_jobs, const int64_
     k_event_table_batch<R><<<grid, 256, 0, c->stream>>>(d_jobs, d_off, n_jobs, total);
 }
 
+// The fused kernels take more shared memory than the static limit: every
+// instantiation gets the attribute on the context's device (prepare_fused).
+template <typename K>
+void fused_smem_attr(K kern, size_t bytes) {
+    MRSIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes));
+}
+
+template <typename R, int NI>
+void launch_fused_batch_ni(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
+                           int n_jobs, unsigned long long *d_counter) {
+    const size_t smem = sizeof(FusedSmem<R>);
+    int per_sm = 1;
+    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, NI>,
+                                                             kThreads, smem));
+    k_fused_batch<R, NI><<<std::max(1, per_sm) * c->sm_count, kThreads, smem, c->stream>>>(
+        d_jobs, d_blk_off, n_jobs, d_counter);
+}
+
 template <typename R>
 void launch_fused_batch(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
                         int n_jobs, unsigned long long *d_counter, int ni) {
     KScope ks(c, "fused_batch");
-    int per_sm = 1;
-    if (ni >= 4) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 4>, kThreads, 0);
-        k_fused_batch<R, 4><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
-            d_jobs, d_blk_off, n_jobs, d_counter);
-    } else if (ni == 2) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 2>, kThreads, 0);
-        k_fused_batch<R, 2><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
-            d_jobs, d_blk_off, n_jobs, d_counter);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, 1>, kThreads, 0);
-        k_fused_batch<R, 1><<<std::max(1, per_sm) * c->sm_count, kThreads, 0, c->stream>>>(
-            d_jobs, d_blk_off, n_jobs, d_counter);
-    }
+    if (ni >= 4) launch_fused_batch_ni<R, 4>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    else if (ni == 2) launch_fused_batch_ni<R, 2>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    else launch_fused_batch_ni<R, 1>(c, d_jobs, d_blk_off, n_jobs, d_counter);
 }
 
 template <typename R>
@@ -690,25 +779,83 @@ void launch_group_signal_batch(mrsim_ctx *c, const GSigJob<R> *d_jobs, const int
     k_group_signal_batch<R><<<n_blk, kThreads, 0, c->stream>>>(d_jobs, d_blk, d_blk_job);
 }
 
-template <typename R, bool DIRECT>
+template <typename R, int NI, int MODE>
+void launch_fused_ni(mrsim_ctx *c, const FusedArgs<R> &a) {
+    const size_t smem = sizeof(FusedSmem<R>);
+    const unsigned nb = (unsigned)((a.K + kThreads * NI - 1) / (kThreads * NI));
+    k_fused<R, NI, MODE><<<nb, kThreads, smem, c->stream>>>(a);
+}
+
+template <typename R, int MODE>
 void launch_fused_v(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
-    if (ni >= 4) {
-        const unsigned nb = (unsigned)((a.K + kThreads * 4 - 1) / (kThreads * 4));
-        k_fused<R, 4, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
-    } else if (ni == 2) {
-        const unsigned nb = (unsigned)((a.K + kThreads * 2 - 1) / (kThreads * 2));
-        k_fused<R, 2, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
-    } else {
-        const unsigned nb = (unsigned)((a.K + kThreads - 1) / kThreads);
-        k_fused<R, 1, DIRECT><<<nb, kThreads, 0, c->stream>>>(a);
-    }
+    if (ni >= 4) launch_fused_ni<R, 4, MODE>(c, a);
+    else if (ni == 2) launch_fused_ni<R, 2, MODE>(c, a);
+    else launch_fused_ni<R, 1, MODE>(c, a);
 }
 
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
     KScope ks(c, sizeof(R) == 4 ? "fused_grouped_f32" : "fused_grouped_f64");
-    if (a.direct) launch_fused_v<R, true>(c, a, ni);
-    else launch_fused_v<R, false>(c, a, ni);
+    if (a.direct) {
+        launch_fused_v<R, FM_DIRECT>(c, a, ni);
+    } else if constexpr (sizeof(R) == 4) {
+        if (a.ax) launch_fused_v<R, FM_AXIS>(c, a, ni);
+        else launch_fused_v<R, FM_FACTOR>(c, a, ni);
+    } else {
+        launch_fused_v<R, FM_FACTOR>(c, a, ni);
+    }
+}
+
+// one thread per (item, entry): exp(-i 2 pi val[j] k) with the phase reduced
+// modulo one turn in FP64 and the phasor evaluated in FP64, stored as float
+__global__ void k_axis_phase(const AxItem *items, int n_items, int max_n, float2 *out) {
+    const int64_t n = (int64_t)n_items * max_n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t it = i / max_n;
+        const int j = (int)(i - it * max_n);
+        const AxItem a = items[it];
+        if (j >= a.n) continue;
+        double t = (double)a.val[j] * a.k;
+        t -= rint(t);
+        double c, s;
+        sincospi(2.0 * t, &s, &c);
+        out[a.off + j] = make_float2((float)c, (float)s);
+    }
+}
+
+// shared-memory attribute of every fused kernel on the context's device
+// (set before any stream capture, which may not accept attribute changes)
+void prepare_fused(mrsim_ctx *) {
+    const size_t f = sizeof(FusedSmem<float>), d = sizeof(FusedSmem<double>);
+    fused_smem_attr(k_fused<float, 1, FM_FACTOR>, f);
+    fused_smem_attr(k_fused<float, 2, FM_FACTOR>, f);
+    fused_smem_attr(k_fused<float, 4, FM_FACTOR>, f);
+    fused_smem_attr(k_fused<float, 1, FM_AXIS>, f);
+    fused_smem_attr(k_fused<float, 2, FM_AXIS>, f);
+    fused_smem_attr(k_fused<float, 4, FM_AXIS>, f);
+    fused_smem_attr(k_fused<float, 1, FM_DIRECT>, f);
+    fused_smem_attr(k_fused<float, 2, FM_DIRECT>, f);
+    fused_smem_attr(k_fused<float, 4, FM_DIRECT>, f);
+    fused_smem_attr(k_fused<double, 1, FM_FACTOR>, d);
+    fused_smem_attr(k_fused<double, 2, FM_FACTOR>, d);
+    fused_smem_attr(k_fused<double, 4, FM_FACTOR>, d);
+    fused_smem_attr(k_fused<double, 1, FM_DIRECT>, d);
+    fused_smem_attr(k_fused<double, 2, FM_DIRECT>, d);
+    fused_smem_attr(k_fused<double, 4, FM_DIRECT>, d);
+    fused_smem_attr(k_fused_batch<float, 1>, f);
+    fused_smem_attr(k_fused_batch<float, 2>, f);
+    fused_smem_attr(k_fused_batch<float, 4>, f);
+}
+
+void launch_axis_phase(mrsim_ctx *c, const AxItem *d_items, int n_items, int max_n,
+                       float2 *out) {
+    if (n_items <= 0 || max_n <= 0) return;
+    KScope ks(c, "axis_phase");
+    const int64_t n = (int64_t)n_items * max_n;
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16));
+    k_axis_phase<<<grid, 256, 0, c->stream>>>(d_items, n_items, max_n, out);
 }
 
 template <typename R>
