@@ -195,6 +195,10 @@ def surrogate_workload(ctx, mrsim, torch):
     st = mrsim.mrsim_surrogate_stats(sur)
     ph = continuous_phantom(512, 512, 105, 8, seed=1005)
     hp = ctx.phantom(ph)
+    # launch parameters tuned on the FSE (945 pulse groups) do not carry over to
+    # 27.5M pulse groups: the preparation step uses its size heuristic here
+    lanes_tuned = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_LANES)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_LANES, 0)
     t0 = time.perf_counter()
     hg = ctx.group(hp, hs)
     group_s = time.perf_counter() - t0
@@ -244,6 +248,8 @@ def surrogate_workload(ctx, mrsim, torch):
     ctx.free("grp", hg)
     ctx.free("ph", hp)
     mrsim.mrsim_free_surrogate(sur)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_PRECOMP_LANES, lanes_tuned)
+    out["precompute_lanes"] = "size heuristic"
     return out
 
 
