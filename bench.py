@@ -298,6 +298,8 @@ def main():
                     help="fse_6m: the same sequences on a 256x256x105 phantom (profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="only the grouped FSE/EPI steps (for profiler launch lists)")
+    ap.add_argument("--tune", default="on", choices=["on", "off"],
+                    help="off: default launch parameters, no autotuner launches (profiling)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
 
@@ -356,7 +358,10 @@ def main():
 
     # autotuner: launch parameters picked by timing the grouped FSE run itself
     t0 = time.perf_counter()
-    tuned = mrsim.mrsim_autotune(ctx.h, hp, hs_f, hg_f, mrsim.GROUPED, mrsim.FP32, 2)
+    if a.tune == "on":
+        tuned = mrsim.mrsim_autotune(ctx.h, hp, hs_f, hg_f, mrsim.GROUPED, mrsim.FP32, 2)
+    else:
+        tuned = {p: mrsim.mrsim_get_tuning(ctx.h, p) for p in range(5)}
     autotune_s = time.perf_counter() - t0
 
     ns_f, ns_e = fse.n_samples, epi.n_samples

@@ -116,7 +116,7 @@ __device__ __forceinline__ R4<R> load4(const R4<R> *p) {
 }
 
 constexpr int kBatch = 16;            // with-ADC windows per shared-memory flush
-constexpr int kAccBytes = 32 * 1024;  // block-sum staging per CTA
+constexpr int kAccBytes = 16 * 1024;  // block-sum staging per CTA
 
 // how the fused kernel advances an isochromat between events
 enum FusedMode : int {
@@ -289,7 +289,7 @@ __device__ __forceinline__ void ev_adc_terms(const Iso<R, NI> &s, const FEvent<R
     }
 }
 
-constexpr int kEvChunk = 128;  // events staged in shared memory at a time
+constexpr int kEvChunk = 64;  // events staged in shared memory at a time
 
 // Shared memory of one fused CTA (dynamic: larger than the static limit).
 template <typename R>
@@ -589,8 +589,19 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
     __syncthreads();
 }
 
+// CTAs per SM each instantiation is compiled for: the most that keep it free
+// of register spills (the kernel is latency bound, so occupancy pays; the
+// shared memory of an FP32 CTA, about 54 KB, lets four share an SM)
 template <typename R, int NI, int MODE>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
+constexpr int fused_min_blocks() {
+    if (sizeof(R) == 8) return 1;
+    if (MODE == FM_AXIS) return 4;
+    if (MODE == FM_FACTOR) return NI == 4 ? 3 : 4;
+    return NI == 4 ? 2 : NI == 2 ? 3 : 4;
+}
+
+template <typename R, int NI, int MODE>
+__global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, MODE>()))
     k_fused(FusedArgs<R> a) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
     fused_chunk<R, NI, MODE>(a, blockIdx.x, *reinterpret_cast<FusedSmem<R> *>(fused_smem));
@@ -600,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) :
 // work item from a device counter until all chunks of all jobs are done, so
 // jobs of very different sizes share the GPU without a tail of idle SMs.
 template <typename R, int NI>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (NI <= 2 ? 3 : 2) : 1)
+__global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, FM_FACTOR>()))
     k_fused_batch(const FusedArgs<R> *jobs, const int64_t *blk_off, int n_jobs,
                   unsigned long long *counter) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
