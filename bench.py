@@ -244,6 +244,9 @@ def surrogate_workload(ctx, mrsim, torch):
                                                      ("precompute_f32", "sur_gate",
                                                       "sur_infer")), 3)},
            "groups_served_fraction": round(n_served / max(n_served + n_exact, 1), 4),
+           # the counters add up every run since mrsim_surrogate_use: timed() makes
+           # 1 + reps + 1 = 4 runs
+           "groups_served_per_run": int(n_served) // 4, "sur_infer_ms": k_sur.get("sur_infer"),
            "signal_rel_l2_vs_exact": float(np.linalg.norm(s_sur - s_exact) / np.linalg.norm(s_exact))}
     ctx.free("grp", hg)
     ctx.free("ph", hp)
@@ -274,6 +277,48 @@ def cpu_baseline(ph, seq, stride, threads=0):
     wall = time.perf_counter() - t0
     cores = threads if threads > 0 else os.cpu_count()
     return wall * ph.K / sub.K, wall, sub.K, cores
+
+
+def rf_runs(seq):
+    """With-RF subsequences of a sequence (maximal runs of segments with RF):
+    total sub-steps and segments over all of them, and sub-steps summed over
+    the distinct ones (exact equality of their segments)."""
+    rf = (seq.b1re != 0) | (seq.b1im != 0)
+    edges = np.flatnonzero(np.diff(np.concatenate([[0], rf.astype(np.int8), [0]])))
+    steps = segs = distinct_steps = 0
+    seen = set()
+    for b, e in zip(edges[0::2], edges[1::2]):
+        n = int(seq.repeat[b:e].astype(np.int64).sum())
+        steps += n
+        segs += int(e - b)
+        key = b"".join(np.ascontiguousarray(getattr(seq, f)[b:e]).tobytes()
+                       for f in ("dt", "repeat", "b1re", "b1im", "gx", "gy", "gz"))
+        if key not in seen:
+            seen.add(key)
+            distinct_steps += n
+    return steps, segs, distinct_steps
+
+
+# algorithmic work of the other kernels (flops, FMA = 2, sin / cos / exp = 1 each):
+#   plain step (App. A per sub-step): |phi|^2 5, series of sin(t)/t and
+#     (1-cos t)/t^2 16, two cross products 18, M += s q + c2 w 12, relaxation 7
+#     -> 58 per isochromat-step, plus the rotation vector 10 per isochromat-segment
+#   plain ADC (Eq. 6): phasor recurrence 6 + sum 2 -> 8 per isochromat-sample
+#   group signal (Eqs. 8, 10): phase 4, sin + cos + exp 3, complex rotate-scale-add 10
+#     -> 17 per (sample, group)
+#   preparation (Eq. 7, FP32 runs): U - I 40, FP32 block composition 72, FP64 fold
+#     every 8 steps ~9 -> ~120 per (group, sub-step)
+#   network inference, 128x128 layer on tensor cores (h1 as hi + lo BF16 halves):
+#     2 x 2 x 128 x 128 = 65,536 per served group
+FLOPS_PLAIN_STEP, FLOPS_PLAIN_SEG, FLOPS_PLAIN_SAMPLE = 58, 10, 8
+FLOPS_GSIG, FLOPS_PREP, FLOPS_SUR_INFER = 17, 120, 65536
+
+
+def roof_entry(name, flops, ms, peak, bound, unit_note):
+    ach = flops / (ms / 1e3) / 1e12
+    return {"kernel": name, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "algorithmic_flops": flops,
+            "ms": round(ms, 4), "work": unit_note}
 
 
 # algorithmic FP32 work of the fused kernel per isochromat and event (flops,
@@ -413,12 +458,18 @@ def main():
         return
 
     # ---- plain forms on the same GPU ----
-    def timed_once(fn):
+    def timed_once(fn, prof_out=None):
+        if prof_out is not None:
+            mrsim.mrsim_profile_reset(ctx.h)
+            mrsim.mrsim_profile_enable(ctx.h, True)
         barrier()
         e0.record(stream)
         fn()
         e1.record(stream)
         barrier()
+        if prof_out is not None:
+            prof_out.update(mrsim.mrsim_profile_get(ctx.h))
+            mrsim.mrsim_profile_enable(ctx.h, False)
         return maxr(e0.elapsed_time(e1) / 1e3)
 
     # plain kernels: tuned on the plain EPI run (the FSE run uses the same kernels)
@@ -427,13 +478,14 @@ def main():
     mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, fused_ni)
     tuned.update({k: v for k, v in tuned_plain.items() if k != mrsim.TUNE_FUSED_NI})
     step(hs_e, None, sig_e, mrsim.PLAIN)  # warm the plain kernels
-    epi_plain_s = timed_once(lambda: step(hs_e, None, sig_e, mrsim.PLAIN))
+    prof_epi_plain, prof_fse_plain = {}, {}
+    epi_plain_s = timed_once(lambda: step(hs_e, None, sig_e, mrsim.PLAIN), prof_epi_plain)
     epi_plain_sig = sig_e.cpu().numpy().view(np.complex128).copy()
     fse_plain_s = fse_plain_sig = None
     fse_cache_s = None
     if a.plain_fse == "on":
         fse_cache_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN_CACHE))
-        fse_plain_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN))
+        fse_plain_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN), prof_fse_plain)
         fse_plain_sig = sig_f.cpu().numpy().view(np.complex128).copy()
 
     # ---- end to end through the public API from pinned host buffers ----
@@ -463,6 +515,25 @@ def main():
     e1.record(stream)
     barrier()
     e2e_s = maxr(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / a.steps)
+    # where one end-to-end step goes (host clock, synchronised after each call)
+    split = {}
+
+    def lap(name, fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        split[name] = round((time.perf_counter() - t) * 1e3, 2)
+        return r
+
+    p_ = lap("phantom_upload", lambda: mrsim.mrsim_phantom(
+        ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0", "M0")]))
+    s_ = lap("sequence", lambda: ctx.sequence(fse))
+    g_ = lap("group", lambda: mrsim.mrsim_group(ctx.h, p_, s_))
+    lap("run_and_readback", lambda: mrsim.mrsim_run(ctx.h, p_, s_, g_, mrsim.GROUPED, mrsim.FP32,
+                                                    out_pin, None, 0))
+    lap("free", lambda: (mrsim.mrsim_free_groups(g_), ctx.free("seq", s_),
+                         mrsim.mrsim_free_phantom(p_)))
 
     # ---- batched workload: 64 uneven jobs in one graph launch ----
     batch = batch_workload(ctx, mrsim, torch, a.steps, a.warmup)
@@ -485,6 +556,43 @@ def main():
                                f"MEASURED_PEAKS.json ({pk_kind})",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": round(avg_s * 1e3, 4),
                 "launches": n_l}
+
+    # ---- achieved fraction of roofline of the other kernels ----
+    alu_peak = 2 * 128 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    bf16_peak = pk.get("bf16_tflops", 1900.0)
+    kroof = {}
+    f_steps, f_segs, f_distinct = rf_runs(fse)
+    gz_f = mrsim.mrsim_group_info(hg_f, mrsim.G_Z)[0]
+    if "precompute_f32" in prof:
+        n_l, ms_l = prof["precompute_f32"]
+        kroof["precompute_f32"] = roof_entry(
+            "k_precompute (FSE)", FLOPS_PREP * gz_f * f_distinct, ms_l / a.steps, alu_peak, "alu",
+            f"{FLOPS_PREP} flops x {gz_f} Gz groups x {f_distinct} sub-steps of the distinct pulses")
+    if "group_signal_f32" in prof:
+        n_l, ms_l = prof["group_signal_f32"]
+        gx_f = mrsim.mrsim_group_info(hg_f, mrsim.G_X)[0]
+        kroof["group_signal_f32"] = roof_entry(
+            "k_group_signal (FSE)", FLOPS_GSIG * ns_f * gx_f, ms_l / a.steps, alu_peak, "alu",
+            f"{FLOPS_GSIG} flops x {ns_f} samples x {gx_f} Gx groups")
+    for nm, pr, seq_, ns_ in (("fse", prof_fse_plain, fse, ns_f), ("epi", prof_epi_plain, epi, ns_e)):
+        steps_, segs_, _ = rf_runs(seq_)
+        if "plain_rf_f32" in pr:
+            kroof[f"plain_rf_{nm}"] = roof_entry(
+                f"k_plain_rf ({nm.upper()})",
+                ph.K * (FLOPS_PLAIN_STEP * steps_ + FLOPS_PLAIN_SEG * segs_), pr["plain_rf_f32"][1],
+                alu_peak, "alu", f"K x ({FLOPS_PLAIN_STEP} x {steps_} sub-steps + "
+                                 f"{FLOPS_PLAIN_SEG} x {segs_} segments)")
+        if "plain_adc_f32" in pr:
+            kroof[f"plain_adc_{nm}"] = roof_entry(
+                f"k_plain_adc ({nm.upper()})", ph.K * FLOPS_PLAIN_SAMPLE * ns_,
+                pr["plain_adc_f32"][1], alu_peak, "alu",
+                f"K x {FLOPS_PLAIN_SAMPLE} x {ns_} samples")
+    if surrogate.get("sur_infer_ms"):
+        kroof["sur_infer"] = roof_entry(
+            "k_sur_infer (27.5M surrogate FSE)", FLOPS_SUR_INFER * surrogate["groups_served_per_run"],
+            surrogate["sur_infer_ms"], bf16_peak, "tensor",
+            f"{FLOPS_SUR_INFER} tensor flops x {surrogate['groups_served_per_run']} served "
+            "(group, pulse) pairs per run (peak: measured cuBLAS bf16 burst)")
 
     # ---- parity against the stored oracle signals ----
     pd, sd_f, sd_e = phantom_digest(ph), sequence_digest(fse), sequence_digest(epi)
@@ -531,9 +639,9 @@ def main():
         "batch64": batch,
         "surrogate": surrogate,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "kernel_roofline": kroof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "split_ms": split},
         "gpu_launches": int(launches), "clocks": clocks,
     }
     ctx.close()
