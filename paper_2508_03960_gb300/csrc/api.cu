@@ -135,28 +135,38 @@ struct AdvOf<double> {
     static AdvD make(const double m[3], double t) { return make_adv_d(m, t); }
 };
 
-uint64_t seg_hash(const mrsim_seq *s, int64_t j, uint64_t h) {
-    auto mixin = [&](const void *p, size_t n) {
-        const unsigned char *b = (const unsigned char *)p;
-        for (size_t i = 0; i < n; ++i) {
-            h ^= b[i];
-            h *= 1099511628211ull;
-        }
+// Bucket key of the with-RF subsequence [b, e): its length and the bit
+// patterns of its first, middle and last segments.  It only picks candidate
+// contents, which are then compared in full (same_run).
+uint64_t run_key(const mrsim_seq *s, int64_t b, int64_t e) {
+    uint64_t h = 0x243f6a8885a308d3ull ^ (uint64_t)(e - b);
+    auto mix = [&](const void *p, size_t n) {
+        uint64_t v = 0;
+        std::memcpy(&v, p, n);
+        h = (h ^ v) * 0x9e3779b97f4a7c15ull;
+        h ^= h >> 29;
     };
-    mixin(&s->dt[j], 8);
-    mixin(&s->rep[j], 4);
-    mixin(&s->b1re[j], 4);
-    mixin(&s->b1im[j], 4);
-    mixin(&s->gx[j], 4);
-    mixin(&s->gy[j], 4);
-    mixin(&s->gz[j], 4);
+    for (int64_t j : {b, b + (e - b) / 2, e - 1}) {
+        mix(&s->dt[j], 8);
+        mix(&s->rep[j], 4);
+        mix(&s->b1re[j], 4);
+        mix(&s->b1im[j], 4);
+        mix(&s->gx[j], 4);
+        mix(&s->gy[j], 4);
+        mix(&s->gz[j], 4);
+    }
     return h;
 }
 
-bool same_seg(const mrsim_seq *s, int64_t a, int64_t b) {
-    return s->dt[a] == s->dt[b] && s->rep[a] == s->rep[b] && s->b1re[a] == s->b1re[b] &&
-           s->b1im[a] == s->b1im[b] && s->gx[a] == s->gx[b] && s->gy[a] == s->gy[b] &&
-           s->gz[a] == s->gz[b];
+// bitwise equality of the segments [a, a + n) and [b, b + n)
+bool same_run(const mrsim_seq *s, int64_t a, int64_t b, int64_t n) {
+    return std::memcmp(&s->dt[a], &s->dt[b], n * sizeof(double)) == 0 &&
+           std::memcmp(&s->rep[a], &s->rep[b], n * sizeof(int32_t)) == 0 &&
+           std::memcmp(&s->b1re[a], &s->b1re[b], n * sizeof(float)) == 0 &&
+           std::memcmp(&s->b1im[a], &s->b1im[b], n * sizeof(float)) == 0 &&
+           std::memcmp(&s->gx[a], &s->gx[b], n * sizeof(float)) == 0 &&
+           std::memcmp(&s->gy[a], &s->gy[b], n * sizeof(float)) == 0 &&
+           std::memcmp(&s->gz[a], &s->gz[b], n * sizeof(float)) == 0;
 }
 
 __global__ void k_validate(int64_t K, const float *x, const float *y, const float *z,
@@ -199,7 +209,6 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
     for (size_t i = 0; i < s->sub.size(); ++i) {
         Subseq &q = s->sub[i];
         bool ax = false, ay = false, az = false;
-        uint64_t h = 1469598103934665603ull;
         for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
             ax |= s->gx[j] != 0.0f;
             ay |= s->gy[j] != 0.0f;
@@ -210,22 +219,21 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
             q.mom[1] += (double)s->gy[j] * d;
             q.mom[2] += (double)s->gz[j] * d;
             if (s->adc[j]) q.n_samples += s->rep[j];
-            if (q.type == SUB_RF) h = seg_hash(s, j, h);
         }
         const int cnt = (int)ax + (int)ay + (int)az;
         q.gtype = cnt == 0 ? G_NONE : cnt > 1 ? G_GENERAL : ax ? G_X : ay ? G_Y : G_Z;
         q.sample0 = smp;
         smp += q.n_samples;
         if (q.type == SUB_RF) {
+            const uint64_t h = run_key(s, q.seg_begin, q.seg_end);
             const int64_t len = q.seg_end - q.seg_begin;
             int found = -1;
             for (int cid : by_hash[h]) {
                 const Subseq &r = s->sub[s->content_first[cid]];
-                if (r.seg_end - r.seg_begin != len) continue;
-                bool eq = true;
-                for (int64_t d = 0; d < len && eq; ++d)
-                    eq = same_seg(s, r.seg_begin + d, q.seg_begin + d);
-                if (eq) { found = cid; break; }
+                if (r.seg_end - r.seg_begin == len && same_run(s, r.seg_begin, q.seg_begin, len)) {
+                    found = cid;
+                    break;
+                }
             }
             if (found < 0) {
                 found = s->n_content++;

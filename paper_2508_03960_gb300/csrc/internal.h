@@ -93,7 +93,7 @@ struct Subseq {
     int type = SUB_RELAX, gtype = G_NONE;
     int64_t seg_begin = 0, seg_end = 0;
     int64_t n_samples = 0, sample0 = 0;
-    int content = -1;       // with-RF: content id (exact equality of segments)
+    int content = -1;       // with-RF: content id (bit equality of all segment fields)
     double dur = 0.0;       // seconds
     double mom[3] = {0, 0, 0};  // int G dt over the subsequence (T s / m)
 };
