@@ -345,6 +345,10 @@ def main():
                     help="only the grouped FSE/EPI steps (for profiler launch lists)")
     ap.add_argument("--tune", default="on", choices=["on", "off"],
                     help="off: default launch parameters, no autotuner launches (profiling)")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="one small run of each kernel besides the fused one, in this order: "
+                         "plain EPI, grouped FSE, surrogate FSE on a continuous phantom "
+                         "(for ncu captures; prints their CUDA-event times)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
 
@@ -353,6 +357,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from mrsim_inputs import configs, phantom_digest, sequence_digest
+
+    if a.profile_kernels:
+        profile_kernels(a, configs)
+        return
 
     if a.impl == "reference":
         if rank != 0:
@@ -649,6 +657,54 @@ def main():
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def profile_kernels(a, configs):
+    """Small runs of the kernels other than the fused one, each launched a few
+    times, for ncu captures: the plain step and ADC kernels (plain EPI on the
+    256x256x105 phantom), the preparation and group-signal kernels (grouped FSE
+    on it), and the surrogate gate and inference (a briefly trained network on
+    the 2 ms-pulse FSE, run on a 256x256x105 phantom with per-isochromat dB0 and
+    b1).  Prints the per-kernel CUDA-event times of one run of each."""
+    import torch
+    from paper_2508_03960_gb300 import mrsim
+    from mrsim_inputs.phantom import continuous_phantom
+    torch.cuda.set_device(0)
+    ctx = mrsim.Context(0, torch.cuda.current_stream().cuda_stream)
+    out = {}
+
+    def runs(hp, hs, hg, mode, ns, name, n=3):
+        sig = torch.zeros(2 * ns, dtype=torch.float64, device="cuda")
+        for i in range(n):
+            last = i == n - 1
+            if last:
+                mrsim.mrsim_profile_reset(ctx.h)
+                mrsim.mrsim_profile_enable(ctx.h, True)
+            mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+            torch.cuda.synchronize()
+        out[name] = {k: [v[0], round(v[1], 4)] for k, v in mrsim.mrsim_profile_get(ctx.h).items()
+                     if v[0]}
+        mrsim.mrsim_profile_enable(ctx.h, False)
+
+    ph = configs.small_phantom(256, 256, 105)
+    hp = ctx.phantom(ph)
+    epi, fse = configs.epi_sequence(), configs.fse_sequence()
+    hs_e, hs_f = ctx.sequence(epi), ctx.sequence(fse)
+    runs(hp, hs_e, None, mrsim.PLAIN, epi.n_samples, "plain_epi")
+    runs(hp, hs_f, ctx.group(hp, hs_f), mrsim.GROUPED, fse.n_samples, "grouped_fse")
+    _, seq = configs.surrogate_fse()
+    hs = ctx.sequence(seq)
+    sur = mrsim.mrsim_surrogate_train(ctx.h, hs, SUR_LO, SUR_HI, n_train=1 << 18, epochs=10,
+                                      batch=8192, lr=1e-2, seed=1005, bound=1e-3)
+    cph = continuous_phantom(256, 256, 105, 8, seed=1005)
+    hp2 = ctx.phantom(cph)
+    hg2 = ctx.group(hp2, hs)
+    mrsim.mrsim_surrogate_use(ctx.h, sur)
+    runs(hp2, hs, hg2, mrsim.SURROGATE, seq.n_samples, "surrogate_fse")
+    mrsim.mrsim_surrogate_use(ctx.h, None)
+    mrsim.mrsim_free_surrogate(sur)
+    ctx.close()
+    print(json.dumps({"profile_kernels": out, "K": ph.K}))
 
 
 def reference_arm(a, configs):

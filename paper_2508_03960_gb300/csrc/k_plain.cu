@@ -192,13 +192,35 @@ __global__ void __launch_bounds__(kThreads) k_plain_adc(PlainState s,
                                                         typename Seg<R>::Adv adv,
                                                         double *signal) {
     using ADS = typename Seg<R>::ADC;
+    // per-warp sums of each sample: added in R by lane 0 (accw) and folded into
+    // FP64 (acc) by the whole warp every kFoldChunks chunks.  A per-sample FP64
+    // add by one lane would keep the FP64 pipe, which this GPU has little of,
+    // busier than all the FP32 work of the recurrence.
     __shared__ double acc[kThreads / 32][kAdcBlockSamples][2];
+    __shared__ R accw[kThreads / 32][sizeof(R) == 4 ? kAdcBlockSamples : 1][2];
+    constexpr int kFoldChunks = 8;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t s_lo = (int64_t)blockIdx.y * kAdcBlockSamples;
     const int64_t s_hi = min(s_lo + kAdcBlockSamples, n_samples);
     for (int t = threadIdx.x; t < kAdcBlockSamples; t += kThreads)
         for (int w = 0; w < kThreads / 32; ++w) acc[w][t][0] = acc[w][t][1] = 0.0;
+    if constexpr (sizeof(R) == 4)
+        for (int t = threadIdx.x; t < kAdcBlockSamples; t += kThreads)
+            for (int w = 0; w < kThreads / 32; ++w) accw[w][t][0] = accw[w][t][1] = 0.0f;
     __syncthreads();
+    auto fold = [&]() {
+        if constexpr (sizeof(R) == 4) {
+            __syncwarp();
+            for (int t = lane; t < (int)(s_hi - s_lo); t += 32) {
+                acc[wid][t][0] += (double)accw[wid][t][0];
+                acc[wid][t][1] += (double)accw[wid][t][1];
+                accw[wid][t][0] = 0.0f;
+                accw[wid][t][1] = 0.0f;
+            }
+            __syncwarp();
+        }
+    };
+    int since_fold = 0;
     const R *Mx = (const R *)s.Mx, *My = (const R *)s.My;
     const int64_t chunk = (int64_t)kThreads * NI;
     const int64_t n_chunks = (s.K + chunk - 1) / chunk;
@@ -253,8 +275,13 @@ __global__ void __launch_bounds__(kThreads) k_plain_adc(PlainState s,
                         vr = warp_sum(vr);
                         vi = warp_sum(vi);
                         if (lane == 0) {
-                            acc[wid][smp - s_lo][0] += (double)vr;
-                            acc[wid][smp - s_lo][1] += (double)vi;
+                            if constexpr (sizeof(R) == 4) {
+                                accw[wid][smp - s_lo][0] += vr;
+                                accw[wid][smp - s_lo][1] += vi;
+                            } else {
+                                acc[wid][smp - s_lo][0] += (double)vr;
+                                acc[wid][smp - s_lo][1] += (double)vi;
+                            }
                         }
                     }
                 }
@@ -262,7 +289,12 @@ __global__ void __launch_bounds__(kThreads) k_plain_adc(PlainState s,
                 for (int i = 0; i < NI; ++i) cmul(ar[i], ai[i], zbr[i], zbi[i]);
             }
         }
+        if (++since_fold == kFoldChunks) {
+            fold();
+            since_fold = 0;
+        }
     }
+    fold();
     __syncthreads();
     for (int t = threadIdx.x; t < (int)(s_hi - s_lo); t += kThreads) {
         double sr = 0, si = 0;
