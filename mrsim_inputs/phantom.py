@@ -29,6 +29,9 @@ class Phantom:
     (shape [3, K], initial magnetization) are optional; when absent the RF
     scale is 1 and the initial state is thermal equilibrium (0, 0, M0).
     ``labels`` (int32, region id per isochromat) is informational.
+    ``coils`` (shape [P, 2, K]: real and imaginary part of each receive coil's
+    sensitivity S(k, p) at every isochromat) is optional; without it the
+    signal is received by one coil with S = 1 (Eq. 6).
     """
 
     x: np.ndarray
@@ -42,6 +45,7 @@ class Phantom:
     M_init: Optional[np.ndarray] = None
     labels: Optional[np.ndarray] = None
     shape: tuple = ()
+    coils: Optional[np.ndarray] = None
 
     @property
     def K(self) -> int:
@@ -58,7 +62,7 @@ class Phantom:
                        T1=pick(self.T1), T2=pick(self.T2), dB0=pick(self.dB0),
                        M0=pick(self.M0), b1=pick(self.b1),
                        M_init=pick(self.M_init), labels=pick(self.labels),
-                       shape=(len(idx),))
+                       shape=(len(idx),), coils=pick(self.coils))
 
 
 def phantom_digest(p: Phantom) -> str:
@@ -70,6 +74,9 @@ def phantom_digest(p: Phantom) -> str:
             h.update(b"none")
         else:
             h.update(np.ascontiguousarray(a).tobytes())
+    if p.coils is not None:
+        h.update(b"coils")
+        h.update(np.ascontiguousarray(p.coils).tobytes())
     return h.hexdigest()
 
 
@@ -190,3 +197,38 @@ def continuous_phantom(nx: int, ny: int, nz: int, n_ellipses: int, seed: int,
     p.b1 = np.ascontiguousarray(rng.uniform(b1_range[0], b1_range[1], size=p.K),
                                 dtype=np.float32)
     return p
+
+
+def coil_maps(p: Phantom, n_coils: int, seed: int, fov: float = 0.256) -> np.ndarray:
+    """Smooth complex receive sensitivities of n_coils coils around the field of
+    view (float32 [n_coils, 2, K]).  Coil c sits at radius 0.6 fov in direction
+    2 atan(t_c), t_c spread evenly over [-2.5, 2.5] (+ a seeded jitter of the
+    position); its magnitude falls off as
+    1 / (1 + d^2 / w^2) with the distance d to the coil (w = 0.3 fov), and its
+    phase is a seeded constant plus a linear ramp along x.  Cosines and sines
+    come from rational parametrisations, so the maps are the same on every
+    platform."""
+    rng = np.random.default_rng(seed)
+    K = p.K
+    x = p.x.astype(np.float64)
+    y = p.y.astype(np.float64)
+    out = np.zeros((n_coils, 2, K), np.float32)
+    w2 = (0.3 * fov) ** 2
+
+    def unit(t):  # (cos, sin) of the angle 2 atan(t)
+        d = 1.0 + t * t
+        return (1.0 - t * t) / d, 2.0 * t / d
+
+    for c in range(n_coils):
+        # direction of coil c: (cos, sin) of 2 atan(t) for t spread over [-2.5, 2.5]
+        # (angles within about +-136 degrees around +x)
+        ca, sa = unit(2.5 * (2.0 * (c + 0.5) / n_coils - 1.0))
+        jit = rng.uniform(-0.05, 0.05, 2) * fov
+        cx, cy = 0.6 * fov * ca + jit[0], 0.6 * fov * sa + jit[1]
+        mag = 1.0 / (1.0 + ((x - cx) ** 2 + (y - cy) ** 2) / w2)
+        t0 = rng.uniform(-1.0, 1.0)
+        ramp = rng.uniform(-2.0, 2.0) * x / fov
+        cr, ci = unit(t0 + ramp)
+        out[c, 0] = (mag * cr).astype(np.float32)
+        out[c, 1] = (mag * ci).astype(np.float32)
+    return out

@@ -47,7 +47,7 @@ def _load():
             I = ctypes.c_int
             lib.or_classify.argtypes = [P] * 8 + [I64, I64] + [P] * 7
             lib.or_group.argtypes = [I64] + [P] * 7 + [I, P, P]
-            lib.or_simulate.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [I, I, I, P, P]
+            lib.or_simulate.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [I, I, I, I, P, P, P]
             lib.or_simulate_grouped.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [P, P]
             lib.or_transition.argtypes = [ctypes.c_double] * 7 + [P] * 7 + [I64, I64, P]
             for f in (lib.or_classify, lib.or_group, lib.or_simulate, lib.or_simulate_grouped,
@@ -120,20 +120,26 @@ def _ph_args(ph):
 
 def simulate(ph, seq, memo: bool = False, adc_recurrence: bool = False,
              n_threads: int = 0, want_M: bool = True):
-    """Ungrouped FP64 simulation.  Returns (signal complex128 [n_samples],
-    M_final float64 [3, K] or None)."""
+    """Ungrouped FP64 simulation.  Returns (signal, M_final float64 [3, K] or
+    None); the signal is complex128 [n_samples], or [P, n_samples] when the
+    phantom carries P receive-coil sensitivities (``ph.coils``)."""
     lib = _load()
     arrs = _ph_args(ph)
     sargs = [np.ascontiguousarray(seq.dt, np.float64), np.ascontiguousarray(seq.repeat, np.int32),
              _f32(seq.b1re), _f32(seq.b1im), _f32(seq.gx), _f32(seq.gy), _f32(seq.gz),
              np.ascontiguousarray(seq.adc, np.uint8)]
     ns = seq.n_samples
-    sig = np.zeros(2 * ns + 1, np.float64)
+    coils = getattr(ph, "coils", None)
+    P = 1 if coils is None else int(coils.shape[0])
+    sens = None if coils is None else np.ascontiguousarray(coils, np.float32).reshape(P, 2, ph.K)
+    sig = np.zeros(2 * ns * P + 1, np.float64)
     M = np.zeros((3, ph.K), np.float64) if want_M else None
     rc = lib.or_simulate(ph.K, *[_p(a) for a in arrs], seq.n_seg, *[_p(a) for a in sargs],
-                         int(memo), int(adc_recurrence), int(n_threads), _p(sig), _p(M))
+                         int(memo), int(adc_recurrence), int(n_threads), P, _p(sens), _p(sig),
+                         _p(M))
     _check(rc, "or_simulate")
-    return sig[: 2 * ns].view(np.complex128).copy(), M
+    out = sig[: 2 * ns * P].view(np.complex128).copy()
+    return (out if coils is None else out.reshape(P, ns)), M
 
 
 def simulate_grouped(ph, seq, want_M: bool = True):

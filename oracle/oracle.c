@@ -12,7 +12,9 @@
  *   - Eq. 2-3 piecewise-constant field, step transitions U composed in time
  *             order; U = D R (App. A: rotate by Eq. A2, then relax by Eq. A1).
  *   - Eq. 4-5 closed-form free precession / relaxation when B1 = 0.
- *   - Eq. 6   received signal A(t) = sum_k M_xy(k,t), one coil, S = 1.
+ *   - Eq. 6   received signal A(p, t) = sum_k S(k, p) M_xy(k, t) for every
+ *             receive coil p (one coil with S = 1 unless sensitivities are
+ *             given; S is complex and constant in time).
  *   - Eq. 7   combined transition of a with-RF subsequence (memoised per
  *             isochromat when the same RF content repeats: the "dynamic
  *             caching" of the conventional method, Sec. 2.2).
@@ -63,6 +65,8 @@ typedef struct {
     const float *x, *y, *z, *T1, *T2, *dB0, *M0;
     const float *b1;    /* NULL => 1 */
     const float *Minit; /* [3][K] or NULL => (0, 0, M0) */
+    int n_coils;        /* receive coils (>= 1) */
+    const float *sens;  /* [n_coils][2][K] (re, im of S(k, p)) or NULL => S = 1 */
 } or_phantom;
 
 typedef struct {
@@ -389,6 +393,24 @@ typedef struct {
     int rc;
 } or_job;
 
+/* Eq. 6: isochromat k's term of sample smp, weighted by every coil's S(k, p);
+ * the signal of coil p occupies [2 n_samples p, 2 n_samples (p + 1)). */
+static void add_sample(const or_job *J, int64_t k, int64_t smp, double mx, double my) {
+    const or_phantom *ph = J->ph;
+    if (!ph->sens) {
+        J->sig[2 * smp] += mx;
+        J->sig[2 * smp + 1] += my;
+        return;
+    }
+    for (int c = 0; c < ph->n_coils; ++c) {
+        const double sr = ph->sens[(2 * (int64_t)c) * ph->K + k];
+        const double si = ph->sens[(2 * (int64_t)c + 1) * ph->K + k];
+        double *o = J->sig + 2 * J->n_samples * c + 2 * smp;
+        o[0] += sr * mx - si * my;
+        o[1] += sr * my + si * mx;
+    }
+}
+
 static void simulate_one(const or_job *J, int64_t k, double (*memo)[3][4], char *have) {
     const or_seq *s = J->s;
     const or_subseqs *q = J->q;
@@ -430,8 +452,7 @@ static void simulate_one(const or_job *J, int64_t k, double (*memo)[3][4], char 
                     for (int32_t r = 0; r < rep; ++r) {
                         double nx = mx * zr - my * zi, ny = mx * zi + my * zr;
                         mx = nx; my = ny;
-                        J->sig[2 * smp] += mx;
-                        J->sig[2 * smp + 1] += my;
+                        add_sample(J, k, smp, mx, my);
                         ++smp;
                     }
                     /* M_xy from one closed-form step over the whole segment, Mz likewise */
@@ -439,8 +460,7 @@ static void simulate_one(const or_job *J, int64_t k, double (*memo)[3][4], char 
                 } else {
                     for (int32_t r = 0; r < rep; ++r) {
                         free_precess(M, &p, s->gx[j], s->gy[j], s->gz[j], dt);
-                        J->sig[2 * smp] += M[0];
-                        J->sig[2 * smp + 1] += M[1];
+                        add_sample(J, k, smp, M[0], M[1]);
                         ++smp;
                     }
                 }
@@ -487,18 +507,24 @@ static int check_phantom(const or_phantom *ph) {
             !isfinite(ph->dB0[k]) || !isfinite(ph->M0[k]) || (ph->b1 && !isfinite(ph->b1[k])))
             return OR_EINVAL;
     }
+    if (ph->n_coils < 1) return OR_EINVAL;
+    if (ph->sens)
+        for (int64_t i = 0; i < 2 * (int64_t)ph->n_coils * ph->K; ++i)
+            if (!isfinite(ph->sens[i])) return OR_EINVAL;
     return OR_OK;
 }
 
-/* Ungrouped FP64 simulation.  signal: [2 * n_samples] interleaved (re, im);
- * Mfinal: [3][K] or NULL.  Returns 0 or a negative error code. */
+/* Ungrouped FP64 simulation.  signal: [n_coils][2 * n_samples] interleaved
+ * (re, im); sens: [n_coils][2][K] or NULL (one coil, S = 1; n_coils must then
+ * be 1); Mfinal: [3][K] or NULL.  Returns 0 or a negative error code. */
 int or_simulate(int64_t K, const float *x, const float *y, const float *z, const float *T1,
                 const float *T2, const float *dB0, const float *M0, const float *b1,
                 const float *Minit, int64_t n_seg, const double *dt, const int32_t *rep,
                 const float *b1re, const float *b1im, const float *gx, const float *gy,
                 const float *gz, const uint8_t *adc, int memo, int adc_recurrence,
-                int n_threads, double *signal, double *Mfinal) {
-    or_phantom ph = {K, x, y, z, T1, T2, dB0, M0, b1, Minit};
+                int n_threads, int n_coils, const float *sens, double *signal, double *Mfinal) {
+    or_phantom ph = {K, x, y, z, T1, T2, dB0, M0, b1, Minit, n_coils, sens};
+    if (!sens && n_coils != 1) return OR_EINVAL;
     or_seq s = {n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc};
     or_opts o = {memo, adc_recurrence, n_threads};
     int rc = check_phantom(&ph);
@@ -511,11 +537,12 @@ int or_simulate(int64_t K, const float *x, const float *y, const float *z, const
     int nt = n_threads_for(&o, K);
     or_job *jobs = calloc(nt, sizeof(or_job));
     pthread_t *th = calloc(nt, sizeof(pthread_t));
-    double *part = calloc((size_t)nt * (size_t)(2 * ns + 1), sizeof(double));
+    const int64_t nsig = 2 * ns * (int64_t)n_coils; /* signal doubles of all coils */
+    double *part = calloc((size_t)nt * (size_t)(nsig + 1), sizeof(double));
     if (!jobs || !th || !part) { free(jobs); free(th); free(part); free_subseqs(&q); return OR_ENOMEM; }
     for (int t = 0; t < nt; ++t) {
         jobs[t] = (or_job){&ph, &s, &q, &o, K * t / nt, K * (t + 1) / nt, ns,
-                           part + (size_t)t * (size_t)(2 * ns + 1), Mfinal, 0};
+                           part + (size_t)t * (size_t)(nsig + 1), Mfinal, 0};
         if (pthread_create(&th[t], NULL, simulate_range, &jobs[t]) != 0) {
             jobs[t].rc = OR_ENOMEM;
             simulate_range(&jobs[t]);
@@ -527,9 +554,9 @@ int or_simulate(int64_t K, const float *x, const float *y, const float *z, const
         if (jobs[t].rc) rc = jobs[t].rc;
     }
     /* combine per-thread partial signals in thread order (deterministic) */
-    for (int64_t i = 0; i < 2 * ns; ++i) {
+    for (int64_t i = 0; i < nsig; ++i) {
         double acc = 0.0;
-        for (int t = 0; t < nt; ++t) acc += part[(size_t)t * (size_t)(2 * ns + 1) + i];
+        for (int t = 0; t < nt; ++t) acc += part[(size_t)t * (size_t)(nsig + 1) + i];
         signal[i] = acc;
     }
     free(jobs); free(th); free(part); free_subseqs(&q);
@@ -562,7 +589,7 @@ int or_simulate_grouped(int64_t K, const float *x, const float *y, const float *
                         const int32_t *rep, const float *b1re, const float *b1im,
                         const float *gx, const float *gy, const float *gz, const uint8_t *adc,
                         double *signal, double *Mfinal) {
-    or_phantom ph = {K, x, y, z, T1, T2, dB0, M0, b1, Minit};
+    or_phantom ph = {K, x, y, z, T1, T2, dB0, M0, b1, Minit, 1, NULL};
     or_seq s = {n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc};
     int rc = check_phantom(&ph);
     if (rc) return rc;

@@ -513,3 +513,68 @@ def test_thread_count_does_not_change_result_beyond_rounding():
     s3, M3 = oracle.simulate(ph, seq, n_threads=3)
     assert oracle.rel_l2(s3, s1) < 1e-14
     assert np.array_equal(M1, M3)
+
+
+# ---------------------------------------------------------------- P13 coils
+# Eq. 6 with P receive coils: A(p, t) = sum_k S(k, p) M_xy(k, t), S complex and
+# constant in time.  Pinned by (a) a constant complex sensitivity, which must
+# scale the one-coil signal by exactly that complex number (a dropped or
+# conjugated term fails), (b) linearity in S, (c) an indicator map, which must
+# reproduce the one-coil signal of the selected isochromats alone (weighting by
+# the wrong isochromat or coil fails).
+
+def _coil_case():
+    from mrsim_inputs.sequence import spin_echo_2d
+    ph = configs.small_phantom(8, 8, 2)
+    seq = spin_echo_2d(n_ro=8, n_pe=8, n_tr=2)
+    return ph, seq
+
+
+def _with_coils(ph, S):
+    import dataclasses
+    return dataclasses.replace(ph, coils=np.ascontiguousarray(S, np.float32))
+
+
+def test_p13_constant_coil_scales_signal():
+    ph, seq = _coil_case()
+    ref, _ = oracle.simulate(ph, seq, want_M=False)
+    s0 = np.array([0.75 + 0.5j, -0.25 + 1.0j])
+    S = np.zeros((2, 2, ph.K), np.float32)
+    S[:, 0] = s0.real[:, None]
+    S[:, 1] = s0.imag[:, None]
+    sig, _ = oracle.simulate(_with_coils(ph, S), seq, want_M=False)
+    assert sig.shape == (2, seq.n_samples)
+    for p in range(2):
+        assert oracle.rel_l2(sig[p], s0[p] * ref) <= 1e-14
+
+
+def test_p13_signal_is_linear_in_sensitivity():
+    from mrsim_inputs import coil_maps
+    ph, seq = _coil_case()
+    # multiples of 2^-12: the sum map S1 + S2 is then exact in float32
+    S = np.round(coil_maps(ph, 2, seed=31).astype(np.float64) * 4096.0) / 4096.0
+    S3 = np.concatenate([S, (S[0] + S[1])[None]], axis=0)
+    sig, _ = oracle.simulate(_with_coils(ph, S3), seq, want_M=False)
+    assert oracle.rel_l2(sig[2], sig[0] + sig[1]) <= 1e-12
+
+
+def test_p13_indicator_coil_selects_isochromats():
+    ph, seq = _coil_case()
+    rng = np.random.default_rng(5)
+    sel = np.sort(rng.choice(ph.K, ph.K // 3, replace=False))
+    S = np.zeros((2, 2, ph.K), np.float32)
+    S[0, 0, sel] = 1.0                 # coil 0: the selected isochromats
+    S[1, 1, :] = 1.0                   # coil 1: S = i everywhere
+    sig, _ = oracle.simulate(_with_coils(ph, S), seq, want_M=False)
+    sub, _ = oracle.simulate(ph.subset(sel), seq, want_M=False)
+    full, _ = oracle.simulate(ph, seq, want_M=False)
+    assert oracle.rel_l2(sig[0], sub) <= 1e-12
+    assert oracle.rel_l2(sig[1], 1j * full) <= 1e-14
+
+
+def test_p13_bad_sensitivities_are_rejected():
+    ph, seq = _coil_case()
+    S = np.ones((1, 2, ph.K), np.float32)
+    S[0, 1, 3] = np.nan
+    with pytest.raises(RuntimeError):
+        oracle.simulate(_with_coils(ph, S), seq, want_M=False)
