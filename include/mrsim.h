@@ -107,6 +107,20 @@ int mrsim_phantom(mrsim_ctx *ctx, int64_t K, const float *x, const float *y, con
                   const float *b1_scale, const float *M_init, unsigned flags,
                   mrsim_phantom_t **out);
 
+/* Attach the complex receive sensitivities of n_coils coils to a phantom
+ * (Eq. 6: A(p, t) = sum_k S(k, p) M_xy(k, t); S constant in time).  sens:
+ * float32 [n_coils][2][K]: for coil p, K real parts then K imaginary parts, in
+ * the phantom's isochromat order.  n_coils = 0 detaches them (one coil with
+ * S = 1, the default).  flags: MRSIM_PTR_DEVICE if sens is a device pointer.
+ * The data are copied.  With P >= 1 coils attached, mrsim_run returns one
+ * signal per coil (see there); grouped runs make one pass of the fused kernel
+ * per coil (Eq. 9 block sums per (group, coil)) after one preparation step.
+ * Errors: MRSIM_EINVAL (n_coils outside [0, MRSIM_MAX_COILS], sens NULL with
+ * n_coils > 0, non-finite value), MRSIM_ENOMEM, MRSIM_ECUDA. */
+#define MRSIM_MAX_COILS 64
+int mrsim_coils(mrsim_ctx *ctx, mrsim_phantom_t *ph, int n_coils, const float *sens,
+                unsigned flags);
+
 /* Describe a pulse sequence as n_seg run-length segments (Sec. 2.1: B(t) is
  * piecewise constant).  Segment j holds repeat[j] >= 1 sub-steps of dt_s[j]
  * > 0 seconds with constant RF b1_re_T + i b1_im_T (tesla), gradient
@@ -151,8 +165,9 @@ int mrsim_group_info(const mrsim_groups *groups, int gtype, int64_t *n_groups, i
  * groups: required for MRSIM_GROUPED / MRSIM_SURROGATE (NULL => error),
  * ignored otherwise.  mode: MRSIM_PLAIN, MRSIM_PLAIN_CACHE, MRSIM_GROUPED,
  * MRSIM_SURROGATE.  precision: MRSIM_FP32 or MRSIM_FP64 for the
- * per-isochromat arithmetic.  signal: [2 * n_samples_total] doubles,
- * interleaved (re, im), in time order.  M_final: [3][K] float32 final
+ * per-isochromat arithmetic.  signal: [P][2 * n_samples_total] doubles,
+ * interleaved (re, im), in time order, one block per receive coil (P = the
+ * phantom's coil count from mrsim_coils, 1 without coils).  M_final: [3][K] float32 final
  * magnetization in the phantom's order, or NULL.  out_flags:
  * MRSIM_OUT_DEVICE if signal / M_final are device pointers.
  * Errors: MRSIM_EINVAL, MRSIM_ESTATE (groups built for another phantom or
@@ -166,6 +181,8 @@ int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
  * signal sums).  groups[i] must come from mrsim_group(ph[i], seq[i]).
  * signals[i]: host [2 * n_samples_total(seq[i])] doubles.
  * Errors: MRSIM_EINVAL, MRSIM_ESTATE, MRSIM_ENOMEM, MRSIM_ECUDA,
+ * MRSIM_EUNSUPPORTED (a phantom with receive coils attached, a job that
+ * needs a plain fallback or starts from a given M_init),
  * MRSIM_ETIMEOUT (a bounded device wait gave up). */
 int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph,
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,

@@ -169,6 +169,12 @@ bool same_run(const mrsim_seq *s, int64_t a, int64_t b, int64_t n) {
            std::memcmp(&s->gz[a], &s->gz[b], n * sizeof(float)) == 0;
 }
 
+__global__ void k_finite(int64_t n, const float *v, int *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicOr(err, 1);
+}
+
 __global__ void k_validate(int64_t K, const float *x, const float *y, const float *z,
                            const float *T1, const float *T2, const float *dB0, const float *M0,
                            const float *b1, const float *Mi, int *err) {
@@ -386,8 +392,16 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
         } else {
             const void *segs = f64 ? (const void *)(dev.adc_d.as<ADCSegD>() + dev.adc_off[i])
                                    : (const void *)(dev.adc_f.as<ADCSegF>() + dev.adc_off[i]);
-            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &adv,
-                                d_signal + 2 * q.sample0, c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+            // one launch per receive coil; the state is only read here
+            for (int pass = 0; pass < std::max(ph->n_coils, 1); ++pass) {
+                if (ph->n_coils > 0) {
+                    st.coil_re = ph->coils.as<float>() + 2 * K * pass;
+                    st.coil_im = st.coil_re + K;
+                }
+                launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples,
+                                    &adv, d_signal + 2 * (s->n_samples * pass + q.sample0),
+                                    c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+            }
             for (int a = 0; a < 3; ++a) mom[a] += q.mom[a];
             tau += q.dur;
         }
@@ -653,35 +667,60 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     }
     const double z0[3] = {0.0, 0.0, 0.0};
     const A zero = AdvOf<R>::make(z0, 0.0);
-    bool first = true;
-    for (const auto &sp : P.spans) {
-        fa.ev = d_ev + sp.b;
-        fa.n_ev = (int)(sp.e - sp.b);
-        fa.init_eq = (first && !g->has_M_init) ? 1 : 0;
-        launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
-        first = false;
-        if (sp.fallback < 0) continue;
-        const Subseq &q = s->sub[sp.fallback];
-        if (q.type == SUB_RF) {
-            launch_plain_rf<R>(c, st, f64 ? s->rf_d[q.content].p : s->rf_f[q.content].p,
-                               (int)(q.seg_end - q.seg_begin), &zero,
-                               c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
-        } else {
-            const void *segs =
-                f64 ? (const void *)(s->adc_d.as<ADCSegD>() + s->adc_off[sp.fallback])
-                    : (const void *)(s->adc_f.as<ADCSegF>() + s->adc_off[sp.fallback]);
-            launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples, &zero,
-                                d_signal + 2 * q.sample0, c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
-        }
-    }
-    // every sample from the block sums (Eqs. 8, 10)
+    GWin *dw = nullptr;
+    int4 *db = nullptr;
     if (!P.blk.empty()) {
-        GWin *dw = (GWin *)scratch(c, 12, P.wins.size() * sizeof(GWin));
-        int4 *db = (int4 *)scratch(c, 13, P.blk.size() * sizeof(int4));
+        dw = (GWin *)scratch(c, 12, P.wins.size() * sizeof(GWin));
+        db = (int4 *)scratch(c, 13, P.blk.size() * sizeof(int4));
         upload(c, dw, P.wins.data(), P.wins.size() * sizeof(GWin));
         upload(c, db, P.blk.data(), P.blk.size() * sizeof(int4));
-        launch_group_signal<R>(c, dw, db, (int)P.blk.size(),
-                               f64 ? s->gs_d.p : s->gs_f.p, sig_tables<R>(g), Ablk, d_signal);
+    }
+    // one pass over the whole sequence per receive coil (Eq. 9 block sums per
+    // (group, coil)); the tables above serve every pass
+    const int n_pass = std::max(ph->n_coils, 1);
+    const int64_t ns = s->n_samples;
+    float *coil_s = ph->n_coils > 0 ? (float *)scratch(c, 18, 2 * K * sizeof(float)) : nullptr;
+    for (int pass = 0; pass < n_pass; ++pass) {
+        double *sig = d_signal + 2 * ns * pass;
+        if (coil_s) {
+            // coil `pass` in layout order
+            const float *src = ph->coils.as<float>() + 2 * K * pass;
+            launch_gather_f32(c, K, g->perm.as<int32_t>(), src, coil_s);
+            launch_gather_f32(c, K, g->perm.as<int32_t>(), src + K, coil_s + K);
+            fa.coil_re = st.coil_re = coil_s;
+            fa.coil_im = st.coil_im = coil_s + K;
+        }
+        if (pass > 0) {
+            MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double),
+                                       c->stream));
+            if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+        }
+        bool first = true;
+        for (const auto &sp : P.spans) {
+            fa.ev = d_ev + sp.b;
+            fa.n_ev = (int)(sp.e - sp.b);
+            fa.init_eq = (first && !g->has_M_init) ? 1 : 0;
+            launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
+            first = false;
+            if (sp.fallback < 0) continue;
+            const Subseq &q = s->sub[sp.fallback];
+            if (q.type == SUB_RF) {
+                launch_plain_rf<R>(c, st, f64 ? s->rf_d[q.content].p : s->rf_f[q.content].p,
+                                   (int)(q.seg_end - q.seg_begin), &zero,
+                                   c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
+            } else {
+                const void *segs =
+                    f64 ? (const void *)(s->adc_d.as<ADCSegD>() + s->adc_off[sp.fallback])
+                        : (const void *)(s->adc_f.as<ADCSegF>() + s->adc_off[sp.fallback]);
+                launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples,
+                                    &zero, sig + 2 * q.sample0,
+                                    c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+            }
+        }
+        // every sample from the block sums (Eqs. 8, 10)
+        if (!P.blk.empty())
+            launch_group_signal<R>(c, dw, db, (int)P.blk.size(), f64 ? s->gs_d.p : s->gs_f.p,
+                                   sig_tables<R>(g), Ablk, sig);
     }
     sync(c);
 }
@@ -988,6 +1027,42 @@ int mrsim_phantom(mrsim_ctx *c, int64_t K, const float *x, const float *y, const
     return rc;
 }
 
+int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sens,
+                unsigned flags) {
+    if (!c) return MRSIM_EINVAL;
+    return guard(c, [&] {
+        if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
+        if (n_coils < 0 || n_coils > MRSIM_MAX_COILS)
+            fail(MRSIM_EINVAL, "n_coils must be in [0, " + std::to_string(MRSIM_MAX_COILS) + "]");
+        if (n_coils > 0 && !sens) fail(MRSIM_EINVAL, "NULL sensitivities");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        if (n_coils == 0) {
+            ph->coils.reset();
+            ph->n_coils = 0;
+            return;
+        }
+        const int64_t n = 2 * (int64_t)n_coils * ph->K;
+        DBuf d = dalloc(n * sizeof(float));
+        MRSIM_CUDA(cudaMemcpyAsync(d.p, sens, n * sizeof(float),
+                                   (flags & MRSIM_PTR_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                              : cudaMemcpyHostToDevice,
+                                   c->stream));
+        int *err = c->dev_err.as<int>();
+        MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+        {
+            KScope ks(c, "validate_coils");
+            const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
+            k_finite<<<blocks, 256, 0, c->stream>>>(n, d.as<float>(), err);
+        }
+        int h = 0;
+        MRSIM_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (h) fail(MRSIM_EINVAL, "coil sensitivities have a non-finite value");
+        ph->coils = std::move(d);
+        ph->n_coils = n_coils;
+    });
+}
+
 int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t *rep,
                    const float *b1re, const float *b1im, const float *gx, const float *gy,
                    const float *gz, const uint8_t *adc, mrsim_seq **out) {
@@ -1097,10 +1172,10 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         }
         MRSIM_CUDA(cudaSetDevice(c->device));
         const int64_t K = ph->K, ns = s->n_samples;
+        const int64_t nsig = std::max<int64_t>(ns, 1) * std::max(ph->n_coils, 1);  // all coils
         const bool dev_out = (out_flags & MRSIM_OUT_DEVICE) != 0;
-        double *d_sig = dev_out ? signal
-                                : (double *)scratch(c, 8, std::max<int64_t>(ns, 1) * 2 * sizeof(double));
-        MRSIM_CUDA(cudaMemsetAsync(d_sig, 0, std::max<int64_t>(ns, 1) * 2 * sizeof(double), c->stream));
+        double *d_sig = dev_out ? signal : (double *)scratch(c, 8, nsig * 2 * sizeof(double));
+        MRSIM_CUDA(cudaMemsetAsync(d_sig, 0, nsig * 2 * sizeof(double), c->stream));
         const size_t esz = precision == MRSIM_FP64 ? 8 : 4;
         const int64_t Kp = plane_stride(K);
         void *Mst = scratch(c, 9, 3 * Kp * esz);
@@ -1126,7 +1201,8 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             sync(c);
         }
         if (!dev_out && ns > 0)
-            MRSIM_CUDA(cudaMemcpyAsync(signal, d_sig, ns * 2 * sizeof(double),
+            MRSIM_CUDA(cudaMemcpyAsync(signal, d_sig, ns * std::max(ph->n_coils, 1) * 2 *
+                                                          sizeof(double),
                                        cudaMemcpyDeviceToHost, c->stream));
         sync(c);
     });
@@ -1141,6 +1217,8 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
         for (int i = 0; i < n_jobs; ++i) {
             if (!ph[i] || !s[i] || !g[i] || !signals[i]) fail(MRSIM_EINVAL, "NULL batch entry");
             if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
+            if (ph[i]->n_coils > 0)
+                fail(MRSIM_EUNSUPPORTED, "batched jobs receive with one coil (S = 1)");
             for (const Subseq &q : s[i]->sub)
                 if ((q.type == SUB_RF || q.type == SUB_ADC) && q.gtype != G_GENERAL &&
                     !g[i]->built[q.gtype])

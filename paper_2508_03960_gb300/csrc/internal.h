@@ -66,7 +66,7 @@ struct mrsim_ctx {
     std::vector<Pending> prof_pending;
     std::vector<cudaEvent_t> ev_pool;
     // growable scratch areas reused across calls
-    mrsim::DBuf scratch[18];
+    mrsim::DBuf scratch[20];
     // error word written by kernels with bounded waits / bounds checks
     mrsim::DBuf dev_err;
     // pinned host staging for uploads of per-run plans
@@ -85,6 +85,8 @@ struct mrsim_phantom_t {
     uint64_t uid = 0;
     mrsim::DBuf x, y, z, T1, T2, dB0, M0, b1, M_init;  // b1 / M_init may be empty
     bool has_b1 = false, has_M_init = false;
+    int n_coils = 0;    // receive coils attached by mrsim_coils (0: one coil, S = 1)
+    mrsim::DBuf coils;  // float [n_coils][2][K] (re, im planes), phantom order
 };
 
 namespace mrsim {
@@ -218,12 +220,17 @@ void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
 constexpr int64_t kMaxAxisValues = 65535;
 void build_axis_index(mrsim_ctx *c, mrsim_groups *g);
+// out[i] = in[perm[i]] for i < K (float32)
+void launch_gather_f32(mrsim_ctx *c, int64_t K, const int32_t *perm, const float *in, float *out);
 
 // ---- plain path (k_plain.cu) ----
 struct PlainState {
     int64_t K;
     const float *x, *y, *z, *T1, *T2, *dB0, *M0, *b1;  // b1 may be null
     void *Mx, *My, *Mz;  // R arrays
+    // receive-coil sensitivity (re, im planes, same order as x) for the with-ADC
+    // kernels, or null for S = 1
+    const float *coil_re = nullptr, *coil_im = nullptr;
 };
 template <typename R>
 void launch_init_state(mrsim_ctx *c, const PlainState &s, const float *M_init);
@@ -280,6 +287,8 @@ struct FusedArgs {
     const int32_t *aidx;     // packed axis indices [K] (layout order)
     const float2 *qtab;      // phasor tables of all events
     int ax_sh[3];            // bit position of each axis' index in aidx
+    // receive-coil sensitivity (re, im planes, layout order) or null for S = 1
+    const float *coil_re, *coil_im;
 };
 // one axis table: out[j] = exp(-i 2 pi val[j] k) for j < n (cos, sin)
 struct AxItem {

@@ -535,4 +535,10 @@ void build_axis_index(mrsim_ctx *c, mrsim_groups *g) {
     g->ax_ok = true;
 }
 
+void launch_gather_f32(mrsim_ctx *c, int64_t K, const int32_t *perm, const float *in,
+                       float *out) {
+    KScope ks(c, "gather");
+    k_gather<float><<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, in, out);
+}
+
 }  // namespace mrsim

@@ -123,6 +123,7 @@ enum FusedMode : int {
     FM_FACTOR = 0,  // group-factor table, per-isochromat phasor evaluated
     FM_AXIS = 1,    // group-factor table, per-isochromat phasor from axis tables
     FM_DIRECT = 2,  // every factor from the isochromat's own parameters
+    FM_COIL = 4,    // flag: with-ADC terms weighted by a receive-coil sensitivity
 };
 
 template <int MASK>
@@ -178,6 +179,7 @@ struct Iso {
     int pofs[NI];  // primary group (row offset in a group-factor table)
     int tofs[NI];  // 12 * RF group (offset in a combined-transition table)
     int aidx[NI];  // axis mode only: packed axis indices
+    R sr[NI], si[NI];  // coil mode only: receive sensitivity S(k, p)
 };
 
 // whole advance of one isochromat from the event record (direct mode):
@@ -306,9 +308,11 @@ struct FusedSmem {
 
 // One chunk of kThreads * NI isochromats (chunk index blk) through all events
 // of a span.  All threads of the CTA take part (shared memory, barriers).
-template <typename R, int NI, int MODE>
+template <typename R, int NI, int MODE_FLAGS>
 __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                                             FusedSmem<R> &sm) {
+    constexpr int MODE = MODE_FLAGS & 3;
+    constexpr bool COIL = (MODE_FLAGS & FM_COIL) != 0;
     constexpr bool DIRECT = MODE == FM_DIRECT;
     FEvent<R> *sev = sm.sev;
     int *batch_prow = sm.batch_prow, *batch_win = sm.batch_win;
@@ -359,6 +363,10 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
             }
             key[i] = gp[k];
             s.tofs[i] = 12 * gr[k];
+            if constexpr (COIL) {
+                s.sr[i] = (R)a.coil_re[k];
+                s.si[i] = (R)a.coil_im[k];
+            }
             if constexpr (DIRECT) {
                 s.dB0[i] = a.dB0[k];
                 const float T1 = a.T1[k], T2 = a.T2[k];
@@ -368,6 +376,7 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
         } else {
             s.x[i] = s.y[i] = s.z[i] = s.M0[i] = 0;
             s.aidx[i] = 0;
+            s.sr[i] = s.si[i] = 0;
             s.mx[i] = s.my[i] = s.mz[i] = 0;
             key[i] = 0x7fffffff;
             s.tofs[i] = 0;
@@ -579,6 +588,14 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                         MRSIM_ADC_CASE(4) MRSIM_ADC_CASE(5) MRSIM_ADC_CASE(6) MRSIM_ADC_CASE(7)
                     }
                 }
+                if constexpr (COIL) {  // Eq. 6 with a receive coil: S(k, p) M_xy
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const R tr = s.sr[i] * vr[i] - s.si[i] * vi[i];
+                        vi[i] = s.sr[i] * vi[i] + s.si[i] * vr[i];
+                        vr[i] = tr;
+                    }
+                }
                 adc_reduce(ev, gtype, vr, vi);
             }
         }
@@ -594,10 +611,13 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
 // shared memory of an FP32 CTA, about 54 KB, lets four share an SM)
 template <typename R, int NI, int MODE>
 constexpr int fused_min_blocks() {
-    if (sizeof(R) == 8) return 1;
-    if (MODE == FM_AXIS) return 4;
-    if (MODE == FM_FACTOR) return NI == 4 ? 3 : 4;
-    return NI == 4 ? 2 : NI == 2 ? 3 : 4;
+    constexpr int base = MODE & 3;
+    constexpr int b = sizeof(R) == 8 ? 1
+                    : base == FM_AXIS ? 4
+                    : base == FM_FACTOR ? (NI == 4 ? 3 : 4)
+                                        : (NI == 4 ? 2 : NI == 2 ? 3 : 4);
+    // the coil's two registers per isochromat do not fit 64 per thread
+    return (MODE & FM_COIL) != 0 && b > 3 ? 3 : b;
 }
 
 template <typename R, int NI, int MODE>
@@ -804,17 +824,23 @@ void launch_fused_v(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
     else launch_fused_ni<R, 1, MODE>(c, a);
 }
 
+template <typename R, int COIL>
+void launch_fused_c(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
+    if (a.direct) {
+        launch_fused_v<R, FM_DIRECT | COIL>(c, a, ni);
+    } else if constexpr (sizeof(R) == 4) {
+        if (a.ax) launch_fused_v<R, FM_AXIS | COIL>(c, a, ni);
+        else launch_fused_v<R, FM_FACTOR | COIL>(c, a, ni);
+    } else {
+        launch_fused_v<R, FM_FACTOR | COIL>(c, a, ni);
+    }
+}
+
 template <typename R>
 void launch_fused(mrsim_ctx *c, const FusedArgs<R> &a, int ni) {
     KScope ks(c, sizeof(R) == 4 ? "fused_grouped_f32" : "fused_grouped_f64");
-    if (a.direct) {
-        launch_fused_v<R, FM_DIRECT>(c, a, ni);
-    } else if constexpr (sizeof(R) == 4) {
-        if (a.ax) launch_fused_v<R, FM_AXIS>(c, a, ni);
-        else launch_fused_v<R, FM_FACTOR>(c, a, ni);
-    } else {
-        launch_fused_v<R, FM_FACTOR>(c, a, ni);
-    }
+    if (a.coil_re) launch_fused_c<R, FM_COIL>(c, a, ni);
+    else launch_fused_c<R, 0>(c, a, ni);
 }
 
 // one thread per (item, entry): exp(-i 2 pi val[j] k) with the phase reduced
@@ -837,23 +863,25 @@ __global__ void k_axis_phase(const AxItem *items, int n_items, int max_n, float2
 
 // shared-memory attribute of every fused kernel on the context's device
 // (set before any stream capture, which may not accept attribute changes)
+template <typename R, int MODE>
+void fused_attr_ni(size_t bytes) {
+    fused_smem_attr(k_fused<R, 1, MODE>, bytes);
+    fused_smem_attr(k_fused<R, 2, MODE>, bytes);
+    fused_smem_attr(k_fused<R, 4, MODE>, bytes);
+}
+
 void prepare_fused(mrsim_ctx *) {
     const size_t f = sizeof(FusedSmem<float>), d = sizeof(FusedSmem<double>);
-    fused_smem_attr(k_fused<float, 1, FM_FACTOR>, f);
-    fused_smem_attr(k_fused<float, 2, FM_FACTOR>, f);
-    fused_smem_attr(k_fused<float, 4, FM_FACTOR>, f);
-    fused_smem_attr(k_fused<float, 1, FM_AXIS>, f);
-    fused_smem_attr(k_fused<float, 2, FM_AXIS>, f);
-    fused_smem_attr(k_fused<float, 4, FM_AXIS>, f);
-    fused_smem_attr(k_fused<float, 1, FM_DIRECT>, f);
-    fused_smem_attr(k_fused<float, 2, FM_DIRECT>, f);
-    fused_smem_attr(k_fused<float, 4, FM_DIRECT>, f);
-    fused_smem_attr(k_fused<double, 1, FM_FACTOR>, d);
-    fused_smem_attr(k_fused<double, 2, FM_FACTOR>, d);
-    fused_smem_attr(k_fused<double, 4, FM_FACTOR>, d);
-    fused_smem_attr(k_fused<double, 1, FM_DIRECT>, d);
-    fused_smem_attr(k_fused<double, 2, FM_DIRECT>, d);
-    fused_smem_attr(k_fused<double, 4, FM_DIRECT>, d);
+    fused_attr_ni<float, FM_FACTOR>(f);
+    fused_attr_ni<float, FM_AXIS>(f);
+    fused_attr_ni<float, FM_DIRECT>(f);
+    fused_attr_ni<float, FM_FACTOR | FM_COIL>(f);
+    fused_attr_ni<float, FM_AXIS | FM_COIL>(f);
+    fused_attr_ni<float, FM_DIRECT | FM_COIL>(f);
+    fused_attr_ni<double, FM_FACTOR>(d);
+    fused_attr_ni<double, FM_DIRECT>(d);
+    fused_attr_ni<double, FM_FACTOR | FM_COIL>(d);
+    fused_attr_ni<double, FM_DIRECT | FM_COIL>(d);
     fused_smem_attr(k_fused_batch<float, 1>, f);
     fused_smem_attr(k_fused_batch<float, 2>, f);
     fused_smem_attr(k_fused_batch<float, 4>, f);

@@ -233,6 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_plain_adc(PlainState s,
                 x[i] = s.x[k]; y[i] = s.y[k]; z[i] = s.z[k]; dB0[i] = s.dB0[k];
                 rT2[i] = inv_or_zero<R>(s.T2[k]) * (R)kLog2e;
                 advance_xy<R>(Mx[k], My[k], x[i], y[i], z[i], dB0[i], rT2[i], adv, cr[i], ci[i]);
+                // receive coil (Eq. 6): S is constant in time and the sample
+                // recurrence below is linear, so weighting the start weights
+                // every sample of the window
+                if (s.coil_re) cmul(cr[i], ci[i], (R)s.coil_re[k], (R)s.coil_im[k]);
             } else {
                 cr[i] = ci[i] = x[i] = y[i] = z[i] = dB0[i] = rT2[i] = 0;
             }

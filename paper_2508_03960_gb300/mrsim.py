@@ -30,7 +30,7 @@ TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1
 TUNE_PRECOMP_STEPS = 4
 
 # every entry point declared in include/mrsim.h
-EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
+EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom", "mrsim_coils",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
            "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
@@ -39,6 +39,7 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_surrogate_eval", "mrsim_free_surrogate",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
+MAX_COILS = 64
 
 
 class MrsimError(RuntimeError):
@@ -60,6 +61,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_last_error": (ctypes.c_char_p, [P]),
         "mrsim_phantom": (I, [P, I64] + [P] * 9 + [U, PP]),
         "mrsim_sequence": (I, [P, I64] + [P] * 8 + [PP]),
+        "mrsim_coils": (I, [P, P, I, P, U]),
         "mrsim_seq_info": (I, [P] * 7),
         "mrsim_group": (I, [P, P, P, PP]),
         "mrsim_group_info": (I, [P, I, P, P]),
@@ -185,6 +187,20 @@ def mrsim_group_info(groups, gtype, K=None):
     if rc:
         raise MrsimError(rc, "mrsim_group_info")
     return n.value, gid
+
+
+def mrsim_coils(ctx, ph, sens, flags=0):
+    """Attach receive-coil sensitivities float32 [P, 2, K] (None: detach)."""
+    if sens is None:
+        _check(ctx, lib().mrsim_coils(ctx, ph, 0, None, flags), "mrsim_coils")
+        return 0
+    if isinstance(sens, np.ndarray):
+        sens = np.ascontiguousarray(sens, np.float32)
+        n = int(sens.shape[0])
+    else:  # torch tensor on the device
+        n = int(sens.shape[0])
+    _check(ctx, lib().mrsim_coils(ctx, ph, n, _ptr(sens), flags), "mrsim_coils")
+    return n
 
 
 def mrsim_run(ctx, ph, seq, groups, mode, precision, signal, M_final=None, out_flags=0):
@@ -325,6 +341,7 @@ class Context:
     def __init__(self, device: int = 0, stream: Optional[int] = None):
         self.h = mrsim_create(device, stream)
         self._handles = []
+        self._coils = {}  # phantom handle -> receive coils attached
 
     def close(self):
         for kind, h in reversed(self._handles):
@@ -354,6 +371,8 @@ class Context:
                     _f32(p.M0), _f32(p.b1),
                     None if p.M_init is None else np.ascontiguousarray(p.M_init, np.float32)]
             h = mrsim_phantom(self.h, p.K, *keep)
+            if getattr(p, "coils", None) is not None:
+                self._coils[h] = mrsim_coils(self.h, h, p.coils)
         self._handles.append(("ph", h))
         return h
 
@@ -372,13 +391,18 @@ class Context:
 
     def run(self, ph, seq, groups=None, mode=GROUPED, precision=FP32, n_samples=None,
             K=None, want_M=False):
+        """Signal complex128 [n_samples] ([P, n_samples] with P receive
+        coils) and, if want_M, the final magnetization [3, K]."""
         if n_samples is None:
             n_samples = mrsim_seq_info(seq)["n_samples_total"]
-        sig = np.zeros(2 * max(n_samples, 1), np.float64)
+        P = self._coils.get(ph, 0)
+        sig = np.zeros(2 * max(n_samples, 1) * max(P, 1), np.float64)
         M = np.zeros((3, K), np.float32) if want_M else None
         mrsim_run(self.h, ph, seq, groups if groups else None, mode, precision, sig, M)
-        return sig[: 2 * n_samples].view(np.complex128).copy(), M
+        out = sig[: 2 * n_samples * max(P, 1)].view(np.complex128).copy()
+        return (out.reshape(P, n_samples) if P else out), M
 
     def free(self, kind: str, h: int):
         self._handles = [(k, x) for (k, x) in self._handles if x != h]
+        self._coils.pop(h, None)
         {"ph": mrsim_free_phantom, "seq": mrsim_free_seq, "grp": mrsim_free_groups}[kind](h)

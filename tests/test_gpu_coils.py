@@ -1,0 +1,145 @@
+"""Receive coils (Eq. 6 with P coils): every mode and precision of the CUDA
+path against the FP64 oracle, coil by coil.
+
+Tolerances are those of the single-coil parity tests: signal rel-L2 1e-4 for
+FP32 runs and 1e-10 for FP64 runs, per coil.  A unit sensitivity (S = 1) must
+reproduce the run without coils bit for bit: the weighting multiplies by
+(1, 0) exactly."""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from mrsim_inputs import coil_maps, configs
+from mrsim_inputs.phantom import continuous_phantom
+from mrsim_inputs.sequence import fse_2d, spin_echo_2d
+
+from test_gpu_parity import general_type_sequence
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-10}
+
+
+@pytest.fixture(scope="module")
+def ctx(mrsim):
+    c = mrsim.Context(0)
+    yield c
+    c.close()
+
+
+def with_coils(ph, n, seed):
+    return dataclasses.replace(ph, coils=coil_maps(ph, n, seed))
+
+
+def run(mrsim, ctx, ph, seq, mode, precision, want_M=False):
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs) if mode in (mrsim.GROUPED, mrsim.SURROGATE) else None
+    out = ctx.run(hp, hs, hg, mode, precision, K=ph.K, want_M=want_M)
+    if hg:
+        ctx.free("grp", hg)
+    ctx.free("seq", hs)
+    ctx.free("ph", hp)
+    return out
+
+
+def check_coils(sig, ref, precision):
+    assert sig.shape == ref.shape
+    for p in range(ref.shape[0]):
+        e = oracle.rel_l2(sig[p], ref[p])
+        assert e <= TOL[precision], f"coil {p}: signal rel-L2 {e:.3e}"
+
+
+@pytest.mark.parametrize("mode", ["plain", "plain_cache", "grouped"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coils_match_oracle(mrsim, ctx, mode, precision):
+    ph = with_coils(configs.small_phantom(24, 20, 3), 3, seed=41)
+    seq = spin_echo_2d(n_ro=16, n_pe=8, n_tr=2)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    m = {"plain": mrsim.PLAIN, "plain_cache": mrsim.PLAIN_CACHE, "grouped": mrsim.GROUPED}[mode]
+    sig, M = run(mrsim, ctx, ph, seq, m, precision, want_M=True)
+    check_coils(sig, ref, precision)
+    assert float(np.max(np.abs(M - Mref))) <= (1e-7 if precision else 1e-4)
+
+
+@pytest.mark.parametrize("ni", [1, 4])
+def test_coils_grouped_fse_every_register_block(mrsim, ctx, ni):
+    ph = with_coils(configs.small_phantom(32, 32, 4), 4, seed=43)
+    seq = fse_2d(n_ro=32, n_pe=32, etl=4, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=1.0, n_shots=2)
+    ref, _ = oracle.simulate(ph, seq, memo=True, adc_recurrence=True, want_M=False)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, ni)
+    try:
+        sig, _ = run(mrsim, ctx, ph, seq, mrsim.GROUPED, 0)
+    finally:
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, 4)
+    check_coils(sig, ref, 0)
+
+
+def test_coils_direct_mode_one_group_per_isochromat(mrsim, ctx):
+    """Per-isochromat dB0 and b1: the fused kernel advances every isochromat
+    from its own parameters (direct mode)."""
+    ph = with_coils(continuous_phantom(16, 16, 2, 3, seed=47), 2, seed=44)
+    seq = spin_echo_2d(n_ro=16, n_pe=8, n_tr=2)
+    ref, _ = oracle.simulate(ph, seq, memo=True, adc_recurrence=True, want_M=False)
+    for precision in (0, 1):
+        sig, _ = run(mrsim, ctx, ph, seq, mrsim.GROUPED, precision)
+        check_coils(sig, ref, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coils_with_fallback_spans_and_initial_state(mrsim, ctx, precision):
+    """Every coil pass restarts the whole span chain (fused spans and plain
+    fallbacks) from the initial state."""
+    ph = with_coils(configs.small_phantom(16, 16, 3), 3, seed=45)
+    rng = np.random.default_rng(12)
+    ph.M_init = rng.uniform(-0.5, 0.5, (3, ph.K)).astype(np.float32)
+    seq = general_type_sequence()
+    ref, Mref = oracle.simulate(ph, seq)
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        sig, M = run(mrsim, ctx, ph, seq, mode, precision, want_M=True)
+        check_coils(sig, ref, precision)
+        assert float(np.max(np.abs(M - Mref))) <= (1e-7 if precision else 1e-4)
+
+
+def test_unit_coil_equals_no_coil(mrsim, ctx):
+    ph = configs.small_phantom(16, 16, 2)
+    seq = spin_echo_2d(n_ro=16, n_pe=8, n_tr=2)
+    unit = np.zeros((1, 2, ph.K), np.float32)
+    unit[0, 0] = 1.0
+    for mode in (mrsim.GROUPED, mrsim.PLAIN):
+        single, _ = run(mrsim, ctx, ph, seq, mode, 0)
+        coil, _ = run(mrsim, ctx, dataclasses.replace(ph, coils=unit), seq, mode, 0)
+        assert coil.shape == (1, seq.n_samples)
+        assert np.array_equal(coil[0], single)
+
+
+def test_coil_errors(mrsim, ctx):
+    ph = configs.small_phantom(8, 8, 2)
+    seq = spin_echo_2d(n_ro=8, n_pe=8, n_tr=1)
+    hp = ctx.phantom(ph)
+    too_many = np.zeros((mrsim.MAX_COILS + 1, 2, ph.K), np.float32)
+    with pytest.raises(mrsim.MrsimError) as e:
+        mrsim.mrsim_coils(ctx.h, hp, too_many)
+    assert e.value.code == mrsim.EINVAL
+    bad = np.ones((2, 2, ph.K), np.float32)
+    bad[1, 0, 5] = np.inf
+    with pytest.raises(mrsim.MrsimError) as e:
+        mrsim.mrsim_coils(ctx.h, hp, bad)
+    assert e.value.code == mrsim.EINVAL
+    # a phantom with coils is not batched
+    mrsim.mrsim_coils(ctx.h, hp, coil_maps(ph, 2, seed=3))
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    with pytest.raises(mrsim.MrsimError) as e:
+        mrsim.mrsim_run_batch(ctx.h, [hp], [hs], [hg], [np.zeros(2 * seq.n_samples)])
+    assert e.value.code == mrsim.EUNSUPPORTED
+    # detached again: one coil, S = 1
+    mrsim.mrsim_coils(ctx.h, hp, None)
+    sig = np.zeros(2 * seq.n_samples)
+    mrsim.mrsim_run(ctx.h, hp, hs, hg, mrsim.GROUPED, mrsim.FP32, sig)
+    ref, _ = oracle.simulate(ph, seq, want_M=False)
+    assert oracle.rel_l2(sig.view(np.complex128), ref) <= 1e-4
