@@ -2,9 +2,11 @@
 path against the FP64 oracle, coil by coil.
 
 Tolerances are those of the single-coil parity tests: signal rel-L2 1e-4 for
-FP32 runs and 1e-10 for FP64 runs, per coil.  A unit sensitivity (S = 1) must
-reproduce the run without coils bit for bit: the weighting multiplies by
-(1, 0) exactly."""
+FP32 runs and 1e-10 for FP64 runs, per coil.  A unit sensitivity (S = 1)
+multiplies every term by (1, 0) exactly, so it must reproduce the run without
+coils up to the order in which atomics add the block sums and the signal
+(FP32 and FP64 atomics, which differ from run to run in the last bits):
+rel-L2 1e-6."""
 
 import dataclasses
 
@@ -114,7 +116,7 @@ def test_unit_coil_equals_no_coil(mrsim, ctx):
         single, _ = run(mrsim, ctx, ph, seq, mode, 0)
         coil, _ = run(mrsim, ctx, dataclasses.replace(ph, coils=unit), seq, mode, 0)
         assert coil.shape == (1, seq.n_samples)
-        assert np.array_equal(coil[0], single)
+        assert oracle.rel_l2(coil[0], single) <= 1e-6
 
 
 def test_coil_errors(mrsim, ctx):
