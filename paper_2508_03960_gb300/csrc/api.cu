@@ -456,8 +456,21 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         const Subseq &q = s->sub[i];
         if (q.type != SUB_ADC || q.gtype == G_GENERAL || q.n_samples == 0) continue;
         win_off[i] = P.ablk_n;
-        P.wins.push_back(GWin{q.gtype, (int)g->n_groups[q.gtype], P.ablk_n, q.sample0,
-                              (int)q.n_samples, 0});
+        GWin w{q.gtype, (int)g->n_groups[q.gtype], P.ablk_n, q.sample0, (int)q.n_samples, 0,
+               0.0f, 0.0f, 0.0f, 0.0f};
+        if (q.seg_end - q.seg_begin == 1 && s->adc[q.seg_begin]) {
+            const int64_t j = q.seg_begin;
+            const double dt = s->dt[j];
+            const float gax = q.gtype == G_X ? s->gx[j] : q.gtype == G_Y ? s->gy[j]
+                            : q.gtype == G_Z ? s->gz[j] : 0.0f;
+            const double dk = kGammaBar * (double)gax * dt;
+            w.uniform = 1;
+            w.dt_hi = (float)dt;
+            w.dt_lo = (float)(dt - (double)w.dt_hi);
+            w.dk_hi = (float)dk;
+            w.dk_lo = (float)(dk - (double)w.dk_hi);
+        }
+        P.wins.push_back(w);
         P.ablk_n += g->n_groups[q.gtype];
     }
     if (P.ablk_n > 0x7fffffffLL) fail(MRSIM_EUNSUPPORTED, "too many block sums");

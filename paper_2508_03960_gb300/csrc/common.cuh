@@ -103,7 +103,11 @@ struct GWin {
     long long ablk;      // offset of the block sums (complex entries)
     long long sample0;   // first sample (global index)
     int n_samples;
-    int pad;
+    // 1: the window is one ADC segment (constant gradient, one dwell), so
+    // every group's samples form a geometric sequence with step dt (s) and
+    // dk = gamma_bar g dt (cycles/m) on the group's axis, as hi + lo floats
+    int uniform;
+    float dt_hi, dt_lo, dk_hi, dk_lo;
 };
 // per-sample time and moment since the window start on the group's axis
 struct GSampleF {

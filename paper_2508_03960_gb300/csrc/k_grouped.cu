@@ -676,6 +676,95 @@ __device__ __forceinline__ float gs_tau(const GSampleF &s) { return s.tau_hi + s
 __device__ __forceinline__ double gs_tau(const GSampleD &s) { return s.tau; }
 
 constexpr int kGTile = 256;
+constexpr int kRun = 8;  // samples per thread on uniform windows
+
+// Uniform window (one ADC segment): a group's term at sample s + j is its term
+// at s times z^j, z = E2(dt) exp(-i 2 pi (pos dk + dB0 dt)) (Eqs. 8, 10 with a
+// constant gradient).  Thread (run ri, lane gl) takes kRun consecutive samples
+// of the block and every LPR-th group of each tile: two phasors and exps per
+// (group, run) instead of one per (group, sample).  Partial sums per sample are
+// combined over the lanes in FP64 shared memory.
+__device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, int nsb,
+                                                  const GSampleF *smp,
+                                                  const GSigTables<float> &tab,
+                                                  const double *Ablk, double *signal) {
+    __shared__ float s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
+    __shared__ double s_red[2][kThreads * kRun];
+    const int NR = (nsb + kRun - 1) / kRun;
+    int NRp = 1;
+    while (NRp < NR) NRp <<= 1;
+    const int LPR = kThreads / NRp;
+    const int ri = threadIdx.x % NRp, gl = threadIdx.x / NRp;
+    const int64_t s0 = (int64_t)b.y + (int64_t)ri * kRun;
+    const int len = ri < NR ? min(kRun, (int)((int64_t)b.y + nsb - s0)) : 0;
+    GSampleF sm{};
+    if (len > 0) sm = smp[s0];
+    const float tau0 = sm.tau_hi + sm.tau_lo;
+    const float dt = w.dt_hi + w.dt_lo;
+    const float *pos = tab.pos[w.gtype], *dB0 = tab.dB0[w.gtype], *rT2 = tab.rT2[w.gtype];
+    double ar_d[kRun], ai_d[kRun];
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) ar_d[j] = ai_d[j] = 0.0;
+    for (int g0 = b.z; g0 < b.w; g0 += kGTile) {
+        const int n = min(kGTile, b.w - g0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            s_pos[t] = pos[g0 + t];
+            s_dB0[t] = dB0[g0 + t];
+            s_rT2[t] = rT2[g0 + t];
+            s_ar[t] = (float)Ablk[2 * (w.ablk + g0 + t)];
+            s_ai[t] = (float)Ablk[2 * (w.ablk + g0 + t) + 1];
+        }
+        __syncthreads();
+        if (len > 0) {
+            float pr[kRun], pi[kRun];
+#pragma unroll
+            for (int j = 0; j < kRun; ++j) pr[j] = pi[j] = 0.0f;
+            for (int t = gl; t < n; t += LPR) {
+                float c, sn, cz, sz;
+                phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, sn);
+                phasor(turns_prod(s_pos[t], w.dk_hi, w.dk_lo) +
+                           turns_prod(s_dB0[t], w.dt_hi, w.dt_lo),
+                       cz, sz);
+                const float e = decay(tau0, s_rT2[t]), ez = decay(dt, s_rT2[t]);
+                // term = E2 exp(-i phi) A with exp(-i phi) = c - i sn
+                const float ar = s_ar[t], ai = s_ai[t];
+                float ur = e * (c * ar + sn * ai), ui = e * (c * ai - sn * ar);
+                const float zr = ez * cz, zi = -ez * sz;
+#pragma unroll
+                for (int j = 0; j < kRun; ++j) {
+                    pr[j] += ur;
+                    pi[j] += ui;
+                    const float nr = ur * zr - ui * zi;
+                    ui = ur * zi + ui * zr;
+                    ur = nr;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kRun; ++j) {
+                ar_d[j] += (double)pr[j];
+                ai_d[j] += (double)pi[j];
+            }
+        }
+    }
+    // samples of run ri at [ri * kRun, ...): lane gl's partials
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+        s_red[0][gl * (NRp * kRun) + ri * kRun + j] = ar_d[j];
+        s_red[1][gl * (NRp * kRun) + ri * kRun + j] = ai_d[j];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nsb; q += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int l = 0; l < LPR; ++l) {
+            sr += s_red[0][l * (NRp * kRun) + q];
+            si += s_red[1][l * (NRp * kRun) + q];
+        }
+        atomicAdd(&signal[2 * ((int64_t)b.y + q)], sr);
+        atomicAdd(&signal[2 * ((int64_t)b.y + q) + 1], si);
+    }
+    __syncthreads();
+}
 
 // block b covers samples [blk.y, blk.y + blockDim) of window blk.x and the
 // groups [blk.z, blk.w); partial sums go to the signal with FP64 atomics
@@ -691,6 +780,12 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
     // block gets several group lanes per sample (lane sl takes groups sl,
     // sl + LPS, ...), combined in shared memory before the FP64 atomics.
     const int nsb = (int)min((long long)kThreads, w.sample0 + w.n_samples - (long long)b.y);
+    if constexpr (sizeof(R) == 4) {
+        if (w.uniform) {
+            group_signal_runs(w, b, nsb, smp, tab, Ablk, signal);
+            return;
+        }
+    }
     int SPB = 32;
     while (SPB < nsb) SPB <<= 1;
     const int LPS = kThreads / SPB;
