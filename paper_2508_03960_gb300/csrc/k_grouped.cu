@@ -702,9 +702,17 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
     const float tau0 = sm.tau_hi + sm.tau_lo;
     const float dt = w.dt_hi + w.dt_lo;
     const float *pos = tab.pos[w.gtype], *dB0 = tab.dB0[w.gtype], *rT2 = tab.rT2[w.gtype];
+    // FP32 partial sums, folded into FP64 every LPR tiles: each partial then
+    // covers 256 groups whatever the mapping (an FP64 fold per tile would make
+    // the FP64 pipe, a small fraction of the FP32 rate here, the bottleneck)
     double ar_d[kRun], ai_d[kRun];
+    float pr[kRun], pi[kRun];
 #pragma unroll
-    for (int j = 0; j < kRun; ++j) ar_d[j] = ai_d[j] = 0.0;
+    for (int j = 0; j < kRun; ++j) {
+        ar_d[j] = ai_d[j] = 0.0;
+        pr[j] = pi[j] = 0.0f;
+    }
+    int tiles = 0;
     for (int g0 = b.z; g0 < b.w; g0 += kGTile) {
         const int n = min(kGTile, b.w - g0);
         __syncthreads();
@@ -717,9 +725,6 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
         }
         __syncthreads();
         if (len > 0) {
-            float pr[kRun], pi[kRun];
-#pragma unroll
-            for (int j = 0; j < kRun; ++j) pr[j] = pi[j] = 0.0f;
             for (int t = gl; t < n; t += LPR) {
                 float c, sn, cz, sz;
                 phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, sn);
@@ -740,12 +745,21 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
                     ur = nr;
                 }
             }
+            if (++tiles == LPR) {
 #pragma unroll
-            for (int j = 0; j < kRun; ++j) {
-                ar_d[j] += (double)pr[j];
-                ai_d[j] += (double)pi[j];
+                for (int j = 0; j < kRun; ++j) {
+                    ar_d[j] += (double)pr[j];
+                    ai_d[j] += (double)pi[j];
+                    pr[j] = pi[j] = 0.0f;
+                }
+                tiles = 0;
             }
         }
+    }
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+        ar_d[j] += (double)pr[j];
+        ai_d[j] += (double)pi[j];
     }
     // samples of run ri at [ri * kRun, ...): lane gl's partials
 #pragma unroll
