@@ -317,6 +317,17 @@ def cpu_baseline(ph, seq, stride, threads=0):
     return wall * ph.K / sub.K, wall, sub.K, cores
 
 
+def reduce_max(v, dist=None, device="cuda"):
+    """Largest v over the ranks of the default process group (the slowest
+    replica's time); v itself without a process group."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def rf_runs(seq):
     """With-RF subsequences of a sequence (maximal runs of segments with RF):
     total sub-steps and segments over all of them, and sub-steps summed over
@@ -427,11 +438,7 @@ def main():
             dist.barrier()
 
     def maxr(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, "cuda")
 
     # ---- resident phantom, prepared sequences and groups (once per phantom) ----
     t0 = time.perf_counter()
