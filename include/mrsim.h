@@ -249,8 +249,10 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              tree); 0 (default) picks by pulse length
  *   MRSIM_TUNE_PRECOMP_STEPS   FP32 runs: sub-steps composed in FP32 registers
  *                              (difference form) before each fold into the
- *                              FP64 combined transition: 1, 2, 4 or 8
- *                              (default).  For 200-step sinc pulses the
+ *                              FP64 combined transition: 1, 2, 4, 8
+ *                              (default), 16 or 32 (fewer FP64 folds: the
+ *                              fold is FP64-pipe work, a small fraction of
+ *                              the FP32 rate on this GPU).  For 200-step sinc pulses the
  *                              composed entries stay within 2e-7 of FP64
  *                              composition at 8 and within 1e-7 at 4 or less
  *                              (an FP32 result is itself rounded to 6e-8);

@@ -1246,7 +1246,7 @@ int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
     static const int allowed[5][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
                                       {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
-                                      {1, 2, 4, 8, -1, -1}};
+                                      {1, 2, 4, 8, 16, 32}};
     if (param < 0 || param > 4) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
     for (int v : allowed[param]) ok |= v >= 0 && v == value;
@@ -1276,7 +1276,7 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
         std::vector<std::pair<int, std::vector<int>>> plan;
         if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
-        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8}});
+        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8, 16, 32}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 4, 8, 16, 32, 128}});
         plan.push_back({MRSIM_TUNE_PLAIN_RF_NI, {1, 2}});
         plan.push_back({MRSIM_TUNE_ADC_CTAS_PER_SM, {1, 2, 4, 8}});

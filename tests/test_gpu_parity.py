@@ -312,7 +312,7 @@ def test_precompute_lane_counts(mrsim, ctx, lanes, precision):
     check(sig, M, ref, Mref, precision, M0max=float(np.max(ph.M0)))
 
 
-@pytest.mark.parametrize("steps", [1, 2, 4, 8])
+@pytest.mark.parametrize("steps", [1, 2, 4, 8, 16, 32])
 def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
     """FP32 runs compose a few sub-steps in FP32 registers before each fold into
     the FP64 combined transition; every allowed block length keeps the FP32
@@ -333,7 +333,7 @@ def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
 
 def test_tuning_parameters_are_validated(mrsim, ctx):
     for param, bad in ((mrsim.TUNE_FUSED_NI, 3), (mrsim.TUNE_PRECOMP_LANES, 64),
-                       (mrsim.TUNE_PRECOMP_STEPS, 16), (5, 1), (-1, 1)):
+                       (mrsim.TUNE_PRECOMP_STEPS, 64), (5, 1), (-1, 1)):
         with pytest.raises(mrsim.MrsimError):
             mrsim.mrsim_set_tuning(ctx.h, param, bad)
     before = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS)
