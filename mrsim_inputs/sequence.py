@@ -282,3 +282,38 @@ def gre_2d(n_ro=64, n_pe=64, fov=0.256, thk=0.010, flip=30.0, rf_dur=2e-3,
         b.grad(d_sp, (0.0, -ky / gb / d_sp, spoil_area_cycles / thk / gb / d_sp))
     b.delay_until(n_pe * tr)
     return b.build(kind="gre", n_ro=n_ro, n_pe=n_pe, tr=tr, flip=flip)
+
+
+def kspace_layout(seq: Sequence) -> dict:
+    """Where each acquisition line of a generated Cartesian sequence (SE, FSE,
+    EPI) sits in k-space, as the generators build them: line a (in ADC-window
+    order) fills grid row ``row[a]`` (ky index, 0..n_pe-1, centre n_pe/2), and
+    its sample i the column ``(col0[a] + dir[a] * i) mod n_ro`` (kx index,
+    centre n_ro/2).  A sample is taken at the end of its dwell, so forward
+    readouts start one column right of -kx_max (col0 = 1), reversed EPI lines
+    at n_ro - 1.  The spin echo encodes ky before its 180-degree pulse, which
+    negates it: row = (n_pe - p) mod n_pe for TR p."""
+    m = seq.meta
+    kind = m.get("kind")
+    if kind == "se":
+        n_ro, n_pe, n_tr = m["n_ro"], m["n_pe"], m["n_tr"]
+        rows = [(n_pe - (p % n_pe)) % n_pe for p in range(n_tr)]
+        col0 = [1] * n_tr
+        dirs = [1] * n_tr
+    elif kind == "fse":
+        n_ro, n_pe, etl, shots = m["n_ro"], m["n_pe"], m["etl"], m["shots"]
+        rows, col0, dirs = [], [], []
+        for s in range(shots):
+            for e in range(1, etl + 1):
+                rows.append(((e - 1) * shots + s) % n_pe)
+                col0.append(1)
+                dirs.append(1)
+    elif kind == "epi":
+        n_ro, n_pe = m["n_ro"], m["n_lines"]
+        rows = list(range(n_pe))
+        col0 = [1 if l % 2 == 0 else n_ro - 1 for l in range(n_pe)]
+        dirs = [1 if l % 2 == 0 else -1 for l in range(n_pe)]
+    else:
+        raise ValueError(f"no Cartesian layout for sequence kind {kind!r}")
+    return dict(n_ro=int(n_ro), n_pe=int(n_pe), row=np.array(rows, np.int32),
+                col0=np.array(col0, np.int32), dir=np.array(dirs, np.int8))

@@ -578,3 +578,74 @@ def test_p13_bad_sensitivities_are_rejected():
     S[0, 1, 3] = np.nan
     with pytest.raises(RuntimeError):
         oracle.simulate(_with_coils(ph, S), seq, want_M=False)
+
+
+# ------------------------------------------------------- P14 reconstruction
+# Cartesian reconstruction (the paper's FFT reconstruction of SE / FSE data;
+# EPI on flat-tops only is Cartesian after line reversal).  Pinned by (a) an
+# explicit centred DFT written as matrices (independent of numpy's FFT) whose
+# k-space, read out through the layout, must reconstruct to the image, and
+# (b) the physics: with T1 = T2 = inf, dB0 = 0 and one z plane every isochromat
+# is excited alike, so the image of the simulated SE, FSE and EPI k-space must
+# be a constant complex multiple of the M0 map (a row flip, a wrong readout
+# direction or a one-column shift fails).
+
+def _centred_dft(n):
+    k = np.arange(n) - n // 2
+    return np.exp(-2j * np.pi * np.outer(k, k) / n)
+
+
+def test_p14_reconstruction_inverts_explicit_dft():
+    from oracle.recon import recon_cartesian
+    from mrsim_inputs.sequence import epi_2d, fse_2d, spin_echo_2d, kspace_layout
+    rng = np.random.default_rng(14)
+    for seq in (spin_echo_2d(n_ro=8, n_pe=6, n_tr=6), fse_2d(n_ro=8, n_pe=8, etl=4),
+                epi_2d(n_ro=8, n_lines=6)):
+        L = kspace_layout(seq)
+        N, M = L["n_ro"], L["n_pe"]
+        img = rng.normal(size=(M, N)) + 1j * rng.normal(size=(M, N))
+        K = _centred_dft(M) @ img @ _centred_dft(N).T
+        i = np.arange(N)
+        sig = np.stack([K[L["row"][a], (L["col0"][a] + L["dir"][a] * i) % N]
+                        for a in range(len(L["row"]))])
+        assert oracle.rel_l2(recon_cartesian(sig.ravel(), L), img) <= 1e-12
+
+
+def _split_by_tr(seq, tr, n):
+    """The n repetitions of a sequence, each as its own sequence (each then
+    starts from equilibrium)."""
+    from mrsim_inputs import Sequence
+    t0 = np.concatenate([[0.0], np.cumsum(seq.dt * seq.repeat)])[:-1]
+    out = []
+    for p in range(n):
+        sel = (t0 >= p * tr - 1e-12) & (t0 < (p + 1) * tr - 1e-12)
+        out.append(Sequence(**{k: np.ascontiguousarray(v[sel]) for k, v in seq.arrays().items()}))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["se", "fse", "epi"])
+def test_p14_image_of_simulated_kspace_is_m0_map(kind):
+    """T1 = T2 = inf keeps the refocusing exact; the spin echo's repetitions
+    are simulated one by one from equilibrium (with infinite T1 the residue of
+    one TR would otherwise echo in the next), the FSE uses one shot."""
+    from oracle.recon import recon_cartesian
+    from mrsim_inputs.sequence import epi_2d, fse_2d, spin_echo_2d, kspace_layout
+    n = 16
+    rng = np.random.default_rng(15)
+    M0map = rng.uniform(0.2, 1.0, (n, n))
+    ph = grid_phantom(M0map, nz=1, fov=0.256)
+    ph.T1 = np.full(ph.K, np.inf, np.float32)
+    ph.T2 = np.full(ph.K, np.inf, np.float32)
+    ph.dB0 = np.zeros(ph.K, np.float32)
+    seq = {"se": lambda: spin_echo_2d(n_ro=n, n_pe=n),
+           "fse": lambda: fse_2d(n_ro=n, n_pe=n, etl=n, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6,
+                                 esp=10e-3, tr=1.0),
+           "epi": lambda: epi_2d(n_ro=n, n_lines=n, dwell=10e-6)}[kind]()
+    parts = _split_by_tr(seq, seq.meta["tr"], n) if kind == "se" else [seq]
+    sig = np.concatenate([oracle.simulate(ph, q, memo=True, adc_recurrence=True,
+                                          want_M=False)[0] for q in parts])
+    img = recon_cartesian(sig, kspace_layout(seq))
+    m = ph.M0.astype(np.float64).reshape(n, n)
+    c = np.vdot(m, img) / np.vdot(m, m)   # least-squares complex scale
+    assert abs(c) > 0.5
+    assert oracle.rel_l2(img, c * m) <= 1e-5
