@@ -294,6 +294,36 @@ def multicoil_workload(ctx, mrsim, torch, ph, seq, hp_single, hg_single, steps, 
     return out
 
 
+def recon_workload(ctx, mrsim, torch, named_signals, steps):
+    """Images of the simulated FSE and EPI k-space (mrsim_recon_cartesian on
+    device buffers), timed with CUDA events, against the oracle's (numpy FFT)
+    reconstruction of the stored FP64 oracle signals."""
+    from mrsim_inputs.sequence import kspace_layout
+    from oracle.recon import recon_cartesian
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, seq, sig in named_signals:
+        L = kspace_layout(seq)
+        d_sig = torch.from_numpy(np.ascontiguousarray(sig).view(np.float64).copy()).cuda()
+        d_img = torch.zeros(2 * L["n_pe"] * L["n_ro"], dtype=torch.float64, device="cuda")
+        mrsim.mrsim_recon_cartesian(ctx.h, d_sig, L, d_img, mrsim.PTR_DEVICE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            mrsim.mrsim_recon_cartesian(ctx.h, d_sig, L, d_img, mrsim.PTR_DEVICE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        img = d_img.cpu().numpy().view(np.complex128).reshape(L["n_pe"], L["n_ro"])
+        ent = {"matrix": [L["n_pe"], L["n_ro"]], "ms": round(e0.elapsed_time(e1) / steps, 4)}
+        path = os.path.join(GOLDEN, f"{name}_27m_oracle.npz")
+        if os.path.exists(path):
+            ref = recon_cartesian(np.load(path)["signal"], L)
+            ent["image_rel_l2_vs_oracle"] = float(np.linalg.norm(img - ref) / np.linalg.norm(ref))
+        out[name] = ent
+    return out
+
+
 def golden_check(name, sig, ph_digest, seq_digest):
     path = os.path.join(GOLDEN, f"{name}_27m_oracle.npz")
     if not os.path.exists(path):
@@ -592,6 +622,9 @@ def main():
     batch = batch_workload(ctx, mrsim, torch, a.steps, a.warmup)
     # ---- learned with-RF transitions ----
     surrogate = surrogate_workload(ctx, mrsim, torch)
+    # ---- image reconstruction of the simulated k-space ----
+    recon = recon_workload(ctx, mrsim, torch, (("fse", fse, fse_sig), ("epi", epi, epi_sig)),
+                           a.steps)
     # ---- receive coils (Eq. 6 with P coils) ----
     multicoil = multicoil_workload(ctx, mrsim, torch, ph, fse, hp, hg_f, a.steps)
 
@@ -694,6 +727,7 @@ def main():
         "batch64": batch,
         "surrogate": surrogate,
         "multicoil": multicoil,
+        "recon": recon,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         "roofline": roof, "kernel_roofline": kroof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),

@@ -188,6 +188,24 @@ int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);
 
+/* Image of one coil's Cartesian k-space signal: the centred, normalised
+ * inverse DFT the paper applies to its SE / FSE data ("Simulations #1"; an
+ * EPI sampled on gradient flat-tops only is Cartesian after reversing every
+ * other line, so it is reconstructed the same way).  signal: [n_lines][2 *
+ * n_ro] doubles (re, im), the acquisition lines in ADC-window order, as
+ * mrsim_run returns them.  Line a goes to k-space row row[a] (0..n_pe-1,
+ * centre n_pe / 2) and its sample i to column (col0[a] + dir[a] * i) mod n_ro
+ * (centre n_ro / 2; dir = +1 or -1); samples landing on one point add.  Then
+ *   image[y][x] = 1/(n_ro n_pe) sum K[ky][kx] exp(+i 2 pi ((kx - n_ro/2)(x - n_ro/2) / n_ro
+ *                                                        + (ky - n_pe/2)(y - n_pe/2) / n_pe))
+ * in FP64.  image: [n_pe][2 * n_ro] doubles.  flags: MRSIM_PTR_DEVICE if
+ * signal and image are device pointers (row, col0, dir are host arrays).
+ * Errors: MRSIM_EINVAL (NULL, n_ro or n_pe odd or outside [2, 2048], a row or
+ * col0 out of range, dir not +-1), MRSIM_ENOMEM, MRSIM_ECUDA. */
+int mrsim_recon_cartesian(mrsim_ctx *ctx, int n_lines, int n_ro, int n_pe, const double *signal,
+                          const int32_t *row, const int32_t *col0, const int8_t *dir,
+                          unsigned flags, double *image);
+
 /* ------------------------------------------------------------------------
  * Learned with-RF transitions (MRSIM_SURROGATE mode).
  *

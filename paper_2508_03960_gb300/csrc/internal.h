@@ -66,7 +66,7 @@ struct mrsim_ctx {
     std::vector<Pending> prof_pending;
     std::vector<cudaEvent_t> ev_pool;
     // growable scratch areas reused across calls
-    mrsim::DBuf scratch[20];
+    mrsim::DBuf scratch[24];
     // error word written by kernels with bounded waits / bounds checks
     mrsim::DBuf dev_err;
     // pinned host staging for uploads of per-run plans

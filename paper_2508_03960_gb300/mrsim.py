@@ -32,7 +32,7 @@ TUNE_PRECOMP_STEPS = 4
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom", "mrsim_coils",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
-           "mrsim_run_batch", "mrsim_profile_enable", "mrsim_profile_reset",
+           "mrsim_run_batch", "mrsim_recon_cartesian", "mrsim_profile_enable", "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
            "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
@@ -67,6 +67,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_group_info": (I, [P, I, P, P]),
         "mrsim_run": (I, [P, P, P, P, I, I, P, P, U]),
         "mrsim_run_batch": (I, [P, I, P, P, P, P]),
+        "mrsim_recon_cartesian": (I, [P, I, I, I, P, P, P, P, U, P]),
         "mrsim_profile_enable": (I, [P, I]),
         "mrsim_profile_reset": (I, [P]),
         "mrsim_profile_get": (I, [P, I, P, I, P, P]),
@@ -215,6 +216,28 @@ def mrsim_run_batch(ctx, phs, seqs, groups, signals):
     rc = lib().mrsim_run_batch(ctx, n, A(*phs), A(*seqs), A(*groups),
                                A(*[_ptr(s) for s in signals]))
     _check(ctx, rc, "mrsim_run_batch")
+
+
+def mrsim_recon_cartesian(ctx, signal, layout, image=None, flags=0):
+    """Image [n_pe, n_ro] complex128 of one coil's signal (numpy, or torch
+    device tensors with flags=PTR_DEVICE) given a k-space layout dict
+    (n_ro, n_pe, row, col0, dir as from mrsim_inputs.kspace_layout)."""
+    n_ro, n_pe = int(layout["n_ro"]), int(layout["n_pe"])
+    row = np.ascontiguousarray(layout["row"], np.int32)
+    col0 = np.ascontiguousarray(layout["col0"], np.int32)
+    d = np.ascontiguousarray(layout["dir"], np.int8)
+    if image is None:
+        image = np.zeros((n_pe, 2 * n_ro), np.float64)
+    if isinstance(signal, np.ndarray):
+        signal = np.ascontiguousarray(signal)
+        if signal.dtype == np.complex128:
+            signal = signal.view(np.float64)
+    _check(ctx, lib().mrsim_recon_cartesian(ctx, len(row), n_ro, n_pe, _ptr(signal), _ptr(row),
+                                            _ptr(col0), _ptr(d), flags, _ptr(image)),
+           "mrsim_recon_cartesian")
+    if isinstance(image, np.ndarray):
+        return image.view(np.complex128).reshape(n_pe, n_ro)
+    return image
 
 
 def mrsim_profile_enable(ctx, on=True):
