@@ -444,11 +444,27 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
     MRSIM_CUDA(cudaMemcpyAsync(hb.data(), cb.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
     MRSIM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
     sync(c);
-    std::vector<int32_t> order(nc);
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int32_t u, int32_t v) {
-        return ha[u] != ha[v] ? ha[u] < ha[v] : hb[u] < hb[v];
-    });
+    // cells sorted by (primary gid, secondary gid): both are group ids below
+    // known bounds, so two stable counting passes (by the secondary id, then by
+    // the primary id) sort in linear time; the pairs are distinct, so the order
+    // is the unique sorted one
+    const int64_t Ga = g->n_groups[p], Gb = s >= 0 ? g->n_groups[s] : 1;
+    std::vector<int32_t> by_b(nc), order(nc);
+    {
+        std::vector<int64_t> pos(Gb + 1, 0);
+        for (int64_t i = 0; i < nc; ++i) ++pos[hb[i] + 1];
+        for (int64_t v = 0; v < Gb; ++v) pos[v + 1] += pos[v];
+        for (int64_t i = 0; i < nc; ++i) by_b[pos[hb[i]]++] = (int32_t)i;
+    }
+    {
+        std::vector<int64_t> pos(Ga + 1, 0);
+        for (int64_t i = 0; i < nc; ++i) ++pos[ha[i] + 1];
+        for (int64_t v = 0; v < Ga; ++v) pos[v + 1] += pos[v];
+        for (int64_t t = 0; t < nc; ++t) {
+            const int32_t i = by_b[t];
+            order[pos[ha[i]]++] = i;
+        }
+    }
     std::vector<int32_t> off(nc);
     int64_t run = 0;
     for (int64_t i = 0; i < nc; ++i) {
