@@ -451,13 +451,13 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
     const int64_t Ga = g->n_groups[p], Gb = s >= 0 ? g->n_groups[s] : 1;
     std::vector<int32_t> by_b(nc), order(nc);
     {
-        std::vector<int64_t> pos(Gb + 1, 0);
+        std::vector<int32_t> pos(Gb + 1, 0);
         for (int64_t i = 0; i < nc; ++i) ++pos[hb[i] + 1];
         for (int64_t v = 0; v < Gb; ++v) pos[v + 1] += pos[v];
         for (int64_t i = 0; i < nc; ++i) by_b[pos[hb[i]]++] = (int32_t)i;
     }
     {
-        std::vector<int64_t> pos(Ga + 1, 0);
+        std::vector<int32_t> pos(Ga + 1, 0);
         for (int64_t i = 0; i < nc; ++i) ++pos[ha[i] + 1];
         for (int64_t v = 0; v < Ga; ++v) pos[v + 1] += pos[v];
         for (int64_t t = 0; t < nc; ++t) {
