@@ -8,12 +8,13 @@ built from +, -, *, / and sqrt on float64 plus a seeded numpy Generator, so
 that the same seed yields bit-identical arrays on x86_64 and aarch64.
 """
 
-from .phantom import Phantom, coil_maps, ellipse_phantom, grid_phantom, phantom_digest
+from .phantom import (Phantom, coil_maps, ellipse_phantom, grid_phantom, mapped_phantom,
+                      phantom_digest)
 from .sequence import Sequence, SeqBuilder, sequence_digest, GAMMA_BAR_HZ_PER_T
 from . import configs
 
 __all__ = [
-    "Phantom", "coil_maps", "ellipse_phantom", "grid_phantom", "phantom_digest",
+    "Phantom", "coil_maps", "ellipse_phantom", "grid_phantom", "mapped_phantom", "phantom_digest",
     "Sequence", "SeqBuilder", "sequence_digest", "GAMMA_BAR_HZ_PER_T",
     "configs",
 ]

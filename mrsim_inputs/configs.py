@@ -15,6 +15,11 @@
                  round-robin SE / GRE (TR 10 ms, 30 deg) / FSE (ETL 8).
 * ``surrogate_fse`` FSE timing with 2 ms pulses at 10 us on the 32x32x4
                  geometry, per-isochromat dB0 and RF scale (seed 1005).
+* ``mapped_27m`` the FSE geometry (512x512 x 105) with T1 / T2 maps of a
+                 parameter-mapping stand-in: 16 ellipse regions, smooth +-40 %
+                 variation and 10 % noise, each value snapped to one of 100
+                 log-spaced candidates (seed 1006); the input of the
+                 clustering preprocessing.
 """
 
 from __future__ import annotations
@@ -24,7 +29,7 @@ from typing import Tuple
 
 import numpy as np
 
-from .phantom import Phantom, ellipse_phantom, continuous_phantom
+from .phantom import Phantom, ellipse_phantom, continuous_phantom, mapped_phantom
 from .sequence import Sequence, spin_echo_2d, fse_2d, epi_2d, gre_2d
 
 FULL_NX, FULL_NY, FULL_NZ = 512, 512, 105
@@ -96,3 +101,11 @@ def surrogate_fse(nx=32, ny=32, nz=4) -> Tuple[Phantom, Sequence]:
     seq = fse_2d(n_ro=32, n_pe=32, etl=8, rf_dur=2e-3, rf_dt=10e-6,
                  dwell=10e-6, esp=10e-3, tr=1.0, n_shots=4)
     return ph, seq
+
+
+def mapped_27m() -> Phantom:
+    return mapped_phantom(FULL_NX, FULL_NY, FULL_NZ, 16, seed=1006)
+
+
+def mapped_small(nx=64, ny=64, nz=4) -> Phantom:
+    return mapped_phantom(nx, ny, nz, 16, seed=1006)

@@ -232,3 +232,81 @@ def coil_maps(p: Phantom, n_coils: int, seed: int, fov: float = 0.256) -> np.nda
         out[c, 0] = (mag * cr).astype(np.float32)
         out[c, 1] = (mag * ci).astype(np.float32)
     return out
+
+
+def log_candidates(lo: float, hi: float, n: int) -> np.ndarray:
+    """n values spaced evenly in log between lo and hi (the candidate set of a
+    parameter-mapping search, Sec. 3.2: 100 values, 10-3000 ms for T1 and
+    10-500 ms for T2).  The ratio q = (hi/lo)^(1/(n-1)) is found by Newton's
+    method on q^(n-1) = hi/lo with products only, so the values are the same on
+    every platform."""
+    r = hi / lo
+    m = n - 1
+    q = 1.0 + 2.0 * (r - 1.0) / m if r < 2.0 else 2.0  # above the root
+    for _ in range(200):
+        p = 1.0
+        for _ in range(m - 1):
+            p *= q
+        q_new = q - (p * q - r) / (m * p)
+        if q_new == q:
+            break
+        q = q_new
+    c = np.empty(n)
+    c[0] = lo
+    for j in range(1, n):
+        c[j] = c[j - 1] * q
+    c[-1] = hi
+    return c
+
+
+def _snap(v: np.ndarray, cand: np.ndarray) -> np.ndarray:
+    """Nearest candidate in log distance: v goes to c_j when it lies between the
+    geometric midpoints sqrt(c_{j-1} c_j) and sqrt(c_j c_{j+1})."""
+    mids = np.sqrt(cand[:-1] * cand[1:])
+    return cand[np.searchsorted(mids, v, side="right")]
+
+
+def _smooth_field(X, Y, rng: np.random.Generator, fov: float, n_bumps: int = 3):
+    """Sum of seeded rational bumps a_j / (1 + |r - c_j|^2 / w_j^2), |field| <= 1."""
+    f = np.zeros_like(X)
+    for _ in range(n_bumps):
+        a = rng.uniform(-1.0, 1.0) / n_bumps
+        cx, cy = rng.uniform(-0.4, 0.4, size=2) * fov
+        w = rng.uniform(0.1, 0.3) * fov
+        f += a / (1.0 + ((X - cx) ** 2 + (Y - cy) ** 2) / (w * w))
+    return f
+
+
+def mapped_phantom(nx: int, ny: int, nz: int, n_ellipses: int, seed: int,
+                   fov: float = 0.256, slab: float = 0.020, n_cand: int = 100,
+                   db0_sigma_hz: float = 0.0) -> Phantom:
+    """Stand-in for a phantom made by parameter mapping (Sec. 3.2): per-pixel T1
+    and T2 maps that vary smoothly inside the ellipse regions (seeded rational
+    bumps, +-40 %) with 10 % pixel noise, each snapped to the nearest of
+    ``n_cand`` log-spaced candidates (10-3000 ms for T1, 10-500 ms for T2), M0
+    per region with a +-5 % smooth variation, and dB0 = 0 as in the paper's
+    evaluations (``db0_sigma_hz`` > 0 adds a smooth dB0 field of that scale
+    plus N(0, 1 %) noise, which makes almost every tuple distinct).  Such a
+    phantom has up to n_cand^2 distinct (T1, T2) pairs, which the clustering
+    preprocessing (Fig. 4) reduces."""
+    rng = np.random.default_rng(seed)
+    lab = ellipse_label_map(nx, ny, n_ellipses, fov, rng)
+    T1r, T2r, _, M0r = region_params(n_ellipses, rng)
+    xs, ys, zs = grid_coords(nx, ny, nz, fov, slab)
+    X, Y = np.meshgrid(xs, ys)  # [ny, nx]
+    g1, g2, g3 = (_smooth_field(X, Y, rng, fov) for _ in range(3))
+    n1, n2 = rng.normal(size=(2, ny, nx))
+    T1 = T1r[lab] * (1.0 + 0.4 * g1) * (1.0 + 0.1 * np.clip(n1, -3.0, 3.0))
+    T2 = T2r[lab] * (1.0 + 0.4 * g2) * (1.0 + 0.1 * np.clip(n2, -3.0, 3.0))
+    T1 = _snap(T1, log_candidates(0.010, 3.0, n_cand))
+    T2 = _snap(T2, log_candidates(0.010, 0.5, n_cand))
+    M0 = M0r[lab] * (1.0 + 0.05 * g3)
+    dB0 = np.zeros_like(X)
+    if db0_sigma_hz > 0.0:
+        g4 = _smooth_field(X, Y, rng, fov)
+        dB0 = db0_sigma_hz * (g4 + 0.01 * rng.normal(size=(ny, nx)))
+    zero = np.zeros(n_ellipses + 1)
+    d = _expand(lab, xs, ys, zs, (zero, zero, zero, zero))
+    rep = lambda a: np.ascontiguousarray(np.repeat(a.reshape(-1), nz), dtype=np.float32)
+    d.update(T1=rep(T1), T2=rep(T2), dB0=rep(dB0), M0=rep(M0))
+    return Phantom(shape=(ny, nx, nz), **d)
