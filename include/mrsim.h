@@ -107,6 +107,13 @@ int mrsim_phantom(mrsim_ctx *ctx, int64_t K, const float *x, const float *y, con
                   const float *b1_scale, const float *M_init, unsigned flags,
                   mrsim_phantom_t **out);
 
+/* Copy a phantom's arrays back to the host (each float32 [K]; a NULL
+ * destination is skipped), e.g. the centre values and refitted M0 made by
+ * mrsim_cluster.  Errors: MRSIM_EINVAL (NULL ctx or ph), MRSIM_ESTATE
+ * (phantom of another context), MRSIM_ECUDA. */
+int mrsim_phantom_read(mrsim_ctx *ctx, const mrsim_phantom_t *ph, float *x, float *y, float *z,
+                       float *T1_s, float *T2_s, float *dB0_hz, float *M0);
+
 /* Attach the complex receive sensitivities of n_coils coils to a phantom
  * (Eq. 6: A(p, t) = sum_k S(k, p) M_xy(k, t); S constant in time).  sens:
  * float32 [n_coils][2][K]: for coil p, K real parts then K imaginary parts, in
@@ -187,6 +194,47 @@ int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
 int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph,
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);
+
+/* Group-reducing preprocessing (Sec. 3.3, Fig. 4): cluster the isochromats'
+ * (T1, T2, dB0) with a bisecting K-means and return a new phantom in which
+ * every isochromat carries its cluster's centre values, so that the groups of
+ * Sec. 2.4 number at most n_clusters per position (per no-grads type: at most
+ * n_clusters in all).
+ *  - Space: integer features x_i = rint(v_i * scale_i) of v = (T1 s, T2 s,
+ *    dB0 Hz); scale NULL => {64000, 64000, 64} (1/64 ms and 1/64 Hz steps, one
+ *    ms weighing as much as one Hz).  Every |x_i| must be <= 2^20 and x_T1,
+ *    x_T2 >= 1 (T1, T2 finite).  Sums over features are exact integers.
+ *  - Splits: the cluster with the largest sum of squared distances to its
+ *    mean (exact comparison; ties: smaller id) is split by 2-means (Lloyd)
+ *    started from the member farthest from its mean and the member farthest
+ *    from that one (ties: smallest isochromat index); a member goes to the
+ *    new side when strictly nearer its centre; passes repeat until the FP64
+ *    centres repeat exactly or max_iter passes (a pass leaving a side empty
+ *    is dropped).  The old id keeps one side, the new side gets the next id
+ *    (ids 0..n-1 in order of creation).  Stops early, with n < n_clusters,
+ *    when every cluster holds one distinct feature value.
+ *  - Values: centre_i = (sum x_i / count) / scale_i in FP64 (written to
+ *    centres), stored as float32 in the new phantom.
+ *  - M0 refit: with n_echo > 0 echo times te_s[e] and repetition time tr_s of
+ *    a T2-weighted spin-echo model f_e(T1, T2) = (1 - exp(-tr/T1)) exp(-te_e/T2)
+ *    (the paper's T2W scan: TR 4.5 s, TE 20/60/100/140 ms), the new M0 is the
+ *    least-squares fit of the modelled images M0 f_e(T1, T2) with the centre
+ *    values: M0' = sum_e M0 f_e(T1, T2) f_e(c) / sum_e f_e(c)^2 (FP64); n_echo
+ *    = 0 keeps M0.
+ * Positions, b1, M_init and receive coils are copied.  labels: host int32 [K]
+ * (cluster id per isochromat) or NULL; centres: host double [n_clusters][3]
+ * (T1 s, T2 s, dB0 Hz; the first n rows written) or NULL; n_out: n, or NULL.
+ * The new phantom is released with mrsim_free_phantom.
+ * Errors: MRSIM_EINVAL (NULL ctx/ph/out, n_clusters outside [1,
+ * MRSIM_MAX_CLUSTERS], max_iter < 1, scale not finite and > 0, n_echo outside
+ * [0, MRSIM_MAX_ECHOES], te not finite >= 0, tr not finite > 0, K > 2^28, a
+ * feature out of range), MRSIM_ESTATE (phantom of another context),
+ * MRSIM_ENOMEM, MRSIM_ECUDA. */
+#define MRSIM_MAX_CLUSTERS 4096
+#define MRSIM_MAX_ECHOES 16
+int mrsim_cluster(mrsim_ctx *ctx, const mrsim_phantom_t *ph, int n_clusters, const double *scale,
+                  int max_iter, int n_echo, const double *te_s, double tr_s, int32_t *labels,
+                  double *centres, int *n_out, mrsim_phantom_t **out);
 
 /* Image of one coil's Cartesian k-space signal: the centred, normalised
  * inverse DFT the paper applies to its SE / FSE data ("Simulations #1"; an

@@ -18,8 +18,10 @@
 * ``mapped_27m`` the FSE geometry (512x512 x 105) with T1 / T2 maps of a
                  parameter-mapping stand-in: 16 ellipse regions, smooth +-40 %
                  variation and 10 % noise, each value snapped to one of 100
-                 log-spaced candidates (seed 1006); the input of the
-                 clustering preprocessing.
+                 log-spaced candidates, and a smooth dB0 field of scale 20 Hz
+                 with 1 % noise (seed 1006); the input of the clustering
+                 preprocessing (db0_sigma_hz=0: dB0 = 0 as in the paper's
+                 evaluations).
 """
 
 from __future__ import annotations
@@ -103,9 +105,9 @@ def surrogate_fse(nx=32, ny=32, nz=4) -> Tuple[Phantom, Sequence]:
     return ph, seq
 
 
-def mapped_27m() -> Phantom:
-    return mapped_phantom(FULL_NX, FULL_NY, FULL_NZ, 16, seed=1006)
+def mapped_27m(db0_sigma_hz: float = 20.0) -> Phantom:
+    return mapped_phantom(FULL_NX, FULL_NY, FULL_NZ, 16, seed=1006, db0_sigma_hz=db0_sigma_hz)
 
 
-def mapped_small(nx=64, ny=64, nz=4) -> Phantom:
-    return mapped_phantom(nx, ny, nz, 16, seed=1006)
+def mapped_small(nx=64, ny=64, nz=4, db0_sigma_hz: float = 20.0) -> Phantom:
+    return mapped_phantom(nx, ny, nz, 16, seed=1006, db0_sigma_hz=db0_sigma_hz)

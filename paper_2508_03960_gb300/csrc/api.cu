@@ -1076,6 +1076,77 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
     });
 }
 
+int mrsim_phantom_read(mrsim_ctx *c, const mrsim_phantom_t *ph, float *x, float *y, float *z,
+                       float *T1, float *T2, float *dB0, float *M0) {
+    if (!c) return MRSIM_EINVAL;
+    return guard(c, [&] {
+        if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
+        if (ph->ctx != c) fail(MRSIM_ESTATE, "phantom of another context");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        const size_t b = ph->K * sizeof(float);
+        const std::pair<float *, const DBuf *> f[7] = {{x, &ph->x},   {y, &ph->y},     {z, &ph->z},
+                                                       {T1, &ph->T1}, {T2, &ph->T2},   {dB0, &ph->dB0},
+                                                       {M0, &ph->M0}};
+        for (const auto &e : f)
+            if (e.first)
+                MRSIM_CUDA(cudaMemcpyAsync(e.first, e.second->p, b, cudaMemcpyDeviceToHost,
+                                           c->stream));
+        sync(c);
+    });
+}
+
+int mrsim_cluster(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters, const double *scale,
+                  int max_iter, int n_echo, const double *te, double tr, int32_t *labels,
+                  double *centres, int *n_out, mrsim_phantom_t **out) {
+    if (!c || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n_out) *n_out = 0;
+    auto p = std::unique_ptr<mrsim_phantom_t>(new (std::nothrow) mrsim_phantom_t());
+    if (!p) return set_err(c, MRSIM_ENOMEM, "host allocation failed");
+    int n = 0;
+    int rc = guard(c, [&] {
+        if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
+        if (ph->ctx != c) fail(MRSIM_ESTATE, "phantom of another context");
+        if (n_clusters < 1 || n_clusters > MRSIM_MAX_CLUSTERS)
+            fail(MRSIM_EINVAL,
+                 "n_clusters must be in [1, " + std::to_string(MRSIM_MAX_CLUSTERS) + "]");
+        if (max_iter < 1) fail(MRSIM_EINVAL, "max_iter must be positive");
+        const double def[3] = {64000.0, 64000.0, 64.0};
+        const double *sc = scale ? scale : def;
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(sc[i]) || !(sc[i] > 0.0))
+                fail(MRSIM_EINVAL, "scale must be finite and positive");
+        if (n_echo < 0 || n_echo > MRSIM_MAX_ECHOES)
+            fail(MRSIM_EINVAL, "n_echo must be in [0, " + std::to_string(MRSIM_MAX_ECHOES) + "]");
+        if (n_echo > 0) {
+            if (!te) fail(MRSIM_EINVAL, "NULL echo times");
+            for (int e = 0; e < n_echo; ++e)
+                if (!std::isfinite(te[e]) || te[e] < 0.0)
+                    fail(MRSIM_EINVAL, "echo times must be finite and >= 0");
+            if (!std::isfinite(tr) || !(tr > 0.0))
+                fail(MRSIM_EINVAL, "repetition time must be finite and positive");
+        }
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        DBuf lab;
+        std::vector<double> cen;
+        cluster_phantom(c, ph, n_clusters, sc, max_iter, n_echo, te, tr, p.get(), lab, cen);
+        n = (int)(cen.size() / 3);
+        p->ctx = c;
+        p->uid = g_uid++;
+        if (labels) {
+            MRSIM_CUDA(cudaMemcpyAsync(labels, lab.p, ph->K * sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, c->stream));
+            sync(c);
+        }
+        if (centres) std::copy(cen.begin(), cen.end(), centres);
+    });
+    if (rc == MRSIM_OK) {
+        *out = p.release();
+        if (n_out) *n_out = n;
+    }
+    return rc;
+}
+
 int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t *rep,
                    const float *b1re, const float *b1im, const float *gx, const float *gy,
                    const float *gz, const uint8_t *adc, mrsim_seq **out) {

@@ -218,7 +218,21 @@ bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid,
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab);
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
+// Distinct integer triples (x[k], x[K + k], x[2K + k]) of K elements: id[k] in
+// [0, U) numbered by first occurrence, table [3][U] of their values and
+// count [U] of their occurrences.  Returns U.  Uses scratch slots 0-5.
+int64_t distinct_triples(mrsim_ctx *c, int64_t K, const int32_t *x, int32_t *id, DBuf &table,
+                         DBuf &count);
 constexpr int64_t kMaxAxisValues = 65535;
+// Group-reducing preprocessing (k_cluster.cu): fills `out` (a phantom with the
+// cluster centre values and the refitted M0; positions, b1, M_init and coils
+// copied), `labels` (device int32 [K]) and `centres` (host [n][3]: T1 s, T2 s,
+// dB0 Hz, FP64) for the n <= n_clusters clusters made.  Arguments checked by
+// the caller.
+constexpr int64_t kMaxClusterK = 1LL << 28;
+void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
+                     const double scale[3], int max_iter, int n_echo, const double *te, double tr,
+                     mrsim_phantom_t *out, DBuf &labels, std::vector<double> &centres);
 void build_axis_index(mrsim_ctx *c, mrsim_groups *g);
 // out[i] = in[perm[i]] for i < K (float32)
 void launch_gather_f32(mrsim_ctx *c, int64_t K, const int32_t *perm, const float *in, float *out);

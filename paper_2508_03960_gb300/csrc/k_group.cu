@@ -63,6 +63,18 @@ struct AxisKey {
     }
 };
 
+// Integer triple key (the quantized clustering features).
+struct TripleKey {
+    static constexpr int W = 3;
+    const int32_t *x0, *x1, *x2;
+    __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
+        w[0] = (uint32_t)x0[k];
+        w[1] = (uint32_t)x1[k];
+        w[2] = (uint32_t)x2[k];
+        return true;
+    }
+};
+
 // (gid_a, gid_b) pair key for the layout cells.
 struct PairKey {
     static constexpr int W = 2;
@@ -224,6 +236,19 @@ __global__ void k_group_table(int64_t K, const int32_t *flag, const int32_t *ran
         o_T2[g] = T2[k];
         o_dB0[g] = dB0[k];
         o_b1[g] = b1 ? (double)b1[k] : 1.0;
+    }
+}
+
+// values of the distinct triples from their representatives
+__global__ void k_triple_table(int64_t K, const int32_t *flag, const int32_t *rank,
+                               const int32_t *x, int32_t *tab, int64_t U) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        const int32_t u = rank[k];
+        tab[u] = x[k];
+        tab[U + u] = x[K + k];
+        tab[2 * U + u] = x[2 * K + k];
     }
 }
 
@@ -549,6 +574,25 @@ void build_axis_index(mrsim_ctx *c, mrsim_groups *g) {
     }
     sync(c);
     g->ax_ok = true;
+}
+
+int64_t distinct_triples(mrsim_ctx *c, int64_t K, const int32_t *x, int32_t *id, DBuf &table,
+                         DBuf &count) {
+    int32_t *flag, *rank;
+    const int64_t U = hash_group(c, K, TripleKey{x, x + K, x + 2 * K}, id, &flag, &rank);
+    table = dalloc(3 * U * sizeof(int32_t));
+    count = dalloc(U * sizeof(int32_t));
+    MRSIM_CUDA(cudaMemsetAsync(count.p, 0, U * sizeof(int32_t), c->stream));
+    {
+        KScope ks(c, "triple_table");
+        k_triple_table<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, x,
+                                                              table.as<int32_t>(), U);
+    }
+    {
+        KScope ks(c, "triple_count");
+        k_count<<<grid_for(c, K), 256, 0, c->stream>>>(K, id, count.as<int32_t>());
+    }
+    return U;
 }
 
 void launch_gather_f32(mrsim_ctx *c, int64_t K, const int32_t *perm, const float *in,

@@ -30,9 +30,11 @@ TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1
 TUNE_PRECOMP_STEPS = 4
 
 # every entry point declared in include/mrsim.h
-EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom", "mrsim_coils",
+EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
+           "mrsim_phantom_read", "mrsim_coils",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
-           "mrsim_run_batch", "mrsim_recon_cartesian", "mrsim_profile_enable", "mrsim_profile_reset",
+           "mrsim_run_batch", "mrsim_recon_cartesian", "mrsim_cluster", "mrsim_profile_enable",
+           "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
            "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
@@ -40,6 +42,12 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
 MAX_COILS = 64
+MAX_CLUSTERS = 4096
+MAX_ECHOES = 16
+# the paper's T2-weighted scan (Table 1: FSE, TR 4500 ms, TE 20/60/100/140 ms),
+# the default model of the M0 refit after clustering
+T2W_TE = (0.020, 0.060, 0.100, 0.140)
+T2W_TR = 4.5
 
 
 class MrsimError(RuntimeError):
@@ -62,12 +70,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_phantom": (I, [P, I64] + [P] * 9 + [U, PP]),
         "mrsim_sequence": (I, [P, I64] + [P] * 8 + [PP]),
         "mrsim_coils": (I, [P, P, I, P, U]),
+        "mrsim_phantom_read": (I, [P] * 9),
         "mrsim_seq_info": (I, [P] * 7),
         "mrsim_group": (I, [P, P, P, PP]),
         "mrsim_group_info": (I, [P, I, P, P]),
         "mrsim_run": (I, [P, P, P, P, I, I, P, P, U]),
         "mrsim_run_batch": (I, [P, I, P, P, P, P]),
         "mrsim_recon_cartesian": (I, [P, I, I, I, P, P, P, P, U, P]),
+        "mrsim_cluster": (I, [P, P, I, P, I, I, P, ctypes.c_double, P, P, P, PP]),
         "mrsim_profile_enable": (I, [P, I]),
         "mrsim_profile_reset": (I, [P]),
         "mrsim_profile_get": (I, [P, I, P, I, P, P]),
@@ -145,6 +155,15 @@ def mrsim_phantom(ctx, K, x, y, z, T1, T2, dB0, M0, b1=None, M_init=None, flags=
                              flags, ctypes.byref(h))
     _check(ctx, rc, "mrsim_phantom")
     return h.value
+
+
+def mrsim_phantom_read(ctx, ph, K, fields=("T1", "T2", "dB0", "M0")):
+    """Dict of the requested phantom arrays (float32 [K]) copied to the host."""
+    names = ("x", "y", "z", "T1", "T2", "dB0", "M0")
+    out = {n: np.empty(K, np.float32) for n in fields}
+    _check(ctx, lib().mrsim_phantom_read(ctx, ph, *[_ptr(out.get(n)) for n in names]),
+           "mrsim_phantom_read")
+    return out
 
 
 def mrsim_sequence(ctx, n_seg, dt, repeat, b1re, b1im, gx, gy, gz, adc) -> int:
@@ -238,6 +257,24 @@ def mrsim_recon_cartesian(ctx, signal, layout, image=None, flags=0):
     if isinstance(image, np.ndarray):
         return image.view(np.complex128).reshape(n_pe, n_ro)
     return image
+
+
+def mrsim_cluster(ctx, ph, K, n_clusters, scale=None, max_iter=300, te=T2W_TE, tr=T2W_TR,
+                  want_labels=True):
+    """Group-reducing preprocessing of phantom ``ph`` (K isochromats).
+    Returns (new phantom handle, number of clusters n, labels int32 [K] or
+    None, centres float64 [n, 3] as T1 s, T2 s, dB0 Hz)."""
+    labels = np.empty(K, np.int32) if want_labels else None
+    centres = np.zeros((max(n_clusters, 1), 3), np.float64)
+    sc = None if scale is None else np.ascontiguousarray(scale, np.float64)
+    te = np.ascontiguousarray(te, np.float64)
+    n = ctypes.c_int(0)
+    out = ctypes.c_void_p()
+    rc = lib().mrsim_cluster(ctx, ph, n_clusters, _ptr(sc), max_iter, len(te),
+                             _ptr(te) if len(te) else None, float(tr), _ptr(labels),
+                             _ptr(centres), ctypes.byref(n), ctypes.byref(out))
+    _check(ctx, rc, "mrsim_cluster")
+    return out.value, n.value, labels, centres[: n.value].copy()
 
 
 def mrsim_profile_enable(ctx, on=True):
@@ -398,6 +435,15 @@ class Context:
                 self._coils[h] = mrsim_coils(self.h, h, p.coils)
         self._handles.append(("ph", h))
         return h
+
+    def cluster(self, ph: int, K: int, n_clusters: int, **kw):
+        """mrsim_cluster on an uploaded phantom; the new phantom is owned by
+        this context (receive coils carried over)."""
+        h, n, labels, centres = mrsim_cluster(self.h, ph, K, n_clusters, **kw)
+        self._handles.append(("ph", h))
+        if self._coils.get(ph):
+            self._coils[h] = self._coils[ph]
+        return h, n, labels, centres
 
     def sequence(self, s) -> int:
         keep = [np.ascontiguousarray(s.dt, np.float64), np.ascontiguousarray(s.repeat, np.int32),
