@@ -762,8 +762,8 @@ def main():
 
     ck = clustering.get("kernels", {})
     hbm_peak = pk.get("hbm_gbs", 6800.0)
-    for kname, bpi, note in (("cluster_apply", 36, "uid 4 + T1, T2, M0 12 read, T1, T2, dB0, "
-                                                    "M0 16 + label 4 written"),
+    for kname, bpi, note in (("cluster_apply", 28, "key id 4 + M0 4 read, T1, T2, dB0, M0 16 "
+                                                    "+ label 4 written"),
                              ("cluster_quantize", 24, "T1, T2, dB0 12 read, 3 features 12 "
                                                       "written")):
         if kname in ck:

@@ -218,11 +218,12 @@ bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid,
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab);
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
-// Distinct integer triples (x[k], x[K + k], x[2K + k]) of K elements: id[k] in
-// [0, U) numbered by first occurrence, table [3][U] of their values and
-// count [U] of their occurrences.  Returns U.  Uses scratch slots 0-5.
-int64_t distinct_triples(mrsim_ctx *c, int64_t K, const int32_t *x, int32_t *id, DBuf &table,
-                         DBuf &count);
+// Distinct keys (x[k], x[K + k], x[2K + k], bits of T1[k], bits of T2[k]) of K
+// elements: id[k] in [0, U) numbered by first occurrence, table [3][U] of the
+// integer words, tf [2][U] of T1 and T2, count [U] of occurrences.  Returns U.
+// Uses scratch slots 0-5.
+int64_t distinct_features(mrsim_ctx *c, int64_t K, const int32_t *x, const float *T1,
+                          const float *T2, int32_t *id, DBuf &table, DBuf &tf, DBuf &count);
 constexpr int64_t kMaxAxisValues = 65535;
 // Group-reducing preprocessing (k_cluster.cu): fills `out` (a phantom with the
 // cluster centre values and the refitted M0; positions, b1, M_init and coils

@@ -11,9 +11,10 @@
 // partition does not depend on the launch configuration.
 //
 // Isochromats with equal features always fall on the same side, so the
-// clustering runs over the U distinct feature triples, each weighted by its
-// number of isochromats; triples are numbered by first occurrence, so "the
-// smallest isochromat index" in the tie rules is "the smallest triple id".
+// clustering runs over the U distinct keys (features, T1 and T2 bit patterns;
+// the latter for the M0 refit), each weighted by its number of isochromats;
+// keys are numbered by first occurrence, so "the smallest isochromat index" in
+// the tie rules is "the smallest key id".
 //
 // One split of cluster c (the one with the largest SSE, ties to the smaller
 // id; SSEs are compared as exact rationals on the host):
@@ -45,7 +46,7 @@ struct ClStats {
 struct ClWork {
     double cen[6];                // centres of side 0 and side 1, feature units
     unsigned long long dmax[2];   // farthest-member searches: largest distance
-    int32_t umin[2];              // ... and the smallest triple id at it
+    int32_t umin[2];              // ... and the smallest key id at it
     ClStats st[2];
 };
 
@@ -206,7 +207,7 @@ __global__ void k_cl_pick_mean(int64_t U, const int32_t *lab, int32_t c, const i
     }
 }
 
-// exact squared distance of triple u to triple a
+// exact squared distance of the features of key u to those of key a
 __device__ __forceinline__ long long cl_dist_int(const int32_t *tx, int64_t U, int64_t u,
                                                  int32_t a) {
     long long d = 0;
@@ -268,9 +269,11 @@ __global__ void k_cl_label(int64_t U, int32_t *lab, int32_t c, int32_t id_new, c
     }
 }
 
-// Every isochromat takes its cluster's centre values; M0 is refitted:
-// M0' = sum_e I_e f_e(c) / sum_e f_e(c)^2 with I_e = M0 f_e(T1, T2) and
-// f_e(T1, T2) = (1 - exp(-TR / T1)) exp(-TE_e / T2), summed over echoes in order.
+// M0 refit: M0' = sum_e I_e f_e(c) / sum_e f_e(c)^2 with I_e = M0 f_e(T1, T2)
+// and f_e(T1, T2) = (1 - exp(-TR / T1)) exp(-TE_e / T2), i.e. M0' = M0 r with
+// r = sum_e f_e(T1, T2) f_e(c) / sum_e f_e(c)^2.  r depends on the exact T1, T2
+// and the cluster only, so it is formed once per distinct key (FP64, echoes
+// summed in order) and the isochromat pass is a gather.
 struct EchoModel {
     int n;
     double tr;
@@ -281,31 +284,53 @@ __device__ __forceinline__ double t2w(double tr, double te, double T1, double T2
     return __dmul_rn(__dsub_rn(1.0, exp(__ddiv_rn(-tr, T1))), exp(__ddiv_rn(-te, T2)));
 }
 
+// per cluster: f_e(c) for every echo and sum_e f_e(c)^2
+__global__ void k_cl_model(int n, const float *cT1, const float *cT2, EchoModel em, double *fc,
+                           double *den) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int e = 0; e < em.n; ++e) {
+            const double f = t2w(em.tr, em.te[e], (double)cT1[c], (double)cT2[c]);
+            fc[(int64_t)c * MRSIM_MAX_ECHOES + e] = f;
+            d = __dadd_rn(d, __dmul_rn(f, f));
+        }
+        den[c] = d;
+    }
+}
+
+// per distinct key: the refit factor r (1 where there is no echo or den = 0)
+__global__ void k_cl_ratio(int64_t U, const float *tf, const int32_t *lab, const double *fc,
+                           const double *den, EchoModel em, double *ratio) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = lab[u];
+        const double T1 = (double)tf[u], T2 = (double)tf[U + u], d = em.n ? den[c] : 0.0;
+        double r = 1.0;
+        if (d > 0.0) {
+            double num = 0.0;
+            for (int e = 0; e < em.n; ++e)
+                num = __dadd_rn(num, __dmul_rn(t2w(em.tr, em.te[e], T1, T2),
+                                               fc[(int64_t)c * MRSIM_MAX_ECHOES + e]));
+            r = __ddiv_rn(num, d);
+        }
+        ratio[u] = r;
+    }
+}
+
+// every isochromat takes its cluster's centre values and M0 r
 __global__ void k_cl_apply(int64_t K, const int32_t *uid, const int32_t *lab, const float *cT1,
-                           const float *cT2, const float *cdB0, const float *T1, const float *T2,
-                           const float *M0, EchoModel em, float *oT1, float *oT2, float *odB0,
-                           float *oM0, int32_t *olab) {
+                           const float *cT2, const float *cdB0, const double *ratio,
+                           const float *M0, float *oT1, float *oT2, float *odB0, float *oM0,
+                           int32_t *olab) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = lab[uid[k]];
-        const float t1c = cT1[c], t2c = cT2[c];
+        const int32_t u = uid[k];
+        const int32_t c = lab[u];
         olab[k] = c;
-        oT1[k] = t1c;
-        oT2[k] = t2c;
+        oT1[k] = cT1[c];
+        oT2[k] = cT2[c];
         odB0[k] = cdB0[c];
-        const double m0 = (double)M0[k];
-        float out = M0[k];
-        if (em.n > 0) {
-            double num = 0.0, den = 0.0;
-            for (int e = 0; e < em.n; ++e) {
-                const double fo = t2w(em.tr, em.te[e], (double)T1[k], (double)T2[k]);
-                const double fc = t2w(em.tr, em.te[e], (double)t1c, (double)t2c);
-                num = __dadd_rn(num, __dmul_rn(__dmul_rn(m0, fo), fc));
-                den = __dadd_rn(den, __dmul_rn(fc, fc));
-            }
-            if (den > 0.0) out = (float)__ddiv_rn(num, den);
-        }
-        oM0[k] = out;
+        oM0[k] = (float)__dmul_rn((double)M0[k], ratio[u]);
     }
 }
 
@@ -363,10 +388,11 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
     if (h_err)
         fail(MRSIM_EINVAL, "a T1, T2 or dB0 value is not finite, outside +-2^20 clustering "
                            "steps, or (T1, T2) below one step");
-    // distinct triples with their weights
+    // distinct keys with their weights
     DBuf uid = dalloc(K * sizeof(int32_t));
-    DBuf tx, wt;
-    const int64_t U = distinct_triples(c, K, xq.as<int32_t>(), uid.as<int32_t>(), tx, wt);
+    DBuf tx, tf, wt;
+    const int64_t U = distinct_features(c, K, xq.as<int32_t>(), ph->T1.as<float>(),
+                                        ph->T2.as<float>(), uid.as<int32_t>(), tx, tf, wt);
     DBuf lab = dalloc(U * sizeof(int32_t));
     MRSIM_CUDA(cudaMemsetAsync(lab.p, 0, U * sizeof(int32_t), c->stream));
     DBuf work = dalloc(sizeof(ClWork));
@@ -394,7 +420,7 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
                                    c->stream));
     };
 
-    // cluster 0: every triple (equal centres put every member on side 0)
+    // cluster 0: every key (equal centres put every member on side 0)
     std::vector<Cluster> cl(1);
     {
         const double zero[6] = {0, 0, 0, 0, 0, 0};
@@ -461,11 +487,23 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
         }
     DBuf dcf = dalloc(cf.size() * sizeof(float));
     upload(c, dcf.p, cf.data(), cf.size() * sizeof(float));
-    // the new phantom
+    // the M0 refit factor of every distinct key
     EchoModel em{};
     em.n = n_echo;
     em.tr = tr;
     for (int e = 0; e < n_echo; ++e) em.te[e] = te[e];
+    DBuf fc = dalloc((size_t)n * MRSIM_MAX_ECHOES * sizeof(double));
+    DBuf den = dalloc((size_t)n * sizeof(double));
+    DBuf ratio = dalloc(U * sizeof(double));
+    {
+        KScope ks(c, "cluster_refit");
+        const float *pc = dcf.as<float>();
+        k_cl_model<<<(n + kClThreads - 1) / kClThreads, kClThreads, 0, c->stream>>>(
+            n, pc, pc + n, em, fc.as<double>(), den.as<double>());
+        k_cl_ratio<<<gU, kClThreads, 0, c->stream>>>(U, tf.as<float>(), plab, fc.as<double>(),
+                                                     den.as<double>(), em, ratio.as<double>());
+    }
+    // the new phantom
     auto copy = [&](DBuf &dst, const DBuf &src, size_t bytes) {
         dst = dalloc(bytes);
         MRSIM_CUDA(cudaMemcpyAsync(dst.p, src.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -490,9 +528,9 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
         KScope ks(c, "cluster_apply");
         const float *pc = dcf.as<float>();
         k_cl_apply<<<grid(c, K), kClThreads, 0, c->stream>>>(
-            K, uid.as<int32_t>(), plab, pc, pc + n, pc + 2 * n, ph->T1.as<float>(),
-            ph->T2.as<float>(), ph->M0.as<float>(), em, out->T1.as<float>(), out->T2.as<float>(),
-            out->dB0.as<float>(), out->M0.as<float>(), labels.as<int32_t>());
+            K, uid.as<int32_t>(), plab, pc, pc + n, pc + 2 * n, ratio.as<double>(),
+            ph->M0.as<float>(), out->T1.as<float>(), out->T2.as<float>(), out->dB0.as<float>(),
+            out->M0.as<float>(), labels.as<int32_t>());
     }
     sync(c);
 }

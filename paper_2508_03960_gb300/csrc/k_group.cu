@@ -63,14 +63,19 @@ struct AxisKey {
     }
 };
 
-// Integer triple key (the quantized clustering features).
-struct TripleKey {
-    static constexpr int W = 3;
-    const int32_t *x0, *x1, *x2;
+// Clustering key: the three integer features and the float32 bit patterns of
+// T1 and T2 (which the M0 refit needs exactly).
+struct FeatureKey {
+    static constexpr int W = 5;
+    const int32_t *x;
+    const float *T1, *T2;
+    int64_t K;
     __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
-        w[0] = (uint32_t)x0[k];
-        w[1] = (uint32_t)x1[k];
-        w[2] = (uint32_t)x2[k];
+        w[0] = (uint32_t)x[k];
+        w[1] = (uint32_t)x[K + k];
+        w[2] = (uint32_t)x[2 * K + k];
+        w[3] = __float_as_uint(T1[k]);
+        w[4] = __float_as_uint(T2[k]);
         return true;
     }
 };
@@ -239,9 +244,10 @@ __global__ void k_group_table(int64_t K, const int32_t *flag, const int32_t *ran
     }
 }
 
-// values of the distinct triples from their representatives
-__global__ void k_triple_table(int64_t K, const int32_t *flag, const int32_t *rank,
-                               const int32_t *x, int32_t *tab, int64_t U) {
+// values of the distinct feature keys from their representatives
+__global__ void k_feature_table(int64_t K, const int32_t *flag, const int32_t *rank,
+                                const int32_t *x, const float *T1, const float *T2, int32_t *tab,
+                                float *tf, int64_t U) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[k]) continue;
@@ -249,6 +255,8 @@ __global__ void k_triple_table(int64_t K, const int32_t *flag, const int32_t *ra
         tab[u] = x[k];
         tab[U + u] = x[K + k];
         tab[2 * U + u] = x[2 * K + k];
+        tf[u] = T1[k];
+        tf[U + u] = T2[k];
     }
 }
 
@@ -576,20 +584,21 @@ void build_axis_index(mrsim_ctx *c, mrsim_groups *g) {
     g->ax_ok = true;
 }
 
-int64_t distinct_triples(mrsim_ctx *c, int64_t K, const int32_t *x, int32_t *id, DBuf &table,
-                         DBuf &count) {
+int64_t distinct_features(mrsim_ctx *c, int64_t K, const int32_t *x, const float *T1,
+                          const float *T2, int32_t *id, DBuf &table, DBuf &tf, DBuf &count) {
     int32_t *flag, *rank;
-    const int64_t U = hash_group(c, K, TripleKey{x, x + K, x + 2 * K}, id, &flag, &rank);
+    const int64_t U = hash_group(c, K, FeatureKey{x, T1, T2, K}, id, &flag, &rank);
     table = dalloc(3 * U * sizeof(int32_t));
+    tf = dalloc(2 * U * sizeof(float));
     count = dalloc(U * sizeof(int32_t));
     MRSIM_CUDA(cudaMemsetAsync(count.p, 0, U * sizeof(int32_t), c->stream));
     {
-        KScope ks(c, "triple_table");
-        k_triple_table<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, x,
-                                                              table.as<int32_t>(), U);
+        KScope ks(c, "feature_table");
+        k_feature_table<<<grid_for(c, K), 256, 0, c->stream>>>(
+            K, flag, rank, x, T1, T2, table.as<int32_t>(), tf.as<float>(), U);
     }
     {
-        KScope ks(c, "triple_count");
+        KScope ks(c, "feature_count");
         k_count<<<grid_for(c, K), 256, 0, c->stream>>>(K, id, count.as<int32_t>());
     }
     return U;
