@@ -501,6 +501,8 @@ def main():
                     help="one small run of each kernel besides the fused one, in this order: "
                          "plain EPI, grouped FSE, surrogate FSE on a continuous phantom "
                          "(for ncu captures; prints their CUDA-event times)")
+    ap.add_argument("--profile-cluster", action="store_true",
+                    help="time the clustering preprocessing kernels (27.5M, 256 clusters)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
 
@@ -510,6 +512,9 @@ def main():
 
     from mrsim_inputs import configs, phantom_digest, sequence_digest
 
+    if a.profile_cluster:
+        profile_cluster(a, configs)
+        return
     if a.profile_kernels:
         profile_kernels(a, configs)
         return
@@ -878,6 +883,30 @@ def profile_kernels(a, configs):
     mrsim.mrsim_free_surrogate(sur)
     ctx.close()
     print(json.dumps({"profile_kernels": out, "K": ph.K}))
+
+
+def profile_cluster(a, configs):
+    """The clustering preprocessing of the 27.5M-isochromat parameter-mapping
+    phantom into 256 clusters, twice; prints the wall time and the per-kernel
+    CUDA-event times of the second call."""
+    import torch
+    from paper_2508_03960_gb300 import mrsim
+    torch.cuda.set_device(0)
+    ph = configs.mapped_27m()
+    ctx = mrsim.Context(0, torch.cuda.current_stream().cuda_stream)
+    hp = ctx.phantom(ph)
+    ctx.cluster(hp, ph.K, 256, want_labels=False)
+    torch.cuda.synchronize()
+    mrsim.mrsim_profile_reset(ctx.h)
+    mrsim.mrsim_profile_enable(ctx.h, True)
+    t = time.perf_counter()
+    _, n, _, _ = ctx.cluster(hp, ph.K, 256, want_labels=False)
+    wall = time.perf_counter() - t
+    prof = {k: [int(v[0]), round(v[1], 4)] for k, v in mrsim.mrsim_profile_get(ctx.h).items()
+            if v[0]}
+    ctx.close()
+    print(json.dumps({"profile_cluster": prof, "wall_s": round(wall, 4), "n_clusters": n,
+                      "K": ph.K}))
 
 
 def reference_arm(a, configs):
