@@ -141,9 +141,11 @@ class SeqBuilder:
             self.add(raster, 1, g=g)
 
     def rf_sinc(self, flip_deg, phase, dur, dt, tbw=4.0, slice_thk=0.010,
-                b1_peak_scale=1.0):
-        """Slice-selective Hamming sinc along z.  Amplitude so that
-        gamma * sum_j |B1_j| dt equals the flip angle.  Returns Gz (T/m)."""
+                b1_peak_scale=1.0, direction=None):
+        """Slice-selective Hamming sinc along z (or along the unit vector
+        ``direction`` for an oblique slice).  Amplitude so that
+        gamma * sum_j |B1_j| dt equals the flip angle.  Returns the
+        slice-select gradient magnitude (T/m)."""
         n = int(round(dur / dt))
         w = hamming_sinc(n, tbw)
         alpha = flip_deg * np.pi / 180.0
@@ -151,9 +153,10 @@ class SeqBuilder:
         amp *= b1_peak_scale
         gss = (tbw / dur) / (GAMMA_BAR_HZ_PER_T * slice_thk) if slice_thk else 0.0
         cr, ci = _PHASES[phase]
+        g = (0.0, 0.0, gss) if direction is None else tuple(d * gss for d in direction)
         for j in range(n):
             a = amp * w[j]
-            self.add(dt, 1, b1=(a * cr, a * ci), g=(0.0, 0.0, gss))
+            self.add(dt, 1, b1=(a * cr, a * ci), g=g)
         self.n_rf += 1
         return gss
 
@@ -282,6 +285,42 @@ def gre_2d(n_ro=64, n_pe=64, fov=0.256, thk=0.010, flip=30.0, rf_dur=2e-3,
         b.grad(d_sp, (0.0, -ky / gb / d_sp, spoil_area_cycles / thk / gb / d_sp))
     b.delay_until(n_pe * tr)
     return b.build(kind="gre", n_ro=n_ro, n_pe=n_pe, tr=tr, flip=flip)
+
+
+def radial_2d(n_ro=32, n_spokes=16, fov=0.256, thk=0.010, flip=30.0, rf_dur=2e-3,
+              rf_dt=10e-6, dwell=10e-6, te=5e-3, tr=10e-3, tbw=4.0, oblique_deg=0.0,
+              spoil_area_cycles=4.0) -> Sequence:
+    """2-D radial spoiled gradient echo: TR p reads one spoke through the
+    k-space centre at angle theta_p = pi p / n_spokes, so the readout has
+    Gx = g cos(theta_p) and Gy = g sin(theta_p) both nonzero (a with-ADC
+    subsequence on two gradient axes) except on spokes along an axis.
+    ``oblique_deg`` tilts the slice normal from z toward x, which puts the
+    slice-select and its rephaser on two axes (Gx and Gz) as well.  Cosines and
+    sines come from this module's polynomial, so the sequence is the same on
+    every platform."""
+    b = SeqBuilder()
+    gb = GAMMA_BAR_HZ_PER_T
+    g_ro = _dk(fov) / (gb * dwell)
+    d1 = 1e-3
+    ob = float(oblique_deg) / 180.0
+    normal = None if oblique_deg == 0.0 else (float(_sin_pi(ob)), 0.0, float(_cos_pi(ob)))
+    nrm = (0.0, 0.0, 1.0) if normal is None else normal
+    for p in range(n_spokes):
+        t0 = p * tr
+        b.delay_until(t0)
+        gss = b.rf_sinc(flip, "x", rf_dur, rf_dt, tbw, thk, direction=normal)
+        th = p / n_spokes
+        c, sn = float(_cos_pi(th)), float(_sin_pi(th))
+        k0 = -(n_ro // 2) * _dk(fov) / gb / d1
+        reph = -gss * (rf_dur / 2) / d1
+        b.grad(d1, (k0 * c + reph * nrm[0], k0 * sn + reph * nrm[1], reph * nrm[2]))
+        b.delay_until(t0 + rf_dur / 2 + te - (n_ro // 2) * dwell)
+        b.readout(n_ro, dwell, (g_ro * c, g_ro * sn, 0.0))
+        d_sp = 1e-3
+        b.grad(d_sp, (0.0, 0.0, spoil_area_cycles / thk / gb / d_sp))
+    b.delay_until(n_spokes * tr)
+    return b.build(kind="radial", n_ro=n_ro, n_spokes=n_spokes, tr=tr, flip=flip,
+                   oblique_deg=oblique_deg)
 
 
 def kspace_layout(seq: Sequence) -> dict:

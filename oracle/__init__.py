@@ -23,6 +23,8 @@ _lib = None
 
 RF, ADC, RELAX = 0, 1, 2
 G_NONE, G_X, G_Y, G_Z, G_GENERAL = 0, 1, 2, 3, 4
+# two-axis gradient types (grouped on both positions; made only on request)
+G_XY, G_XZ, G_YZ = 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -45,10 +47,10 @@ def _load():
             P = ctypes.c_void_p
             I64 = ctypes.c_int64
             I = ctypes.c_int
-            lib.or_classify.argtypes = [P] * 8 + [I64, I64] + [P] * 7
+            lib.or_classify.argtypes = [P] * 8 + [I64, I64] + [P] * 7 + [I]
             lib.or_group.argtypes = [I64] + [P] * 7 + [I, P, P]
             lib.or_simulate.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [I, I, I, I, P, P, P]
-            lib.or_simulate_grouped.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [P, P]
+            lib.or_simulate_grouped.argtypes = [I64] + [P] * 9 + [I64] + [P] * 8 + [I, P, P]
             lib.or_transition.argtypes = [ctypes.c_double] * 7 + [P] * 7 + [I64, I64, P]
             for f in (lib.or_classify, lib.or_group, lib.or_simulate, lib.or_simulate_grouped,
                       lib.or_transition):
@@ -80,9 +82,11 @@ def _check(rc, what):
         raise OracleError(f"{what} failed with code {rc}")
 
 
-def classify(seq):
+def classify(seq, two_axis: bool = False):
     """Subsequence split + classification.  Returns a dict of numpy arrays:
-    type, gtype, seg_begin, seg_end, n_samples, content_id."""
+    type, gtype, seg_begin, seg_end, n_samples, content_id.  With two_axis, a
+    subsequence whose gradients use exactly two axes gets G_XY / G_XZ / G_YZ
+    instead of G_GENERAL."""
     lib = _load()
     keep = [np.ascontiguousarray(seq.dt, np.float64), np.ascontiguousarray(seq.repeat, np.int32),
             _f32(seq.b1re), _f32(seq.b1im), _f32(seq.gx), _f32(seq.gy), _f32(seq.gz),
@@ -94,7 +98,8 @@ def classify(seq):
                n_samples=np.zeros(cap, np.int64), content_id=np.zeros(cap, np.int32))
     rc = lib.or_classify(*[_p(a) for a in keep], seq.n_seg, cap, ctypes.byref(n),
                          *[_p(out[k]) for k in ("type", "gtype", "seg_begin", "seg_end",
-                                                "n_samples", "content_id")])
+                                                "n_samples", "content_id")],
+                         int(two_axis))
     _check(rc, "or_classify")
     return {k: v[: n.value].copy() for k, v in out.items()}
 
@@ -142,8 +147,10 @@ def simulate(ph, seq, memo: bool = False, adc_recurrence: bool = False,
     return (out if coils is None else out.reshape(P, ns)), M
 
 
-def simulate_grouped(ph, seq, want_M: bool = True):
-    """Grouped FP64 simulation (Eqs. 8-10 and per-group Eq. 7)."""
+def simulate_grouped(ph, seq, want_M: bool = True, two_axis: bool = False):
+    """Grouped FP64 simulation (Eqs. 8-10 and per-group Eq. 7).  With
+    two_axis, subsequences on exactly two gradient axes are grouped on both
+    positions instead of being simulated per isochromat."""
     lib = _load()
     arrs = _ph_args(ph)
     sargs = [np.ascontiguousarray(seq.dt, np.float64), np.ascontiguousarray(seq.repeat, np.int32),
@@ -153,7 +160,7 @@ def simulate_grouped(ph, seq, want_M: bool = True):
     sig = np.zeros(2 * ns + 1, np.float64)
     M = np.zeros((3, ph.K), np.float64) if want_M else None
     rc = lib.or_simulate_grouped(ph.K, *[_p(a) for a in arrs], seq.n_seg,
-                                 *[_p(a) for a in sargs], _p(sig), _p(M))
+                                 *[_p(a) for a in sargs], int(two_axis), _p(sig), _p(M))
     _check(rc, "or_simulate_grouped")
     return sig[: 2 * ns].view(np.complex128).copy(), M
 

@@ -20,7 +20,9 @@
  *             caching" of the conventional method, Sec. 2.2).
  *   - Sec. 2.1 / Fig. 1 subsequence split (with-RF / with-ADC / relaxation),
  *             Sec. 2.4 gradient types (Gx-only, Gy-only, Gz-only, no-grads),
- *             Fig. 2 grouping by equal keys.
+ *             Fig. 2 grouping by equal keys; on request also the two-axis
+ *             types (Gx+Gy, Gx+Gz, Gy+Gz, grouped on both positions) that
+ *             Sec. 5 leaves open.
  *   - Eq. 8-10 grouped with-ADC three-step method and the grouped with-RF
  *             combined transition (Sec. 2.3), used only for the brute-force
  *             "grouped equals ungrouped" check.
@@ -51,6 +53,23 @@
 enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNSUPPORTED = -2, OR_ENOMEM = -3 };
 enum { OR_RF = 0, OR_ADC = 1, OR_RELAX = 2 };
 enum { OR_G_NONE = 0, OR_G_X = 1, OR_G_Y = 2, OR_G_Z = 3, OR_G_GENERAL = 4 };
+/* two-axis gradient types (the paper's open problem, Sec. 5): a subsequence
+ * whose gradients use exactly two axes, grouped on both positions; only made
+ * when asked for (two_axis), otherwise such a subsequence is OR_G_GENERAL */
+enum { OR_G_XY = 5, OR_G_XZ = 6, OR_G_YZ = 7, OR_N_GTYPES = 8 };
+
+/* position axes (0 = x, 1 = y, 2 = z) of a gradient type; returns their count */
+static int type_axes(int g, int ax[2]) {
+    switch (g) {
+    case OR_G_X: ax[0] = 0; return 1;
+    case OR_G_Y: ax[0] = 1; return 1;
+    case OR_G_Z: ax[0] = 2; return 1;
+    case OR_G_XY: ax[0] = 0; ax[1] = 1; return 2;
+    case OR_G_XZ: ax[0] = 0; ax[1] = 2; return 2;
+    case OR_G_YZ: ax[0] = 1; ax[1] = 2; return 2;
+    default: return 0;
+    }
+}
 
 typedef struct {
     int64_t n_seg;
@@ -112,7 +131,7 @@ static void free_subseqs(or_subseqs *q) {
     memset(q, 0, sizeof(*q));
 }
 
-static int build_subseqs(const or_seq *s, or_subseqs *q) {
+static int build_subseqs(const or_seq *s, or_subseqs *q, int two_axis) {
     memset(q, 0, sizeof(*q));
     if (s->n_seg <= 0) return OR_EINVAL;
     int64_t n = 0;
@@ -151,10 +170,9 @@ static int build_subseqs(const or_seq *s, or_subseqs *q) {
         }
         int cnt = ax + ay + az;
         q->gtype[i] = cnt == 0 ? OR_G_NONE
-                    : cnt > 1  ? OR_G_GENERAL
-                    : ax       ? OR_G_X
-                    : ay       ? OR_G_Y
-                               : OR_G_Z;
+                    : cnt == 1 ? (ax ? OR_G_X : ay ? OR_G_Y : OR_G_Z)
+                    : cnt == 2 && two_axis ? (!az ? OR_G_XY : !ay ? OR_G_XZ : OR_G_YZ)
+                               : OR_G_GENERAL;
         q->n_samples[i] = ns;
     }
     /* content ids of with-RF subsequences: exact segment-by-segment equality */
@@ -190,10 +208,11 @@ static int build_subseqs(const or_seq *s, or_subseqs *q) {
 int or_classify(const double *dt, const int32_t *rep, const float *b1re, const float *b1im,
                 const float *gx, const float *gy, const float *gz, const uint8_t *adc,
                 int64_t n_seg, int64_t cap, int64_t *n_sub, uint8_t *type, uint8_t *gtype,
-                int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples, int32_t *content_id) {
+                int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples, int32_t *content_id,
+                int two_axis) {
     or_seq s = {n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc};
     or_subseqs q;
-    int rc = build_subseqs(&s, &q);
+    int rc = build_subseqs(&s, &q, two_axis);
     if (rc) return rc;
     *n_sub = q.n;
     if (q.n <= cap) {
@@ -214,13 +233,13 @@ int or_classify(const double *dt, const int32_t *rep, const float *b1re, const f
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    uint32_t k[5];
+    uint32_t k[6];
     int64_t idx;
 } or_key;
 
 static int key_cmp(const void *pa, const void *pb) {
     const or_key *a = pa, *b = pb;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         if (a->k[i] != b->k[i]) return a->k[i] < b->k[i] ? -1 : 1;
     return a->idx < b->idx ? -1 : (a->idx > b->idx);
 }
@@ -241,22 +260,28 @@ static int rep_cmp(const void *pa, const void *pb) {
     return a->idx < b->idx ? -1 : (a->idx > b->idx);
 }
 
-/* gtype: OR_G_X / Y / Z use (r_axis, T1, T2, dB0[, b1]); OR_G_NONE uses
+/* gtype: OR_G_X / Y / Z use (r_axis, T1, T2, dB0[, b1]); the two-axis types
+ * OR_G_XY / XZ / YZ use (r_a, r_b, T1, T2, dB0[, b1]); OR_G_NONE uses
  * (T1, T2, dB0[, b1]).  Writes gid[K], returns the group count. */
 int or_group(int64_t K, const float *x, const float *y, const float *z, const float *T1,
              const float *T2, const float *dB0, const float *b1, int gtype, int32_t *gid,
              int64_t *n_groups) {
-    if (K <= 0 || gtype < OR_G_NONE || gtype > OR_G_Z) return OR_EINVAL;
-    const float *pos = gtype == OR_G_X ? x : gtype == OR_G_Y ? y : gtype == OR_G_Z ? z : NULL;
+    if (K <= 0 || gtype < OR_G_NONE || gtype >= OR_N_GTYPES || gtype == OR_G_GENERAL)
+        return OR_EINVAL;
+    const float *axis[3] = {x, y, z};
+    int ax[2];
+    const int n_ax = type_axes(gtype, ax);
+    const float *pa = n_ax > 0 ? axis[ax[0]] : NULL, *pb = n_ax > 1 ? axis[ax[1]] : NULL;
     or_key *keys = malloc((size_t)K * sizeof(or_key));
     if (!keys) return OR_ENOMEM;
     for (int64_t k = 0; k < K; ++k) {
         int rc = 0;
-        rc |= key_bits(pos ? pos[k] : 0.0f, &keys[k].k[0]);
+        rc |= key_bits(pa ? pa[k] : 0.0f, &keys[k].k[0]);
         rc |= key_bits(T1[k], &keys[k].k[1]);
         rc |= key_bits(T2[k], &keys[k].k[2]);
         rc |= key_bits(dB0[k], &keys[k].k[3]);
         rc |= key_bits(b1 ? b1[k] : 1.0f, &keys[k].k[4]);
+        rc |= key_bits(pb ? pb[k] : 0.0f, &keys[k].k[5]);
         if (rc) { free(keys); return OR_EINVAL; }
         keys[k].idx = k;
     }
@@ -530,7 +555,7 @@ int or_simulate(int64_t K, const float *x, const float *y, const float *z, const
     int rc = check_phantom(&ph);
     if (rc) return rc;
     or_subseqs q;
-    rc = build_subseqs(&s, &q);
+    rc = build_subseqs(&s, &q, 0);
     if (rc) return rc;
     int64_t ns = 0;
     for (int64_t i = 0; i < q.n; ++i) ns += q.n_samples[i];
@@ -588,18 +613,18 @@ int or_simulate_grouped(int64_t K, const float *x, const float *y, const float *
                         const float *b1, const float *Minit, int64_t n_seg, const double *dt,
                         const int32_t *rep, const float *b1re, const float *b1im,
                         const float *gx, const float *gy, const float *gz, const uint8_t *adc,
-                        double *signal, double *Mfinal) {
+                        int two_axis, double *signal, double *Mfinal) {
     or_phantom ph = {K, x, y, z, T1, T2, dB0, M0, b1, Minit, 1, NULL};
     or_seq s = {n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc};
     int rc = check_phantom(&ph);
     if (rc) return rc;
     or_subseqs q;
-    rc = build_subseqs(&s, &q);
+    rc = build_subseqs(&s, &q, two_axis);
     if (rc) return rc;
     double *M = malloc((size_t)K * 3 * sizeof(double));
-    int32_t *gid[4] = {NULL, NULL, NULL, NULL};
-    int64_t ng[4] = {0, 0, 0, 0};
-    int64_t *rep_of[4] = {NULL, NULL, NULL, NULL};
+    int32_t *gid[OR_N_GTYPES] = {NULL};
+    int64_t ng[OR_N_GTYPES] = {0};
+    int64_t *rep_of[OR_N_GTYPES] = {NULL};
     if (!M) { free_subseqs(&q); return OR_ENOMEM; }
     for (int64_t k = 0; k < K; ++k) iso_init(&ph, k, &M[3 * k]);
     /* groups for every known gradient type used by a with-RF / with-ADC subsequence */
@@ -650,19 +675,27 @@ int or_simulate_grouped(int64_t K, const float *x, const float *y, const float *
                 Ab[2 * gid[g][k]] += M[3 * k];
                 Ab[2 * gid[g][k] + 1] += M[3 * k + 1];
             }
-            /* Step 2 (Eqs. 8, 10): each sample from the group blocks. */
-            double tau = 0.0, mom = 0.0; /* time and gradient moment since t0 */
+            /* Step 2 (Eqs. 8, 10): each sample from the group blocks.  The
+             * phase uses the gradient moment of every axis of the type (one
+             * axis, or two for the two-axis types). */
+            int ax[2];
+            const int n_ax = type_axes(g, ax);
+            const float *gax[3] = {gx, gy, gz};
+            double tau = 0.0, mom[2] = {0.0, 0.0}; /* time and moments since t0 */
             for (int64_t j = q.seg_begin[i]; j < q.seg_end[i]; ++j) {
-                double ga = g == OR_G_X ? gx[j] : g == OR_G_Y ? gy[j] : g == OR_G_Z ? gz[j] : 0.0;
+                double ga[2] = {0.0, 0.0};
+                for (int a = 0; a < n_ax; ++a) ga[a] = gax[ax[a]][j];
                 for (int32_t r = 0; r < rep[j]; ++r) {
                     double t_s = tau + (r + 1) * dt[j];
-                    double m_s = mom + ga * (r + 1) * dt[j];
+                    double m_s[2] = {mom[0] + ga[0] * (r + 1) * dt[j],
+                                     mom[1] + ga[1] * (r + 1) * dt[j]};
                     double ar = 0.0, ai = 0.0;
                     for (int64_t G = 0; G < ng[g]; ++G) {
                         or_iso p = iso_at(&ph, rep_of[g][G]);
-                        double pos = g == OR_G_X ? p.x : g == OR_G_Y ? p.y : g == OR_G_Z ? p.z : 0.0;
+                        const double pv[3] = {p.x, p.y, p.z};
                         double E2 = exp(-t_s / p.T2);
-                        double phi = OR_GAMMA * pos * m_s + 2.0 * OR_PI * p.dB0 * t_s;
+                        double phi = 2.0 * OR_PI * p.dB0 * t_s;
+                        for (int a = 0; a < n_ax; ++a) phi += OR_GAMMA * pv[ax[a]] * m_s[a];
                         double c = cos(phi), sn = sin(phi);
                         double br = Ab[2 * G], bi = Ab[2 * G + 1];
                         ar += E2 * (br * c + bi * sn);
@@ -673,7 +706,8 @@ int or_simulate_grouped(int64_t K, const float *x, const float *y, const float *
                     ++smp;
                 }
                 tau += dt[j] * rep[j];
-                mom += ga * dt[j] * rep[j];
+                mom[0] += ga[0] * dt[j] * rep[j];
+                mom[1] += ga[1] * dt[j] * rep[j];
             }
             free(Ab);
             /* Step 3 (Eqs. 4-5): every isochromat to the end of the window. */
@@ -702,7 +736,7 @@ int or_simulate_grouped(int64_t K, const float *x, const float *y, const float *
     if (rc == OR_OK && Mfinal)
         for (int64_t k = 0; k < K; ++k)
             for (int c = 0; c < 3; ++c) Mfinal[c * K + k] = M[3 * k + c];
-    for (int g = 0; g < 4; ++g) { free(gid[g]); free(rep_of[g]); }
+    for (int g = 0; g < OR_N_GTYPES; ++g) { free(gid[g]); free(rep_of[g]); }
     free(M);
     free_subseqs(&q);
     return rc;
