@@ -9,6 +9,8 @@
 #include <new>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace mrsim {
@@ -60,6 +62,8 @@ void sync(mrsim_ctx *c) {
 
 KScope::KScope(mrsim_ctx *ctx, const char *name) : c(ctx) {
     ++c->launches;
+    // a named NVTX range around the launch (profilers can select passes by it)
+    nvtxRangePushA(name);
     if (!c->prof_on) return;
     for (size_t i = 0; i < c->prof_names.size(); ++i)
         if (c->prof_names[i] == name) { id = (int)i; break; }
@@ -81,6 +85,7 @@ KScope::KScope(mrsim_ctx *ctx, const char *name) : c(ctx) {
 }
 
 KScope::~KScope() {
+    nvtxRangePop();
     if (id < 0 || !a || !b) return;
     cudaEventRecord(b, c->stream);
     c->prof_pending.push_back({id, a, b});

@@ -161,13 +161,16 @@ struct mrsim_groups {
 
 namespace mrsim {
 
-// Counts a kernel launch and brackets it with events when profiling is on.
+// Counts a kernel launch, names it with an NVTX range (host side, around the
+// launch) and brackets it with events when profiling is on.
 struct KScope {
     mrsim_ctx *c;
     int id = -1;
     cudaEvent_t a = nullptr, b = nullptr;
     KScope(mrsim_ctx *ctx, const char *name);
     ~KScope();
+    KScope(const KScope &) = delete;
+    KScope &operator=(const KScope &) = delete;
 };
 
 // after a synchronize: fold pending event pairs into the per-kernel totals
