@@ -144,6 +144,24 @@ int mrsim_sequence(mrsim_ctx *ctx, int64_t n_seg, const double *dt_s, const int3
                    const float *gy_Tpm, const float *gz_Tpm, const uint8_t *adc,
                    mrsim_seq **out);
 
+/* The host part of mrsim_sequence on its own, without a context or a device:
+ * split the sequence (same arrays and rules as mrsim_sequence) into with-RF /
+ * with-ADC / relaxation subsequences (Fig. 1) and type each by its gradient
+ * axes (Sec. 2.4).  n_subseq receives the count m; when m <= cap, entry i of
+ * each non-NULL output gets subsequence i: type (MRSIM_SUB_*), gtype
+ * (MRSIM_G_*), seg_begin / seg_end (segment range), n_samples (ADC samples in
+ * it) and content_id (with-RF subsequences: index of its distinct content,
+ * numbered by first appearance, two pulses sharing one when every field of
+ * every segment is bit-equal; -1 otherwise).  Host arrays.
+ * Errors: MRSIM_EINVAL (n_subseq NULL, n_seg <= 0, NULL array, dt <= 0,
+ * repeat < 1, non-finite value), MRSIM_EUNSUPPORTED (RF and ADC in one
+ * segment), MRSIM_ENOMEM. */
+int mrsim_classify(int64_t n_seg, const double *dt_s, const int32_t *repeat, const float *b1_re_T,
+                   const float *b1_im_T, const float *gx_Tpm, const float *gy_Tpm,
+                   const float *gz_Tpm, const uint8_t *adc, int64_t cap, int64_t *n_subseq,
+                   uint8_t *type, uint8_t *gtype, int64_t *seg_begin, int64_t *seg_end,
+                   int64_t *n_samples, int32_t *content_id);
+
 /* Subsequence table of a sequence.  n_subseq receives the count; each output
  * array (host, n_subseq entries) may be NULL.  type: MRSIM_SUB_*; gtype:
  * MRSIM_G_*; seg_begin/seg_end: half-open segment range; n_samples_total:

@@ -193,7 +193,9 @@ __global__ void k_validate(int64_t K, const float *x, const float *y, const floa
     }
 }
 
-void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
+// Host part of a sequence: subsequence split (Fig. 1), gradient types
+// (Sec. 2.4), sample offsets and with-RF content ids.  Needs no device.
+void classify_sequence(mrsim_seq *s) {
     const int64_t n = s->n_seg;
     // split into maximal runs of one class (Fig. 1)
     auto cls = [&](int64_t j) {
@@ -257,6 +259,10 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
         }
     }
     s->n_samples = smp;
+}
+
+void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
+    classify_sequence(s);
     // device waveforms of every distinct with-RF content
     mrsim_seq *dev = s;
     s->rf_f.resize(s->n_content);
@@ -290,6 +296,7 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
     // ADC segments and per-sample window-relative (tau, k)
     std::vector<ADCSegF> af;
     std::vector<ADCSegD> ad;
+    const int64_t smp = s->n_samples;
     std::vector<GSampleF> gf(std::max<int64_t>(smp, 1));
     std::vector<GSampleD> gd(std::max<int64_t>(smp, 1));
     dev->adc_off.assign(s->sub.size(), -1);
@@ -1179,6 +1186,47 @@ int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t 
     });
     if (rc == MRSIM_OK) *out = s.release();
     return rc;
+}
+
+int mrsim_classify(int64_t n_seg, const double *dt, const int32_t *rep, const float *b1re,
+                   const float *b1im, const float *gx, const float *gy, const float *gz,
+                   const uint8_t *adc, int64_t cap, int64_t *n_subseq, uint8_t *type,
+                   uint8_t *gtype, int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples,
+                   int32_t *content_id) {
+    if (!n_subseq) return MRSIM_EINVAL;
+    *n_subseq = 0;
+    if (n_seg <= 0 || !dt || !rep || !b1re || !b1im || !gx || !gy || !gz || !adc)
+        return MRSIM_EINVAL;
+    try {
+        mrsim_seq s;
+        s.n_seg = n_seg;
+        s.dt.assign(dt, dt + n_seg);
+        s.rep.assign(rep, rep + n_seg);
+        s.b1re.assign(b1re, b1re + n_seg);
+        s.b1im.assign(b1im, b1im + n_seg);
+        s.gx.assign(gx, gx + n_seg);
+        s.gy.assign(gy, gy + n_seg);
+        s.gz.assign(gz, gz + n_seg);
+        s.adc.assign(adc, adc + n_seg);
+        classify_sequence(&s);
+        const int64_t m = (int64_t)s.sub.size();
+        *n_subseq = m;
+        if (m > cap) return MRSIM_OK;
+        for (int64_t i = 0; i < m; ++i) {
+            const Subseq &q = s.sub[i];
+            if (type) type[i] = (uint8_t)q.type;
+            if (gtype) gtype[i] = (uint8_t)q.gtype;
+            if (seg_begin) seg_begin[i] = q.seg_begin;
+            if (seg_end) seg_end[i] = q.seg_end;
+            if (n_samples) n_samples[i] = q.n_samples;
+            if (content_id) content_id[i] = q.content;
+        }
+        return MRSIM_OK;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return MRSIM_ENOMEM;
+    }
 }
 
 int mrsim_seq_info(const mrsim_seq *s, int64_t *n_subseq, uint8_t *type, uint8_t *gtype,

@@ -31,7 +31,7 @@ TUNE_PRECOMP_STEPS = 4
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
-           "mrsim_phantom_read", "mrsim_coils",
+           "mrsim_phantom_read", "mrsim_coils", "mrsim_classify",
            "mrsim_sequence", "mrsim_seq_info", "mrsim_group", "mrsim_group_info", "mrsim_run",
            "mrsim_run_batch", "mrsim_recon_cartesian", "mrsim_cluster", "mrsim_profile_enable",
            "mrsim_profile_reset",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_sequence": (I, [P, I64] + [P] * 8 + [PP]),
         "mrsim_coils": (I, [P, P, I, P, U]),
         "mrsim_phantom_read": (I, [P] * 9),
+        "mrsim_classify": (I, [I64] + [P] * 8 + [I64] + [P] * 7),
         "mrsim_seq_info": (I, [P] * 7),
         "mrsim_group": (I, [P, P, P, PP]),
         "mrsim_group_info": (I, [P, I, P, P]),
@@ -173,6 +174,25 @@ def mrsim_sequence(ctx, n_seg, dt, repeat, b1re, b1im, gx, gy, gz, adc) -> int:
                               ctypes.byref(h))
     _check(ctx, rc, "mrsim_sequence")
     return h.value
+
+
+def mrsim_classify(seq):
+    """Subsequence table of a sequence (numpy arrays; no context, no device):
+    dict of type, gtype, seg_begin, seg_end, n_samples, content_id."""
+    keep = [np.ascontiguousarray(seq.dt, np.float64), np.ascontiguousarray(seq.repeat, np.int32),
+            _f32(seq.b1re), _f32(seq.b1im), _f32(seq.gx), _f32(seq.gy), _f32(seq.gz),
+            np.ascontiguousarray(seq.adc, np.uint8)]
+    cap = int(seq.n_seg)
+    out = dict(type=np.zeros(cap, np.uint8), gtype=np.zeros(cap, np.uint8),
+               seg_begin=np.zeros(cap, np.int64), seg_end=np.zeros(cap, np.int64),
+               n_samples=np.zeros(cap, np.int64), content_id=np.zeros(cap, np.int32))
+    n = ctypes.c_int64(0)
+    rc = lib().mrsim_classify(int(seq.n_seg), *[_ptr(a) for a in keep], cap, ctypes.byref(n),
+                              *[_ptr(out[k]) for k in ("type", "gtype", "seg_begin", "seg_end",
+                                                       "n_samples", "content_id")])
+    if rc:
+        raise MrsimError(rc, "mrsim_classify")
+    return {k: v[: n.value].copy() for k, v in out.items()}
 
 
 def mrsim_seq_info(seq):
