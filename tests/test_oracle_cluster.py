@@ -222,3 +222,23 @@ def test_mapped_phantom_clusters_reduce_groups():
     assert gx <= 32 * len(np.unique(q.x))
     # every isochromat carries its cluster's centre
     assert np.array_equal(q.T1, r.centres[r.labels, 0].astype(np.float32))
+
+
+def test_equal_sse_goes_to_the_smaller_id():
+    """Two translated copies of one two-blob set: the first split separates the
+    copies, which then have exactly equal SSE, so the second split must take
+    id 0, and the third the other copy (id 1)."""
+    rng = np.random.default_rng(14)
+    half = np.concatenate([rng.integers(0, 6, size=(3, 40)),
+                           rng.integers(0, 6, size=(3, 40)) + np.array([[300], [0], [0]])],
+                          axis=1)
+    X = np.concatenate([half, half + np.array([[0], [50000], [0]])], axis=1).astype(np.int64)
+    X = X[:, rng.permutation(X.shape[1])]
+    labels, centres, history = oc.bisecting_kmeans(X, 4)
+    assert history[0] == (0, 1)
+    sizes = np.bincount(labels)
+    assert history[1] == (0, 2) and history[2] == (1, 3)
+    cols = list(X.T)
+    s0 = py_sse([cols[k] for k in np.flatnonzero((labels == 0) | (labels == 2))])
+    s1 = py_sse([cols[k] for k in np.flatnonzero((labels == 1) | (labels == 3))])
+    assert s0 == s1 and np.all(sizes == 40)
