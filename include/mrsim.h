@@ -61,6 +61,12 @@ extern "C" {
 #define MRSIM_G_Y 2
 #define MRSIM_G_Z 3
 #define MRSIM_G_GENERAL 4
+/* two-axis types (Gx+Gy, Gx+Gz, Gy+Gz: the paper's open problem, Sec. 5), reported
+ * only by mrsim_classify with MRSIM_CLASSIFY_TWO_AXIS; mrsim_sequence types such
+ * subsequences MRSIM_G_GENERAL (simulated per isochromat) */
+#define MRSIM_G_XY 5
+#define MRSIM_G_XZ 6
+#define MRSIM_G_YZ 7
 
 /* run modes */
 #define MRSIM_PLAIN 0       /* every isochromat stepped individually (Eq. 3, Eq. 6) */
@@ -147,7 +153,9 @@ int mrsim_sequence(mrsim_ctx *ctx, int64_t n_seg, const double *dt_s, const int3
 /* The host part of mrsim_sequence on its own, without a context or a device:
  * split the sequence (same arrays and rules as mrsim_sequence) into with-RF /
  * with-ADC / relaxation subsequences (Fig. 1) and type each by its gradient
- * axes (Sec. 2.4).  n_subseq receives the count m; when m <= cap, entry i of
+ * axes (Sec. 2.4; with flags = MRSIM_CLASSIFY_TWO_AXIS a subsequence on exactly
+ * two axes is typed MRSIM_G_XY / XZ / YZ instead of MRSIM_G_GENERAL; flags = 0
+ * types as mrsim_sequence does).  n_subseq receives the count m; when m <= cap, entry i of
  * each non-NULL output gets subsequence i: type (MRSIM_SUB_*), gtype
  * (MRSIM_G_*), seg_begin / seg_end (segment range), n_samples (ADC samples in
  * it) and content_id (with-RF subsequences: index of its distinct content,
@@ -156,11 +164,12 @@ int mrsim_sequence(mrsim_ctx *ctx, int64_t n_seg, const double *dt_s, const int3
  * Errors: MRSIM_EINVAL (n_subseq NULL, n_seg <= 0, NULL array, dt <= 0,
  * repeat < 1, non-finite value), MRSIM_EUNSUPPORTED (RF and ADC in one
  * segment), MRSIM_ENOMEM. */
+#define MRSIM_CLASSIFY_TWO_AXIS 1u
 int mrsim_classify(int64_t n_seg, const double *dt_s, const int32_t *repeat, const float *b1_re_T,
                    const float *b1_im_T, const float *gx_Tpm, const float *gy_Tpm,
-                   const float *gz_Tpm, const uint8_t *adc, int64_t cap, int64_t *n_subseq,
-                   uint8_t *type, uint8_t *gtype, int64_t *seg_begin, int64_t *seg_end,
-                   int64_t *n_samples, int32_t *content_id);
+                   const float *gz_Tpm, const uint8_t *adc, unsigned flags, int64_t cap,
+                   int64_t *n_subseq, uint8_t *type, uint8_t *gtype, int64_t *seg_begin,
+                   int64_t *seg_end, int64_t *n_samples, int32_t *content_id);
 
 /* Subsequence table of a sequence.  n_subseq receives the count; each output
  * array (host, n_subseq entries) may be NULL.  type: MRSIM_SUB_*; gtype:

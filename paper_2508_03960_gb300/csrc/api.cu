@@ -194,8 +194,9 @@ __global__ void k_validate(int64_t K, const float *x, const float *y, const floa
 }
 
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
-// (Sec. 2.4), sample offsets and with-RF content ids.  Needs no device.
-void classify_sequence(mrsim_seq *s) {
+// (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
+// of G_GENERAL), sample offsets and with-RF content ids.  Needs no device.
+void classify_sequence(mrsim_seq *s, bool two_axis) {
     const int64_t n = s->n_seg;
     // split into maximal runs of one class (Fig. 1)
     auto cls = [&](int64_t j) {
@@ -234,7 +235,10 @@ void classify_sequence(mrsim_seq *s) {
             if (s->adc[j]) q.n_samples += s->rep[j];
         }
         const int cnt = (int)ax + (int)ay + (int)az;
-        q.gtype = cnt == 0 ? G_NONE : cnt > 1 ? G_GENERAL : ax ? G_X : ay ? G_Y : G_Z;
+        q.gtype = cnt == 0   ? G_NONE
+                  : cnt == 1 ? (ax ? G_X : ay ? G_Y : G_Z)
+                  : cnt == 2 && two_axis ? (!az ? G_XY : !ay ? G_XZ : G_YZ)
+                             : G_GENERAL;
         q.sample0 = smp;
         smp += q.n_samples;
         if (q.type == SUB_RF) {
@@ -262,7 +266,7 @@ void classify_sequence(mrsim_seq *s) {
 }
 
 void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
-    classify_sequence(s);
+    classify_sequence(s, false);
     // device waveforms of every distinct with-RF content
     mrsim_seq *dev = s;
     s->rf_f.resize(s->n_content);
@@ -1190,12 +1194,13 @@ int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t 
 
 int mrsim_classify(int64_t n_seg, const double *dt, const int32_t *rep, const float *b1re,
                    const float *b1im, const float *gx, const float *gy, const float *gz,
-                   const uint8_t *adc, int64_t cap, int64_t *n_subseq, uint8_t *type,
-                   uint8_t *gtype, int64_t *seg_begin, int64_t *seg_end, int64_t *n_samples,
-                   int32_t *content_id) {
+                   const uint8_t *adc, unsigned flags, int64_t cap, int64_t *n_subseq,
+                   uint8_t *type, uint8_t *gtype, int64_t *seg_begin, int64_t *seg_end,
+                   int64_t *n_samples, int32_t *content_id) {
     if (!n_subseq) return MRSIM_EINVAL;
     *n_subseq = 0;
-    if (n_seg <= 0 || !dt || !rep || !b1re || !b1im || !gx || !gy || !gz || !adc)
+    if (n_seg <= 0 || !dt || !rep || !b1re || !b1im || !gx || !gy || !gz || !adc ||
+        (flags & ~MRSIM_CLASSIFY_TWO_AXIS))
         return MRSIM_EINVAL;
     try {
         mrsim_seq s;
@@ -1208,7 +1213,7 @@ int mrsim_classify(int64_t n_seg, const double *dt, const int32_t *rep, const fl
         s.gy.assign(gy, gy + n_seg);
         s.gz.assign(gz, gz + n_seg);
         s.adc.assign(adc, adc + n_seg);
-        classify_sequence(&s);
+        classify_sequence(&s, (flags & MRSIM_CLASSIFY_TWO_AXIS) != 0);
         const int64_t m = (int64_t)s.sub.size();
         *n_subseq = m;
         if (m > cap) return MRSIM_OK;

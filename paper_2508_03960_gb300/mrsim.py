@@ -71,7 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_sequence": (I, [P, I64] + [P] * 8 + [PP]),
         "mrsim_coils": (I, [P, P, I, P, U]),
         "mrsim_phantom_read": (I, [P] * 9),
-        "mrsim_classify": (I, [I64] + [P] * 8 + [I64] + [P] * 7),
+        "mrsim_classify": (I, [I64] + [P] * 8 + [U, I64] + [P] * 7),
         "mrsim_seq_info": (I, [P] * 7),
         "mrsim_group": (I, [P, P, P, PP]),
         "mrsim_group_info": (I, [P, I, P, P]),
@@ -176,9 +176,14 @@ def mrsim_sequence(ctx, n_seg, dt, repeat, b1re, b1im, gx, gy, gz, adc) -> int:
     return h.value
 
 
-def mrsim_classify(seq):
+CLASSIFY_TWO_AXIS = 1
+G_XY, G_XZ, G_YZ = 5, 6, 7
+
+
+def mrsim_classify(seq, flags=0):
     """Subsequence table of a sequence (numpy arrays; no context, no device):
-    dict of type, gtype, seg_begin, seg_end, n_samples, content_id."""
+    dict of type, gtype, seg_begin, seg_end, n_samples, content_id.  flags =
+    CLASSIFY_TWO_AXIS types subsequences on exactly two axes G_XY / G_XZ / G_YZ."""
     keep = [np.ascontiguousarray(seq.dt, np.float64), np.ascontiguousarray(seq.repeat, np.int32),
             _f32(seq.b1re), _f32(seq.b1im), _f32(seq.gx), _f32(seq.gy), _f32(seq.gz),
             np.ascontiguousarray(seq.adc, np.uint8)]
@@ -187,7 +192,8 @@ def mrsim_classify(seq):
                seg_begin=np.zeros(cap, np.int64), seg_end=np.zeros(cap, np.int64),
                n_samples=np.zeros(cap, np.int64), content_id=np.zeros(cap, np.int32))
     n = ctypes.c_int64(0)
-    rc = lib().mrsim_classify(int(seq.n_seg), *[_ptr(a) for a in keep], cap, ctypes.byref(n),
+    rc = lib().mrsim_classify(int(seq.n_seg), *[_ptr(a) for a in keep], flags, cap,
+                              ctypes.byref(n),
                               *[_ptr(out[k]) for k in ("type", "gtype", "seg_begin", "seg_end",
                                                        "n_samples", "content_id")])
     if rc:

@@ -34,11 +34,12 @@ SEQUENCES = {
 }
 
 
+@pytest.mark.parametrize("two_axis", [False, True])
 @pytest.mark.parametrize("name", list(SEQUENCES))
-def test_classification_equals_oracle(mrsim, name):
+def test_classification_equals_oracle(mrsim, name, two_axis):
     seq = SEQUENCES[name]()
-    got = mrsim.mrsim_classify(seq)
-    ref = oracle.classify(seq)
+    got = mrsim.mrsim_classify(seq, mrsim.CLASSIFY_TWO_AXIS if two_axis else 0)
+    ref = oracle.classify(seq, two_axis=two_axis)
     assert set(got) == set(ref)
     for k in ref:
         assert np.array_equal(got[k].astype(np.int64), ref[k].astype(np.int64)), k
@@ -78,9 +79,11 @@ def test_small_capacity_reports_the_count_only(mrsim):
     arrs += [np.ascontiguousarray(seq.adc, np.uint8)]
     n = ctypes.c_int64(-1)
     typ = np.full(4, 99, np.uint8)
-    rc = lib.mrsim_classify(seq.n_seg, *[a.ctypes.data for a in arrs], 1, ctypes.byref(n),
+    rc = lib.mrsim_classify(seq.n_seg, *[a.ctypes.data for a in arrs], 0, 1, ctypes.byref(n),
                             typ.ctypes.data, None, None, None, None, None)
     assert rc == 0 and n.value == len(oracle.classify(seq)["type"]) > 1
     assert np.all(typ == 99)
-    assert lib.mrsim_classify(seq.n_seg, *[a.ctypes.data for a in arrs], 1, None,
+    assert lib.mrsim_classify(seq.n_seg, *[a.ctypes.data for a in arrs], 0, 1, None,
                               *[None] * 6) == mrsim.EINVAL
+    assert lib.mrsim_classify(seq.n_seg, *[a.ctypes.data for a in arrs], 2, 1, ctypes.byref(n),
+                              *[None] * 6) == mrsim.EINVAL  # unknown flag
