@@ -193,6 +193,10 @@ __global__ void k_validate(int64_t K, const float *x, const float *y, const floa
     }
 }
 
+// two-axis gradient types (Gx+Gy, Gx+Gz, Gy+Gz; the numbers of MRSIM_G_XY /
+// XZ / YZ), made only by the host classifier on request
+constexpr int G_XY = MRSIM_G_XY, G_XZ = MRSIM_G_XZ, G_YZ = MRSIM_G_YZ;
+
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
 // (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
 // of G_GENERAL), sample offsets and with-RF content ids.  Needs no device.

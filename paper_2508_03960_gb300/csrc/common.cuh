@@ -14,8 +14,7 @@ constexpr double kGamma = kTwoPi * kGammaBar;
 constexpr double kLog2e = 1.4426950408889634073599246810019;
 
 enum SubType : int { SUB_RF = 0, SUB_ADC = 1, SUB_RELAX = 2 };
-enum GType : int { G_NONE = 0, G_X = 1, G_Y = 2, G_Z = 3, G_GENERAL = 4,
-                   G_XY = 5, G_XZ = 6, G_YZ = 7 };  // two-axis: host classification only
+enum GType : int { G_NONE = 0, G_X = 1, G_Y = 2, G_Z = 3, G_GENERAL = 4 };
 enum EvKind : int { EV_RF = 0, EV_ADC = 1, EV_END = 2 };
 
 // Free-precession parameters of an advance from the state time t_w to a
