@@ -59,3 +59,8 @@ def test_mapped_phantom_takes_values_from_the_candidate_sets():
     assert not p.dB0.any() and p.K == 32 * 32 * 2
     n_pairs = np.unique(np.stack([p.T1, p.T2]), axis=1).shape[1]
     assert 50 < n_pairs < 100 * 100
+
+
+def test_generator_reproduces_the_stored_clustering_input():
+    d = np.load(os.path.join(GOLDEN, "cluster_mapped_27m_oracle.npz"))
+    assert str(d["phantom_digest"]) == phantom_digest(configs.mapped_27m())
