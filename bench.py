@@ -595,7 +595,7 @@ def main():
     if a.tune == "on":
         tuned = mrsim.mrsim_autotune(ctx.h, hp, hs_f, hg_f, mrsim.GROUPED, mrsim.FP32, 2)
     else:
-        tuned = {p: mrsim.mrsim_get_tuning(ctx.h, p) for p in range(5)}
+        tuned = {p: mrsim.mrsim_get_tuning(ctx.h, p) for p in range(6)}
     autotune_s = time.perf_counter() - t0
 
     ns_f, ns_e = fse.n_samples, epi.n_samples

@@ -355,12 +355,23 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              preparation of 6.9M groups takes 31 / 24 ms
  *                              instead of 44 ms at 8;
  *                              FP64 runs compose every sub-step in FP64
+ *   MRSIM_TUNE_CELL_NI         FP32 grouped runs: isochromats per thread of the
+ *                              cell form of the fused kernel (every thread
+ *                              holds isochromats of one (with-ADC group,
+ *                              with-RF group) cell and applies one combined
+ *                              row per cell to each with-RF subsequence): 4
+ *                              (default) or 8; 0 turns the cell form off (the
+ *                              per-isochromat form of MRSIM_TUNE_FUSED_NI runs).
+ *                              Runs with receive coils, per-isochromat
+ *                              advances ("direct" form) or gradient types that
+ *                              vary inside a cell use the other form anyway.
  * mrsim_set_tuning returns MRSIM_EINVAL for another parameter or value. */
 #define MRSIM_TUNE_FUSED_NI 0
 #define MRSIM_TUNE_PLAIN_RF_NI 1
 #define MRSIM_TUNE_ADC_CTAS_PER_SM 2
 #define MRSIM_TUNE_PRECOMP_LANES 3
 #define MRSIM_TUNE_PRECOMP_STEPS 4
+#define MRSIM_TUNE_CELL_NI 5
 int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
 int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
 

@@ -454,10 +454,18 @@ struct GPlan {
     std::vector<AxItem> ax_items;
     int64_t ax_n = 0;       // table entries of all events
     int ax_max = 0;         // longest table
+    // cell form of the fused kernel (FP32): see CellArgs
+    bool cell = false;
+    int cell_w = 0;         // 0: 4 isochromats per thread, 1: 8
+    int free_bits = 0, r_axis = -1;
+    CellForm form{};
+    std::vector<CellKey> ckeys;  // distinct RF / END advances
+    std::vector<CellEv> cev;     // the events in the cell form's record
 };
 
 template <typename R>
-void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan<R> &P) {
+void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan<R> &P,
+                  bool allow_cell = false) {
     // 1) combined transitions for every (content, gradient type) of a known with-RF
     std::map<std::pair<int, int>, int64_t> row_of;
     for (const Subseq &q : s->sub) {
@@ -563,15 +571,50 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
     P.direct = (int64_t)P.ev.size() * P.Gp > (int64_t)1 << 26 || P.Gp * 4 > g->K;
     if (P.direct)
         for (auto &e : P.ev) e.prow = 0;
-    // FP32 factor-table runs take the per-isochromat phasor of every axis in an
-    // event's mask from a table over that axis' distinct positions
     if constexpr (sizeof(R) == 4) {
-        if (!P.direct && g->ax_ok) {
+        // cell form (see CellArgs): every RF type and every with-ADC type must
+        // be constant inside a cell (primary, secondary or no-grads)
+        const int ni = c->tune[MRSIM_TUNE_CELL_NI];
+        P.cell_w = ni == 8 ? 1 : 0;
+        const int r = g->secondary;
+        P.cell = allow_cell && ni != 0 && !P.direct && g->ax_ok && p >= G_X && p <= G_Z &&
+                 g->n_cell_thr[P.cell_w] > 0 && g->n_cells > 0;
+        P.r_axis = (r >= G_X && r <= G_Z) ? r - 1 : -1;
+        P.free_bits = 7 & ~(1 << (p - 1)) & ~(P.r_axis >= 0 ? 1 << P.r_axis : 0);
+        const int rbit = P.r_axis >= 0 ? 1 << P.r_axis : 0;
+        auto const_in_cell = [&](int gt) {
+            return gt == p || gt == r || (gt == G_NONE && g->built[G_NONE]);
+        };
+        P.form = CellForm{ni, __builtin_popcount(P.free_bits), false, false, false};
+        for (size_t i = 0; P.cell && i < P.ev.size(); ++i) {
+            const int kind = ev_kind(P.ev[i].op), mask = ev_mask(P.ev[i].op);
+            if (kind != EV_END && !const_in_cell(ev_gtype(P.ev[i].op))) P.cell = false;
+            if (kind != EV_ADC) P.form.rfq |= (mask & P.free_bits) != 0;
+            if (kind == EV_ADC) {
+                P.form.adq |= (mask & P.free_bits) != 0;
+                P.form.rb |= (mask & rbit) != 0;
+            }
+        }
+        // FP32 factor-table runs take the per-isochromat phasor of every axis in
+        // an event's mask from a table over that axis' distinct positions; the
+        // cell form applies the same phasors to every event of a kind, so it
+        // needs the tables of all free axes (and the secondary axis for with-ADC
+        // windows) wherever the form applies them
+        auto axis_tables = [&](bool cell) {
+            P.ax_items.clear();
+            P.ax_n = 0;
+            P.ax_max = 0;
             for (size_t i = 0; i < P.ev.size(); ++i) {
-                const int mask = ev_mask(P.ev[i].op);
+                const int kind = ev_kind(P.ev[i].op);
+                int need = ev_mask(P.ev[i].op);
+                if (cell) {
+                    if (kind != EV_ADC && P.form.rfq) need |= P.free_bits;
+                    if (kind == EV_ADC && P.form.adq) need |= P.free_bits;
+                    if (kind == EV_ADC && P.form.rb) need |= rbit;
+                }
                 for (int a = 0; a < 3; ++a) {
                     P.ev[i].q[a] = 0;
-                    if (!(mask & (1 << a))) continue;
+                    if (!(need & (1 << a))) continue;
                     P.ev[i].q[a] = (int)P.ax_n;
                     P.ax_items.push_back(AxItem{P.kd[i][a], g->ax_val[a].as<float>(),
                                                 (int)g->n_ax[a], 0, P.ax_n});
@@ -580,6 +623,72 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
                 }
             }
             P.ax = P.ax_n <= ((int64_t)1 << 24);
+        };
+        if (!P.direct && g->ax_ok) {
+            axis_tables(P.cell);
+            if (P.cell && !P.ax) {
+                P.cell = false;
+                axis_tables(false);
+            }
+        }
+        if (P.cell) {
+            // one key per distinct (transition rows, primary and secondary
+            // moments, duration) of an RF or END event: the free-axis moment
+            // stays per isochromat.  Moments and durations equal to 1e-12
+            // relative share a key: sequences built on an absolute time grid
+            // give one repeated interval durations that differ by ~1e-15 s,
+            // eight orders of magnitude below what the FP32 factors resolve
+            auto near = [](double u, double v) {
+                return std::fabs(u - v) <= 1e-12 * std::max(std::fabs(u), std::fabs(v));
+            };
+            int fa[2] = {-1, -1}, nfa = 0;
+            for (int a = 0; a < 3; ++a)
+                if (P.free_bits & (1 << a)) fa[nfa++] = a;
+            P.cev.resize(P.ev.size());
+            for (size_t i = 0; i < P.ev.size() && P.cell; ++i) {
+                const FEvent<R> &e = P.ev[i];
+                const int kind = ev_kind(e.op);
+                CellEv &ce = P.cev[i];
+                ce = CellEv{};
+                ce.qf[0] = fa[0] >= 0 ? e.q[fa[0]] : 0;
+                ce.qf[1] = fa[1] >= 0 ? e.q[fa[1]] : 0;
+                ce.qr = P.r_axis >= 0 ? e.q[P.r_axis] : 0;
+                if (kind == EV_ADC) {
+                    ce.kind = ev_gtype(e.op) == p ? CE_ADC : CE_ADC_OTHER;
+                    ce.row = e.prow;
+                    ce.win = e.win;
+                    ce.gtype = ev_gtype(e.op);
+                    continue;
+                }
+                // END: the advance alone (identity transition, trow = -1)
+                ce.kind = kind == EV_RF ? CE_RF : CE_END;
+                CellKey k{};
+                k.trow = kind == EV_RF ? e.row : -1;
+                k.gtype = kind == EV_RF ? ev_gtype(e.op) : p;
+                k.kp = P.kd[i][p - 1];
+                k.kr = P.r_axis >= 0 ? P.kd[i][P.r_axis] : 0.0;
+                k.tau = P.adv[i].tau;
+                int id = -1;
+                for (size_t j = 0; j < P.ckeys.size() && id < 0; ++j) {
+                    const CellKey &o = P.ckeys[j];
+                    if (o.trow == k.trow && o.gtype == k.gtype && near(o.kp, k.kp) &&
+                        near(o.kr, k.kr) && near(o.tau, k.tau))
+                        id = (int)j;
+                }
+                if (id < 0) {
+                    id = (int)P.ckeys.size();
+                    P.ckeys.push_back(k);
+                    // combined rows within 1 GiB (and row indices within int32)
+                    if ((int64_t)P.ckeys.size() * g->n_cells * 48 > ((int64_t)1 << 30))
+                        P.cell = false;
+                }
+                ce.row = (int)((int64_t)id * g->n_cells);
+            }
+            if (!P.cell) {
+                P.cev.clear();
+                P.ckeys.clear();
+                axis_tables(false);
+            }
         }
     }
     // 4) group-signal blocks: 256 samples x a slice of the groups
@@ -652,7 +761,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     const bool f64 = sizeof(R) == 8;
     using A = typename AdvOf<R>::T;
     GPlan<R> P;
-    plan_grouped<R>(c, s, g, P);
+    plan_grouped<R>(c, s, g, P, ph->n_coils == 0);
     R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(P.rows, 1) * 12 * sizeof(R));
     for (auto &t : P.tabs) {
         if constexpr (sizeof(R) == 4) {
@@ -698,6 +807,43 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             fa.qtab = qtab;
         }
     }
+    // cell form: combined rows C = T Adv of every distinct RF advance and cell
+    CellArgs ca{};
+    CellEv *d_cev = nullptr;
+    if constexpr (sizeof(R) == 4) {
+        if (P.cell) {
+            const int nk = (int)P.ckeys.size();
+            float *C_tab = (float *)scratch(
+                c, 23, std::max<int64_t>((int64_t)nk * g->n_cells, 1) * 12 * sizeof(float));
+            if (nk > 0) {
+                CellKey *d_keys = (CellKey *)scratch(c, 24, nk * sizeof(CellKey));
+                upload(c, d_keys, P.ckeys.data(), nk * sizeof(CellKey));
+                launch_cell_rows(c, d_keys, nk, g, T_tab, C_tab);
+            }
+            const int w = P.cell_w;
+            ca.n_thr = g->n_cell_thr[w];
+            ca.thr = g->cell_thr[w].as<int2>();
+            ca.cell_gp = g->cell_gp.as<int32_t>();
+            ca.cell_count = g->cell_count.as<int32_t>();
+            ca.M0 = fa.M0;
+            ca.aidx = fa.aidx;
+            ca.Mx = M;
+            ca.My = M + Kp;
+            ca.Mz = M + 2 * Kp;
+            ca.C_tab = C_tab;
+            ca.P_raw = d_P;
+            ca.Ablk = Ablk;
+            ca.qtab = fa.qtab;
+            int nf = 0;
+            for (int a = 0; a < 3; ++a)
+                if (P.free_bits & (1 << a)) ca.f_sh[nf++] = fa.ax_sh[a];
+            if (nf < 2) ca.f_sh[1] = 0;
+            ca.r_sh = P.r_axis >= 0 ? fa.ax_sh[P.r_axis] : 0;
+            for (int t = 0; t < 4; ++t) ca.gid[t] = fa.gid[t];
+            d_cev = (CellEv *)scratch(c, 25, P.cev.size() * sizeof(CellEv));
+            upload(c, d_cev, P.cev.data(), P.cev.size() * sizeof(CellEv));
+        }
+    }
     const double z0[3] = {0.0, 0.0, 0.0};
     const A zero = AdvOf<R>::make(z0, 0.0);
     GWin *dw = nullptr;
@@ -733,7 +879,18 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             fa.ev = d_ev + sp.b;
             fa.n_ev = (int)(sp.e - sp.b);
             fa.init_eq = (first && !g->has_M_init) ? 1 : 0;
-            launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
+            if constexpr (sizeof(R) == 4) {
+                if (P.cell) {
+                    ca.ev = d_cev + sp.b;
+                    ca.n_ev = (int)(sp.e - sp.b);
+                    ca.init_eq = fa.init_eq;
+                    launch_fused_cell(c, ca, P.form);
+                } else {
+                    launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
+                }
+            } else {
+                launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
+            }
             first = false;
             if (sp.fallback < 0) continue;
             const Subseq &q = s->sub[sp.fallback];
@@ -1377,10 +1534,10 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
 
 int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
-    static const int allowed[5][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
+    static const int allowed[6][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
                                       {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
-                                      {1, 2, 4, 8, 16, 32}};
-    if (param < 0 || param > 4) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
+                                      {1, 2, 4, 8, 16, 32}, {0, 4, 8, -1, -1, -1}};
+    if (param < 0 || param > 5) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
     for (int v : allowed[param]) ok |= v >= 0 && v == value;
     if (!ok) return set_err(c, MRSIM_EINVAL, "value not allowed for this tuning parameter");
@@ -1389,7 +1546,7 @@ int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
 }
 
 int mrsim_get_tuning(const mrsim_ctx *c, int param, int *value) {
-    if (!c || !value || param < 0 || param > 4) return MRSIM_EINVAL;
+    if (!c || !value || param < 0 || param > 5) return MRSIM_EINVAL;
     *value = c->tune[param];
     return MRSIM_OK;
 }
@@ -1408,6 +1565,7 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         // one parameter at a time, in the order they matter for the mode
         const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
         std::vector<std::pair<int, std::vector<int>>> plan;
+        if (grouped && precision == MRSIM_FP32) plan.push_back({MRSIM_TUNE_CELL_NI, {4, 8, 0}});
         if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8, 16, 32}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 4, 8, 16, 32, 128}});

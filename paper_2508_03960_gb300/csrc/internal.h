@@ -66,7 +66,7 @@ struct mrsim_ctx {
     std::vector<Pending> prof_pending;
     std::vector<cudaEvent_t> ev_pool;
     // growable scratch areas reused across calls
-    mrsim::DBuf scratch[24];
+    mrsim::DBuf scratch[32];
     // error word written by kernels with bounded waits / bounds checks
     mrsim::DBuf dev_err;
     // pinned host staging for uploads of per-run plans
@@ -76,7 +76,7 @@ struct mrsim_ctx {
     const struct mrsim_surrogate *sur = nullptr;
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
-    int tune[5] = {4, 2, 2, 0, 8};  // indexed by the MRSIM_TUNE_* parameters
+    int tune[6] = {4, 2, 2, 0, 8, 4};  // indexed by the MRSIM_TUNE_* parameters
 };
 
 struct mrsim_phantom_t {
@@ -154,6 +154,15 @@ struct mrsim_groups {
     int64_t n_ax[3] = {0, 0, 0};
     mrsim::DBuf ax_val[3];  // float [n_ax[a]]
     mrsim::DBuf ax_idx;     // int32 [K], layout order
+    // cells: maximal runs of one (primary gid, secondary gid) pair in the
+    // layout, in layout order: first isochromat, count and both group ids
+    mrsim::DBuf cell_start, cell_count, cell_gp, cell_gr;  // int32 [n_cells]
+    // per-thread work of the cell-mode fused kernel for 4 and 8 isochromats
+    // per thread: {first layout index, cell << 4 | count}; a cell of n
+    // isochromats has ceil(n / NI) threads whose isochromats interleave with
+    // stride ceil(n / NI) (a thread never straddles two cells)
+    mrsim::DBuf cell_thr[2];
+    int64_t n_cell_thr[2] = {0, 0};
     mrsim::DBuf perm;  // int32 [K]: layout position -> phantom index
     mrsim::DBuf x, y, z, T1, T2, dB0, M0, b1, M_init;  // layout order
     bool has_b1 = false, has_M_init = false;
@@ -308,6 +317,65 @@ struct FusedArgs {
     // receive-coil sensitivity (re, im planes, layout order) or null for S = 1
     const float *coil_re, *coil_im;
 };
+// Cell mode of the fused kernel (FP32): every thread holds isochromats of one
+// cell, so the positions on the primary axis and (if any) the secondary axis,
+// T1, T2, dB0 and b1 are the thread's own; only the phase on the remaining
+// ("free") axes differs between its isochromats.  An RF event then applies one
+// combined row C = T Adv per cell; a with-ADC event adds Q_free M_xy.
+// Event record of the cell form (32 bytes), decoded on the host.
+enum CellEvKind : int { CE_RF = 0, CE_END = 1, CE_ADC = 2, CE_ADC_OTHER = 3 };
+struct CellEv {
+    int kind;   // CellEvKind (CE_ADC: a window of the primary type)
+    int row;    // RF / END: first combined row (key * n_cells); ADC: first
+                // group-factor row (event * G_primary)
+    int win;    // ADC: offset of the window's block sums (complex entries)
+    int gtype;  // CE_ADC_OTHER: the window's gradient type
+    int qf[2];  // free-axis phasor table offsets (lower axis first)
+    int qr;     // ADC: secondary-axis phasor table offset
+    int pad;
+};
+struct CellArgs {
+    int64_t n_thr;            // threads that hold isochromats
+    const int2 *thr;          // per thread: {first layout index, cell << 4 | count}
+    const int32_t *cell_gp;   // primary group of each cell
+    const int32_t *cell_count;  // isochromats of each cell (thread stride ceil(count / NI))
+    const float *M0;
+    const int32_t *aidx;      // packed non-primary axis indices (layout order)
+    float *Mx, *My, *Mz;
+    int init_eq;
+    const CellEv *ev;
+    int n_ev;
+    const float *C_tab;       // [RF advance keys][cells][12]
+    const void *P_raw;        // per-(event, primary group) factors (with-ADC flush)
+    double *Ablk;             // complex block sums (interleaved re, im)
+    const float2 *qtab;       // per-event axis phasor tables
+    int f_sh[2];              // bit position of each free axis' index in aidx
+    int r_sh;                 // bit position of the secondary axis' index, or -1
+    const int32_t *gid[4];    // layout-order gids per gradient type (with-ADC
+                              // windows of the secondary or no-grads type)
+};
+// Which per-isochromat and per-thread phasors a cell-form launch applies
+// (fixed for the whole span, so the kernel is specialised on them).
+struct CellForm {
+    int ni;     // isochromats per thread (4, 8)
+    int nf;     // free axes (1, 2)
+    bool rfq;   // RF / END events rotate by the free-axis phasor
+    bool adq;   // with-ADC events rotate by the free-axis phasor
+    bool rb;    // with-ADC events rotate by the secondary-axis phasor
+};
+// One distinct RF advance of a cell run: C rows of every cell for transition
+// table rows [trow, trow + G_t) of gradient type gtype, after an advance with
+// moments kp (primary axis), kr (secondary axis) and duration tau.
+struct CellKey {
+    int64_t trow;
+    int gtype;
+    int pad;
+    double kp, kr, tau;
+};
+void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f);
+void launch_cell_rows(mrsim_ctx *c, const CellKey *d_keys, int n_keys, const mrsim_groups *g,
+                      const float *T_tab, float *C);
+void build_cell_threads(mrsim_ctx *c, mrsim_groups *g, const std::vector<int32_t> &count);
 // one axis table: out[j] = exp(-i 2 pi val[j] k) for j < n (cos, sin)
 struct AxItem {
     double k;      // gamma_bar * moment on the axis (cycles/m)

@@ -1,0 +1,408 @@
+// Cell mode of the fused grouped kernel (FP32; Sec. 2.3 update step and step
+// 1 of the with-ADC method, Eq. 9).
+//
+// The layout sorts isochromats by (with-ADC group, with-RF group).  A cell is
+// one run of a single pair: its isochromats share the primary-axis position,
+// the secondary-axis position (the with-RF group's axis), T1, T2, dB0 and b1,
+// so they differ only in their position on the remaining "free" axis (two
+// free axes when the with-RF subsequences carry no one-axis gradient).  Every
+// thread holds up to NI isochromats of ONE cell: a cell of n isochromats has
+// T = ceil(n / NI) threads, thread j holding isochromats j, j + T, ... (so
+// the lanes of a warp read consecutive table entries); missing isochromats
+// carry M = M0 = 0 and stay zero.  Every per-group quantity becomes a
+// per-thread one:
+//
+//  RF event:  the closed-form advance from the state time (Eqs. 4-5) factors
+//             into the cell's own part Adv (primary and secondary axis phase,
+//             dB0 tau, E2, E1) and the free-axis phase Q; the z-rotations Adv
+//             and Q commute, so  T Adv Q M = C (Q M)  with one combined affine
+//             row C = T Adv per (distinct advance, cell), built by k_cell_rows
+//             in FP64 and rounded to float.  Per isochromat: one phasor load
+//             (only if the free-axis moment is nonzero) and 12 FMAs.
+//  ADC event: the block-sum term of an isochromat is P_g Q_r Q_free M_xy
+//             (Eq. 9): the thread sums Q_free M_xy over its isochromats,
+//             multiplies once by its cell's secondary-axis phasor Q_r and its
+//             group's factor P_g and stages the partial.
+//  END event: the advance alone (a combined row with T = I), then the state
+//             is stored at the isochromats' layout positions.
+//
+// M stays in registers from the first event of the span to the last.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace mrsim {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBatch = 8;             // with-ADC windows per shared-memory flush
+constexpr int kAccFloats = 2048;      // block-sum staging per CTA (8 KB)
+constexpr int kEvChunk = 64;          // events staged in shared memory at a time
+constexpr int kPad = 0x7fffffff;      // key of a thread without isochromats
+
+struct CellSmem {
+    __align__(16) float acc[kAccFloats];           // staged block sums [batch][slot][re, im]
+    __align__(16) CellEv sev[kEvChunk];            // staged events
+    // per-thread partials of warps whose threads share one group, [window][thread]
+    // (row padded by one entry: conflict-free column reads)
+    __align__(16) float tpart[kBatch][kThreads + 1][2];
+    float wpart[kBatch][kThreads / 32][2];         // their per-warp sums
+    int batch_win[kBatch];
+    int wslot[kThreads / 32];                      // that group's slot, or -1
+};
+
+// exp(-i 2 pi sum_f r_f k_f) over the free axes from the event's tables
+template <int NF>
+__device__ __forceinline__ void free_phasor(const float2 *qtab, const int (&qf)[2], int f0,
+                                            int f1, float &c, float &s) {
+    const float2 q0 = __ldg(qtab + qf[0] + f0);
+    c = q0.x;
+    s = q0.y;
+    if constexpr (NF == 2) {
+        const float2 q1 = __ldg(qtab + qf[1] + f1);
+        const float nc = c * q1.x - s * q1.y;
+        s = s * q1.x + c * q1.y;
+        c = nc;
+    }
+}
+
+template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
+__global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(CellArgs a) {
+    __shared__ CellSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t t = t0 + tid;
+    const int64_t t_end = min(t0 + kThreads, a.n_thr);  // threads with work in this CTA
+    const float2 *qtab = a.qtab;
+
+    float mx[NI], my[NI], mz[NI], M0[NI];
+    int f0[NI], f1[NI];  // free-axis table indices of each isochromat
+    // isochromat i of this thread is layout position start + i * stride
+    int key = kPad, cell = 0, start = 0, stride = 0, n = 0, ridx = 0;
+    if (t < a.n_thr) {
+        const int2 d = a.thr[t];
+        start = d.x;
+        cell = d.y >> 4;
+        n = d.y & 15;
+        key = a.cell_gp[cell];
+        stride = (a.cell_count[cell] + NI - 1) / NI;
+    }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        int ai = 0;
+        if (i < n) {
+            const int k = start + i * stride;
+            M0[i] = a.M0[k];
+            ai = a.aidx[k];
+            if (a.init_eq) {
+                mx[i] = 0.0f;
+                my[i] = 0.0f;
+                mz[i] = M0[i];
+            } else {
+                mx[i] = a.Mx[k];
+                my[i] = a.My[k];
+                mz[i] = a.Mz[k];
+            }
+        } else {
+            M0[i] = mx[i] = my[i] = mz[i] = 0.0f;
+        }
+        f0[i] = (ai >> a.f_sh[0]) & 0xffff;
+        f1[i] = NF == 2 ? (ai >> a.f_sh[1]) & 0xffff : 0;
+        if (i == 0 && RB) ridx = (ai >> a.r_sh) & 0xffff;
+    }
+    // primary groups of this CTA: keys rise along the threads and every group
+    // between the first and the last one has isochromats here
+    const int32_t g_first = a.cell_gp[a.thr[t0].y >> 4];
+    const int32_t g_last = a.cell_gp[a.thr[t_end - 1].y >> 4];
+    const int S = (int)(g_last - g_first + 1);  // at most kThreads
+    const int B = max(1, min(kBatch, kAccFloats / (2 * S)));
+    for (int i = tid; i < B * S * 2; i += kThreads) sm.acc[i] = 0.0f;
+    // a warp whose threads all share one group stages per-thread partials
+    const int32_t w0 = __shfl_sync(0xffffffffu, key, 0);
+    const bool warp_uni = __all_sync(0xffffffffu, key == w0 || key == kPad) && w0 != kPad;
+    if (lane == 0) sm.wslot[warp] = warp_uni ? w0 - g_first : -1;
+    const bool any_uni = __syncthreads_or(warp_uni) != 0;
+    const float4 *Pt = reinterpret_cast<const float4 *>(a.P_raw);
+    const int pkey = key == kPad ? g_first : key;  // group-factor column (padding: any valid)
+
+    int nb = 0;  // windows staged (uniform)
+    auto flush = [&]() {
+        if (warp_uni) {
+            // column sums of this warp's staged partials: lane (h, b) adds
+            // kBatch threads of part h for window b, then the parts combine
+            __syncwarp();
+            const int b = lane % kBatch, h = lane / kBatch;
+            float sr = 0.0f, si = 0.0f;
+            if (b < nb) {
+                const float(*col)[2] = &sm.tpart[b][warp * 32 + h * kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    sr += col[j][0];
+                    si += col[j][1];
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= kBatch; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (h == 0 && b < nb) {
+                sm.wpart[b][warp][0] = sr;
+                sm.wpart[b][warp][1] = si;
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * S; q += kThreads) {
+            const int b = q / S, slot = q - b * S;
+            float sr = sm.acc[2 * q], si = sm.acc[2 * q + 1];
+            if (any_uni) {
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    if (sm.wslot[w] == slot) {
+                        sr += sm.wpart[b][w][0];
+                        si += sm.wpart[b][w][1];
+                    }
+                }
+            }
+            if (sr != 0.0f || si != 0.0f) {
+                const int64_t o = 2 * ((int64_t)sm.batch_win[b] + g_first + slot);
+                if (slot != 0 && slot != S - 1) {
+                    // a group strictly inside the CTA has no other contributor
+                    *reinterpret_cast<double2 *>(&a.Ablk[o]) = make_double2(sr, si);
+                } else {
+                    atomicAdd(&a.Ablk[o], (double)sr);
+                    atomicAdd(&a.Ablk[o + 1], (double)si);
+                }
+            }
+            // cleared even when the total is zero: staged partials can cancel
+            // exactly, and a value left here would be added to a later window
+            sm.acc[2 * q] = 0.0f;
+            sm.acc[2 * q + 1] = 0.0f;
+        }
+        __syncthreads();
+        nb = 0;
+    };
+
+    auto stage = [&](int win, float sr, float si) {
+        if (warp_uni) {
+            sm.tpart[nb][tid][0] = sr;
+            sm.tpart[nb][tid][1] = si;
+        } else {
+            // keys rise along the lanes: a segmented inclusive scan leaves each
+            // run's sum in the run's last lane
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float orr = __shfl_up_sync(0xffffffffu, sr, d);
+                const float oii = __shfl_up_sync(0xffffffffu, si, d);
+                const int32_t ok = __shfl_up_sync(0xffffffffu, key, d);
+                if (lane >= d && ok == key) {
+                    sr += orr;
+                    si += oii;
+                }
+            }
+            const int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
+            if ((lane == 31 || nk != key) && key != kPad) {
+                float *accb = sm.acc + 2 * (nb * S + (key - g_first));
+                atomicAdd(accb, sr);
+                atomicAdd(accb + 1, si);
+            }
+        }
+        if (tid == 0) sm.batch_win[nb] = win;
+        ++nb;
+        if (nb == B) flush();
+    };
+
+    for (int e0 = 0; e0 < a.n_ev; e0 += kEvChunk) {
+        const int ne = min(kEvChunk, a.n_ev - e0);
+        __syncthreads();
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(a.ev + e0);
+            int4 *dst = reinterpret_cast<int4 *>(sm.sev);
+            const int nw = ne * (int)(sizeof(CellEv) / sizeof(int4));
+            for (int q = tid; q < nw; q += kThreads) dst[q] = src[q];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int e = 0; e < ne; ++e) {
+            const int4 ev0 = *reinterpret_cast<const int4 *>(&sm.sev[e]);
+            const int kind = ev0.x;
+            if (kind <= CE_END) {
+                // RF: advance and transition, M <- C (Q M); END: the advance
+                // alone (C built with T = I), then the state is stored
+                const float4 *cr =
+                    reinterpret_cast<const float4 *>(a.C_tab + ((int64_t)ev0.y + cell) * 12);
+                const float4 r0 = __ldg(cr), r1 = __ldg(cr + 1), r2 = __ldg(cr + 2);
+                int qf[2] = {0, 0};
+                if constexpr (RFQ) {
+                    const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
+                    qf[0] = ev1.x;
+                    qf[1] = ev1.y;
+                }
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    float x = mx[i], y = my[i];
+                    if constexpr (RFQ) {
+                        float c, s;
+                        free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
+                        const float nx = c * x + s * y;  // (c - i s) (x + i y)
+                        y = c * y - s * x;
+                        x = nx;
+                    }
+                    const float z = mz[i], m0 = M0[i];
+                    mx[i] = r0.x * x + r0.y * y + r0.z * z + r0.w * m0;
+                    my[i] = r1.x * x + r1.y * y + r1.z * z + r1.w * m0;
+                    mz[i] = r2.x * x + r2.y * y + r2.z * z + r2.w * m0;
+                }
+                if (kind == CE_END && a.Mx) {
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        if (i < n) {
+                            const int k = start + i * stride;
+                            a.Mx[k] = mx[i];
+                            a.My[k] = my[i];
+                            a.Mz[k] = mz[i];
+                        }
+                    }
+                }
+            } else {
+                // with-ADC window: block-sum term P_g Q_r sum_i Q_free M_xy (Eq. 9);
+                // the group factor is issued first, it multiplies the sums
+                const float4 P = __ldg(Pt + ev0.y + pkey);
+                const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
+                float sr = 0.0f, si = 0.0f;
+                const int qf[2] = {ev1.x, ev1.y};
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    if constexpr (ADQ) {
+                        float c, s;
+                        free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
+                        sr += c * mx[i] + s * my[i];
+                        si += c * my[i] - s * mx[i];
+                    } else {
+                        sr += mx[i];
+                        si += my[i];
+                    }
+                }
+                if constexpr (RB) {
+                    // the cell's secondary-axis phasor, once per thread
+                    const float2 q = __ldg(qtab + ev1.z + ridx);
+                    const float nr = q.x * sr + q.y * si;
+                    si = q.x * si - q.y * sr;
+                    sr = nr;
+                }
+                {
+                    const float nr = P.x * sr - P.y * si;
+                    si = P.x * si + P.y * sr;
+                    sr = nr;
+                }
+                if (kind == CE_ADC) {
+                    stage(ev0.z, sr, si);
+                } else if (n > 0) {
+                    // a window of the secondary or no-grads type: its group is
+                    // constant in the cell, the thread adds its term directly
+                    const int64_t o = 2 * ((int64_t)ev0.z + a.gid[ev0.w][start]);
+                    atomicAdd(&a.Ablk[o], (double)sr);
+                    atomicAdd(&a.Ablk[o + 1], (double)si);
+                }
+            }
+        }
+    }
+    if (nb > 0) flush();
+}
+
+template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
+void launch_cell_v(mrsim_ctx *c, const CellArgs &a) {
+    const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
+    k_fused_cell<NI, NF, RFQ, ADQ, RB><<<nb, kThreads, 0, c->stream>>>(a);
+}
+template <int NI, int NF, bool RFQ, bool ADQ>
+void launch_cell_rb(mrsim_ctx *c, const CellArgs &a, bool rb) {
+    if (rb) launch_cell_v<NI, NF, RFQ, ADQ, true>(c, a);
+    else launch_cell_v<NI, NF, RFQ, ADQ, false>(c, a);
+}
+template <int NI, int NF>
+void launch_cell_q(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
+    if (f.rfq && f.adq) launch_cell_rb<NI, NF, true, true>(c, a, f.rb);
+    else if (f.rfq) launch_cell_rb<NI, NF, true, false>(c, a, f.rb);
+    else if (f.adq) launch_cell_rb<NI, NF, false, true>(c, a, f.rb);
+    else launch_cell_rb<NI, NF, false, false>(c, a, f.rb);
+}
+
+// C = T Adv for every (key, cell): Adv advances a cell's isochromats by the
+// key's primary- and secondary-axis moments and duration (Eqs. 4-5, evaluated
+// in FP64 from the cell's primary group and secondary-axis position), T is the
+// cell's combined transition row of the key's gradient type (Eq. 7).
+__global__ void k_cell_rows(const CellKey *keys, int n_keys, int64_t nc, const int32_t *cstart,
+                            const int32_t *cgp, const int32_t *cgr, const int32_t *gid_none,
+                            int p, int r, const double *par_p, int64_t Gp, const float *pos_r,
+                            const float *T_tab, float *C) {
+    const int64_t n = (int64_t)n_keys * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / nc, c = i - j * nc;
+        const CellKey k = keys[j];
+        const int gp = cgp[c];
+        // trow < 0: the advance alone (end of a span), T = [I | 0]
+        float Tid[12] = {1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f};
+        const float *T = Tid;
+        if (k.trow >= 0) {
+            const int gt = k.gtype == p ? gp : k.gtype == r ? cgr[c] : gid_none[cstart[c]];
+            T = T_tab + (k.trow + gt) * 12;
+        }
+        double ph = par_p[gp] * k.kp + par_p[3 * Gp + gp] * k.tau;
+        if (k.kr != 0.0) ph += (double)pos_r[cstart[c]] * k.kr;
+        ph -= rint(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        const double T1 = par_p[Gp + gp], T2 = par_p[2 * Gp + gp];
+        const double E2 = isinf(T2) ? 1.0 : exp(-k.tau / T2);
+        const double E1 = isinf(T1) ? 1.0 : exp(-k.tau / T1);
+        const double u = -expm1(-k.tau / T1);  // 1 - E1 (0 for T1 = inf)
+        const double cr = E2 * cs, ci = E2 * sn;
+        float *o = C + i * 12;
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+            const double A0 = T[4 * row], A1 = T[4 * row + 1], A2 = T[4 * row + 2];
+            const double b = T[4 * row + 3];
+            // mx' = E2 (c mx + s my), my' = E2 (c my - s mx), mz' = E1 mz + (1 - E1) M0
+            o[4 * row] = (float)(A0 * cr - A1 * ci);
+            o[4 * row + 1] = (float)(A0 * ci + A1 * cr);
+            o[4 * row + 2] = (float)(A2 * E1);
+            o[4 * row + 3] = (float)(A2 * u + b);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
+    if (a.n_thr <= 0) return;
+    KScope ks(c, "fused_cell_f32");
+    if (f.ni == 8) {
+        if (f.nf == 2) launch_cell_q<8, 2>(c, a, f);
+        else launch_cell_q<8, 1>(c, a, f);
+    } else {
+        if (f.nf == 2) launch_cell_q<4, 2>(c, a, f);
+        else launch_cell_q<4, 1>(c, a, f);
+    }
+}
+
+void launch_cell_rows(mrsim_ctx *c, const CellKey *d_keys, int n_keys, const mrsim_groups *g,
+                      const float *T_tab, float *C) {
+    const int64_t nc = g->n_cells;
+    const int64_t n = (int64_t)n_keys * nc;
+    if (n <= 0) return;
+    const int p = g->primary, r = g->secondary;
+    const float *pos[3] = {g->x.as<float>(), g->y.as<float>(), g->z.as<float>()};
+    KScope ks(c, "cell_rows");
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16));
+    k_cell_rows<<<grid, 256, 0, c->stream>>>(
+        d_keys, n_keys, nc, g->cell_start.as<int32_t>(), g->cell_gp.as<int32_t>(),
+        g->cell_gr.as<int32_t>(), g->built[G_NONE] ? g->gid_sorted[G_NONE].as<int32_t>() : nullptr,
+        p, r, g->tab[p].d_par64.as<double>(), g->n_groups[p],
+        (r >= G_X && r <= G_Z) ? pos[r - 1] : nullptr, T_tab, C);
+}
+
+}  // namespace mrsim

@@ -320,6 +320,27 @@ __global__ void k_scatter(int64_t K, const int32_t *cell, const int32_t *cell_of
     }
 }
 
+// Thread t of the cell-mode fused kernel: cell c with off[c] <= t < off[c + 1]
+// has T = ceil(count / NI) threads; its thread j = t - off[c] takes the cell's
+// isochromats j, j + T, j + 2T, ... (at most NI), so the lanes of a warp hold
+// consecutive isochromats of the layout at every register index.
+__global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *start,
+                               const int32_t *count, int NI, int2 *out) {
+    const int64_t n = off[nc];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nc - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int j = (int)(t - off[lo]);
+        const int T = (count[lo] + NI - 1) / NI;
+        const int n_iso = (count[lo] - j + T - 1) / T;
+        out[t] = make_int2(start[lo] + j, (int)((lo << 4) | n_iso));
+    }
+}
+
 template <typename T>
 __global__ void k_gather(int64_t K, const int32_t *perm, const T *in, T *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
@@ -506,6 +527,26 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
     }
     DBuf doff = dalloc(nc * sizeof(int32_t));
     upload(c, doff.p, off.data(), nc * 4);
+    {
+        // cell tables in layout order, for the cell-mode fused kernel
+        std::vector<int32_t> s_start(nc), s_cnt(nc), s_gp(nc), s_gr(nc);
+        for (int64_t i = 0; i < nc; ++i) {
+            const int32_t cc = order[i];
+            s_start[i] = off[cc];
+            s_cnt[i] = hc[cc];
+            s_gp[i] = ha[cc];
+            s_gr[i] = hb[cc];
+        }
+        auto up32 = [&](DBuf &d, const std::vector<int32_t> &v) {
+            d = dalloc(std::max<int64_t>(nc, 1) * sizeof(int32_t));
+            upload(c, d.p, v.data(), nc * sizeof(int32_t));
+        };
+        up32(g->cell_start, s_start);
+        up32(g->cell_count, s_cnt);
+        up32(g->cell_gp, s_gp);
+        up32(g->cell_gr, s_gr);
+        build_cell_threads(c, g, s_cnt);
+    }
     MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
     g->perm = dalloc(K * sizeof(int32_t));
     {
@@ -546,6 +587,29 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
             K, perm, g->gid_orig[t].as<int32_t>(), g->gid_sorted[t].as<int32_t>());
     }
     sync(c);
+}
+
+void build_cell_threads(mrsim_ctx *c, mrsim_groups *g, const std::vector<int32_t> &count) {
+    const int64_t nc = (int64_t)count.size();
+    g->n_cell_thr[0] = g->n_cell_thr[1] = 0;
+    if (nc <= 0 || nc >= (1LL << 27)) return;  // cell index must fit 27 bits
+    DBuf d_off = dalloc((nc + 1) * sizeof(int64_t));
+    for (int w = 0; w < 2; ++w) {
+        const int NI = w == 0 ? 4 : 8;
+        std::vector<int64_t> off(nc + 1, 0);
+        for (int64_t i = 0; i < nc; ++i) off[i + 1] = off[i] + (count[i] + NI - 1) / NI;
+        const int64_t n = off[nc];
+        if (n >= (1LL << 31)) return;
+        upload(c, d_off.p, off.data(), (nc + 1) * sizeof(int64_t));
+        g->cell_thr[w] = dalloc(n * sizeof(int2));
+        KScope ks(c, "layout_cell_threads");
+        k_cell_threads<<<grid_for(c, n), 256, 0, c->stream>>>(
+            nc, d_off.as<int64_t>(), g->cell_start.as<int32_t>(), g->cell_count.as<int32_t>(), NI,
+            g->cell_thr[w].as<int2>());
+        // the next upload reuses d_off: wait for this expansion first
+        sync(c);
+        g->n_cell_thr[w] = n;
+    }
 }
 
 // Distinct positions of the two non-primary axes (layout order) and the

@@ -28,6 +28,7 @@ FP32, FP64 = 0, 1
 PTR_DEVICE, OUT_DEVICE = 1, 2
 TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1, 2, 3
 TUNE_PRECOMP_STEPS = 4
+TUNE_CELL_NI = 5
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
@@ -348,7 +349,7 @@ def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):
            "mrsim_autotune")
     return {p: mrsim_get_tuning(ctx, p) for p in (TUNE_FUSED_NI, TUNE_PLAIN_RF_NI,
                                                    TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES,
-                                                   TUNE_PRECOMP_STEPS)}
+                                                   TUNE_PRECOMP_STEPS, TUNE_CELL_NI)}
 
 
 def mrsim_surrogate_train(ctx, seq, lo, hi, n_train=1 << 22, epochs=20, batch=16384, lr=3e-3,

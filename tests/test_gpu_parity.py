@@ -333,7 +333,8 @@ def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
 
 def test_tuning_parameters_are_validated(mrsim, ctx):
     for param, bad in ((mrsim.TUNE_FUSED_NI, 3), (mrsim.TUNE_PRECOMP_LANES, 64),
-                       (mrsim.TUNE_PRECOMP_STEPS, 64), (5, 1), (-1, 1)):
+                       (mrsim.TUNE_PRECOMP_STEPS, 64), (mrsim.TUNE_CELL_NI, 1), (6, 1),
+                       (-1, 1)):
         with pytest.raises(mrsim.MrsimError):
             mrsim.mrsim_set_tuning(ctx.h, param, bad)
     before = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS)
@@ -376,16 +377,21 @@ def cancelling_group_case(ni, n_a):
     return ph, b.build()
 
 
-@pytest.mark.parametrize("ni,n_a", [(1, 16), (2, 32), (4, 64)])
-def test_group_sum_cancelling_exactly(mrsim, ctx, ni, n_a):
+@pytest.mark.parametrize("cell,ni,n_a", [(0, 1, 16), (0, 2, 32), (0, 4, 64), (4, 4, 64),
+                                         (8, 8, 128)])
+def test_group_sum_cancelling_exactly(mrsim, ctx, cell, ni, n_a):
     """A group whose staged with-ADC partials cancel to exactly zero in one
     window must leave nothing behind for the window that reuses its staging
-    slot (a leftover partial once leaked into a later window)."""
+    slot (a leftover partial once leaked into a later window).  Cells of 32
+    isochromats keep the cell form's threads on the same isochromats as the
+    per-isochromat form's."""
     ph, seq = cancelling_group_case(ni, n_a)
     ref, Mref = oracle.simulate(ph, seq)
-    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, ni)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, cell)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, min(ni, 4))
     try:
         sig, M = run_both(mrsim, ctx, ph, seq, mrsim.GROUPED, 0)
         check(sig, M, ref, Mref, 0)
     finally:
         mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, 4)
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 4)
