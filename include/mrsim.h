@@ -360,7 +360,7 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              holds isochromats of one (with-ADC group,
  *                              with-RF group) cell and applies one combined
  *                              row per cell to each with-RF subsequence): 4
- *                              (default) or 8; 0 turns the cell form off (the
+ *                              or 8 (default); 0 turns the cell form off (the
  *                              per-isochromat form of MRSIM_TUNE_FUSED_NI runs).
  *                              Runs with receive coils, per-isochromat
  *                              advances ("direct" form) or gradient types that

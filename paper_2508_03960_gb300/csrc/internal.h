@@ -76,7 +76,7 @@ struct mrsim_ctx {
     const struct mrsim_surrogate *sur = nullptr;
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
-    int tune[6] = {4, 2, 2, 0, 8, 4};  // indexed by the MRSIM_TUNE_* parameters
+    int tune[6] = {4, 2, 2, 0, 8, 8};  // indexed by the MRSIM_TUNE_* parameters
 };
 
 struct mrsim_phantom_t {

@@ -36,7 +36,7 @@ namespace mrsim {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBatch = 8;             // with-ADC windows per shared-memory flush
+constexpr int kBatch = 16;            // with-ADC windows per shared-memory flush
 constexpr int kAccFloats = 2048;      // block-sum staging per CTA (8 KB)
 constexpr int kEvChunk = 64;          // events staged in shared memory at a time
 constexpr int kPad = 0x7fffffff;      // key of a thread without isochromats

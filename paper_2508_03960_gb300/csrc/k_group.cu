@@ -341,6 +341,44 @@ __global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *st
     }
 }
 
+// Sorts every cell's run of the layout permutation by phantom index (the
+// scatter leaves members in atomic order): the layout becomes deterministic,
+// and along a cell consecutive positions hold isochromats in phantom order,
+// so neighbouring lanes of the fused kernel read neighbouring table entries.
+// One CTA per cell (bitonic sort in shared memory); runs longer than
+// kSortMax keep the scatter order.
+constexpr int kSortMax = 4096;
+__global__ void __launch_bounds__(256) k_sort_cells(const int32_t *cstart, const int32_t *ccount,
+                                                    int64_t nc, int32_t *perm) {
+    __shared__ int32_t v[kSortMax];
+    for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        const int n = ccount[c];
+        if (n < 2 || n > kSortMax) continue;  // uniform in the CTA
+        int p2 = 2;
+        while (p2 < n) p2 <<= 1;
+        const int s = cstart[c];
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) v[i] = i < n ? perm[s + i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= p2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const int x = v[i], y = v[l];
+                        if ((x > y) == ((i & k) == 0)) {
+                            v[i] = y;
+                            v[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) perm[s + i] = v[i];
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void k_gather(int64_t K, const int32_t *perm, const T *in, T *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
@@ -553,6 +591,14 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
         KScope ks(c, "layout_scatter");
         k_scatter<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), doff.as<int32_t>(),
                                                          cnt.as<int32_t>(), g->perm.as<int32_t>());
+    }
+    {
+        KScope ks(c, "layout_sort_cells");
+        const unsigned grid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>(nc, (int64_t)c->sm_count * 16));
+        k_sort_cells<<<grid, 256, 0, c->stream>>>(g->cell_start.as<int32_t>(),
+                                                  g->cell_count.as<int32_t>(), nc,
+                                                  g->perm.as<int32_t>());
     }
     const int32_t *perm = g->perm.as<int32_t>();
     auto gather_f = [&](DBuf &dst, const DBuf &src) {

@@ -43,7 +43,7 @@ def run_cell(mrsim, ctx, ph, seq, cell_ni):
         prof = mrsim.mrsim_profile_get(ctx.h)
     finally:
         mrsim.mrsim_profile_enable(ctx.h, False)
-        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 4)
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 8)
         ctx.free("grp", hg)
         ctx.free("seq", hs)
         ctx.free("ph", hp)
@@ -187,6 +187,6 @@ def test_cell_tuning_values(mrsim, ctx):
     for bad in (1, 2, 16, -4):
         with pytest.raises(mrsim.MrsimError):
             mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, bad)
-    for v in (0, 8, 4):
+    for v in (0, 4, 8):
         mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, v)
         assert mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_CELL_NI) == v

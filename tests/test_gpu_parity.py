@@ -394,4 +394,4 @@ def test_group_sum_cancelling_exactly(mrsim, ctx, cell, ni, n_a):
         check(sig, M, ref, Mref, 0)
     finally:
         mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_FUSED_NI, 4)
-        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 4)
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 8)
