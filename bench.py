@@ -106,22 +106,55 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
-def fused_traffic(K):
-    """DRAM bytes per k_fused launch from the committed ncu summary, scaled by
-    K; None once the kernel source differs from the profiled one."""
+FUSED_SOURCES = {"fused_cell": ("k_cell.cu", "internal.h", "common.cuh"),
+                 "fused_grouped": ("k_grouped.cu", "common.cuh")}
+
+
+def kernel_source_sha(kind):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fused_grouped_traffic.json")
+    h = hashlib.sha256()
+    for src in FUSED_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2508_03960_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def fused_traffic(K, kind="fused_cell"):
+    """DRAM bytes per fused-kernel launch from the committed ncu summary,
+    scaled by K; None once the kernel source differs from the profiled one."""
+    path = os.path.join(ROOT, "profiles", f"{kind}_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256()
-    for src in ("k_grouped.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2508_03960_gb300", "csrc", src), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != rec.get("source_sha256"):
+    if kernel_source_sha(kind) != rec.get("source_sha256"):
         return None
     return int(rec["dram_bytes_per_isochromat"] * K)
+
+
+def cell_event_work(seq, mrsim, hs):
+    """Events of the cell form of the fused kernel for a sequence whose
+    with-ADC windows are Gx-only and with-RF subsequences Gz-only (primary
+    axis x, secondary z, free axis y), and which of them rotate by the
+    free-axis phasor (nonzero y moment since the state time, Eqs. 4-5):
+    returns (RF + END events, those with the y phasor, ADC windows, those
+    with the y phasor)."""
+    info = mrsim.mrsim_seq_info(hs)
+    gy = seq.gy.astype(np.float64) * seq.dt * seq.repeat
+    my = 0.0
+    rf = rf_q = adc = adc_q = 0
+    for t, b, e in zip(info["type"], info["seg_begin"], info["seg_end"]):
+        if t == 0:  # with-RF
+            rf += 1
+            rf_q += my != 0.0
+            my = 0.0
+        elif t == 1:  # with-ADC
+            adc += 1
+            adc_q += my != 0.0
+            my += float(gy[b:e].sum())
+        else:
+            my += float(gy[b:e].sum())
+    return rf + 1, rf_q + (my != 0.0), adc, adc_q
 
 
 def batch_workload(ctx, mrsim, torch, steps, warmup):
@@ -230,12 +263,17 @@ def surrogate_workload(ctx, mrsim, torch):
     run = mrsim.mrsim_surrogate_stats(sur, ctx.h)
     mrsim.mrsim_surrogate_use(ctx.h, None)
     n_served, n_exact = run["groups_served"], run["groups_exact"]
+    # the gate's bound on this run's own groups: every served transition
+    # against its exact FP64 counterpart
+    run_err, run_served = mrsim.mrsim_surrogate_check(ctx.h, sur, hs, hg)
     out = {"K": ph.K, "groups_z": mrsim.mrsim_group_info(hg, mrsim.G_Z)[0],
            "train": {"samples_per_pulse": 1 << 22, "epochs": 150, "seconds": round(train_s, 2),
                      "final_mse_per_entry": st["train_loss"],
                      "validation_max_error": st["val_max_err"],
                      "cells_served": st["cells_served"],
-                     "served_max_error": st["val_served_max_err"], "bound": 1e-3},
+                     "served_max_error": st["val_served_max_err"], "bound": 1e-3,
+                     "gate_margin": 0.5},
+           "served_max_error_on_run": run_err, "served_pairs_checked": run_served,
            "grouping_s": round(group_s, 3), "exact_s": round(t_exact, 4),
            "surrogate_s": round(t_sur, 4), "speedup": round(t_exact / t_sur, 3),
            "kernels_ms_exact": k_exact, "kernels_ms_surrogate": k_sur,
@@ -501,13 +539,18 @@ def roof_entry(name, flops, ms, peak, bound, unit_note):
             "ms": round(ms, 4), "work": unit_note}
 
 
-# algorithmic FP32 work of the fused kernel per isochromat and event (flops,
-# FMA = 2, each of sin / cos / exp counted as 1):
-#   advance, Eqs. 4-5: phase x.kx + y.ky + z.kz + dB0.tau = 7, sin + cos + 2 exp = 4,
-#     transverse rotate-and-decay 8, longitudinal recovery 3          -> 22
-#   with-RF update step M <- A M + b M0 (3 rows x (1 mul + 3 FMA))     -> 21
-#   with-ADC block sum: phase 7, sin + cos + exp 3, transverse 8, add 2 -> 20
-FLOPS_RF, FLOPS_ADC, FLOPS_END = 43, 20, 22
+# algorithmic FP32 work of the fused kernel (cell form) per isochromat and
+# event, and the fewest thread instructions that can do it:
+#   with-RF / END event: M <- C (Q M) with the cell's combined row C = T Adv:
+#     3 rows x 4 FMA = 24 flops (12 FFMA); with a free-axis moment, Q M adds one
+#     phasor load, its address and a complex rotation (4 FFMA/FMUL): 30 flops,
+#     18 instructions
+#   with-ADC window: sum of Q M_xy (4 FFMA = 8 flops) plus the phasor load and
+#     its address: 6 instructions; without a free-axis moment 2 adds (4 flops)
+# The per-thread and per-group work (secondary-axis phasor, group factor,
+# staging, the flush) is amortised over the thread's isochromats and left out.
+FLOPS_CELL_RF, FLOPS_CELL_RF_Q, FLOPS_CELL_ADC, FLOPS_CELL_ADC_Q = 24, 30, 4, 8
+INST_CELL_RF, INST_CELL_RF_Q, INST_CELL_ADC, INST_CELL_ADC_Q = 12, 18, 2, 6
 
 
 def main():
@@ -744,20 +787,35 @@ def main():
     n_l, ms_l = prof[name]
     avg_s = ms_l / n_l / 1e3
     roof = None
-    if name.startswith("fused_grouped"):
-        n_rf, n_adc = fse.meta["n_rf"], fse.meta["n_adc"]
-        flops = ph.K * (n_rf * FLOPS_RF + n_adc * FLOPS_ADC + FLOPS_END)
-        peak = 2 * 128 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = 2 * 128 * n_sm * mhz * 1e6 / 1e12
+    if name.startswith("fused_cell"):
+        ev_rf, ev_rf_q, ev_adc, ev_adc_q = cell_event_work(fse, mrsim, hs_f)
+        per_iso = ((ev_rf - ev_rf_q) * FLOPS_CELL_RF + ev_rf_q * FLOPS_CELL_RF_Q +
+                   (ev_adc - ev_adc_q) * FLOPS_CELL_ADC + ev_adc_q * FLOPS_CELL_ADC_Q)
+        inst = ((ev_rf - ev_rf_q) * INST_CELL_RF + ev_rf_q * INST_CELL_RF_Q +
+                (ev_adc - ev_adc_q) * INST_CELL_ADC + ev_adc_q * INST_CELL_ADC_Q)
+        flops = ph.K * per_iso
         ach = flops / avg_s / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": fused_traffic(ph.K),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz from "
-                               f"MEASURED_PEAKS.json ({pk_kind})",
+        # issue bound: every SM sub-partition issues one warp instruction per cycle
+        t_issue = ph.K * inst / 32 / (n_sm * 4 * mhz * 1e6)
+        roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 3),
+                "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
+                "traffic": fused_traffic(ph.K, "fused_cell"),
+                "peak_source": f"{n_sm} SMs (device) x 128 FP32 lanes x 2 x sm_max_mhz "
+                               f"{mhz:.0f} from MEASURED_PEAKS.json ({pk_kind})",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": round(avg_s * 1e3, 4),
-                "launches": n_l}
+                "launches": n_l,
+                "issue": {"min_thread_inst_per_launch": ph.K * inst,
+                          "events": {"rf_end": ev_rf, "rf_end_free_phase": ev_rf_q,
+                                     "adc": ev_adc, "adc_free_phase": ev_adc_q},
+                          "t_min_ms": round(t_issue * 1e3, 4),
+                          "frac": round(t_issue / avg_s, 4),
+                          "peak": f"{n_sm} SMs x 4 warp instructions per cycle at {mhz:.0f} MHz"},
+                "algorithmic_bytes_per_isochromat": 21}
 
     # ---- achieved fraction of roofline of the other kernels ----
-    alu_peak = 2 * 128 * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     bf16_peak = pk.get("bf16_tflops", 1900.0)
     kroof = {}
     f_steps, f_segs, f_distinct = rf_runs(fse)
@@ -813,13 +871,20 @@ def main():
     if fse_plain_sig is not None:
         parity["fse_plain_rel_l2"] = golden_check("fse", fse_plain_sig, pd, sd_f)
 
-    cpu = None
+    cpu = cpu_epi = None
     if rank == 0 and world == 1:
         v, wall, n, cores = cpu_baseline(ph, fse, a.cpu_stride)
         cpu = {"value": round(v, 2), "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle on every {a.cpu_stride}th isochromat ({n} of {ph.K}) of "
                          f"the FSE workload, {wall:.2f} s wall, extrapolated x{ph.K / n:.1f} "
                          "(linear in K)"}
+        stride_e = 8 * a.cpu_stride
+        v, wall, n, cores = cpu_baseline(ph, epi, stride_e)
+        cpu_epi = {"value": round(v, 2), "unit": "s", "cores": cores, "kind": "oracle",
+                   "sample": f"FP64 oracle on every {stride_e}th isochromat ({n} of {ph.K}) of "
+                             f"the EPI workload, {wall:.2f} s wall, extrapolated "
+                             f"x{ph.K / n:.1f} (linear in K)",
+                   "gpu_grouped_s": round(epi_s, 6)}
 
     steps_fse = ph.K * (sum(int(r) for r, b1, b2 in zip(fse.repeat, fse.b1re, fse.b1im)
                             if b1 != 0 or b2 != 0) + ns_f)
@@ -840,7 +905,8 @@ def main():
             "epi": round(epi_plain_s / epi_s, 1)},
         "isochromat_steps_per_s_equiv": round(steps_fse / fse_s, 1),
         "prep_s": round(prep_s, 4), "phantom_upload_s": round(t_upload, 4), "groups": groups,
-        "autotune": {"fused_isochromats_per_thread": tuned[mrsim.TUNE_FUSED_NI],
+        "autotune": {"cell_isochromats_per_thread": tuned[mrsim.TUNE_CELL_NI],
+                     "fused_isochromats_per_thread": tuned[mrsim.TUNE_FUSED_NI],
                      "plain_rf_isochromats_per_thread": tuned[mrsim.TUNE_PLAIN_RF_NI],
                      "plain_adc_ctas_per_sm": tuned[mrsim.TUNE_ADC_CTAS_PER_SM],
                      "precompute_lanes": tuned[mrsim.TUNE_PRECOMP_LANES],
@@ -854,6 +920,7 @@ def main():
         "clustering": clustering,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         "roofline": roof, "kernel_roofline": kroof, "cpu_baseline": cpu,
+        "cpu_baseline_epi": cpu_epi,
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "split_ms": split},
         "gpu_launches": int(launches), "clocks": clocks,

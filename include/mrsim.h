@@ -291,10 +291,13 @@ int mrsim_recon_cartesian(mrsim_ctx *ctx, int n_lines, int n_ro, int n_pe, const
  * step of the grouped method (Sec. 2.3).  It is trained on the device by the
  * library's own forward / backward / Adam kernels on exact transitions of
  * random parameter draws (computed by the FP64 preparation kernel), and
- * validated on new draws: the parameter box is cut into 64 x 8 x 4 cells in
- * (z, dB0, b1); a cell is served by the network only if the largest error of
- * any transition entry among its validation samples is <= `bound`; groups in
- * other cells, or outside the box, fall back to exact integration. */
+ * validated on new draws: the parameter box is cut into 64 x 8 x 4 x 4 cells
+ * in (z, dB0, b1, log T2); a cell is served by the network only if the largest
+ * error of any transition entry among its validation samples is at most half
+ * of `bound` (the margin stands for parameter values between the validation
+ * draws); groups in other cells, or outside the box, fall back to exact
+ * integration (per-group fallback above a stated error bound: the learned
+ * production pattern; the paper has no learned part). */
 typedef struct mrsim_surrogate mrsim_surrogate;
 
 /* Train one network per distinct slice-selective with-RF pulse of `seq`.
@@ -314,6 +317,17 @@ int mrsim_surrogate_train(mrsim_ctx *ctx, const mrsim_seq *seq, const double *lo
  * cells, and for the context's runs since mrsim_surrogate_use: groups served
  * by the network, groups integrated exactly.  ctx may be NULL. */
 int mrsim_surrogate_stats(const mrsim_surrogate *sur, const mrsim_ctx *ctx, double *out);
+
+/* Check of the gate on a real run: for every slice-selective with-RF pulse of
+ * `seq` that `sur` serves, the groups of `groups` the gate serves get the
+ * network's transition and, independently, the exact one (FP64 sub-steps and
+ * composition, Eq. 7); *max_err is the largest |entry| difference over all of
+ * them (0 when none is served), *n_served (may be NULL) the number of served
+ * (group, pulse) pairs.  The quantity the gate bounds, measured on the run's
+ * own groups instead of validation draws.  Errors: MRSIM_EINVAL (NULL),
+ * MRSIM_ESTATE (groups without the Gz-only type), MRSIM_ENOMEM, MRSIM_ECUDA. */
+int mrsim_surrogate_check(mrsim_ctx *ctx, const mrsim_surrogate *sur, const mrsim_seq *seq,
+                          const mrsim_groups *groups, double *max_err, int64_t *n_served);
 
 /* Make `sur` the network used by this context's MRSIM_SURROGATE runs (NULL:
  * none, every pulse is integrated exactly).  The handle must outlive its use. */

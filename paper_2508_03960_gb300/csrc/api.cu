@@ -668,6 +668,8 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
                 k.kp = P.kd[i][p - 1];
                 k.kr = P.r_axis >= 0 ? P.kd[i][P.r_axis] : 0.0;
                 k.tau = P.adv[i].tau;
+                k.prow = e.prow;
+                k.qr = (P.r_axis >= 0 && (ev_mask(e.op) & rbit)) ? e.q[P.r_axis] : -1;
                 int id = -1;
                 for (size_t j = 0; j < P.ckeys.size() && id < 0; ++j) {
                     const CellKey &o = P.ckeys[j];
@@ -818,7 +820,8 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             if (nk > 0) {
                 CellKey *d_keys = (CellKey *)scratch(c, 24, nk * sizeof(CellKey));
                 upload(c, d_keys, P.ckeys.data(), nk * sizeof(CellKey));
-                launch_cell_rows(c, d_keys, nk, g, T_tab, C_tab);
+                launch_cell_rows(c, d_keys, nk, g, T_tab, d_P, fa.qtab,
+                                 P.r_axis >= 0 ? fa.ax_sh[P.r_axis] : 0, C_tab);
             }
             const int w = P.cell_w;
             ca.n_thr = g->n_cell_thr[w];

@@ -199,8 +199,12 @@ struct SurPulse {
     double mz;   // int Gz dt over the pulse (T s / m)
     double dur;  // pulse duration (s)
 };
-constexpr int kCellsZ = 64, kCellsB0 = 8, kCellsB1 = 4;
-constexpr int kCells = kCellsZ * kCellsB0 * kCellsB1;
+// validation cells of the gate: z, dB0, b1 uniform, T2 log-uniform over the domain
+constexpr int kCellsZ = 64, kCellsB0 = 8, kCellsB1 = 4, kCellsT2 = 4;
+constexpr int kCells = kCellsZ * kCellsB0 * kCellsB1 * kCellsT2;
+// a cell is served only if its validated largest error is at most this
+// fraction of the bound (the validation draws cover a cell only so densely)
+constexpr double kGateMargin = 0.5;
 void sur_sample(mrsim_ctx *c, const SurDomain &d, uint64_t seed, int64_t n, double *par, float *X);
 void sur_core(mrsim_ctx *c, const SurPulse &p, const double *par, int64_t n, const double *T,
               float *C);
@@ -220,6 +224,10 @@ void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d
                const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
                float *out, int32_t *idx, int32_t *cnt);
 int sur_n_params();
+// largest |entry| difference between out (float [G][12]) and exact (double
+// [G][12]) over the groups listed in idx[0 .. *cnt); result as float bits
+void sur_served_error(mrsim_ctx *c, const float *out, const double *exact, const int32_t *idx,
+                      const int32_t *cnt, unsigned int *result);
 // run-time use by the grouped planner: fills rows [0, G) of `out` for with-RF
 // content `cid` of `s` from the context's active network, then integrates the
 // fallback groups exactly; returns false if no network serves this content
@@ -363,18 +371,23 @@ struct CellForm {
     bool adq;   // with-ADC events rotate by the free-axis phasor
     bool rb;    // with-ADC events rotate by the secondary-axis phasor
 };
-// One distinct RF advance of a cell run: C rows of every cell for transition
-// table rows [trow, trow + G_t) of gradient type gtype, after an advance with
-// moments kp (primary axis), kr (secondary axis) and duration tau.
+// One distinct RF / END advance of a cell run: C rows of every cell for
+// transition table rows [trow, trow + G_t) of gradient type gtype (trow < 0:
+// no transition, END), after an advance with moments kp (primary axis), kr
+// (secondary axis) and duration tau.  prow / qr: the group-factor row and the
+// secondary-axis phasor table (-1: kr = 0) of the first event with this key.
 struct CellKey {
     int64_t trow;
     int gtype;
+    int prow;
+    int qr;
     int pad;
     double kp, kr, tau;
 };
 void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f);
 void launch_cell_rows(mrsim_ctx *c, const CellKey *d_keys, int n_keys, const mrsim_groups *g,
-                      const float *T_tab, float *C);
+                      const float *T_tab, const void *P_tab, const float2 *qtab, int r_sh,
+                      float *C);
 void build_cell_threads(mrsim_ctx *c, mrsim_groups *g, const std::vector<int32_t> &count);
 // one axis table: out[j] = exp(-i 2 pi val[j] k) for j < n (cos, sin)
 struct AxItem {

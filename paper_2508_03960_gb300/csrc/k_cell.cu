@@ -17,7 +17,8 @@
 //             dB0 tau, E2, E1) and the free-axis phase Q; the z-rotations Adv
 //             and Q commute, so  T Adv Q M = C (Q M)  with one combined affine
 //             row C = T Adv per (distinct advance, cell), built by k_cell_rows
-//             in FP64 and rounded to float.  Per isochromat: one phasor load
+//             from the FP32 group-factor and axis-phasor tables the
+//             per-isochromat form applies.  Per isochromat: one phasor load
 //             (only if the free-axis moment is nonzero) and 12 FMAs.
 //  ADC event: the block-sum term of an isochromat is P_g Q_r Q_free M_xy
 //             (Eq. 9): the thread sums Q_free M_xy over its isochromats,
@@ -329,47 +330,46 @@ void launch_cell_q(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
     else launch_cell_rb<NI, NF, false, false>(c, a, f.rb);
 }
 
-// C = T Adv for every (key, cell): Adv advances a cell's isochromats by the
-// key's primary- and secondary-axis moments and duration (Eqs. 4-5, evaluated
-// in FP64 from the cell's primary group and secondary-axis position), T is the
-// cell's combined transition row of the key's gradient type (Eq. 7).
+// C = T Adv for every (key, cell).  Adv is the advance of Eqs. 4-5 that the
+// per-isochromat form applies in FP32 per isochromat, from the same tables:
+// the group factor (E2 e^{-i phi_p}, E1) of the cell's primary group at the
+// key's first event, times the phasor of the cell's secondary-axis position
+// (when that moment is nonzero); T is the cell's combined transition row of
+// the key's gradient type (Eq. 7), or the identity for the end of a span.
 __global__ void k_cell_rows(const CellKey *keys, int n_keys, int64_t nc, const int32_t *cstart,
                             const int32_t *cgp, const int32_t *cgr, const int32_t *gid_none,
-                            int p, int r, const double *par_p, int64_t Gp, const float *pos_r,
-                            const float *T_tab, float *C) {
+                            int p, int r, const float4 *Pt, const float2 *qtab,
+                            const int32_t *aidx, int r_sh, const float *T_tab, float *C) {
     const int64_t n = (int64_t)n_keys * nc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = i / nc, c = i - j * nc;
         const CellKey k = keys[j];
         const int gp = cgp[c];
-        // trow < 0: the advance alone (end of a span), T = [I | 0]
-        float Tid[12] = {1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f};
-        const float *T = Tid;
-        if (k.trow >= 0) {
-            const int gt = k.gtype == p ? gp : k.gtype == r ? cgr[c] : gid_none[cstart[c]];
-            T = T_tab + (k.trow + gt) * 12;
+        const float4 P = __ldg(Pt + k.prow + gp);
+        float fr = P.x, fi = P.y;
+        if (k.qr >= 0) {
+            const float2 q = __ldg(qtab + k.qr + ((aidx[cstart[c]] >> r_sh) & 0xffff));
+            const float tr = fr * q.x + fi * q.y;  // P exp(-i psi)
+            fi = fi * q.x - fr * q.y;
+            fr = tr;
         }
-        double ph = par_p[gp] * k.kp + par_p[3 * Gp + gp] * k.tau;
-        if (k.kr != 0.0) ph += (double)pos_r[cstart[c]] * k.kr;
-        ph -= rint(ph);
-        double sn, cs;
-        sincospi(2.0 * ph, &sn, &cs);
-        const double T1 = par_p[Gp + gp], T2 = par_p[2 * Gp + gp];
-        const double E2 = isinf(T2) ? 1.0 : exp(-k.tau / T2);
-        const double E1 = isinf(T1) ? 1.0 : exp(-k.tau / T1);
-        const double u = -expm1(-k.tau / T1);  // 1 - E1 (0 for T1 = inf)
-        const double cr = E2 * cs, ci = E2 * sn;
-        float *o = C + i * 12;
+        // Adv: mx' = fr mx - fi my, my' = fr my + fi mx, mz' = E1 mz + (1 - E1) M0
+        const float E1 = P.z, u = 1.0f - P.z;
+        float4 *o = reinterpret_cast<float4 *>(C + i * 12);
+        if (k.trow < 0) {
+            o[0] = make_float4(fr, -fi, 0.0f, 0.0f);
+            o[1] = make_float4(fi, fr, 0.0f, 0.0f);
+            o[2] = make_float4(0.0f, 0.0f, E1, u);
+            continue;
+        }
+        const int gt = k.gtype == p ? gp : k.gtype == r ? cgr[c] : gid_none[cstart[c]];
+        const float4 *T = reinterpret_cast<const float4 *>(T_tab + (k.trow + gt) * 12);
 #pragma unroll
         for (int row = 0; row < 3; ++row) {
-            const double A0 = T[4 * row], A1 = T[4 * row + 1], A2 = T[4 * row + 2];
-            const double b = T[4 * row + 3];
-            // mx' = E2 (c mx + s my), my' = E2 (c my - s mx), mz' = E1 mz + (1 - E1) M0
-            o[4 * row] = (float)(A0 * cr - A1 * ci);
-            o[4 * row + 1] = (float)(A0 * ci + A1 * cr);
-            o[4 * row + 2] = (float)(A2 * E1);
-            o[4 * row + 3] = (float)(A2 * u + b);
+            const float4 t = __ldg(T + row);  // A0, A1, A2, b
+            o[row] = make_float4(t.x * fr + t.y * fi, t.y * fr - t.x * fi, t.z * E1,
+                                 fmaf(t.z, u, t.w));
         }
     }
 }
@@ -389,20 +389,20 @@ void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
 }
 
 void launch_cell_rows(mrsim_ctx *c, const CellKey *d_keys, int n_keys, const mrsim_groups *g,
-                      const float *T_tab, float *C) {
+                      const float *T_tab, const void *P_tab, const float2 *qtab, int r_sh,
+                      float *C) {
     const int64_t nc = g->n_cells;
     const int64_t n = (int64_t)n_keys * nc;
     if (n <= 0) return;
     const int p = g->primary, r = g->secondary;
-    const float *pos[3] = {g->x.as<float>(), g->y.as<float>(), g->z.as<float>()};
     KScope ks(c, "cell_rows");
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16));
     k_cell_rows<<<grid, 256, 0, c->stream>>>(
         d_keys, n_keys, nc, g->cell_start.as<int32_t>(), g->cell_gp.as<int32_t>(),
         g->cell_gr.as<int32_t>(), g->built[G_NONE] ? g->gid_sorted[G_NONE].as<int32_t>() : nullptr,
-        p, r, g->tab[p].d_par64.as<double>(), g->n_groups[p],
-        (r >= G_X && r <= G_Z) ? pos[r - 1] : nullptr, T_tab, C);
+        p, r, reinterpret_cast<const float4 *>(P_tab), qtab, g->ax_idx.as<int32_t>(), r_sh, T_tab,
+        C);
 }
 
 }  // namespace mrsim

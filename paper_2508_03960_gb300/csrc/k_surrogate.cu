@@ -375,7 +375,7 @@ __device__ __forceinline__ double u01(uint64_t seed, uint64_t i) {
 struct FeatCoef {
     float a[5], c[5];         // f = a v + c, v = z, dB0, b1, log T1, log T2
     double lo[5], hi[5];      // the domain (inclusive)
-    double cell_scale[3];     // cells per unit of z, dB0, b1
+    double cell_scale[4];     // cells per unit of z, dB0, b1 and log T2
 };
 
 FeatCoef feat_coef(const SurDomain &d) {
@@ -390,6 +390,7 @@ FeatCoef feat_coef(const SurDomain &d) {
     }
     const int nb[3] = {kCellsZ, kCellsB0, kCellsB1};
     for (int i = 0; i < 3; ++i) k.cell_scale[i] = nb[i] / (d.hi[i] - d.lo[i]);
+    k.cell_scale[3] = kCellsT2 / (std::log(d.hi[4]) - std::log(d.lo[4]));
     return k;
 }
 
@@ -466,28 +467,44 @@ __global__ void k_sur_core(SurPulse pulse, const double *par, int64_t n, const d
     }
 }
 
-__device__ __forceinline__ int cell_of(const FeatCoef &k, double z, double dB0, double b1) {
-    const double v[3] = {z, dB0, b1};
-    const int nb[3] = {kCellsZ, kCellsB0, kCellsB1};
+__device__ __forceinline__ int cell_of(const FeatCoef &k, double z, double dB0, double b1,
+                                       double T2) {
+    const double v[4] = {z - k.lo[0], dB0 - k.lo[1], b1 - k.lo[2], log(T2 / k.lo[4])};
+    const int nb[4] = {kCellsZ, kCellsB0, kCellsB1, kCellsT2};
     int c = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int q = (int)floor((v[a] - k.lo[a]) * k.cell_scale[a]);
+    for (int a = 0; a < 4; ++a) {
+        int q = (int)floor(v[a] * k.cell_scale[a]);
         q = q < 0 ? 0 : (q >= nb[a] ? nb[a] - 1 : q);
         c = c * nb[a] + q;
     }
     return c;
 }
 
-// validation: largest |error| of any transition entry per (z, dB0, b1) cell
+// validation: largest |error| of any transition entry per (z, dB0, b1, T2) cell
 __global__ void k_sur_cell_error(FeatCoef fc, const double *par, int64_t n, const float *Y,
                                  const float *Tgt, unsigned int *cell_err) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         float e = 0.0f;
         for (int r = 0; r < kOut; ++r) e = fmaxf(e, fabsf(Y[k * kOut + r] - Tgt[k * kOut + r]));
-        const int c = cell_of(fc, par[k], par[3 * n + k], par[4 * n + k]);
+        const int c = cell_of(fc, par[k], par[3 * n + k], par[4 * n + k], par[2 * n + k]);
         atomicMax(&cell_err[c], __float_as_uint(e));
+    }
+}
+
+// largest |entry| difference of the listed groups (non-negative floats order
+// like their bit patterns, so an integer max is a float max)
+__global__ void k_sur_served_error(const float *out, const double *exact, const int32_t *idx,
+                                   const int32_t *cnt, unsigned int *result) {
+    const int64_t n = *cnt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = idx[i];
+        float e = 0.0f;
+        for (int r = 0; r < kOut; ++r)
+            e = fmaxf(e, (float)fabs((double)out[g * kOut + r] - exact[g * kOut + r]));
+        atomicMax(result, __float_as_uint(e));
     }
 }
 
@@ -514,7 +531,7 @@ __global__ void k_sur_gate(FeatCoef fc, const unsigned char *cell_ok, const doub
                                 dB0 <= fc.hi[1] && b1 >= fc.lo[2] && b1 <= fc.hi[2] &&
                                 T1 >= fc.lo[3] && T1 <= fc.hi[3] && T2 >= fc.lo[4] &&
                                 T2 <= fc.hi[4];
-            served = inside && cell_ok[cell_of(fc, z, dB0, b1)];
+            served = inside && cell_ok[cell_of(fc, z, dB0, b1, T2)];
         }
         const unsigned ms = __ballot_sync(0xffffffffu, live && served);
         const unsigned mf = __ballot_sync(0xffffffffu, live && !served);
@@ -771,6 +788,12 @@ void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d
                              (int64_t)c->sm_count * std::max(occ, 1)));
     k_sur_infer<<<grid, kInfWarps * 32, sizeof(InferSmem), c->stream>>>(
         P, (const __nv_bfloat16 *)W2b, fc, pulse, par, G, srv, cnt + 1, out);
+}
+
+void sur_served_error(mrsim_ctx *c, const float *out, const double *exact, const int32_t *idx,
+                      const int32_t *cnt, unsigned int *result) {
+    KScope ks(c, "sur_served_error");
+    k_sur_served_error<<<c->sm_count * 4, 256, 0, c->stream>>>(out, exact, idx, cnt, result);
 }
 
 int sur_n_params() { return kNParams; }

@@ -220,7 +220,8 @@ int mrsim_surrogate_train(mrsim_ctx *c, const mrsim_seq *s, const double *lo, co
                 float e;
                 std::memcpy(&e, &ce[i], 4);
                 vmax = std::max(vmax, (double)e);
-                okc[i] = (ce[i] != 0u) && (double)e <= bound;  // cells without samples stay exact
+                // cells without samples stay exact
+                okc[i] = (ce[i] != 0u) && (double)e <= kGateMargin * bound;
                 if (okc[i]) { ++n_ok; amax = std::max(amax, (double)e); }
             }
             net.val_max = vmax;
@@ -236,6 +237,56 @@ int mrsim_surrogate_train(mrsim_ctx *c, const mrsim_seq *s, const double *lo, co
     });
     if (rc == MRSIM_OK) *out = S.release();
     return rc;
+}
+
+int mrsim_surrogate_check(mrsim_ctx *c, const mrsim_surrogate *S, const mrsim_seq *s,
+                          const mrsim_groups *g, double *max_err, int64_t *n_served) {
+    if (!c) return MRSIM_EINVAL;
+    return sguard(c, [&] {
+        if (!S || !s || !g || !max_err) fail(MRSIM_EINVAL, "NULL argument");
+        if (!g->built[G_Z]) fail(MRSIM_ESTATE, "the groups have no Gz-only type");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        const int64_t G = g->n_groups[G_Z];
+        const double *par = g->tab[G_Z].d_par64.as<double>();
+        DBuf out = dalloc(std::max<int64_t>(G, 1) * 12 * sizeof(float));
+        DBuf exact = dalloc(std::max<int64_t>(G, 1) * 12 * sizeof(double));
+        DBuf idx = dalloc(std::max<int64_t>(2 * G, 1) * sizeof(int32_t));
+        DBuf cnt = dalloc(2 * sizeof(int32_t));
+        DBuf res = dalloc(sizeof(unsigned int));
+        MRSIM_CUDA(cudaMemsetAsync(res.p, 0, sizeof(unsigned int), c->stream));
+        int64_t served = 0;
+        for (int cid = 0; cid < s->n_content; ++cid) {
+            const Subseq &q = s->sub[s->content_first[cid]];
+            if (q.type != SUB_RF || q.gtype != G_Z) continue;
+            const mrsim_surrogate::Net *net = nullptr;
+            for (const auto &n : S->nets)
+                if (same_content(n, s, cid)) { net = &n; break; }
+            if (!net) continue;
+            MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), c->stream));
+            sur_infer(c, net->P.as<float>(), net->W2b.p, S->dom, net->pulse,
+                      net->cell_ok.as<unsigned char>(), par, G, out.as<float>(),
+                      idx.as<int32_t>(), cnt.as<int32_t>());
+            // the exact transitions (FP64 steps and composition) of the served groups
+            PrecompArgs pa = exact_args(s, cid, G, par, exact.as<double>());
+            pa.gidx = idx.as<int32_t>() + G;
+            pa.gcount = cnt.as<int32_t>() + 1;
+            launch_precompute<double>(c, pa);
+            sur_served_error(c, out.as<float>(), exact.as<double>(), idx.as<int32_t>() + G,
+                             cnt.as<int32_t>() + 1, res.as<unsigned int>());
+            int32_t h[2] = {0, 0};
+            MRSIM_CUDA(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                       c->stream));
+            sync(c);
+            served += h[1];
+        }
+        unsigned int r = 0;
+        MRSIM_CUDA(cudaMemcpyAsync(&r, res.p, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        float e;
+        std::memcpy(&e, &r, sizeof(e));
+        *max_err = (double)e;
+        if (n_served) *n_served = served;
+    });
 }
 
 int mrsim_surrogate_stats(const mrsim_surrogate *S, const mrsim_ctx *c, double *out) {

@@ -39,6 +39,7 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
            "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
+           "mrsim_surrogate_check",
            "mrsim_surrogate_eval", "mrsim_free_surrogate",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_double, PP]),
         "mrsim_surrogate_stats": (I, [P, P, P]),
         "mrsim_surrogate_use": (I, [P, P]),
+        "mrsim_surrogate_check": (I, [P, P, P, P, P, P]),
         "mrsim_surrogate_eval": (I, [P, P, I64, P, P, P, P, P]),
         "mrsim_free_surrogate": (None, [P]),
         "mrsim_free_phantom": (None, [P]),
@@ -374,6 +376,17 @@ def mrsim_surrogate_stats(sur, ctx=None) -> dict:
     if rc:
         raise MrsimError(rc, "mrsim_surrogate_stats")
     return dict(zip(SURROGATE_STATS, out.tolist()))
+
+
+def mrsim_surrogate_check(ctx, sur, seq, groups):
+    """Largest entry error of the network's transitions over the groups the
+    gate serves in a run, against the exact FP64 transitions; returns
+    (max_err, n_served)."""
+    e = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(ctx, lib().mrsim_surrogate_check(ctx, sur, seq, groups, ctypes.byref(e),
+                                            ctypes.byref(n)), "mrsim_surrogate_check")
+    return e.value, n.value
 
 
 def mrsim_surrogate_use(ctx, sur):

@@ -88,6 +88,28 @@ def test_training_converges_and_gate_bounds_served_error(mrsim, ctx, trained):
     assert st["val_served_max_err"] <= 1e-3  # the gate's bound holds on validation draws
 
 
+@pytest.mark.parametrize("shape", [(32, 32, 4), (128, 128, 16)])
+def test_every_served_transition_of_a_run_is_within_the_bound(mrsim, ctx, trained, shape):
+    """The gate bounds the error of each served group, not only of the
+    validation draws: on the groups of real phantoms (per-isochromat dB0 and
+    b1, the configuration's T1 / T2 regions) the transition the network
+    serves differs from the exact FP64 one by at most the bound in every
+    entry, for every served (group, pulse) pair."""
+    seq, hs, sur, _ = trained
+    ph = continuous_phantom(*shape, 3, seed=1005 + shape[0])
+    hp = ctx.phantom(ph)
+    hs2 = ctx.sequence(seq)
+    hg = ctx.group(hp, hs2)
+    err, served = mrsim.mrsim_surrogate_check(ctx.h, sur, hs2, hg)
+    n_z = mrsim.mrsim_group_info(hg, mrsim.G_Z)[0]
+    ctx.free("grp", hg)
+    ctx.free("seq", hs2)
+    ctx.free("ph", hp)
+    print(f"served {served} of {2 * n_z} (group, pulse) pairs, largest entry error {err:.3e}")
+    assert served > 0.1 * n_z
+    assert err <= 1e-3, err
+
+
 def test_surrogate_run_against_oracle_and_exact_grouped(mrsim, ctx, trained):
     seq, hs, sur, _ = trained
     ph, _ = configs.surrogate_fse()
