@@ -341,6 +341,15 @@ int mrsim_surrogate_use(mrsim_ctx *ctx, const mrsim_surrogate *sur);
 int mrsim_surrogate_eval(mrsim_ctx *ctx, const float *params, int64_t n, const float *x,
                          const float *t, float *y, float *grad, double *loss);
 
+/* The inference kernel of MRSIM_SURROGATE runs (tensor-core 128x128 layer,
+ * h1 entering as BF16 hi + lo parts) on n host feature rows x[n][5] with the
+ * given parameters (layout as for mrsim_surrogate_eval, W2 rounded to BF16):
+ * the network's raw outputs y[n][12], before the precession of the pulse is
+ * put back.  Errors: MRSIM_EINVAL, MRSIM_ENOMEM, MRSIM_ECUDA, MRSIM_ETIMEOUT
+ * (a bounded wait of the tensor-core kernel ran out). */
+int mrsim_surrogate_infer(mrsim_ctx *ctx, const float *params, int64_t n, const float *x,
+                          float *y);
+
 void mrsim_free_surrogate(mrsim_surrogate *sur);
 
 /* Launch parameters (one value per context).

@@ -191,6 +191,10 @@ DBuf dalloc(size_t bytes);
 void upload(mrsim_ctx *c, void *dst, const void *src, size_t bytes);
 void sync(mrsim_ctx *c);
 
+// word of mrsim_ctx::dev_err set by the tensor-core kernels when a bounded
+// mbarrier wait runs out (the other words belong to the group builder)
+constexpr int kErrWordTensor = 4;
+
 // ---- learned with-RF transitions (k_surrogate.cu, surrogate.cu) ----
 struct SurDomain {
     double lo[5], hi[5];  // z (m), dB0 (Hz), b1, T1 (s), T2 (s)
@@ -224,6 +228,9 @@ void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d
                const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
                float *out, int32_t *idx, int32_t *cnt);
 int sur_n_params();
+// the inference kernel on given features X [n][5]: raw outputs Y [n][12]
+void sur_infer_raw(mrsim_ctx *c, const float *P, const void *W2b, const float *X, int64_t n,
+                   float *Y);
 // largest |entry| difference between out (float [G][12]) and exact (double
 // [G][12]) over the groups listed in idx[0 .. *cnt); result as float bits
 void sur_served_error(mrsim_ctx *c, const float *out, const double *exact, const int32_t *idx,

@@ -469,7 +469,9 @@ __global__ void k_sur_core(SurPulse pulse, const double *par, int64_t n, const d
 
 __device__ __forceinline__ int cell_of(const FeatCoef &k, double z, double dB0, double b1,
                                        double T2) {
-    const double v[4] = {z - k.lo[0], dB0 - k.lo[1], b1 - k.lo[2], log(T2 / k.lo[4])};
+    // (the T2 bin from a float logarithm: validation and gate share this function)
+    const double v[4] = {z - k.lo[0], dB0 - k.lo[1], b1 - k.lo[2],
+                         (double)logf((float)(T2 / k.lo[4]))};
     const int nb[4] = {kCellsZ, kCellsB0, kCellsB1, kCellsT2};
     int c = 0;
 #pragma unroll
@@ -548,144 +550,283 @@ __global__ void k_sur_gate(FeatCoef fc, const unsigned char *cell_ok, const doub
     }
 }
 
-// Network inference, one warp per tile of 16 served groups, activations in
-// registers.  Layer 1 is evaluated directly into the m16n8k16 A fragments
-// (thread (g, t) of the warp owns rows g and g + 8, columns 2t, 2t + 1,
-// 2t + 8, 2t + 9 of each 16-column slice) as hi + lo BF16 pairs; layer 2 runs
-// on the tensor cores with W2 in shared memory; GELU and the FP32 output
-// layer work on the accumulator fragments, whose partial sums over a row's
-// columns are combined across the four threads of a quad.  The rows of the
-// transition are then rebuilt from the core (T = P(th/2) [C_A P(th/2) | C_b])
-// and stored.
-constexpr int kInfWarps = 4;
-struct InferSmem {
-    __nv_bfloat16 W2b[kH * kLdW];
-    float W1[kH * kIn], b1[kH], b2[kH], W3[kOut * kH], b3[16];
-    float stage[kInfWarps][16][kOut + 1];
+// ----------------------------------------------------- tensor-core path ----
+// Network inference on the 5th-generation tensor cores (tcgen05): a CTA of
+// 256 threads takes tiles of 128 served groups.  Thread (w, l) owns row
+// r = 32 (w mod 4) + l of the tile (TMEM lane quadrant w mod 4) and half
+// h = w / 4 of the hidden units.
+//   layer 1 (FP32 lanes): a1 = W1 x + b1, h1 = gelu(a1), written as BF16
+//     hi + lo parts into two K-major operand tiles in shared memory
+//   layer 2 (tensor cores): one thread issues 16 tcgen05.mma (M = N = 128,
+//     K = 16: hi and lo parts of each 16-wide K step) into a 128-column FP32
+//     accumulator in tensor memory, then commits them to an mbarrier
+//   epilogue (FP32 lanes): tcgen05.ld of the row's 64 accumulator columns,
+//     + b2, gelu, the 12 outputs' partial sums; the two halves of a row are
+//     added in shared memory and the transition rebuilt from the core.
+// Operand tiles use the no-swizzle K-major canonical layout: 8-row x 16-byte
+// core matrices, K-adjacent cores 128 bytes apart (LBO), 8-row groups 2048
+// bytes apart (SBO); W2 (the B operand, N x K = output x input) is staged once
+// per CTA.  Every mbarrier wait is bounded: on expiry the kernel sets an
+// error flag, stops issuing, frees its tensor memory and returns.
+constexpr int kTcRows = 128;          // groups per tile (MMA M)
+constexpr int kTcThreads = 256;
+constexpr int kTileBytes = kTcRows * kH * 2;  // one BF16 128 x 128 operand tile
+constexpr int kTmemCols = 128;                // FP32 accumulator columns (N)
+constexpr uint64_t kWaitNs = 1000000000ull;   // mbarrier wait limit (1 s)
+
+struct TcSmem {
+    __align__(16) unsigned char W2[kTileBytes];   // B operand (core-matrix layout)
+    __align__(16) unsigned char Ahi[kTileBytes];  // A operand, h1 high parts
+    __align__(16) unsigned char Alo[kTileBytes];  // A operand, h1 low parts
+    float4 W1b[kH][2];                 // (w0, w1, w2, w3), (w4, b1, 0, 0) per hidden unit
+    float b2[kH];
+    float4 W3t[kH][3];                 // W3 transposed: 12 outputs per hidden unit
+    float b3[kOut];
+    float part[kTcRows][kOut + 1];     // second half's output partial sums
+    float half_turns[kTcRows];
+    int grp[kTcRows];
+    unsigned long long mbar;
+    uint32_t tmem_base;
 };
 
-__global__ void __launch_bounds__(kInfWarps * 32, 3)
+// byte offset of element (row, k) of a 128 x 128 BF16 tile in the layout above
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)((((row >> 3) * (kH / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, LBO and SBO in 16-byte units,
+// descriptor version 1 (bit 46), no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                                ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// wait for completion of phase `parity` of an mbarrier, at most kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_sur_infer(const float *P, const __nv_bfloat16 *W2b_g, FeatCoef fc, SurPulse pulse,
                 const double *par, int64_t G, const int32_t *srv, const int32_t *cnt,
-                float *out) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    InferSmem &sm = *reinterpret_cast<InferSmem *>(raw);
+                float *out, int *err, const float *X, int64_t n_x) {
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(tc_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
-    for (int j = tid; j < kH * kH / 8; j += kInfWarps * 32) {
-        const int r = (j * 8) / kH, c = (j * 8) % kH;
-        *reinterpret_cast<int4 *>(&sm.W2b[r * kLdW + c]) = reinterpret_cast<const int4 *>(W2b_g)[j];
+    const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+    // weights: W2 into the B operand layout (row = output o, k = input i)
+    for (int j = tid; j < kH * kH / 8; j += kTcThreads) {
+        const int o = (j * 8) / kH, i = (j * 8) % kH;
+        *reinterpret_cast<int4 *>(sm.W2 + core_off(o, i)) = reinterpret_cast<const int4 *>(W2b_g)[j];
     }
-    for (int j = tid; j < kH * kIn; j += kInfWarps * 32) sm.W1[j] = P[oW1 + j];
-    for (int j = tid; j < kH; j += kInfWarps * 32) {
-        sm.b1[j] = P[ob1 + j];
-        sm.b2[j] = P[ob2 + j];
+    for (int i = tid; i < kH; i += kTcThreads) {
+        const float *w = P + oW1 + i * kIn;
+        sm.W1b[i][0] = make_float4(w[0], w[1], w[2], w[3]);
+        sm.W1b[i][1] = make_float4(w[4], P[ob1 + i], 0.0f, 0.0f);
+        sm.b2[i] = P[ob2 + i];
+        sm.W3t[i][0] = make_float4(P[oW3 + 0 * kH + i], P[oW3 + 1 * kH + i], P[oW3 + 2 * kH + i],
+                                   P[oW3 + 3 * kH + i]);
+        sm.W3t[i][1] = make_float4(P[oW3 + 4 * kH + i], P[oW3 + 5 * kH + i], P[oW3 + 6 * kH + i],
+                                   P[oW3 + 7 * kH + i]);
+        sm.W3t[i][2] = make_float4(P[oW3 + 8 * kH + i], P[oW3 + 9 * kH + i],
+                                   P[oW3 + 10 * kH + i], P[oW3 + 11 * kH + i]);
     }
-    for (int j = tid; j < kOut * kH; j += kInfWarps * 32) sm.W3[j] = P[oW3 + j];
     if (tid < kOut) sm.b3[tid] = P[ob3 + tid];
+    const uint32_t mbar = smem_u32(&sm.mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&sm.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    const int64_t n = *cnt;
-    float (*stage)[kOut + 1] = sm.stage[warp];
-    for (int64_t tile = blockIdx.x * (int64_t)kInfWarps + warp; tile * 16 < n;
-         tile += (int64_t)gridDim.x * kInfWarps) {
-        // features of the tile's groups (lanes 0-15) and their precession angle
-        const int64_t s0 = tile * 16;
-        const int ns = (int)min((int64_t)16, n - s0);
-        float f[kIn] = {0, 0, 0, 0, 0};
-        float half_turns = 0.0f;
-        int64_t grp = -1;
-        if (lane < ns) {
-            grp = srv[s0 + lane];
-            const double z = par[grp], T1 = par[G + grp], T2 = par[2 * G + grp];
-            const double dB0 = par[3 * G + grp], b1 = par[4 * G + grp];
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = sm.tmem_base;
+    const uint32_t a_hi = smem_u32(sm.Ahi), a_lo = smem_u32(sm.Alo), b_w = smem_u32(sm.W2);
+    // X != null: rows are the given features, outputs the network's raw ones
+    const int64_t n = X ? n_x : *cnt;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile * kTcRows < n && ok; tile += gridDim.x) {
+        const int64_t s = tile * kTcRows + row;
+        // features of this row's group and layer 1 for this thread's half
+        float f[kIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const bool live = s < n;
+        if (live && X) {
+#pragma unroll
+            for (int c = 0; c < kIn; ++c) f[c] = X[s * kIn + c];
+            if (half == 0) {
+                sm.grp[row] = (int)s;
+                sm.half_turns[row] = 0.0f;
+            }
+        } else if (live) {
+            const int64_t g = srv[s];
+            const double z = par[g], T1 = par[G + g], T2 = par[2 * G + g];
+            const double dB0 = par[3 * G + g], b1 = par[4 * G + g];
             features(fc, z, dB0, b1, T1, T2, f);
-            double h = 0.5 * (kGammaBar * z * pulse.mz + dB0 * pulse.dur);
-            half_turns = (float)(h - rint(h));
-        }
-        float xg[kIn], xg8[kIn];
-#pragma unroll
-        for (int c = 0; c < kIn; ++c) {
-            xg[c] = __shfl_sync(0xffffffffu, f[c], g);
-            xg8[c] = __shfl_sync(0xffffffffu, f[c], g + 8);
-        }
-        float acc[16][4];
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const float bl = sm.b2[nt * 8 + 2 * t], bh = sm.b2[nt * 8 + 2 * t + 1];
-            acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
+            if (half == 0) {
+                sm.grp[row] = (int)g;
+                const double h = 0.5 * (kGammaBar * z * pulse.mz + dB0 * pulse.dur);
+                sm.half_turns[row] = (float)(h - rint(h));
+            }
+        } else if (half == 0) {
+            sm.grp[row] = -1;
         }
 #pragma unroll 1
-        for (int ks = 0; ks < kH / 16; ++ks) {
-            // h1 at rows g, g + 8 and columns ks*16 + {2t, 2t+1, 2t+8, 2t+9}
-            float h[2][4];
+        for (int k8 = half * 8; k8 < half * 8 + 8; ++k8) {  // 8 hidden units per chunk
+            uint32_t hi[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int col = ks * 16 + 2 * t + (q & 1) + (q >> 1) * 8;
-                float a0 = sm.b1[col], a1 = a0;
+                float hv[2];
 #pragma unroll
-                for (int c = 0; c < kIn; ++c) {
-                    const float w = sm.W1[col * kIn + c];
-                    a0 = fmaf(w, xg[c], a0);
-                    a1 = fmaf(w, xg8[c], a1);
+                for (int e = 0; e < 2; ++e) {
+                    const int i = k8 * 8 + 2 * q + e;
+                    const float4 wa = sm.W1b[i][0], wb = sm.W1b[i][1];
+                    float a = wb.y;
+                    a = fmaf(wa.x, f[0], a);
+                    a = fmaf(wa.y, f[1], a);
+                    a = fmaf(wa.z, f[2], a);
+                    a = fmaf(wa.w, f[3], a);
+                    a = fmaf(wb.x, f[4], a);
+                    hv[e] = live ? gelu(a) : 0.0f;
                 }
-                h[0][q] = gelu(a0);
-                h[1][q] = gelu(a1);
+                const __nv_bfloat162 hb = __floats2bfloat162_rn(hv[0], hv[1]);
+                const __nv_bfloat162 lb =
+                    __floats2bfloat162_rn(hv[0] - __low2float(hb), hv[1] - __high2float(hb));
+                hi[q] = *reinterpret_cast<const uint32_t *>(&hb);
+                lo[q] = *reinterpret_cast<const uint32_t *>(&lb);
             }
-            uint32_t ahi[4], alo[4];
+            const uint32_t off = core_off(row, k8 * 8);
+            *reinterpret_cast<uint4 *>(sm.Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(sm.Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        // operands visible to the tensor cores, previous accumulator reads done
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (tid == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                // fragment register q: row g (q even) or g + 8 (q odd), columns
-                // 2t, 2t + 1 (q < 2) or 2t + 8, 2t + 9 (q >= 2)
-                const int row = q & 1, pair = q >> 1;
-                const float v0 = h[row][2 * pair], v1 = h[row][2 * pair + 1];
-                const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
-                const __nv_bfloat162 lb = __floats2bfloat162_rn(v0 - __low2float(hb),
-                                                                v1 - __high2float(hb));
-                ahi[q] = *reinterpret_cast<const uint32_t *>(&hb);
-                alo[q] = *reinterpret_cast<const uint32_t *>(&lb);
+            for (int ks = 0; ks < kH / 16; ++ks) {
+                const uint64_t bd = umma_desc(b_w + ks * 256, 128, 2048);
+                umma_bf16(tmem, umma_desc(a_hi + ks * 256, 128, 2048), bd, ks > 0 ? 1u : 0u);
+                umma_bf16(tmem, umma_desc(a_lo + ks * 256, 128, 2048), bd, 1u);
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    mbar)
+                : "memory");
+        }
+        // every thread waits; the outcome is made the same for the whole CTA
+        ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (!ok) {
+            if (tid == 0) atomicOr(err, 1);
+            // the MMAs may still be in flight: wait once more (bounded)
+            // before the tensor memory is freed below
+            mbar_wait(mbar, phase ^ 1u);
+            break;
+        }
+        // epilogue: this thread's 64 columns of its row
+        float y[kOut];
 #pragma unroll
-            for (int nt = 0; nt < 16; ++nt) {
-                uint32_t b[2];
-                load_b(b, sm.W2b, kLdW, nt * 8, ks * 16);
-                mma16816(acc[nt], ahi, b);
-                mma16816(acc[nt], alo, b);
+        for (int r = 0; r < kOut; ++r) y[r] = half == 0 ? sm.b3[r] : 0.0f;
+#pragma unroll 1
+        for (int c32 = 0; c32 < 2; ++c32) {
+            const int col0 = half * 64 + c32 * 32;
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int o = col0 + j;
+                const float h2 = gelu(v[j] + sm.b2[o]);
+                const float4 w0 = sm.W3t[o][0], w1 = sm.W3t[o][1], w2 = sm.W3t[o][2];
+                y[0] = fmaf(w0.x, h2, y[0]); y[1] = fmaf(w0.y, h2, y[1]);
+                y[2] = fmaf(w0.z, h2, y[2]); y[3] = fmaf(w0.w, h2, y[3]);
+                y[4] = fmaf(w1.x, h2, y[4]); y[5] = fmaf(w1.y, h2, y[5]);
+                y[6] = fmaf(w1.z, h2, y[6]); y[7] = fmaf(w1.w, h2, y[7]);
+                y[8] = fmaf(w2.x, h2, y[8]); y[9] = fmaf(w2.y, h2, y[9]);
+                y[10] = fmaf(w2.z, h2, y[10]); y[11] = fmaf(w2.w, h2, y[11]);
             }
         }
-        // h2 = gelu(a2); output layer partial sums over this thread's columns
-        float part[2][kOut];
+        if (half == 1) {
 #pragma unroll
-        for (int r = 0; r < kOut; ++r) part[0][r] = part[1][r] = 0.0f;
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const float h00 = gelu(acc[nt][0]), h01 = gelu(acc[nt][1]);
-            const float h10 = gelu(acc[nt][2]), h11 = gelu(acc[nt][3]);
-#pragma unroll
-            for (int r = 0; r < kOut; ++r) {
-                const float2 w = *reinterpret_cast<const float2 *>(&sm.W3[r * kH + nt * 8 + 2 * t]);
-                part[0][r] = fmaf(w.x, h00, fmaf(w.y, h01, part[0][r]));
-                part[1][r] = fmaf(w.x, h10, fmaf(w.y, h11, part[1][r]));
-            }
+            for (int r = 0; r < kOut; ++r) sm.part[row][r] = y[r];
         }
-#pragma unroll
-        for (int r = 0; r < kOut; ++r) {
-#pragma unroll
-            for (int m = 1; m < 4; m <<= 1) {
-                part[0][r] += __shfl_xor_sync(0xffffffffu, part[0][r], m);
-                part[1][r] += __shfl_xor_sync(0xffffffffu, part[1][r], m);
-            }
-            if ((r & 3) == t) {
-                stage[g][r] = part[0][r] + sm.b3[r];
-                stage[g + 8][r] = part[1][r] + sm.b3[r];
-            }
-        }
-        __syncwarp();
-        if (lane < ns) {  // T = P(th/2) [C_A P(th/2) | C_b]
+        __syncthreads();
+        if (half == 0 && sm.grp[row] >= 0) {  // T = P(th/2) [C_A P(th/2) | C_b]
             float T[kOut];
 #pragma unroll
-            for (int e = 0; e < kOut; ++e) T[e] = stage[lane][e];
+            for (int r = 0; r < kOut; ++r) T[r] = y[r] + sm.part[row][r];
+            if (X) {  // raw outputs
+                float4 *o = reinterpret_cast<float4 *>(out + (int64_t)sm.grp[row] * kOut);
+                o[0] = make_float4(T[0], T[1], T[2], T[3]);
+                o[1] = make_float4(T[4], T[5], T[6], T[7]);
+                o[2] = make_float4(T[8], T[9], T[10], T[11]);
+                continue;
+            }
             float sn, cs;
-            sincospif(2.0f * half_turns, &sn, &cs);
+            sincospif(2.0f * sm.half_turns[row], &sn, &cs);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const float a0 = T[4 * r], a1 = T[4 * r + 1];
@@ -698,12 +839,20 @@ __global__ void __launch_bounds__(kInfWarps * 32, 3)
                 T[col] = cs * r0 + sn * r1;
                 T[4 + col] = -sn * r0 + cs * r1;
             }
-            float4 *o = reinterpret_cast<float4 *>(out + grp * kOut);
+            float4 *o = reinterpret_cast<float4 *>(out + (int64_t)sm.grp[row] * kOut);
             o[0] = make_float4(T[0], T[1], T[2], T[3]);
             o[1] = make_float4(T[4], T[5], T[6], T[7]);
             o[2] = make_float4(T[8], T[9], T[10], T[11]);
         }
-        __syncwarp();
+    }
+    // the accumulator is free once every thread's loads are done
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
     }
 }
 
@@ -761,15 +910,45 @@ void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t
                                                                 cell_err);
 }
 
-void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
-               const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
-               float *out, int32_t *idx, int32_t *cnt) {
+namespace {
+
+// launch of the tensor-core inference kernel over up to G rows; X: features
+// of n_x rows (raw outputs), else the served groups listed in srv / cnt
+void launch_sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const FeatCoef &fc,
+                      const SurPulse &pulse, const double *par, int64_t G, const int32_t *srv,
+                      const int32_t *cnt, float *out, const float *X, int64_t n_x) {
     static bool attr = false;
     if (!attr) {
         MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(InferSmem)));
+                                        (int)sizeof(TcSmem)));
         attr = true;
     }
+    int *err = c->dev_err.as<int>() + kErrWordTensor;
+    MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+    {
+        KScope ks(c, "sur_infer");
+        int occ = 0;
+        MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sur_infer, kTcThreads,
+                                                                 sizeof(TcSmem)));
+        // persistent CTAs over the tiles (the served count is on the device):
+        // every CTA holds 128 of an SM's 512 TMEM columns
+        const int64_t tiles = (G + kTcRows - 1) / kTcRows;
+        const unsigned grid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>(tiles, (int64_t)c->sm_count * std::max(std::min(occ, 4), 1)));
+        k_sur_infer<<<grid, kTcThreads, sizeof(TcSmem), c->stream>>>(
+            P, (const __nv_bfloat16 *)W2b, fc, pulse, par, G, srv, cnt, out, err, X, n_x);
+    }
+    int h = 0;
+    MRSIM_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MRSIM_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) fail(MRSIM_ETIMEOUT, "tensor-core inference: a bounded mbarrier wait ran out");
+}
+
+}  // namespace
+
+void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d,
+               const SurPulse &pulse, const unsigned char *cell_ok, const double *par, int64_t G,
+               float *out, int32_t *idx, int32_t *cnt) {
     if (G <= 0) return;
     const FeatCoef fc = feat_coef(d);
     int32_t *fb = idx, *srv = idx + G;
@@ -778,16 +957,13 @@ void sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const SurDomain &d
         const unsigned grid = (unsigned)std::min<int64_t>((G + 255) / 256, (int64_t)c->sm_count * 16);
         k_sur_gate<<<grid, 256, 0, c->stream>>>(fc, cell_ok, par, G, srv, fb, cnt);
     }
-    KScope ks(c, "sur_infer");
-    int occ = 0;
-    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sur_infer, kInfWarps * 32,
-                                                             sizeof(InferSmem)));
-    const int64_t tiles = (G + 15) / 16;
-    const unsigned grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((tiles + kInfWarps - 1) / kInfWarps,
-                             (int64_t)c->sm_count * std::max(occ, 1)));
-    k_sur_infer<<<grid, kInfWarps * 32, sizeof(InferSmem), c->stream>>>(
-        P, (const __nv_bfloat16 *)W2b, fc, pulse, par, G, srv, cnt + 1, out);
+    launch_sur_infer(c, P, W2b, fc, pulse, par, G, srv, cnt + 1, out, nullptr, 0);
+}
+
+void sur_infer_raw(mrsim_ctx *c, const float *P, const void *W2b, const float *X, int64_t n,
+                   float *Y) {
+    if (n <= 0) return;
+    launch_sur_infer(c, P, W2b, FeatCoef{}, SurPulse{}, nullptr, n, nullptr, nullptr, Y, X, n);
 }
 
 void sur_served_error(mrsim_ctx *c, const float *out, const double *exact, const int32_t *idx,

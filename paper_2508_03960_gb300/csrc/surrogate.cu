@@ -346,6 +346,24 @@ int mrsim_surrogate_eval(mrsim_ctx *c, const float *params, int64_t n, const flo
     });
 }
 
+int mrsim_surrogate_infer(mrsim_ctx *c, const float *params, int64_t n, const float *x,
+                          float *y) {
+    if (!c) return MRSIM_EINVAL;
+    return sguard(c, [&] {
+        if (!params || !x || !y || n < 1) fail(MRSIM_EINVAL, "bad arguments");
+        MRSIM_CUDA(cudaSetDevice(c->device));
+        const int NP = sur_n_params();
+        DBuf P = dalloc(NP * 4), W2b = dalloc(128 * 128 * 2), W2Tb = dalloc(128 * 128 * 2);
+        DBuf X = dalloc(n * 5 * 4), Y = dalloc(n * 12 * 4);
+        upload(c, P.p, params, NP * 4);
+        upload(c, X.p, x, n * 5 * 4);
+        sur_bf16_copies(c, P.as<float>(), W2b.p, W2Tb.p);
+        sur_infer_raw(c, P.as<float>(), W2b.p, X.as<float>(), n, Y.as<float>());
+        MRSIM_CUDA(cudaMemcpyAsync(y, Y.p, n * 12 * 4, cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+    });
+}
+
 void mrsim_free_surrogate(mrsim_surrogate *S) {
     if (!S) return;
     if (S->ctx) {

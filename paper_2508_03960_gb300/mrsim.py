@@ -39,7 +39,7 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
            "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
-           "mrsim_surrogate_check",
+           "mrsim_surrogate_check", "mrsim_surrogate_infer",
            "mrsim_surrogate_eval", "mrsim_free_surrogate",
            "mrsim_free_phantom", "mrsim_free_seq", "mrsim_free_groups"]
 NOALLOC_MAX_GROUPS = 65536
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_surrogate_stats": (I, [P, P, P]),
         "mrsim_surrogate_use": (I, [P, P]),
         "mrsim_surrogate_check": (I, [P, P, P, P, P, P]),
+        "mrsim_surrogate_infer": (I, [P, P, I64, P, P]),
         "mrsim_surrogate_eval": (I, [P, P, I64, P, P, P, P, P]),
         "mrsim_free_surrogate": (None, [P]),
         "mrsim_free_phantom": (None, [P]),
@@ -387,6 +388,17 @@ def mrsim_surrogate_check(ctx, sur, seq, groups):
     _check(ctx, lib().mrsim_surrogate_check(ctx, sur, seq, groups, ctypes.byref(e),
                                             ctypes.byref(n)), "mrsim_surrogate_check")
     return e.value, n.value
+
+
+def mrsim_surrogate_infer(ctx, params, x):
+    """Raw network outputs [n, 12] of the tensor-core inference kernel."""
+    p = np.ascontiguousarray(params, np.float32)
+    xx = np.ascontiguousarray(x, np.float32)
+    n = xx.shape[0]
+    y = np.zeros((n, 12), np.float32)
+    _check(ctx, lib().mrsim_surrogate_infer(ctx, _ptr(p), n, _ptr(xx), _ptr(y)),
+           "mrsim_surrogate_infer")
+    return y
 
 
 def mrsim_surrogate_use(ctx, sur):

@@ -67,6 +67,24 @@ def test_network_forward_and_gradients_match_fp64_reference(mrsim, ctx, n):
         o += m
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 300, 4096])
+def test_tensor_core_inference_matches_fp64_reference(mrsim, ctx, n):
+    """The tcgen05 inference kernel (layer 2 on the tensor cores with a TMEM
+    accumulator; h1 as BF16 hi + lo) against the FP64 network of
+    oracle/mlp.py with the same (BF16-representable) W2: ragged tiles of 128
+    rows, one row, several tiles."""
+    rng = np.random.default_rng(1000 + n)
+    p = {k: rng.normal(0, 0.3, s) for k, s in mlp.SHAPES.items()}
+    p["W2"] = bf16(p["W2"]).astype(np.float64)
+    flat = mlp.pack(p).astype(np.float32)
+    x = rng.uniform(-1, 1, (n, 5)).astype(np.float32)
+    y = mrsim.mrsim_surrogate_infer(ctx.h, flat, x)
+    y_ref, _ = mlp.forward(p, x.astype(np.float64))
+    e = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
+    assert e < 1e-4, e
+    assert np.max(np.abs(y - y_ref)) < 1e-3 * np.max(np.abs(y_ref))
+
+
 @pytest.fixture(scope="module")
 def trained(mrsim, ctx):
     _, seq = configs.surrogate_fse()
@@ -84,7 +102,7 @@ def test_training_converges_and_gate_bounds_served_error(mrsim, ctx, trained):
     st = mrsim.mrsim_surrogate_stats(sur)
     assert st["networks"] == 2  # the 90x and 180y slice-selective pulses
     assert st["train_loss"] < 1e-6
-    assert st["cells_served"] > 0.1
+    assert st["cells_served"] > 0.05  # the gate serves a cell only at half the bound
     assert st["val_served_max_err"] <= 1e-3  # the gate's bound holds on validation draws
 
 
