@@ -47,7 +47,7 @@ extern "C" {
 #define MRSIM_EUNSUPPORTED 2 /* RF and ADC active in the same segment (Sec. 2.1) */
 #define MRSIM_ENOMEM 3       /* device or host allocation failed */
 #define MRSIM_ECUDA 4        /* a CUDA runtime call or kernel failed */
-#define MRSIM_ETIMEOUT 5     /* a bounded device wait ran out (batched launcher) */
+#define MRSIM_ETIMEOUT 5     /* a bounded wait of a tensor-core kernel ran out (surrogate) */
 #define MRSIM_ESTATE 6       /* handles do not belong together (e.g. groups of another phantom) */
 
 /* subsequence types (Fig. 1) */
@@ -205,7 +205,8 @@ int mrsim_group_info(const mrsim_groups *groups, int gtype, int64_t *n_groups, i
  * magnetization in the phantom's order, or NULL.  out_flags:
  * MRSIM_OUT_DEVICE if signal / M_final are device pointers.
  * Errors: MRSIM_EINVAL, MRSIM_ESTATE (groups built for another phantom or
- * without a needed type), MRSIM_ENOMEM, MRSIM_ECUDA. */
+ * without a needed type), MRSIM_ENOMEM, MRSIM_ECUDA, MRSIM_ETIMEOUT
+ * (MRSIM_SURROGATE: a bounded wait of the tensor-core inference ran out). */
 int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
               const mrsim_groups *groups, int mode, int precision, double *signal,
               float *M_final, unsigned out_flags);
@@ -216,8 +217,7 @@ int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
  * signals[i]: host [2 * n_samples_total(seq[i])] doubles.
  * Errors: MRSIM_EINVAL, MRSIM_ESTATE, MRSIM_ENOMEM, MRSIM_ECUDA,
  * MRSIM_EUNSUPPORTED (a phantom with receive coils attached, a job that
- * needs a plain fallback or starts from a given M_init),
- * MRSIM_ETIMEOUT (a bounded device wait gave up). */
+ * needs a plain fallback or starts from a given M_init). */
 int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph,
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);
@@ -306,7 +306,8 @@ typedef struct mrsim_surrogate mrsim_surrogate;
  * `epochs` passes in minibatches of `batch` (Adam, learning rate `lr`
  * decayed by a cosine to lr/100), `seed` for the counter-based draws, `bound` the per-entry error
  * bound of the fallback gate.  Errors: MRSIM_EINVAL (bad arguments, no
- * slice-selective pulse), MRSIM_ENOMEM, MRSIM_ECUDA. */
+ * slice-selective pulse), MRSIM_ENOMEM, MRSIM_ECUDA, MRSIM_ETIMEOUT (a bounded
+ * wait of the tensor-core inference kernel ran out). */
 int mrsim_surrogate_train(mrsim_ctx *ctx, const mrsim_seq *seq, const double *lo,
                           const double *hi, int64_t n_train, int epochs, int batch, double lr,
                           uint64_t seed, double bound, mrsim_surrogate **out);
@@ -325,7 +326,8 @@ int mrsim_surrogate_stats(const mrsim_surrogate *sur, const mrsim_ctx *ctx, doub
  * them (0 when none is served), *n_served (may be NULL) the number of served
  * (group, pulse) pairs.  The quantity the gate bounds, measured on the run's
  * own groups instead of validation draws.  Errors: MRSIM_EINVAL (NULL),
- * MRSIM_ESTATE (groups without the Gz-only type), MRSIM_ENOMEM, MRSIM_ECUDA. */
+ * MRSIM_ESTATE (groups without the Gz-only type), MRSIM_ENOMEM, MRSIM_ECUDA,
+ * MRSIM_ETIMEOUT. */
 int mrsim_surrogate_check(mrsim_ctx *ctx, const mrsim_surrogate *sur, const mrsim_seq *seq,
                           const mrsim_groups *groups, double *max_err, int64_t *n_served);
 
@@ -452,8 +454,11 @@ int64_t mrsim_launch_count(const mrsim_ctx *ctx);
  * return.
  *
  * The first call on a device looks up the device address of the scratch
- * array with that device current; make that first call before any stream
- * capture.  Every call shares the array, which keeps the last call's
+ * array with that device current and keeps it for the life of the process;
+ * make that first call before any stream capture.  The kept address does not
+ * survive a reset of the device's primary context (cudaDeviceReset): a
+ * program that resets the device must not call this entry point afterwards.
+ * Every call shares the array, which keeps the last call's
  * contents (each call clears what it uses first); calls that overlap on the
  * GPU (other streams, other host threads) race on it.
  * Errors: MRSIM_EINVAL (K < 1, n_samples < 0, a NULL pointer, n_groups
