@@ -61,9 +61,11 @@ extern "C" {
 #define MRSIM_G_Y 2
 #define MRSIM_G_Z 3
 #define MRSIM_G_GENERAL 4
-/* two-axis types (Gx+Gy, Gx+Gz, Gy+Gz: the paper's open problem, Sec. 5), reported
- * only by mrsim_classify with MRSIM_CLASSIFY_TWO_AXIS; mrsim_sequence types such
- * subsequences MRSIM_G_GENERAL (simulated per isochromat) */
+/* two-axis types (Gx+Gy, Gx+Gz, Gy+Gz: the paper's open problem, Sec. 5): the
+ * isochromats are grouped on both positions, keys (r_a, r_b, T1, T2, dB0[, b1]).
+ * Reported by mrsim_classify with MRSIM_CLASSIFY_TWO_AXIS, and by sequences
+ * made while MRSIM_TUNE_TWO_AXIS is 1 (the default); otherwise such
+ * subsequences are MRSIM_G_GENERAL (simulated per isochromat) */
 #define MRSIM_G_XY 5
 #define MRSIM_G_XZ 6
 #define MRSIM_G_YZ 7
@@ -191,8 +193,9 @@ int mrsim_group(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
                 mrsim_groups **out);
 
 /* Group count and (optionally) the group id of every isochromat, in the
- * phantom's original order, for gradient type gtype (MRSIM_G_NONE..Z).
- * gid: host int32[K] or NULL.  Errors: MRSIM_EINVAL (type not built). */
+ * phantom's original order, for gradient type gtype (MRSIM_G_NONE..Z,
+ * MRSIM_G_XY..YZ).  gid: host int32[K] or NULL.  Errors: MRSIM_EINVAL (type
+ * not built). */
 int mrsim_group_info(const mrsim_groups *groups, int gtype, int64_t *n_groups, int32_t *gid);
 
 /* Simulate the sequence on the phantom and return the received signal.
@@ -390,6 +393,14 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              Runs with receive coils, per-isochromat
  *                              advances ("direct" form) or gradient types that
  *                              vary inside a cell use the other form anyway.
+ *   MRSIM_TUNE_TWO_AXIS        typing of subsequences whose gradients use exactly
+ *                              two axes, for the sequences made by
+ *                              mrsim_sequence afterwards: 1 (default) types them
+ *                              MRSIM_G_XY / XZ / YZ and groups their isochromats
+ *                              on both positions (the extension of the paper's
+ *                              Sec. 2.4 keys its Sec. 5 leaves open); 0 types
+ *                              them MRSIM_G_GENERAL (per-isochromat fallback).
+ *                              Not a launch parameter: mrsim_autotune leaves it.
  * mrsim_set_tuning returns MRSIM_EINVAL for another parameter or value. */
 #define MRSIM_TUNE_FUSED_NI 0
 #define MRSIM_TUNE_PLAIN_RF_NI 1
@@ -397,6 +408,7 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
 #define MRSIM_TUNE_PRECOMP_LANES 3
 #define MRSIM_TUNE_PRECOMP_STEPS 4
 #define MRSIM_TUNE_CELL_NI 5
+#define MRSIM_TUNE_TWO_AXIS 6
 int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
 int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
 

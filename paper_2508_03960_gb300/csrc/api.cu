@@ -193,9 +193,8 @@ __global__ void k_validate(int64_t K, const float *x, const float *y, const floa
     }
 }
 
-// two-axis gradient types (Gx+Gy, Gx+Gz, Gy+Gz; the numbers of MRSIM_G_XY /
-// XZ / YZ), made only by the host classifier on request
-constexpr int G_XY = MRSIM_G_XY, G_XZ = MRSIM_G_XZ, G_YZ = MRSIM_G_YZ;
+static_assert(G_XY == MRSIM_G_XY && G_XZ == MRSIM_G_XZ && G_YZ == MRSIM_G_YZ,
+              "two-axis type numbers");
 
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
 // (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
@@ -270,7 +269,7 @@ void classify_sequence(mrsim_seq *s, bool two_axis) {
 }
 
 void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
-    classify_sequence(s, false);
+    classify_sequence(s, c->tune[MRSIM_TUNE_TWO_AXIS] != 0);
     // device waveforms of every distinct with-RF content
     mrsim_seq *dev = s;
     s->rf_f.resize(s->n_content);
@@ -314,7 +313,7 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
         dev->adc_off[i] = (int64_t)af.size();
         double tau = 0.0, m[3] = {0, 0, 0};
         int64_t si = q.sample0;
-        const int ax = q.gtype == G_X ? 0 : q.gtype == G_Y ? 1 : q.gtype == G_Z ? 2 : -1;
+        const int ax = gtype_axis0(q.gtype), ax2 = gtype_axis1(q.gtype);
         for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
             const double dt = s->dt[j];
             const double g[3] = {(double)s->gx[j], (double)s->gy[j], (double)s->gz[j]};
@@ -333,10 +332,13 @@ void build_sequence(mrsim_ctx *c, mrsim_seq *s) {
                 for (int32_t r = 0; r < s->rep[j]; ++r, ++si) {
                     const double ts = tau + (r + 1) * dt;
                     const double ks = ax >= 0 ? kGammaBar * (m[ax] + g[ax] * (r + 1) * dt) : 0.0;
-                    gd[si] = GSampleD{ts, ks};
+                    const double ks2 =
+                        ax2 >= 0 ? kGammaBar * (m[ax2] + g[ax2] * (r + 1) * dt) : 0.0;
+                    gd[si] = GSampleD{ts, ks, ks2};
                     GSampleF f;
                     sp(ts, f.tau_hi, f.tau_lo);
                     sp(ks, f.k_hi, f.k_lo);
+                    sp(ks2, f.k2_hi, f.k2_lo);
                     gf[si] = f;
                 }
             }
@@ -485,18 +487,21 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         if (q.type != SUB_ADC || q.gtype == G_GENERAL || q.n_samples == 0) continue;
         win_off[i] = P.ablk_n;
         GWin w{q.gtype, (int)g->n_groups[q.gtype], P.ablk_n, q.sample0, (int)q.n_samples, 0,
-               0.0f, 0.0f, 0.0f, 0.0f};
+               0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (q.seg_end - q.seg_begin == 1 && s->adc[q.seg_begin]) {
             const int64_t j = q.seg_begin;
             const double dt = s->dt[j];
-            const float gax = q.gtype == G_X ? s->gx[j] : q.gtype == G_Y ? s->gy[j]
-                            : q.gtype == G_Z ? s->gz[j] : 0.0f;
-            const double dk = kGammaBar * (double)gax * dt;
+            const float gs[3] = {s->gx[j], s->gy[j], s->gz[j]};
+            const int a0 = gtype_axis0(q.gtype), a1 = gtype_axis1(q.gtype);
+            const double dk = a0 >= 0 ? kGammaBar * (double)gs[a0] * dt : 0.0;
+            const double dk2 = a1 >= 0 ? kGammaBar * (double)gs[a1] * dt : 0.0;
             w.uniform = 1;
             w.dt_hi = (float)dt;
             w.dt_lo = (float)(dt - (double)w.dt_hi);
             w.dk_hi = (float)dk;
             w.dk_lo = (float)(dk - (double)w.dk_hi);
+            w.dk2_hi = (float)dk2;
+            w.dk2_lo = (float)(dk2 - (double)w.dk2_hi);
         }
         P.wins.push_back(w);
         P.ablk_n += g->n_groups[q.gtype];
@@ -518,7 +523,8 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         int mask = 0;
         const double kt[4] = {k[0], k[1], k[2], tau};
         for (int a = 0; a < 4; ++a) {
-            if (a < 3 && a != p - 1 && k[a] != 0.0) mask |= 1 << a;
+            // per-isochromat phase: the axes outside the primary type's
+            if (a < 3 && !(gtype_axes(p) & (1 << a)) && k[a] != 0.0) mask |= 1 << a;
             if constexpr (sizeof(R) == 4) {
                 e.k_hi[a] = (float)kt[a];
                 e.k_lo[a] = (float)(kt[a] - (double)e.k_hi[a]);
@@ -527,7 +533,8 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
             }
         }
         e.op = ev_op(kind, mask, gtype);
-        P.adv.push_back(EvAdv{p >= 1 ? k[p - 1] : 0.0, tau});
+        const int pa0 = gtype_axis0(p), pa1 = gtype_axis1(p);
+        P.adv.push_back(EvAdv{pa0 >= 0 ? k[pa0] : 0.0, tau, pa1 >= 0 ? k[pa1] : 0.0});
         P.kd.push_back({k[0], k[1], k[2]});
         return e;
     };
@@ -728,11 +735,12 @@ template <typename R>
 GSigTables<R> sig_tables(const mrsim_groups *g) {
     const bool f64 = sizeof(R) == 8;
     GSigTables<R> tab{};
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < kNTypes; ++t) {
         if (!g->built[t]) continue;
         tab.pos[t] = f64 ? (const R *)g->tab[t].d_pos64.p : (const R *)g->tab[t].d_pos.p;
         tab.dB0[t] = f64 ? (const R *)g->tab[t].d_dB064.p : (const R *)g->tab[t].d_dB0.p;
         tab.rT2[t] = f64 ? (const R *)g->tab[t].d_rT264.p : (const R *)g->tab[t].d_rT2.p;
+        tab.pos2[t] = f64 ? (const R *)g->tab[t].d_pos264.p : (const R *)g->tab[t].d_pos2.p;
     }
     return tab;
 }
@@ -745,7 +753,8 @@ FusedArgs<R> fused_args(const mrsim_groups *g, int p, R *Mx, R *My, R *Mz, const
     fa.x = g->x.as<float>(); fa.y = g->y.as<float>(); fa.z = g->z.as<float>();
     fa.T1 = g->T1.as<float>(); fa.T2 = g->T2.as<float>(); fa.dB0 = g->dB0.as<float>();
     fa.M0 = g->M0.as<float>();
-    for (int t = 0; t < 4; ++t) fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
+    for (int t = 0; t < kNTypes; ++t)
+        fa.gid[t] = g->built[t] ? g->gid_sorted[t].as<int32_t>() : nullptr;
     fa.gtype_p = p;
     fa.gtype_r = g->secondary >= 0 ? g->secondary : p;
     fa.Mx = Mx; fa.My = My; fa.Mz = Mz;
@@ -842,7 +851,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                 if (P.free_bits & (1 << a)) ca.f_sh[nf++] = fa.ax_sh[a];
             if (nf < 2) ca.f_sh[1] = 0;
             ca.r_sh = P.r_axis >= 0 ? fa.ax_sh[P.r_axis] : 0;
-            for (int t = 0; t < 4; ++t) ca.gid[t] = fa.gid[t];
+            for (int t = 0; t < kNTypes; ++t) ca.gid[t] = fa.gid[t];
             d_cev = (CellEv *)scratch(c, 25, P.cev.size() * sizeof(CellEv));
             upload(c, d_cev, P.cev.data(), P.cev.size() * sizeof(CellEv));
         }
@@ -1112,10 +1121,11 @@ int guard(mrsim_ctx *c, F &&f) {
     }
 }
 
-int most_frequent(const int cnt[5]) {
+// the most frequent gradient type with groups (ties: the smaller number)
+int most_frequent(const int cnt[kNTypes]) {
     int best = -1, bc = 0;
-    for (int t = 0; t < 4; ++t)
-        if (cnt[t] > bc) { bc = cnt[t]; best = t; }
+    for (int t = 0; t < kNTypes; ++t)
+        if (t != G_GENERAL && cnt[t] > bc) { bc = cnt[t]; best = t; }
     return best;
 }
 
@@ -1424,7 +1434,7 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
         g->uid = g_uid++;
         g->phantom_uid = ph->uid;
         g->K = ph->K;
-        int cnt_rf[5] = {0, 0, 0, 0, 0}, cnt_adc[5] = {0, 0, 0, 0, 0};
+        int cnt_rf[kNTypes] = {}, cnt_adc[kNTypes] = {};
         for (const Subseq &q : s->sub) {
             if (q.type == SUB_RF) cnt_rf[q.gtype]++;
             if (q.type == SUB_ADC) cnt_adc[q.gtype]++;
@@ -1432,10 +1442,11 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
         const int rf_t = most_frequent(cnt_rf), adc_t = most_frequent(cnt_adc);
         g->primary = adc_t >= 0 ? adc_t : (rf_t >= 0 ? rf_t : G_NONE);
         g->secondary = (rf_t >= 0 && rf_t != g->primary) ? rf_t : -1;
-        bool need[4] = {false, false, false, false};
-        for (int t = 0; t < 4; ++t) need[t] = cnt_rf[t] > 0 || cnt_adc[t] > 0;
+        bool need[kNTypes] = {};
+        for (int t = 0; t < kNTypes; ++t)
+            need[t] = t != G_GENERAL && (cnt_rf[t] > 0 || cnt_adc[t] > 0);
         need[g->primary] = true;
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kNTypes; ++t) {
             if (!need[t]) continue;
             build_group_type(c, ph, t, g->gid_orig[t], g->n_groups[t], g->tab[t]);
             g->built[t] = true;
@@ -1448,7 +1459,7 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
 }
 
 int mrsim_group_info(const mrsim_groups *g, int gtype, int64_t *n_groups, int32_t *gid) {
-    if (!g || gtype < 0 || gtype > 3 || !g->built[gtype]) return MRSIM_EINVAL;
+    if (!g || gtype < 0 || gtype >= kNTypes || !g->built[gtype]) return MRSIM_EINVAL;
     if (n_groups) *n_groups = g->n_groups[gtype];
     if (gid) {
         if (cudaMemcpyAsync(gid, g->gid_orig[gtype].p, g->K * sizeof(int32_t),
@@ -1537,10 +1548,11 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
 
 int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
-    static const int allowed[6][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
+    static const int allowed[7][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
                                       {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
-                                      {1, 2, 4, 8, 16, 32}, {0, 4, 8, -1, -1, -1}};
-    if (param < 0 || param > 5) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
+                                      {1, 2, 4, 8, 16, 32}, {0, 4, 8, -1, -1, -1},
+                                      {0, 1, -1, -1, -1, -1}};
+    if (param < 0 || param > 6) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
     for (int v : allowed[param]) ok |= v >= 0 && v == value;
     if (!ok) return set_err(c, MRSIM_EINVAL, "value not allowed for this tuning parameter");
@@ -1549,7 +1561,7 @@ int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
 }
 
 int mrsim_get_tuning(const mrsim_ctx *c, int param, int *value) {
-    if (!c || !value || param < 0 || param > 5) return MRSIM_EINVAL;
+    if (!c || !value || param < 0 || param > 6) return MRSIM_EINVAL;
     *value = c->tune[param];
     return MRSIM_OK;
 }

@@ -14,7 +14,25 @@ constexpr double kGamma = kTwoPi * kGammaBar;
 constexpr double kLog2e = 1.4426950408889634073599246810019;
 
 enum SubType : int { SUB_RF = 0, SUB_ADC = 1, SUB_RELAX = 2 };
-enum GType : int { G_NONE = 0, G_X = 1, G_Y = 2, G_Z = 3, G_GENERAL = 4 };
+// gradient types (Sec. 2.4); the two-axis types group on both positions
+enum GType : int {
+    G_NONE = 0, G_X = 1, G_Y = 2, G_Z = 3, G_GENERAL = 4, G_XY = 5, G_XZ = 6, G_YZ = 7
+};
+constexpr int kNTypes = 8;  // gradient type numbers (G_GENERAL has no groups)
+// position axes of a gradient type: a0 (or -1 for no-grads / general) and a1
+// (the second axis of a two-axis type, else -1)
+__host__ __device__ constexpr int gtype_axis0(int t) {
+    return t == G_X ? 0 : t == G_Y ? 1 : t == G_Z ? 2 : t == G_XY ? 0 : t == G_XZ ? 0
+         : t == G_YZ ? 1 : -1;
+}
+__host__ __device__ constexpr int gtype_axis1(int t) {
+    return t == G_XY ? 1 : t == G_XZ ? 2 : t == G_YZ ? 2 : -1;
+}
+// bit mask of the axes of a gradient type
+__host__ __device__ constexpr int gtype_axes(int t) {
+    return (gtype_axis0(t) >= 0 ? 1 << gtype_axis0(t) : 0) |
+           (gtype_axis1(t) >= 0 ? 1 << gtype_axis1(t) : 0);
+}
 enum EvKind : int { EV_RF = 0, EV_ADC = 1, EV_END = 2 };
 
 // Free-precession parameters of an advance from the state time t_w to a
@@ -92,8 +110,9 @@ __host__ __device__ constexpr int ev_mask(int op) { return (op >> 2) & 7; }
 __host__ __device__ constexpr int ev_gtype(int op) { return (op >> 5) & 7; }
 // per-event inputs of the group-factor table
 struct EvAdv {
-    double kp;   // gamma_bar * moment on the primary axis (cycles/m)
+    double kp;   // gamma_bar * moment on the primary type's first axis (cycles/m)
     double tau;  // time since the state time (s)
+    double kp2;  // ... on its second axis (two-axis primary types; else 0)
 };
 
 // A with-ADC window for the grouped signal kernel (Eqs. 8, 10).
@@ -108,13 +127,15 @@ struct GWin {
     // dk = gamma_bar g dt (cycles/m) on the group's axis, as hi + lo floats
     int uniform;
     float dt_hi, dt_lo, dk_hi, dk_lo;
+    float dk2_hi, dk2_lo;  // the same on the second axis of a two-axis type
 };
-// per-sample time and moment since the window start on the group's axis
+// per-sample time and moments since the window start on the group type's
+// axes (k2: second axis of a two-axis type, else 0)
 struct GSampleF {
-    float tau_hi, tau_lo, k_hi, k_lo;
+    float tau_hi, tau_lo, k_hi, k_lo, k2_hi, k2_lo;
 };
 struct GSampleD {
-    double tau, k;
+    double tau, k, k2;
 };
 
 // ------------------------------------------------------------------------

@@ -76,7 +76,7 @@ struct mrsim_ctx {
     const struct mrsim_surrogate *sur = nullptr;
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
-    int tune[6] = {4, 2, 2, 0, 8, 8};  // indexed by the MRSIM_TUNE_* parameters
+    int tune[7] = {4, 2, 2, 0, 8, 8, 1};  // indexed by the MRSIM_TUNE_* parameters
 };
 
 struct mrsim_phantom_t {
@@ -102,10 +102,11 @@ struct Subseq {
 
 struct GroupTable {
     int64_t n = 0;
-    std::vector<double> pos, T1, T2, dB0, b1;  // host copies
-    DBuf d_par64;                    // [5][n] doubles: pos, T1, T2, dB0, b1 (precompute)
-    DBuf d_pos, d_dB0, d_rT2;        // float copies for the group-signal kernel
-    DBuf d_pos64, d_dB064, d_rT264;  // double copies for the group-signal kernel
+    // host copies; pos2: second position of a two-axis type (else 0)
+    std::vector<double> pos, T1, T2, dB0, b1, pos2;
+    DBuf d_par64;                    // [6][n] doubles: pos, T1, T2, dB0, b1, pos2
+    DBuf d_pos, d_dB0, d_rT2, d_pos2;          // float copies for the group-signal kernel
+    DBuf d_pos64, d_dB064, d_rT264, d_pos264;  // double copies for the group-signal kernel
 };
 
 }  // namespace mrsim
@@ -138,11 +139,12 @@ struct mrsim_groups {
     uint64_t uid = 0;
     uint64_t phantom_uid = 0;
     int64_t K = 0;
-    bool built[4] = {false, false, false, false};
-    int64_t n_groups[4] = {0, 0, 0, 0};
-    mrsim::DBuf gid_orig[4];    // int32 [K], phantom order
-    mrsim::DBuf gid_sorted[4];  // int32 [K], layout order
-    mrsim::GroupTable tab[4];
+    // per gradient type (G_GENERAL, number 4, has none)
+    bool built[mrsim::kNTypes] = {};
+    int64_t n_groups[mrsim::kNTypes] = {};
+    mrsim::DBuf gid_orig[mrsim::kNTypes];    // int32 [K], phantom order
+    mrsim::DBuf gid_sorted[mrsim::kNTypes];  // int32 [K], layout order
+    mrsim::GroupTable tab[mrsim::kNTypes];
     int primary = -1, secondary = -1;  // layout keys (gradient types)
     int64_t n_cells = 0;
     // distinct positions of the two axes other than the primary one, numbered
@@ -300,7 +302,8 @@ struct PrecompArgs {
     int64_t n_steps;
     int gtype;
     int64_t n_groups;
-    const double *par;       // [5][n_groups]: pos, T1, T2, dB0, b1
+    const double *par;       // [5][n_groups]: pos, T1, T2, dB0, b1 (+ pos2 in row 5 for a
+                             // two-axis type)
     void *out;               // R [n_groups][12]
     const int32_t *gidx = nullptr;    // optional: only the groups gidx[0 .. *gcount)
     const int32_t *gcount = nullptr;
@@ -313,7 +316,7 @@ template <typename R>
 struct FusedArgs {
     int64_t K;
     const float *x, *y, *z, *T1, *T2, *dB0, *M0;
-    const int32_t *gid[4];   // layout-order gids per gradient type (null if not built)
+    const int32_t *gid[kNTypes];  // layout-order gids per gradient type (null if not built)
     int gtype_p, gtype_r;    // ADC-sorted type, preferred RF type (-1: none)
     R *Mx, *My, *Mz;
     int init_eq;
@@ -366,8 +369,8 @@ struct CellArgs {
     const float2 *qtab;       // per-event axis phasor tables
     int f_sh[2];              // bit position of each free axis' index in aidx
     int r_sh;                 // bit position of the secondary axis' index, or -1
-    const int32_t *gid[4];    // layout-order gids per gradient type (with-ADC
-                              // windows of the secondary or no-grads type)
+    const int32_t *gid[kNTypes];  // layout-order gids per gradient type (with-ADC
+                                  // windows of the secondary or no-grads type)
 };
 // Which per-isochromat and per-thread phasors a cell-form launch applies
 // (fixed for the whole span, so the kernel is specialised on them).
@@ -416,7 +419,7 @@ void launch_event_table(mrsim_ctx *c, const EvAdv *d_adv, int n_ev, int64_t G, c
 
 template <typename R>
 struct GSigTables {
-    const R *pos[4], *dB0[4], *rT2[4];
+    const R *pos[kNTypes], *dB0[kNTypes], *rT2[kNTypes], *pos2[kNTypes];
 };
 // batched forms (one launch for many jobs)
 struct EvTabJob {

@@ -31,14 +31,16 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z;
 }
 
-// Grouping key of one gradient type: (r_axis, T1, T2, dB0, b1) as float32
-// bit patterns, -0 folded to +0.  No-grads uses 0 for the position word; a
-// phantom without b1 uses 1.0f for it.
+// Grouping key of one gradient type: (r_axis, T1, T2, dB0, b1, r_axis2) as
+// float32 bit patterns, -0 folded to +0 (Fig. 2; the second position only for
+// a two-axis type).  No-grads uses 0 for the position words, one-axis types 0
+// for the second; a phantom without b1 uses 1.0f for it.
 struct PhantomKey {
-    static constexpr int W = 5;
-    const float *pos, *T1, *T2, *dB0, *b1;
+    static constexpr int W = 6;
+    const float *pos, *T1, *T2, *dB0, *b1, *pos2;
     __device__ __forceinline__ bool words(int64_t k, uint32_t w[W]) const {
-        float v[W] = {pos ? pos[k] : 0.0f, T1[k], T2[k], dB0[k], b1 ? b1[k] : 1.0f};
+        float v[W] = {pos ? pos[k] : 0.0f, T1[k], T2[k], dB0[k], b1 ? b1[k] : 1.0f,
+                      pos2 ? pos2[k] : 0.0f};
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
@@ -230,8 +232,9 @@ __global__ void k_scan_apply(const int32_t *in, int64_t n, const int64_t *tile_o
 // per-group parameters from the representatives
 __global__ void k_group_table(int64_t K, const int32_t *flag, const int32_t *rank,
                               const float *pos, const float *T1, const float *T2,
-                              const float *dB0, const float *b1, double *o_pos, double *o_T1,
-                              double *o_T2, double *o_dB0, double *o_b1) {
+                              const float *dB0, const float *b1, const float *pos2,
+                              double *o_pos, double *o_T1, double *o_T2, double *o_dB0,
+                              double *o_b1, double *o_pos2) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
          k += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[k]) continue;
@@ -241,6 +244,7 @@ __global__ void k_group_table(int64_t K, const int32_t *flag, const int32_t *ran
         o_T2[g] = T2[k];
         o_dB0[g] = dB0[k];
         o_b1[g] = b1 ? (double)b1[k] : 1.0;
+        o_pos2[g] = pos2 ? (double)pos2[k] : 0.0;
     }
 }
 
@@ -459,27 +463,27 @@ int64_t hash_group(mrsim_ctx *c, int64_t K, const KF &kf, int32_t *gid, int32_t 
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab) {
     const int64_t K = ph->K;
-    const float *pos = gtype == G_X ? ph->x.as<float>()
-                     : gtype == G_Y ? ph->y.as<float>()
-                     : gtype == G_Z ? ph->z.as<float>()
-                                    : nullptr;
+    const float *axis[3] = {ph->x.as<float>(), ph->y.as<float>(), ph->z.as<float>()};
+    const int a0 = gtype_axis0(gtype), a1 = gtype_axis1(gtype);
+    const float *pos = a0 >= 0 ? axis[a0] : nullptr;
+    const float *pos2 = a1 >= 0 ? axis[a1] : nullptr;
     PhantomKey kf{pos, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
-                  ph->has_b1 ? ph->b1.as<float>() : nullptr};
+                  ph->has_b1 ? ph->b1.as<float>() : nullptr, pos2};
     gid = dalloc(K * sizeof(int32_t));
     int32_t *flag, *rank;
     n_groups = hash_group(c, K, kf, gid.as<int32_t>(), &flag, &rank);
     const int64_t G = n_groups;
-    DBuf t = dalloc(5 * G * sizeof(double));
+    DBuf t = dalloc(6 * G * sizeof(double));
     double *tp = t.as<double>();
     {
         KScope ks(c, "group_table");
         k_group_table<<<grid_for(c, K), 256, 0, c->stream>>>(
             K, flag, rank, pos, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
-            ph->has_b1 ? ph->b1.as<float>() : nullptr, tp, tp + G, tp + 2 * G, tp + 3 * G,
-            tp + 4 * G);
+            ph->has_b1 ? ph->b1.as<float>() : nullptr, pos2, tp, tp + G, tp + 2 * G, tp + 3 * G,
+            tp + 4 * G, tp + 5 * G);
     }
-    std::vector<double> h(5 * G);
-    MRSIM_CUDA(cudaMemcpyAsync(h.data(), tp, 5 * G * sizeof(double), cudaMemcpyDeviceToHost,
+    std::vector<double> h(6 * G);
+    MRSIM_CUDA(cudaMemcpyAsync(h.data(), tp, 6 * G * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
     sync(c);
     tab.n = G;
@@ -488,14 +492,16 @@ void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &
     tab.T2.assign(h.begin() + 2 * G, h.begin() + 3 * G);
     tab.dB0.assign(h.begin() + 3 * G, h.begin() + 4 * G);
     tab.b1.assign(h.begin() + 4 * G, h.begin() + 5 * G);
+    tab.pos2.assign(h.begin() + 5 * G, h.begin() + 6 * G);
     // device copies used by the precompute and group-signal kernels
-    std::vector<float> fpos(G), fdB0(G), frT2(G);
+    std::vector<float> fpos(G), fdB0(G), frT2(G), fpos2(G);
     std::vector<double> rT2d(G);
     for (int64_t g = 0; g < G; ++g) {
         fpos[g] = (float)tab.pos[g];
         fdB0[g] = (float)tab.dB0[g];
         rT2d[g] = std::isinf(tab.T2[g]) ? 0.0 : kLog2e / tab.T2[g];
         frT2[g] = (float)rT2d[g];
+        fpos2[g] = (float)tab.pos2[g];
     }
     auto up = [&](DBuf &d, const void *src, size_t bytes) {
         d = dalloc(bytes);
@@ -504,10 +510,12 @@ void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &
     up(tab.d_pos, fpos.data(), G * 4);
     up(tab.d_dB0, fdB0.data(), G * 4);
     up(tab.d_rT2, frT2.data(), G * 4);
+    up(tab.d_pos2, fpos2.data(), G * 4);
     up(tab.d_pos64, tab.pos.data(), G * 8);
     up(tab.d_dB064, tab.dB0.data(), G * 8);
     up(tab.d_rT264, rT2d.data(), G * 8);
-    // FP64 parameter block (pos, T1, T2, dB0, b1) for the precompute kernel
+    up(tab.d_pos264, tab.pos2.data(), G * 8);
+    // FP64 parameter block (pos, T1, T2, dB0, b1, pos2) for the precompute kernel
     tab.d_par64 = std::move(t);
 }
 
@@ -625,7 +633,7 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
                 K, perm, ph->M_init.as<float>() + r * K, g->M_init.as<float>() + r * K);
         }
     }
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < kNTypes; ++t) {
         if (!g->built[t]) continue;
         g->gid_sorted[t] = dalloc(K * sizeof(int32_t));
         KScope ks(c, "layout_gather");

@@ -55,7 +55,9 @@ __device__ __forceinline__ void load_row(const R *p, R (&T)[12]) {
 template <typename R>
 struct R4 { R x, y, z, w; };
 
-// P(e, g) = E2 exp(-i 2 pi (pos_g kp_e + dB0_g tau_e)), E1 = exp(-tau_e / T1_g).
+// P(e, g) = E2 exp(-i 2 pi (pos_g kp_e + pos2_g kp2_e + dB0_g tau_e)),
+// E1 = exp(-tau_e / T1_g); pos2 and kp2 belong to the second axis of a
+// two-axis primary type (both 0 otherwise).
 // The phase is reduced modulo one turn in FP64, the rest is evaluated in R.
 template <typename R>
 __global__ void k_event_table(const EvAdv *adv, int n_ev, int64_t G, const double *par,
@@ -66,7 +68,8 @@ __global__ void k_event_table(const EvAdv *adv, int n_ev, int64_t G, const doubl
         const int64_t e = i / G, g = i - e * G;
         const EvAdv ea = adv[e];
         const double pos = par[g], T1 = par[G + g], T2 = par[2 * G + g], dB0 = par[3 * G + g];
-        double ph = pos * ea.kp + dB0 * ea.tau;
+        // pos2 (row 5): the second position of a two-axis primary type, else 0
+        double ph = pos * ea.kp + par[5 * G + g] * ea.kp2 + dB0 * ea.tau;
         ph -= rint(ph);
         R c, s;
         phasor((R)ph, c, s);
@@ -93,7 +96,7 @@ __global__ void k_event_table_batch(const EvTabJob *jobs, const int64_t *off, in
         const EvAdv ea = jb.adv[e];
         const double pos = jb.par[g], T1 = jb.par[jb.G + g], T2 = jb.par[2 * jb.G + g];
         const double dB0 = jb.par[3 * jb.G + g];
-        double ph = pos * ea.kp + dB0 * ea.tau;
+        double ph = pos * ea.kp + jb.par[5 * jb.G + g] * ea.kp2 + dB0 * ea.tau;
         ph -= rint(ph);
         R c, sn;
         phasor((R)ph, c, sn);
@@ -665,11 +668,15 @@ struct GS<float> { using S = GSampleF; };
 template <>
 struct GS<double> { using S = GSampleD; };
 
-__device__ __forceinline__ float gs_turns(const GSampleF &s, float pos, float dB0) {
-    return turns_prod(pos, s.k_hi, s.k_lo) + turns_prod(dB0, s.tau_hi, s.tau_lo);
+// phase (turns) of a group at a sample: its positions times the moments on
+// its type's axes (pos2: second axis of a two-axis type, else 0) plus dB0 tau
+__device__ __forceinline__ float gs_turns(const GSampleF &s, float pos, float pos2, float dB0) {
+    return turns_prod(pos, s.k_hi, s.k_lo) + turns_prod(pos2, s.k2_hi, s.k2_lo) +
+           turns_prod(dB0, s.tau_hi, s.tau_lo);
 }
-__device__ __forceinline__ double gs_turns(const GSampleD &s, double pos, double dB0) {
-    double v = pos * s.k + dB0 * s.tau;
+__device__ __forceinline__ double gs_turns(const GSampleD &s, double pos, double pos2,
+                                           double dB0) {
+    double v = pos * s.k + pos2 * s.k2 + dB0 * s.tau;
     return v - rint(v);
 }
 __device__ __forceinline__ float gs_tau(const GSampleF &s) { return s.tau_hi + s.tau_lo; }
@@ -689,6 +696,7 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
                                                   const GSigTables<float> &tab,
                                                   const double *Ablk, double *signal) {
     __shared__ float s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
+    __shared__ float s_pos2[kGTile];
     __shared__ double s_red[2][kThreads * kRun];
     const int NR = (nsb + kRun - 1) / kRun;
     int NRp = 1;
@@ -702,6 +710,7 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
     const float tau0 = sm.tau_hi + sm.tau_lo;
     const float dt = w.dt_hi + w.dt_lo;
     const float *pos = tab.pos[w.gtype], *dB0 = tab.dB0[w.gtype], *rT2 = tab.rT2[w.gtype];
+    const float *pos2 = tab.pos2[w.gtype];
     // FP32 partial sums, folded into FP64 every LPR tiles: each partial then
     // covers 256 groups whatever the mapping (an FP64 fold per tile would make
     // the FP64 pipe, a small fraction of the FP32 rate here, the bottleneck)
@@ -718,6 +727,7 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
         __syncthreads();
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             s_pos[t] = pos[g0 + t];
+            s_pos2[t] = pos2[g0 + t];
             s_dB0[t] = dB0[g0 + t];
             s_rT2[t] = rT2[g0 + t];
             s_ar[t] = (float)Ablk[2 * (w.ablk + g0 + t)];
@@ -727,8 +737,9 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
         if (len > 0) {
             for (int t = gl; t < n; t += LPR) {
                 float c, sn, cz, sz;
-                phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, sn);
+                phasor(gs_turns(sm, s_pos[t], s_pos2[t], s_dB0[t]), c, sn);
                 phasor(turns_prod(s_pos[t], w.dk_hi, w.dk_lo) +
+                           turns_prod(s_pos2[t], w.dk2_hi, w.dk2_lo) +
                            turns_prod(s_dB0[t], w.dt_hi, w.dt_lo),
                        cz, sz);
                 const float e = decay(tau0, s_rT2[t]), ez = decay(dt, s_rT2[t]);
@@ -788,6 +799,7 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
                                                    const GSigTables<R> &tab, const double *Ablk,
                                                    double *signal) {
     __shared__ R s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
+    __shared__ R s_pos2[kGTile];
     __shared__ double s_red[2][kThreads];
     const GWin w = wins[b.x];
     // samples of this block: [b.y, b.y + nsb).  A window shorter than the
@@ -810,12 +822,14 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
     if (act) sm = smp[s_idx];
     const R tau = act ? (R)gs_tau(sm) : (R)0;
     const R *pos = tab.pos[w.gtype], *dB0 = tab.dB0[w.gtype], *rT2 = tab.rT2[w.gtype];
+    const R *pos2 = tab.pos2[w.gtype];
     double accr = 0, acci = 0;
     for (int g0 = b.z; g0 < b.w; g0 += kGTile) {
         const int n = min(kGTile, b.w - g0);
         __syncthreads();
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             s_pos[t] = pos[g0 + t];
+            s_pos2[t] = pos2[g0 + t];
             s_dB0[t] = dB0[g0 + t];
             s_rT2[t] = rT2[g0 + t];
             s_ar[t] = (R)Ablk[2 * (w.ablk + g0 + t)];
@@ -826,7 +840,7 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
         if (act) {
             for (int t = sl; t < n; t += LPS) {
                 R c, s;
-                phasor(gs_turns(sm, s_pos[t], s_dB0[t]), c, s);
+                phasor(gs_turns(sm, s_pos[t], s_pos2[t], s_dB0[t]), c, s);
                 const R e = decay(tau, s_rT2[t]);
                 const R ar = s_ar[t], ai = s_ai[t];
                 pr += e * (c * ar + s * ai);

@@ -81,6 +81,9 @@ __device__ __forceinline__ void compose_run(const PrecompArgs &a, int64_t g, int
     if (s1 <= s0) return;
     const R pos = (R)par[g], T1 = (R)par[G + g], T2 = (R)par[2 * G + g];
     const R dB0 = (R)par[3 * G + g], b1 = (R)par[4 * G + g];
+    // second position of a two-axis type (its rows carry a sixth parameter)
+    const int a0 = gtype_axis0(gtype), a1 = gtype_axis1(gtype);
+    const R pos2 = a1 >= 0 ? (R)par[5 * G + g] : (R)0;
     const R iT1 = isinf((double)T1) ? (R)0 : (R)1 / T1;
     const R iT2 = isinf((double)T2) ? (R)0 : (R)1 / T2;
     // segment holding step s0 (binary search on the prefix offsets)
@@ -103,10 +106,13 @@ __device__ __forceinline__ void compose_run(const PrecompArgs &a, int64_t g, int
             em1 = expm1(-dt_prev * iT1);
             em2 = expm1(-dt_prev * iT2);
         }
-        const R cA = gtype == G_X ? (R)sg.cx : gtype == G_Y ? (R)sg.cy
-                   : gtype == G_Z ? (R)sg.cz : (R)0;
+        const R cax[3] = {(R)sg.cx, (R)sg.cy, (R)sg.cz};
+        const R cA = a0 >= 0 ? cax[a0] : (R)0;
+        const R cB = a1 >= 0 ? cax[a1] : (R)0;
         const R px = -b1 * (R)sg.are, py = -b1 * (R)sg.aim;
-        const R pz = -(cA * pos + (R)sg.cdw * dB0);
+        // the gradient is zero on axes outside the group's type: Bz needs only
+        // the group's positions (Sec. 2.4; two positions for a two-axis type)
+        const R pz = -(cA * pos + cB * pos2 + (R)sg.cdw * dB0);
         const R th2 = px * px + py * py + pz * pz;
         R s, c2;
         rot_coeffs(th2, s, c2);

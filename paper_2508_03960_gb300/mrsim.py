@@ -29,6 +29,7 @@ PTR_DEVICE, OUT_DEVICE = 1, 2
 TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1, 2, 3
 TUNE_PRECOMP_STEPS = 4
 TUNE_CELL_NI = 5
+TUNE_TWO_AXIS = 6
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",

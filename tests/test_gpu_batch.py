@@ -71,7 +71,7 @@ def test_batch_errors(mrsim, ctx):
     b = SeqBuilder()
     b.rf_hard(30, "x", 100e-6, 10e-6)
     b.add(1e-3, 1, g=(1e-3, 1e-3, 0))
-    b.add(10e-6, 8, g=(2e-3, 1e-3, 0), adc=True)  # Gx and Gy during the ADC: general
+    b.add(10e-6, 8, g=(2e-3, 1e-3, 1e-3), adc=True)  # all three axes during the ADC: general
     gseq = b.build()
     hs2 = ctx.sequence(gseq)
     hg2 = ctx.group(hp, hs2)

@@ -70,16 +70,25 @@ def test_spin_echo_32x32x4_all_modes(mrsim, ctx, mode, precision):
     check(sig, M, ref, Mref, precision)
 
 
-def test_classification_bit_exact(mrsim, ctx):
-    for seq in (configs.se_32()[1], fse_2d(n_ro=32, n_pe=32, etl=8, n_shots=1),
-                epi_2d(n_ro=32, n_lines=16), gre_2d(n_ro=16, n_pe=4)):
-        hs = ctx.sequence(seq)
-        info = mrsim.mrsim_seq_info(hs)
-        ctx.free("seq", hs)
-        q = oracle.classify(seq)
-        for k in ("type", "gtype", "seg_begin", "seg_end"):
-            assert np.array_equal(info[k], q[k].astype(info[k].dtype)), k
-        assert info["n_samples_total"] == int(q["n_samples"].sum())
+@pytest.mark.parametrize("two_axis", [1, 0])
+def test_classification_bit_exact(mrsim, ctx, two_axis):
+    """Subsequence split and gradient types of the library's sequences equal
+    the oracle's classifier, with two-axis typing on (the default) and off."""
+    from mrsim_inputs.sequence import radial_2d
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, two_axis)
+    try:
+        for seq in (configs.se_32()[1], fse_2d(n_ro=32, n_pe=32, etl=8, n_shots=1),
+                    epi_2d(n_ro=32, n_lines=16), gre_2d(n_ro=16, n_pe=4),
+                    radial_2d(n_ro=16, n_spokes=6, oblique_deg=20.0)):
+            hs = ctx.sequence(seq)
+            info = mrsim.mrsim_seq_info(hs)
+            ctx.free("seq", hs)
+            q = oracle.classify(seq, two_axis=bool(two_axis))
+            for k in ("type", "gtype", "seg_begin", "seg_end"):
+                assert np.array_equal(info[k], q[k].astype(info[k].dtype)), k
+            assert info["n_samples_total"] == int(q["n_samples"].sum())
+    finally:
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, 1)
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 4), (16, 24, 3), (64, 64, 8)])
@@ -175,16 +184,25 @@ def general_type_sequence():
     return b.build()
 
 
+@pytest.mark.parametrize("two_axis", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_general_type_fallback_and_no_grads(mrsim, ctx, precision):
+def test_general_type_fallback_and_no_grads(mrsim, ctx, precision, two_axis):
+    """With two-axis typing off, the Gx+Gz pulse and the Gx+Gy window are
+    general subsequences (the per-isochromat fallback between spans); with it
+    on they are grouped on two positions.  Both match the oracle."""
     ph = configs.small_phantom(16, 16, 3)
     seq = general_type_sequence()
-    q = oracle.classify(seq)
-    assert 4 in set(q["gtype"][q["type"] != oracle.RELAX])  # has GENERAL subsequences
+    q = oracle.classify(seq, two_axis=bool(two_axis))
+    kinds = set(q["gtype"][q["type"] != oracle.RELAX])
+    assert (4 in kinds) if not two_axis else (oracle.G_XZ in kinds and oracle.G_XY in kinds)
     ref, Mref = oracle.simulate(ph, seq)
-    for mode in (mrsim.GROUPED, mrsim.PLAIN, mrsim.PLAIN_CACHE):
-        sig, M = run_both(mrsim, ctx, ph, seq, mode, precision)
-        check(sig, M, ref, Mref, precision)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, two_axis)
+    try:
+        for mode in (mrsim.GROUPED, mrsim.PLAIN, mrsim.PLAIN_CACHE):
+            sig, M = run_both(mrsim, ctx, ph, seq, mode, precision)
+            check(sig, M, ref, Mref, precision)
+    finally:
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, 1)
 
 
 def test_initial_state_b1_scale_and_infinite_relaxation(mrsim, ctx):
@@ -333,8 +351,8 @@ def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
 
 def test_tuning_parameters_are_validated(mrsim, ctx):
     for param, bad in ((mrsim.TUNE_FUSED_NI, 3), (mrsim.TUNE_PRECOMP_LANES, 64),
-                       (mrsim.TUNE_PRECOMP_STEPS, 64), (mrsim.TUNE_CELL_NI, 1), (6, 1),
-                       (-1, 1)):
+                       (mrsim.TUNE_PRECOMP_STEPS, 64), (mrsim.TUNE_CELL_NI, 1),
+                       (mrsim.TUNE_TWO_AXIS, 2), (7, 1), (-1, 1)):
         with pytest.raises(mrsim.MrsimError):
             mrsim.mrsim_set_tuning(ctx.h, param, bad)
     before = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS)
