@@ -332,6 +332,60 @@ def multicoil_workload(ctx, mrsim, torch, ph, seq, hp_single, hg_single, steps, 
     return out
 
 
+def radial_workload(ctx, mrsim, torch, hp, K, steps):
+    """Radial readouts at 27.5M isochromats: 62 of the 64 spokes read on Gx and
+    Gy together (two-axis with-ADC windows, the open problem of Sec. 5).  The
+    same GPU runs them grouped on both positions, with two-axis typing off
+    (those windows per isochromat, the conventional fallback) and fully per
+    isochromat (plain)."""
+    from mrsim_inputs import configs
+    seq = configs.radial_sequence()
+    stream = torch.cuda.current_stream()
+    sig = torch.zeros(2 * seq.n_samples, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(hs, hg, mode, reps, warm=True):
+        if warm:
+            mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+        mrsim.mrsim_profile_reset(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            mrsim.mrsim_run(ctx.h, hp, hs, hg, mode, mrsim.FP32, sig, None, mrsim.OUT_DEVICE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = {k: round(v[1] / reps, 3) for k, v in mrsim.mrsim_profile_get(ctx.h).items()
+                if v[0]}
+        mrsim.mrsim_profile_enable(ctx.h, False)
+        return e0.elapsed_time(e1) / reps / 1e3, sig.cpu().numpy().view(np.complex128).copy(), prof
+
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    groups = {n: mrsim.mrsim_group_info(hg, t)[0] for n, t in
+              (("xy", mrsim.G_XY), ("x", mrsim.G_X), ("y", mrsim.G_Y), ("z", mrsim.G_Z))}
+    t_g, s_g, k_g = timed(hs, hg, mrsim.GROUPED, steps)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, 0)
+    hs0 = ctx.sequence(seq)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_TWO_AXIS, 1)
+    hg0 = ctx.group(hp, hs0)
+    t_f, s_f, k_f = timed(hs0, hg0, mrsim.GROUPED, 1)
+    t_p, s_p, k_p = timed(hs, None, mrsim.PLAIN, 1, warm=False)
+    ctx.free("grp", hg0)
+    ctx.free("seq", hs0)
+    ctx.free("grp", hg)
+    ctx.free("seq", hs)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"K": K, "spokes": 64, "samples": seq.n_samples, "groups": groups,
+            "grouped_two_axis_s": round(t_g, 5), "general_fallback_s": round(t_f, 4),
+            "plain_s": round(t_p, 3), "speedup_vs_plain": round(t_p / t_g, 1),
+            "speedup_vs_general_fallback": round(t_f / t_g, 1),
+            "kernels_ms_grouped": k_g, "kernels_ms_general_fallback": k_f,
+            "kernels_ms_plain": k_p,
+            "rel_l2_grouped_vs_plain": rel(s_g, s_p),
+            "rel_l2_fallback_vs_plain": rel(s_f, s_p)}
+
+
 def recon_workload(ctx, mrsim, torch, named_signals, steps):
     """Images of the simulated FSE and EPI k-space (mrsim_recon_cartesian on
     device buffers), timed with CUDA events, against the oracle's (numpy FFT)
@@ -776,6 +830,11 @@ def main():
                            a.steps)
     # ---- receive coils (Eq. 6 with P coils) ----
     multicoil = multicoil_workload(ctx, mrsim, torch, ph, fse, hp, hg_f, a.steps)
+    # ---- two-axis gradient types: radial readouts ----
+    try:
+        radial = radial_workload(ctx, mrsim, torch, hp, ph.K, a.steps)
+    except Exception as e:  # reported in the line; the main metric stands on its own
+        radial = {"error": f"{type(e).__name__}: {e}"}
     # ---- group-reducing preprocessing (clustering) of a mapped phantom ----
     try:
         clustering = cluster_workload(ctx, mrsim, torch, (("fse", fse), ("epi", epi)))
@@ -917,6 +976,7 @@ def main():
         "surrogate": surrogate,
         "multicoil": multicoil,
         "recon": recon,
+        "radial": radial,
         "clustering": clustering,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
         "roofline": roof, "kernel_roofline": kroof, "cpu_baseline": cpu,

@@ -7,6 +7,9 @@
                  8 ellipses, 3 ms sinc 90x/180y at 1 us, ETL 16, 256 phase
                  encodes in 16 shots, 256 samples at 4 us, ESP 8 ms, TR 3 s
                  (seed 1002).
+* ``radial_27m`` radial spoiled gradient echo on the same phantom: 64 spokes
+                 of 256 samples at 4 us (Gx and Gy together off the axes),
+                 3 ms sinc 30 deg at 1 us, TE 5 ms, TR 10 ms.
 * ``epi_27m``    single-shot EPI on the same phantom: 3 ms sinc 90x at 1 us,
                  128 lines x 128 samples at 3 us on alternating Gx trapezoids
                  with 100 us ramps at a 1 us raster, Gy blips on the ramps.
@@ -32,7 +35,7 @@ from typing import Tuple
 import numpy as np
 
 from .phantom import Phantom, ellipse_phantom, continuous_phantom, mapped_phantom
-from .sequence import Sequence, spin_echo_2d, fse_2d, epi_2d, gre_2d
+from .sequence import Sequence, spin_echo_2d, fse_2d, epi_2d, gre_2d, radial_2d
 
 FULL_NX, FULL_NY, FULL_NZ = 512, 512, 105
 
@@ -51,6 +54,18 @@ def epi_sequence() -> Sequence:
 
 def full_phantom() -> Phantom:
     return ellipse_phantom(FULL_NX, FULL_NY, FULL_NZ, 8, seed=1002)
+
+
+def radial_sequence(n_spokes=64, oblique_deg=0.0) -> Sequence:
+    """Radial spoiled gradient echo on the full-size geometry: 3 ms sinc
+    30 deg pulses at 1 us, 256 samples per spoke at 4 us, TE 5 ms, TR 10 ms;
+    spokes off the x and y axes read on Gx and Gy together."""
+    return radial_2d(n_ro=256, n_spokes=n_spokes, rf_dur=3e-3, rf_dt=1e-6, dwell=4e-6,
+                     te=5e-3, tr=10e-3, oblique_deg=oblique_deg)
+
+
+def radial_27m() -> Tuple[Phantom, Sequence]:
+    return full_phantom(), radial_sequence()
 
 
 def fse_27m() -> Tuple[Phantom, Sequence]:

@@ -585,7 +585,7 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
         P.cell_w = ni == 8 ? 1 : 0;
         const int r = g->secondary;
         P.cell = allow_cell && ni != 0 && !P.direct && g->ax_ok && p >= G_X && p <= G_Z &&
-                 g->n_cell_thr[P.cell_w] > 0 && g->n_cells > 0;
+                 g->n_cell_thr[P.cell_w] > 0 && g->n_cell_thr[0] > 0 && g->n_cells > 0;
         P.r_axis = (r >= G_X && r <= G_Z) ? r - 1 : -1;
         P.free_bits = 7 & ~(1 << (p - 1)) & ~(P.r_axis >= 0 ? 1 << P.r_axis : 0);
         const int rbit = P.r_axis >= 0 ? 1 << P.r_axis : 0;
@@ -772,7 +772,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     const bool f64 = sizeof(R) == 8;
     using A = typename AdvOf<R>::T;
     GPlan<R> P;
-    plan_grouped<R>(c, s, g, P, ph->n_coils == 0);
+    plan_grouped<R>(c, s, g, P, true);
     R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(P.rows, 1) * 12 * sizeof(R));
     for (auto &t : P.tabs) {
         if constexpr (sizeof(R) == 4) {
@@ -784,7 +784,10 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         launch_precompute<R>(c, precomp_args<R>(s, g, t.first.first, t.first.second,
                                                  T_tab + t.second * 12));
     }
-    double *Ablk = (double *)scratch(c, 7, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double));
+    // block sums of one coil, or of up to four coils per pass in the cell form
+    const int coils_per_pass = P.cell && ph->n_coils > 0 ? 4 : 1;
+    double *Ablk = (double *)scratch(
+        c, 7, std::max<int64_t>(P.ablk_n, 1) * 2 * coils_per_pass * sizeof(double));
     MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double),
                                c->stream));
     const int64_t Kp = plane_stride(K);
@@ -832,7 +835,9 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                 launch_cell_rows(c, d_keys, nk, g, T_tab, d_P, fa.qtab,
                                  P.r_axis >= 0 ? fa.ax_sh[P.r_axis] : 0, C_tab);
             }
-            const int w = P.cell_w;
+            // per-thread work for the kernel's width: the coil kernels hold
+            // 4 isochromats per thread
+            const int w = ph->n_coils > 0 ? 0 : P.cell_w;
             ca.n_thr = g->n_cell_thr[w];
             ca.thr = g->cell_thr[w].as<int2>();
             ca.cell_gp = g->cell_gp.as<int32_t>();
@@ -866,25 +871,42 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         upload(c, dw, P.wins.data(), P.wins.size() * sizeof(GWin));
         upload(c, db, P.blk.data(), P.blk.size() * sizeof(int4));
     }
-    // one pass over the whole sequence per receive coil (Eq. 9 block sums per
-    // (group, coil)); the tables above serve every pass
-    const int n_pass = std::max(ph->n_coils, 1);
+    // Receive coils (Eq. 6 with P coils, Eq. 9 block sums per (group, coil)):
+    // the tables above serve every pass.  The cell form takes up to four coils
+    // per pass over the sequence (their state evolution is the same); the
+    // per-isochromat form one.
+    const int n_coils = ph->n_coils;
     const int64_t ns = s->n_samples;
-    float *coil_s = ph->n_coils > 0 ? (float *)scratch(c, 18, 2 * K * sizeof(float)) : nullptr;
-    for (int pass = 0; pass < n_pass; ++pass) {
-        double *sig = d_signal + 2 * ns * pass;
+    const int per_pass = coils_per_pass;
+    float *coil_s = n_coils > 0
+                        ? (float *)scratch(c, 18, (size_t)2 * per_pass * K * sizeof(float))
+                        : nullptr;
+    const int64_t ablk_sz = std::max<int64_t>(P.ablk_n, 1) * 2 * per_pass;
+    for (int c0 = 0; c0 < std::max(n_coils, 1);) {
+        const int rem = n_coils - c0;
+        const int pc = n_coils == 0 ? 0 : per_pass == 1 ? 1 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
         if (coil_s) {
-            // coil `pass` in layout order
-            const float *src = ph->coils.as<float>() + 2 * K * pass;
-            launch_gather_f32(c, K, g->perm.as<int32_t>(), src, coil_s);
-            launch_gather_f32(c, K, g->perm.as<int32_t>(), src + K, coil_s + K);
+            // coils c0 .. c0 + pc - 1 in layout order, [coil][re, im][K]
+            for (int j = 0; j < pc; ++j) {
+                const float *src = ph->coils.as<float>() + 2 * K * (c0 + j);
+                launch_gather_f32(c, K, g->perm.as<int32_t>(), src, coil_s + 2 * K * j);
+                launch_gather_f32(c, K, g->perm.as<int32_t>(), src + K, coil_s + 2 * K * j + K);
+            }
             fa.coil_re = st.coil_re = coil_s;
             fa.coil_im = st.coil_im = coil_s + K;
         }
-        if (pass > 0) {
-            MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, std::max<int64_t>(P.ablk_n, 1) * 2 * sizeof(double),
-                                       c->stream));
+        if (c0 > 0) {
+            MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, ablk_sz * sizeof(double), c->stream));
             if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
+        } else if (per_pass > 1) {
+            MRSIM_CUDA(cudaMemsetAsync(Ablk, 0, ablk_sz * sizeof(double), c->stream));
+        }
+        CellForm form = P.form;
+        if constexpr (sizeof(R) == 4) {
+            form.pc = pc;
+            ca.coil = coil_s;
+            ca.K = K;
+            ca.ablk_stride = std::max<int64_t>(P.ablk_n, 1);
         }
         bool first = true;
         for (const auto &sp : P.spans) {
@@ -896,7 +918,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                     ca.ev = d_cev + sp.b;
                     ca.n_ev = (int)(sp.e - sp.b);
                     ca.init_eq = fa.init_eq;
-                    launch_fused_cell(c, ca, P.form);
+                    launch_fused_cell(c, ca, form);
                 } else {
                     launch_fused<R>(c, fa, c->tune[MRSIM_TUNE_FUSED_NI]);
                 }
@@ -914,15 +936,26 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                 const void *segs =
                     f64 ? (const void *)(s->adc_d.as<ADCSegD>() + s->adc_off[sp.fallback])
                         : (const void *)(s->adc_f.as<ADCSegF>() + s->adc_off[sp.fallback]);
-                launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples,
-                                    &zero, sig + 2 * q.sample0,
-                                    c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+                // one launch per coil of this pass (the state is only read)
+                for (int j = 0; j < std::max(pc, 1); ++j) {
+                    if (coil_s) {
+                        st.coil_re = coil_s + 2 * K * j;
+                        st.coil_im = st.coil_re + K;
+                    }
+                    launch_plain_adc<R>(c, st, segs, (int)(q.seg_end - q.seg_begin), q.n_samples,
+                                        &zero, d_signal + 2 * (ns * (c0 + j) + q.sample0),
+                                        c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+                }
             }
         }
-        // every sample from the block sums (Eqs. 8, 10)
-        if (!P.blk.empty())
-            launch_group_signal<R>(c, dw, db, (int)P.blk.size(), f64 ? s->gs_d.p : s->gs_f.p,
-                                   sig_tables<R>(g), Ablk, sig);
+        // every sample from the block sums (Eqs. 8, 10), per coil of the pass
+        for (int j = 0; j < std::max(pc, 1); ++j) {
+            if (!P.blk.empty())
+                launch_group_signal<R>(c, dw, db, (int)P.blk.size(), f64 ? s->gs_d.p : s->gs_f.p,
+                                       sig_tables<R>(g), Ablk + 2 * std::max<int64_t>(P.ablk_n, 1) * j,
+                                       d_signal + 2 * ns * (c0 + j));
+        }
+        c0 += std::max(pc, 1);
     }
     sync(c);
 }

@@ -371,6 +371,14 @@ struct CellArgs {
     int r_sh;                 // bit position of the secondary axis' index, or -1
     const int32_t *gid[kNTypes];  // layout-order gids per gradient type (with-ADC
                                   // windows of the secondary or no-grads type)
+    // receive coils of this pass (Eq. 6 with P coils): sensitivities S of
+    // `n_coil` coils in layout order, [coil][re, im][K]; block sums of coil j
+    // at Ablk + 2 * ablk_stride * j.  n_coil = 0: one coil with S = 1.
+    const float *coil;
+    int64_t K;
+    int64_t ablk_stride;
+    // phasor flags of the form (kernels compiled for coils read them here)
+    int rfq, adq, rb;
 };
 // Which per-isochromat and per-thread phasors a cell-form launch applies
 // (fixed for the whole span, so the kernel is specialised on them).
@@ -380,6 +388,7 @@ struct CellForm {
     bool rfq;   // RF / END events rotate by the free-axis phasor
     bool adq;   // with-ADC events rotate by the free-axis phasor
     bool rb;    // with-ADC events rotate by the secondary-axis phasor
+    int pc = 0; // receive coils of this pass (0: none; 1, 2 or 4)
 };
 // One distinct RF / END advance of a cell run: C rows of every cell for
 // transition table rows [trow, trow + G_t) of gradient type gtype (trow < 0:

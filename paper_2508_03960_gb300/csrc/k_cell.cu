@@ -37,20 +37,25 @@ namespace mrsim {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBatch = 16;            // with-ADC windows per shared-memory flush
+constexpr int kBatch = 16;            // with-ADC windows x coils per shared-memory flush
 constexpr int kAccFloats = 2048;      // block-sum staging per CTA (8 KB)
 constexpr int kEvChunk = 64;          // events staged in shared memory at a time
 constexpr int kPad = 0x7fffffff;      // key of a thread without isochromats
 
+// Shared memory of a CTA for PC receive coils per pass (PC = 0: one coil,
+// S = 1): kBatch / max(PC, 1) windows are staged per flush.
+template <int PC>
 struct CellSmem {
-    __align__(16) float acc[kAccFloats];           // staged block sums [batch][slot][re, im]
-    __align__(16) CellEv sev[kEvChunk];            // staged events
-    // per-thread partials of warps whose threads share one group, [window][thread]
-    // (row padded by one entry: conflict-free column reads)
-    __align__(16) float tpart[kBatch][kThreads + 1][2];
-    float wpart[kBatch][kThreads / 32][2];         // their per-warp sums
-    int batch_win[kBatch];
-    int wslot[kThreads / 32];                      // that group's slot, or -1
+    static constexpr int NC = PC > 0 ? PC : 1;  // coils per pass
+    static constexpr int NB = kBatch / NC;      // windows per flush
+    __align__(16) float acc[kAccFloats];        // staged block sums [batch][slot][coil][re, im]
+    __align__(16) CellEv sev[kEvChunk];         // staged events
+    // per-thread partials of warps whose threads share one group,
+    // [window][thread][coil, re/im] (row padded: conflict-free column reads)
+    __align__(16) float tpart[NB][kThreads + 1][2 * NC];
+    float wpart[NB][kThreads / 32][2 * NC];     // their per-warp sums
+    int batch_win[NB];
+    int wslot[kThreads / 32];                   // that group's slot, or -1
 };
 
 // exp(-i 2 pi sum_f r_f k_f) over the free axes from the event's tables
@@ -68,16 +73,25 @@ __device__ __forceinline__ void free_phasor(const float2 *qtab, const int (&qf)[
     }
 }
 
-template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
-__global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(CellArgs a) {
-    __shared__ CellSmem sm;
+// RFQ / ADQ / RB: 0 or 1 fixes the phasor flag at compile time, 2 reads it from
+// the arguments.  PC: receive coils handled in this pass (0: S = 1).
+template <int NI, int NF, int RFQ, int ADQ, int RB, int PC>
+__global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4 ? 4 : 2))
+    k_fused_cell(CellArgs a) {
+    using Smem = CellSmem<PC>;
+    constexpr int NC = Smem::NC, NB = Smem::NB;
+    __shared__ Smem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * kThreads;
     const int64_t t = t0 + tid;
     const int64_t t_end = min(t0 + kThreads, a.n_thr);  // threads with work in this CTA
     const float2 *qtab = a.qtab;
+    const bool rfq = RFQ == 2 ? a.rfq != 0 : RFQ == 1;
+    const bool adq = ADQ == 2 ? a.adq != 0 : ADQ == 1;
+    const bool rb = RB == 2 ? a.rb != 0 : RB == 1;
 
     float mx[NI], my[NI], mz[NI], M0[NI];
+    float sre[NC][NI], sim[NC][NI];  // receive sensitivities (PC > 0)
     int f0[NI], f1[NI];  // free-axis table indices of each isochromat
     // isochromat i of this thread is layout position start + i * stride
     int key = kPad, cell = 0, start = 0, stride = 0, n = 0, ridx = 0;
@@ -85,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
         const int2 d = a.thr[t];
         start = d.x;
         cell = d.y >> 4;
-        n = d.y & 15;
+        n = min(d.y & 15, NI);  // descriptors are built for this width
         key = a.cell_gp[cell];
         stride = (a.cell_count[cell] + NI - 1) / NI;
     }
@@ -105,20 +119,31 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
                 my[i] = a.My[k];
                 mz[i] = a.Mz[k];
             }
+            if constexpr (PC > 0) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    sre[j][i] = a.coil[(2 * j) * a.K + k];
+                    sim[j][i] = a.coil[(2 * j + 1) * a.K + k];
+                }
+            }
         } else {
             M0[i] = mx[i] = my[i] = mz[i] = 0.0f;
+            if constexpr (PC > 0) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) sre[j][i] = sim[j][i] = 0.0f;
+            }
         }
         f0[i] = (ai >> a.f_sh[0]) & 0xffff;
         f1[i] = NF == 2 ? (ai >> a.f_sh[1]) & 0xffff : 0;
-        if (i == 0 && RB) ridx = (ai >> a.r_sh) & 0xffff;
+        if (i == 0 && RB != 0) ridx = (ai >> a.r_sh) & 0xffff;
     }
     // primary groups of this CTA: keys rise along the threads and every group
     // between the first and the last one has isochromats here
     const int32_t g_first = a.cell_gp[a.thr[t0].y >> 4];
     const int32_t g_last = a.cell_gp[a.thr[t_end - 1].y >> 4];
     const int S = (int)(g_last - g_first + 1);  // at most kThreads
-    const int B = max(1, min(kBatch, kAccFloats / (2 * S)));
-    for (int i = tid; i < B * S * 2; i += kThreads) sm.acc[i] = 0.0f;
+    const int B = max(1, min(NB, kAccFloats / (2 * NC * S)));
+    for (int i = tid; i < B * S * 2 * NC; i += kThreads) sm.acc[i] = 0.0f;
     // a warp whose threads all share one group stages per-thread partials
     const int32_t w0 = __shfl_sync(0xffffffffu, key, 0);
     const bool warp_uni = __all_sync(0xffffffffu, key == w0 || key == kPad) && w0 != kPad;
@@ -131,43 +156,48 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
     auto flush = [&]() {
         if (warp_uni) {
             // column sums of this warp's staged partials: lane (h, b) adds
-            // kBatch threads of part h for window b, then the parts combine
+            // 32 / H threads of part h for window b (H = 32 / NB), then the
+            // parts combine
             __syncwarp();
-            const int b = lane % kBatch, h = lane / kBatch;
-            float sr = 0.0f, si = 0.0f;
-            if (b < nb) {
-                const float(*col)[2] = &sm.tpart[b][warp * 32 + h * kBatch];
+            constexpr int H = 32 / NB, J = 32 / H;
+            const int b = lane % NB, h = lane / NB;
+            float sr[2 * NC];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    sr += col[j][0];
-                    si += col[j][1];
+            for (int v = 0; v < 2 * NC; ++v) sr[v] = 0.0f;
+            if (b < nb) {
+                const float(*col)[2 * NC] = &sm.tpart[b][warp * 32 + h * J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+#pragma unroll
+                    for (int v = 0; v < 2 * NC; ++v) sr[v] += col[j][v];
                 }
             }
 #pragma unroll
-            for (int o = 16; o >= kBatch; o >>= 1) {
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                si += __shfl_xor_sync(0xffffffffu, si, o);
+            for (int o = 16; o >= NB; o >>= 1) {
+#pragma unroll
+                for (int v = 0; v < 2 * NC; ++v) sr[v] += __shfl_xor_sync(0xffffffffu, sr[v], o);
             }
             if (h == 0 && b < nb) {
-                sm.wpart[b][warp][0] = sr;
-                sm.wpart[b][warp][1] = si;
+#pragma unroll
+                for (int v = 0; v < 2 * NC; ++v) sm.wpart[b][warp][v] = sr[v];
             }
         }
         __syncthreads();
-        for (int q = tid; q < nb * S; q += kThreads) {
-            const int b = q / S, slot = q - b * S;
+        for (int q = tid; q < nb * S * NC; q += kThreads) {
+            const int b = q / (S * NC), r = q - b * S * NC, slot = r / NC, j = r - slot * NC;
             float sr = sm.acc[2 * q], si = sm.acc[2 * q + 1];
             if (any_uni) {
 #pragma unroll
                 for (int w = 0; w < kThreads / 32; ++w) {
                     if (sm.wslot[w] == slot) {
-                        sr += sm.wpart[b][w][0];
-                        si += sm.wpart[b][w][1];
+                        sr += sm.wpart[b][w][2 * j];
+                        si += sm.wpart[b][w][2 * j + 1];
                     }
                 }
             }
             if (sr != 0.0f || si != 0.0f) {
-                const int64_t o = 2 * ((int64_t)sm.batch_win[b] + g_first + slot);
+                const int64_t o =
+                    2 * (a.ablk_stride * j + (int64_t)sm.batch_win[b] + g_first + slot);
                 if (slot != 0 && slot != S - 1) {
                     // a group strictly inside the CTA has no other contributor
                     *reinterpret_cast<double2 *>(&a.Ablk[o]) = make_double2(sr, si);
@@ -185,28 +215,37 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
         nb = 0;
     };
 
-    auto stage = [&](int win, float sr, float si) {
+    auto stage = [&](int win, float (&sr)[NC], float (&si)[NC]) {
         if (warp_uni) {
-            sm.tpart[nb][tid][0] = sr;
-            sm.tpart[nb][tid][1] = si;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                sm.tpart[nb][tid][2 * j] = sr[j];
+                sm.tpart[nb][tid][2 * j + 1] = si[j];
+            }
         } else {
             // keys rise along the lanes: a segmented inclusive scan leaves each
             // run's sum in the run's last lane
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const float orr = __shfl_up_sync(0xffffffffu, sr, d);
-                const float oii = __shfl_up_sync(0xffffffffu, si, d);
                 const int32_t ok = __shfl_up_sync(0xffffffffu, key, d);
-                if (lane >= d && ok == key) {
-                    sr += orr;
-                    si += oii;
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    const float orr = __shfl_up_sync(0xffffffffu, sr[j], d);
+                    const float oii = __shfl_up_sync(0xffffffffu, si[j], d);
+                    if (lane >= d && ok == key) {
+                        sr[j] += orr;
+                        si[j] += oii;
+                    }
                 }
             }
             const int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
             if ((lane == 31 || nk != key) && key != kPad) {
-                float *accb = sm.acc + 2 * (nb * S + (key - g_first));
-                atomicAdd(accb, sr);
-                atomicAdd(accb + 1, si);
+                float *accb = sm.acc + 2 * NC * (nb * S + (key - g_first));
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    atomicAdd(accb + 2 * j, sr[j]);
+                    atomicAdd(accb + 2 * j + 1, si[j]);
+                }
             }
         }
         if (tid == 0) sm.batch_win[nb] = win;
@@ -235,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
                     reinterpret_cast<const float4 *>(a.C_tab + ((int64_t)ev0.y + cell) * 12);
                 const float4 r0 = __ldg(cr), r1 = __ldg(cr + 1), r2 = __ldg(cr + 2);
                 int qf[2] = {0, 0};
-                if constexpr (RFQ) {
+                if (rfq) {
                     const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
                     qf[0] = ev1.x;
                     qf[1] = ev1.y;
@@ -243,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
 #pragma unroll
                 for (int i = 0; i < NI; ++i) {
                     float x = mx[i], y = my[i];
-                    if constexpr (RFQ) {
+                    if (rfq) {
                         float c, s;
                         free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
                         const float nx = c * x + s * y;  // (c - i s) (x + i y)
@@ -267,44 +306,62 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
                     }
                 }
             } else {
-                // with-ADC window: block-sum term P_g Q_r sum_i Q_free M_xy (Eq. 9);
-                // the group factor is issued first, it multiplies the sums
+                // with-ADC window: block-sum term P_g Q_r sum_i S_i Q_free M_xy
+                // (Eqs. 6, 9); the group factor is issued first, it multiplies
+                // the sums
                 const float4 P = __ldg(Pt + ev0.y + pkey);
                 const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
-                float sr = 0.0f, si = 0.0f;
+                float sr[NC], si[NC];
+#pragma unroll
+                for (int j = 0; j < NC; ++j) sr[j] = si[j] = 0.0f;
                 const int qf[2] = {ev1.x, ev1.y};
 #pragma unroll
                 for (int i = 0; i < NI; ++i) {
-                    if constexpr (ADQ) {
+                    float vr = mx[i], vi = my[i];
+                    if (adq) {
                         float c, s;
                         free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
-                        sr += c * mx[i] + s * my[i];
-                        si += c * my[i] - s * mx[i];
+                        vr = c * mx[i] + s * my[i];
+                        vi = c * my[i] - s * mx[i];
+                    }
+                    if constexpr (PC > 0) {
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) {
+                            sr[j] += sre[j][i] * vr - sim[j][i] * vi;
+                            si[j] += sre[j][i] * vi + sim[j][i] * vr;
+                        }
                     } else {
-                        sr += mx[i];
-                        si += my[i];
+                        sr[0] += vr;
+                        si[0] += vi;
                     }
                 }
-                if constexpr (RB) {
-                    // the cell's secondary-axis phasor, once per thread
+                // the factor shared by the thread's isochromats: the group's P
+                // times the cell's secondary-axis phasor
+                float fr = P.x, fi = P.y;
+                if (rb) {
                     const float2 q = __ldg(qtab + ev1.z + ridx);
-                    const float nr = q.x * sr + q.y * si;
-                    si = q.x * si - q.y * sr;
-                    sr = nr;
+                    const float tr = fr * q.x + fi * q.y;  // P exp(-i psi)
+                    fi = fi * q.x - fr * q.y;
+                    fr = tr;
                 }
-                {
-                    const float nr = P.x * sr - P.y * si;
-                    si = P.x * si + P.y * sr;
-                    sr = nr;
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    const float nr = fr * sr[j] - fi * si[j];
+                    si[j] = fr * si[j] + fi * sr[j];
+                    sr[j] = nr;
                 }
                 if (kind == CE_ADC) {
                     stage(ev0.z, sr, si);
                 } else if (n > 0) {
                     // a window of the secondary or no-grads type: its group is
                     // constant in the cell, the thread adds its term directly
-                    const int64_t o = 2 * ((int64_t)ev0.z + a.gid[ev0.w][start]);
-                    atomicAdd(&a.Ablk[o], (double)sr);
-                    atomicAdd(&a.Ablk[o + 1], (double)si);
+                    const int64_t g = a.gid[ev0.w][start];
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) {
+                        const int64_t o = 2 * (a.ablk_stride * j + (int64_t)ev0.z + g);
+                        atomicAdd(&a.Ablk[o], (double)sr[j]);
+                        atomicAdd(&a.Ablk[o + 1], (double)si[j]);
+                    }
                 }
             }
         }
@@ -315,7 +372,13 @@ __global__ void __launch_bounds__(kThreads, (NI == 4 ? 4 : 2)) k_fused_cell(Cell
 template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
 void launch_cell_v(mrsim_ctx *c, const CellArgs &a) {
     const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
-    k_fused_cell<NI, NF, RFQ, ADQ, RB><<<nb, kThreads, 0, c->stream>>>(a);
+    k_fused_cell<NI, NF, RFQ, ADQ, RB, 0><<<nb, kThreads, 0, c->stream>>>(a);
+}
+// receive coils: 4 isochromats per thread, phasor flags read at run time
+template <int NF, int PC>
+void launch_cell_coil(mrsim_ctx *c, const CellArgs &a) {
+    const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
+    k_fused_cell<4, NF, 2, 2, 2, PC><<<nb, kThreads, 0, c->stream>>>(a);
 }
 template <int NI, int NF, bool RFQ, bool ADQ>
 void launch_cell_rb(mrsim_ctx *c, const CellArgs &a, bool rb) {
@@ -378,6 +441,23 @@ __global__ void k_cell_rows(const CellKey *keys, int n_keys, int64_t nc, const i
 
 void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
     if (a.n_thr <= 0) return;
+    if (f.pc > 0) {
+        KScope ks(c, "fused_cell_coils_f32");
+        CellArgs b = a;
+        b.rfq = f.rfq;
+        b.adq = f.adq;
+        b.rb = f.rb;
+        if (f.nf == 2) {
+            if (f.pc == 4) launch_cell_coil<2, 4>(c, b);
+            else if (f.pc == 2) launch_cell_coil<2, 2>(c, b);
+            else launch_cell_coil<2, 1>(c, b);
+        } else {
+            if (f.pc == 4) launch_cell_coil<1, 4>(c, b);
+            else if (f.pc == 2) launch_cell_coil<1, 2>(c, b);
+            else launch_cell_coil<1, 1>(c, b);
+        }
+        return;
+    }
     KScope ks(c, "fused_cell_f32");
     if (f.ni == 8) {
         if (f.nf == 2) launch_cell_q<8, 2>(c, a, f);

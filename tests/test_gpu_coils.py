@@ -145,3 +145,27 @@ def test_coil_errors(mrsim, ctx):
     mrsim.mrsim_run(ctx.h, hp, hs, hg, mrsim.GROUPED, mrsim.FP32, sig)
     ref, _ = oracle.simulate(ph, seq, want_M=False)
     assert oracle.rel_l2(sig.view(np.complex128), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("n_coils", [1, 2, 3, 5, 8])
+def test_coils_cell_form_takes_several_coils_per_pass(mrsim, ctx, n_coils):
+    """The cell form of the fused kernel takes up to four coils per pass over
+    the sequence (passes of 4, 2 and 1 coils); every coil's signal matches the
+    oracle with the cell form on and off, and the coil kernel ran."""
+    ph = with_coils(configs.small_phantom(24, 24, 4), n_coils, seed=50 + n_coils)
+    seq = fse_2d(n_ro=32, n_pe=32, etl=4, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=1.0, n_shots=2)
+    ref, _ = oracle.simulate(ph, seq, memo=True, adc_recurrence=True, want_M=False)
+    for cell in (8, 0):
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, cell)
+        mrsim.mrsim_profile_reset(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, True)
+        try:
+            sig, _ = run(mrsim, ctx, ph, seq, mrsim.GROUPED, 0)
+            prof = mrsim.mrsim_profile_get(ctx.h)
+        finally:
+            mrsim.mrsim_profile_enable(ctx.h, False)
+            mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 8)
+        check_coils(sig, ref, 0)
+        ran = {k for k, v in prof.items() if k.startswith("fused") and v[0] > 0}
+        assert ran == ({"fused_cell_coils_f32"} if cell else {"fused_grouped_f32"}), ran

@@ -154,3 +154,15 @@ def test_two_axis_windows_and_pulses(mrsim, ctx, name, precision):
         sig, M, info = run(mrsim, ctx, ph, seq, precision, cell_ni=cell)
         assert two_axis_types(info)
         check(sig, M, ref, Mref, precision, float(np.max(ph.M0)))
+
+
+def test_radial_benchmark_sequence_on_a_reduced_phantom(mrsim, ctx):
+    """The benchmark's radial sequence itself (3 ms pulses at 1 us, 64 spokes
+    of 256 samples) on a 64 x 64 x 4 phantom of the same construction."""
+    from mrsim_inputs import configs
+    seq = configs.radial_sequence()
+    ph = configs.small_phantom(64, 64, 4)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    sig, M, info = run(mrsim, ctx, ph, seq, 0)
+    assert mrsim.G_XY in two_axis_types(info)
+    check(sig, M, ref, Mref, 0, float(np.max(ph.M0)))
