@@ -17,7 +17,7 @@
 // the tie rules is "the smallest key id".
 //
 // One split of cluster c (the one with the largest SSE, ties to the smaller
-// id; SSEs are compared as exact rationals on the host):
+// id; SSEs are compared as exact rationals, 128-bit integers, on the device):
 //   a = member farthest from the mean, b = member farthest from a;
 //   2-means from centres (a, b): side 1 iff strictly nearer centre 1; centres
 //   = side means; until the centres repeat, max_iter passes, or a side would
@@ -42,12 +42,19 @@ struct ClStats {
     unsigned long long sq[3][2];  // sum w x_i^2 as (low, high) words
 };
 
-// Device work area of the split in progress.
+// Device work area of the split in progress.  The split is decided on the
+// device: k_cl_choose picks the cluster, k_cl_update advances the 2-means
+// passes and decides when they stop, k_cl_commit records the two sides.
 struct ClWork {
     double cen[6];                // centres of side 0 and side 1, feature units
     unsigned long long dmax[2];   // farthest-member searches: largest distance
     int32_t umin[2];              // ... and the smallest key id at it
-    ClStats st[2];
+    ClStats st[2];                // sums of the pass in progress
+    double kept_cen[6];           // centres of the last pass with both sides filled
+    ClStats kept[2];              // ... and its sums
+    int32_t cid, nid;             // cluster being split (-1: none left), id of side 1
+    int32_t done, have, passes;   // 2-means stopped; a pass was kept; passes run
+    int32_t n_cur;                // clusters made so far
 };
 
 // Per-thread partial sums (plain data: also held in shared memory).
@@ -143,12 +150,174 @@ __global__ void k_cl_quant(int64_t K, const float *T1, const float *T2, const fl
     }
 }
 
-// Sums of each side of the split of cluster c under the centres in w->cen.
-__global__ void __launch_bounds__(kClThreads) k_cl_assign(int64_t U, const int32_t *lab, int32_t c,
-                                                          const int32_t *tx, const int32_t *wt,
+// rint(v * S) for a float v and an integer scale S < 2^24 in integer
+// arithmetic: v = m 2^e with an integer m < 2^24, so v S = (m S) 2^e exactly
+// (m S < 2^48; the FP64 product of the other path is exact as well) and
+// rint is a right shift rounding half to even.  ok: v finite and the result
+// within 2^62 (the caller checks the feature range).
+__device__ __forceinline__ long long quant_int(float v, long long S, bool &ok) {
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xff);
+    ok = ex != 0xff;
+    if (!ok) return 0;
+    uint64_t m = b & 0x7fffffu;
+    int e;
+    if (ex == 0) {
+        e = -149;  // subnormal: m 2^-149
+    } else {
+        m |= 0x800000u;
+        e = ex - 150;  // m 2^(ex - 127 - 23)
+    }
+    const uint64_t p = m * (uint64_t)S;
+    uint64_t q;
+    if (p == 0) {
+        q = 0;
+    } else if (e >= 0) {
+        if (e > 14) {  // beyond 2^62 (p >= 2^0): out of every feature range
+            ok = false;
+            return 0;
+        }
+        q = p << e;
+    } else if (e <= -64) {
+        q = 0;  // below one half
+    } else {
+        const int k = -e;
+        const uint64_t fl = p >> k, rem = p & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+        q = fl + ((rem > half || (rem == half && (fl & 1ull))) ? 1ull : 0ull);
+    }
+    return (b >> 31) ? -(long long)q : (long long)q;
+}
+
+__global__ void k_cl_quant_int(int64_t K, const float *T1, const float *T2, const float *dB0,
+                               long long s0, long long s1, long long s2, int32_t *x, int *err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float v[3] = {T1[k], T2[k], dB0[k]};
+        const long long s[3] = {s0, s1, s2};
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            bool fin;
+            const long long q = quant_int(v[i], s[i], fin);
+            const bool ok = fin && (q <= (long long)kMaxFeature && q >= -(long long)kMaxFeature) &&
+                            (i == 2 || q >= 1);
+            bad |= !ok;
+            x[i * K + k] = ok ? (int32_t)q : 0;
+        }
+        if (bad) atomicOr(err, 1);
+    }
+}
+
+using u128 = unsigned __int128;
+
+// n * SSE of a cluster's exact sums: sum_i (n sum w x_i^2 - (sum w x_i)^2)
+__device__ __forceinline__ u128 cl_nsse(const ClStats &s) {
+    u128 N = 0;
+    for (int i = 0; i < 3; ++i) {
+        const u128 sq = ((u128)s.sq[i][1] << 64) | s.sq[i][0];
+        const long long x = (long long)s.sx[i];
+        const u128 a = x < 0 ? (u128)(-x) : (u128)x;
+        N += (u128)s.n * sq - a * a;
+    }
+    return N;
+}
+
+// One cluster of the device table: its exact sums and n * SSE (two words).
+struct ClEntry {
+    ClStats s;
+    unsigned long long N[2];  // low, high
+};
+
+// Last-block completion: every block adds one to the counter after its
+// results are visible (fence first); the block that brings it to gridDim.x
+// finishes the step alone and resets the counter for the next launch.  No
+// block waits for another.
+__device__ __forceinline__ bool cl_last_block(unsigned int *counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(counter, 1u);
+        last = prev == gridDim.x - 1;
+        if (last) *counter = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// the next split, chosen by one block: the cluster with the largest SSE,
+// compared as exact rationals N_a / n_a > N_b / n_b, ties to the smaller id
+// (clusters of one distinct value have N = 0 and are never split); its mean
+// seeds the farthest-member search.  cid = -1 at n_clusters or when nothing
+// can be split.
+__device__ void cl_choose_block(const ClEntry *tab, int n_clusters, ClWork *w) {
+    __shared__ int s_best[kClThreads];
+    const int n = w->n_cur;
+    const int t = threadIdx.x;
+    auto better = [&](int a, int b) {  // a strictly better than b
+        if (a < 0) return false;
+        if (b < 0) return true;
+        const u128 Na = ((u128)tab[a].N[1] << 64) | tab[a].N[0];
+        const u128 Nb = ((u128)tab[b].N[1] << 64) | tab[b].N[0];
+        const u128 l = Na * (u128)tab[b].s.n, r = Nb * (u128)tab[a].s.n;
+        return l > r || (l == r && a < b);
+    };
+    int best = -1;
+    for (int i = t; n < n_clusters && i < n; i += blockDim.x) {
+        if (tab[i].N[0] == 0 && tab[i].N[1] == 0) continue;
+        if (better(i, best)) best = i;
+    }
+    s_best[t] = best;
+    __syncthreads();
+    for (int off = kClThreads / 2; off > 0; off >>= 1) {
+        if (t < off && better(s_best[t + off], s_best[t])) s_best[t] = s_best[t + off];
+        __syncthreads();
+    }
+    if (t == 0) {
+        best = s_best[0];
+        w->cid = best;
+        w->nid = n;
+        w->done = 0;
+        w->have = 0;
+        w->passes = 0;
+        for (int s = 0; s < 2; ++s) w->st[s] = ClStats{};
+        if (best >= 0)
+            for (int i = 0; i < 3; ++i) {
+                w->cen[i] = (double)(long long)tab[best].s.sx[i] / (double)tab[best].s.n;
+                w->cen[3 + i] = 0.0;
+            }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kClThreads) k_cl_choose(const ClEntry *tab, int n_clusters,
                                                           ClWork *w) {
+    cl_choose_block(tab, n_clusters, w);
+}
+
+// the cluster's entry (one thread): exact sums and n * SSE
+__device__ __forceinline__ void cl_set_entry(ClEntry &e, const ClStats &s) {
+    e.s = s;
+    const u128 N = cl_nsse(s);
+    e.N[0] = (unsigned long long)N;
+    e.N[1] = (unsigned long long)(N >> 64);
+}
+
+// One 2-means pass over the keys of the split cluster: sums of each side under
+// the centres in w->cen; the last block then advances the passes (an empty side
+// ends them, the previous pass standing; otherwise the pass is kept, and they
+// end when the side means repeat the centres or after max_iter passes).
+// first_entry: the pass that sums cluster 0 (every key) into table entry 0.
+__global__ void __launch_bounds__(kClThreads) k_cl_assign(int64_t U, const int32_t *lab,
+                                                          const int32_t *tx, const int32_t *wt,
+                                                          ClWork *w, int max_iter,
+                                                          unsigned int *counter, ClEntry *tab,
+                                                          int first_entry) {
     __shared__ double cen[6];
     __shared__ ClAcc part[kClThreads / 32][2];
+    const int32_t c = w->cid;
+    if (c < 0 || w->done) return;  // nothing left to split, or the passes stopped
     if (threadIdx.x < 6) cen[threadIdx.x] = w->cen[threadIdx.x];
     __syncthreads();
     ClAcc a0, a1;
@@ -179,32 +348,31 @@ __global__ void __launch_bounds__(kClThreads) k_cl_assign(int64_t U, const int32
         for (int i = 1; i < kClThreads / 32; ++i) t.merge(part[i][threadIdx.x]);
         t.flush(&w->st[threadIdx.x]);
     }
-}
-
-// Largest distance of a member of cluster c to the centre in w->cen[0..2].
-__global__ void k_cl_far_mean(int64_t U, const int32_t *lab, int32_t c, const int32_t *tx,
-                              ClWork *w) {
-    unsigned long long best = 0;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        const double d = cl_dist(tx[u], tx[U + u], tx[2 * U + u], w->cen);
-        best = max(best, (unsigned long long)__double_as_longlong(d));  // d >= 0
+    if (!cl_last_block(counter) || threadIdx.x != 0) return;
+    if (first_entry) {
+        cl_set_entry(tab[0], w->st[0]);
+        w->n_cur = 1;
+        return;
     }
-    for (int off = 16; off > 0; off >>= 1)
-        best = max(best, __shfl_down_sync(0xffffffffu, best, off));
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(&w->dmax[0], best);
-}
-
-__global__ void k_cl_pick_mean(int64_t U, const int32_t *lab, int32_t c, const int32_t *tx,
-                               ClWork *w) {
-    const unsigned long long dm = w->dmax[0];
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        const double d = cl_dist(tx[u], tx[U + u], tx[2 * U + u], w->cen);
-        if ((unsigned long long)__double_as_longlong(d) == dm) atomicMin(&w->umin[0], (int32_t)u);
+    ++w->passes;
+    if (w->st[0].n == 0 || w->st[1].n == 0) {
+        w->done = 1;
+        return;
     }
+    for (int i = 0; i < 6; ++i) w->kept_cen[i] = w->cen[i];
+    w->kept[0] = w->st[0];
+    w->kept[1] = w->st[1];
+    w->have = 1;
+    double m[6];
+    bool same = true;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 3; ++i) {
+            m[3 * s + i] = (double)(long long)w->st[s].sx[i] / (double)w->st[s].n;
+            same &= m[3 * s + i] == w->cen[3 * s + i];
+        }
+    for (int i = 0; i < 6; ++i) w->cen[i] = m[i];
+    for (int s = 0; s < 2; ++s) w->st[s] = ClStats{};
+    if (same || w->passes >= max_iter) w->done = 1;
 }
 
 // exact squared distance of the features of key u to those of key a
@@ -219,54 +387,115 @@ __device__ __forceinline__ long long cl_dist_int(const int32_t *tx, int64_t U, i
     return d;
 }
 
-// Largest distance of a member of cluster c to member w->umin[0].
-__global__ void k_cl_far_point(int64_t U, const int32_t *lab, int32_t c, const int32_t *tx,
-                               ClWork *w) {
-    const int32_t a = w->umin[0];
-    unsigned long long best = 0;
+// (distance, key) pairs: larger distance first, then the smaller key id
+__device__ __forceinline__ bool cl_far_better(unsigned long long d, int32_t u,
+                                              unsigned long long bd, int32_t bu) {
+    return d > bd || (d == bd && u < bu);
+}
+
+// Farthest member of the split cluster (ties to the smallest key id) from
+// its mean (stage 0, FP64 distances; distances are >= 0, so their bit
+// patterns order like the values) or from the member found before (stage 1,
+// exact integer distances).  Per-block results go to far_d / far_u; the last
+// block combines them, and after stage 1 seeds the first 2-means pass with
+// the two members.
+__global__ void __launch_bounds__(kClThreads) k_cl_far(int64_t U, const int32_t *lab,
+                                                       const int32_t *tx, ClWork *w, int stage,
+                                                       unsigned long long *far_d,
+                                                       int32_t *far_u, unsigned int *counter) {
+    __shared__ unsigned long long sd[kClThreads];
+    __shared__ int32_t su[kClThreads];
+    const int32_t c = w->cid;
+    if (c < 0) return;
+    const int32_t a = stage ? w->umin[0] : 0;
+    const double cen[3] = {w->cen[0], w->cen[1], w->cen[2]};
+    unsigned long long bd = 0;
+    int32_t bu = 0x7fffffff;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
          u += (int64_t)gridDim.x * blockDim.x) {
         if (lab[u] != c) continue;
-        best = max(best, (unsigned long long)cl_dist_int(tx, U, u, a));
+        const unsigned long long d =
+            stage ? (unsigned long long)cl_dist_int(tx, U, u, a)
+                  : (unsigned long long)__double_as_longlong(
+                        cl_dist(tx[u], tx[U + u], tx[2 * U + u], cen));
+        if (cl_far_better(d, (int32_t)u, bd, bu)) {
+            bd = d;
+            bu = (int32_t)u;
+        }
     }
-    for (int off = 16; off > 0; off >>= 1)
-        best = max(best, __shfl_down_sync(0xffffffffu, best, off));
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(&w->dmax[1], best);
+    const int t = threadIdx.x;
+    sd[t] = bd;
+    su[t] = bu;
+    __syncthreads();
+    for (int off = kClThreads / 2; off > 0; off >>= 1) {
+        if (t < off && cl_far_better(sd[t + off], su[t + off], sd[t], su[t])) {
+            sd[t] = sd[t + off];
+            su[t] = su[t + off];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        far_d[blockIdx.x] = sd[0];
+        far_u[blockIdx.x] = su[0];
+    }
+    if (!cl_last_block(counter)) return;
+    bd = 0;
+    bu = 0x7fffffff;
+    for (int b = t; b < (int)gridDim.x; b += blockDim.x) {
+        const unsigned long long d = far_d[b];
+        const int32_t u = far_u[b];
+        if (cl_far_better(d, u, bd, bu)) {
+            bd = d;
+            bu = u;
+        }
+    }
+    sd[t] = bd;
+    su[t] = bu;
+    __syncthreads();
+    for (int off = kClThreads / 2; off > 0; off >>= 1) {
+        if (t < off && cl_far_better(sd[t + off], su[t + off], sd[t], su[t])) {
+            sd[t] = sd[t + off];
+            su[t] = su[t + off];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        w->umin[stage] = su[0];
+        if (stage == 1) {  // centres of the first 2-means pass
+            const int32_t m0 = w->umin[0], m1 = su[0];
+            for (int i = 0; i < 3; ++i) {
+                w->cen[i] = (double)tx[i * U + m0];
+                w->cen[3 + i] = (double)tx[i * U + m1];
+            }
+        }
+    }
 }
 
-__global__ void k_cl_pick_point(int64_t U, const int32_t *lab, int32_t c, const int32_t *tx,
-                                ClWork *w) {
-    const int32_t a = w->umin[0];
-    const unsigned long long dm = w->dmax[1];
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        if ((unsigned long long)cl_dist_int(tx, U, u, a) == dm)
-            atomicMin(&w->umin[1], (int32_t)u);
-    }
-}
-
-// centres of the first 2-means pass: the two members found above
-__global__ void k_cl_seed(int64_t U, const int32_t *tx, ClWork *w) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int32_t a = w->umin[0], b = w->umin[1];
-    for (int i = 0; i < 3; ++i) {
-        w->cen[i] = (double)tx[i * U + a];
-        w->cen[3 + i] = (double)tx[i * U + b];
-    }
-}
-
-// members of cluster c on side 1 under w->cen move to cluster id_new
-__global__ void k_cl_label(int64_t U, int32_t *lab, int32_t c, int32_t id_new, const int32_t *tx,
-                           const ClWork *w) {
+// Members of the split cluster on side 1 under the kept centres move to id
+// nid; the last block records both sides in the table and chooses the next
+// split.
+__global__ void __launch_bounds__(kClThreads) k_cl_label(int64_t U, int32_t *lab,
+                                                         const int32_t *tx, ClWork *w,
+                                                         ClEntry *tab, int n_clusters,
+                                                         unsigned int *counter) {
     __shared__ double cen[6];
-    if (threadIdx.x < 6) cen[threadIdx.x] = w->cen[threadIdx.x];
+    const int32_t c = w->cid, id_new = w->nid;
+    if (c < 0 || !w->have) return;
+    if (threadIdx.x < 6) cen[threadIdx.x] = w->kept_cen[threadIdx.x];
     __syncthreads();
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
          u += (int64_t)gridDim.x * blockDim.x) {
         if (lab[u] != c) continue;
         if (cl_side(tx[u], tx[U + u], tx[2 * U + u], cen)) lab[u] = id_new;
     }
+    if (!cl_last_block(counter)) return;
+    if (threadIdx.x == 0) {
+        cl_set_entry(tab[c], w->kept[0]);
+        cl_set_entry(tab[id_new], w->kept[1]);
+        w->n_cur = id_new + 1;
+    }
+    __syncthreads();
+    cl_choose_block(tab, n_clusters, w);
 }
 
 // M0 refit: M0' = sum_e I_e f_e(c) / sum_e f_e(c)^2 with I_e = M0 f_e(T1, T2)
@@ -339,8 +568,6 @@ int grid(const mrsim_ctx *c, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)c->sm_count * 8));
 }
 
-using u128 = unsigned __int128;
-
 // Host copy of one cluster's exact sums.
 struct Cluster {
     uint64_t n = 0;
@@ -362,8 +589,6 @@ struct Cluster {
     }
 };
 
-// SSE_a > SSE_b, i.e. N_a / n_a > N_b / n_b, exactly
-bool sse_greater(const Cluster &a, const Cluster &b) { return a.N * b.n > b.N * a.n; }
 
 }  // namespace
 
@@ -378,9 +603,20 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
     MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
     {
         KScope ks(c, "cluster_quantize");
-        k_cl_quant<<<grid(c, K), kClThreads, 0, c->stream>>>(
-            K, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(), scale[0], scale[1],
-            scale[2], xq.as<int32_t>(), err);
+        // integer scales below 2^24 (the default grid): the same features in
+        // integer arithmetic; other scales: FP64 products
+        bool int_scale = true;
+        for (int i = 0; i < 3; ++i)
+            int_scale &= scale[i] >= 1.0 && scale[i] < 16777216.0 && scale[i] == std::floor(scale[i]);
+        if (int_scale)
+            k_cl_quant_int<<<grid(c, K), kClThreads, 0, c->stream>>>(
+                K, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(),
+                (long long)scale[0], (long long)scale[1], (long long)scale[2], xq.as<int32_t>(),
+                err);
+        else
+            k_cl_quant<<<grid(c, K), kClThreads, 0, c->stream>>>(
+                K, ph->T1.as<float>(), ph->T2.as<float>(), ph->dB0.as<float>(), scale[0],
+                scale[1], scale[2], xq.as<int32_t>(), err);
     }
     int h_err = 0;
     MRSIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -397,85 +633,72 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
     MRSIM_CUDA(cudaMemsetAsync(lab.p, 0, U * sizeof(int32_t), c->stream));
     DBuf work = dalloc(sizeof(ClWork));
     ClWork *w = work.as<ClWork>();
+    DBuf table = dalloc((size_t)n_clusters * sizeof(ClEntry));
+    ClEntry *tab = table.as<ClEntry>();
     const int32_t *ptx = tx.as<int32_t>(), *pwt = wt.as<int32_t>();
     int32_t *plab = lab.as<int32_t>();
-    const int gU = grid(c, U);
-    ClStats hs[2];
-
-    // sums of one pass of cluster cl under the device centres
-    auto stats_pass = [&](int32_t cl, double *cen_back) {
-        MRSIM_CUDA(cudaMemsetAsync(&w->st, 0, sizeof(w->st), c->stream));
-        {
-            KScope ks(c, "cluster_assign");
-            k_cl_assign<<<gU, kClThreads, 0, c->stream>>>(U, plab, cl, ptx, pwt, w);
-        }
-        MRSIM_CUDA(cudaMemcpyAsync(hs, &w->st, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-        if (cen_back)
-            MRSIM_CUDA(cudaMemcpyAsync(cen_back, &w->cen, 6 * sizeof(double),
-                                       cudaMemcpyDeviceToHost, c->stream));
-        sync(c);
-    };
-    auto put_cen = [&](const double *cen) {
-        MRSIM_CUDA(cudaMemcpyAsync(&w->cen, cen, 6 * sizeof(double), cudaMemcpyHostToDevice,
-                                   c->stream));
-    };
-
-    // cluster 0: every key (equal centres put every member on side 0)
-    std::vector<Cluster> cl(1);
+    // passes over the distinct keys: two CTAs per SM (the last-block steps
+    // combine one partial per CTA)
+    const int gU = (int)std::max<int64_t>(
+        1, std::min<int64_t>((U + kClThreads - 1) / kClThreads, (int64_t)c->sm_count * 2));
+    DBuf far_d = dalloc(gU * sizeof(unsigned long long)), far_u = dalloc(gU * sizeof(int32_t));
+    DBuf counter = dalloc(sizeof(unsigned int));
+    MRSIM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), c->stream));
+    unsigned int *cnt = counter.as<unsigned int>();
+    // cluster 0 holds every key: one pass with equal centres (every key on
+    // side 0, cluster id 0) gives its entry; then the first split is chosen
     {
-        const double zero[6] = {0, 0, 0, 0, 0, 0};
-        put_cen(zero);
-        stats_pass(0, nullptr);
-        cl[0].set(hs[0]);
+        ClWork w0{};
+        w0.cid = 0;
+        upload(c, w, &w0, sizeof(ClWork));
+        KScope ks(c, "cluster_assign");
+        k_cl_assign<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, pwt, w, max_iter, cnt, tab, 1);
+        k_cl_choose<<<1, kClThreads, 0, c->stream>>>(tab, n_clusters, w);
     }
-    while ((int)cl.size() < n_clusters) {
-        int best = -1;
-        for (int i = 0; i < (int)cl.size(); ++i)
-            if (cl[i].N > 0 && (best < 0 || sse_greater(cl[i], cl[best]))) best = i;
-        if (best < 0) break;  // every cluster is one distinct value
-        const int32_t cid = best, nid = (int32_t)cl.size();
-        // initial centres: farthest member from the mean, then farthest from it
-        const double mu[6] = {cl[best].mu[0], cl[best].mu[1], cl[best].mu[2], 0, 0, 0};
-        put_cen(mu);
-        MRSIM_CUDA(cudaMemsetAsync(&w->dmax, 0, sizeof(w->dmax), c->stream));
-        MRSIM_CUDA(cudaMemsetAsync(&w->umin, 0x7f, sizeof(w->umin), c->stream));
+    // Splits, decided on the device: the farthest-member searches, 2-means
+    // passes queued four at a time (they return at once after the passes
+    // stopped), the relabelling, which also records both sides and chooses the
+    // next split.  The host reads a few words back once per split.
+    constexpr int kPassBatch = 4;
+    struct Status { int32_t cid, nid, done, have, passes; } st{};
+    for (int split = 1; split < n_clusters; ++split) {
         {
             KScope ks(c, "cluster_farthest");
-            k_cl_far_mean<<<gU, kClThreads, 0, c->stream>>>(U, plab, cid, ptx, w);
-            k_cl_pick_mean<<<gU, kClThreads, 0, c->stream>>>(U, plab, cid, ptx, w);
-            k_cl_far_point<<<gU, kClThreads, 0, c->stream>>>(U, plab, cid, ptx, w);
-            k_cl_pick_point<<<gU, kClThreads, 0, c->stream>>>(U, plab, cid, ptx, w);
-            k_cl_seed<<<1, 32, 0, c->stream>>>(U, ptx, w);
+            k_cl_far<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, 0,
+                                                       far_d.as<unsigned long long>(),
+                                                       far_u.as<int32_t>(), cnt);
+            k_cl_far<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, 1,
+                                                       far_d.as<unsigned long long>(),
+                                                       far_u.as<int32_t>(), cnt);
         }
-        double cur[6] = {0, 0, 0, 0, 0, 0};
-        double kept_cen[6] = {0, 0, 0, 0, 0, 0};
-        ClStats kept[2] = {};
-        bool have = false;
-        for (int it = 0; it < max_iter; ++it) {
-            if (it > 0) put_cen(cur);
-            stats_pass(cid, it == 0 ? cur : nullptr);
-            if (hs[0].n == 0 || hs[1].n == 0) break;
-            std::copy(cur, cur + 6, kept_cen);
-            kept[0] = hs[0];
-            kept[1] = hs[1];
-            have = true;
-            double m[6];
-            for (int s = 0; s < 2; ++s)
-                for (int i = 0; i < 3; ++i)
-                    m[3 * s + i] = (double)(int64_t)hs[s].sx[i] / (double)hs[s].n;
-            if (std::equal(m, m + 6, cur)) break;
-            std::copy(m, m + 6, cur);
+        for (;;) {
+            {
+                KScope ks(c, "cluster_assign");
+                for (int p = 0; p < kPassBatch; ++p)
+                    k_cl_assign<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, pwt, w, max_iter,
+                                                                  cnt, tab, 0);
+            }
+            MRSIM_CUDA(cudaMemcpyAsync(&st, &w->cid, sizeof(Status), cudaMemcpyDeviceToHost,
+                                       c->stream));
+            sync(c);
+            if (st.cid < 0 || st.done) break;
         }
-        if (!have) fail(MRSIM_ECUDA, "clustering: the first 2-means pass left a side empty");
-        put_cen(kept_cen);
-        {
-            KScope ks(c, "cluster_label");
-            k_cl_label<<<gU, kClThreads, 0, c->stream>>>(U, plab, cid, nid, ptx, w);
-        }
-        cl[best].set(kept[0]);
-        cl.emplace_back();
-        cl.back().set(kept[1]);
+        if (st.cid < 0) break;  // every cluster is one distinct value
+        if (!st.have) fail(MRSIM_ECUDA, "clustering: the first 2-means pass left a side empty");
+        KScope ks(c, "cluster_label");
+        k_cl_label<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, tab, n_clusters, cnt);
     }
+    // the clusters' exact sums, back on the host for the centre values
+    int32_t n_made = 0;
+    MRSIM_CUDA(cudaMemcpyAsync(&n_made, &w->n_cur, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c->stream));
+    sync(c);
+    std::vector<ClEntry> hs(std::max(n_made, 1));
+    MRSIM_CUDA(cudaMemcpyAsync(hs.data(), tab, n_made * sizeof(ClEntry), cudaMemcpyDeviceToHost,
+                               c->stream));
+    sync(c);
+    std::vector<Cluster> cl(n_made);
+    for (int i = 0; i < n_made; ++i) cl[i].set(hs[i].s);
     const int n = (int)cl.size();
     // centre values in phantom units, as stored (float32)
     centres.assign(3 * (size_t)n, 0.0);
