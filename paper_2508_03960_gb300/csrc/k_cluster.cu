@@ -25,6 +25,8 @@
 //   next id.
 #include <algorithm>
 #include <cmath>
+#include <queue>
+#include <vector>
 
 #include "internal.h"
 
@@ -40,21 +42,6 @@ struct ClStats {
     unsigned long long n;         // sum of weights (isochromats)
     unsigned long long sx[3];     // sum w x_i, two's complement
     unsigned long long sq[3][2];  // sum w x_i^2 as (low, high) words
-};
-
-// Device work area of the split in progress.  The split is decided on the
-// device: k_cl_choose picks the cluster, k_cl_update advances the 2-means
-// passes and decides when they stop, k_cl_commit records the two sides.
-struct ClWork {
-    double cen[6];                // centres of side 0 and side 1, feature units
-    unsigned long long dmax[2];   // farthest-member searches: largest distance
-    int32_t umin[2];              // ... and the smallest key id at it
-    ClStats st[2];                // sums of the pass in progress
-    double kept_cen[6];           // centres of the last pass with both sides filled
-    ClStats kept[2];              // ... and its sums
-    int32_t cid, nid;             // cluster being split (-1: none left), id of side 1
-    int32_t done, have, passes;   // 2-means stopped; a pass was kept; passes run
-    int32_t n_cur;                // clusters made so far
 };
 
 // Per-thread partial sums (plain data: also held in shared memory).
@@ -210,132 +197,67 @@ __global__ void k_cl_quant_int(int64_t K, const float *T1, const float *T2, cons
 
 using u128 = unsigned __int128;
 
-// n * SSE of a cluster's exact sums: sum_i (n sum w x_i^2 - (sum w x_i)^2)
-__device__ __forceinline__ u128 cl_nsse(const ClStats &s) {
-    u128 N = 0;
-    for (int i = 0; i < 3; ++i) {
-        const u128 sq = ((u128)s.sq[i][1] << 64) | s.sq[i][0];
-        const long long x = (long long)s.sx[i];
-        const u128 a = x < 0 ? (u128)(-x) : (u128)x;
-        N += (u128)s.n * sq - a * a;
-    }
-    return N;
-}
-
-// One cluster of the device table: its exact sums and n * SSE (two words).
-struct ClEntry {
+// One node of the split tree: the exact sums of its keys and where its keys
+// lie (a contiguous range of one of the two order buffers).
+struct ClNode {
     ClStats s;
-    unsigned long long N[2];  // low, high
+    int32_t buf, start, count, pad;
 };
 
-// Last-block completion: every block adds one to the counter after its
-// results are visible (fence first); the block that brings it to gridDim.x
-// finishes the step alone and resets the counter for the next launch.  No
+// One split computed in a round ("slot"): the node, its two children and the
+// state of the split's steps.  The host fills the first group of fields; the
+// kernels the rest.
+struct ClSlot {
+    double cen[6];                // centres of side 0 / side 1; cen[0..2] = the mean first
+    int32_t node, child0, child1;  // node ids in the tree table
+    int32_t buf, start, count;    // the node's keys
+    int32_t tile0, n_tiles;       // its tiles in the round's tile list
+    double kept_cen[6];           // centres of the last pass with both sides filled
+    ClStats st[2];                // sums of the pass in progress
+    ClStats kept[2];              // ... and of the kept pass
+    int32_t umin[2];              // farthest-member searches: the key found
+    int32_t done, have, passes;   // 2-means stopped; a pass was kept; passes run
+    unsigned int counter;         // tiles finished in the step in progress
+    unsigned int front, back;     // partition: keys placed on side 0 / side 1
+};
+
+// Completion per slot: every block adds one to the slot's counter after its
+// tile's results are visible (fence first); the block that brings it to
+// n_tiles finishes the step for the slot alone and resets the counter.  No
 // block waits for another.
-__device__ __forceinline__ bool cl_last_block(unsigned int *counter) {
+__device__ __forceinline__ bool cl_last_tile(ClSlot *w) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int prev = atomicAdd(counter, 1u);
-        last = prev == gridDim.x - 1;
-        if (last) *counter = 0u;
+        const unsigned int prev = atomicAdd(&w->counter, 1u);
+        last = prev == (unsigned int)w->n_tiles - 1u;
+        if (last) w->counter = 0u;
     }
     __syncthreads();
     if (last) __threadfence();
     return last;
 }
 
-// the next split, chosen by one block: the cluster with the largest SSE,
-// compared as exact rationals N_a / n_a > N_b / n_b, ties to the smaller id
-// (clusters of one distinct value have N = 0 and are never split); its mean
-// seeds the farthest-member search.  cid = -1 at n_clusters or when nothing
-// can be split.
-__device__ void cl_choose_block(const ClEntry *tab, int n_clusters, ClWork *w) {
-    __shared__ int s_best[kClThreads];
-    const int n = w->n_cur;
-    const int t = threadIdx.x;
-    auto better = [&](int a, int b) {  // a strictly better than b
-        if (a < 0) return false;
-        if (b < 0) return true;
-        const u128 Na = ((u128)tab[a].N[1] << 64) | tab[a].N[0];
-        const u128 Nb = ((u128)tab[b].N[1] << 64) | tab[b].N[0];
-        const u128 l = Na * (u128)tab[b].s.n, r = Nb * (u128)tab[a].s.n;
-        return l > r || (l == r && a < b);
-    };
-    int best = -1;
-    for (int i = t; n < n_clusters && i < n; i += blockDim.x) {
-        if (tab[i].N[0] == 0 && tab[i].N[1] == 0) continue;
-        if (better(i, best)) best = i;
+// sums written by other blocks' atomics, read from L2
+__device__ __forceinline__ ClStats cl_ld_l2(const ClStats *p) {
+    ClStats s;
+    s.n = __ldcg(&p->n);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        s.sx[i] = __ldcg(&p->sx[i]);
+        s.sq[i][0] = __ldcg(&p->sq[i][0]);
+        s.sq[i][1] = __ldcg(&p->sq[i][1]);
     }
-    s_best[t] = best;
-    __syncthreads();
-    for (int off = kClThreads / 2; off > 0; off >>= 1) {
-        if (t < off && better(s_best[t + off], s_best[t])) s_best[t] = s_best[t + off];
-        __syncthreads();
-    }
-    if (t == 0) {
-        best = s_best[0];
-        w->cid = best;
-        w->nid = n;
-        w->done = 0;
-        w->have = 0;
-        w->passes = 0;
-        for (int s = 0; s < 2; ++s) w->st[s] = ClStats{};
-        if (best >= 0)
-            for (int i = 0; i < 3; ++i) {
-                w->cen[i] = (double)(long long)tab[best].s.sx[i] / (double)tab[best].s.n;
-                w->cen[3 + i] = 0.0;
-            }
-    }
-    __syncthreads();
+    return s;
 }
 
-__global__ void __launch_bounds__(kClThreads) k_cl_choose(const ClEntry *tab, int n_clusters,
-                                                          ClWork *w) {
-    cl_choose_block(tab, n_clusters, w);
-}
-
-// the cluster's entry (one thread): exact sums and n * SSE
-__device__ __forceinline__ void cl_set_entry(ClEntry &e, const ClStats &s) {
-    e.s = s;
-    const u128 N = cl_nsse(s);
-    e.N[0] = (unsigned long long)N;
-    e.N[1] = (unsigned long long)(N >> 64);
-}
-
-// One 2-means pass over the keys of the split cluster: sums of each side under
-// the centres in w->cen; the last block then advances the passes (an empty side
-// ends them, the previous pass standing; otherwise the pass is kept, and they
-// end when the side means repeat the centres or after max_iter passes).
-// first_entry: the pass that sums cluster 0 (every key) into table entry 0.
-__global__ void __launch_bounds__(kClThreads) k_cl_assign(int64_t U, const int32_t *lab,
-                                                          const int32_t *tx, const int32_t *wt,
-                                                          ClWork *w, int max_iter,
-                                                          unsigned int *counter, ClEntry *tab,
-                                                          int first_entry) {
-    __shared__ double cen[6];
+// the block's sums of one or two sides, added into dst[0..1] (exact)
+__device__ __forceinline__ void cl_block_flush(ClAcc a0, ClAcc a1, ClStats *dst, int sides) {
     __shared__ ClAcc part[kClThreads / 32][2];
-    const int32_t c = w->cid;
-    if (c < 0 || w->done) return;  // nothing left to split, or the passes stopped
-    if (threadIdx.x < 6) cen[threadIdx.x] = w->cen[threadIdx.x];
-    __syncthreads();
-    ClAcc a0, a1;
-    a0.zero();
-    a1.zero();
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        const int32_t x0 = tx[u], x1 = tx[U + u], x2 = tx[2 * U + u];
-        const unsigned long long wu = (unsigned long long)wt[u];
-        if (cl_side(x0, x1, x2, cen))
-            a1.add(wu, x0, x1, x2);
-        else
-            a0.add(wu, x0, x1, x2);
-    }
     for (int off = 16; off > 0; off >>= 1) {
         a0.shfl_down(off);
-        a1.shfl_down(off);
+        if (sides > 1) a1.shfl_down(off);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
@@ -343,36 +265,42 @@ __global__ void __launch_bounds__(kClThreads) k_cl_assign(int64_t U, const int32
         part[wid][1] = a1;
     }
     __syncthreads();
-    if (threadIdx.x < 2) {
+    if (threadIdx.x < sides) {
         ClAcc t = part[0][threadIdx.x];
         for (int i = 1; i < kClThreads / 32; ++i) t.merge(part[i][threadIdx.x]);
-        t.flush(&w->st[threadIdx.x]);
+        t.flush(&dst[threadIdx.x]);
     }
-    if (!cl_last_block(counter) || threadIdx.x != 0) return;
-    if (first_entry) {
-        cl_set_entry(tab[0], w->st[0]);
-        w->n_cur = 1;
-        return;
+}
+
+// Sums of every key: the root node of the tree (its sums zeroed before).
+__global__ void __launch_bounds__(kClThreads) k_cl_root(int64_t U, const int32_t *tx,
+                                                        const int32_t *wt, int32_t *ord,
+                                                        ClNode *root) {
+    ClAcc a, none;
+    a.zero();
+    none.zero();
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        a.add((unsigned long long)wt[u], tx[u], tx[U + u], tx[2 * U + u]);
+        ord[u] = (int32_t)u;
     }
-    ++w->passes;
-    if (w->st[0].n == 0 || w->st[1].n == 0) {
-        w->done = 1;
-        return;
-    }
-    for (int i = 0; i < 6; ++i) w->kept_cen[i] = w->cen[i];
-    w->kept[0] = w->st[0];
-    w->kept[1] = w->st[1];
-    w->have = 1;
-    double m[6];
-    bool same = true;
-    for (int s = 0; s < 2; ++s)
-        for (int i = 0; i < 3; ++i) {
-            m[3 * s + i] = (double)(long long)w->st[s].sx[i] / (double)w->st[s].n;
-            same &= m[3 * s + i] == w->cen[3 * s + i];
-        }
-    for (int i = 0; i < 6; ++i) w->cen[i] = m[i];
-    for (int s = 0; s < 2; ++s) w->st[s] = ClStats{};
-    if (same || w->passes >= max_iter) w->done = 1;
+    cl_block_flush(a, none, &root->s, 1);
+}
+
+// the tile's keys: [lo, hi) of the slot's range in its order buffer
+struct ClTile {
+    const int32_t *keys;
+    int64_t lo, hi;
+};
+
+__device__ __forceinline__ ClTile cl_tile(const ClSlot *w, const int32_t *ord, int64_t U, int t,
+                                          int tile_keys) {
+    ClTile r;
+    r.keys = ord + (int64_t)w->buf * U + w->start;
+    r.lo = (int64_t)(t - w->tile0) * tile_keys;
+    const int64_t end = r.lo + tile_keys;
+    r.hi = end < w->count ? end : (int64_t)w->count;
+    return r;
 }
 
 // exact squared distance of the features of key u to those of key a
@@ -393,36 +321,10 @@ __device__ __forceinline__ bool cl_far_better(unsigned long long d, int32_t u,
     return d > bd || (d == bd && u < bu);
 }
 
-// Farthest member of the split cluster (ties to the smallest key id) from
-// its mean (stage 0, FP64 distances; distances are >= 0, so their bit
-// patterns order like the values) or from the member found before (stage 1,
-// exact integer distances).  Per-block results go to far_d / far_u; the last
-// block combines them, and after stage 1 seeds the first 2-means pass with
-// the two members.
-__global__ void __launch_bounds__(kClThreads) k_cl_far(int64_t U, const int32_t *lab,
-                                                       const int32_t *tx, ClWork *w, int stage,
-                                                       unsigned long long *far_d,
-                                                       int32_t *far_u, unsigned int *counter) {
-    __shared__ unsigned long long sd[kClThreads];
-    __shared__ int32_t su[kClThreads];
-    const int32_t c = w->cid;
-    if (c < 0) return;
-    const int32_t a = stage ? w->umin[0] : 0;
-    const double cen[3] = {w->cen[0], w->cen[1], w->cen[2]};
-    unsigned long long bd = 0;
-    int32_t bu = 0x7fffffff;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        const unsigned long long d =
-            stage ? (unsigned long long)cl_dist_int(tx, U, u, a)
-                  : (unsigned long long)__double_as_longlong(
-                        cl_dist(tx[u], tx[U + u], tx[2 * U + u], cen));
-        if (cl_far_better(d, (int32_t)u, bd, bu)) {
-            bd = d;
-            bu = (int32_t)u;
-        }
-    }
+// block-wide best (distance, key) pair of the values held by each thread;
+// the result in sd[0], su[0]
+__device__ __forceinline__ void cl_far_reduce(unsigned long long *sd, int32_t *su,
+                                              unsigned long long bd, int32_t bu) {
     const int t = threadIdx.x;
     sd[t] = bd;
     su[t] = bu;
@@ -434,68 +336,210 @@ __global__ void __launch_bounds__(kClThreads) k_cl_far(int64_t U, const int32_t 
         }
         __syncthreads();
     }
-    if (t == 0) {
-        far_d[blockIdx.x] = sd[0];
-        far_u[blockIdx.x] = su[0];
-    }
-    if (!cl_last_block(counter)) return;
-    bd = 0;
-    bu = 0x7fffffff;
-    for (int b = t; b < (int)gridDim.x; b += blockDim.x) {
-        const unsigned long long d = far_d[b];
-        const int32_t u = far_u[b];
-        if (cl_far_better(d, u, bd, bu)) {
-            bd = d;
-            bu = u;
+}
+
+// Farthest member of each slot's node (ties to the smallest key id) from the
+// node's mean (stage 0, FP64 distances; distances are >= 0, so their bit
+// patterns order like the values) or from the member found before (stage 1,
+// exact integer distances).  Each tile's best pair goes to far_d / far_u; the
+// slot's last tile combines its tiles and, after stage 1, seeds the first
+// 2-means pass with the two members.
+__global__ void __launch_bounds__(kClThreads) k_cl_far(int64_t U, const int32_t *ord,
+                                                       const int32_t *tx, ClSlot *slots,
+                                                       const int32_t *tile_slot, int n_tiles,
+                                                       int tile_keys, int stage,
+                                                       unsigned long long *far_d,
+                                                       int32_t *far_u) {
+    __shared__ unsigned long long sd[kClThreads];
+    __shared__ int32_t su[kClThreads];
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        ClSlot *w = slots + tile_slot[t];
+        const ClTile r = cl_tile(w, ord, U, t, tile_keys);
+        const int32_t a = stage ? w->umin[0] : 0;
+        const double cen[3] = {w->cen[0], w->cen[1], w->cen[2]};
+        unsigned long long bd = 0;
+        int32_t bu = 0x7fffffff;
+        for (int64_t i = r.lo + threadIdx.x; i < r.hi; i += blockDim.x) {
+            const int64_t u = r.keys[i];
+            const unsigned long long d =
+                stage ? (unsigned long long)cl_dist_int(tx, U, u, a)
+                      : (unsigned long long)__double_as_longlong(
+                            cl_dist(tx[u], tx[U + u], tx[2 * U + u], cen));
+            if (cl_far_better(d, (int32_t)u, bd, bu)) {
+                bd = d;
+                bu = (int32_t)u;
+            }
         }
-    }
-    sd[t] = bd;
-    su[t] = bu;
-    __syncthreads();
-    for (int off = kClThreads / 2; off > 0; off >>= 1) {
-        if (t < off && cl_far_better(sd[t + off], su[t + off], sd[t], su[t])) {
-            sd[t] = sd[t + off];
-            su[t] = su[t + off];
+        cl_far_reduce(sd, su, bd, bu);
+        if (threadIdx.x == 0) {
+            far_d[t] = sd[0];
+            far_u[t] = su[0];
+        }
+        if (cl_last_tile(w)) {
+            bd = 0;
+            bu = 0x7fffffff;
+            for (int j = w->tile0 + threadIdx.x; j < w->tile0 + w->n_tiles; j += blockDim.x) {
+                const unsigned long long d = __ldcg(&far_d[j]);
+                const int32_t u = __ldcg(&far_u[j]);
+                if (cl_far_better(d, u, bd, bu)) {
+                    bd = d;
+                    bu = u;
+                }
+            }
+            cl_far_reduce(sd, su, bd, bu);
+            if (threadIdx.x == 0) {
+                w->umin[stage] = su[0];
+                if (stage == 1) {  // centres of the first 2-means pass
+                    const int32_t m0 = w->umin[0], m1 = su[0];
+                    for (int i = 0; i < 3; ++i) {
+                        w->cen[i] = (double)tx[i * U + m0];
+                        w->cen[3 + i] = (double)tx[i * U + m1];
+                    }
+                }
+            }
         }
         __syncthreads();
     }
-    if (t == 0) {
-        w->umin[stage] = su[0];
-        if (stage == 1) {  // centres of the first 2-means pass
-            const int32_t m0 = w->umin[0], m1 = su[0];
-            for (int i = 0; i < 3; ++i) {
-                w->cen[i] = (double)tx[i * U + m0];
-                w->cen[3 + i] = (double)tx[i * U + m1];
+}
+
+// One 2-means pass over the keys of every slot still running: sums of each
+// side under the slot's centres; the slot's last tile then advances its passes
+// (an empty side ends them, the previous pass standing; otherwise the pass is
+// kept, and they end when the side means repeat the centres or after max_iter
+// passes).  n_running counts the slots whose passes have not ended.
+__global__ void __launch_bounds__(kClThreads) k_cl_pass(int64_t U, const int32_t *ord,
+                                                        const int32_t *tx, const int32_t *wt,
+                                                        ClSlot *slots, const int32_t *tile_slot,
+                                                        int n_tiles, int tile_keys, int max_iter,
+                                                        int *n_running) {
+    __shared__ double cen[6];
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        ClSlot *w = slots + tile_slot[t];
+        if (w->done) continue;  // the same value for every thread of the block
+        if (threadIdx.x < 6) cen[threadIdx.x] = w->cen[threadIdx.x];
+        __syncthreads();
+        const ClTile r = cl_tile(w, ord, U, t, tile_keys);
+        ClAcc a0, a1;
+        a0.zero();
+        a1.zero();
+        for (int64_t i = r.lo + threadIdx.x; i < r.hi; i += blockDim.x) {
+            const int64_t u = r.keys[i];
+            const int32_t x0 = tx[u], x1 = tx[U + u], x2 = tx[2 * U + u];
+            const unsigned long long wu = (unsigned long long)wt[u];
+            if (cl_side(x0, x1, x2, cen))
+                a1.add(wu, x0, x1, x2);
+            else
+                a0.add(wu, x0, x1, x2);
+        }
+        cl_block_flush(a0, a1, w->st, 2);
+        const bool last = cl_last_tile(w);
+        if (last && threadIdx.x == 0) {
+            ++w->passes;
+            const ClStats st[2] = {cl_ld_l2(&w->st[0]), cl_ld_l2(&w->st[1])};
+            bool stop;
+            if (st[0].n == 0 || st[1].n == 0) {
+                stop = true;
+            } else {
+                for (int i = 0; i < 6; ++i) w->kept_cen[i] = w->cen[i];
+                w->kept[0] = st[0];
+                w->kept[1] = st[1];
+                w->have = 1;
+                double m[6];
+                bool same = true;
+                for (int s = 0; s < 2; ++s)
+                    for (int i = 0; i < 3; ++i) {
+                        m[3 * s + i] = (double)(long long)st[s].sx[i] / (double)st[s].n;
+                        same &= m[3 * s + i] == w->cen[3 * s + i];
+                    }
+                for (int i = 0; i < 6; ++i) w->cen[i] = m[i];
+                stop = same || w->passes >= max_iter;
+            }
+            for (int s = 0; s < 2; ++s) w->st[s] = ClStats{};
+            if (stop) {
+                w->done = 1;
+                atomicSub(n_running, 1);
             }
         }
+        __syncthreads();
     }
 }
 
-// Members of the split cluster on side 1 under the kept centres move to id
-// nid; the last block records both sides in the table and chooses the next
-// split.
-__global__ void __launch_bounds__(kClThreads) k_cl_label(int64_t U, int32_t *lab,
-                                                         const int32_t *tx, ClWork *w,
-                                                         ClEntry *tab, int n_clusters,
-                                                         unsigned int *counter) {
+// Each slot's keys on side 1 under the kept centres form child 1, the rest
+// child 0: the node's range is partitioned into the other order buffer, side 0
+// from the front and side 1 from the back (the order inside a range is free:
+// ties go by key id and sums are exact).  The slot's last tile records both
+// children in the tree table.
+__global__ void __launch_bounds__(kClThreads) k_cl_part(int64_t U, int32_t *ord,
+                                                        const int32_t *tx, ClSlot *slots,
+                                                        const int32_t *tile_slot, int n_tiles,
+                                                        int tile_keys, ClNode *nodes, int *err) {
     __shared__ double cen[6];
-    const int32_t c = w->cid, id_new = w->nid;
-    if (c < 0 || !w->have) return;
-    if (threadIdx.x < 6) cen[threadIdx.x] = w->kept_cen[threadIdx.x];
-    __syncthreads();
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        if (lab[u] != c) continue;
-        if (cl_side(tx[u], tx[U + u], tx[2 * U + u], cen)) lab[u] = id_new;
+    const int lane = threadIdx.x & 31;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        ClSlot *w = slots + tile_slot[t];
+        if (threadIdx.x < 6) cen[threadIdx.x] = w->kept_cen[threadIdx.x];
+        __syncthreads();
+        const ClTile r = cl_tile(w, ord, U, t, tile_keys);
+        int32_t *dst = ord + (int64_t)(1 - w->buf) * U + w->start;
+        const int32_t n = w->count;
+        // whole warps take part in the ballots: tiles are whole blocks long
+        for (int64_t i = r.lo + threadIdx.x; i < r.lo + tile_keys; i += blockDim.x) {
+            const bool live = i < r.hi;
+            const int64_t u = live ? r.keys[i] : 0;
+            const bool one = live && cl_side(tx[u], tx[U + u], tx[2 * U + u], cen);
+            const unsigned m1 = __ballot_sync(0xffffffffu, one);
+            const unsigned m0 = __ballot_sync(0xffffffffu, live && !one);
+            if (!(m0 | m1)) continue;  // the same for the whole warp
+            unsigned b0 = 0, b1 = 0;
+            if (lane == 0) {
+                if (m0) b0 = atomicAdd(&w->front, (unsigned)__popc(m0));
+                if (m1) b1 = atomicAdd(&w->back, (unsigned)__popc(m1));
+            }
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            b1 = __shfl_sync(0xffffffffu, b1, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (live && !one) dst[b0 + __popc(m0 & below)] = (int32_t)u;
+            if (one) dst[n - 1 - (b1 + __popc(m1 & below))] = (int32_t)u;
+        }
+        if (cl_last_tile(w) && threadIdx.x == 0) {
+            const unsigned int front = __ldcg(&w->front), back = __ldcg(&w->back);
+            if (!w->have || (int64_t)front + back != n) atomicOr(err, 2);
+            const int32_t nf = (int32_t)front;
+            ClNode c0, c1;
+            c0.s = w->kept[0];
+            c0.buf = 1 - w->buf;
+            c0.start = w->start;
+            c0.count = nf;
+            c0.pad = 0;
+            c1.s = w->kept[1];
+            c1.buf = 1 - w->buf;
+            c1.start = w->start + nf;
+            c1.count = n - nf;
+            c1.pad = 0;
+            nodes[w->child0] = c0;
+            nodes[w->child1] = c1;
+        }
+        __syncthreads();
     }
-    if (!cl_last_block(counter)) return;
-    if (threadIdx.x == 0) {
-        cl_set_entry(tab[c], w->kept[0]);
-        cl_set_entry(tab[id_new], w->kept[1]);
-        w->n_cur = id_new + 1;
+}
+
+// The final clusters: every key of cluster id's node takes label id.  leaf[j]
+// = (buf, start, count, id), tiles as in the split kernels (tile0 in leaf_t0).
+__global__ void __launch_bounds__(kClThreads) k_cl_leaf_label(int64_t U, const int32_t *ord,
+                                                              const int4 *leaf,
+                                                              const int32_t *leaf_t0,
+                                                              const int32_t *tile_leaf,
+                                                              int n_tiles, int tile_keys,
+                                                              int32_t *lab) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int j = tile_leaf[t];
+        const int4 l = leaf[j];
+        const int32_t *keys = ord + (int64_t)l.x * U + l.y;
+        const int64_t lo = (int64_t)(t - leaf_t0[j]) * tile_keys;
+        const int64_t end = lo + tile_keys;
+        const int64_t hi = end < l.z ? end : (int64_t)l.z;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) lab[keys[i]] = l.w;
     }
-    __syncthreads();
-    cl_choose_block(tab, n_clusters, w);
 }
 
 // M0 refit: M0' = sum_e I_e f_e(c) / sum_e f_e(c)^2 with I_e = M0 f_e(T1, T2)
@@ -590,6 +634,88 @@ struct Cluster {
 };
 
 
+// n * SSE of exact sums, on the host
+u128 host_nsse(const ClStats &s) {
+    u128 N = 0;
+    for (int i = 0; i < 3; ++i) {
+        const u128 sq = ((u128)s.sq[i][1] << 64) | s.sq[i][0];
+        const int64_t x = (int64_t)s.sx[i];
+        const u128 a = x < 0 ? (u128)(-x) : (u128)x;
+        N += (u128)s.n * sq - a * a;
+    }
+    return N;
+}
+
+// Host copy of one node of the split tree; c0 / c1 are its children once its
+// split is computed (-1 before).
+struct TreeNode {
+    ClStats s{};
+    u128 N = 0;
+    int32_t buf = 0, start = 0, count = 0;
+    int c0 = -1, c1 = -1;
+
+    void set(const ClNode &e) {
+        s = e.s;
+        N = host_nsse(s);
+        buf = e.buf;
+        start = e.start;
+        count = e.count;
+    }
+};
+
+// A leaf in the greedy replay: score N / n, id, tree node.
+struct Pick {
+    u128 N;
+    uint64_t n;
+    int id, node;
+};
+
+// heap order: b comes out before a when its SSE is larger (exact rationals),
+// or equal with the smaller id
+struct PickAfter {
+    bool operator()(const Pick &a, const Pick &b) const {
+        const u128 l = b.N * (u128)a.n, r = a.N * (u128)b.n;
+        return l > r || (l == r && b.id < a.id);
+    }
+};
+
+// The greedy choice replayed on the tree: split the leaf with the largest SSE
+// (ties to the smaller id; leaves of one distinct value are never split), side
+// 0 keeping the id and side 1 taking the next, until n_clusters.  Returns true
+// when every pick had its split computed: leaf_node[id] is then the node of
+// every cluster.  Otherwise front lists the picks without a split, in pick
+// order (the first is the one the greedy needs next; the later ones are
+// counted as splits without their sides and may not be needed).
+bool greedy_replay(const std::vector<TreeNode> &tree, int n_clusters,
+                   std::vector<int> &leaf_node, std::vector<int> &front) {
+    std::priority_queue<Pick, std::vector<Pick>, PickAfter> q;
+    auto push = [&](int node, int id) {
+        if (tree[node].N != 0) q.push(Pick{tree[node].N, tree[node].s.n, id, node});
+    };
+    leaf_node.assign(1, 0);
+    front.clear();
+    push(0, 0);
+    bool exact = true;
+    for (int n_cur = 1; n_cur < n_clusters && !q.empty(); ++n_cur) {
+        const Pick p = q.top();
+        q.pop();
+        const TreeNode &h = tree[p.node];
+        if (h.c0 < 0) {
+            front.push_back(p.node);
+            exact = false;
+            continue;
+        }
+        if (exact) {
+            leaf_node[p.id] = h.c0;
+            leaf_node.push_back(h.c1);
+        }
+        push(h.c0, p.id);
+        push(h.c1, n_cur);
+    }
+    return exact;
+}
+
+
 }  // namespace
 
 void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
@@ -629,76 +755,170 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
     DBuf tx, tf, wt;
     const int64_t U = distinct_features(c, K, xq.as<int32_t>(), ph->T1.as<float>(),
                                         ph->T2.as<float>(), uid.as<int32_t>(), tx, tf, wt);
-    DBuf lab = dalloc(U * sizeof(int32_t));
-    MRSIM_CUDA(cudaMemsetAsync(lab.p, 0, U * sizeof(int32_t), c->stream));
-    DBuf work = dalloc(sizeof(ClWork));
-    ClWork *w = work.as<ClWork>();
-    DBuf table = dalloc((size_t)n_clusters * sizeof(ClEntry));
-    ClEntry *tab = table.as<ClEntry>();
+    // ---- the split tree, grown in rounds ----
+    // Every split of a cluster depends on its keys alone, not on when it is
+    // made, and a split's sides never have a larger SSE than the cluster (the
+    // chosen SSEs do not increase).  So the splits the greedy order will make
+    // can be computed many at a time: each round, the host replays the greedy
+    // choice (largest SSE, ties to the smaller id) on the splits computed so
+    // far; the replay's picks that are not computed yet, the first of which
+    // the greedy certainly needs, are computed together in one round of
+    // kernels over all their keys.  When the replay reaches n_clusters (or
+    // runs out of clusters with more than one distinct value) on computed
+    // splits alone, it is the sequential result, ids included.
+    const int cap = 6 * n_clusters + 8;  // tree nodes (bound below)
+    DBuf dnodes = dalloc((size_t)cap * sizeof(ClNode));
+    ClNode *pn = dnodes.as<ClNode>();
+    DBuf order = dalloc(2 * U * sizeof(int32_t));
+    int32_t *pord = order.as<int32_t>();
     const int32_t *ptx = tx.as<int32_t>(), *pwt = wt.as<int32_t>();
-    int32_t *plab = lab.as<int32_t>();
-    // passes over the distinct keys: two CTAs per SM (the last-block steps
-    // combine one partial per CTA)
-    const int gU = (int)std::max<int64_t>(
-        1, std::min<int64_t>((U + kClThreads - 1) / kClThreads, (int64_t)c->sm_count * 2));
-    DBuf far_d = dalloc(gU * sizeof(unsigned long long)), far_u = dalloc(gU * sizeof(int32_t));
-    DBuf counter = dalloc(sizeof(unsigned int));
-    MRSIM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), c->stream));
-    unsigned int *cnt = counter.as<unsigned int>();
-    // cluster 0 holds every key: one pass with equal centres (every key on
-    // side 0, cluster id 0) gives its entry; then the first split is chosen
+    std::vector<TreeNode> tree(1);
     {
-        ClWork w0{};
-        w0.cid = 0;
-        upload(c, w, &w0, sizeof(ClWork));
-        KScope ks(c, "cluster_assign");
-        k_cl_assign<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, pwt, w, max_iter, cnt, tab, 1);
-        k_cl_choose<<<1, kClThreads, 0, c->stream>>>(tab, n_clusters, w);
+        MRSIM_CUDA(cudaMemsetAsync(pn, 0, sizeof(ClNode), c->stream));
+        {
+            KScope ks(c, "cluster_root");
+            k_cl_root<<<grid(c, U), kClThreads, 0, c->stream>>>(U, ptx, pwt, pord, pn);
+        }
+        ClNode r;
+        MRSIM_CUDA(cudaMemcpyAsync(&r, pn, sizeof(ClNode), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        r.buf = 0;
+        r.start = 0;
+        r.count = (int32_t)U;
+        tree[0].set(r);
+        upload(c, pn, &r, sizeof(ClNode));
     }
-    // Splits, decided on the device: the farthest-member searches, 2-means
-    // passes queued four at a time (they return at once after the passes
-    // stopped), the relabelling, which also records both sides and chooses the
-    // next split.  The host reads a few words back once per split.
+    // per-round work areas: a slot per split, tiles of at least 256 keys
+    const int64_t tile_cap = U / kClThreads + n_clusters + 1;
+    DBuf dslots = dalloc((size_t)n_clusters * sizeof(ClSlot));
+    DBuf dtiles = dalloc(tile_cap * sizeof(int32_t));
+    DBuf far_d = dalloc(tile_cap * sizeof(unsigned long long));
+    DBuf far_u = dalloc(tile_cap * sizeof(int32_t));
+    DBuf drun = dalloc(sizeof(int));
+    ClSlot *psl = dslots.as<ClSlot>();
+    int32_t *ptl = dtiles.as<int32_t>();
+    int *prun = drun.as<int>();
+    std::vector<int> leaf_node, front;
+    std::vector<ClSlot> hs;
+    std::vector<int32_t> tiles;
+    std::vector<ClNode> made;
     constexpr int kPassBatch = 4;
-    struct Status { int32_t cid, nid, done, have, passes; } st{};
-    for (int split = 1; split < n_clusters; ++split) {
+    while (!greedy_replay(tree, n_clusters, leaf_node, front)) {
+        // picks after the first only while the table keeps room for the splits
+        // the greedy certainly needs (at most n_clusters - 1, two nodes each):
+        // the tree never holds more than 4 n + 2 (n - 1) + 1 nodes
+        size_t m = 1;
+        while (m < front.size() && tree.size() + 2 * (m + 1) <= (size_t)4 * n_clusters) ++m;
+        int64_t total = 0;
+        for (size_t j = 0; j < m; ++j) total += tree[front[j]].count;
+        const int64_t per = (total + 2 * c->sm_count - 1) / (2 * c->sm_count);
+        const int tile_keys = (int)std::min<int64_t>(
+            16384, std::max<int64_t>(kClThreads, (per + kClThreads - 1) / kClThreads * kClThreads));
+        hs.assign(m, ClSlot{});
+        tiles.clear();
+        for (size_t j = 0; j < m; ++j) {
+            TreeNode &h = tree[front[j]];
+            ClSlot &s = hs[j];
+            for (int i = 0; i < 3; ++i)
+                s.cen[i] = (double)(int64_t)h.s.sx[i] / (double)h.s.n;
+            s.node = front[j];
+            s.child0 = (int32_t)tree.size();
+            s.child1 = s.child0 + 1;
+            h.c0 = s.child0;
+            h.c1 = s.child1;
+            tree.emplace_back();
+            tree.emplace_back();
+            s.buf = h.buf;
+            s.start = h.start;
+            s.count = h.count;
+            s.tile0 = (int32_t)tiles.size();
+            s.n_tiles = (int32_t)((h.count + tile_keys - 1) / tile_keys);
+            tiles.insert(tiles.end(), s.n_tiles, (int32_t)j);
+        }
+        const int nt = (int)tiles.size();
+        const int g = std::min(nt, c->sm_count * 4);
+        const int n_run = (int)m;
+        upload(c, psl, hs.data(), m * sizeof(ClSlot));
+        upload(c, ptl, tiles.data(), nt * sizeof(int32_t));
+        upload(c, prun, &n_run, sizeof(int));
         {
             KScope ks(c, "cluster_farthest");
-            k_cl_far<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, 0,
-                                                       far_d.as<unsigned long long>(),
-                                                       far_u.as<int32_t>(), cnt);
-            k_cl_far<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, 1,
-                                                       far_d.as<unsigned long long>(),
-                                                       far_u.as<int32_t>(), cnt);
+            for (int stage = 0; stage < 2; ++stage)
+                k_cl_far<<<g, kClThreads, 0, c->stream>>>(U, pord, ptx, psl, ptl, nt, tile_keys,
+                                                          stage, far_d.as<unsigned long long>(),
+                                                          far_u.as<int32_t>());
         }
-        for (;;) {
+        for (int batch = 0;; ++batch) {
+            if (batch * kPassBatch > max_iter + kPassBatch)
+                fail(MRSIM_ECUDA, "clustering: 2-means passes did not stop");
             {
-                KScope ks(c, "cluster_assign");
+                KScope ks(c, "cluster_pass");
                 for (int p = 0; p < kPassBatch; ++p)
-                    k_cl_assign<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, pwt, w, max_iter,
-                                                                  cnt, tab, 0);
+                    k_cl_pass<<<g, kClThreads, 0, c->stream>>>(U, pord, ptx, pwt, psl, ptl, nt,
+                                                               tile_keys, max_iter, prun);
             }
-            MRSIM_CUDA(cudaMemcpyAsync(&st, &w->cid, sizeof(Status), cudaMemcpyDeviceToHost,
+            int running = 0;
+            MRSIM_CUDA(cudaMemcpyAsync(&running, prun, sizeof(int), cudaMemcpyDeviceToHost,
                                        c->stream));
             sync(c);
-            if (st.cid < 0 || st.done) break;
+            if (running == 0) break;
         }
-        if (st.cid < 0) break;  // every cluster is one distinct value
-        if (!st.have) fail(MRSIM_ECUDA, "clustering: the first 2-means pass left a side empty");
-        KScope ks(c, "cluster_label");
-        k_cl_label<<<gU, kClThreads, 0, c->stream>>>(U, plab, ptx, w, tab, n_clusters, cnt);
+        {
+            KScope ks(c, "cluster_partition");
+            k_cl_part<<<g, kClThreads, 0, c->stream>>>(U, pord, ptx, psl, ptl, nt, tile_keys, pn,
+                                                       err);
+        }
+        // the children back on the host
+        const int first = hs[0].child0;
+        made.resize(2 * m);
+        MRSIM_CUDA(cudaMemcpyAsync(made.data(), pn + first, 2 * m * sizeof(ClNode),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (h_err) fail(MRSIM_ECUDA, "clustering: a split left a side empty");
+        for (size_t j = 0; j < 2 * m; ++j) tree[first + j].set(made[j]);
     }
-    // the clusters' exact sums, back on the host for the centre values
-    int32_t n_made = 0;
-    MRSIM_CUDA(cudaMemcpyAsync(&n_made, &w->n_cur, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               c->stream));
-    sync(c);
-    std::vector<ClEntry> hs(std::max(n_made, 1));
-    MRSIM_CUDA(cudaMemcpyAsync(hs.data(), tab, n_made * sizeof(ClEntry), cudaMemcpyDeviceToHost,
-                               c->stream));
-    sync(c);
+    const int n_made = (int)leaf_node.size();
+    // labels of the distinct keys.  A cluster whose split was computed but not
+    // taken may have had its range overwritten by splits below it; the leaves
+    // of the computed tree are never overwritten, so every cluster labels the
+    // computed leaves under its node.
+    DBuf lab = dalloc(U * sizeof(int32_t));
+    int32_t *plab = lab.as<int32_t>();
+    {
+        const int tile_keys = 2048;
+        std::vector<int4> leaf;
+        std::vector<int32_t> leaf_t0, stack;
+        tiles.clear();
+        for (int i = 0; i < n_made; ++i) {
+            stack.assign(1, leaf_node[i]);
+            while (!stack.empty()) {
+                const TreeNode &h = tree[stack.back()];
+                stack.pop_back();
+                if (h.c0 >= 0) {
+                    stack.push_back(h.c0);
+                    stack.push_back(h.c1);
+                    continue;
+                }
+                leaf_t0.push_back((int32_t)tiles.size());
+                tiles.insert(tiles.end(), (h.count + tile_keys - 1) / tile_keys,
+                             (int32_t)leaf.size());
+                leaf.push_back(make_int4(h.buf, h.start, h.count, i));
+            }
+        }
+        const int n_leaf = (int)leaf.size();
+        DBuf dleaf = dalloc(n_leaf * sizeof(int4)), dt0 = dalloc(n_leaf * sizeof(int32_t));
+        DBuf dlt = dalloc(tiles.size() * sizeof(int32_t));
+        upload(c, dleaf.p, leaf.data(), n_leaf * sizeof(int4));
+        upload(c, dt0.p, leaf_t0.data(), n_leaf * sizeof(int32_t));
+        upload(c, dlt.p, tiles.data(), tiles.size() * sizeof(int32_t));
+        KScope ks(c, "cluster_label");
+        const int nt = (int)tiles.size();
+        k_cl_leaf_label<<<std::min(nt, c->sm_count * 4), kClThreads, 0, c->stream>>>(
+            U, pord, dleaf.as<int4>(), dt0.as<int32_t>(), dlt.as<int32_t>(), nt, tile_keys, plab);
+    }
     std::vector<Cluster> cl(n_made);
-    for (int i = 0; i < n_made; ++i) cl[i].set(hs[i].s);
+    for (int i = 0; i < n_made; ++i) cl[i].set(tree[leaf_node[i]].s);
     const int n = (int)cl.size();
     // centre values in phantom units, as stored (float32)
     centres.assign(3 * (size_t)n, 0.0);
@@ -723,7 +943,7 @@ void cluster_phantom(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters,
         const float *pc = dcf.as<float>();
         k_cl_model<<<(n + kClThreads - 1) / kClThreads, kClThreads, 0, c->stream>>>(
             n, pc, pc + n, em, fc.as<double>(), den.as<double>());
-        k_cl_ratio<<<gU, kClThreads, 0, c->stream>>>(U, tf.as<float>(), plab, fc.as<double>(),
+        k_cl_ratio<<<grid(c, U), kClThreads, 0, c->stream>>>(U, tf.as<float>(), plab, fc.as<double>(),
                                                      den.as<double>(), em, ratio.as<double>());
     }
     // the new phantom

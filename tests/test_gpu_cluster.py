@@ -104,6 +104,30 @@ def test_cluster_settings_and_early_stop(mrsim, ctx):
         assert np.array_equal(arrays[name], getattr(ph, name))
 
 
+def test_cluster_deep_and_wide_trees(mrsim, ctx):
+    """Splits are computed many at a time and the greedy order is replayed on
+    them: a chain-like tree (geometric dB0 values, every split peels off the
+    top values) and a wide one (1024 clusters of 2048 distinct values) give
+    the sequential result, ids included."""
+    base = mapped_phantom(16, 16, 2, 3, seed=12)
+    i = np.arange(base.K) % 200
+    ph = dataclasses.replace(base, T1=np.full(base.K, 0.8, np.float32),
+                             T2=np.full(base.K, 0.07, np.float32),
+                             dB0=np.ascontiguousarray(0.5 * 1.05 ** i, np.float32))
+    for n in (2, 150):
+        r = oc.cluster_phantom(ph, n)
+        hp, h, m, labels, centres, arrays = gpu_cluster(mrsim, ctx, ph, n)
+        check(r, m, labels, centres, arrays)
+        ctx.free("ph", h)
+        ctx.free("ph", hp)
+    ph = continuous_phantom(32, 32, 2, 3, seed=48)
+    r = oc.cluster_phantom(ph, 1024)
+    hp, h, m, labels, centres, arrays = gpu_cluster(mrsim, ctx, ph, 1024)
+    check(r, m, labels, centres, arrays)
+    ctx.free("ph", h)
+    ctx.free("ph", hp)
+
+
 def test_clustered_phantom_groups_and_signal(mrsim, ctx):
     """The clustered phantom has the group counts of its distinct keys, and its
     grouped simulation matches the oracle's simulation of the oracle's
