@@ -296,7 +296,8 @@ def surrogate_workload(ctx, mrsim, torch):
 
 def multicoil_workload(ctx, mrsim, torch, ph, seq, hp_single, hg_single, steps, n_coils=8):
     """The grouped FSE received by n_coils coils (Eq. 6 with P coils): one
-    preparation step, then one fused pass per coil.  Coil maps from
+    preparation step, then fused passes of up to four coils each (the cell
+    form shares the state evolution between them).  Coil maps from
     mrsim_inputs.coil_maps on a second handle of the same phantom."""
     from mrsim_inputs import coil_maps
     t0 = time.perf_counter()
@@ -324,7 +325,7 @@ def multicoil_workload(ctx, mrsim, torch, ph, seq, hp_single, hg_single, steps, 
     t = e0.elapsed_time(e1) / steps / 1e3
     out = {"coils": n_coils, "fse_grouped_s": round(t, 5),
            "per_coil_ms": round(t / n_coils * 1e3, 3), "coil_maps_host_s": round(maps_s, 2),
-           "note": "one preparation step and one fused pass per coil; coil signals "
+           "note": "one preparation step and fused passes of up to 4 coils; coil signals "
                    "checked against the FP64 oracle in tests/test_gpu_coils.py"}
     ctx.free("grp", hg)
     ctx.free("seq", hs)
@@ -774,6 +775,32 @@ def main():
         fse_plain_s = timed_once(lambda: step(hs_f, None, sig_f, mrsim.PLAIN), prof_fse_plain)
         fse_plain_sig = sig_f.cpu().numpy().view(np.complex128).copy()
 
+    # ---- reproducible sums (fixed-point block and signal sums): cost and
+    # bit-identical repeats, beside two repeats of the default path ----
+    def two_runs():
+        step(hs_f, hg_f, sig_f)
+        first = sig_f.cpu().numpy().copy()
+        step(hs_f, hg_f, sig_f)
+        return first, sig_f.cpu().numpy().copy()
+
+    d1, d2 = two_runs()
+    mrsim.mrsim_set_reproducible(ctx.h, True)
+    try:
+        r1, r2 = two_runs()
+        repro_s = timed_once(lambda: [step(hs_f, hg_f, sig_f) for _ in range(a.steps)]) / a.steps
+    finally:
+        mrsim.mrsim_set_reproducible(ctx.h, False)
+    rv, dv = r1.view(np.complex128), d1.view(np.complex128)
+    reproducible = {
+        "fse_grouped_ms": round(repro_s * 1e3, 3),
+        "default_fse_grouped_ms": round(fse_s * 1e3, 3),
+        "cost_vs_default": round(repro_s / fse_s, 3),
+        "repeat_bit_identical": bool(np.array_equal(r1, r2)),
+        "default_repeat_bit_identical": bool(np.array_equal(d1, d2)),
+        "default_repeat_max_abs_diff": float(np.max(np.abs(d1 - d2))),
+        "rel_l2_vs_default": float(np.linalg.norm(rv - dv) / np.linalg.norm(dv)),
+    }
+
     # ---- end to end through the public API from pinned host buffers ----
     pin = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).pin_memory()
            for k, v in dict(x=ph.x, y=ph.y, z=ph.z, T1=ph.T1, T2=ph.T2, dB0=ph.dB0,
@@ -975,6 +1002,7 @@ def main():
         "batch64": batch,
         "surrogate": surrogate,
         "multicoil": multicoil,
+        "reproducible": reproducible,
         "recon": recon,
         "radial": radial,
         "clustering": clustering,

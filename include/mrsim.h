@@ -412,6 +412,25 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
 int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
 int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
 
+/* Reproducible sums (not part of the paper's method; an option for users who
+ * compare outputs bit for bit).  With on = 1, every later mrsim_run of the
+ * context forms the block sums of Eq. 9 and the signal sums of Eqs. 6 / 8 / 10
+ * in 64-bit fixed point: each contribution v, which the default path adds with
+ * FP64 atomics in an order that varies from run to run, is added as the
+ * integer rint(v 2^e), and integer addition does not depend on the order.  e
+ * is chosen per phantom from B = sum_k (|M0_k| + |M_init_k|) max(1, max_j
+ * |S_jk|), which bounds every sum (the magnetisation's norm never exceeds
+ * |M_init| + |M0|): 2^e B < 2^56.  Each contribution is then rounded to 2^-e
+ * (about 5e-10 for a 27.5M-isochromat phantom of M0 <= 1; the FP64 path's
+ * tolerances hold).  Repeated runs, in FP32 or FP64, give identical signals,
+ * and one receive coil with S = 1 gives the signal of no coil (FP32 grouped
+ * runs then hold 4 isochromats per thread in the cell form, the receive-coil
+ * width, whatever MRSIM_TUNE_CELL_NI says).  mrsim_run_batch and
+ * mrsim_adc_grouped_noalloc keep FP64 atomics.  Default 0.
+ * Errors: MRSIM_EINVAL (NULL ctx / on, or on not 0 or 1). */
+int mrsim_set_reproducible(mrsim_ctx *ctx, int on);
+int mrsim_get_reproducible(const mrsim_ctx *ctx, int *on);
+
 /* Autotuner: for the given problem and mode, time every allowed value of each
  * launch parameter the mode uses (one warm-up run plus `reps` timed runs of
  * mrsim_run per value, CUDA events on the context stream, one parameter at a

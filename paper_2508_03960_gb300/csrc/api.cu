@@ -383,6 +383,7 @@ void run_plain(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, bool
     const mrsim_seq &dev = *s;
     const int64_t Kp = plane_stride(K);
     PlainState st = plain_state(ph, M, M + Kp, M + 2 * Kp);
+    st.fx = c->fx;
     launch_init_state<R>(c, st, ph->has_M_init ? ph->M_init.as<float>() : nullptr);
     std::vector<DBuf> cache(s->n_content);
     double mom[3] = {0, 0, 0}, tau = 0.0;
@@ -581,7 +582,10 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
     if constexpr (sizeof(R) == 4) {
         // cell form (see CellArgs): every RF type and every with-ADC type must
         // be constant inside a cell (primary, secondary or no-grads)
-        const int ni = c->tune[MRSIM_TUNE_CELL_NI];
+        // (reproducible sums: 4 per thread, the width of the receive-coil
+        // kernels, so that a unit coil gives the same bits as none)
+        const int ni = c->fx > 0.0 && c->tune[MRSIM_TUNE_CELL_NI] != 0
+                           ? 4 : c->tune[MRSIM_TUNE_CELL_NI];
         P.cell_w = ni == 8 ? 1 : 0;
         const int r = g->secondary;
         P.cell = allow_cell && ni != 0 && !P.direct && g->ax_ok && p >= G_X && p <= G_Z &&
@@ -792,6 +796,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                                c->stream));
     const int64_t Kp = plane_stride(K);
     PlainState st = sorted_state(g, M, M + Kp, M + 2 * Kp);
+    st.fx = c->fx;
     const int n_ev = (int)P.ev.size();
     EvAdv *d_adv = (EvAdv *)scratch(c, 14, n_ev * sizeof(EvAdv));
     void *d_P = scratch(c, 15, (P.direct ? 1 : (size_t)n_ev * std::max<int64_t>(P.Gp, 1)) * 4 *
@@ -805,6 +810,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     if (g->has_M_init) launch_init_state<R>(c, st, g->M_init.as<float>());
     FusedArgs<R> fa = fused_args<R>(g, P.p, M, M + Kp, M + 2 * Kp, T_tab, d_P, Ablk);
     fa.direct = P.direct ? 1 : 0;
+    fa.fx = c->fx;
     if (P.ax) {
         fa.ax = 1;
         fa.aidx = g->ax_idx.as<int32_t>();
@@ -850,6 +856,7 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             ca.C_tab = C_tab;
             ca.P_raw = d_P;
             ca.Ablk = Ablk;
+            ca.fx = c->fx;
             ca.qtab = fa.qtab;
             int nf = 0;
             for (int a = 0; a < 3; ++a)
@@ -1275,6 +1282,7 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
         if (n_coils == 0) {
             ph->coils.reset();
             ph->n_coils = 0;
+            ph->sum_bound = -1.0;
             return;
         }
         const int64_t n = 2 * (int64_t)n_coils * ph->K;
@@ -1296,6 +1304,7 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
         if (h) fail(MRSIM_EINVAL, "coil sensitivities have a non-finite value");
         ph->coils = std::move(d);
         ph->n_coils = n_coils;
+        ph->sum_bound = -1.0;
     });
 }
 
@@ -1526,6 +1535,19 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         const bool dev_out = (out_flags & MRSIM_OUT_DEVICE) != 0;
         double *d_sig = dev_out ? signal : (double *)scratch(c, 8, nsig * 2 * sizeof(double));
         MRSIM_CUDA(cudaMemsetAsync(d_sig, 0, nsig * 2 * sizeof(double), c->stream));
+        // reproducible sums: the signal and block-sum buffers hold integers
+        // rint(v fx) during the run, fx = 2^e with 2^56 above any sum's bound
+        // (room for 128 times the bound), converted back at the end
+        struct FxScope {
+            mrsim_ctx *c;
+            ~FxScope() { c->fx = 0.0; }
+        } fx_scope{c};
+        c->fx = 0.0;
+        if (c->repro) {
+            int ex = 0;
+            std::frexp(sum_bound(c, ph) * (1.0 + 1e-9) + 1.0, &ex);
+            c->fx = std::ldexp(1.0, 56 - ex);
+        }
         const size_t esz = precision == MRSIM_FP64 ? 8 : 4;
         const int64_t Kp = plane_stride(K);
         void *Mst = scratch(c, 9, 3 * Kp * esz);
@@ -1550,12 +1572,26 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
                                            cudaMemcpyDeviceToHost, c->stream));
             sync(c);
         }
+        if (c->fx > 0.0) launch_fixed_to_double(c, d_sig, nsig * 2, c->fx);
         if (!dev_out && ns > 0)
             MRSIM_CUDA(cudaMemcpyAsync(signal, d_sig, ns * std::max(ph->n_coils, 1) * 2 *
                                                           sizeof(double),
                                        cudaMemcpyDeviceToHost, c->stream));
         sync(c);
     });
+}
+
+int mrsim_set_reproducible(mrsim_ctx *c, int on) {
+    if (!c) return MRSIM_EINVAL;
+    if (on != 0 && on != 1) return set_err(c, MRSIM_EINVAL, "reproducible is 0 or 1");
+    c->repro = on;
+    return MRSIM_OK;
+}
+
+int mrsim_get_reproducible(const mrsim_ctx *c, int *on) {
+    if (!c || !on) return MRSIM_EINVAL;
+    *on = c->repro;
+    return MRSIM_OK;
 }
 
 int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,

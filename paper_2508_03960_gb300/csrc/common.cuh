@@ -143,6 +143,22 @@ struct GSampleD {
 // ------------------------------------------------------------------------
 #ifdef __CUDACC__
 
+// Reproducible sums.  With fx > 0 (a power of two) a sum buffer holds 64-bit
+// integers and every contribution v is added as rint(v fx): integer addition
+// is associative, so the total does not depend on the order in which threads
+// add (FP64 atomics make the last bits vary from run to run).  The buffer is
+// read back as i / fx.  fx is chosen so that no partial sum can reach 2^62.
+__device__ __forceinline__ void sum_add(double *p, double v, double fx) {
+    if (fx > 0.0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                  (unsigned long long)__double2ll_rn(v * fx));
+    else
+        atomicAdd(p, v);
+}
+__device__ __forceinline__ double sum_get(const double *p, double fx) {
+    return fx > 0.0 ? (double)*reinterpret_cast<const long long *>(p) * (1.0 / fx) : *p;
+}
+
 // fractional part (turns) of a * (hi + lo), a float32 value times a
 // double-length constant: the product a*hi is split exactly with one FMA.
 __device__ __forceinline__ float turns_prod(float a, float hi, float lo) {

@@ -77,6 +77,10 @@ struct mrsim_ctx {
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
     int tune[7] = {4, 2, 2, 0, 8, 8, 1};  // indexed by the MRSIM_TUNE_* parameters
+    // reproducible sums (mrsim_set_reproducible) and, during a run, the
+    // fixed-point scale of the sum buffers (0: FP64 atomics)
+    int repro = 0;
+    double fx = 0.0;
 };
 
 struct mrsim_phantom_t {
@@ -87,6 +91,7 @@ struct mrsim_phantom_t {
     bool has_b1 = false, has_M_init = false;
     int n_coils = 0;    // receive coils attached by mrsim_coils (0: one coil, S = 1)
     mrsim::DBuf coils;  // float [n_coils][2][K] (re, im planes), phantom order
+    double sum_bound = -1.0;  // bound on |any signal or block sum| (< 0: not formed yet)
 };
 
 namespace mrsim {
@@ -275,6 +280,7 @@ struct PlainState {
     // receive-coil sensitivity (re, im planes, same order as x) for the with-ADC
     // kernels, or null for S = 1
     const float *coil_re = nullptr, *coil_im = nullptr;
+    double fx = 0.0;  // fixed-point scale of the signal sums (0: FP64 atomics)
 };
 template <typename R>
 void launch_init_state(mrsim_ctx *c, const PlainState &s, const float *M_init);
@@ -284,6 +290,12 @@ void launch_plain_rf(mrsim_ctx *c, const PlainState &s, const void *segs, int n_
 template <typename R>
 void launch_plain_adc(mrsim_ctx *c, const PlainState &s, const void *segs, int n_seg,
                       int64_t n_samples, const void *adv, double *signal, int ctas_per_sm = 2);
+// Reproducible sums: a bound on |any signal or block sum| of a run on the
+// phantom, sum_k (|M0_k| + |M_init_k|) max(1, max_j |S_jk|) (the magnetisation
+// never exceeds |M_init| + |M0| in norm), formed in a fixed order; and the
+// in-place conversion of n fixed-point sums (integers i) to i / fx.
+double sum_bound(mrsim_ctx *c, const mrsim_phantom_t *ph);
+void launch_fixed_to_double(mrsim_ctx *c, double *buf, int64_t n, double fx);
 template <typename R>
 void launch_advance(mrsim_ctx *c, const PlainState &s, const void *adv);
 template <typename R>
@@ -334,6 +346,7 @@ struct FusedArgs {
     int ax_sh[3];            // bit position of each axis' index in aidx
     // receive-coil sensitivity (re, im planes, layout order) or null for S = 1
     const float *coil_re, *coil_im;
+    double fx;               // fixed-point scale of the block sums (0: FP64 atomics)
 };
 // Cell mode of the fused kernel (FP32): every thread holds isochromats of one
 // cell, so the positions on the primary axis and (if any) the secondary axis,
@@ -379,6 +392,7 @@ struct CellArgs {
     int64_t ablk_stride;
     // phasor flags of the form (kernels compiled for coils read them here)
     int rfq, adq, rb;
+    double fx;                // fixed-point scale of the block sums (0: FP64 atomics)
 };
 // Which per-isochromat and per-thread phasors a cell-form launch applies
 // (fixed for the whole span, so the kernel is specialised on them).
@@ -444,6 +458,7 @@ struct GSigJob {
     GSigTables<R> tab;
     const double *Ablk;
     double *signal;
+    double fx;  // fixed-point scale of the sums (0: FP64 atomics)
 };
 template <typename R>
 void launch_precompute_batch(mrsim_ctx *c, const PrecompArgs *d_tabs, const int64_t *d_off,

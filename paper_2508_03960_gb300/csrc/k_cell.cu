@@ -67,8 +67,8 @@ __device__ __forceinline__ void free_phasor(const float2 *qtab, const int (&qf)[
     s = q0.y;
     if constexpr (NF == 2) {
         const float2 q1 = __ldg(qtab + qf[1] + f1);
-        const float nc = c * q1.x - s * q1.y;
-        s = s * q1.x + c * q1.y;
+        const float nc = __fmaf_rn(c, q1.x, -__fmul_rn(s, q1.y));
+        s = __fmaf_rn(s, q1.x, __fmul_rn(c, q1.y));
         c = nc;
     }
 }
@@ -198,12 +198,14 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
             if (sr != 0.0f || si != 0.0f) {
                 const int64_t o =
                     2 * (a.ablk_stride * j + (int64_t)sm.batch_win[b] + g_first + slot);
-                if (slot != 0 && slot != S - 1) {
+                if (slot != 0 && slot != S - 1 && a.fx == 0.0) {
                     // a group strictly inside the CTA has no other contributor
                     *reinterpret_cast<double2 *>(&a.Ablk[o]) = make_double2(sr, si);
                 } else {
-                    atomicAdd(&a.Ablk[o], (double)sr);
-                    atomicAdd(&a.Ablk[o + 1], (double)si);
+                    // (reproducible sums: the non-uniform warps add theirs
+                    // directly, so every slot is added)
+                    sum_add(&a.Ablk[o], (double)sr, a.fx);
+                    sum_add(&a.Ablk[o + 1], (double)si, a.fx);
                 }
             }
             // cleared even when the total is zero: staged partials can cancel
@@ -240,11 +242,23 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
             }
             const int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
             if ((lane == 31 || nk != key) && key != kPad) {
-                float *accb = sm.acc + 2 * NC * (nb * S + (key - g_first));
+                if (a.fx > 0.0) {
+                    // reproducible sums: the run's total goes to the block sum
+                    // as an integer (the shared accumulator's float atomics
+                    // would depend on the order of the warps)
 #pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    atomicAdd(accb + 2 * j, sr[j]);
-                    atomicAdd(accb + 2 * j + 1, si[j]);
+                    for (int j = 0; j < NC; ++j) {
+                        const int64_t o = 2 * (a.ablk_stride * j + (int64_t)win + key);
+                        sum_add(&a.Ablk[o], (double)sr[j], a.fx);
+                        sum_add(&a.Ablk[o + 1], (double)si[j], a.fx);
+                    }
+                } else {
+                    float *accb = sm.acc + 2 * NC * (nb * S + (key - g_first));
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) {
+                        atomicAdd(accb + 2 * j, sr[j]);
+                        atomicAdd(accb + 2 * j + 1, si[j]);
+                    }
                 }
             }
         }
@@ -285,14 +299,15 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
                     if (rfq) {
                         float c, s;
                         free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
-                        const float nx = c * x + s * y;  // (c - i s) (x + i y)
-                        y = c * y - s * x;
+                        // (c - i s) (x + i y)
+                        const float nx = __fmaf_rn(c, x, __fmul_rn(s, y));
+                        y = __fmaf_rn(c, y, -__fmul_rn(s, x));
                         x = nx;
                     }
                     const float z = mz[i], m0 = M0[i];
-                    mx[i] = r0.x * x + r0.y * y + r0.z * z + r0.w * m0;
-                    my[i] = r1.x * x + r1.y * y + r1.z * z + r1.w * m0;
-                    mz[i] = r2.x * x + r2.y * y + r2.z * z + r2.w * m0;
+                    mx[i] = __fmaf_rn(r0.w, m0, __fmaf_rn(r0.z, z, __fmaf_rn(r0.y, y, __fmul_rn(r0.x, x))));
+                    my[i] = __fmaf_rn(r1.w, m0, __fmaf_rn(r1.z, z, __fmaf_rn(r1.y, y, __fmul_rn(r1.x, x))));
+                    mz[i] = __fmaf_rn(r2.w, m0, __fmaf_rn(r2.z, z, __fmaf_rn(r2.y, y, __fmul_rn(r2.x, x))));
                 }
                 if (kind == CE_END && a.Mx) {
 #pragma unroll
@@ -315,24 +330,29 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
 #pragma unroll
                 for (int j = 0; j < NC; ++j) sr[j] = si[j] = 0.0f;
                 const int qf[2] = {ev1.x, ev1.y};
+                // (roundings written out: every instantiation, with coils or
+                // without, forms the same products and sums, so a unit coil
+                // gives the bits of none)
 #pragma unroll
                 for (int i = 0; i < NI; ++i) {
                     float vr = mx[i], vi = my[i];
                     if (adq) {
                         float c, s;
                         free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
-                        vr = c * mx[i] + s * my[i];
-                        vi = c * my[i] - s * mx[i];
+                        vr = __fmaf_rn(c, mx[i], __fmul_rn(s, my[i]));
+                        vi = __fmaf_rn(c, my[i], -__fmul_rn(s, mx[i]));
                     }
                     if constexpr (PC > 0) {
 #pragma unroll
                         for (int j = 0; j < NC; ++j) {
-                            sr[j] += sre[j][i] * vr - sim[j][i] * vi;
-                            si[j] += sre[j][i] * vi + sim[j][i] * vr;
+                            sr[j] = __fadd_rn(sr[j], __fmaf_rn(sre[j][i], vr,
+                                                               -__fmul_rn(sim[j][i], vi)));
+                            si[j] = __fadd_rn(si[j], __fmaf_rn(sre[j][i], vi,
+                                                               __fmul_rn(sim[j][i], vr)));
                         }
                     } else {
-                        sr[0] += vr;
-                        si[0] += vi;
+                        sr[0] = __fadd_rn(sr[0], vr);
+                        si[0] = __fadd_rn(si[0], vi);
                     }
                 }
                 // the factor shared by the thread's isochromats: the group's P
@@ -340,14 +360,14 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
                 float fr = P.x, fi = P.y;
                 if (rb) {
                     const float2 q = __ldg(qtab + ev1.z + ridx);
-                    const float tr = fr * q.x + fi * q.y;  // P exp(-i psi)
-                    fi = fi * q.x - fr * q.y;
+                    const float tr = __fmaf_rn(fr, q.x, __fmul_rn(fi, q.y));  // P exp(-i psi)
+                    fi = __fmaf_rn(fi, q.x, -__fmul_rn(fr, q.y));
                     fr = tr;
                 }
 #pragma unroll
                 for (int j = 0; j < NC; ++j) {
-                    const float nr = fr * sr[j] - fi * si[j];
-                    si[j] = fr * si[j] + fi * sr[j];
+                    const float nr = __fmaf_rn(fr, sr[j], -__fmul_rn(fi, si[j]));
+                    si[j] = __fmaf_rn(fr, si[j], __fmul_rn(fi, sr[j]));
                     sr[j] = nr;
                 }
                 if (kind == CE_ADC) {
@@ -359,8 +379,8 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
 #pragma unroll
                     for (int j = 0; j < NC; ++j) {
                         const int64_t o = 2 * (a.ablk_stride * j + (int64_t)ev0.z + g);
-                        atomicAdd(&a.Ablk[o], (double)sr[j]);
-                        atomicAdd(&a.Ablk[o + 1], (double)si[j]);
+                        sum_add(&a.Ablk[o], (double)sr[j], a.fx);
+                        sum_add(&a.Ablk[o + 1], (double)si[j], a.fx);
                     }
                 }
             }

@@ -442,12 +442,14 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                 if constexpr (!DIRECT) P = load4(Pt + batch_prow[b] + g_first + slot);
                 const int64_t o = 2 * ((int64_t)batch_win[b] + g_first + slot);
                 const double vr = (double)(P.x * sr - P.y * si), vi = (double)(P.x * si + P.y * sr);
-                if (slot != 0 && slot != S - 1) {
+                if (slot != 0 && slot != S - 1 && a.fx == 0.0) {
                     // a group strictly inside the chunk has no other contributor
                     *reinterpret_cast<double2 *>(&Ablk[o]) = make_double2(vr, vi);
                 } else {
-                    atomicAdd(&Ablk[o], vr);
-                    atomicAdd(&Ablk[o + 1], vi);
+                    // (reproducible sums: the non-uniform warps add theirs
+                    // directly, so every slot is added)
+                    sum_add(&Ablk[o], vr, a.fx);
+                    sum_add(&Ablk[o + 1], vi, a.fx);
                 }
             }
             // cleared even when the slot's total is zero: the staged partial
@@ -508,8 +510,19 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                     }
                     const int32_t nk = __shfl_down_sync(0xffffffffu, key[i], 1);
                     if ((lane == 31 || nk != key[i]) && key[i] != 0x7fffffff) {
-                        atomicAdd(&accb[2 * (key[i] - g_first)], sr);
-                        atomicAdd(&accb[2 * (key[i] - g_first) + 1], si);
+                        if (a.fx > 0.0) {
+                            // reproducible sums: the run's term goes to the
+                            // block sum as an integer (the shared accumulator's
+                            // atomics would depend on the order of the warps)
+                            R4<R> P{(R)1, (R)0, (R)1, (R)0};
+                            if constexpr (!DIRECT) P = load4(Pt + ev.prow + key[i]);
+                            const int64_t o = 2 * ((int64_t)ev.win + key[i]);
+                            sum_add(&Ablk[o], (double)(P.x * sr - P.y * si), a.fx);
+                            sum_add(&Ablk[o + 1], (double)(P.x * si + P.y * sr), a.fx);
+                        } else {
+                            atomicAdd(&accb[2 * (key[i] - g_first)], sr);
+                            atomicAdd(&accb[2 * (key[i] - g_first) + 1], si);
+                        }
                     }
                 }
             }
@@ -529,8 +542,8 @@ __device__ __forceinline__ void fused_chunk(const FusedArgs<R> &a, int64_t blk,
                     R4<R> P{(R)1, (R)0, (R)1, (R)0};
                     if constexpr (!DIRECT) P = load4(Pt + ev.prow + s.pofs[i]);
                     const int64_t o = 2 * ((int64_t)ev.win + g[k]);
-                    atomicAdd(&Ablk[o], (double)(P.x * vr[i] - P.y * vi[i]));
-                    atomicAdd(&Ablk[o + 1], (double)(P.x * vi[i] + P.y * vr[i]));
+                    sum_add(&Ablk[o], (double)(P.x * vr[i] - P.y * vi[i]), a.fx);
+                    sum_add(&Ablk[o + 1], (double)(P.x * vi[i] + P.y * vr[i]), a.fx);
                 }
             }
         }
@@ -694,7 +707,8 @@ constexpr int kRun = 8;  // samples per thread on uniform windows
 __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, int nsb,
                                                   const GSampleF *smp,
                                                   const GSigTables<float> &tab,
-                                                  const double *Ablk, double *signal) {
+                                                  const double *Ablk, double *signal,
+                                                  double fx) {
     __shared__ float s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
     __shared__ float s_pos2[kGTile];
     __shared__ double s_red[2][kThreads * kRun];
@@ -730,8 +744,8 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
             s_pos2[t] = pos2[g0 + t];
             s_dB0[t] = dB0[g0 + t];
             s_rT2[t] = rT2[g0 + t];
-            s_ar[t] = (float)Ablk[2 * (w.ablk + g0 + t)];
-            s_ai[t] = (float)Ablk[2 * (w.ablk + g0 + t) + 1];
+            s_ar[t] = (float)sum_get(&Ablk[2 * (w.ablk + g0 + t)], fx);
+            s_ai[t] = (float)sum_get(&Ablk[2 * (w.ablk + g0 + t) + 1], fx);
         }
         __syncthreads();
         if (len > 0) {
@@ -785,8 +799,8 @@ __device__ __forceinline__ void group_signal_runs(const GWin &w, const int4 b, i
             sr += s_red[0][l * (NRp * kRun) + q];
             si += s_red[1][l * (NRp * kRun) + q];
         }
-        atomicAdd(&signal[2 * ((int64_t)b.y + q)], sr);
-        atomicAdd(&signal[2 * ((int64_t)b.y + q) + 1], si);
+        sum_add(&signal[2 * ((int64_t)b.y + q)], sr, fx);
+        sum_add(&signal[2 * ((int64_t)b.y + q) + 1], si, fx);
     }
     __syncthreads();
 }
@@ -797,7 +811,7 @@ template <typename R>
 __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 b,
                                                    const typename GS<R>::S *smp,
                                                    const GSigTables<R> &tab, const double *Ablk,
-                                                   double *signal) {
+                                                   double *signal, double fx) {
     __shared__ R s_pos[kGTile], s_dB0[kGTile], s_rT2[kGTile], s_ar[kGTile], s_ai[kGTile];
     __shared__ R s_pos2[kGTile];
     __shared__ double s_red[2][kThreads];
@@ -808,7 +822,7 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
     const int nsb = (int)min((long long)kThreads, w.sample0 + w.n_samples - (long long)b.y);
     if constexpr (sizeof(R) == 4) {
         if (w.uniform) {
-            group_signal_runs(w, b, nsb, smp, tab, Ablk, signal);
+            group_signal_runs(w, b, nsb, smp, tab, Ablk, signal, fx);
             return;
         }
     }
@@ -832,8 +846,8 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
             s_pos2[t] = pos2[g0 + t];
             s_dB0[t] = dB0[g0 + t];
             s_rT2[t] = rT2[g0 + t];
-            s_ar[t] = (R)Ablk[2 * (w.ablk + g0 + t)];
-            s_ai[t] = (R)Ablk[2 * (w.ablk + g0 + t) + 1];
+            s_ar[t] = (R)sum_get(&Ablk[2 * (w.ablk + g0 + t)], fx);
+            s_ai[t] = (R)sum_get(&Ablk[2 * (w.ablk + g0 + t) + 1], fx);
         }
         __syncthreads();
         R pr = 0, pi = 0;
@@ -862,8 +876,8 @@ __device__ __forceinline__ void group_signal_block(const GWin *wins, const int4 
         }
     }
     if (act && sl == 0) {
-        atomicAdd(&signal[2 * s_idx], accr);
-        atomicAdd(&signal[2 * s_idx + 1], acci);
+        sum_add(&signal[2 * s_idx], accr, fx);
+        sum_add(&signal[2 * s_idx + 1], acci, fx);
     }
     __syncthreads();
 }
@@ -872,8 +886,9 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_group_signal(const GWin *wins, const int4 *blk,
                                                            const typename GS<R>::S *smp,
                                                            GSigTables<R> tab,
-                                                           const double *Ablk, double *signal) {
-    group_signal_block<R>(wins, blk[blockIdx.x], smp, tab, Ablk, signal);
+                                                           const double *Ablk, double *signal,
+                                                           double fx) {
+    group_signal_block<R>(wins, blk[blockIdx.x], smp, tab, Ablk, signal, fx);
 }
 
 template <typename R>
@@ -882,7 +897,7 @@ __global__ void __launch_bounds__(kThreads) k_group_signal_batch(const GSigJob<R
                                                                  const int *blk_job) {
     const GSigJob<R> &j = jobs[blk_job[blockIdx.x]];
     group_signal_block<R>(j.wins, blk[blockIdx.x], (const typename GS<R>::S *)j.samples, j.tab,
-                          j.Ablk, j.signal);
+                          j.Ablk, j.signal, j.fx);
 }
 
 }  // namespace
@@ -1038,7 +1053,7 @@ void launch_group_signal(mrsim_ctx *c, const GWin *d_win, const int4 *d_blk, int
     if (n_blk <= 0) return;
     KScope ks(c, sizeof(R) == 4 ? "group_signal_f32" : "group_signal_f64");
     k_group_signal<R><<<n_blk, kThreads, 0, c->stream>>>(
-        d_win, d_blk, (const typename GS<R>::S *)d_samples, tab, Ablk, signal);
+        d_win, d_blk, (const typename GS<R>::S *)d_samples, tab, Ablk, signal, c->fx);
 }
 
 template void launch_event_table<float>(mrsim_ctx *, const EvAdv *, int, int64_t,

@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kThreads) k_plain_adc(PlainState s,
             sr += acc[w][t][0];
             si += acc[w][t][1];
         }
-        atomicAdd(&signal[2 * (s_lo + t)], sr);
-        atomicAdd(&signal[2 * (s_lo + t) + 1], si);
+        sum_add(&signal[2 * (s_lo + t)], sr, s.fx);
+        sum_add(&signal[2 * (s_lo + t) + 1], si, s.fx);
     }
 }
 
@@ -484,6 +484,75 @@ void launch_gather_out(mrsim_ctx *c, int64_t K, const void *Mx, const void *My, 
     else
         k_gather_out<float><<<grid_stride_blocks(c, K), kThreads, 0, c->stream>>>(
             K, (const float *)Mx, (const float *)My, (const float *)Mz, perm, out);
+}
+
+namespace {
+
+constexpr int kBoundBlocks = 256;
+
+// per isochromat (|M0| + |M_init|) max(1, max_j |S_j|) in FP64; each thread
+// takes a fixed set of isochromats and each block sums its threads in a
+// fixed tree, so the partials do not depend on scheduling
+__global__ void __launch_bounds__(kThreads) k_sum_bound(int64_t K, const float *M0,
+                                                        const float *M_init, const float *coils,
+                                                        int n_coils, double *part) {
+    __shared__ double red[kThreads];
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double m = fabs((double)M0[k]);
+        if (M_init) {
+            const double a = M_init[k], b = M_init[K + k], c = M_init[2 * K + k];
+            m += sqrt(a * a + b * b + c * c);
+        }
+        double s = 1.0;
+        for (int j = 0; j < n_coils; ++j) {
+            const double re = coils[2 * K * j + k], im = coils[2 * K * j + K + k];
+            s = fmax(s, sqrt(re * re + im * im));
+        }
+        acc += m * s;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_fixed_to_double(double *buf, int64_t n, double inv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const long long v = reinterpret_cast<const long long *>(buf)[i];
+        buf[i] = (double)v * inv;
+    }
+}
+
+}  // namespace
+
+double sum_bound(mrsim_ctx *c, const mrsim_phantom_t *ph) {
+    if (ph->sum_bound >= 0.0) return ph->sum_bound;
+    double *part = (double *)scratch(c, 26, kBoundBlocks * sizeof(double));
+    {
+        KScope ks(c, "sum_bound");
+        k_sum_bound<<<kBoundBlocks, kThreads, 0, c->stream>>>(
+            ph->K, ph->M0.as<float>(), ph->has_M_init ? ph->M_init.as<float>() : nullptr,
+            ph->n_coils > 0 ? ph->coils.as<float>() : nullptr, ph->n_coils, part);
+    }
+    double h[kBoundBlocks];
+    MRSIM_CUDA(cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    double b = 0.0;
+    for (int i = 0; i < kBoundBlocks; ++i) b += h[i];
+    const_cast<mrsim_phantom_t *>(ph)->sum_bound = b;
+    return b;
+}
+
+void launch_fixed_to_double(mrsim_ctx *c, double *buf, int64_t n, double fx) {
+    if (n <= 0) return;
+    KScope ks(c, "fixed_to_double");
+    k_fixed_to_double<<<grid_stride_blocks(c, n), kThreads, 0, c->stream>>>(buf, n, 1.0 / fx);
 }
 
 #define INST(R)                                                                              \

@@ -39,6 +39,7 @@ EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
            "mrsim_profile_reset",
            "mrsim_profile_get", "mrsim_launch_count", "mrsim_adc_grouped_noalloc",
            "mrsim_set_tuning", "mrsim_get_tuning", "mrsim_autotune",
+           "mrsim_set_reproducible", "mrsim_get_reproducible",
            "mrsim_surrogate_train", "mrsim_surrogate_stats", "mrsim_surrogate_use",
            "mrsim_surrogate_check", "mrsim_surrogate_infer",
            "mrsim_surrogate_eval", "mrsim_free_surrogate",
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mrsim_adc_grouped_noalloc": (I, [I64, P, P, P, ctypes.c_int32, P, P, P, I64, P, P, P, P]),
         "mrsim_set_tuning": (I, [P, I, I]),
         "mrsim_get_tuning": (I, [P, I, P]),
+        "mrsim_set_reproducible": (I, [P, I]),
+        "mrsim_get_reproducible": (I, [P, P]),
         "mrsim_autotune": (I, [P, P, P, P, I, I, I]),
         "mrsim_surrogate_train": (I, [P, P, P, P, I64, I, I, ctypes.c_double, ctypes.c_uint64,
                                       ctypes.c_double, PP]),
@@ -346,6 +349,18 @@ def mrsim_get_tuning(ctx, param) -> int:
     if rc:
         raise MrsimError(rc, "mrsim_get_tuning")
     return v.value
+
+
+def mrsim_set_reproducible(ctx, on):
+    _check(ctx, lib().mrsim_set_reproducible(ctx, int(on)), "mrsim_set_reproducible")
+
+
+def mrsim_get_reproducible(ctx) -> bool:
+    v = ctypes.c_int()
+    rc = lib().mrsim_get_reproducible(ctx, ctypes.byref(v))
+    if rc:
+        raise MrsimError(rc, "mrsim_get_reproducible")
+    return bool(v.value)
 
 
 def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):

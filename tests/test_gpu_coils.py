@@ -107,16 +107,28 @@ def test_coils_with_fallback_spans_and_initial_state(mrsim, ctx, precision):
         assert float(np.max(np.abs(M - Mref))) <= (1e-7 if precision else 1e-4)
 
 
-def test_unit_coil_equals_no_coil(mrsim, ctx):
+@pytest.mark.parametrize("reproducible", [False, True])
+def test_unit_coil_equals_no_coil(mrsim, ctx, reproducible):
+    """With reproducible sums the order of the atomics no longer matters and
+    a unit coil gives exactly the signal of none; otherwise up to 1e-6."""
     ph = configs.small_phantom(16, 16, 2)
     seq = spin_echo_2d(n_ro=16, n_pe=8, n_tr=2)
     unit = np.zeros((1, 2, ph.K), np.float32)
     unit[0, 0] = 1.0
-    for mode in (mrsim.GROUPED, mrsim.PLAIN):
-        single, _ = run(mrsim, ctx, ph, seq, mode, 0)
-        coil, _ = run(mrsim, ctx, dataclasses.replace(ph, coils=unit), seq, mode, 0)
-        assert coil.shape == (1, seq.n_samples)
-        assert oracle.rel_l2(coil[0], single) <= 1e-6
+    mrsim.mrsim_set_reproducible(ctx.h, reproducible)
+    try:
+        for mode in (mrsim.GROUPED, mrsim.PLAIN):
+            for precision in (0, 1):
+                single, _ = run(mrsim, ctx, ph, seq, mode, precision)
+                coil, _ = run(mrsim, ctx, dataclasses.replace(ph, coils=unit), seq, mode,
+                              precision)
+                assert coil.shape == (1, seq.n_samples)
+                if reproducible:
+                    assert np.array_equal(coil[0], single), (mode, precision)
+                else:
+                    assert oracle.rel_l2(coil[0], single) <= 1e-6
+    finally:
+        mrsim.mrsim_set_reproducible(ctx.h, False)
 
 
 def test_coil_errors(mrsim, ctx):
