@@ -214,13 +214,24 @@ int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
               const mrsim_groups *groups, int mode, int precision, double *signal,
               float *M_final, unsigned out_flags);
 
-/* Run n_jobs independent (phantom, sequence) jobs of uneven sizes in one
- * persistent, CUDA-graph-captured launch chain (grouped FP32 steps, FP64
- * signal sums).  groups[i] must come from mrsim_group(ph[i], seq[i]).
- * signals[i]: host [2 * n_samples_total(seq[i])] doubles.
- * Errors: MRSIM_EINVAL, MRSIM_ESTATE, MRSIM_ENOMEM, MRSIM_ECUDA,
- * MRSIM_EUNSUPPORTED (a phantom with receive coils attached, a job that
- * needs a plain fallback or starts from a given M_init). */
+/* Run n_jobs independent (phantom, sequence) jobs of uneven sizes as one
+ * CUDA graph (grouped FP32 steps, FP64 signal sums): every job's transition
+ * tables in one launch, its group factors in one, persistent fused kernels
+ * that take (job, chunk) work items from a device counter, and every job's
+ * group signal in one launch.  Any job mrsim_run takes in MRSIM_GROUPED /
+ * FP32 is accepted: subsequences without a type run through the
+ * per-isochromat fallback kernels inside the same graph between fused spans;
+ * a given M_init, direct advances (about one group per isochromat) and
+ * receive coils (one instance of the job per coil) are handled as in
+ * mrsim_run.  The graph is kept and relaunched while the same jobs (and
+ * coils, and tuning) are run again.  groups[i] must come from
+ * mrsim_group(ph[i], seq[i]).  signals[i]: host [P][2 * n_samples_total]
+ * doubles as in mrsim_run (P = ph[i]'s coil count, 1 without coils).  The
+ * per-isochromat form of the fused kernel runs (MRSIM_TUNE_FUSED_NI); sums
+ * use FP64 atomics whatever mrsim_set_reproducible says.
+ * Errors: MRSIM_EINVAL (n_jobs <= 0, NULL arrays or entries), MRSIM_ESTATE
+ * (groups of another phantom or without a needed type), MRSIM_ENOMEM,
+ * MRSIM_ECUDA. */
 int mrsim_run_batch(mrsim_ctx *ctx, int n_jobs, const mrsim_phantom_t *const *ph,
                     const mrsim_seq *const *seq, const mrsim_groups *const *groups,
                     double *const *signals);

@@ -994,34 +994,49 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
     std::vector<uint64_t> key;
     for (int i = 0; i < n; ++i) {
         key.push_back(ph[i]->uid);
+        key.push_back(ph[i]->coil_uid);
         key.push_back(s[i]->uid);
         key.push_back(g[i]->uid);
     }
-    key.push_back((uint64_t)c->tune[MRSIM_TUNE_FUSED_NI]);
-    key.push_back((uint64_t)c->tune[MRSIM_TUNE_PRECOMP_STEPS]);
+    for (int t = 0; t < 7; ++t) key.push_back((uint64_t)c->tune[t]);
     auto &slot = batch_caches()[c];
     if (!slot || slot->key != key) {
         auto bc = std::make_unique<BatchCache>();
         bc->key = key;
         std::vector<GPlan<R>> plans(n);
+        for (int i = 0; i < n; ++i) plan_grouped<R>(c, s[i], g[i], plans[i]);
+        // Instances: one per (job, receive coil); the coils of a job share its
+        // tables and windows, each has its own block sums, signal and state.
+        // An instance keeps its state in device memory when its sequence has
+        // subsequences without a type (several fused spans with the
+        // per-isochromat fallback between them) or starts from a given state.
+        struct Inst { int job, coil; bool state; };
+        std::vector<Inst> inst;
+        std::vector<int> inst0(n);
         for (int i = 0; i < n; ++i) {
-            plan_grouped<R>(c, s[i], g[i], plans[i]);
-            if (plans[i].spans.size() != 1)
-                fail(MRSIM_EUNSUPPORTED, "batched jobs need known gradient types only");
-            if (plans[i].direct)
-                fail(MRSIM_EUNSUPPORTED, "batched jobs need few groups per isochromat");
+            inst0[i] = (int)inst.size();
+            const bool st = plans[i].spans.size() > 1 || g[i]->has_M_init;
+            for (int j = 0; j < std::max(ph[i]->n_coils, 1); ++j) inst.push_back(Inst{i, j, st});
         }
-        // sizes and per-job offsets inside shared device buffers
-        int64_t rows = 0, ablk = 0, nev = 0, ptab = 0, nsig = 0, blks = 0, nblk = 0;
-        std::vector<int64_t> o_rows(n), o_ablk(n), o_ev(n), o_p(n), o_sig(n), o_blk(n);
+        const int ni_ = (int)inst.size();
+        // sizes and offsets inside shared device buffers
+        int64_t rows = 0, ablk = 0, nev = 0, ptab = 0, nsig = 0, nst = 0, ncoil = 0;
+        std::vector<int64_t> o_rows(n), o_ev(n), o_p(n), o_sig(n);
+        std::vector<int64_t> o_ablk(ni_), o_st(ni_), o_coil(ni_);
         for (int i = 0; i < n; ++i) {
             o_rows[i] = rows; rows += plans[i].rows;
-            o_ablk[i] = ablk; ablk += plans[i].ablk_n;
             o_ev[i] = nev; nev += (int64_t)plans[i].ev.size();
-            o_p[i] = ptab; ptab += (int64_t)plans[i].ev.size() * plans[i].Gp;
-            o_sig[i] = nsig; nsig += s[i]->n_samples;
-            o_blk[i] = blks; blks += (g[i]->K + kFusedChunk(c) - 1) / kFusedChunk(c);
-            nblk += (int64_t)plans[i].blk.size();
+            o_p[i] = ptab;
+            if (!plans[i].direct) ptab += (int64_t)plans[i].ev.size() * plans[i].Gp;
+            o_sig[i] = nsig; nsig += s[i]->n_samples * std::max(ph[i]->n_coils, 1);
+        }
+        for (int q = 0; q < ni_; ++q) {
+            const int i = inst[q].job;
+            o_ablk[q] = ablk; ablk += plans[i].ablk_n;
+            o_st[q] = nst;
+            if (inst[q].state) nst += 3 * plane_stride(g[i]->K);
+            o_coil[q] = ncoil;
+            if (ph[i]->n_coils > 0) ncoil += 2 * g[i]->K;
         }
         auto alloc = [&](size_t bytes) {
             bc->bufs.push_back(dalloc(std::max<size_t>(bytes, 256)));
@@ -1033,17 +1048,28 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         EvAdv *adv = (EvAdv *)alloc(nev * sizeof(EvAdv));
         void *Pt = alloc(ptab * 4 * sizeof(R));
         double *sig = (double *)alloc(std::max<int64_t>(nsig, 1) * 2 * sizeof(double));
+        R *Mst = (R *)alloc(nst * sizeof(R));
+        float *cmap = (float *)alloc(ncoil * sizeof(float));
+        // receive-coil maps in each job's layout order (fixed while the
+        // phantom's coils are: the cache key holds their version)
+        for (int q = 0; q < ni_; ++q) {
+            const int i = inst[q].job, j = inst[q].coil;
+            if (ph[i]->n_coils == 0) continue;
+            const int64_t K = g[i]->K;
+            const float *src = ph[i]->coils.as<float>() + 2 * K * j;
+            launch_gather_f32(c, K, g[i]->perm.as<int32_t>(), src, cmap + o_coil[q]);
+            launch_gather_f32(c, K, g[i]->perm.as<int32_t>(), src + K, cmap + o_coil[q] + K);
+        }
         // descriptors
         std::vector<PrecompArgs> pre;
         std::vector<int64_t> pre_off{0};
         std::vector<EvTabJob> et;
         std::vector<int64_t> et_off{0};
-        std::vector<FusedArgs<R>> fj;
-        std::vector<int64_t> fj_off{0};
         std::vector<GSigJob<R>> gj;
         std::vector<int4> gblk;
         std::vector<int> gblk_job;
         std::vector<GWin> allwin;
+        std::vector<int64_t> win0(n);
         for (int i = 0; i < n; ++i) {
             GPlan<R> &P = plans[i];
             for (auto &t : P.tabs) {
@@ -1052,32 +1078,66 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
                 pre.back().kb = c->tune[MRSIM_TUNE_PRECOMP_STEPS];
                 pre_off.push_back(pre_off.back() + g[i]->n_groups[t.first.second]);
             }
-            const int prim = P.p;
-            et.push_back(EvTabJob{adv + o_ev[i], P.Gp, g[i]->tab[prim].d_par64.as<double>(),
-                                  (R *)Pt + o_p[i] * 4});
-            et_off.push_back(et_off.back() + (int64_t)P.ev.size() * P.Gp);
-            FusedArgs<R> fa = fused_args<R>(g[i], P.p, nullptr, nullptr, nullptr,
-                                            T + o_rows[i] * 12, (R *)Pt + o_p[i] * 4,
-                                            Ab + 2 * o_ablk[i]);
-            fa.ev = ev + o_ev[i];
-            fa.n_ev = (int)P.ev.size();
-            fa.init_eq = 1;
-            if (g[i]->has_M_init) fail(MRSIM_EUNSUPPORTED, "batched jobs start from equilibrium");
-            fj.push_back(fa);
-            fj_off.push_back(fj_off.back() + (g[i]->K + kFusedChunk(c) - 1) / kFusedChunk(c));
-            const int64_t w0 = (int64_t)allwin.size();
-            for (GWin w : P.wins) allwin.push_back(w);
-            gj.push_back(GSigJob<R>{nullptr, s[i]->gs_f.p, sig_tables<R>(g[i]),
-                                    Ab + 2 * o_ablk[i], sig + 2 * o_sig[i]});
-            gj.back().wins = (const GWin *)(intptr_t)w0;  // fixed up after upload
-            for (int4 b : P.blk) {
-                gblk.push_back(b);
-                gblk_job.push_back(i);
+            if (!P.direct) {
+                et.push_back(EvTabJob{adv + o_ev[i], P.Gp, g[i]->tab[P.p].d_par64.as<double>(),
+                                      (R *)Pt + o_p[i] * 4});
+                et_off.push_back(et_off.back() + (int64_t)P.ev.size() * P.Gp);
             }
+            win0[i] = (int64_t)allwin.size();
+            for (GWin w : P.wins) allwin.push_back(w);
             upload(c, ev + o_ev[i], P.ev.data(), P.ev.size() * sizeof(FEvent<R>));
             upload(c, adv + o_ev[i], P.adv.data(), P.adv.size() * sizeof(EvAdv));
             bc->d_sig.push_back(sig + 2 * o_sig[i]);
-            bc->n_samples.push_back(s[i]->n_samples);
+            bc->n_samples.push_back(s[i]->n_samples * std::max(ph[i]->n_coils, 1));
+        }
+        // fused launches: one per (span number, form) over the instances with
+        // that span; the per-isochromat fallbacks follow each span number
+        size_t n_span = 0;
+        for (auto &P : plans) n_span = std::max(n_span, P.spans.size());
+        struct Fb { int q, sub; };
+        std::vector<std::array<std::vector<FusedArgs<R>>, 4>> fj(n_span);
+        std::vector<std::array<std::vector<int64_t>, 4>> fj_off(n_span);
+        std::vector<std::vector<Fb>> fb(n_span);
+        auto state = [&](int q, R *&x, R *&y, R *&z) {
+            const int64_t Kp = plane_stride(g[inst[q].job]->K);
+            x = inst[q].state ? Mst + o_st[q] : nullptr;
+            y = x ? x + Kp : nullptr;
+            z = x ? x + 2 * Kp : nullptr;
+        };
+        for (int q = 0; q < ni_; ++q) {
+            const int i = inst[q].job;
+            GPlan<R> &P = plans[i];
+            R *x, *y, *z;
+            state(q, x, y, z);
+            const int64_t K = g[i]->K;
+            const bool coil = ph[i]->n_coils > 0;
+            const int form = (P.direct ? 1 : 0) | (coil ? 2 : 0);
+            for (size_t k = 0; k < P.spans.size(); ++k) {
+                const auto &sp = P.spans[k];
+                FusedArgs<R> fa = fused_args<R>(g[i], P.p, x, y, z, T + o_rows[i] * 12,
+                                                (R *)Pt + o_p[i] * 4, Ab + 2 * o_ablk[q]);
+                fa.ev = ev + o_ev[i] + sp.b;
+                fa.n_ev = (int)(sp.e - sp.b);
+                fa.init_eq = (k == 0 && !g[i]->has_M_init) ? 1 : 0;
+                fa.direct = P.direct ? 1 : 0;
+                if (coil) {
+                    fa.coil_re = cmap + o_coil[q];
+                    fa.coil_im = fa.coil_re + K;
+                }
+                auto &off = fj_off[k][form];
+                if (off.empty()) off.push_back(0);
+                fj[k][form].push_back(fa);
+                off.push_back(off.back() + (K + kFusedChunk(c) - 1) / kFusedChunk(c));
+                if (sp.fallback >= 0) fb[k].push_back(Fb{q, sp.fallback});
+            }
+            const double *ab = Ab + 2 * o_ablk[q];
+            double *sq = sig + 2 * (o_sig[i] + s[i]->n_samples * inst[q].coil);
+            gj.push_back(GSigJob<R>{nullptr, s[i]->gs_f.p, sig_tables<R>(g[i]), ab, sq, 0.0});
+            gj.back().wins = (const GWin *)(intptr_t)win0[i];  // fixed up after upload
+            for (int4 b : P.blk) {
+                gblk.push_back(b);
+                gblk_job.push_back(q);
+            }
         }
         GWin *d_win = (GWin *)alloc(std::max<size_t>(allwin.size(), 1) * sizeof(GWin));
         upload(c, d_win, allwin.data(), allwin.size() * sizeof(GWin));
@@ -1089,18 +1149,31 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         };
         auto *d_pre = (PrecompArgs *)up(pre.data(), pre.size() * sizeof(PrecompArgs));
         auto *d_pre_off = (int64_t *)up(pre_off.data(), pre_off.size() * sizeof(int64_t));
-        auto *d_et = (EvTabJob *)up(et.data(), et.size() * sizeof(EvTabJob));
+        auto *d_et = (EvTabJob *)up(et.data(), std::max<size_t>(et.size(), 1) * sizeof(EvTabJob));
         auto *d_et_off = (int64_t *)up(et_off.data(), et_off.size() * sizeof(int64_t));
-        auto *d_fj = (FusedArgs<R> *)up(fj.data(), fj.size() * sizeof(FusedArgs<R>));
-        auto *d_fj_off = (int64_t *)up(fj_off.data(), fj_off.size() * sizeof(int64_t));
+        struct FL { const FusedArgs<R> *jobs; const int64_t *off; int n, form; };
+        std::vector<std::vector<FL>> fl(n_span);
+        int n_fl = 0;
+        for (size_t k = 0; k < n_span; ++k)
+            for (int f = 0; f < 4; ++f) {
+                if (fj[k][f].empty()) continue;
+                fl[k].push_back(FL{(const FusedArgs<R> *)up(fj[k][f].data(),
+                                                            fj[k][f].size() * sizeof(FusedArgs<R>)),
+                                   (const int64_t *)up(fj_off[k][f].data(),
+                                                       fj_off[k][f].size() * sizeof(int64_t)),
+                                   (int)fj[k][f].size(), f});
+                ++n_fl;
+            }
         auto *d_gj = (GSigJob<R> *)up(gj.data(), gj.size() * sizeof(GSigJob<R>));
         auto *d_gblk = (int4 *)up(gblk.data(), std::max<size_t>(gblk.size(), 1) * sizeof(int4));
         auto *d_gbj = (int *)up(gblk_job.data(), std::max<size_t>(gblk_job.size(), 1) * sizeof(int));
-        auto *d_cnt = (unsigned long long *)alloc(sizeof(unsigned long long));
+        auto *d_cnt = (unsigned long long *)alloc(std::max(n_fl, 1) * sizeof(unsigned long long));
         sync(c);
-        // capture the four launches
+        // capture every launch of the batch into one graph
         const bool prof = c->prof_on;
         c->prof_on = false;
+        const double z0[3] = {0.0, 0.0, 0.0};
+        const typename AdvOf<R>::T zero = AdvOf<R>::make(z0, 0.0);
         cudaGraph_t graph = nullptr;
         MRSIM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t cap = cudaSuccess;
@@ -1109,10 +1182,47 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
             if (cap == cudaSuccess)
                 cap = cudaMemsetAsync(sig, 0, std::max<int64_t>(nsig, 1) * 2 * sizeof(double),
                                       c->stream);
-            if (cap == cudaSuccess) cap = cudaMemsetAsync(d_cnt, 0, sizeof(*d_cnt), c->stream);
+            if (cap == cudaSuccess)
+                cap = cudaMemsetAsync(d_cnt, 0, std::max(n_fl, 1) * sizeof(*d_cnt), c->stream);
             launch_precompute_batch<R>(c, d_pre, d_pre_off, (int)pre.size(), pre_off.back());
-            launch_event_table_batch<R>(c, d_et, d_et_off, n, et_off.back());
-            launch_fused_batch<R>(c, d_fj, d_fj_off, n, d_cnt, c->tune[MRSIM_TUNE_FUSED_NI]);
+            if (!et.empty())
+                launch_event_table_batch<R>(c, d_et, d_et_off, (int)et.size(), et_off.back());
+            for (int q = 0; q < ni_; ++q) {
+                const int i = inst[q].job;
+                if (!inst[q].state || !g[i]->has_M_init) continue;
+                R *x, *y, *z;
+                state(q, x, y, z);
+                launch_init_state<R>(c, sorted_state(g[i], x, y, z), g[i]->M_init.as<float>());
+            }
+            int li = 0;
+            for (size_t k = 0; k < n_span; ++k) {
+                for (const FL &f : fl[k])
+                    launch_fused_batch<R>(c, f.jobs, f.off, f.n, d_cnt + li++,
+                                          c->tune[MRSIM_TUNE_FUSED_NI], (f.form & 1) != 0,
+                                          (f.form & 2) != 0);
+                for (const Fb &b : fb[k]) {
+                    const int i = inst[b.q].job;
+                    const Subseq &qq = s[i]->sub[b.sub];
+                    R *x, *y, *z;
+                    state(b.q, x, y, z);
+                    PlainState st = sorted_state(g[i], x, y, z);
+                    if (ph[i]->n_coils > 0) {
+                        st.coil_re = cmap + o_coil[b.q];
+                        st.coil_im = st.coil_re + g[i]->K;
+                    }
+                    const int nseg = (int)(qq.seg_end - qq.seg_begin);
+                    if (qq.type == SUB_RF) {
+                        launch_plain_rf<R>(c, st, s[i]->rf_f[qq.content].p, nseg, &zero,
+                                           c->tune[MRSIM_TUNE_PLAIN_RF_NI]);
+                    } else {
+                        double *out = sig + 2 * (o_sig[i] + s[i]->n_samples * inst[b.q].coil +
+                                                 qq.sample0);
+                        launch_plain_adc<R>(c, st, s[i]->adc_f.as<ADCSegF>() + s[i]->adc_off[b.sub],
+                                            nseg, qq.n_samples, &zero, out,
+                                            c->tune[MRSIM_TUNE_ADC_CTAS_PER_SM]);
+                    }
+                }
+            }
             launch_group_signal_batch<R>(c, d_gj, d_gblk, d_gbj, (int)gblk.size());
         } catch (...) {
             cudaStreamEndCapture(c->stream, &graph);
@@ -1124,9 +1234,9 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         c->prof_on = prof;
         MRSIM_CUDA(cap);
         MRSIM_CUDA(end);
-        const cudaError_t inst = cudaGraphInstantiate(&bc->exec, graph, 0);
+        const cudaError_t inst_rc = cudaGraphInstantiate(&bc->exec, graph, 0);
         cudaGraphDestroy(graph);
-        MRSIM_CUDA(inst);
+        MRSIM_CUDA(inst_rc);
         slot = std::move(bc);
     }
     {
@@ -1283,6 +1393,7 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
             ph->coils.reset();
             ph->n_coils = 0;
             ph->sum_bound = -1.0;
+            ph->coil_uid = g_uid++;
             return;
         }
         const int64_t n = 2 * (int64_t)n_coils * ph->K;
@@ -1305,6 +1416,7 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
         ph->coils = std::move(d);
         ph->n_coils = n_coils;
         ph->sum_bound = -1.0;
+        ph->coil_uid = g_uid++;
     });
 }
 
@@ -1603,8 +1715,6 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
         for (int i = 0; i < n_jobs; ++i) {
             if (!ph[i] || !s[i] || !g[i] || !signals[i]) fail(MRSIM_EINVAL, "NULL batch entry");
             if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
-            if (ph[i]->n_coils > 0)
-                fail(MRSIM_EUNSUPPORTED, "batched jobs receive with one coil (S = 1)");
             for (const Subseq &q : s[i]->sub)
                 if ((q.type == SUB_RF || q.type == SUB_ADC) && q.gtype != G_GENERAL &&
                     !g[i]->built[q.gtype])

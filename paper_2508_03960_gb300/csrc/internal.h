@@ -92,6 +92,7 @@ struct mrsim_phantom_t {
     int n_coils = 0;    // receive coils attached by mrsim_coils (0: one coil, S = 1)
     mrsim::DBuf coils;  // float [n_coils][2][K] (re, im planes), phantom order
     double sum_bound = -1.0;  // bound on |any signal or block sum| (< 0: not formed yet)
+    uint64_t coil_uid = 0;    // changes whenever mrsim_coils attaches or detaches coils
 };
 
 namespace mrsim {
@@ -466,9 +467,12 @@ void launch_precompute_batch(mrsim_ctx *c, const PrecompArgs *d_tabs, const int6
 template <typename R>
 void launch_event_table_batch(mrsim_ctx *c, const EvTabJob *d_jobs, const int64_t *d_off,
                               int n_jobs, int64_t total);
+// jobs of one form: factor tables or direct advances (direct), with or
+// without a receive-coil sensitivity (coil)
 template <typename R>
 void launch_fused_batch(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
-                        int n_jobs, unsigned long long *d_counter, int ni);
+                        int n_jobs, unsigned long long *d_counter, int ni, bool direct,
+                        bool coil);
 template <typename R>
 void launch_group_signal_batch(mrsim_ctx *c, const GSigJob<R> *d_jobs, const int4 *d_blk,
                                const int *d_blk_job, int n_blk);

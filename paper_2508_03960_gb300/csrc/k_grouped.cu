@@ -646,8 +646,10 @@ __global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, MODE>()))
 // Persistent form for a batch of jobs: every CTA takes the next (job, chunk)
 // work item from a device counter until all chunks of all jobs are done, so
 // jobs of very different sizes share the GPU without a tail of idle SMs.
-template <typename R, int NI>
-__global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, FM_FACTOR>()))
+// MODE: the form shared by the launch's jobs (factor tables or direct
+// advances, with or without a receive coil).
+template <typename R, int NI, int MODE>
+__global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, MODE>()))
     k_fused_batch(const FusedArgs<R> *jobs, const int64_t *blk_off, int n_jobs,
                   unsigned long long *counter) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, NI, FM_FACTOR>(
         }
         __syncthreads();
         if (item >= total) break;
-        fused_chunk<R, NI, FM_FACTOR>(ja, jblk, sm);
+        fused_chunk<R, NI, MODE>(ja, jblk, sm);
     }
 }
 
@@ -920,24 +922,38 @@ void fused_smem_attr(K kern, size_t bytes) {
                                     (int)bytes));
 }
 
-template <typename R, int NI>
+template <typename R, int NI, int MODE>
 void launch_fused_batch_ni(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
                            int n_jobs, unsigned long long *d_counter) {
     const size_t smem = sizeof(FusedSmem<R>);
     int per_sm = 1;
-    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, NI>,
+    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_batch<R, NI, MODE>,
                                                              kThreads, smem));
-    k_fused_batch<R, NI><<<std::max(1, per_sm) * c->sm_count, kThreads, smem, c->stream>>>(
+    k_fused_batch<R, NI, MODE><<<std::max(1, per_sm) * c->sm_count, kThreads, smem, c->stream>>>(
         d_jobs, d_blk_off, n_jobs, d_counter);
+}
+
+template <typename R, int MODE>
+void launch_fused_batch_m(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
+                          int n_jobs, unsigned long long *d_counter, int ni) {
+    if (ni >= 4) launch_fused_batch_ni<R, 4, MODE>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    else if (ni == 2) launch_fused_batch_ni<R, 2, MODE>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    else launch_fused_batch_ni<R, 1, MODE>(c, d_jobs, d_blk_off, n_jobs, d_counter);
 }
 
 template <typename R>
 void launch_fused_batch(mrsim_ctx *c, const FusedArgs<R> *d_jobs, const int64_t *d_blk_off,
-                        int n_jobs, unsigned long long *d_counter, int ni) {
+                        int n_jobs, unsigned long long *d_counter, int ni, bool direct,
+                        bool coil) {
     KScope ks(c, "fused_batch");
-    if (ni >= 4) launch_fused_batch_ni<R, 4>(c, d_jobs, d_blk_off, n_jobs, d_counter);
-    else if (ni == 2) launch_fused_batch_ni<R, 2>(c, d_jobs, d_blk_off, n_jobs, d_counter);
-    else launch_fused_batch_ni<R, 1>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    if (direct && coil)
+        launch_fused_batch_m<R, FM_DIRECT | FM_COIL>(c, d_jobs, d_blk_off, n_jobs, d_counter, ni);
+    else if (direct)
+        launch_fused_batch_m<R, FM_DIRECT>(c, d_jobs, d_blk_off, n_jobs, d_counter, ni);
+    else if (coil)
+        launch_fused_batch_m<R, FM_FACTOR | FM_COIL>(c, d_jobs, d_blk_off, n_jobs, d_counter, ni);
+    else
+        launch_fused_batch_m<R, FM_FACTOR>(c, d_jobs, d_blk_off, n_jobs, d_counter, ni);
 }
 
 template <typename R>
@@ -1008,6 +1024,13 @@ void fused_attr_ni(size_t bytes) {
     fused_smem_attr(k_fused<R, 4, MODE>, bytes);
 }
 
+template <int MODE>
+void fused_batch_attr(size_t bytes) {
+    fused_smem_attr(k_fused_batch<float, 1, MODE>, bytes);
+    fused_smem_attr(k_fused_batch<float, 2, MODE>, bytes);
+    fused_smem_attr(k_fused_batch<float, 4, MODE>, bytes);
+}
+
 void prepare_fused(mrsim_ctx *) {
     const size_t f = sizeof(FusedSmem<float>), d = sizeof(FusedSmem<double>);
     fused_attr_ni<float, FM_FACTOR>(f);
@@ -1020,9 +1043,10 @@ void prepare_fused(mrsim_ctx *) {
     fused_attr_ni<double, FM_DIRECT>(d);
     fused_attr_ni<double, FM_FACTOR | FM_COIL>(d);
     fused_attr_ni<double, FM_DIRECT | FM_COIL>(d);
-    fused_smem_attr(k_fused_batch<float, 1>, f);
-    fused_smem_attr(k_fused_batch<float, 2>, f);
-    fused_smem_attr(k_fused_batch<float, 4>, f);
+    fused_batch_attr<FM_FACTOR>(f);
+    fused_batch_attr<FM_DIRECT>(f);
+    fused_batch_attr<FM_FACTOR | FM_COIL>(f);
+    fused_batch_attr<FM_DIRECT | FM_COIL>(f);
 }
 
 void launch_axis_phase(mrsim_ctx *c, const AxItem *d_items, int n_items, int max_n,
@@ -1064,7 +1088,7 @@ template void launch_fused<float>(mrsim_ctx *, const FusedArgs<float> &, int);
 template void launch_event_table_batch<float>(mrsim_ctx *, const EvTabJob *, const int64_t *,
                                               int, int64_t);
 template void launch_fused_batch<float>(mrsim_ctx *, const FusedArgs<float> *, const int64_t *,
-                                        int, unsigned long long *, int);
+                                        int, unsigned long long *, int, bool, bool);
 template void launch_group_signal_batch<float>(mrsim_ctx *, const GSigJob<float> *,
                                                const int4 *, const int *, int);
 template void launch_fused<double>(mrsim_ctx *, const FusedArgs<double> &, int);
