@@ -113,6 +113,36 @@ def batch_job(i: int, K: int):
     return ph, seq
 
 
+def batch_job_mixed(i: int, K: int):
+    """Job i of the mixed batched workload: batch_job(i, K), then by i mod 4
+    unchanged, a given initial state (M_init, seeded), two receive coils, or
+    an oblique readout sequence whose with-RF and with-ADC subsequences use all
+    three gradient axes (no gradient type: per-isochromat fallback)."""
+    import dataclasses
+    from .phantom import coil_maps
+    from .sequence import SeqBuilder
+    ph, seq = batch_job(i, K)
+    kind = i % 4
+    if kind == 1:
+        rng = np.random.default_rng(2000 + i)
+        Mi = np.stack([rng.uniform(-0.3, 0.3, ph.K), rng.uniform(-0.3, 0.3, ph.K),
+                       rng.uniform(0.2, 1.0, ph.K)]) * ph.M0
+        ph = dataclasses.replace(ph, M_init=np.ascontiguousarray(Mi, np.float32))
+    elif kind == 2:
+        ph = dataclasses.replace(ph, coils=coil_maps(ph, 2, seed=3000 + i))
+    elif kind == 3:
+        b = SeqBuilder()
+        for _ in range(4):
+            b.rf_sinc(90, "x", 1e-3, 10e-6, 4.0, 0.01)
+            b.add(1e-3, 1, g=(-2e-3, -1e-3, -3e-3))
+            for _ in range(20):  # a refocusing block with all three axes on
+                b.add(10e-6, 1, b1=(2e-6, 0.5e-6), g=(1e-3, 0.5e-3, 2e-3))
+            b.add(10e-6, 64, g=(4e-3, 2e-3, 1e-3), adc=True)  # oblique readout
+            b.add(5e-3, 1)
+        seq = b.build()
+    return ph, seq
+
+
 def surrogate_fse(nx=32, ny=32, nz=4) -> Tuple[Phantom, Sequence]:
     ph = continuous_phantom(nx, ny, nz, 3, seed=1005)
     seq = fse_2d(n_ro=32, n_pe=32, etl=8, rf_dur=2e-3, rf_dt=10e-6,
