@@ -35,10 +35,35 @@ constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH
               oW3 = ob2 + kH, ob3 = oW3 + kOut * kH, kNParams = ob3 + kOut;
 static_assert(kNParams == 18828, "parameter count");
 
-__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float a) {
-    return 0.5f * (1.0f + erff(a * 0.70710678118654752f)) +
-           a * expf(-0.5f * a * a) * 0.39894228040143268f;
+// GELU a Phi(a), Phi(a) = (1 + erf(a / sqrt 2)) / 2, with erf from the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// eq. 7.1.26 (Hastings): for z >= 0, erf(z) = 1 - E(z),
+// E(z) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-z^2), t = 1 / (1 + p z),
+// |error| <= 1.5e-7.  Phi(a) = 1 - E / 2 for a >= 0 and E / 2 below.  About a
+// third of the instructions of the library erf; the network is trained and
+// evaluated with this same function, and tests compare it with an FP64
+// network that uses the exact erf.
+struct GeluParts {
+    float E;  // E(|a| / sqrt 2)
+    float g;  // exp(-a^2 / 2)
+};
+__device__ __forceinline__ GeluParts gelu_parts(float a) {
+    const float z = fabsf(a) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    float q = fmaf(t, 1.061405429f, -1.453152027f);
+    q = fmaf(t, q, 1.421413741f);
+    q = fmaf(t, q, -0.284496736f);
+    q = fmaf(t, q, 0.254829592f);
+    const float g = __expf(-z * z);
+    return GeluParts{q * t * g, g};
+}
+__device__ __forceinline__ float gelu_phi(float a, float E) {
+    return a >= 0.0f ? fmaf(-0.5f, E, 1.0f) : 0.5f * E;
+}
+__device__ __forceinline__ float gelu(float a) { return a * gelu_phi(a, gelu_parts(a).E); }
+__device__ __forceinline__ float gelu_grad(float a) {  // Phi(a) + a phi(a)
+    const GeluParts p = gelu_parts(a);
+    return fmaf(a * 0.39894228040143268f, p.g, gelu_phi(a, p.E));
 }
 
 // D += A B for one 16x8x16 tile: A 16x16 row-major, B 16x8 column-major, BF16
@@ -582,7 +607,6 @@ struct TcSmem {
     float b2[kH];
     float4 W3t[kH][3];                 // W3 transposed: 12 outputs per hidden unit
     float b3[kOut];
-    float part[kTcRows][kOut + 1];     // second half's output partial sums
     float half_turns[kTcRows];
     int grp[kTcRows];
     unsigned long long mbar;
@@ -659,7 +683,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_sur_infer(const float *P, const __nv_bfloat16 *W2b_g, FeatCoef fc, SurPulse pulse,
                 const double *par, int64_t G, const int32_t *srv, const int32_t *cnt,
                 float *out, int *err, const float *X, int64_t n_x) {
@@ -706,7 +730,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int64_t n = X ? n_x : *cnt;
     uint32_t phase = 0;
     bool ok = true;
+    // the second half's output partial sums share the low-part operand tile,
+    // which the MMAs no longer read once their completion is seen
+    float(*part)[kOut + 1] = reinterpret_cast<float(*)[kOut + 1]>(sm.Alo);
     for (int64_t tile = blockIdx.x; tile * kTcRows < n && ok; tile += gridDim.x) {
+        // the previous tile's partial sums are read before this tile's operands
+        // overwrite them
+        __syncthreads();
         const int64_t s = tile * kTcRows + row;
         // features of this row's group and layer 1 for this thread's half
         float f[kIn] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -811,13 +841,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (half == 1) {
 #pragma unroll
-            for (int r = 0; r < kOut; ++r) sm.part[row][r] = y[r];
+            for (int r = 0; r < kOut; ++r) part[row][r] = y[r];
         }
         __syncthreads();
         if (half == 0 && sm.grp[row] >= 0) {  // T = P(th/2) [C_A P(th/2) | C_b]
             float T[kOut];
 #pragma unroll
-            for (int r = 0; r < kOut; ++r) T[r] = y[r] + sm.part[row][r];
+            for (int r = 0; r < kOut; ++r) T[r] = y[r] + part[row][r];
             if (X) {  // raw outputs
                 float4 *o = reinterpret_cast<float4 *>(out + (int64_t)sm.grp[row] * kOut);
                 o[0] = make_float4(T[0], T[1], T[2], T[3]);
@@ -857,6 +887,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 static_assert(sizeof(SurSmem) <= 227 * 1024, "tile exceeds the per-CTA shared memory");
+static_assert(2 * (sizeof(TcSmem) + 1024) <= 228 * 1024,
+              "two inference CTAs must fit an SM's shared memory");
+static_assert(kTcRows * (kOut + 1) * sizeof(float) <= kTileBytes, "partials fit one operand tile");
 size_t sur_smem() { return sizeof(SurSmem); }
 
 }  // namespace
@@ -921,6 +954,10 @@ void launch_sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const FeatC
     if (!attr) {
         MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(TcSmem)));
+        // the whole unified L1 / shared array as shared memory: two CTAs per SM
+        MRSIM_CUDA(cudaFuncSetAttribute(k_sur_infer,
+                                        cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
         attr = true;
     }
     int *err = c->dev_err.as<int>() + kErrWordTensor;
