@@ -321,7 +321,7 @@ typedef struct mrsim_surrogate mrsim_surrogate;
  * decayed by a cosine to lr/100), `seed` for the counter-based draws, `bound` the per-entry error
  * bound of the fallback gate.  Errors: MRSIM_EINVAL (bad arguments, no
  * slice-selective pulse), MRSIM_ENOMEM, MRSIM_ECUDA, MRSIM_ETIMEOUT (a bounded
- * wait of the tensor-core inference kernel ran out). */
+ * wait of the tensor-core training or inference kernel ran out). */
 int mrsim_surrogate_train(mrsim_ctx *ctx, const mrsim_seq *seq, const double *lo,
                           const double *hi, int64_t n_train, int epochs, int batch, double lr,
                           uint64_t seed, double bound, mrsim_surrogate **out);
@@ -353,7 +353,10 @@ int mrsim_surrogate_use(mrsim_ctx *ctx, const mrsim_surrogate *sur);
  * (host float[18828], layout W1[128][5], b1[128], W2[128][128], b2[128],
  * W3[12][128], b3[12]) on n host samples x[n][5] with targets t[n][12]:
  * returns y[n][12], the gradient of the loss sum((y - t)^2) / (12 n) and
- * the loss (any output may be NULL).  The same kernels as training. */
+ * the loss (any output may be NULL).  The same kernel as training: the
+ * tile's contractions on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation in tensor memory), the rest in FP32.  Errors: MRSIM_EINVAL,
+ * MRSIM_ENOMEM, MRSIM_ECUDA, MRSIM_ETIMEOUT (a bounded wait ran out). */
 int mrsim_surrogate_eval(mrsim_ctx *ctx, const float *params, int64_t n, const float *x,
                          const float *t, float *y, float *grad, double *loss);
 

@@ -226,6 +226,10 @@ void sur_train_step(mrsim_ctx *c, const float *P, const void *W2b, const void *W
                     float *Yout);
 void sur_adam(mrsim_ctx *c, float *P, float *grad, float *m, float *v, int step, float lr,
               void *W2b, void *W2Tb);
+// word kErrWordTensor of the context's error area: cleared before training,
+// read (synchronising) after it; MRSIM_ETIMEOUT if a bounded wait ran out
+void sur_tensor_err_reset(mrsim_ctx *c);
+void sur_tensor_err_check(mrsim_ctx *c);
 void sur_cell_error(mrsim_ctx *c, const SurDomain &d, const double *par, int64_t n,
                     const float *Y, const float *T, unsigned int *cell_err);
 // Gate + network inference for the G groups of one table.  cell_ok == nullptr

@@ -7,12 +7,14 @@
 // integration where the network's error exceeds the bound.
 //
 // Precision: the 128 x 128 hidden layer holds 16,384 of the 18,828 weights;
-// they are stored in BF16 (FP32 master copies for training) and that layer and
-// its two backward products run on the tensor cores (mma.sync m16n8k16, BF16
-// inputs, FP32 accumulation).  Its input activations enter as an unevaluated
-// sum of two BF16 numbers (hi + lo, two MMAs), so they keep ~16 bits.  The
-// 5-wide input layer and the 12-wide output layer are not contraction-shaped;
-// they run on FP32 lanes with FP32 weights.
+// they are stored in BF16 (FP32 master copies for training).  That layer and,
+// in training, every contraction over the samples of a tile (its two backward
+// products and the weight gradients of the other layers) run on the tensor
+// cores: tcgen05.mma with BF16 operands in shared memory and FP32 accumulators
+// in tensor memory.  The layer's input activations enter as an unevaluated sum
+// of two BF16 numbers (hi + lo, two MMAs), so they keep ~16 bits.  The 5-wide
+// input layer and the 12-wide output layer of each sample are not
+// contraction-shaped; they run on FP32 lanes with FP32 weights.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -21,14 +23,9 @@ namespace mrsim {
 
 namespace {
 
-constexpr int kTS = 64;       // samples per tile
-constexpr int kNT = 128;      // threads per tile CTA (4 warps x 16 samples)
 constexpr int kH = 128;       // hidden width
 constexpr int kIn = 5;
 constexpr int kOut = 12;
-constexpr int kLdH = kH + 8;  // bf16 row stride of [samples][hidden] tiles
-constexpr int kLdT = kTS + 8; // bf16 row stride of [hidden][samples] tiles
-constexpr int kLdW = kH + 8;  // bf16 row stride of W2 and W2^T
 
 // flat parameter layout (FP32 master, gradients, Adam moments)
 constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
@@ -64,291 +61,6 @@ __device__ __forceinline__ float gelu(float a) { return a * gelu_phi(a, gelu_par
 __device__ __forceinline__ float gelu_grad(float a) {  // Phi(a) + a phi(a)
     const GeluParts p = gelu_parts(a);
     return fmaf(a * 0.39894228040143268f, p.g, gelu_phi(a, p.E));
-}
-
-// D += A B for one 16x8x16 tile: A 16x16 row-major, B 16x8 column-major, BF16
-// inputs, FP32 accumulators (warp-wide).
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// A fragment of rows r0..r0+15, columns k0..k0+15 of a row-major bf16 array
-__device__ __forceinline__ void load_a(uint32_t (&a)[4], const __nv_bfloat16 *M, int ld, int r0,
-                                       int k0) {
-    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
-    const uint32_t *p0 = reinterpret_cast<const uint32_t *>(M + (r0 + g) * ld + k0 + 2 * t);
-    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(M + (r0 + g + 8) * ld + k0 + 2 * t);
-    a[0] = p0[0];
-    a[1] = p1[0];
-    a[2] = p0[4];
-    a[3] = p1[4];
-}
-// B fragment (k0..k0+15) x (n0..n0+7) of a matrix whose column n is stored as
-// row n of the bf16 array Mt (so Mt[n][k] = B[k][n])
-__device__ __forceinline__ void load_b(uint32_t (&b)[2], const __nv_bfloat16 *Mt, int ld, int n0,
-                                       int k0) {
-    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
-    const uint32_t *p = reinterpret_cast<const uint32_t *>(Mt + (n0 + g) * ld + k0 + 2 * t);
-    b[0] = p[0];
-    b[1] = p[4];
-}
-
-struct SurSmem {
-    __nv_bfloat16 W2b[kH * kLdW];   // W2[o][i]
-    __nv_bfloat16 W2Tb[kH * kLdW];  // W2[o][i] at [i][o]
-    __nv_bfloat16 H1b[kTS * kLdH];  // h1[s][i], high part
-    union {                          // the forward and backward phases never overlap
-        __nv_bfloat16 H1lo[kTS * kLdH];  // h1[s][i] - high part, rounded (forward)
-        __nv_bfloat16 dA2b[kTS * kLdH];  // da2[s][o] (backward)
-    };
-    __nv_bfloat16 H1Tb[kH * kLdT];  // h1[s][i] at [i][s]
-    __nv_bfloat16 dA2Tb[kH * kLdT];
-    float F[kTS * kH];  // a2, then h2; later da1
-    float G[kTS * kH];  // gelu'(a2), then da2
-    float W1[kH * kIn], b1[kH], b2[kH], W3[kOut * kH], b3[16];
-    float X[kTS * kIn], T[kTS * kOut], dY[kTS * kOut];
-    float red[kNT / 32];
-};
-
-// weights into shared memory (W2 in BF16; the rest FP32)
-__device__ void load_weights(SurSmem &sm, const float *P, const __nv_bfloat16 *W2b_g,
-                             const __nv_bfloat16 *W2Tb_g, bool need_T) {
-    const int tid = threadIdx.x;
-    for (int j = tid; j < kH * kH / 8; j += kNT) {
-        const int r = (j * 8) / kH, c = (j * 8) % kH;
-        *reinterpret_cast<int4 *>(&sm.W2b[r * kLdW + c]) = reinterpret_cast<const int4 *>(W2b_g)[j];
-        if (need_T)
-            *reinterpret_cast<int4 *>(&sm.W2Tb[r * kLdW + c]) =
-                reinterpret_cast<const int4 *>(W2Tb_g)[j];
-    }
-    for (int j = tid; j < kH * kIn; j += kNT) sm.W1[j] = P[oW1 + j];
-    for (int j = tid; j < kH; j += kNT) {
-        sm.b1[j] = P[ob1 + j];
-        sm.b2[j] = P[ob2 + j];
-    }
-    for (int j = tid; j < kOut * kH; j += kNT) sm.W3[j] = P[oW3 + j];
-    if (tid < kOut) sm.b3[tid] = P[ob3 + tid];
-}
-
-// Forward pass of one tile: h1 (bf16, both layouts), a2 -> F = h2 and
-// G = gelu'(a2); outputs y [kTS][12] written to `y` (shared or global).
-__device__ void tile_forward(SurSmem &sm, int ns, bool keep_grad) {
-    const int tid = threadIdx.x, warp = tid >> 5;
-    // layer 1 (FP32): a1 = W1 x + b1, h1 = gelu(a1) rounded to bf16
-    for (int j = tid; j < kTS * kH; j += kNT) {
-        const int s = j / kH, i = j % kH;
-        float a = sm.b1[i];
-#pragma unroll
-        for (int c = 0; c < kIn; ++c) a = fmaf(sm.W1[i * kIn + c], sm.X[s * kIn + c], a);
-        const float h = s < ns ? gelu(a) : 0.0f;
-        const __nv_bfloat16 hb = __float2bfloat16_rn(h);
-        sm.H1b[s * kLdH + i] = hb;
-        sm.H1lo[s * kLdH + i] = __float2bfloat16_rn(h - __bfloat162float(hb));
-        sm.H1Tb[i * kLdT + s] = hb;
-    }
-    __syncthreads();
-    // layer 2 on tensor cores: a2[s][o] = sum_i h1[s][i] W2[o][i] + b2[o]
-    {
-        const int g = (tid & 31) >> 2, t = tid & 3, r0 = warp * 16;
-        float acc[16][4];
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const float bl = sm.b2[nt * 8 + 2 * t], bh = sm.b2[nt * 8 + 2 * t + 1];
-            acc[nt][0] = bl; acc[nt][1] = bh; acc[nt][2] = bl; acc[nt][3] = bh;
-        }
-#pragma unroll
-        for (int ks = 0; ks < kH / 16; ++ks) {
-            uint32_t a[4], al[4];
-            load_a(a, sm.H1b, kLdH, r0, ks * 16);
-            load_a(al, sm.H1lo, kLdH, r0, ks * 16);
-#pragma unroll
-            for (int nt = 0; nt < 16; ++nt) {
-                uint32_t b[2];
-                load_b(b, sm.W2b, kLdW, nt * 8, ks * 16);
-                mma16816(acc[nt], a, b);
-                mma16816(acc[nt], al, b);
-            }
-        }
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const int c = nt * 8 + 2 * t;
-            sm.F[(r0 + g) * kH + c] = acc[nt][0];
-            sm.F[(r0 + g) * kH + c + 1] = acc[nt][1];
-            sm.F[(r0 + g + 8) * kH + c] = acc[nt][2];
-            sm.F[(r0 + g + 8) * kH + c + 1] = acc[nt][3];
-        }
-    }
-    __syncthreads();
-    for (int j = tid; j < kTS * kH; j += kNT) {
-        const float a = sm.F[j];
-        if (keep_grad) sm.G[j] = gelu_grad(a);
-        sm.F[j] = gelu(a);
-    }
-    __syncthreads();
-}
-
-// output layer for sample s, output r
-__device__ __forceinline__ float out_layer(const SurSmem &sm, int s, int r) {
-    float y = sm.b3[r];
-    for (int o = 0; o < kH; ++o) y = fmaf(sm.W3[r * kH + o], sm.F[s * kH + o], y);
-    return y;
-}
-
-__device__ double block_sum(SurSmem &sm, float v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double tot = 0;
-    for (int w = 0; w < kNT / 32; ++w) tot += sm.red[w];
-    __syncthreads();
-    return tot;
-}
-
-// One training tile: forward, loss, backward; gradients added into `grad`.
-// inv_n = 1 / (12 * samples in the whole minibatch).
-__global__ void __launch_bounds__(kNT) k_sur_train(const float *P, const __nv_bfloat16 *W2b_g,
-                                                   const __nv_bfloat16 *W2Tb_g, const float *X,
-                                                   const float *Tgt, int64_t n, float inv_n,
-                                                   float *grad, double *loss, float *Yout) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    SurSmem &sm = *reinterpret_cast<SurSmem *>(raw);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t s0 = blockIdx.x * (int64_t)kTS;
-    const int ns = (int)min((int64_t)kTS, n - s0);
-    load_weights(sm, P, W2b_g, W2Tb_g, true);
-    for (int j = tid; j < kTS * kIn; j += kNT) sm.X[j] = j < ns * kIn ? X[s0 * kIn + j] : 0.0f;
-    for (int j = tid; j < kTS * kOut; j += kNT) sm.T[j] = j < ns * kOut ? Tgt[s0 * kOut + j] : 0.0f;
-    __syncthreads();
-    tile_forward(sm, ns, true);
-    // output layer, residual and dL/dy
-    float lsum = 0.0f;
-    for (int j = tid; j < kTS * kOut; j += kNT) {
-        const int s = j / kOut, r = j % kOut;
-        float d = 0.0f;
-        if (s < ns) {
-            const float y = out_layer(sm, s, r);
-            if (Yout) Yout[(s0 + s) * kOut + r] = y;
-            const float res = y - sm.T[j];
-            lsum += res * res;
-            d = 2.0f * res * inv_n;
-        }
-        sm.dY[j] = d;
-    }
-    const double ls = block_sum(sm, lsum);
-    if (tid == 0 && loss) atomicAdd(loss, ls);
-    __syncthreads();
-    // dW3[r][o] = sum_s dY[s][r] h2[s][o]; db3[r] = sum_s dY[s][r]
-    for (int j = tid; j < kOut * kH; j += kNT) {
-        const int r = j / kH, o = j % kH;
-        float acc = 0.0f;
-        for (int s = 0; s < ns; ++s) acc = fmaf(sm.dY[s * kOut + r], sm.F[s * kH + o], acc);
-        atomicAdd(&grad[oW3 + j], acc);
-    }
-    if (tid < kOut) {
-        float acc = 0.0f;
-        for (int s = 0; s < ns; ++s) acc += sm.dY[s * kOut + tid];
-        atomicAdd(&grad[ob3 + tid], acc);
-    }
-    // da2[s][o] = (sum_r dY[s][r] W3[r][o]) gelu'(a2[s][o])
-    for (int j = tid; j < kTS * kH; j += kNT) {
-        const int s = j / kH, o = j % kH;
-        float d = 0.0f;
-#pragma unroll
-        for (int r = 0; r < kOut; ++r) d = fmaf(sm.dY[s * kOut + r], sm.W3[r * kH + o], d);
-        d *= sm.G[j];
-        sm.G[j] = d;
-        const __nv_bfloat16 db = __float2bfloat16_rn(d);
-        sm.dA2b[s * kLdH + o] = db;
-        sm.dA2Tb[o * kLdT + s] = db;
-    }
-    __syncthreads();
-    if (tid < kH) {
-        float acc = 0.0f;
-        for (int s = 0; s < ns; ++s) acc += sm.G[s * kH + tid];
-        atomicAdd(&grad[ob2 + tid], acc);
-    }
-    // dh1 = da2 W2 (tensor cores), then da1 = dh1 gelu'(a1) into F
-    {
-        const int g = (tid & 31) >> 2, t = tid & 3, r0 = warp * 16;
-        float acc[16][4];
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-        for (int ks = 0; ks < kH / 16; ++ks) {
-            uint32_t a[4];
-            load_a(a, sm.dA2b, kLdH, r0, ks * 16);
-#pragma unroll
-            for (int nt = 0; nt < 16; ++nt) {
-                uint32_t b[2];
-                load_b(b, sm.W2Tb, kLdW, nt * 8, ks * 16);  // B[k=o][n=i] = W2[o][i]
-                mma16816(acc[nt], a, b);
-            }
-        }
-        __syncthreads();  // every warp is done reading F (h2) before it becomes da1
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = r0 + g + (q >= 2 ? 8 : 0), i = nt * 8 + 2 * t + (q & 1);
-                float a1 = sm.b1[i];
-#pragma unroll
-                for (int c = 0; c < kIn; ++c) a1 = fmaf(sm.W1[i * kIn + c], sm.X[s * kIn + c], a1);
-                sm.F[s * kH + i] = s < ns ? acc[nt][q] * gelu_grad(a1) : 0.0f;
-            }
-        }
-    }
-    __syncthreads();
-    // dW1[i][c] = sum_s da1[s][i] x[s][c]; db1[i] = sum_s da1[s][i]
-    for (int j = tid; j < kH * kIn; j += kNT) {
-        const int i = j / kIn, c = j % kIn;
-        float acc = 0.0f;
-        for (int s = 0; s < ns; ++s) acc = fmaf(sm.F[s * kH + i], sm.X[s * kIn + c], acc);
-        atomicAdd(&grad[oW1 + j], acc);
-    }
-    if (tid < kH) {
-        float acc = 0.0f;
-        for (int s = 0; s < ns; ++s) acc += sm.F[s * kH + tid];
-        atomicAdd(&grad[ob1 + tid], acc);
-    }
-    // dW2[o][i] = sum_s da2[s][o] h1[s][i] (tensor cores; K = samples)
-    {
-        const int g = (tid & 31) >> 2, t = tid & 3;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int o0 = warp * 32 + mt * 16;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float acc[8][4];
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-                for (int ks = 0; ks < kTS / 16; ++ks) {
-                    uint32_t a[4];
-                    load_a(a, sm.dA2Tb, kLdT, o0, ks * 16);  // A[m=o][k=s]
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        uint32_t b[2];
-                        load_b(b, sm.H1Tb, kLdT, (half * 8 + nt) * 8, ks * 16);  // B[k=s][n=i]
-                        mma16816(acc[nt], a, b);
-                    }
-                }
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int i = (half * 8 + nt) * 8 + 2 * t;
-                    atomicAdd(&grad[oW2 + (o0 + g) * kH + i], acc[nt][0]);
-                    atomicAdd(&grad[oW2 + (o0 + g) * kH + i + 1], acc[nt][1]);
-                    atomicAdd(&grad[oW2 + (o0 + g + 8) * kH + i], acc[nt][2]);
-                    atomicAdd(&grad[oW2 + (o0 + g + 8) * kH + i + 1], acc[nt][3]);
-                }
-            }
-        }
-    }
 }
 
 // Adam (bias-corrected); zeroes the gradient and refreshes the BF16 copies
@@ -886,11 +598,389 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
 }
 
-static_assert(sizeof(SurSmem) <= 227 * 1024, "tile exceeds the per-CTA shared memory");
+
+// ------------------------------------------------------------- training ----
+// One CTA per tile of 128 samples (256 threads; a thread holds one sample row
+// and half of its 128 columns, as in inference).  The contractions of the
+// minibatch step run on the tensor cores, in four groups of tcgen05.mma (BF16
+// operands in the same no-swizzle K-major layout, FP32 accumulators in TMEM),
+// each committed to the CTA's mbarrier:
+//   forward   D1[s][o] = sum_i h1[s][i] W2[o][i]           (h1 as hi + lo)
+//   backward  D2[s][i] = sum_o da2[s][o] W2[o][i]          (dh1)
+//             D3[o][j] = sum_s da2[s][o] [h1 | 1][s][j]    (dW2; j = 128: db2)
+//             D4[o][r] = sum_s h2[s][o] dY[s][r]           (dW3)
+//   then      D5[i][c] = sum_s da1[s][i] [x | 1][s][c]     (dW1; c = 5: db1)
+// The elementwise work between them (GELU and its derivative, the 12-wide
+// output layer, the loss and dY = dL/dy, da2 = (dY W3) gelu'(a2), da1 = dh1
+// gelu'(a1)) runs on the FP32 lanes of the row's thread.  The weight gradients
+// of the tile leave TMEM once, as FP32 atomics into `grad`.  TMEM columns: D1
+// 0-127, D2 128-255, D3 256-399, D4 416-431, D5 448-463 (every 32-column load
+// starts at a multiple of 32); 512 are allocated (the shared memory already
+// keeps one CTA per SM).
+constexpr int kTrCols = 512;
+constexpr int kColD2 = 128, kColD3 = 256, kColD4 = 416, kColD5 = 448;
+constexpr int kN3 = kH + 16;             // dW2 operand rows: h1^T, the ones row, zero rows
+constexpr int kOp16Bytes = 16 * kH * 2;  // a 16-row operand over K = 128
+
+struct TrSmem {
+    __align__(16) unsigned char R0[kTileBytes];  // W2 (B, forward) -> h2^T (A, dW3)
+    __align__(16) unsigned char R1[kTileBytes];  // W2^T (B, dh1) -> da1^T (A, dW1)
+    __align__(16) unsigned char R2[kTileBytes];  // h1 hi (A, forward) -> da2 (A, dh1)
+    __align__(16) unsigned char R3[kTileBytes];  // h1 lo (A, forward) -> da2^T (A, dW2)
+    __align__(16) unsigned char R4[kN3 * kH * 2];  // [h1^T; 1; 0] (B, dW2)
+    __align__(16) unsigned char R5[kOp16Bytes];  // [dY^T; 0] (B, dW3) -> [x^T; 1; 0] (B, dW1)
+    float4 W1b[kH][2];                 // (w0, w1, w2, w3), (w4, b1, 0, 0) per hidden unit
+    float b2[kH];
+    float4 W3t[kH][3];                 // W3 transposed: 12 outputs per hidden unit
+    float b3[kOut];
+    float X[kTcRows][kIn];
+    float Tg[kTcRows][kOut];
+    float dY[kTcRows][kOut];
+    float part[kTcRows][kOut + 1];     // second half's output partial sums
+    float red[kTcThreads / 32];
+    unsigned long long mbar;
+    uint32_t tmem_base;
+};
+
+// instruction descriptor of kind::f16 (D FP32, A and B BF16, K-major, M = 128)
+// for N columns
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// D (+)= A B over K = 128 (8 MMAs of K = 16) for A and B in the layout of
+// core_off, then (if commit) a commit of everything issued to the mbarrier
+__device__ __forceinline__ void umma_k128(uint32_t tmem_d, uint32_t a, uint32_t b, uint32_t n) {
+#pragma unroll
+    for (int ks = 0; ks < kH / 16; ++ks)
+        umma_bf16_n(tmem_d, umma_desc(a + ks * 256, 128, 2048), umma_desc(b + ks * 256, 128, 2048),
+                    idesc_bf16(n), ks > 0 ? 1u : 0u);
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            mbar)
+        : "memory");
+}
+
+// operands written by the threads become visible to the tensor cores, and the
+// threads' earlier TMEM loads are ordered before the MMAs issued next
+__device__ __forceinline__ void to_tensor_cores() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char *base, int row, int k, float v) {
+    *reinterpret_cast<__nv_bfloat16 *>(base + core_off(row, k)) = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_sur_train(const float *P, const __nv_bfloat16 *W2b_g, const __nv_bfloat16 *W2Tb_g,
+                const float *X, const float *Tgt, int64_t n, float inv_n, float *grad,
+                double *loss, float *Yout, int *err) {
+    extern __shared__ __align__(16) unsigned char tr_raw[];
+    TrSmem &sm = *reinterpret_cast<TrSmem *>(tr_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+    const int64_t s0 = (int64_t)blockIdx.x * kTcRows;
+    const int ns = (int)min((int64_t)kTcRows, n - s0);
+    const bool live = row < ns;
+    // weights: W2 as (N = o, K = i) and W2^T as (N = i, K = o), both K-major
+    for (int j = tid; j < kH * kH / 8; j += kTcThreads) {
+        const int r = (j * 8) / kH, k = (j * 8) % kH;
+        *reinterpret_cast<int4 *>(sm.R0 + core_off(r, k)) = reinterpret_cast<const int4 *>(W2b_g)[j];
+        *reinterpret_cast<int4 *>(sm.R1 + core_off(r, k)) =
+            reinterpret_cast<const int4 *>(W2Tb_g)[j];
+    }
+    for (int i = tid; i < kH; i += kTcThreads) {
+        const float *w = P + oW1 + i * kIn;
+        sm.W1b[i][0] = make_float4(w[0], w[1], w[2], w[3]);
+        sm.W1b[i][1] = make_float4(w[4], P[ob1 + i], 0.0f, 0.0f);
+        sm.b2[i] = P[ob2 + i];
+        sm.W3t[i][0] = make_float4(P[oW3 + 0 * kH + i], P[oW3 + 1 * kH + i], P[oW3 + 2 * kH + i],
+                                   P[oW3 + 3 * kH + i]);
+        sm.W3t[i][1] = make_float4(P[oW3 + 4 * kH + i], P[oW3 + 5 * kH + i], P[oW3 + 6 * kH + i],
+                                   P[oW3 + 7 * kH + i]);
+        sm.W3t[i][2] = make_float4(P[oW3 + 8 * kH + i], P[oW3 + 9 * kH + i],
+                                   P[oW3 + 10 * kH + i], P[oW3 + 11 * kH + i]);
+    }
+    if (tid < kOut) sm.b3[tid] = P[ob3 + tid];
+    for (int j = tid; j < kTcRows * kIn; j += kTcThreads) {
+        const int s = j / kIn;
+        sm.X[s][j - s * kIn] = s < ns ? X[s0 * kIn + j] : 0.0f;
+    }
+    for (int j = tid; j < kTcRows * kOut; j += kTcThreads) {
+        const int s = j / kOut;
+        sm.Tg[s][j - s * kOut] = s < ns ? Tgt[s0 * kOut + j] : 0.0f;
+    }
+    // rows 128.. of the dW2 operand: ones over the tile's samples (db2), zeros
+    for (int j = tid; j < (kN3 - kH) * kH; j += kTcThreads) {
+        const int r = kH + j / kH, s = j % kH;
+        st_bf16(sm.R4, r, s, r == kH && s < ns ? 1.0f : 0.0f);
+    }
+    const uint32_t mbar = smem_u32(&sm.mbar);
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&sm.tmem_base)),
+                     "r"(kTrCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    to_tensor_cores();
+    const uint32_t tmem = sm.tmem_base;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t r0 = smem_u32(sm.R0), r1 = smem_u32(sm.R1), r2 = smem_u32(sm.R2),
+                   r3 = smem_u32(sm.R3), r4 = smem_u32(sm.R4), r5 = smem_u32(sm.R5);
+    float x[kIn];
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) x[c] = sm.X[row][c];
+    // a1 = W1 x + b1 of hidden unit i
+    auto pre1 = [&](int i) {
+        const float4 wa = sm.W1b[i][0], wb = sm.W1b[i][1];
+        float a = wb.y;
+        a = fmaf(wa.x, x[0], a);
+        a = fmaf(wa.y, x[1], a);
+        a = fmaf(wa.z, x[2], a);
+        a = fmaf(wa.w, x[3], a);
+        return fmaf(wb.x, x[4], a);
+    };
+    // ---- layer 1: h1 = gelu(a1) as BF16 hi + lo (forward A) and hi (dW2 B) ----
+#pragma unroll 1
+    for (int k8 = half * 8; k8 < half * 8 + 8; ++k8) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float hv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) hv[e] = live ? gelu(pre1(k8 * 8 + 2 * q + e)) : 0.0f;
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(hv[0], hv[1]);
+            const __nv_bfloat162 lb =
+                __floats2bfloat162_rn(hv[0] - __low2float(hb), hv[1] - __high2float(hb));
+            hi[q] = *reinterpret_cast<const uint32_t *>(&hb);
+            lo[q] = *reinterpret_cast<const uint32_t *>(&lb);
+            *reinterpret_cast<__nv_bfloat16 *>(sm.R4 + core_off(k8 * 8 + 2 * q, row)) = hb.x;
+            *reinterpret_cast<__nv_bfloat16 *>(sm.R4 + core_off(k8 * 8 + 2 * q + 1, row)) = hb.y;
+        }
+        const uint32_t off = core_off(row, k8 * 8);
+        *reinterpret_cast<uint4 *>(sm.R2 + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(sm.R3 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    to_tensor_cores();
+    if (tid == 0) {
+        umma_k128(tmem, r2, r0, kH);  // h1 hi W2^T
+#pragma unroll
+        for (int ks = 0; ks < kH / 16; ++ks)  // + h1 lo W2^T
+            umma_bf16_n(tmem, umma_desc(r3 + ks * 256, 128, 2048),
+                        umma_desc(r0 + ks * 256, 128, 2048), idesc_bf16(kH), 1u);
+        umma_commit(mbar);
+    }
+    uint32_t phase = 0;
+    // every thread waits; the outcome is made the same for the whole CTA; on
+    // expiry the kernel flags it, waits once more (bounded) for the MMAs in
+    // flight, frees its tensor memory and returns
+    auto wait_mma = [&]() {
+        const bool ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (!ok && tid == 0) atomicOr(err, 1);
+        if (!ok) mbar_wait(mbar, phase ^ 1u);
+        return ok;
+    };
+    bool ok = wait_mma();
+    if (ok) {
+        // ---- output layer, loss and dY = dL/dy ----
+        float y[kOut];
+#pragma unroll
+        for (int r = 0; r < kOut; ++r) y[r] = half == 0 ? sm.b3[r] : 0.0f;
+#pragma unroll 1
+        for (int c32 = 0; c32 < 2; ++c32) {
+            const int col0 = half * 64 + c32 * 32;
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)col0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int o = col0 + j;
+                const float h2 = gelu(v[j] + sm.b2[o]);
+                const float4 w0 = sm.W3t[o][0], w1 = sm.W3t[o][1], w2 = sm.W3t[o][2];
+                y[0] = fmaf(w0.x, h2, y[0]); y[1] = fmaf(w0.y, h2, y[1]);
+                y[2] = fmaf(w0.z, h2, y[2]); y[3] = fmaf(w0.w, h2, y[3]);
+                y[4] = fmaf(w1.x, h2, y[4]); y[5] = fmaf(w1.y, h2, y[5]);
+                y[6] = fmaf(w1.z, h2, y[6]); y[7] = fmaf(w1.w, h2, y[7]);
+                y[8] = fmaf(w2.x, h2, y[8]); y[9] = fmaf(w2.y, h2, y[9]);
+                y[10] = fmaf(w2.z, h2, y[10]); y[11] = fmaf(w2.w, h2, y[11]);
+            }
+        }
+        if (half == 1) {
+#pragma unroll
+            for (int r = 0; r < kOut; ++r) sm.part[row][r] = y[r];
+        }
+        __syncthreads();
+        float lsum = 0.0f;
+        if (half == 0) {
+#pragma unroll
+            for (int r = 0; r < kOut; ++r) {
+                float d = 0.0f;
+                if (live) {
+                    const float yr = y[r] + sm.part[row][r];
+                    if (Yout) Yout[(s0 + row) * kOut + r] = yr;
+                    const float res = yr - sm.Tg[row][r];
+                    lsum = fmaf(res, res, lsum);
+                    d = 2.0f * res * inv_n;
+                }
+                sm.dY[row][r] = d;
+                st_bf16(sm.R5, r, row, d);  // dY^T (B of dW3)
+            }
+#pragma unroll
+            for (int r = kOut; r < 16; ++r) st_bf16(sm.R5, r, row, 0.0f);
+        }
+        // loss and db3 = sum_s dY[s][r]: warp sums, then one atomic per warp
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, d);
+        if (lane == 0) sm.red[warp] = lsum;
+        if (half == 0) {
+#pragma unroll
+            for (int r = 0; r < kOut; ++r) {
+                float g = sm.dY[row][r];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) g += __shfl_xor_sync(0xffffffffu, g, d);
+                if (lane == 0 && g != 0.0f) atomicAdd(&grad[ob3 + r], g);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && loss) {
+            double t = 0.0;
+            for (int w = 0; w < kTcThreads / 32; ++w) t += sm.red[w];
+            atomicAdd(loss, t);
+        }
+        // ---- da2 = (dY W3) gelu'(a2): A of dh1, A^T of dW2; h2^T for dW3 ----
+#pragma unroll 1
+        for (int c32 = 0; c32 < 2; ++c32) {
+            const int col0 = half * 64 + c32 * 32;
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)col0, v);
+#pragma unroll 1
+            for (int j8 = 0; j8 < 32; j8 += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float dv[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int j = j8 + 2 * q + e, o = col0 + j;
+                        const float a2 = v[j] + sm.b2[o];
+                        const GeluParts gp = gelu_parts(a2);
+                        const float h2 = a2 * gelu_phi(a2, gp.E);
+                        const float gd = fmaf(a2 * 0.39894228040143268f, gp.g, gelu_phi(a2, gp.E));
+                        const float4 w0 = sm.W3t[o][0], w1 = sm.W3t[o][1], w2 = sm.W3t[o][2];
+                        const float *dy = sm.dY[row];
+                        float dz = w0.x * dy[0];
+                        dz = fmaf(w0.y, dy[1], dz); dz = fmaf(w0.z, dy[2], dz);
+                        dz = fmaf(w0.w, dy[3], dz); dz = fmaf(w1.x, dy[4], dz);
+                        dz = fmaf(w1.y, dy[5], dz); dz = fmaf(w1.z, dy[6], dz);
+                        dz = fmaf(w1.w, dy[7], dz); dz = fmaf(w2.x, dy[8], dz);
+                        dz = fmaf(w2.y, dy[9], dz); dz = fmaf(w2.z, dy[10], dz);
+                        dz = fmaf(w2.w, dy[11], dz);
+                        dv[e] = dz * gd;
+                        st_bf16(sm.R3, o, row, dv[e]);             // da2^T (A of dW2)
+                        st_bf16(sm.R0, o, row, live ? h2 : 0.0f);  // h2^T (A of dW3)
+                    }
+                    const __nv_bfloat162 db = __floats2bfloat162_rn(dv[0], dv[1]);
+                    pk[q] = *reinterpret_cast<const uint32_t *>(&db);
+                }
+                *reinterpret_cast<uint4 *>(sm.R2 + core_off(row, col0 + j8)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);  // da2 (A of dh1)
+            }
+        }
+        to_tensor_cores();
+        if (tid == 0) {
+            umma_k128(tmem + kColD2, r2, r1, kH);   // dh1 = da2 W2
+            umma_k128(tmem + kColD3, r3, r4, kN3);  // [dW2 | db2] = da2^T [h1 | 1]
+            umma_k128(tmem + kColD4, r0, r5, 16);   // dW3^T = h2^T dY
+            umma_commit(mbar);
+        }
+        ok = wait_mma();
+    }
+    if (ok) {
+        // ---- da1 = dh1 gelu'(a1): A^T of dW1; [x | 1]^T as its B ----
+#pragma unroll 1
+        for (int c32 = 0; c32 < 2; ++c32) {
+            const int col0 = half * 64 + c32 * 32;
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(kColD2 + col0), v);
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) {
+                const int i = col0 + j;
+                st_bf16(sm.R1, i, row, live ? v[j] * gelu_grad(pre1(i)) : 0.0f);
+            }
+        }
+        if (half == 0) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                st_bf16(sm.R5, c, row, !live ? 0.0f : c < kIn ? x[c] : c == kIn ? 1.0f : 0.0f);
+        }
+        to_tensor_cores();
+        if (tid == 0) {
+            umma_k128(tmem + kColD5, r1, r5, 16);  // [dW1 | db1] = da1^T [x | 1]
+            umma_commit(mbar);
+        }
+        ok = wait_mma();
+    }
+    if (ok) {
+        // ---- the tile's weight gradients, out of TMEM (row = o or i) ----
+        const int m = row;
+#pragma unroll 1
+        for (int c32 = 0; c32 < 2; ++c32) {  // dW2[m][i], this thread's 64 columns
+            const int col0 = half * 64 + c32 * 32;
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(kColD3 + col0), v);
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) atomicAdd(&grad[oW2 + m * kH + col0 + j], v[j]);
+        }
+        float v[32];
+        if (half == 0) {
+            tmem_ld32(tmem + lane_base + (uint32_t)kColD4, v);  // dW3[r][m], r < 12
+#pragma unroll
+            for (int r = 0; r < kOut; ++r) atomicAdd(&grad[oW3 + r * kH + m], v[r]);
+        } else {
+            tmem_ld32(tmem + lane_base + (uint32_t)(kColD3 + kH), v);  // db2[m]
+            atomicAdd(&grad[ob2 + m], v[0]);
+            tmem_ld32(tmem + lane_base + (uint32_t)kColD5, v);  // dW1[m][c], db1[m]
+#pragma unroll
+            for (int c = 0; c < kIn; ++c) atomicAdd(&grad[oW1 + m * kIn + c], v[c]);
+            atomicAdd(&grad[ob1 + m], v[kIn]);
+        }
+    }
+    // the accumulators are free once every thread's loads are done
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(kTrCols)
+                     : "memory");
+    }
+}
+
+static_assert(sizeof(TrSmem) <= 227 * 1024, "training tile exceeds the per-CTA shared memory");
+static_assert(kColD5 + 32 <= kTrCols && kColD3 + kH + 32 <= kTrCols, "TMEM loads stay allocated");
+
+
 static_assert(2 * (sizeof(TcSmem) + 1024) <= 228 * 1024,
               "two inference CTAs must fit an SM's shared memory");
 static_assert(kTcRows * (kOut + 1) * sizeof(float) <= kTileBytes, "partials fit one operand tile");
-size_t sur_smem() { return sizeof(SurSmem); }
+size_t sur_smem() { return sizeof(TrSmem); }
 
 }  // namespace
 
@@ -922,10 +1012,22 @@ void sur_train_step(mrsim_ctx *c, const float *P, const void *W2b, const void *W
         attr = true;
     }
     KScope ks(c, "sur_train");
-    const unsigned grid = (unsigned)((n + kTS - 1) / kTS);
-    k_sur_train<<<grid, kNT, sur_smem(), c->stream>>>(
+    const unsigned grid = (unsigned)((n + kTcRows - 1) / kTcRows);
+    k_sur_train<<<grid, kTcThreads, sur_smem(), c->stream>>>(
         P, (const __nv_bfloat16 *)W2b, (const __nv_bfloat16 *)W2Tb, X, T, n,
-        1.0f / (12.0f * (float)n), grad, loss, Yout);
+        1.0f / (12.0f * (float)n), grad, loss, Yout, c->dev_err.as<int>() + kErrWordTensor);
+}
+
+void sur_tensor_err_reset(mrsim_ctx *c) {
+    MRSIM_CUDA(cudaMemsetAsync(c->dev_err.as<int>() + kErrWordTensor, 0, sizeof(int), c->stream));
+}
+
+void sur_tensor_err_check(mrsim_ctx *c) {
+    int h = 0;
+    MRSIM_CUDA(cudaMemcpyAsync(&h, c->dev_err.as<int>() + kErrWordTensor, sizeof(int),
+                               cudaMemcpyDeviceToHost, c->stream));
+    MRSIM_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) fail(MRSIM_ETIMEOUT, "tensor-core training: a bounded mbarrier wait ran out");
 }
 
 void sur_adam(mrsim_ctx *c, float *P, float *grad, float *m, float *v, int step, float lr,
@@ -964,14 +1066,13 @@ void launch_sur_infer(mrsim_ctx *c, const float *P, const void *W2b, const FeatC
     MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
     {
         KScope ks(c, "sur_infer");
-        int occ = 0;
-        MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sur_infer, kTcThreads,
-                                                                 sizeof(TcSmem)));
-        // persistent CTAs over the tiles (the served count is on the device):
-        // every CTA holds 128 of an SM's 512 TMEM columns
+        // persistent CTAs over the tiles (the served count is on the device),
+        // two per SM: the kernel is built for that (registers and shared
+        // memory are asserted above; each CTA holds 128 of the SM's 512 TMEM
+        // columns), so one CTA's FP32 layers overlap the other's MMAs
         const int64_t tiles = (G + kTcRows - 1) / kTcRows;
-        const unsigned grid = (unsigned)std::max<int64_t>(
-            1, std::min<int64_t>(tiles, (int64_t)c->sm_count * std::max(std::min(occ, 4), 1)));
+        const unsigned grid =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)c->sm_count * 2));
         k_sur_infer<<<grid, kTcThreads, sizeof(TcSmem), c->stream>>>(
             P, (const __nv_bfloat16 *)W2b, fc, pulse, par, G, srv, cnt, out, err, X, n_x);
     }

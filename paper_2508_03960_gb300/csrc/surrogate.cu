@@ -179,6 +179,7 @@ int mrsim_surrogate_train(mrsim_ctx *c, const mrsim_seq *s, const double *lo, co
             const double lr0 = lr, lr1 = lr * 1e-2;
             int64_t it = 0;
             double last = 0;
+            sur_tensor_err_reset(c);
             for (int ep = 0; ep < epochs; ++ep) {
                 MRSIM_CUDA(cudaMemsetAsync(loss.p, 0, sizeof(double), c->stream));
                 for (int64_t st = 0; st < steps; ++st, ++it) {
@@ -193,6 +194,7 @@ int mrsim_surrogate_train(mrsim_ctx *c, const mrsim_seq *s, const double *lo, co
                 MRSIM_CUDA(cudaMemcpyAsync(&h, loss.p, sizeof(double), cudaMemcpyDeviceToHost,
                                            c->stream));
                 sync(c);
+                sur_tensor_err_check(c);
                 last = h / (12.0 * (double)n_train);
             }
             net.loss = last;
@@ -334,8 +336,10 @@ int mrsim_surrogate_eval(mrsim_ctx *c, const float *params, int64_t n, const flo
         MRSIM_CUDA(cudaMemsetAsync(g.p, 0, NP * 4, c->stream));
         MRSIM_CUDA(cudaMemsetAsync(L.p, 0, 8, c->stream));
         sur_bf16_copies(c, P.as<float>(), W2b.p, W2Tb.p);
+        sur_tensor_err_reset(c);
         sur_train_step(c, P.as<float>(), W2b.p, W2Tb.p, X.as<float>(), T.as<float>(), n,
                        g.as<float>(), L.as<double>(), Y.as<float>());
+        sur_tensor_err_check(c);
         if (y) MRSIM_CUDA(cudaMemcpyAsync(y, Y.p, n * 12 * 4, cudaMemcpyDeviceToHost, c->stream));
         if (grad_out)
             MRSIM_CUDA(cudaMemcpyAsync(grad_out, g.p, NP * 4, cudaMemcpyDeviceToHost, c->stream));
