@@ -106,7 +106,12 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
-FUSED_SOURCES = {"fused_cell": ("k_cell.cu", "internal.h", "common.cuh"),
+# The source a fused kernel is compiled from: whole files, or (file, first
+# line's text, text of the line that ends the part) for the part of a shared
+# header that holds the kernel's argument and event records.
+FUSED_SOURCES = {"fused_cell": ("k_cell.cu", "common.cuh",
+                                ("internal.h", "// Cell mode of the fused kernel",
+                                 "struct CellKey {")),
                  "fused_grouped": ("k_grouped.cu", "common.cuh")}
 
 
@@ -114,8 +119,13 @@ def kernel_source_sha(kind):
     import hashlib
     h = hashlib.sha256()
     for src in FUSED_SOURCES[kind]:
-        with open(os.path.join(ROOT, "paper_2508_03960_gb300", "csrc", src), "rb") as f:
-            h.update(f.read())
+        name, first, stop = (src, None, None) if isinstance(src, str) else src
+        with open(os.path.join(ROOT, "paper_2508_03960_gb300", "csrc", name), "rb") as f:
+            data = f.read()
+        if first is not None:
+            i = data.index(first.encode())
+            data = data[i:data.index(stop.encode(), i)]
+        h.update(data)
     return h.hexdigest()
 
 
