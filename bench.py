@@ -711,7 +711,10 @@ def main():
     if a.tune == "on":
         tuned = mrsim.mrsim_autotune(ctx.h, hp, hs_f, hg_f, mrsim.GROUPED, mrsim.FP32, 2)
     else:
-        tuned = {p: mrsim.mrsim_get_tuning(ctx.h, p) for p in range(6)}
+        tuned = {p: mrsim.mrsim_get_tuning(ctx.h, p) for p in
+                 (mrsim.TUNE_FUSED_NI, mrsim.TUNE_PLAIN_RF_NI, mrsim.TUNE_ADC_CTAS_PER_SM,
+                  mrsim.TUNE_PRECOMP_LANES, mrsim.TUNE_PRECOMP_STEPS, mrsim.TUNE_CELL_NI,
+                  mrsim.TUNE_CELL_ROWS)}
     autotune_s = time.perf_counter() - t0
 
     ns_f, ns_e = fse.n_samples, epi.n_samples
@@ -1014,6 +1017,8 @@ def main():
         "isochromat_steps_per_s_equiv": round(steps_fse / fse_s, 1),
         "prep_s": round(prep_s, 4), "phantom_upload_s": round(t_upload, 4), "groups": groups,
         "autotune": {"cell_isochromats_per_thread": tuned[mrsim.TUNE_CELL_NI],
+                     "cell_rows": {0: "auto", 1: "table", 2: "per thread"}[
+                         tuned[mrsim.TUNE_CELL_ROWS]],
                      "fused_isochromats_per_thread": tuned[mrsim.TUNE_FUSED_NI],
                      "plain_rf_isochromats_per_thread": tuned[mrsim.TUNE_PLAIN_RF_NI],
                      "plain_adc_ctas_per_sm": tuned[mrsim.TUNE_ADC_CTAS_PER_SM],

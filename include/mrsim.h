@@ -415,6 +415,14 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *                              Sec. 2.4 keys its Sec. 5 leaves open); 0 types
  *                              them MRSIM_G_GENERAL (per-isochromat fallback).
  *                              Not a launch parameter: mrsim_autotune leaves it.
+ *   MRSIM_TUNE_CELL_ROWS       the combined rows C = T Adv of the cell form: 0
+ *                              (default) a table per run when it holds at most
+ *                              four times the state's bytes (and 1 GiB), else
+ *                              formed by each thread from the transition and
+ *                              group-factor tables; 1 the table whenever it fits
+ *                              1 GiB; 2 always per thread.  Both give the same
+ *                              rows up to FP32 rounding order (the per-thread
+ *                              form is the same arithmetic as the table builder).
  * mrsim_set_tuning returns MRSIM_EINVAL for another parameter or value. */
 #define MRSIM_TUNE_FUSED_NI 0
 #define MRSIM_TUNE_PLAIN_RF_NI 1
@@ -423,6 +431,7 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
 #define MRSIM_TUNE_PRECOMP_STEPS 4
 #define MRSIM_TUNE_CELL_NI 5
 #define MRSIM_TUNE_TWO_AXIS 6
+#define MRSIM_TUNE_CELL_ROWS 7
 int mrsim_set_tuning(mrsim_ctx *ctx, int param, int value);
 int mrsim_get_tuning(const mrsim_ctx *ctx, int param, int *value);
 

@@ -459,6 +459,7 @@ struct GPlan {
     int ax_max = 0;         // longest table
     // cell form of the fused kernel (FP32): see CellArgs
     bool cell = false;
+    bool otf = false;       // cell form with rows formed per thread (no row table)
     int cell_w = 0;         // 0: 4 isochromats per thread, 1: 8
     int free_bits = 0, r_axis = -1;
     CellForm form{};
@@ -655,6 +656,9 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
             int fa[2] = {-1, -1}, nfa = 0;
             for (int a = 0; a < 3; ++a)
                 if (P.free_bits & (1 << a)) fa[nfa++] = a;
+            // combined rows: 0 automatic, 1 a table when it fits 1 GiB, 2 per thread
+            const int rows_mode = c->tune[MRSIM_TUNE_CELL_ROWS];
+            P.otf = rows_mode == 2;
             P.cev.resize(P.ev.size());
             for (size_t i = 0; i < P.ev.size() && P.cell; ++i) {
                 const FEvent<R> &e = P.ev[i];
@@ -681,6 +685,12 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
                 k.tau = P.adv[i].tau;
                 k.prow = e.prow;
                 k.qr = (P.r_axis >= 0 && (ev_mask(e.op) & rbit)) ? e.q[P.r_axis] : -1;
+                // the same key, for the form that builds the row per thread
+                ce.win = k.trow;
+                ce.gtype = k.gtype;
+                ce.qr = k.qr;
+                ce.prow = k.prow;
+                if (P.otf) continue;
                 int id = -1;
                 for (size_t j = 0; j < P.ckeys.size() && id < 0; ++j) {
                     const CellKey &o = P.ckeys[j];
@@ -691,9 +701,18 @@ void plan_grouped(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, GPlan
                 if (id < 0) {
                     id = (int)P.ckeys.size();
                     P.ckeys.push_back(k);
-                    // combined rows within 1 GiB (and row indices within int32)
-                    if ((int64_t)P.ckeys.size() * g->n_cells * 48 > ((int64_t)1 << 30))
-                        P.cell = false;
+                    // a row table within 1 GiB (and row indices within int32)
+                    // and, unless asked for, within four times the state;
+                    // beyond, every thread forms its cell's rows itself
+                    const int64_t bytes = (int64_t)P.ckeys.size() * g->n_cells * 48;
+                    if (bytes > ((int64_t)1 << 30) ||
+                        (rows_mode == 0 && bytes > 4 * 12 * g->K)) {
+                        P.otf = true;
+                        P.ckeys.clear();
+                        for (size_t j = 0; j <= i; ++j)
+                            if (P.cev[j].kind <= CE_END) P.cev[j].row = 0;
+                        continue;
+                    }
                 }
                 ce.row = (int)((int64_t)id * g->n_cells);
             }
@@ -832,9 +851,11 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     CellEv *d_cev = nullptr;
     if constexpr (sizeof(R) == 4) {
         if (P.cell) {
-            const int nk = (int)P.ckeys.size();
-            float *C_tab = (float *)scratch(
-                c, 23, std::max<int64_t>((int64_t)nk * g->n_cells, 1) * 12 * sizeof(float));
+            const int nk = P.otf ? 0 : (int)P.ckeys.size();
+            float *C_tab = P.otf ? nullptr
+                                 : (float *)scratch(c, 23,
+                                                    std::max<int64_t>((int64_t)nk * g->n_cells, 1) *
+                                                        12 * sizeof(float));
             if (nk > 0) {
                 CellKey *d_keys = (CellKey *)scratch(c, 24, nk * sizeof(CellKey));
                 upload(c, d_keys, P.ckeys.data(), nk * sizeof(CellKey));
@@ -857,6 +878,11 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
             ca.P_raw = d_P;
             ca.Ablk = Ablk;
             ca.fx = c->fx;
+            ca.otf = P.otf ? 1 : 0;
+            ca.T_tab = T_tab;
+            ca.cell_gr = g->cell_gr.as<int32_t>();
+            ca.gtype_p = P.p;
+            ca.gtype_r = g->secondary;
             ca.qtab = fa.qtab;
             int nf = 0;
             for (int a = 0; a < 3; ++a)
@@ -998,7 +1024,7 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         key.push_back(s[i]->uid);
         key.push_back(g[i]->uid);
     }
-    for (int t = 0; t < 7; ++t) key.push_back((uint64_t)c->tune[t]);
+    for (int t = 0; t < 8; ++t) key.push_back((uint64_t)c->tune[t]);
     auto &slot = batch_caches()[c];
     if (!slot || slot->key != key) {
         auto bc = std::make_unique<BatchCache>();
@@ -1727,11 +1753,11 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
 
 int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
-    static const int allowed[7][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
+    static const int allowed[8][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
                                       {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
                                       {1, 2, 4, 8, 16, 32}, {0, 4, 8, -1, -1, -1},
-                                      {0, 1, -1, -1, -1, -1}};
-    if (param < 0 || param > 6) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
+                                      {0, 1, -1, -1, -1, -1}, {0, 1, 2, -1, -1, -1}};
+    if (param < 0 || param > 7) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
     for (int v : allowed[param]) ok |= v >= 0 && v == value;
     if (!ok) return set_err(c, MRSIM_EINVAL, "value not allowed for this tuning parameter");
@@ -1740,7 +1766,7 @@ int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
 }
 
 int mrsim_get_tuning(const mrsim_ctx *c, int param, int *value) {
-    if (!c || !value || param < 0 || param > 6) return MRSIM_EINVAL;
+    if (!c || !value || param < 0 || param > 7) return MRSIM_EINVAL;
     *value = c->tune[param];
     return MRSIM_OK;
 }
@@ -1760,6 +1786,7 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
         std::vector<std::pair<int, std::vector<int>>> plan;
         if (grouped && precision == MRSIM_FP32) plan.push_back({MRSIM_TUNE_CELL_NI, {4, 8, 0}});
+        if (grouped && precision == MRSIM_FP32) plan.push_back({MRSIM_TUNE_CELL_ROWS, {0, 2}});
         if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8, 16, 32}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 4, 8, 16, 32, 128}});

@@ -76,7 +76,7 @@ struct mrsim_ctx {
     const struct mrsim_surrogate *sur = nullptr;
     int64_t sur_groups = 0, sur_fallback = 0;
     // launch parameters chosen by mrsim_autotune (or mrsim_set_tuning)
-    int tune[7] = {4, 2, 2, 0, 8, 8, 1};  // indexed by the MRSIM_TUNE_* parameters
+    int tune[8] = {4, 2, 2, 0, 8, 8, 1, 0};  // indexed by the MRSIM_TUNE_* parameters
     // reproducible sums (mrsim_set_reproducible) and, during a run, the
     // fixed-point scale of the sum buffers (0: FP64 atomics)
     int repro = 0;
@@ -357,18 +357,22 @@ struct FusedArgs {
 // cell, so the positions on the primary axis and (if any) the secondary axis,
 // T1, T2, dB0 and b1 are the thread's own; only the phase on the remaining
 // ("free") axes differs between its isochromats.  An RF event then applies one
-// combined row C = T Adv per cell; a with-ADC event adds Q_free M_xy.
+// combined row C = T Adv per cell; a with-ADC event adds Q_free M_xy.  The
+// rows are read from a table built per run, or (when cells are too many for
+// it) formed by each thread from the transition and group-factor tables.
 // Event record of the cell form (32 bytes), decoded on the host.
 enum CellEvKind : int { CE_RF = 0, CE_END = 1, CE_ADC = 2, CE_ADC_OTHER = 3 };
 struct CellEv {
     int kind;   // CellEvKind (CE_ADC: a window of the primary type)
-    int row;    // RF / END: first combined row (key * n_cells); ADC: first
-                // group-factor row (event * G_primary)
-    int win;    // ADC: offset of the window's block sums (complex entries)
-    int gtype;  // CE_ADC_OTHER: the window's gradient type
+    int row;    // RF / END: first combined row (key * n_cells), table form;
+                // ADC: first group-factor row (event * G_primary)
+    int win;    // ADC: offset of the window's block sums (complex entries);
+                // RF / END: first transition row of the event's type (-1: END)
+    int gtype;  // CE_ADC_OTHER: the window's gradient type; RF: the pulse's type
     int qf[2];  // free-axis phasor table offsets (lower axis first)
-    int qr;     // ADC: secondary-axis phasor table offset
-    int pad;
+    int qr;     // secondary-axis phasor table offset (RF: -1 when the advance
+                // has no moment on that axis)
+    int prow;   // RF / END: first group-factor row of the event's advance
 };
 struct CellArgs {
     int64_t n_thr;            // threads that hold isochromats
@@ -398,6 +402,12 @@ struct CellArgs {
     // phasor flags of the form (kernels compiled for coils read them here)
     int rfq, adq, rb;
     double fx;                // fixed-point scale of the block sums (0: FP64 atomics)
+    // rows formed per thread (otf = 1; C_tab unused): the transition table,
+    // each cell's secondary group and the layout's primary / secondary types
+    int otf;
+    const float *T_tab;
+    const int32_t *cell_gr;
+    int gtype_p, gtype_r;
 };
 // Which per-isochromat and per-thread phasors a cell-form launch applies
 // (fixed for the whole span, so the kernel is specialised on them).

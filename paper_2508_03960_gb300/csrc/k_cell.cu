@@ -75,7 +75,8 @@ __device__ __forceinline__ void free_phasor(const float2 *qtab, const int (&qf)[
 
 // RFQ / ADQ / RB: 0 or 1 fixes the phasor flag at compile time, 2 reads it from
 // the arguments.  PC: receive coils handled in this pass (0: S = 1).
-template <int NI, int NF, int RFQ, int ADQ, int RB, int PC>
+// OTF: the combined rows are formed by each thread (no row table).
+template <int NI, int NF, int RFQ, int ADQ, int RB, int PC, bool OTF>
 __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4 ? 4 : 2))
     k_fused_cell(CellArgs a) {
     using Smem = CellSmem<PC>;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
     int f0[NI], f1[NI];  // free-axis table indices of each isochromat
     // isochromat i of this thread is layout position start + i * stride
     int key = kPad, cell = 0, start = 0, stride = 0, n = 0, ridx = 0;
+    int g_sec = 0, g_none = 0;  // the cell's secondary and no-grads groups (rows per thread)
     if (t < a.n_thr) {
         const int2 d = a.thr[t];
         start = d.x;
@@ -102,6 +104,10 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
         n = min(d.y & 15, NI);  // descriptors are built for this width
         key = a.cell_gp[cell];
         stride = (a.cell_count[cell] + NI - 1) / NI;
+        if constexpr (OTF) {
+            if (a.gtype_r >= 0) g_sec = a.cell_gr[cell];
+            if (a.gid[G_NONE]) g_none = a.gid[G_NONE][start];
+        }
     }
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
         }
         f0[i] = (ai >> a.f_sh[0]) & 0xffff;
         f1[i] = NF == 2 ? (ai >> a.f_sh[1]) & 0xffff : 0;
-        if (i == 0 && RB != 0) ridx = (ai >> a.r_sh) & 0xffff;
+        if (i == 0 && (RB != 0 || OTF)) ridx = (ai >> a.r_sh) & 0xffff;
     }
     // primary groups of this CTA: keys rise along the threads and every group
     // between the first and the last one has isochromats here
@@ -284,9 +290,50 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
             if (kind <= CE_END) {
                 // RF: advance and transition, M <- C (Q M); END: the advance
                 // alone (C built with T = I), then the state is stored
-                const float4 *cr =
-                    reinterpret_cast<const float4 *>(a.C_tab + ((int64_t)ev0.y + cell) * 12);
-                const float4 r0 = __ldg(cr), r1 = __ldg(cr + 1), r2 = __ldg(cr + 2);
+                float4 r0, r1, r2;
+                if constexpr (!OTF) {
+                    const float4 *cr =
+                        reinterpret_cast<const float4 *>(a.C_tab + ((int64_t)ev0.y + cell) * 12);
+                    r0 = __ldg(cr);
+                    r1 = __ldg(cr + 1);
+                    r2 = __ldg(cr + 2);
+                } else {
+                    // the row C = T Adv of this cell, as the row table would
+                    // hold it: the group factor (E2 e^{-i phi}, E1) of the
+                    // cell's primary group, times the secondary-axis phasor,
+                    // under the transition of the pulse's group
+                    const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
+                    const float4 P = __ldg(Pt + sm.sev[e].prow + pkey);
+                    float fr = P.x, fi = P.y;
+                    if (ev1.z >= 0) {
+                        const float2 q = __ldg(qtab + ev1.z + ridx);
+                        const float tr = fr * q.x + fi * q.y;  // P exp(-i psi)
+                        fi = fi * q.x - fr * q.y;
+                        fr = tr;
+                    }
+                    const float E1 = P.z, u = 1.0f - P.z;
+                    if (ev0.z < 0) {
+                        r0 = make_float4(fr, -fi, 0.0f, 0.0f);
+                        r1 = make_float4(fi, fr, 0.0f, 0.0f);
+                        r2 = make_float4(0.0f, 0.0f, E1, u);
+                    } else {
+                        const int gt =
+                            ev0.w == a.gtype_p ? pkey : ev0.w == a.gtype_r ? g_sec : g_none;
+                        const float4 *T =
+                            reinterpret_cast<const float4 *>(a.T_tab + ((int64_t)ev0.z + gt) * 12);
+                        float4 tv[3] = {__ldg(T), __ldg(T + 1), __ldg(T + 2)};
+                        float4 rr[3];
+#pragma unroll
+                        for (int row = 0; row < 3; ++row) {
+                            const float4 tt = tv[row];  // A0, A1, A2, b
+                            rr[row] = make_float4(tt.x * fr + tt.y * fi, tt.y * fr - tt.x * fi,
+                                                  tt.z * E1, fmaf(tt.z, u, tt.w));
+                        }
+                        r0 = rr[0];
+                        r1 = rr[1];
+                        r2 = rr[2];
+                    }
+                }
                 int qf[2] = {0, 0};
                 if (rfq) {
                     const int4 ev1 = *reinterpret_cast<const int4 *>(&sm.sev[e].qf[0]);
@@ -392,13 +439,19 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
 template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
 void launch_cell_v(mrsim_ctx *c, const CellArgs &a) {
     const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
-    k_fused_cell<NI, NF, RFQ, ADQ, RB, 0><<<nb, kThreads, 0, c->stream>>>(a);
+    k_fused_cell<NI, NF, RFQ, ADQ, RB, 0, false><<<nb, kThreads, 0, c->stream>>>(a);
 }
 // receive coils: 4 isochromats per thread, phasor flags read at run time
-template <int NF, int PC>
+template <int NF, int PC, bool OTF>
 void launch_cell_coil(mrsim_ctx *c, const CellArgs &a) {
     const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
-    k_fused_cell<4, NF, 2, 2, 2, PC><<<nb, kThreads, 0, c->stream>>>(a);
+    k_fused_cell<4, NF, 2, 2, 2, PC, OTF><<<nb, kThreads, 0, c->stream>>>(a);
+}
+// rows formed per thread: phasor flags read at run time
+template <int NI, int NF>
+void launch_cell_otf(mrsim_ctx *c, const CellArgs &a) {
+    const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
+    k_fused_cell<NI, NF, 2, 2, 2, 0, true><<<nb, kThreads, 0, c->stream>>>(a);
 }
 template <int NI, int NF, bool RFQ, bool ADQ>
 void launch_cell_rb(mrsim_ctx *c, const CellArgs &a, bool rb) {
@@ -459,26 +512,42 @@ __global__ void k_cell_rows(const CellKey *keys, int n_keys, int64_t nc, const i
 
 }  // namespace
 
+template <bool OTF>
+void launch_cell_coils(mrsim_ctx *c, const CellArgs &b, const CellForm &f) {
+    if (f.nf == 2) {
+        if (f.pc == 4) launch_cell_coil<2, 4, OTF>(c, b);
+        else if (f.pc == 2) launch_cell_coil<2, 2, OTF>(c, b);
+        else launch_cell_coil<2, 1, OTF>(c, b);
+    } else {
+        if (f.pc == 4) launch_cell_coil<1, 4, OTF>(c, b);
+        else if (f.pc == 2) launch_cell_coil<1, 2, OTF>(c, b);
+        else launch_cell_coil<1, 1, OTF>(c, b);
+    }
+}
+
 void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
     if (a.n_thr <= 0) return;
+    CellArgs b = a;
+    b.rfq = f.rfq;
+    b.adq = f.adq;
+    b.rb = f.rb;
     if (f.pc > 0) {
         KScope ks(c, "fused_cell_coils_f32");
-        CellArgs b = a;
-        b.rfq = f.rfq;
-        b.adq = f.adq;
-        b.rb = f.rb;
-        if (f.nf == 2) {
-            if (f.pc == 4) launch_cell_coil<2, 4>(c, b);
-            else if (f.pc == 2) launch_cell_coil<2, 2>(c, b);
-            else launch_cell_coil<2, 1>(c, b);
-        } else {
-            if (f.pc == 4) launch_cell_coil<1, 4>(c, b);
-            else if (f.pc == 2) launch_cell_coil<1, 2>(c, b);
-            else launch_cell_coil<1, 1>(c, b);
-        }
+        if (a.otf) launch_cell_coils<true>(c, b, f);
+        else launch_cell_coils<false>(c, b, f);
         return;
     }
     KScope ks(c, "fused_cell_f32");
+    if (a.otf) {
+        if (f.ni == 8) {
+            if (f.nf == 2) launch_cell_otf<8, 2>(c, b);
+            else launch_cell_otf<8, 1>(c, b);
+        } else {
+            if (f.nf == 2) launch_cell_otf<4, 2>(c, b);
+            else launch_cell_otf<4, 1>(c, b);
+        }
+        return;
+    }
     if (f.ni == 8) {
         if (f.nf == 2) launch_cell_q<8, 2>(c, a, f);
         else launch_cell_q<8, 1>(c, a, f);

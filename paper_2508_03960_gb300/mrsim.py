@@ -30,6 +30,7 @@ TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1
 TUNE_PRECOMP_STEPS = 4
 TUNE_CELL_NI = 5
 TUNE_TWO_AXIS = 6
+TUNE_CELL_ROWS = 7
 
 # every entry point declared in include/mrsim.h
 EXPORTS = ["mrsim_create", "mrsim_destroy", "mrsim_last_error", "mrsim_phantom",
@@ -368,7 +369,8 @@ def mrsim_autotune(ctx, ph, seq, groups, mode, precision, reps=1):
            "mrsim_autotune")
     return {p: mrsim_get_tuning(ctx, p) for p in (TUNE_FUSED_NI, TUNE_PLAIN_RF_NI,
                                                    TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES,
-                                                   TUNE_PRECOMP_STEPS, TUNE_CELL_NI)}
+                                                   TUNE_PRECOMP_STEPS, TUNE_CELL_NI,
+                                                   TUNE_CELL_ROWS)}
 
 
 def mrsim_surrogate_train(ctx, seq, lo, hi, n_train=1 << 22, epochs=20, batch=16384, lr=3e-3,

@@ -4,9 +4,10 @@ In the cell form every thread holds isochromats of one (with-ADC group,
 with-RF group) cell and applies one combined row C = T Adv per cell to each
 with-RF subsequence (Sec. 2.3 update step; Eqs. 4-5 and 7), and sums the
 free-axis-rotated transverse magnetization for each with-ADC window (Eq. 9).
-Every case runs at 4 and 8 isochromats per thread and with the form off, at
-the FP32 bar (signal rel-L2 1e-4, M_final max error 1e-4 of max M0), and
-checks from the per-kernel profile which form actually ran.
+Every case runs at 4 and 8 isochromats per thread, with the combined rows read
+from a table and formed by each thread, and with the form off, at the FP32 bar
+(signal rel-L2 1e-4, M_final max error 1e-4 of max M0), and checks from the
+per-kernel profile which form actually ran.
 """
 
 import numpy as np
@@ -29,10 +30,12 @@ def ctx(mrsim):
     c.close()
 
 
-def run_cell(mrsim, ctx, ph, seq, cell_ni):
-    """Grouped FP32 run with the cell form set to cell_ni; returns the
-    signal, M_final and the names of the fused kernels that ran."""
+def run_cell(mrsim, ctx, ph, seq, cell_ni, rows=0):
+    """Grouped FP32 run with the cell form set to cell_ni and the combined
+    rows to `rows` (0 automatic, 1 table, 2 per thread); returns the signal,
+    M_final and the names of the fused kernels that ran."""
     mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, cell_ni)
+    mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_ROWS, rows)
     hp = ctx.phantom(ph)
     hs = ctx.sequence(seq)
     hg = ctx.group(hp, hs)
@@ -44,6 +47,7 @@ def run_cell(mrsim, ctx, ph, seq, cell_ni):
     finally:
         mrsim.mrsim_profile_enable(ctx.h, False)
         mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, 8)
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_ROWS, 0)
         ctx.free("grp", hg)
         ctx.free("seq", hs)
         ctx.free("ph", hp)
@@ -134,14 +138,14 @@ def test_cell_form_against_oracle(mrsim, ctx, name):
     ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
     M0max = float(np.max(ph.M0))
     sigs = {}
-    for ni in (4, 8, 0):
-        sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni)
+    for ni, rows in ((4, 1), (8, 1), (4, 2), (8, 2), (0, 0)):
+        sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni, rows)
         check(sig, M, ref, Mref, M0max)
         assert ran == ({"fused_cell_f32"} if ni else {"fused_grouped_f32"}), ran
-        sigs[ni] = sig
-    # both forms compute the same sums up to FP32 rounding order
-    assert oracle.rel_l2(sigs[4], sigs[0]) <= 1e-5
-    assert oracle.rel_l2(sigs[8], sigs[0]) <= 1e-5
+        sigs[ni, rows] = sig
+    # every form computes the same sums up to FP32 rounding order
+    for key in ((4, 1), (8, 1), (4, 2), (8, 2)):
+        assert oracle.rel_l2(sigs[key], sigs[0, 0]) <= 1e-5, key
 
 
 @pytest.mark.parametrize("K", [1, 5, 130, 1025, 1700, 2323])
@@ -157,8 +161,8 @@ def test_cell_form_ragged_phantoms(mrsim, ctx, K):
     ph = full.subset(np.sort(rng.choice(inside, size=K, replace=False)))
     seq = spin_echo_2d(n_ro=16, n_pe=16, n_tr=3)
     ref, Mref = oracle.simulate(ph, seq)
-    for ni in (4, 8):
-        sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni)
+    for ni, rows in ((4, 1), (8, 1), (8, 2)):
+        sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni, rows)
         if K >= 1000:
             assert ran == {"fused_cell_f32"}
         check(sig, M, ref, Mref, float(np.max(ph.M0)))
@@ -180,8 +184,8 @@ def test_cell_form_initial_state_b1_and_fallback_spans(mrsim, ctx):
     try:
         for seq in (spin_echo_2d(n_ro=16, n_pe=16, n_tr=2), fallback_span_sequence()):
             ref, Mref = oracle.simulate(ph, seq)
-            for ni in (4, 8):
-                sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni)
+            for ni, rows in ((4, 1), (8, 1), (4, 2), (8, 2)):
+                sig, M, ran = run_cell(mrsim, ctx, ph, seq, ni, rows)
                 assert "fused_cell_f32" in ran
                 check(sig, M, ref, Mref, float(np.max(ph.M0)))
     finally:
@@ -195,3 +199,36 @@ def test_cell_tuning_values(mrsim, ctx):
     for v in (0, 4, 8):
         mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_NI, v)
         assert mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_CELL_NI) == v
+    for bad in (3, -1):
+        with pytest.raises(mrsim.MrsimError):
+            mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_ROWS, bad)
+    for v in (1, 2, 0):
+        mrsim.mrsim_set_tuning(ctx.h, mrsim.TUNE_CELL_ROWS, v)
+        assert mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_CELL_ROWS) == v
+
+
+def test_clustered_phantom_runs_the_cell_form(mrsim, ctx):
+    """A clustered parameter-mapping phantom has many small cells (position
+    pairs times clusters): the automatic choice forms the rows per thread
+    instead of building a table several times the size of the state."""
+    from oracle import cluster as oc
+    base = mapped_phantom(32, 32, 8, 6, seed=21)
+    ph = oc.cluster_phantom(base, 24).phantom
+    seq = fse_2d(n_ro=32, n_pe=16, etl=4, rf_dur=2e-3, rf_dt=10e-6, dwell=10e-6, esp=10e-3,
+                 tr=0.5, n_shots=2)
+    ref, Mref = oracle.simulate(ph, seq, memo=True, adc_recurrence=True)
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    try:
+        mrsim.mrsim_profile_reset(ctx.h)
+        mrsim.mrsim_profile_enable(ctx.h, True)
+        sig, M = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32, K=ph.K, want_M=True)
+        prof = {k for k, v in mrsim.mrsim_profile_get(ctx.h).items() if v[0] > 0}
+    finally:
+        mrsim.mrsim_profile_enable(ctx.h, False)
+        ctx.free("grp", hg)
+        ctx.free("seq", hs)
+        ctx.free("ph", hp)
+    assert "fused_cell_f32" in prof and "cell_rows" not in prof, prof
+    check(sig, M, ref, Mref, float(np.max(ph.M0)))

@@ -352,7 +352,7 @@ def test_precompute_fp32_block_lengths(mrsim, ctx, steps):
 def test_tuning_parameters_are_validated(mrsim, ctx):
     for param, bad in ((mrsim.TUNE_FUSED_NI, 3), (mrsim.TUNE_PRECOMP_LANES, 64),
                        (mrsim.TUNE_PRECOMP_STEPS, 64), (mrsim.TUNE_CELL_NI, 1),
-                       (mrsim.TUNE_TWO_AXIS, 2), (7, 1), (-1, 1)):
+                       (mrsim.TUNE_TWO_AXIS, 2), (mrsim.TUNE_CELL_ROWS, 3), (8, 1), (-1, 1)):
         with pytest.raises(mrsim.MrsimError):
             mrsim.mrsim_set_tuning(ctx.h, param, bad)
     before = mrsim.mrsim_get_tuning(ctx.h, mrsim.TUNE_PRECOMP_STEPS)
