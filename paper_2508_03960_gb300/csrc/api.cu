@@ -1030,7 +1030,8 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         auto bc = std::make_unique<BatchCache>();
         bc->key = key;
         std::vector<GPlan<R>> plans(n);
-        for (int i = 0; i < n; ++i) plan_grouped<R>(c, s[i], g[i], plans[i]);
+        // the cell form for jobs without coils whose plan takes it
+        for (int i = 0; i < n; ++i) plan_grouped<R>(c, s[i], g[i], plans[i], ph[i]->n_coils == 0);
         // Instances: one per (job, receive coil); the coils of a job share its
         // tables and windows, each has its own block sums, signal and state.
         // An instance keeps its state in device memory when its sequence has
@@ -1076,6 +1077,50 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         double *sig = (double *)alloc(std::max<int64_t>(nsig, 1) * 2 * sizeof(double));
         R *Mst = (R *)alloc(nst * sizeof(R));
         float *cmap = (float *)alloc(ncoil * sizeof(float));
+        // cell-form jobs: axis phasor tables, combined rows (unless formed per
+        // thread), their keys and the event records, each job at its offset
+        int64_t nq = 0, ncev = 0, ncrow = 0, nkey = 0;
+        std::vector<int64_t> o_q(n), o_cev(n), o_crow(n), o_key(n);
+        std::vector<AxItem> items;
+        int ax_max = 0;
+        for (int i = 0; i < n; ++i) {
+            const GPlan<R> &P = plans[i];
+            o_q[i] = nq;
+            o_cev[i] = ncev;
+            o_crow[i] = ncrow;
+            o_key[i] = nkey;
+            if (!P.cell) continue;
+            for (AxItem it : P.ax_items) {
+                it.off += nq;
+                items.push_back(it);
+            }
+            ax_max = std::max(ax_max, P.ax_max);
+            nq += P.ax_n;
+            ncev += (int64_t)P.cev.size();
+            if (!P.otf) {
+                ncrow += (int64_t)P.ckeys.size() * g[i]->n_cells * 12;
+                nkey += (int64_t)P.ckeys.size();
+            }
+        }
+        float2 *qtab = (float2 *)alloc(nq * sizeof(float2));
+        CellEv *cev = (CellEv *)alloc(ncev * sizeof(CellEv));
+        float *crow = (float *)alloc(ncrow * sizeof(float));
+        CellKey *ckey = (CellKey *)alloc(nkey * sizeof(CellKey));
+        AxItem *d_items = (AxItem *)alloc(std::max<size_t>(items.size(), 1) * sizeof(AxItem));
+        upload(c, d_items, items.data(), items.size() * sizeof(AxItem));
+        for (int i = 0; i < n; ++i) {
+            const GPlan<R> &P = plans[i];
+            if (!P.cell) continue;
+            upload(c, cev + o_cev[i], P.cev.data(), P.cev.size() * sizeof(CellEv));
+            if (!P.otf)
+                upload(c, ckey + o_key[i], P.ckeys.data(), P.ckeys.size() * sizeof(CellKey));
+        }
+        // bit position of each axis' index in the packed axis index (the
+        // primary axis has none)
+        auto ax_sh = [&](int i, int (&sh)[3]) {
+            int m = 0;
+            for (int a = 0; a < 3; ++a) sh[a] = a == plans[i].p - 1 ? 0 : 16 * m++;
+        };
         // receive-coil maps in each job's layout order (fixed while the
         // phantom's coils are: the cache key holds their version)
         for (int q = 0; q < ni_; ++q) {
@@ -1123,6 +1168,10 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
         struct Fb { int q, sub; };
         std::vector<std::array<std::vector<FusedArgs<R>>, 4>> fj(n_span);
         std::vector<std::array<std::vector<int64_t>, 4>> fj_off(n_span);
+        // cell form: one launch per (span number, free axes, rows per thread)
+        std::vector<std::array<std::vector<CellArgs>, 4>> cj(n_span);
+        std::vector<std::array<std::vector<int64_t>, 4>> cj_off(n_span);
+        int cell_ni = 8;
         std::vector<std::vector<Fb>> fb(n_span);
         auto state = [&](int q, R *&x, R *&y, R *&z) {
             const int64_t Kp = plane_stride(g[inst[q].job]->K);
@@ -1150,11 +1199,56 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
                     fa.coil_re = cmap + o_coil[q];
                     fa.coil_im = fa.coil_re + K;
                 }
+                if (sp.fallback >= 0) fb[k].push_back(Fb{q, sp.fallback});
+                if (P.cell) {
+                    CellArgs ca{};
+                    const int w = P.cell_w;
+                    cell_ni = P.form.ni;
+                    ca.n_thr = g[i]->n_cell_thr[w];
+                    ca.thr = g[i]->cell_thr[w].as<int2>();
+                    ca.cell_gp = g[i]->cell_gp.as<int32_t>();
+                    ca.cell_count = g[i]->cell_count.as<int32_t>();
+                    ca.M0 = fa.M0;
+                    ca.aidx = g[i]->ax_idx.as<int32_t>();
+                    ca.Mx = x;
+                    ca.My = y;
+                    ca.Mz = z;
+                    ca.init_eq = fa.init_eq;
+                    ca.ev = cev + o_cev[i] + sp.b;
+                    ca.n_ev = (int)(sp.e - sp.b);
+                    ca.C_tab = P.otf ? nullptr : crow + o_crow[i];
+                    ca.P_raw = (R *)Pt + o_p[i] * 4;
+                    ca.Ablk = Ab + 2 * o_ablk[q];
+                    ca.qtab = qtab + o_q[i];
+                    int sh[3];
+                    ax_sh(i, sh);
+                    int nf = 0;
+                    for (int a = 0; a < 3; ++a)
+                        if (P.free_bits & (1 << a)) ca.f_sh[nf++] = sh[a];
+                    if (nf < 2) ca.f_sh[1] = 0;
+                    ca.r_sh = P.r_axis >= 0 ? sh[P.r_axis] : 0;
+                    for (int t = 0; t < kNTypes; ++t) ca.gid[t] = fa.gid[t];
+                    ca.K = K;
+                    ca.ablk_stride = std::max<int64_t>(P.ablk_n, 1);
+                    ca.rfq = P.form.rfq ? 1 : 0;
+                    ca.adq = P.form.adq ? 1 : 0;
+                    ca.rb = P.form.rb ? 1 : 0;
+                    ca.otf = P.otf ? 1 : 0;
+                    ca.T_tab = T + o_rows[i] * 12;
+                    ca.cell_gr = g[i]->cell_gr.as<int32_t>();
+                    ca.gtype_p = P.p;
+                    ca.gtype_r = g[i]->secondary;
+                    const int grp = (P.form.nf == 2 ? 1 : 0) | (P.otf ? 2 : 0);
+                    auto &co = cj_off[k][grp];
+                    if (co.empty()) co.push_back(0);
+                    cj[k][grp].push_back(ca);
+                    co.push_back(co.back() + (ca.n_thr + 255) / 256);
+                    continue;
+                }
                 auto &off = fj_off[k][form];
                 if (off.empty()) off.push_back(0);
                 fj[k][form].push_back(fa);
                 off.push_back(off.back() + (K + kFusedChunk(c) - 1) / kFusedChunk(c));
-                if (sp.fallback >= 0) fb[k].push_back(Fb{q, sp.fallback});
             }
             const double *ab = Ab + 2 * o_ablk[q];
             double *sq = sig + 2 * (o_sig[i] + s[i]->n_samples * inst[q].coil);
@@ -1190,6 +1284,18 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
                                    (int)fj[k][f].size(), f});
                 ++n_fl;
             }
+        struct CL { const CellArgs *jobs; const int64_t *off; int n, nf; bool otf; };
+        std::vector<std::vector<CL>> cl(n_span);
+        for (size_t k = 0; k < n_span; ++k)
+            for (int f = 0; f < 4; ++f) {
+                if (cj[k][f].empty()) continue;
+                cl[k].push_back(CL{(const CellArgs *)up(cj[k][f].data(),
+                                                        cj[k][f].size() * sizeof(CellArgs)),
+                                   (const int64_t *)up(cj_off[k][f].data(),
+                                                       cj_off[k][f].size() * sizeof(int64_t)),
+                                   (int)cj[k][f].size(), (f & 1) ? 2 : 1, (f & 2) != 0});
+                ++n_fl;
+            }
         auto *d_gj = (GSigJob<R> *)up(gj.data(), gj.size() * sizeof(GSigJob<R>));
         auto *d_gblk = (int4 *)up(gblk.data(), std::max<size_t>(gblk.size(), 1) * sizeof(int4));
         auto *d_gbj = (int *)up(gblk_job.data(), std::max<size_t>(gblk_job.size(), 1) * sizeof(int));
@@ -1213,6 +1319,18 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
             launch_precompute_batch<R>(c, d_pre, d_pre_off, (int)pre.size(), pre_off.back());
             if (!et.empty())
                 launch_event_table_batch<R>(c, d_et, d_et_off, (int)et.size(), et_off.back());
+            // cell-form jobs: every job's axis phasors in one launch, then the
+            // combined rows of the jobs that read them from a table
+            if (!items.empty()) launch_axis_phase(c, d_items, (int)items.size(), ax_max, qtab);
+            for (int i = 0; i < n; ++i) {
+                const GPlan<R> &P = plans[i];
+                if (!P.cell || P.otf || P.ckeys.empty()) continue;
+                int sh[3];
+                ax_sh(i, sh);
+                launch_cell_rows(c, ckey + o_key[i], (int)P.ckeys.size(), g[i], T + o_rows[i] * 12,
+                                 (R *)Pt + o_p[i] * 4, qtab + o_q[i],
+                                 P.r_axis >= 0 ? sh[P.r_axis] : 0, crow + o_crow[i]);
+            }
             for (int q = 0; q < ni_; ++q) {
                 const int i = inst[q].job;
                 if (!inst[q].state || !g[i]->has_M_init) continue;
@@ -1226,6 +1344,9 @@ void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsi
                     launch_fused_batch<R>(c, f.jobs, f.off, f.n, d_cnt + li++,
                                           c->tune[MRSIM_TUNE_FUSED_NI], (f.form & 1) != 0,
                                           (f.form & 2) != 0);
+                for (const CL &f : cl[k])
+                    launch_fused_cell_batch(c, f.jobs, f.off, f.n, d_cnt + li++, cell_ni, f.nf,
+                                            f.otf);
                 for (const Fb &b : fb[k]) {
                     const int i = inst[b.q].job;
                     const Subseq &qq = s[i]->sub[b.sub];

@@ -433,6 +433,10 @@ struct CellKey {
     double kp, kr, tau;
 };
 void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f);
+// Batched cell form: CTAs take (job, block) work items from a device counter;
+// every job's CellArgs carries its phasor flags (rfq, adq, rb); one coil.
+void launch_fused_cell_batch(mrsim_ctx *c, const CellArgs *d_jobs, const int64_t *d_blk_off,
+                             int n_jobs, unsigned long long *d_counter, int ni, int nf, bool otf);
 void launch_cell_rows(mrsim_ctx *c, const CellKey *d_keys, int n_keys, const mrsim_groups *g,
                       const float *T_tab, const void *P_tab, const float2 *qtab, int r_sh,
                       float *C);

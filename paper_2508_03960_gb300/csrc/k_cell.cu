@@ -76,14 +76,13 @@ __device__ __forceinline__ void free_phasor(const float2 *qtab, const int (&qf)[
 // RFQ / ADQ / RB: 0 or 1 fixes the phasor flag at compile time, 2 reads it from
 // the arguments.  PC: receive coils handled in this pass (0: S = 1).
 // OTF: the combined rows are formed by each thread (no row table).
+// One CTA's 256 threads of a launch (block blk of the thread list).
 template <int NI, int NF, int RFQ, int ADQ, int RB, int PC, bool OTF>
-__global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4 ? 4 : 2))
-    k_fused_cell(CellArgs a) {
+__device__ __forceinline__ void cell_block(const CellArgs &a, int64_t blk, CellSmem<PC> &sm) {
     using Smem = CellSmem<PC>;
     constexpr int NC = Smem::NC, NB = Smem::NB;
-    __shared__ Smem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t t0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t t0 = blk * kThreads;
     const int64_t t = t0 + tid;
     const int64_t t_end = min(t0 + kThreads, a.n_thr);  // threads with work in this CTA
     const float2 *qtab = a.qtab;
@@ -436,6 +435,44 @@ __global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4
     if (nb > 0) flush();
 }
 
+template <int NI, int NF, int RFQ, int ADQ, int RB, int PC, bool OTF>
+__global__ void __launch_bounds__(kThreads, (PC >= 2 ? 2 : PC == 1 ? 3 : NI == 4 ? 4 : 2))
+    k_fused_cell(CellArgs a) {
+    __shared__ CellSmem<PC> sm;
+    cell_block<NI, NF, RFQ, ADQ, RB, PC, OTF>(a, blockIdx.x, sm);
+}
+
+// Persistent form for a batch of jobs (one coil, phasor flags read at run
+// time): every CTA takes the next (job, block) work item from a device counter
+// until all blocks of all jobs are done.
+template <int NI, int NF, bool OTF>
+__global__ void __launch_bounds__(kThreads, (NI == 4 ? 3 : 2))
+    k_fused_cell_batch(const CellArgs *jobs, const int64_t *blk_off, int n_jobs,
+                       unsigned long long *counter) {
+    __shared__ CellSmem<0> sm;
+    __shared__ CellArgs ja;
+    __shared__ long long item, jblk;
+    const int64_t total = blk_off[n_jobs];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            item = (long long)atomicAdd(counter, 1ull);
+            if (item < total) {
+                int lo = 0, hi = n_jobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (blk_off[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                ja = jobs[lo];
+                jblk = item - blk_off[lo];
+            }
+        }
+        __syncthreads();
+        if (item >= total) break;
+        cell_block<NI, NF, 2, 2, 2, 0, OTF>(ja, jblk, sm);
+        __syncthreads();  // the item's shared state is free before the next one
+    }
+}
+
 template <int NI, int NF, bool RFQ, bool ADQ, bool RB>
 void launch_cell_v(mrsim_ctx *c, const CellArgs &a) {
     const unsigned nb = (unsigned)((a.n_thr + kThreads - 1) / kThreads);
@@ -554,6 +591,33 @@ void launch_fused_cell(mrsim_ctx *c, const CellArgs &a, const CellForm &f) {
     } else {
         if (f.nf == 2) launch_cell_q<4, 2>(c, a, f);
         else launch_cell_q<4, 1>(c, a, f);
+    }
+}
+
+template <int NI, int NF, bool OTF>
+void launch_cell_batch_v(mrsim_ctx *c, const CellArgs *d_jobs, const int64_t *d_blk_off,
+                         int n_jobs, unsigned long long *d_counter) {
+    int per_sm = 1;
+    MRSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_fused_cell_batch<NI, NF, OTF>, kThreads, 0));
+    k_fused_cell_batch<NI, NF, OTF><<<std::max(1, per_sm) * c->sm_count, kThreads, 0,
+                                      c->stream>>>(d_jobs, d_blk_off, n_jobs, d_counter);
+}
+
+void launch_fused_cell_batch(mrsim_ctx *c, const CellArgs *d_jobs, const int64_t *d_blk_off,
+                             int n_jobs, unsigned long long *d_counter, int ni, int nf,
+                             bool otf) {
+    KScope ks(c, "fused_cell_batch");
+    if (ni == 8) {
+        if (nf == 2) otf ? launch_cell_batch_v<8, 2, true>(c, d_jobs, d_blk_off, n_jobs, d_counter)
+                         : launch_cell_batch_v<8, 2, false>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+        else otf ? launch_cell_batch_v<8, 1, true>(c, d_jobs, d_blk_off, n_jobs, d_counter)
+                 : launch_cell_batch_v<8, 1, false>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+    } else {
+        if (nf == 2) otf ? launch_cell_batch_v<4, 2, true>(c, d_jobs, d_blk_off, n_jobs, d_counter)
+                         : launch_cell_batch_v<4, 2, false>(c, d_jobs, d_blk_off, n_jobs, d_counter);
+        else otf ? launch_cell_batch_v<4, 1, true>(c, d_jobs, d_blk_off, n_jobs, d_counter)
+                 : launch_cell_batch_v<4, 1, false>(c, d_jobs, d_blk_off, n_jobs, d_counter);
     }
 }
 
