@@ -226,9 +226,11 @@ int mrsim_run(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
  * mrsim_run.  The graph is kept and relaunched while the same jobs (and
  * coils, and tuning) are run again.  groups[i] must come from
  * mrsim_group(ph[i], seq[i]).  signals[i]: host [P][2 * n_samples_total]
- * doubles as in mrsim_run (P = ph[i]'s coil count, 1 without coils).  The
- * per-isochromat form of the fused kernel runs (MRSIM_TUNE_FUSED_NI); sums
- * use FP64 atomics whatever mrsim_set_reproducible says.
+ * doubles as in mrsim_run (P = ph[i]'s coil count, 1 without coils).  Jobs
+ * without coils run the cell form of the fused kernel when their plan takes
+ * it (MRSIM_TUNE_CELL_NI, MRSIM_TUNE_CELL_ROWS), the others the per-isochromat
+ * form (MRSIM_TUNE_FUSED_NI); sums use FP64 atomics whatever
+ * mrsim_set_reproducible says.
  * Errors: MRSIM_EINVAL (n_jobs <= 0, NULL arrays or entries), MRSIM_ESTATE
  * (groups of another phantom or without a needed type), MRSIM_ENOMEM,
  * MRSIM_ECUDA. */
