@@ -376,12 +376,26 @@ __device__ __forceinline__ void cell_block(const CellArgs &a, int64_t blk, CellS
 #pragma unroll
                 for (int j = 0; j < NC; ++j) sr[j] = si[j] = 0.0f;
                 const int qf[2] = {ev1.x, ev1.y};
-                // (roundings written out: every instantiation, with coils or
-                // without, forms the same products and sums, so a unit coil
-                // gives the bits of none)
+                // (roundings written out: every 4-wide instantiation, with
+                // coils or without, forms the same products and sums, so a unit
+                // coil gives the bits of none; reproducible sums and the coil
+                // kernels are 4-wide.  The 8-wide form folds the rotation into
+                // the sum, two FMAs per component)
 #pragma unroll
                 for (int i = 0; i < NI; ++i) {
                     float vr = mx[i], vi = my[i];
+                    if constexpr (NI == 8 && PC == 0) {
+                        if (adq) {
+                            float c, s;
+                            free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
+                            sr[0] = fmaf(c, mx[i], fmaf(s, my[i], sr[0]));
+                            si[0] = fmaf(c, my[i], fmaf(-s, mx[i], si[0]));
+                        } else {
+                            sr[0] += vr;
+                            si[0] += vi;
+                        }
+                        continue;
+                    }
                     if (adq) {
                         float c, s;
                         free_phasor<NF>(qtab, qf, f0[i], f1[i], c, s);
