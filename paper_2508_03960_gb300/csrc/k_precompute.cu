@@ -123,10 +123,12 @@ __device__ __forceinline__ void compose_run(const PrecompArgs &a, int64_t g, int
         const R r02 = s * py + c2 * px * pz, r20 = -s * py + c2 * px * pz;
         const R r12 = -s * px + c2 * py * pz, r21 = s * px + c2 * py * pz;
         const R f2 = (R)1 + em2, f1 = (R)1 + em1;
-        const double D[9] = {(double)(r00 * f2 + em2), (double)(r01 * f2), (double)(r02 * f2),
-                             (double)(r10 * f2), (double)(r11 * f2 + em2), (double)(r12 * f2),
-                             (double)(r20 * f1), (double)(r21 * f1), (double)(r22 * f1 + em1)};
-        const double bz = -(double)em1;
+        // D = U - I in the run precision (an FP32 table never converts it to
+        // FP64: conversions run on the FP64 pipe, a small fraction of the FP32
+        // rate on this GPU, and a step's D is formed once per segment)
+        const R D[9] = {r00 * f2 + em2, r01 * f2, r02 * f2, r10 * f2, r11 * f2 + em2,
+                        r12 * f2, r20 * f1, r21 * f1, r22 * f1 + em1};
+        const R bz = -em1;
         if constexpr (sizeof(R) == 8) {
             for (int64_t q = 0; q < n_here; ++q) {
 #pragma unroll
@@ -139,10 +141,8 @@ __device__ __forceinline__ void compose_run(const PrecompArgs &a, int64_t g, int
                 T[11] += bz;
             }
         } else {
-            float Df[9];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) Df[e] = (float)D[e];
-            const float bzf = (float)bz;
+            const float(&Df)[9] = D;
+            const float bzf = bz;
             for (int64_t q = 0; q < n_here; ++q) {
                 float En[9], cn[3];
 #pragma unroll
