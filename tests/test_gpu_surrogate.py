@@ -92,7 +92,7 @@ def trained(mrsim, ctx):
     hs = ctx.sequence(seq)
     t0 = time.time()
     sur = mrsim.mrsim_surrogate_train(ctx.h, hs, DOMAIN_LO, DOMAIN_HI, n_train=1 << 22,
-                                      epochs=150, batch=8192, lr=1e-2, seed=1005, bound=1e-3)
+                                      epochs=300, batch=8192, lr=1e-2, seed=1005, bound=1e-3)
     dt = time.time() - t0
     yield seq, hs, sur, dt
     mrsim.mrsim_free_surrogate(sur)
