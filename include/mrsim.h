@@ -381,9 +381,10 @@ void mrsim_free_surrogate(mrsim_surrogate *sur);
  *   MRSIM_TUNE_ADC_CTAS_PER_SM CTAs per SM of the persistent plain with-ADC
  *                              kernel: 1, 2, 4 or 8 (default 2)
  *   MRSIM_TUNE_PRECOMP_LANES   threads composing one group's combined
- *                              transition: 4, 8, 16, 32 (one warp or less,
- *                              shuffle tree) or 128 (a CTA, shared-memory
- *                              tree); 0 (default) picks by pulse length
+ *                              transition: 1, 2, 4, 8, 16, 32 (one warp or
+ *                              less, shuffle tree) or 128 (a CTA, shared-memory
+ *                              tree); 0 (default) takes the fewest lanes that
+ *                              fill the GPU, a CTA for few, long tables
  *   MRSIM_TUNE_PRECOMP_STEPS   FP32 runs: sub-steps composed in FP32 registers
  *                              (difference form) before each fold into the
  *                              FP64 combined transition: 1, 2, 4, 8

@@ -1874,10 +1874,14 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
 
 int mrsim_set_tuning(mrsim_ctx *c, int param, int value) {
     if (!c) return MRSIM_EINVAL;
-    static const int allowed[8][6] = {{1, 2, 4, -1, -1, -1}, {1, 2, -1, -1, -1, -1},
-                                      {1, 2, 4, 8, -1, -1}, {0, 4, 8, 16, 32, 128},
-                                      {1, 2, 4, 8, 16, 32}, {0, 4, 8, -1, -1, -1},
-                                      {0, 1, -1, -1, -1, -1}, {0, 1, 2, -1, -1, -1}};
+    static const int allowed[8][8] = {{1, 2, 4, -1, -1, -1, -1, -1},
+                                      {1, 2, -1, -1, -1, -1, -1, -1},
+                                      {1, 2, 4, 8, -1, -1, -1, -1},
+                                      {0, 1, 2, 4, 8, 16, 32, 128},
+                                      {1, 2, 4, 8, 16, 32, -1, -1},
+                                      {0, 4, 8, -1, -1, -1, -1, -1},
+                                      {0, 1, -1, -1, -1, -1, -1, -1},
+                                      {0, 1, 2, -1, -1, -1, -1, -1}};
     if (param < 0 || param > 7) return set_err(c, MRSIM_EINVAL, "unknown tuning parameter");
     bool ok = false;
     for (int v : allowed[param]) ok |= v >= 0 && v == value;
@@ -1910,7 +1914,7 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
         if (grouped && precision == MRSIM_FP32) plan.push_back({MRSIM_TUNE_CELL_ROWS, {0, 2}});
         if (grouped) plan.push_back({MRSIM_TUNE_FUSED_NI, {1, 2, 4}});
         if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_STEPS, {1, 2, 4, 8, 16, 32}});
-        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 4, 8, 16, 32, 128}});
+        if (grouped) plan.push_back({MRSIM_TUNE_PRECOMP_LANES, {0, 1, 2, 4, 8, 16, 32, 128}});
         plan.push_back({MRSIM_TUNE_PLAIN_RF_NI, {1, 2}});
         plan.push_back({MRSIM_TUNE_ADC_CTAS_PER_SM, {1, 2, 4, 8}});
         for (auto &pv : plan) {

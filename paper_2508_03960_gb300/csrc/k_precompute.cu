@@ -281,14 +281,16 @@ void launch_precompute(mrsim_ctx *c, const PrecompArgs &a_in) {
     PrecompArgs a = a_in;
     a.kb = c->tune[MRSIM_TUNE_PRECOMP_STEPS];
     KScope ks(c, sizeof(R) == 4 ? "precompute_f32" : "precompute_f64");
-    // lanes per group: the tuned value, or by default the fewest lanes (each
-    // tree level costs about one fold of FP64 work) that keep runs to about
-    // 64 sub-steps and fill the GPU; a whole CTA only for few, long tables
+    // lanes per group: the tuned value, or by default the fewest lanes that
+    // fill the GPU (every lane ends its run with a partial FP64 fold and every
+    // tree level costs about one fold, FP64-pipe work: 27.5M groups of a
+    // 200-step pulse take 66 ms with one lane, 90 ms with four); a whole CTA
+    // only for few, long tables
     int L = c->tune[MRSIM_TUNE_PRECOMP_LANES];
     if (L == 0) {
         const int64_t fill = (int64_t)c->sm_count * 512;
-        L = 4;
-        while (L < 32 && (a.n_steps > 64 * L || a.n_groups * L < fill)) L <<= 1;
+        L = 1;
+        while (L < 32 && a.n_groups * L < fill) L <<= 1;
         if (a.n_groups * 32 < fill && a.n_steps > 64 * 32) L = 128;
     }
     if (L >= 128) {
@@ -300,6 +302,8 @@ void launch_precompute(mrsim_ctx *c, const PrecompArgs &a_in) {
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256,
                                                                           (int64_t)c->sm_count * 32));
     switch (L) {
+        case 1: k_precompute_lanes<R, 1><<<grid, 256, 0, c->stream>>>(a); break;
+        case 2: k_precompute_lanes<R, 2><<<grid, 256, 0, c->stream>>>(a); break;
         case 4: k_precompute_lanes<R, 4><<<grid, 256, 0, c->stream>>>(a); break;
         case 8: k_precompute_lanes<R, 8><<<grid, 256, 0, c->stream>>>(a); break;
         case 16: k_precompute_lanes<R, 16><<<grid, 256, 0, c->stream>>>(a); break;

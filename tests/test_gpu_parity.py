@@ -310,7 +310,7 @@ def test_repeated_runs_are_consistent(mrsim, ctx):
     assert oracle.rel_l2(a, ref) <= 1e-4 and oracle.rel_l2(b, a) <= 1e-6
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32, 128])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, 128])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_precompute_lane_counts(mrsim, ctx, lanes, precision):
     """Every lane count of the combined-transition step (shuffle tree inside a
