@@ -26,9 +26,45 @@ void cuda_check(cudaError_t e, const char *what) {
     fail(MRSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// the context whose entry point is running on this thread (its pool serves
+// dalloc); set by the entry points' guard
+thread_local mrsim_ctx *tl_ctx = nullptr;
+
+CtxScope::CtxScope(mrsim_ctx *c) : prev(tl_ctx) { tl_ctx = c; }
+CtxScope::~CtxScope() { tl_ctx = prev; }
+
 DBuf dalloc(size_t bytes) {
     DBuf d;
     if (bytes == 0) return d;
+    const mrsim_ctx *c = tl_ctx;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c && c->pool && cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: keep out of the stream order
+    }
+    if (c && c->pool && cs == cudaStreamCaptureStatusNone) {
+        const size_t want = (bytes + 255) / 256 * 256;
+        cudaError_t e = cudaMallocFromPoolAsync(&d.p, want, c->pool->pool, c->stream);
+        if (e != cudaSuccess) {  // hand the pool's idle reserve back, then once more
+            cudaGetLastError();
+            MRSIM_CUDA(cudaStreamSynchronize(c->stream));
+            cudaMemPoolTrimTo(c->pool->pool, 0);
+            e = cudaMallocFromPoolAsync(&d.p, want, c->pool->pool, c->stream);
+        }
+        if (e == cudaSuccess && ((uintptr_t)d.p & 255) == 0) {
+            d.bytes = bytes;
+            d.pool = c->pool;
+            return d;
+        }
+        cudaGetLastError();
+        if (e == cudaSuccess) {  // 256-byte alignment is what the kernels assume
+            cudaFreeAsync(d.p, c->stream);
+        } else {
+            d.p = nullptr;
+            fail(MRSIM_ENOMEM, "pool allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        d.p = nullptr;
+    }
     cudaError_t e = cudaMalloc(&d.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1405,6 +1441,7 @@ int set_err(mrsim_ctx *c, int code, const std::string &m) {
 
 template <class F>
 int guard(mrsim_ctx *c, F &&f) {
+    CtxScope scope(c);
     try {
         f();
         if (c) c->err.clear();
@@ -1455,6 +1492,17 @@ int mrsim_create(mrsim_ctx **ctx, int device, void *cuda_stream) {
             MRSIM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
             c->own_stream = true;
         }
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        auto pool = std::make_shared<DevPool>();
+        MRSIM_CUDA(cudaMemPoolCreate(&pool->pool, &props));
+        uint64_t keep = UINT64_MAX;  // keep the reserve between calls
+        MRSIM_CUDA(cudaMemPoolSetAttribute(pool->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        pool->stream = c->stream;
+        c->pool = std::move(pool);
         c->dev_err = dalloc(64);
         MRSIM_CUDA(cudaMemsetAsync(c->dev_err.p, 0, 64, c->stream));
         prepare_fused(c);
@@ -1477,6 +1525,12 @@ void mrsim_destroy(mrsim_ctx *c) {
     c->dev_err.reset();
     if (c->pinned) cudaFreeHost(c->pinned);
     batch_caches().erase(c);
+    if (c->pool) {  // buffers that outlive the context are freed synchronously
+        cudaStreamSynchronize(c->stream);
+        c->pool->stream = nullptr;
+        cudaMemPoolTrimTo(c->pool->pool, 0);
+        c->pool.reset();
+    }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -15,23 +15,59 @@
 
 namespace mrsim {
 
-// Owned device allocation.
+// Stream-ordered device memory pool of one context.  Buffers freed while the
+// context lives go back to the pool in stream order (cudaFreeAsync on the
+// context's stream) and are reused by later allocations on that stream
+// without a device synchronisation; the pool keeps what it has reserved until
+// the context is destroyed or an allocation would otherwise fail.  Once the
+// context is gone (stream == nullptr), buffers that outlive it are freed with
+// the synchronous cudaFree, and the pool itself goes with the last of them.
+struct DevPool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;
+    DevPool() = default;
+    DevPool(const DevPool &) = delete;
+    DevPool &operator=(const DevPool &) = delete;
+    ~DevPool() {
+        if (pool) cudaMemPoolDestroy(pool);
+    }
+};
+
+// Owned device allocation (from the pool of the context that made it, or
+// from cudaMalloc where no pool applies).
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    std::shared_ptr<DevPool> pool;
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), pool(std::move(o.pool)) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
     DBuf &operator=(DBuf &&o) noexcept {
-        if (this != &o) { reset(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            reset();
+            p = o.p;
+            bytes = o.bytes;
+            pool = std::move(o.pool);
+            o.p = nullptr;
+            o.bytes = 0;
+        }
         return *this;
     }
     ~DBuf() { reset(); }
     void reset() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (pool && pool->stream)
+                cudaFreeAsync(p, pool->stream);
+            else
+                cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        pool.reset();
     }
     template <typename T>
     T *as() const { return static_cast<T *>(p); }
@@ -55,6 +91,8 @@ struct mrsim_ctx {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // stream-ordered pool of the context's device buffers
+    std::shared_ptr<mrsim::DevPool> pool;
     std::string err;
     int64_t launches = 0;
     // profiling
@@ -195,7 +233,19 @@ void prof_flush(mrsim_ctx *c);
 
 // scratch area `slot` of at least `bytes` bytes (grows, contents undefined)
 void *scratch(mrsim_ctx *c, int slot, size_t bytes);
+// Device allocation from the pool of the context whose entry point runs on
+// this thread (CtxScope), else from cudaMalloc.  Throws MRSIM_ENOMEM.
 DBuf dalloc(size_t bytes);
+
+// Marks the context whose entry point runs on this thread for the scope's
+// lifetime (restores the previous one after).
+struct CtxScope {
+    mrsim_ctx *prev;
+    explicit CtxScope(mrsim_ctx *c);
+    ~CtxScope();
+    CtxScope(const CtxScope &) = delete;
+    CtxScope &operator=(const CtxScope &) = delete;
+};
 void upload(mrsim_ctx *c, void *dst, const void *src, size_t bytes);
 void sync(mrsim_ctx *c);
 

@@ -77,6 +77,7 @@ extern "C" int mrsim_recon_cartesian(mrsim_ctx *c, int n_lines, int n_ro, int n_
                                      const int32_t *col0, const int8_t *dir, unsigned flags,
                                      double *image) {
     if (!c) return MRSIM_EINVAL;
+    CtxScope scope(c);
     try {
         if (!signal || !row || !col0 || !dir || !image) fail(MRSIM_EINVAL, "NULL argument");
         if (n_lines < 1) fail(MRSIM_EINVAL, "n_lines must be positive");

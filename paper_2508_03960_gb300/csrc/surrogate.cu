@@ -100,6 +100,7 @@ namespace {
 
 template <class F>
 int sguard(mrsim_ctx *c, F &&f) {
+    CtxScope scope(c);
     try {
         f();
         if (c) c->err.clear();
