@@ -91,11 +91,18 @@ typedef struct mrsim_seq mrsim_seq;
 typedef struct mrsim_groups mrsim_groups;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
- * run on (not owned), or NULL for a context-owned stream.
+ * run on (not owned), or NULL for a context-owned stream.  The context's
+ * device buffers (phantoms, sequences, groups, scratch) come from its own
+ * stream-ordered memory pool: memory the library frees is returned in stream
+ * order and kept reserved for the context's later calls (freeing never
+ * synchronises the device); the reserve is handed back when an allocation
+ * would otherwise fail and at mrsim_destroy.
  * Errors: MRSIM_EINVAL (ctx NULL or bad device), MRSIM_ECUDA. */
 int mrsim_create(mrsim_ctx **ctx, int device, void *cuda_stream);
 
-/* Release the context and its stream (if owned).  NULL is a no-op. */
+/* Release the context, its memory pool's reserve and its stream (if owned).
+ * Handles made by the context may still be freed afterwards (synchronously).
+ * NULL is a no-op. */
 void mrsim_destroy(mrsim_ctx *ctx);
 
 /* Message of the last failure on this context ("" if none).  The string is
