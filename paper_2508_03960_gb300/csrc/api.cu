@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -235,51 +236,64 @@ static_assert(G_XY == MRSIM_G_XY && G_XZ == MRSIM_G_XZ && G_YZ == MRSIM_G_YZ,
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
 // (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
 // of G_GENERAL), sample offsets and with-RF content ids.  Needs no device.
+// first index in [j, n) whose class byte differs from v (n if none)
+int64_t class_run_end(const uint8_t *cl, int64_t j, int64_t n, uint8_t v) {
+    const uint64_t pat = 0x0101010101010101ull * v;
+    for (; j + 8 <= n; j += 8) {
+        uint64_t w;
+        std::memcpy(&w, cl + j, 8);
+        if (w != pat) break;
+    }
+    while (j < n && cl[j] == v) ++j;
+    return j;
+}
+
 void classify_sequence(mrsim_seq *s, bool two_axis) {
     const int64_t n = s->n_seg;
-    // split into maximal runs of one class (Fig. 1)
-    auto cls = [&](int64_t j) {
-        bool rf = s->b1re[j] != 0.0f || s->b1im[j] != 0.0f;
-        if (rf && s->adc[j]) fail(MRSIM_EUNSUPPORTED, "RF and ADC active in segment " + std::to_string(j));
-        return rf ? SUB_RF : (s->adc[j] ? SUB_ADC : SUB_RELAX);
-    };
+    // the class of every segment, and whether any segment is invalid or has
+    // RF and ADC at once (branch-free passes over one or two arrays each, so
+    // that they vectorise)
+    auto finite = [](float v) { return std::fabs(v) <= FLT_MAX; };
+    const double *dt = s->dt.data();
+    const int32_t *rep = s->rep.data();
+    const float *bre = s->b1re.data(), *bim = s->b1im.data();
+    const float *gx = s->gx.data(), *gy = s->gy.data(), *gz = s->gz.data();
+    const uint8_t *adc = s->adc.data();
+    std::vector<uint8_t> cl(n);
+    int bad = 0;
+    for (int64_t j = 0; j < n; ++j) bad |= !(dt[j] > 0.0) | !(dt[j] <= DBL_MAX) | (rep[j] < 1);
+    for (int64_t j = 0; j < n; ++j) bad |= !finite(gx[j]) | !finite(gy[j]) | !finite(gz[j]);
+    static_assert(SUB_RF == 0 && SUB_ADC == 1 && SUB_RELAX == 2, "class codes");
     for (int64_t j = 0; j < n; ++j) {
-        if (!(std::isfinite(s->dt[j]) && s->dt[j] > 0.0) || s->rep[j] < 1 ||
-            !std::isfinite(s->b1re[j]) || !std::isfinite(s->b1im[j]) ||
-            !std::isfinite(s->gx[j]) || !std::isfinite(s->gy[j]) || !std::isfinite(s->gz[j]))
-            fail(MRSIM_EINVAL, "invalid segment " + std::to_string(j));
-        int t = cls(j);
-        if (j == 0 || t != s->sub.back().type) {
-            Subseq q;
-            q.type = t;
-            q.seg_begin = j;
-            s->sub.push_back(q);
+        const int rf = (bre[j] != 0.0f) | (bim[j] != 0.0f);
+        const int a = adc[j] != 0;
+        bad |= !finite(bre[j]) | !finite(bim[j]) | (rf & a);
+        cl[j] = (uint8_t)(rf ? SUB_RF : SUB_RELAX - a);
+    }
+    if (bad) {  // name the first offending segment, invalid before RF with ADC
+        for (int64_t j = 0; j < n; ++j) {
+            if (!(std::isfinite(s->dt[j]) && s->dt[j] > 0.0) || s->rep[j] < 1 ||
+                !std::isfinite(s->b1re[j]) || !std::isfinite(s->b1im[j]) ||
+                !std::isfinite(s->gx[j]) || !std::isfinite(s->gy[j]) || !std::isfinite(s->gz[j]))
+                fail(MRSIM_EINVAL, "invalid segment " + std::to_string(j));
+            if ((s->b1re[j] != 0.0f || s->b1im[j] != 0.0f) && s->adc[j])
+                fail(MRSIM_EUNSUPPORTED, "RF and ADC active in segment " + std::to_string(j));
         }
-        s->sub.back().seg_end = j + 1;
+    }
+    // split into maximal runs of one class (Fig. 1)
+    for (int64_t j = 0; j < n;) {
+        Subseq q;
+        q.type = cl[j];
+        q.seg_begin = j;
+        j = class_run_end(cl.data(), j + 1, n, cl[j]);
+        q.seg_end = j;
+        s->sub.push_back(q);
     }
     int64_t smp = 0;
     std::unordered_map<uint64_t, std::vector<int>> by_hash;
     for (size_t i = 0; i < s->sub.size(); ++i) {
         Subseq &q = s->sub[i];
-        bool ax = false, ay = false, az = false;
-        for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
-            ax |= s->gx[j] != 0.0f;
-            ay |= s->gy[j] != 0.0f;
-            az |= s->gz[j] != 0.0f;
-            const double d = s->dt[j] * s->rep[j];
-            q.dur += d;
-            q.mom[0] += (double)s->gx[j] * d;
-            q.mom[1] += (double)s->gy[j] * d;
-            q.mom[2] += (double)s->gz[j] * d;
-            if (s->adc[j]) q.n_samples += s->rep[j];
-        }
-        const int cnt = (int)ax + (int)ay + (int)az;
-        q.gtype = cnt == 0   ? G_NONE
-                  : cnt == 1 ? (ax ? G_X : ay ? G_Y : G_Z)
-                  : cnt == 2 && two_axis ? (!az ? G_XY : !ay ? G_XZ : G_YZ)
-                             : G_GENERAL;
-        q.sample0 = smp;
-        smp += q.n_samples;
+        int first = (int)i;  // the subsequence whose segments this one repeats bit for bit
         if (q.type == SUB_RF) {
             const uint64_t h = run_key(s, q.seg_begin, q.seg_end);
             const int64_t len = q.seg_end - q.seg_begin;
@@ -299,7 +313,35 @@ void classify_sequence(mrsim_seq *s, bool two_axis) {
             }
             q.content = found;
             s->content_count[found]++;
+            first = (int)s->content_first[found];
         }
+        if (first != (int)i) {  // same segments: same type, duration and moments
+            const Subseq &r = s->sub[first];
+            q.gtype = r.gtype;
+            q.dur = r.dur;
+            for (int a = 0; a < 3; ++a) q.mom[a] = r.mom[a];
+            q.n_samples = r.n_samples;
+        } else {
+            bool ax = false, ay = false, az = false;
+            for (int64_t j = q.seg_begin; j < q.seg_end; ++j) {
+                ax |= s->gx[j] != 0.0f;
+                ay |= s->gy[j] != 0.0f;
+                az |= s->gz[j] != 0.0f;
+                const double d = s->dt[j] * s->rep[j];
+                q.dur += d;
+                q.mom[0] += (double)s->gx[j] * d;
+                q.mom[1] += (double)s->gy[j] * d;
+                q.mom[2] += (double)s->gz[j] * d;
+                if (s->adc[j]) q.n_samples += s->rep[j];
+            }
+            const int cnt = (int)ax + (int)ay + (int)az;
+            q.gtype = cnt == 0   ? G_NONE
+                      : cnt == 1 ? (ax ? G_X : ay ? G_Y : G_Z)
+                      : cnt == 2 && two_axis ? (!az ? G_XY : !ay ? G_XZ : G_YZ)
+                                 : G_GENERAL;
+        }
+        q.sample0 = smp;
+        smp += q.n_samples;
     }
     s->n_samples = smp;
 }

@@ -9,6 +9,7 @@
 // lay the isochromats out sorted by (ADC group, RF group): contiguous runs of
 // one ADC group make the block sums of Eq. 9 a segmented reduction, and runs
 // of one RF group make the combined-transition lookups warp-uniform.
+#include <climits>
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -21,6 +22,7 @@ namespace {
 
 constexpr int kErrNaN = 1;
 constexpr int kErrTableFull = 2;
+constexpr int kErrGrow = 8;  // more distinct keys than the table was sized for
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z ^= z >> 30;
@@ -93,50 +95,145 @@ struct PairKey {
     }
 };
 
+__device__ __forceinline__ uint64_t key_hash(const uint32_t *w, int n) {
+    uint64_t h = 0x9e3779b97f4a7c15ull;
+    for (int i = 0; i < n; ++i) h = mix64(h ^ (uint64_t)w[i] ^ ((uint64_t)i << 40));
+    return h;
+}
+
+// Two-level insert.  A CTA takes a tile of kHashTile consecutive elements,
+// numbers the tile's distinct keys in a shared-memory table, probes the global
+// table once per distinct key (with the key's smallest index in the tile), and
+// hands every element its global slot.  With thousands of groups over millions
+// of isochromats a tile holds few distinct keys, so few global probes are made
+// and no global slot becomes a hot spot.  Global slot: the owner is any member
+// (it only serves key comparisons); minidx ends as the smallest member index.
+constexpr int kHashThreads = 256;
+constexpr int kHashPer = 4;
+constexpr int kHashTile = kHashThreads * kHashPer;
+constexpr int kHashLocal = 2 * kHashTile;  // never more than half full
+
 template <class KF>
-__global__ void k_hash_insert(int64_t K, KF kf, int32_t *owner, int32_t *minidx,
-                              int32_t *slot_of, uint32_t mask, int *err) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t w[KF::W];
-        if (!kf.words(k, w)) {
-            atomicOr(err, kErrNaN);
-            slot_of[k] = 0;
-            continue;
-        }
-        uint64_t h = 0x9e3779b97f4a7c15ull;
+__global__ void __launch_bounds__(kHashThreads)
+    k_hash_insert(int64_t K, KF kf, int32_t *owner, int32_t *minidx, int32_t *slot_of,
+                  uint32_t mask, int key_limit, int *err, int *n_keys) {
+    __shared__ int32_t l_rep[kHashLocal];   // tile index of the entry's first member, -1: free
+    __shared__ int32_t l_min[kHashLocal];   // smallest tile index with the entry's key
+    __shared__ int32_t l_slot[kHashLocal];  // global slot of the entry's key
+    __shared__ int32_t l_used[kHashTile];   // occupied entries
+    __shared__ int l_n;
+    for (int i = threadIdx.x; i < kHashLocal; i += kHashThreads) {
+        l_rep[i] = -1;
+        l_min[i] = INT_MAX;
+    }
+    if (threadIdx.x == 0) l_n = 0;
+    __syncthreads();
+    for (int64_t base = blockIdx.x * (int64_t)kHashTile; base < K;
+         base += (int64_t)gridDim.x * kHashTile) {
+        // 1. the tile's distinct keys, numbered in shared memory
+        int ent[kHashPer];
 #pragma unroll
-        for (int i = 0; i < KF::W; ++i) h = mix64(h ^ (uint64_t)w[i] ^ ((uint64_t)i << 40));
-        uint32_t s = (uint32_t)h & mask;
-        // bounded linear probing: at most mask + 1 slots are visited
-        for (uint32_t probes = 0;; ++probes) {
-            if (probes > mask) {
-                atomicOr(err, kErrTableFull);
-                slot_of[k] = 0;
-                break;
+        for (int r = 0; r < kHashPer; ++r) {
+            const int t = r * kHashThreads + threadIdx.x;
+            const int64_t k = base + t;
+            ent[r] = -1;
+            if (k >= K) continue;
+            uint32_t w[KF::W];
+            if (!kf.words(k, w)) {
+                atomicOr(err, kErrNaN);
+                continue;
             }
-            int32_t o = __ldcg(&owner[s]);
-            if (o < 0) {
-                int32_t prev = atomicCAS(&owner[s], -1, (int32_t)k);
-                if (prev < 0) {
-                    atomicMin(&minidx[s], (int32_t)k);
-                    slot_of[k] = (int32_t)s;
+            // local entry: a cheap 32-bit multiplicative fold of the words
+            uint32_t hl = 0x9e3779b9u;
+#pragma unroll
+            for (int i = 0; i < KF::W; ++i) hl = (hl ^ w[i]) * 0x85ebca6bu;
+            uint32_t e = (hl ^ (hl >> 15)) & (kHashLocal - 1);
+            for (int probes = 0; probes < kHashLocal; ++probes) {
+                int32_t rep = *(volatile int32_t *)&l_rep[e];
+                if (rep < 0) {
+                    rep = atomicCAS(&l_rep[e], -1, t);
+                    if (rep < 0) {
+                        l_used[atomicAdd(&l_n, 1)] = (int32_t)e;
+                        ent[r] = (int)e;
+                        break;
+                    }
+                }
+                uint32_t w2[KF::W];
+                kf.words(base + rep, w2);
+                bool eq = true;
+#pragma unroll
+                for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
+                if (eq) {
+                    ent[r] = (int)e;
                     break;
                 }
-                o = prev;
+                e = (e + 1) & (kHashLocal - 1);
             }
-            uint32_t w2[KF::W];
-            kf.words(o, w2);
-            bool eq = true;
-#pragma unroll
-            for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
-            if (eq) {
-                if ((int32_t)k < __ldcg(&minidx[s])) atomicMin(&minidx[s], (int32_t)k);
-                slot_of[k] = (int32_t)s;
-                break;
+            if (ent[r] < 0) {  // unreachable: the table has room for every key of a tile
+                atomicOr(err, kErrTableFull);
+                continue;
             }
-            s = (s + 1) & mask;
+            if (t < *(volatile int32_t *)&l_min[ent[r]]) atomicMin(&l_min[ent[r]], t);
         }
+        __syncthreads();
+        // 2. one global probe per distinct key (bounded linear probing)
+        const int nl = l_n;
+        for (int u = threadIdx.x; u < nl; u += kHashThreads) {
+            const int e = l_used[u];
+            int32_t found = 0;
+            if (*(volatile int *)err & kErrGrow) {  // the table is outgrown: the pass is redone
+                l_slot[e] = found;
+                continue;
+            }
+            const int64_t k = base + l_min[e];
+            uint32_t w[KF::W];
+            kf.words(k, w);
+            uint32_t s = (uint32_t)key_hash(w, KF::W) & mask;
+            for (uint32_t probes = 0;; ++probes) {
+                if (probes > mask) {
+                    atomicOr(err, kErrTableFull);
+                    break;
+                }
+                int32_t o = __ldcg(&owner[s]);
+                if (o < 0) {
+                    int32_t prev = atomicCAS(&owner[s], -1, (int32_t)k);
+                    if (prev < 0) {
+                        if (atomicAdd(n_keys, 1) >= key_limit) atomicOr(err, kErrGrow);
+                        atomicMin(&minidx[s], (int32_t)k);
+                        found = (int32_t)s;
+                        break;
+                    }
+                    o = prev;
+                }
+                uint32_t w2[KF::W];
+                kf.words(o, w2);
+                bool eq = true;
+#pragma unroll
+                for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
+                if (eq) {
+                    if ((int32_t)k < __ldcg(&minidx[s])) atomicMin(&minidx[s], (int32_t)k);
+                    found = (int32_t)s;
+                    break;
+                }
+                s = (s + 1) & mask;
+            }
+            l_slot[e] = found;
+        }
+        __syncthreads();
+        // 3. every element's slot; then the used entries are freed
+#pragma unroll
+        for (int r = 0; r < kHashPer; ++r) {
+            const int64_t k = base + r * kHashThreads + threadIdx.x;
+            if (k < K) slot_of[k] = ent[r] >= 0 ? l_slot[ent[r]] : 0;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < nl; u += kHashThreads) {
+            const int e = l_used[u];
+            l_rep[e] = -1;
+            l_min[e] = INT_MAX;
+        }
+        if (threadIdx.x == 0) l_n = 0;
+        __syncthreads();
     }
 }
 
@@ -198,15 +295,20 @@ __global__ void k_scan_tiles(const int32_t *in, int64_t n, int64_t *tile_sum) {
     if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
 }
 
+// exclusive scan of the tile sums in one CTA: thread t sums its contiguous
+// chunk, one block scan gives the chunk offsets, and the chunks are written
+// back in order
 __global__ void k_scan_tile_sums(int64_t *tile_sum, int64_t nt) {
-    int64_t carry = 0;
-    for (int64_t base = 0; base < nt; base += kScanThreads) {
-        int64_t idx = base + threadIdx.x;
-        int64_t v = idx < nt ? tile_sum[idx] : 0;
-        int64_t tot;
-        int64_t ex = block_exclusive_scan(v, tot);
-        if (idx < nt) tile_sum[idx] = carry + ex;
-        carry += tot;
+    const int64_t per = (nt + kScanThreads - 1) / kScanThreads;
+    const int64_t b = threadIdx.x * per, e = min(nt, b + per);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += tile_sum[i];
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(s, tot);
+    for (int64_t i = b; i < e; ++i) {
+        const int64_t v = tile_sum[i];
+        tile_sum[i] = ex;
+        ex += v;
     }
 }
 
@@ -349,37 +451,53 @@ __global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *st
 // scatter leaves members in atomic order): the layout becomes deterministic,
 // and along a cell consecutive positions hold isochromats in phantom order,
 // so neighbouring lanes of the fused kernel read neighbouring table entries.
-// One CTA per cell (bitonic sort in shared memory); runs longer than
-// kSortMax keep the scatter order.
+// One CTA per cell; the members are distinct, so each one's place in the run
+// is the number of members below it (counted over the run in shared memory).
+// Runs longer than kSortMax keep the scatter order.
 constexpr int kSortMax = 4096;
 __global__ void __launch_bounds__(256) k_sort_cells(const int32_t *cstart, const int32_t *ccount,
                                                     int64_t nc, int32_t *perm) {
-    __shared__ int32_t v[kSortMax];
+    __shared__ __align__(16) int32_t v[kSortMax];
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
         const int n = ccount[c];
         if (n < 2 || n > kSortMax) continue;  // uniform in the CTA
-        int p2 = 2;
-        while (p2 < n) p2 <<= 1;
+        const int n4 = (n + 3) & ~3;
         const int s = cstart[c];
-        for (int i = threadIdx.x; i < p2; i += blockDim.x) v[i] = i < n ? perm[s + i] : 0x7fffffff;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) v[i] = i < n ? perm[s + i] : INT_MAX;
         __syncthreads();
-        for (int k = 2; k <= p2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-                    const int l = i ^ j;
-                    if (l > i) {
-                        const int x = v[i], y = v[l];
-                        if ((x > y) == ((i & k) == 0)) {
-                            v[i] = y;
-                            v[l] = x;
-                        }
-                    }
-                }
-                __syncthreads();
+        const int4 *v4 = reinterpret_cast<const int4 *>(v);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int x = v[i];
+            int r = 0;
+            for (int j = 0; j < n4 / 4; ++j) {
+                const int4 q = v4[j];
+                r += (int)(q.x < x) + (int)(q.y < x) + (int)(q.z < x) + (int)(q.w < x);
             }
+            perm[s + r] = x;
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) perm[s + i] = v[i];
         __syncthreads();
+    }
+}
+
+// out[a][i] = in[a][perm[i]] for up to kGatherMax 32-bit arrays in one pass
+constexpr int kGatherMax = 24;
+struct GatherSet {
+    const uint32_t *in[kGatherMax];
+    uint32_t *out[kGatherMax];
+    int n;
+};
+
+__global__ void k_gather_set(int64_t K, const int32_t *perm, GatherSet g) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = perm[i];
+        uint32_t v[kGatherMax];  // every load issued before the first store
+#pragma unroll
+        for (int a = 0; a < kGatherMax; ++a)
+            if (a < g.n) v[a] = __ldg(g.in[a] + p);
+#pragma unroll
+        for (int a = 0; a < kGatherMax; ++a)
+            if (a < g.n) g.out[a][i] = v[a];
     }
 }
 
@@ -397,65 +515,74 @@ int grid_for(mrsim_ctx *c, int64_t n, int threads = 256) {
 }
 
 // Hash-group K elements; writes rank-of-representative gid[K] and returns the
-// group count.  flag/rank stay in scratch slots 2/3 for table extraction.
+// group count.  flag/rank stay in scratch slots 2/3 for table extraction.  The
+// table first gets kHashFirstSlots slots (it then stays in L2 and is cheap to
+// clear); if more than half of them fill, the kernel says so and the whole
+// pass is redone with room for K distinct keys.  Callers that expect many
+// distinct keys (few_keys = false) start with that room.
+constexpr uint64_t kHashFirstSlots = 1ull << 21;
+
 template <class KF>
 int64_t hash_group(mrsim_ctx *c, int64_t K, const KF &kf, int32_t *gid, int32_t **flag_out,
-                   int32_t **rank_out) {
-    uint64_t C = 1024;
-    while (C < (uint64_t)(2 * K)) C <<= 1;
-    if (C > (1ull << 31)) fail(MRSIM_EINVAL, "too many isochromats for the group hash table");
-    int32_t *owner = (int32_t *)scratch(c, 0, C * sizeof(int32_t));
-    int32_t *minidx = (int32_t *)scratch(c, 1, C * sizeof(int32_t));
-    int32_t *flag = (int32_t *)scratch(c, 2, K * sizeof(int32_t));
-    int32_t *rank = (int32_t *)scratch(c, 3, K * sizeof(int32_t));
-    int32_t *slot_of = (int32_t *)scratch(c, 4, K * sizeof(int32_t));
-    int64_t nt = (K + kScanTile - 1) / kScanTile;
-    int64_t *tsum = (int64_t *)scratch(c, 5, nt * sizeof(int64_t));
-    int *err = c->dev_err.as<int>();
-    MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-    MRSIM_CUDA(cudaMemsetAsync(owner, 0xff, C * sizeof(int32_t), c->stream));
-    {
-        KScope ks(c, "group_fill");
-        k_fill_i32<<<grid_for(c, C), 256, 0, c->stream>>>(minidx, C, 0x7fffffff);
+                   int32_t **rank_out, bool few_keys = true) {
+    uint64_t C_full = 1024;
+    while (C_full < (uint64_t)(2 * K)) C_full <<= 1;
+    if (C_full > (1ull << 31)) fail(MRSIM_EINVAL, "too many isochromats for the group hash table");
+    for (uint64_t C = few_keys ? std::min(C_full, kHashFirstSlots) : C_full;; C = C_full) {
+        int32_t *owner = (int32_t *)scratch(c, 0, C * sizeof(int32_t));
+        int32_t *minidx = (int32_t *)scratch(c, 1, C * sizeof(int32_t));
+        int32_t *flag = (int32_t *)scratch(c, 2, K * sizeof(int32_t));
+        int32_t *rank = (int32_t *)scratch(c, 3, K * sizeof(int32_t));
+        int32_t *slot_of = (int32_t *)scratch(c, 4, K * sizeof(int32_t));
+        int64_t nt = (K + kScanTile - 1) / kScanTile;
+        int64_t *tsum = (int64_t *)scratch(c, 5, nt * sizeof(int64_t));
+        int *err = c->dev_err.as<int>();  // [0] error bits, [1] distinct keys inserted
+        MRSIM_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), c->stream));
+        MRSIM_CUDA(cudaMemsetAsync(owner, 0xff, C * sizeof(int32_t), c->stream));
+        {
+            KScope ks(c, "group_fill");
+            k_fill_i32<<<grid_for(c, C), 256, 0, c->stream>>>(minidx, C, 0x7fffffff);
+        }
+        {
+            KScope ks(c, "group_hash_insert");
+            k_hash_insert<<<grid_for(c, K, kHashTile), kHashThreads, 0, c->stream>>>(
+                K, kf, owner, minidx, slot_of, (uint32_t)(C - 1), (int)(C / 2), err, err + 1);
+        }
+        {
+            KScope ks(c, "group_rep_flag");
+            k_rep_flag<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, flag);
+        }
+        {
+            KScope ks(c, "scan_tiles");
+            k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum);
+        }
+        {
+            KScope ks(c, "scan_tile_sums");
+            k_scan_tile_sums<<<1, kScanThreads, 0, c->stream>>>(tsum, nt);
+        }
+        {
+            KScope ks(c, "scan_apply");
+            k_scan_apply<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum, rank);
+        }
+        {
+            KScope ks(c, "group_assign");
+            k_assign<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, rank, gid);
+        }
+        int h_err = 0;
+        int32_t last[2] = {0, 0};
+        MRSIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(&last[0], rank + (K - 1), sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(&last[1], flag + (K - 1), sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (h_err & kErrNaN) fail(MRSIM_EINVAL, "NaN in a grouping key");
+        if ((h_err & kErrGrow) && C < C_full) continue;
+        if (h_err & (kErrTableFull | kErrGrow)) fail(MRSIM_ECUDA, "group hash table overflow");
+        *flag_out = flag;
+        *rank_out = rank;
+        return (int64_t)last[0] + last[1];
     }
-    {
-        KScope ks(c, "group_hash_insert");
-        k_hash_insert<<<grid_for(c, K), 256, 0, c->stream>>>(K, kf, owner, minidx, slot_of,
-                                                            (uint32_t)(C - 1), err);
-    }
-    {
-        KScope ks(c, "group_rep_flag");
-        k_rep_flag<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, flag);
-    }
-    {
-        KScope ks(c, "scan_tiles");
-        k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum);
-    }
-    {
-        KScope ks(c, "scan_tile_sums");
-        k_scan_tile_sums<<<1, kScanThreads, 0, c->stream>>>(tsum, nt);
-    }
-    {
-        KScope ks(c, "scan_apply");
-        k_scan_apply<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(flag, K, tsum, rank);
-    }
-    {
-        KScope ks(c, "group_assign");
-        k_assign<<<grid_for(c, K), 256, 0, c->stream>>>(K, slot_of, minidx, rank, gid);
-    }
-    int h_err = 0;
-    int32_t last[2] = {0, 0};
-    MRSIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    MRSIM_CUDA(cudaMemcpyAsync(&last[0], rank + (K - 1), sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               c->stream));
-    MRSIM_CUDA(cudaMemcpyAsync(&last[1], flag + (K - 1), sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               c->stream));
-    sync(c);
-    if (h_err & kErrNaN) fail(MRSIM_EINVAL, "NaN in a grouping key");
-    if (h_err & kErrTableFull) fail(MRSIM_ECUDA, "group hash table overflow");
-    *flag_out = flag;
-    *rank_out = rank;
-    return (int64_t)last[0] + last[1];
 }
 
 }  // namespace
@@ -609,36 +736,41 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
                                                   g->perm.as<int32_t>());
     }
     const int32_t *perm = g->perm.as<int32_t>();
-    auto gather_f = [&](DBuf &dst, const DBuf &src) {
-        dst = dalloc(K * sizeof(float));
-        KScope ks(c, "layout_gather");
-        k_gather<float><<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, src.as<float>(),
-                                                               dst.as<float>());
+    // every per-isochromat array in layout order, in one gather pass
+    GatherSet gs{};
+    auto add = [&](DBuf &dst, const void *src) {
+        dst = dalloc(K * sizeof(uint32_t));
+        gs.in[gs.n] = static_cast<const uint32_t *>(src);
+        gs.out[gs.n] = dst.as<uint32_t>();
+        ++gs.n;
     };
-    gather_f(g->x, ph->x);
-    gather_f(g->y, ph->y);
-    gather_f(g->z, ph->z);
-    gather_f(g->T1, ph->T1);
-    gather_f(g->T2, ph->T2);
-    gather_f(g->dB0, ph->dB0);
-    gather_f(g->M0, ph->M0);
+    add(g->x, ph->x.p);
+    add(g->y, ph->y.p);
+    add(g->z, ph->z.p);
+    add(g->T1, ph->T1.p);
+    add(g->T2, ph->T2.p);
+    add(g->dB0, ph->dB0.p);
+    add(g->M0, ph->M0.p);
     g->has_b1 = ph->has_b1;
-    if (ph->has_b1) gather_f(g->b1, ph->b1);
+    if (ph->has_b1) add(g->b1, ph->b1.p);
+    for (int t = 0; t < kNTypes; ++t)
+        if (g->built[t]) add(g->gid_sorted[t], g->gid_orig[t].p);
+    static_assert(7 + 1 + kNTypes <= kGatherMax, "gather set too small");
+    {
+        KScope ks(c, "layout_gather");
+        k_gather_set<<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, gs);
+    }
     g->has_M_init = ph->has_M_init;
     if (ph->has_M_init) {
         g->M_init = dalloc(3 * K * sizeof(float));
+        GatherSet gm{};
         for (int r = 0; r < 3; ++r) {
-            KScope ks(c, "layout_gather");
-            k_gather<float><<<grid_for(c, K), 256, 0, c->stream>>>(
-                K, perm, ph->M_init.as<float>() + r * K, g->M_init.as<float>() + r * K);
+            gm.in[r] = ph->M_init.as<uint32_t>() + r * K;
+            gm.out[r] = g->M_init.as<uint32_t>() + r * K;
         }
-    }
-    for (int t = 0; t < kNTypes; ++t) {
-        if (!g->built[t]) continue;
-        g->gid_sorted[t] = dalloc(K * sizeof(int32_t));
+        gm.n = 3;
         KScope ks(c, "layout_gather");
-        k_gather<int32_t><<<grid_for(c, K), 256, 0, c->stream>>>(
-            K, perm, g->gid_orig[t].as<int32_t>(), g->gid_sorted[t].as<int32_t>());
+        k_gather_set<<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, gm);
     }
     sync(c);
 }
@@ -705,7 +837,7 @@ void build_axis_index(mrsim_ctx *c, mrsim_groups *g) {
 int64_t distinct_features(mrsim_ctx *c, int64_t K, const int32_t *x, const float *T1,
                           const float *T2, int32_t *id, DBuf &table, DBuf &tf, DBuf &count) {
     int32_t *flag, *rank;
-    const int64_t U = hash_group(c, K, FeatureKey{x, T1, T2, K}, id, &flag, &rank);
+    const int64_t U = hash_group(c, K, FeatureKey{x, T1, T2, K}, id, &flag, &rank, false);
     table = dalloc(3 * U * sizeof(int32_t));
     tf = dalloc(2 * U * sizeof(float));
     count = dalloc(U * sizeof(int32_t));

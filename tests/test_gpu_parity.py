@@ -110,6 +110,34 @@ def test_group_ids_bit_exact(mrsim, ctx, shape):
     ctx.free("ph", hp)
 
 
+@pytest.mark.parametrize("n_distinct", [1_000_000, 1_310_720])
+def test_group_ids_bit_exact_many_distinct_keys(mrsim, ctx, n_distinct):
+    """Group numbering with about a million distinct keys per type: the group
+    build's first hash table takes 2^20 keys and the pass is redone with room
+    for every isochromat once more arrive.  Here only dB0 separates the Gz
+    groups, so they number exactly n_distinct; the Gx groups (x, dB0) number
+    more and take the redo in both cases."""
+    ph = configs.small_phantom(128, 128, 80)
+    rng = np.random.default_rng(11)
+    ph.z = np.zeros(ph.K, np.float32)
+    ph.T1 = np.full(ph.K, 1.0, np.float32)
+    ph.T2 = np.full(ph.K, 0.1, np.float32)
+    ph.dB0 = (rng.permutation(ph.K) % n_distinct).astype(np.float32) * np.float32(0.01)
+    seq = fse_2d(n_ro=16, n_pe=16, etl=4, n_shots=1)
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    hg = ctx.group(hp, hs)
+    for gt in (mrsim.G_X, mrsim.G_Z):
+        n, gid = mrsim.mrsim_group_info(hg, gt, ph.K)
+        ref, nref = oracle.group(ph, gt)
+        assert n == nref
+        assert np.array_equal(gid, ref)
+    assert mrsim.mrsim_group_info(hg, mrsim.G_Z)[0] == n_distinct
+    ctx.free("grp", hg)
+    ctx.free("seq", hs)
+    ctx.free("ph", hp)
+
+
 def test_group_ids_with_b1_and_negative_zero(mrsim, ctx):
     ph = configs.small_phantom(16, 16, 2)
     rng = np.random.default_rng(3)
