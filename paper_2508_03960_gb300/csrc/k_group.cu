@@ -414,6 +414,45 @@ __global__ void k_count(int64_t K, const int32_t *key, int32_t *count) {
     }
 }
 
+// Dense cells: when (primary groups) x (secondary groups) is small, the cell
+// key g_p * G_s + g_s indexes a flag array directly; an exclusive scan of the
+// flags numbers the present keys in (g_p, g_s) order, which is the layout's
+// cell order, so no hashing or host sort is needed.
+__global__ void k_cell_mark(int64_t K, const int32_t *ga, const int32_t *gb, int32_t Gb,
+                            int32_t *present) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        present[(int64_t)ga[k] * Gb + (gb ? gb[k] : 0)] = 1;
+}
+
+// cell of every isochromat (the rank of its key) and the member count per cell
+__global__ void k_cell_assign(int64_t K, const int32_t *ga, const int32_t *gb, int32_t Gb,
+                              const int32_t *rank, int32_t *cell, int32_t *count) {
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < K;
+         k0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = k0 + threadIdx.x;
+        const bool act = k < K;
+        int32_t c = 0;
+        if (act) {
+            c = rank[(int64_t)ga[k] * Gb + (gb ? gb[k] : 0)];
+            cell[k] = c;
+        }
+        warp_agg_inc(count, c, act);
+    }
+}
+
+// primary and secondary group of every cell
+__global__ void k_cell_keys(int64_t NK, const int32_t *present, const int32_t *rank, int32_t Gb,
+                            int32_t *cgp, int32_t *cgr) {
+    for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < NK;
+         key += (int64_t)gridDim.x * blockDim.x) {
+        if (!present[key]) continue;
+        const int32_t c = rank[key];
+        cgp[c] = (int32_t)(key / Gb);
+        cgr[c] = (int32_t)(key % Gb);
+    }
+}
+
 __global__ void k_scatter(int64_t K, const int32_t *cell, const int32_t *cell_off,
                           int32_t *cursor, int32_t *perm) {
     for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < K;
@@ -646,63 +685,144 @@ void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &
     tab.d_par64 = std::move(t);
 }
 
+namespace {
+
+// exclusive prefix sum of n int32 values (three passes) into out
+void scan_i32(mrsim_ctx *c, const int32_t *in, int64_t n, int32_t *out) {
+    const int64_t nt = (n + kScanTile - 1) / kScanTile;
+    int64_t *tsum = (int64_t *)scratch(c, 5, nt * sizeof(int64_t));
+    {
+        KScope ks(c, "scan_tiles");
+        k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(in, n, tsum);
+    }
+    {
+        KScope ks(c, "scan_tile_sums");
+        k_scan_tile_sums<<<1, kScanThreads, 0, c->stream>>>(tsum, nt);
+    }
+    {
+        KScope ks(c, "scan_apply");
+        k_scan_apply<<<(unsigned)nt, kScanThreads, 0, c->stream>>>(in, n, tsum, out);
+    }
+}
+
+// largest (primary groups) x (secondary groups) laid out through a flag array
+constexpr int64_t kDenseCells = 1 << 24;
+
+}  // namespace
+
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
     const int64_t K = ph->K;
     const int p = g->primary, s = g->secondary;
-    PairKey kf{g->gid_orig[p].as<int32_t>(), s >= 0 ? g->gid_orig[s].as<int32_t>() : nullptr};
-    DBuf cell = dalloc(K * sizeof(int32_t));
-    int32_t *flag, *rank;
-    const int64_t nc = hash_group(c, K, kf, cell.as<int32_t>(), &flag, &rank);
-    g->n_cells = nc;
-    DBuf ca = dalloc(nc * sizeof(int32_t)), cb = dalloc(nc * sizeof(int32_t));
-    DBuf cnt = dalloc(nc * sizeof(int32_t));
-    {
-        KScope ks(c, "layout_cell_table");
-        k_cell_table<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, kf.a, kf.b,
-                                                            ca.as<int32_t>(), cb.as<int32_t>());
-    }
-    MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
-    {
-        KScope ks(c, "layout_count");
-        k_count<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), cnt.as<int32_t>());
-    }
-    std::vector<int32_t> ha(nc), hb(nc), hc(nc);
-    MRSIM_CUDA(cudaMemcpyAsync(ha.data(), ca.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
-    MRSIM_CUDA(cudaMemcpyAsync(hb.data(), cb.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
-    MRSIM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
-    sync(c);
-    // cells sorted by (primary gid, secondary gid): both are group ids below
-    // known bounds, so two stable counting passes (by the secondary id, then by
-    // the primary id) sort in linear time; the pairs are distinct, so the order
-    // is the unique sorted one
+    const int32_t *ga = g->gid_orig[p].as<int32_t>();
+    const int32_t *gb = s >= 0 ? g->gid_orig[s].as<int32_t>() : nullptr;
     const int64_t Ga = g->n_groups[p], Gb = s >= 0 ? g->n_groups[s] : 1;
-    std::vector<int32_t> by_b(nc), order(nc);
-    {
-        std::vector<int32_t> pos(Gb + 1, 0);
-        for (int64_t i = 0; i < nc; ++i) ++pos[hb[i] + 1];
-        for (int64_t v = 0; v < Gb; ++v) pos[v + 1] += pos[v];
-        for (int64_t i = 0; i < nc; ++i) by_b[pos[hb[i]]++] = (int32_t)i;
-    }
-    {
-        std::vector<int32_t> pos(Ga + 1, 0);
-        for (int64_t i = 0; i < nc; ++i) ++pos[ha[i] + 1];
-        for (int64_t v = 0; v < Ga; ++v) pos[v + 1] += pos[v];
-        for (int64_t t = 0; t < nc; ++t) {
-            const int32_t i = by_b[t];
-            order[pos[ha[i]]++] = i;
+    DBuf cell = dalloc(K * sizeof(int32_t));  // cell id of every isochromat
+    DBuf doff_own;                            // layout offset of every cell id (hashed ids)
+    const int32_t *doff = nullptr;
+    std::vector<int32_t> s_cnt;  // member counts, cells in layout order
+    int64_t nc = 0;
+    auto up32 = [&](DBuf &d, const std::vector<int32_t> &v) {
+        d = dalloc(std::max<int64_t>(nc, 1) * sizeof(int32_t));
+        upload(c, d.p, v.data(), nc * sizeof(int32_t));
+    };
+    if (Ga * Gb <= kDenseCells) {
+        // cell ids are the ranks of the present keys g_p * G_s + g_s: layout order
+        const int64_t NK = Ga * Gb;
+        DBuf present = dalloc(NK * sizeof(int32_t)), rank = dalloc(NK * sizeof(int32_t));
+        MRSIM_CUDA(cudaMemsetAsync(present.p, 0, NK * sizeof(int32_t), c->stream));
+        {
+            KScope ks(c, "layout_cell_mark");
+            k_cell_mark<<<grid_for(c, K), 256, 0, c->stream>>>(K, ga, gb, (int32_t)Gb,
+                                                               present.as<int32_t>());
         }
-    }
-    std::vector<int32_t> off(nc);
-    int64_t run = 0;
-    for (int64_t i = 0; i < nc; ++i) {
-        off[order[i]] = (int32_t)run;
-        run += hc[order[i]];
-    }
-    DBuf doff = dalloc(nc * sizeof(int32_t));
-    upload(c, doff.p, off.data(), nc * 4);
-    {
+        scan_i32(c, present.as<int32_t>(), NK, rank.as<int32_t>());
+        int32_t last[2] = {0, 0};
+        MRSIM_CUDA(cudaMemcpyAsync(&last[0], rank.as<int32_t>() + (NK - 1), sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(&last[1], present.as<int32_t>() + (NK - 1), sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        nc = (int64_t)last[0] + last[1];
+        g->n_cells = nc;
+        g->cell_count = dalloc(nc * sizeof(int32_t));
+        g->cell_start = dalloc(nc * sizeof(int32_t));
+        g->cell_gp = dalloc(nc * sizeof(int32_t));
+        g->cell_gr = dalloc(nc * sizeof(int32_t));
+        MRSIM_CUDA(cudaMemsetAsync(g->cell_count.p, 0, nc * sizeof(int32_t), c->stream));
+        {
+            KScope ks(c, "layout_cell_assign");
+            k_cell_assign<<<grid_for(c, K), 256, 0, c->stream>>>(
+                K, ga, gb, (int32_t)Gb, rank.as<int32_t>(), cell.as<int32_t>(),
+                g->cell_count.as<int32_t>());
+        }
+        {
+            KScope ks(c, "layout_cell_table");
+            k_cell_keys<<<grid_for(c, NK), 256, 0, c->stream>>>(
+                NK, present.as<int32_t>(), rank.as<int32_t>(), (int32_t)Gb,
+                g->cell_gp.as<int32_t>(), g->cell_gr.as<int32_t>());
+        }
+        scan_i32(c, g->cell_count.as<int32_t>(), nc, g->cell_start.as<int32_t>());
+        s_cnt.resize(nc);
+        MRSIM_CUDA(cudaMemcpyAsync(s_cnt.data(), g->cell_count.p, nc * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        doff = g->cell_start.as<int32_t>();
+    } else {
+        // hashed cell ids, ordered on the host
+        PairKey kf{ga, gb};
+        int32_t *flag, *rank;
+        nc = hash_group(c, K, kf, cell.as<int32_t>(), &flag, &rank);
+        g->n_cells = nc;
+        DBuf ca = dalloc(nc * sizeof(int32_t)), cb = dalloc(nc * sizeof(int32_t));
+        DBuf cnt = dalloc(nc * sizeof(int32_t));
+        {
+            KScope ks(c, "layout_cell_table");
+            k_cell_table<<<grid_for(c, K), 256, 0, c->stream>>>(K, flag, rank, kf.a, kf.b,
+                                                                ca.as<int32_t>(), cb.as<int32_t>());
+        }
+        MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
+        {
+            KScope ks(c, "layout_count");
+            k_count<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(),
+                                                           cnt.as<int32_t>());
+        }
+        std::vector<int32_t> ha(nc), hb(nc), hc(nc);
+        MRSIM_CUDA(cudaMemcpyAsync(ha.data(), ca.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(hb.data(), cb.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+        MRSIM_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        // cells sorted by (primary gid, secondary gid): both are group ids below
+        // known bounds, so two stable counting passes (by the secondary id, then by
+        // the primary id) sort in linear time; the pairs are distinct, so the order
+        // is the unique sorted one
+        std::vector<int32_t> by_b(nc), order(nc);
+        {
+            std::vector<int32_t> pos(Gb + 1, 0);
+            for (int64_t i = 0; i < nc; ++i) ++pos[hb[i] + 1];
+            for (int64_t v = 0; v < Gb; ++v) pos[v + 1] += pos[v];
+            for (int64_t i = 0; i < nc; ++i) by_b[pos[hb[i]]++] = (int32_t)i;
+        }
+        {
+            std::vector<int32_t> pos(Ga + 1, 0);
+            for (int64_t i = 0; i < nc; ++i) ++pos[ha[i] + 1];
+            for (int64_t v = 0; v < Ga; ++v) pos[v + 1] += pos[v];
+            for (int64_t t = 0; t < nc; ++t) {
+                const int32_t i = by_b[t];
+                order[pos[ha[i]]++] = i;
+            }
+        }
+        std::vector<int32_t> off(nc);
+        int64_t run = 0;
+        for (int64_t i = 0; i < nc; ++i) {
+            off[order[i]] = (int32_t)run;
+            run += hc[order[i]];
+        }
+        doff_own = dalloc(nc * sizeof(int32_t));
+        upload(c, doff_own.p, off.data(), nc * 4);
+        doff = doff_own.as<int32_t>();
         // cell tables in layout order, for the cell-mode fused kernel
-        std::vector<int32_t> s_start(nc), s_cnt(nc), s_gp(nc), s_gr(nc);
+        std::vector<int32_t> s_start(nc), s_gp(nc), s_gr(nc);
+        s_cnt.resize(nc);
         for (int64_t i = 0; i < nc; ++i) {
             const int32_t cc = order[i];
             s_start[i] = off[cc];
@@ -710,22 +830,19 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
             s_gp[i] = ha[cc];
             s_gr[i] = hb[cc];
         }
-        auto up32 = [&](DBuf &d, const std::vector<int32_t> &v) {
-            d = dalloc(std::max<int64_t>(nc, 1) * sizeof(int32_t));
-            upload(c, d.p, v.data(), nc * sizeof(int32_t));
-        };
         up32(g->cell_start, s_start);
         up32(g->cell_count, s_cnt);
         up32(g->cell_gp, s_gp);
         up32(g->cell_gr, s_gr);
-        build_cell_threads(c, g, s_cnt);
     }
-    MRSIM_CUDA(cudaMemsetAsync(cnt.p, 0, nc * sizeof(int32_t), c->stream));
+    build_cell_threads(c, g, s_cnt);
+    DBuf cursor = dalloc(nc * sizeof(int32_t));
+    MRSIM_CUDA(cudaMemsetAsync(cursor.p, 0, nc * sizeof(int32_t), c->stream));
     g->perm = dalloc(K * sizeof(int32_t));
     {
         KScope ks(c, "layout_scatter");
-        k_scatter<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), doff.as<int32_t>(),
-                                                         cnt.as<int32_t>(), g->perm.as<int32_t>());
+        k_scatter<<<grid_for(c, K), 256, 0, c->stream>>>(K, cell.as<int32_t>(), doff,
+                                                         cursor.as<int32_t>(), g->perm.as<int32_t>());
     }
     {
         KScope ks(c, "layout_sort_cells");

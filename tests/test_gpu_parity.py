@@ -138,6 +138,41 @@ def test_group_ids_bit_exact_many_distinct_keys(mrsim, ctx, n_distinct):
     ctx.free("ph", hp)
 
 
+@pytest.mark.parametrize("n_db0", [10, 40])
+def test_layout_dense_and_hashed_cells(mrsim, ctx, n_db0):
+    """The layout's cells come from a flag array over (Gx group, Gz group)
+    pairs when there are at most 2^24 pairs (10 dB0 classes: 1,280 x 1,280)
+    and from the hashed cell path above that (40 classes: 5,120 x 5,120).
+    Either way the grouped FSE signal and final magnetization match the
+    per-isochromat GPU form, and reproducible-mode runs are bit-identical
+    across group builds (the layout is deterministic)."""
+    ph = configs.small_phantom(128, 128, 128)
+    rng = np.random.default_rng(17)
+    ph.T1 = np.full(ph.K, 0.9, np.float32)
+    ph.T2 = np.full(ph.K, 0.08, np.float32)
+    ph.dB0 = rng.integers(0, n_db0, ph.K).astype(np.float32) * np.float32(0.5)
+    seq = fse_2d(n_ro=16, n_pe=16, etl=4, n_shots=1)
+    hp = ctx.phantom(ph)
+    hs = ctx.sequence(seq)
+    assert mrsim.mrsim_group_info(hg := ctx.group(hp, hs), mrsim.G_X)[0] == 128 * n_db0
+    assert mrsim.mrsim_group_info(hg, mrsim.G_Z)[0] == 128 * n_db0
+    hg2 = ctx.group(hp, hs)
+    mrsim.mrsim_set_reproducible(ctx.h, 1)  # fixed-point sums: bit-identical runs
+    try:
+        sig, M = ctx.run(hp, hs, hg, mrsim.GROUPED, mrsim.FP32, K=ph.K, want_M=True)
+        sig2, M2 = ctx.run(hp, hs, hg2, mrsim.GROUPED, mrsim.FP32, K=ph.K, want_M=True)
+    finally:
+        mrsim.mrsim_set_reproducible(ctx.h, 0)
+    assert np.array_equal(sig, sig2) and np.array_equal(M, M2)
+    ref, Mref = ctx.run(hp, hs, None, mrsim.PLAIN, mrsim.FP32, K=ph.K, want_M=True)
+    assert oracle.rel_l2(sig, ref) <= 1e-4
+    assert float(np.max(np.abs(M - Mref))) <= 1e-4
+    for h in (hg, hg2):
+        ctx.free("grp", h)
+    ctx.free("seq", hs)
+    ctx.free("ph", hp)
+
+
 def test_group_ids_with_b1_and_negative_zero(mrsim, ctx):
     ph = configs.small_phantom(16, 16, 2)
     rng = np.random.default_rng(3)
