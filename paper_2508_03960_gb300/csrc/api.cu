@@ -6,6 +6,9 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <functional>
+#include <thread>
+#include <exception>
 #include <map>
 #include <new>
 #include <unordered_map>
@@ -236,6 +239,49 @@ static_assert(G_XY == MRSIM_G_XY && G_XZ == MRSIM_G_XZ && G_YZ == MRSIM_G_YZ,
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
 // (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
 // of G_GENERAL), sample offsets and with-RF content ids.  Needs no device.
+// The caller's segment arrays, copied into the sequence.  Long sequences copy
+// their eight arrays on eight host threads (one core copies at a fraction of
+// the host's memory bandwidth); a thread that cannot be started leaves its
+// copy to the calling thread, and a failed copy is rethrown here.
+void copy_segments(mrsim_seq *s, int64_t n, const double *dt, const int32_t *rep,
+                   const float *b1re, const float *b1im, const float *gx, const float *gy,
+                   const float *gz, const uint8_t *adc) {
+    s->n_seg = n;
+    std::function<void()> jobs[8] = {
+        [&] { s->dt.assign(dt, dt + n); },     [&] { s->rep.assign(rep, rep + n); },
+        [&] { s->b1re.assign(b1re, b1re + n); }, [&] { s->b1im.assign(b1im, b1im + n); },
+        [&] { s->gx.assign(gx, gx + n); },     [&] { s->gy.assign(gy, gy + n); },
+        [&] { s->gz.assign(gz, gz + n); },     [&] { s->adc.assign(adc, adc + n); }};
+    std::exception_ptr ep[8];
+    auto run = [&](int i) {
+        try {
+            jobs[i]();
+        } catch (...) {
+            ep[i] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    bool inline_job[8] = {};
+    if (n >= (1 << 16)) {
+        th.reserve(7);
+        for (int i = 1; i < 8; ++i) {
+            try {
+                th.emplace_back(run, i);
+            } catch (...) {
+                inline_job[i] = true;
+            }
+        }
+    } else {
+        for (int i = 1; i < 8; ++i) inline_job[i] = true;
+    }
+    run(0);
+    for (int i = 1; i < 8; ++i)
+        if (inline_job[i]) run(i);
+    for (auto &t : th) t.join();
+    for (auto &e : ep)
+        if (e) std::rethrow_exception(e);
+}
+
 // first index in [j, n) whose class byte differs from v (n if none)
 int64_t class_run_end(const uint8_t *cl, int64_t j, int64_t n, uint8_t v) {
     const uint64_t pat = 0x0101010101010101ull * v;
@@ -1748,15 +1794,7 @@ int mrsim_sequence(mrsim_ctx *c, int64_t n_seg, const double *dt, const int32_t 
         MRSIM_CUDA(cudaSetDevice(c->device));
         s->ctx = c;
         s->uid = g_uid++;
-        s->n_seg = n_seg;
-        s->dt.assign(dt, dt + n_seg);
-        s->rep.assign(rep, rep + n_seg);
-        s->b1re.assign(b1re, b1re + n_seg);
-        s->b1im.assign(b1im, b1im + n_seg);
-        s->gx.assign(gx, gx + n_seg);
-        s->gy.assign(gy, gy + n_seg);
-        s->gz.assign(gz, gz + n_seg);
-        s->adc.assign(adc, adc + n_seg);
+        copy_segments(s.get(), n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc);
         build_sequence(c, s.get());
     });
     if (rc == MRSIM_OK) *out = s.release();
@@ -1775,15 +1813,7 @@ int mrsim_classify(int64_t n_seg, const double *dt, const int32_t *rep, const fl
         return MRSIM_EINVAL;
     try {
         mrsim_seq s;
-        s.n_seg = n_seg;
-        s.dt.assign(dt, dt + n_seg);
-        s.rep.assign(rep, rep + n_seg);
-        s.b1re.assign(b1re, b1re + n_seg);
-        s.b1im.assign(b1im, b1im + n_seg);
-        s.gx.assign(gx, gx + n_seg);
-        s.gy.assign(gy, gy + n_seg);
-        s.gz.assign(gz, gz + n_seg);
-        s.adc.assign(adc, adc + n_seg);
+        copy_segments(&s, n_seg, dt, rep, b1re, b1im, gx, gy, gz, adc);
         classify_sequence(&s, (flags & MRSIM_CLASSIFY_TWO_AXIS) != 0);
         const int64_t m = (int64_t)s.sub.size();
         *n_subseq = m;
