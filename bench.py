@@ -626,6 +626,35 @@ FLOPS_CELL_RF, FLOPS_CELL_RF_Q, FLOPS_CELL_ADC, FLOPS_CELL_ADC_Q = 24, 30, 4, 8
 INST_CELL_RF, INST_CELL_RF_Q, INST_CELL_ADC, INST_CELL_ADC_Q = 12, 18, 2, 6
 
 
+def profile_prep(configs):
+    """One preparation of the 27.5M FSE through the public API, each call timed
+    on the host clock (synchronised), with the library's kernel times."""
+    import torch
+    from paper_2508_03960_gb300 import mrsim
+    ph, fse = configs.fse_27m()
+    ctx = mrsim.Context(0, torch.cuda.current_stream().cuda_stream)
+    mrsim.mrsim_profile_enable(ctx.h, True)
+    split = {}
+
+    def lap(name, fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        split[name] = round((time.perf_counter() - t) * 1e3, 2)
+        return r
+
+    hp = lap("phantom_upload", lambda: ctx.phantom(ph))
+    hs = lap("sequence", lambda: ctx.sequence(fse))
+    hg = lap("group", lambda: ctx.group(hp, hs))
+    prof = mrsim.mrsim_profile_get(ctx.h)
+    mrsim.mrsim_profile_enable(ctx.h, False)
+    print(json.dumps({"case": "prep_fse_27m", "K": ph.K, "split_ms": split,
+                      "groups": {"gx": mrsim.mrsim_group_info(hg, mrsim.G_X)[0],
+                                 "gz": mrsim.mrsim_group_info(hg, mrsim.G_Z)[0]},
+                      "kernels": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0]}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -647,6 +676,10 @@ def main():
                          "(for ncu captures; prints their CUDA-event times)")
     ap.add_argument("--profile-cluster", action="store_true",
                     help="time the clustering preprocessing kernels (27.5M, 256 clusters)")
+    ap.add_argument("--profile-prep", action="store_true",
+                    help="one preparation of the 27.5M FSE through the API (phantom upload, "
+                         "sequence, groups and layout), for profiler launch lists; prints "
+                         "the host-clock split and the kernels' CUDA-event times")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
 
@@ -661,6 +694,9 @@ def main():
         return
     if a.profile_kernels:
         profile_kernels(a, configs)
+        return
+    if a.profile_prep:
+        profile_prep(configs)
         return
 
     if a.impl == "reference":
