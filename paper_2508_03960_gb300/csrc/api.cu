@@ -239,6 +239,29 @@ static_assert(G_XY == MRSIM_G_XY && G_XZ == MRSIM_G_XZ && G_YZ == MRSIM_G_YZ,
 // Host part of a sequence: subsequence split (Fig. 1), gradient types
 // (Sec. 2.4; two_axis: exactly two nonzero axes give G_XY / G_XZ / G_YZ instead
 // of G_GENERAL), sample offsets and with-RF content ids.  Needs no device.
+// Runs f(0) .. f(n - 1) split over up to `threads` host threads (f must not
+// throw); shares whose thread cannot be started run on the calling thread.
+template <class F>
+void host_parallel(int n, int threads, const F &f) {
+    threads = std::max(1, std::min(threads, n));
+    auto share = [&](int w) {
+        for (int i = (int)((int64_t)n * w / threads); i < (int)((int64_t)n * (w + 1) / threads); ++i)
+            f(i);
+    };
+    std::vector<std::thread> th;
+    std::vector<int> inline_share;
+    for (int w = 1; w < threads; ++w) {
+        try {
+            th.emplace_back(share, w);
+        } catch (...) {
+            inline_share.push_back(w);
+        }
+    }
+    share(0);
+    for (int w : inline_share) share(w);
+    for (auto &t : th) t.join();
+}
+
 // The caller's segment arrays, copied into the sequence.  Long sequences copy
 // their eight arrays on eight host threads (one core copies at a fraction of
 // the host's memory bandwidth); a thread that cannot be started leaves its
@@ -335,20 +358,52 @@ void classify_sequence(mrsim_seq *s, bool two_axis) {
         q.seg_end = j;
         s->sub.push_back(q);
     }
+    // with-RF runs: bucket keys, and (on host threads when there is much to
+    // compare) whether each run repeats the first run of its bucket bit for
+    // bit, the common case of a sequence repeating a few pulses; the ordered
+    // content numbering below then compares only when that fails
+    std::vector<int> rf_sub;
+    for (size_t i = 0; i < s->sub.size(); ++i)
+        if (s->sub[i].type == SUB_RF) rf_sub.push_back((int)i);
+    const int n_rf = (int)rf_sub.size();
+    std::vector<uint64_t> rf_key(n_rf);
+    std::vector<int> rf_cand(n_rf);
+    std::vector<uint8_t> rf_same(n_rf, 0);
+    {
+        std::unordered_map<uint64_t, int> first_of;
+        int64_t cmp_segs = 0;
+        for (int t = 0; t < n_rf; ++t) {
+            const Subseq &q = s->sub[rf_sub[t]];
+            rf_key[t] = run_key(s, q.seg_begin, q.seg_end);
+            rf_cand[t] = first_of.emplace(rf_key[t], rf_sub[t]).first->second;
+            if (rf_cand[t] != rf_sub[t]) cmp_segs += q.seg_end - q.seg_begin;
+        }
+        auto compare = [&](int t) {
+            const Subseq &q = s->sub[rf_sub[t]], &r = s->sub[rf_cand[t]];
+            const int64_t len = q.seg_end - q.seg_begin;
+            rf_same[t] = rf_cand[t] != rf_sub[t] && r.seg_end - r.seg_begin == len &&
+                         same_run(s, r.seg_begin, q.seg_begin, len);
+        };
+        host_parallel(n_rf, cmp_segs >= (1 << 16) ? 8 : 1, compare);
+    }
     int64_t smp = 0;
     std::unordered_map<uint64_t, std::vector<int>> by_hash;
-    for (size_t i = 0; i < s->sub.size(); ++i) {
+    for (size_t i = 0, t = 0; i < s->sub.size(); ++i) {
         Subseq &q = s->sub[i];
         int first = (int)i;  // the subsequence whose segments this one repeats bit for bit
         if (q.type == SUB_RF) {
-            const uint64_t h = run_key(s, q.seg_begin, q.seg_end);
+            const uint64_t h = rf_key[t];
             const int64_t len = q.seg_end - q.seg_begin;
-            int found = -1;
-            for (int cid : by_hash[h]) {
-                const Subseq &r = s->sub[s->content_first[cid]];
-                if (r.seg_end - r.seg_begin == len && same_run(s, r.seg_begin, q.seg_begin, len)) {
-                    found = cid;
-                    break;
+            int found = rf_same[t] ? s->sub[rf_cand[t]].content : -1;
+            ++t;
+            if (found < 0) {
+                for (int cid : by_hash[h]) {
+                    const Subseq &r = s->sub[s->content_first[cid]];
+                    if (r.seg_end - r.seg_begin == len &&
+                        same_run(s, r.seg_begin, q.seg_begin, len)) {
+                        found = cid;
+                        break;
+                    }
                 }
             }
             if (found < 0) {
