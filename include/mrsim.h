@@ -84,6 +84,7 @@ extern "C" {
 /* flags */
 #define MRSIM_PTR_DEVICE 1u /* mrsim_phantom: input arrays are device pointers */
 #define MRSIM_OUT_DEVICE 2u /* mrsim_run: signal and M_final are device pointers */
+#define MRSIM_PHANTOM_ASYNC 4u /* mrsim_phantom: return once the copies and checks are queued */
 
 typedef struct mrsim_ctx mrsim_ctx;
 typedef struct mrsim_phantom_t mrsim_phantom_t;
@@ -114,7 +115,12 @@ const char *mrsim_last_error(const mrsim_ctx *ctx);
  * M0.  b1_scale: relative RF amplitude per isochromat, NULL => 1.  M_init:
  * initial magnetization as [3][K] (Mx block, My block, Mz block), NULL =>
  * thermal equilibrium (0, 0, M0).  flags: MRSIM_PTR_DEVICE if the arrays are
- * device pointers on the context's device.  The data are copied.
+ * device pointers on the context's device; MRSIM_PHANTOM_ASYNC to return as
+ * soon as the copies and the value checks are queued on the context's stream
+ * (host work such as mrsim_sequence then overlaps the transfer): the arrays
+ * must then stay valid and unchanged until the context's next call returns,
+ * and the value checks are reported by the first call that uses the phantom
+ * (MRSIM_EINVAL there, and the phantom stays unusable).  The data are copied.
  * Errors: MRSIM_EINVAL (K <= 0, NULL array, NaN, T <= 0), MRSIM_ENOMEM,
  * MRSIM_ECUDA. */
 int mrsim_phantom(mrsim_ctx *ctx, int64_t K, const float *x, const float *y, const float *z,

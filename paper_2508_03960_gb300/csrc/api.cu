@@ -1582,6 +1582,21 @@ int set_err(mrsim_ctx *c, int code, const std::string &m) {
     return code;
 }
 
+// The value checks of a phantom uploaded with MRSIM_PHANTOM_ASYNC, read at its
+// first use (waiting once for the queued checks); a phantom that failed them
+// stays unusable.
+void phantom_ready(mrsim_ctx *, const mrsim_phantom_t *ph) {
+    if (ph->check == 1) {
+        // the checks ran on the stream of the context that made the phantom
+        int h = 0;
+        MRSIM_CUDA(cudaEventSynchronize(ph->checked));
+        MRSIM_CUDA(cudaMemcpy(&h, ph->bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+        ph->check = h ? 2 : 0;
+    }
+    if (ph->check == 2)
+        fail(MRSIM_EINVAL, "phantom has a non-finite value or T1/T2 <= 0 (checked at first use)");
+}
+
 template <class F>
 int guard(mrsim_ctx *c, F &&f) {
     CtxScope scope(c);
@@ -1704,7 +1719,9 @@ int mrsim_phantom(mrsim_ctx *c, int64_t K, const float *x, const float *y, const
         put(p->T1, T1, K); put(p->T2, T2, K); put(p->dB0, dB0, K); put(p->M0, M0, K);
         if (b1) { put(p->b1, b1, K); p->has_b1 = true; }
         if (M_init) { put(p->M_init, M_init, 3 * K); p->has_M_init = true; }
-        int *err = c->dev_err.as<int>();
+        const bool async = (flags & MRSIM_PHANTOM_ASYNC) != 0;
+        if (async) p->bad = dalloc(sizeof(int));
+        int *err = async ? p->bad.as<int>() : c->dev_err.as<int>();
         MRSIM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
         {
             KScope ks(c, "validate_phantom");
@@ -1714,6 +1731,13 @@ int mrsim_phantom(mrsim_ctx *c, int64_t K, const float *x, const float *y, const
                 p->T2.as<float>(), p->dB0.as<float>(), p->M0.as<float>(),
                 p->has_b1 ? p->b1.as<float>() : nullptr,
                 p->has_M_init ? p->M_init.as<float>() : nullptr, err);
+        }
+        if (async) {
+            MRSIM_CUDA(cudaEventCreateWithFlags(&p->checked, cudaEventDisableTiming));
+            MRSIM_CUDA(cudaEventRecord(p->checked, c->stream));
+            MRSIM_CUDA(cudaGetLastError());
+            p->check = 1;
+            return;
         }
         int h = 0;
         MRSIM_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1729,6 +1753,7 @@ int mrsim_coils(mrsim_ctx *c, mrsim_phantom_t *ph, int n_coils, const float *sen
     if (!c) return MRSIM_EINVAL;
     return guard(c, [&] {
         if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
+        phantom_ready(c, ph);
         if (n_coils < 0 || n_coils > MRSIM_MAX_COILS)
             fail(MRSIM_EINVAL, "n_coils must be in [0, " + std::to_string(MRSIM_MAX_COILS) + "]");
         if (n_coils > 0 && !sens) fail(MRSIM_EINVAL, "NULL sensitivities");
@@ -1770,6 +1795,7 @@ int mrsim_phantom_read(mrsim_ctx *c, const mrsim_phantom_t *ph, float *x, float 
     return guard(c, [&] {
         if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
         if (ph->ctx != c) fail(MRSIM_ESTATE, "phantom of another context");
+        phantom_ready(c, ph);
         MRSIM_CUDA(cudaSetDevice(c->device));
         const size_t b = ph->K * sizeof(float);
         const std::pair<float *, const DBuf *> f[7] = {{x, &ph->x},   {y, &ph->y},     {z, &ph->z},
@@ -1795,6 +1821,7 @@ int mrsim_cluster(mrsim_ctx *c, const mrsim_phantom_t *ph, int n_clusters, const
     int rc = guard(c, [&] {
         if (!ph) fail(MRSIM_EINVAL, "NULL phantom");
         if (ph->ctx != c) fail(MRSIM_ESTATE, "phantom of another context");
+        phantom_ready(c, ph);
         if (n_clusters < 1 || n_clusters > MRSIM_MAX_CLUSTERS)
             fail(MRSIM_EINVAL,
                  "n_clusters must be in [1, " + std::to_string(MRSIM_MAX_CLUSTERS) + "]");
@@ -1911,6 +1938,7 @@ int mrsim_group(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s, mrs
     if (!g) return set_err(c, MRSIM_ENOMEM, "host allocation failed");
     int rc = guard(c, [&] {
         if (!ph || !s) fail(MRSIM_EINVAL, "NULL phantom or sequence");
+        phantom_ready(c, ph);
         MRSIM_CUDA(cudaSetDevice(c->device));
         g->ctx = c;
         g->uid = g_uid++;
@@ -1958,6 +1986,7 @@ int mrsim_run(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     if (!c) return MRSIM_EINVAL;
     return guard(c, [&] {
         if (!ph || !s || !signal) fail(MRSIM_EINVAL, "NULL phantom, sequence or signal");
+        phantom_ready(c, ph);
         if (precision != MRSIM_FP32 && precision != MRSIM_FP64) fail(MRSIM_EINVAL, "bad precision");
         if (mode < MRSIM_PLAIN || mode > MRSIM_SURROGATE) fail(MRSIM_EINVAL, "bad mode");
         const bool grouped = mode == MRSIM_GROUPED || mode == MRSIM_SURROGATE;
@@ -2042,6 +2071,7 @@ int mrsim_run_batch(mrsim_ctx *c, int n_jobs, const mrsim_phantom_t *const *ph,
         if (n_jobs <= 0 || !ph || !s || !g || !signals) fail(MRSIM_EINVAL, "bad batch arguments");
         for (int i = 0; i < n_jobs; ++i) {
             if (!ph[i] || !s[i] || !g[i] || !signals[i]) fail(MRSIM_EINVAL, "NULL batch entry");
+            phantom_ready(c, ph[i]);
             if (g[i]->phantom_uid != ph[i]->uid) fail(MRSIM_ESTATE, "groups of another phantom");
             for (const Subseq &q : s[i]->sub)
                 if ((q.type == SUB_RF || q.type == SUB_ADC) && q.gtype != G_GENERAL &&
@@ -2082,6 +2112,7 @@ int mrsim_autotune(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     if (!c) return MRSIM_EINVAL;
     return guard(c, [&] {
         if (!ph || !s) fail(MRSIM_EINVAL, "NULL phantom or sequence");
+        phantom_ready(c, ph);
         if (reps < 1) reps = 1;
         const int64_t ns = std::max<int64_t>(s->n_samples, 1);
         DBuf sig = dalloc(ns * 2 * sizeof(double));

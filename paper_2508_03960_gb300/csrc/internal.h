@@ -131,6 +131,15 @@ struct mrsim_phantom_t {
     mrsim::DBuf coils;  // float [n_coils][2][K] (re, im planes), phantom order
     double sum_bound = -1.0;  // bound on |any signal or block sum| (< 0: not formed yet)
     uint64_t coil_uid = 0;    // changes whenever mrsim_coils attaches or detaches coils
+    // value checks of an upload queued without waiting (MRSIM_PHANTOM_ASYNC):
+    // the device flag and whether it is still to be read (1), read and clear
+    // (0) or read and set (2)
+    mrsim::DBuf bad;
+    cudaEvent_t checked = nullptr;  // recorded after the checks
+    mutable int check = 0;
+    ~mrsim_phantom_t() {
+        if (checked) cudaEventDestroy(checked);
+    }
 };
 
 namespace mrsim {

@@ -25,7 +25,7 @@ SUB_RF, SUB_ADC, SUB_RELAX = 0, 1, 2
 G_NONE, G_X, G_Y, G_Z, G_GENERAL = 0, 1, 2, 3, 4
 PLAIN, PLAIN_CACHE, GROUPED, SURROGATE = 0, 1, 2, 3
 FP32, FP64 = 0, 1
-PTR_DEVICE, OUT_DEVICE = 1, 2
+PTR_DEVICE, OUT_DEVICE, PHANTOM_ASYNC = 1, 2, 4
 TUNE_FUSED_NI, TUNE_PLAIN_RF_NI, TUNE_ADC_CTAS_PER_SM, TUNE_PRECOMP_LANES = 0, 1, 2, 3
 TUNE_PRECOMP_STEPS = 4
 TUNE_CELL_NI = 5
