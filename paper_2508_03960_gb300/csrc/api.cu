@@ -220,17 +220,41 @@ __global__ void k_finite(int64_t n, const float *v, int *err) {
         if (!isfinite(v[i])) atomicOr(err, 1);
 }
 
+__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) <= FLT_MAX; }
+__device__ __forceinline__ bool finite4(float4 v) {
+    return finite_f(v.x) & finite_f(v.y) & finite_f(v.z) & finite_f(v.w);
+}
+__device__ __forceinline__ bool positive4(float4 v) {
+    return (v.x > 0.0f) & (v.y > 0.0f) & (v.z > 0.0f) & (v.w > 0.0f);
+}
+
+// Value checks of a phantom (every array 16-byte aligned): non-finite values,
+// T1 or T2 not > 0 (NaN fails, +inf passes).  Four isochromats per thread and
+// step with 16-byte loads, then the tail; M_init is checked as one flat array.
 __global__ void k_validate(int64_t K, const float *x, const float *y, const float *z,
                            const float *T1, const float *T2, const float *dB0, const float *M0,
                            const float *b1, const float *Mi, int *err) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        bool bad = !isfinite(x[k]) || !isfinite(y[k]) || !isfinite(z[k]) || !isfinite(dB0[k]) ||
-                   !isfinite(M0[k]) || !(T1[k] > 0.0f) || !(T2[k] > 0.0f) ||
-                   (b1 && !isfinite(b1[k]));
-        if (Mi) bad |= !isfinite(Mi[k]) || !isfinite(Mi[K + k]) || !isfinite(Mi[2 * K + k]);
-        if (bad) atomicOr(err, 1);
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto v4 = [](const float *p, int64_t q) { return __ldg(reinterpret_cast<const float4 *>(p) + q); };
+    bool ok = true;
+    const int64_t K4 = K / 4;
+    for (int64_t q = tid; q < K4; q += stride) {
+        ok &= finite4(v4(x, q)) & finite4(v4(y, q)) & finite4(v4(z, q)) & finite4(v4(dB0, q)) &
+              finite4(v4(M0, q)) & positive4(v4(T1, q)) & positive4(v4(T2, q));
+        if (b1) ok &= finite4(v4(b1, q));
     }
+    for (int64_t k = 4 * K4 + tid; k < K; k += stride) {
+        ok &= finite_f(x[k]) & finite_f(y[k]) & finite_f(z[k]) & finite_f(dB0[k]) &
+              finite_f(M0[k]) & (T1[k] > 0.0f) & (T2[k] > 0.0f);
+        if (b1) ok &= finite_f(b1[k]);
+    }
+    if (Mi) {
+        const int64_t n = 3 * K, n4 = n / 4;
+        for (int64_t q = tid; q < n4; q += stride) ok &= finite4(v4(Mi, q));
+        for (int64_t k = 4 * n4 + tid; k < n; k += stride) ok &= finite_f(Mi[k]);
+    }
+    if (!ok) atomicOr(err, 1);
 }
 
 static_assert(G_XY == MRSIM_G_XY && G_XZ == MRSIM_G_XZ && G_YZ == MRSIM_G_YZ,

@@ -490,29 +490,54 @@ __global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *st
 // scatter leaves members in atomic order): the layout becomes deterministic,
 // and along a cell consecutive positions hold isochromats in phantom order,
 // so neighbouring lanes of the fused kernel read neighbouring table entries.
-// One CTA per cell; the members are distinct, so each one's place in the run
-// is the number of members below it (counted over the run in shared memory).
-// Runs longer than kSortMax keep the scatter order.
+// The members are distinct, so each one's place in the run is the number of
+// members below it, counted over the run in shared memory: one warp per run
+// of at most kWarpSortMax, one CTA per longer run.  Runs longer than kSortMax
+// keep the scatter order.
 constexpr int kSortMax = 4096;
+constexpr int kWarpSortMax = 256;  // runs up to this length: one warp each
+
+__device__ __forceinline__ int rank_below(const int32_t *v, int n4, int x) {
+    const int4 *v4 = reinterpret_cast<const int4 *>(v);
+    int r = 0;
+    for (int j = 0; j < n4 / 4; ++j) {
+        const int4 q = v4[j];
+        r += (int)(q.x < x) + (int)(q.y < x) + (int)(q.z < x) + (int)(q.w < x);
+    }
+    return r;
+}
+
 __global__ void __launch_bounds__(256) k_sort_cells(const int32_t *cstart, const int32_t *ccount,
                                                     int64_t nc, int32_t *perm) {
-    __shared__ __align__(16) int32_t v[kSortMax];
+    __shared__ __align__(16) int32_t v[kSortMax];  // one run, or one run per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // runs of at most kWarpSortMax: a warp each, in its own part of v
+    int32_t *wv = v + warp * kWarpSortMax;
+    for (int64_t c = (int64_t)blockIdx.x * 8 + warp; c < nc; c += (int64_t)gridDim.x * 8) {
+        const int n = ccount[c];
+        if (n < 2 || n > kWarpSortMax) continue;  // uniform in the warp
+        const int n4 = (n + 3) & ~3;
+        const int s = cstart[c];
+        for (int i = lane; i < n4; i += 32) wv[i] = i < n ? perm[s + i] : INT_MAX;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int x = wv[i];
+            perm[s + rank_below(wv, n4, x)] = x;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // longer runs: the whole CTA on one run
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
         const int n = ccount[c];
-        if (n < 2 || n > kSortMax) continue;  // uniform in the CTA
+        if (n <= kWarpSortMax || n > kSortMax) continue;  // uniform in the CTA
         const int n4 = (n + 3) & ~3;
         const int s = cstart[c];
         for (int i = threadIdx.x; i < n4; i += blockDim.x) v[i] = i < n ? perm[s + i] : INT_MAX;
         __syncthreads();
-        const int4 *v4 = reinterpret_cast<const int4 *>(v);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int x = v[i];
-            int r = 0;
-            for (int j = 0; j < n4 / 4; ++j) {
-                const int4 q = v4[j];
-                r += (int)(q.x < x) + (int)(q.y < x) + (int)(q.z < x) + (int)(q.w < x);
-            }
-            perm[s + r] = x;
+            perm[s + rank_below(v, n4, x)] = x;
         }
         __syncthreads();
     }
