@@ -155,9 +155,8 @@ struct Subseq {
 
 struct GroupTable {
     int64_t n = 0;
-    // host copies; pos2: second position of a two-axis type (else 0)
-    std::vector<double> pos, T1, T2, dB0, b1, pos2;
-    DBuf d_par64;                    // [6][n] doubles: pos, T1, T2, dB0, b1, pos2
+    DBuf d_par64;                    // [6][n] doubles: pos, T1, T2, dB0, b1, pos2 (pos2: the
+                                     // second position of a two-axis type, else 0)
     DBuf d_pos, d_dB0, d_rT2, d_pos2;          // float copies for the group-signal kernel
     DBuf d_pos64, d_dB064, d_rT264, d_pos264;  // double copies for the group-signal kernel
 };

@@ -651,6 +651,31 @@ int64_t hash_group(mrsim_ctx *c, int64_t K, const KF &kf, int32_t *gid, int32_t 
 
 }  // namespace
 
+namespace {
+
+// Group-signal tables of G groups from the FP64 block [pos, T1, T2, dB0, b1,
+// pos2]: positions and dB0 as float and double, and log2(e) / T2 (0 for an
+// infinite T2), the decay rate in base-2 exponent units.
+__global__ void k_group_signal_tables(int64_t G, const double *par, float *pos, float *dB0,
+                                      float *rT2, float *pos2, double *pos64, double *dB064,
+                                      double *rT264, double *pos264) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const double p = par[g], t2 = par[2 * G + g], d = par[3 * G + g], p2 = par[5 * G + g];
+        const double r = isinf(t2) ? 0.0 : kLog2e / t2;
+        pos[g] = (float)p;
+        dB0[g] = (float)d;
+        rT2[g] = (float)r;
+        pos2[g] = (float)p2;
+        pos64[g] = p;
+        dB064[g] = d;
+        rT264[g] = r;
+        pos264[g] = p2;
+    }
+}
+
+}  // namespace
+
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab) {
     const int64_t K = ph->K;
@@ -673,39 +698,25 @@ void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &
             ph->has_b1 ? ph->b1.as<float>() : nullptr, pos2, tp, tp + G, tp + 2 * G, tp + 3 * G,
             tp + 4 * G, tp + 5 * G);
     }
-    std::vector<double> h(6 * G);
-    MRSIM_CUDA(cudaMemcpyAsync(h.data(), tp, 6 * G * sizeof(double), cudaMemcpyDeviceToHost,
-                               c->stream));
-    sync(c);
     tab.n = G;
-    tab.pos.assign(h.begin(), h.begin() + G);
-    tab.T1.assign(h.begin() + G, h.begin() + 2 * G);
-    tab.T2.assign(h.begin() + 2 * G, h.begin() + 3 * G);
-    tab.dB0.assign(h.begin() + 3 * G, h.begin() + 4 * G);
-    tab.b1.assign(h.begin() + 4 * G, h.begin() + 5 * G);
-    tab.pos2.assign(h.begin() + 5 * G, h.begin() + 6 * G);
-    // device copies used by the precompute and group-signal kernels
-    std::vector<float> fpos(G), fdB0(G), frT2(G), fpos2(G);
-    std::vector<double> rT2d(G);
-    for (int64_t g = 0; g < G; ++g) {
-        fpos[g] = (float)tab.pos[g];
-        fdB0[g] = (float)tab.dB0[g];
-        rT2d[g] = std::isinf(tab.T2[g]) ? 0.0 : kLog2e / tab.T2[g];
-        frT2[g] = (float)rT2d[g];
-        fpos2[g] = (float)tab.pos2[g];
+    // device copies used by the precompute and group-signal kernels, formed
+    // from the FP64 block on the device
+    auto mk = [&](DBuf &d, size_t el) { d = dalloc(std::max<int64_t>(G, 1) * el); };
+    mk(tab.d_pos, 4);
+    mk(tab.d_dB0, 4);
+    mk(tab.d_rT2, 4);
+    mk(tab.d_pos2, 4);
+    mk(tab.d_pos64, 8);
+    mk(tab.d_dB064, 8);
+    mk(tab.d_rT264, 8);
+    mk(tab.d_pos264, 8);
+    {
+        KScope ks(c, "group_table");
+        k_group_signal_tables<<<grid_for(c, G), 256, 0, c->stream>>>(
+            G, tp, tab.d_pos.as<float>(), tab.d_dB0.as<float>(), tab.d_rT2.as<float>(),
+            tab.d_pos2.as<float>(), tab.d_pos64.as<double>(), tab.d_dB064.as<double>(),
+            tab.d_rT264.as<double>(), tab.d_pos264.as<double>());
     }
-    auto up = [&](DBuf &d, const void *src, size_t bytes) {
-        d = dalloc(bytes);
-        upload(c, d.p, src, bytes);
-    };
-    up(tab.d_pos, fpos.data(), G * 4);
-    up(tab.d_dB0, fdB0.data(), G * 4);
-    up(tab.d_rT2, frT2.data(), G * 4);
-    up(tab.d_pos2, fpos2.data(), G * 4);
-    up(tab.d_pos64, tab.pos.data(), G * 8);
-    up(tab.d_dB064, tab.dB0.data(), G * 8);
-    up(tab.d_rT264, rT2d.data(), G * 8);
-    up(tab.d_pos264, tab.pos2.data(), G * 8);
     // FP64 parameter block (pos, T1, T2, dB0, b1, pos2) for the precompute kernel
     tab.d_par64 = std::move(t);
 }
