@@ -235,8 +235,10 @@ def surrogate_workload(ctx, mrsim, torch):
     _, seq = configs.surrogate_fse()
     hs = ctx.sequence(seq)
     t0 = time.perf_counter()
+    # batch 4096: twice the optimizer steps of 8192 over the same 300 epochs
+    # (two trainings each: 51-75 % of the gate's cells served, against 38-58 %)
     sur = mrsim.mrsim_surrogate_train(ctx.h, hs, SUR_LO, SUR_HI, n_train=1 << 22, epochs=300,
-                                      batch=8192, lr=1e-2, seed=1005, bound=1e-3)
+                                      batch=4096, lr=1e-2, seed=1005, bound=1e-3)
     train_s = time.perf_counter() - t0
     st = mrsim.mrsim_surrogate_stats(sur)
     ph = continuous_phantom(512, 512, 105, 8, seed=1005)
@@ -280,7 +282,8 @@ def surrogate_workload(ctx, mrsim, torch):
     # against its exact FP64 counterpart
     run_err, run_served = mrsim.mrsim_surrogate_check(ctx.h, sur, hs, hg)
     out = {"K": ph.K, "groups_z": mrsim.mrsim_group_info(hg, mrsim.G_Z)[0],
-           "train": {"samples_per_pulse": 1 << 22, "epochs": 300, "seconds": round(train_s, 2),
+           "train": {"samples_per_pulse": 1 << 22, "epochs": 300, "batch": 4096,
+                     "seconds": round(train_s, 2),
                      "final_mse_per_entry": st["train_loss"],
                      "validation_max_error": st["val_max_err"],
                      "cells_served": st["cells_served"],
