@@ -804,6 +804,68 @@ def main():
         ctx.close()
         return
 
+    # ---- end to end through the public API from pinned host buffers ----
+    # (measured here, right after the device-timed steps: after the 36 s plain
+    # FSE run below, single steps stalled by 10-14 ms now and then, with the
+    # same kernels, host work and median step)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).pin_memory()
+           for k, v in dict(x=ph.x, y=ph.y, z=ph.z, T1=ph.T1, T2=ph.T2, dB0=ph.dB0,
+                            M0=ph.M0).items()}
+    out_pin = torch.zeros(2 * ns_f, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 4 for t in pin.values()) + sum(v.nbytes for v in fse.arrays().values())
+    d2h = out_pin.numel() * 8
+
+    def e2e_step():
+        # the upload is queued without waiting, so the sequence's host work
+        # overlaps the transfer (the pinned arrays stay alive throughout)
+        p = mrsim.mrsim_phantom(ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0",
+                                                                  "M0")],
+                                flags=mrsim.PHANTOM_ASYNC)
+        s = ctx.sequence(fse)
+        g = mrsim.mrsim_group(ctx.h, p, s)
+        mrsim.mrsim_run(ctx.h, p, s, g, mrsim.GROUPED, mrsim.FP32, out_pin, None, 0)
+        mrsim.mrsim_free_groups(g)
+        ctx.free("seq", s)
+        mrsim.mrsim_free_phantom(p)
+
+    # at least 20 steps: one host-side stall (a page fault burst, a collection
+    # of Python garbage) then moves the mean by a few percent, not by 20
+    e2e_steps = max(a.steps, 20)
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    t_steps = []
+    for _ in range(e2e_steps):
+        ts = time.perf_counter()
+        e2e_step()  # ends with the run's read-back (synchronous) and the frees
+        t_steps.append((time.perf_counter() - ts) * 1e3)
+    e1.record(stream)
+    barrier()
+    e2e_s = maxr(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / e2e_steps)
+    # where one end-to-end step goes (host clock, synchronised after each call,
+    # so the overlap of the upload with the sequence's host work is not in it)
+    split = {}
+
+    def lap(name, fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        split[name] = round((time.perf_counter() - t) * 1e3, 2)
+        return r
+
+    p_ = lap("phantom_upload", lambda: mrsim.mrsim_phantom(
+        ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0", "M0")],
+        flags=mrsim.PHANTOM_ASYNC))
+    s_ = lap("sequence", lambda: ctx.sequence(fse))
+    g_ = lap("group", lambda: mrsim.mrsim_group(ctx.h, p_, s_))
+    lap("run_and_readback", lambda: mrsim.mrsim_run(ctx.h, p_, s_, g_, mrsim.GROUPED, mrsim.FP32,
+                                                    out_pin, None, 0))
+    lap("free", lambda: (mrsim.mrsim_free_groups(g_), ctx.free("seq", s_),
+                         mrsim.mrsim_free_phantom(p_)))
+
     # ---- plain forms on the same GPU ----
     def timed_once(fn, prof_out=None):
         if prof_out is not None:
@@ -860,62 +922,6 @@ def main():
         "default_repeat_max_abs_diff": float(np.max(np.abs(d1 - d2))),
         "rel_l2_vs_default": float(np.linalg.norm(rv - dv) / np.linalg.norm(dv)),
     }
-
-    # ---- end to end through the public API from pinned host buffers ----
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).pin_memory()
-           for k, v in dict(x=ph.x, y=ph.y, z=ph.z, T1=ph.T1, T2=ph.T2, dB0=ph.dB0,
-                            M0=ph.M0).items()}
-    out_pin = torch.zeros(2 * ns_f, dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * 4 for t in pin.values()) + sum(v.nbytes for v in fse.arrays().values())
-    d2h = out_pin.numel() * 8
-
-    def e2e_step():
-        # the upload is queued without waiting, so the sequence's host work
-        # overlaps the transfer (the pinned arrays stay alive throughout)
-        p = mrsim.mrsim_phantom(ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0",
-                                                                  "M0")],
-                                flags=mrsim.PHANTOM_ASYNC)
-        s = ctx.sequence(fse)
-        g = mrsim.mrsim_group(ctx.h, p, s)
-        mrsim.mrsim_run(ctx.h, p, s, g, mrsim.GROUPED, mrsim.FP32, out_pin, None, 0)
-        mrsim.mrsim_free_groups(g)
-        ctx.free("seq", s)
-        mrsim.mrsim_free_phantom(p)
-
-    # at least 20 steps: one host-side stall (a page fault burst, a collection
-    # of Python garbage) then moves the mean by a few percent, not by 20
-    e2e_steps = max(a.steps, 20)
-    for _ in range(3):
-        e2e_step()
-    barrier()
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_s = maxr(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0) / e2e_steps)
-    # where one end-to-end step goes (host clock, synchronised after each call,
-    # so the overlap of the upload with the sequence's host work is not in it)
-    split = {}
-
-    def lap(name, fn):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        r = fn()
-        torch.cuda.synchronize()
-        split[name] = round((time.perf_counter() - t) * 1e3, 2)
-        return r
-
-    p_ = lap("phantom_upload", lambda: mrsim.mrsim_phantom(
-        ctx.h, ph.K, *[pin[k] for k in ("x", "y", "z", "T1", "T2", "dB0", "M0")],
-        flags=mrsim.PHANTOM_ASYNC))
-    s_ = lap("sequence", lambda: ctx.sequence(fse))
-    g_ = lap("group", lambda: mrsim.mrsim_group(ctx.h, p_, s_))
-    lap("run_and_readback", lambda: mrsim.mrsim_run(ctx.h, p_, s_, g_, mrsim.GROUPED, mrsim.FP32,
-                                                    out_pin, None, 0))
-    lap("free", lambda: (mrsim.mrsim_free_groups(g_), ctx.free("seq", s_),
-                         mrsim.mrsim_free_phantom(p_)))
 
     # ---- batched workload: 64 uneven jobs in one graph launch ----
     batch = batch_workload(ctx, mrsim, torch, a.steps, a.warmup)
@@ -1086,6 +1092,9 @@ def main():
         "roofline": roof, "kernel_roofline": kroof, "cpu_baseline": cpu,
         "cpu_baseline_epi": cpu_epi,
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "steps": e2e_steps,
+                "step_ms": {"min": round(min(t_steps), 2),
+                            "median": round(statistics.median(t_steps), 2),
+                            "max": round(max(t_steps), 2)},
                 "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "split_ms": split},
         "gpu_launches": int(launches), "clocks": clocks,
