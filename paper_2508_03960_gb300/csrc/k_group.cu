@@ -490,10 +490,10 @@ __global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *st
 // scatter leaves members in atomic order): the layout becomes deterministic,
 // and along a cell consecutive positions hold isochromats in phantom order,
 // so neighbouring lanes of the fused kernel read neighbouring table entries.
-// The members are distinct, so each one's place in the run is the number of
-// members below it, counted over the run in shared memory: one warp per run
-// of at most kWarpSortMax, one CTA per longer run.  Runs longer than kSortMax
-// keep the scatter order.
+// Runs of at most kWarpSortMax members: one warp each, a bitonic network in
+// registers; longer runs: one CTA each, every member placed by the number of
+// members below it (they are distinct), counted over the run in shared
+// memory.  Runs longer than kSortMax keep the scatter order.
 constexpr int kSortMax = 4096;
 constexpr int kWarpSortMax = 256;  // runs up to this length: one warp each
 
@@ -507,27 +507,78 @@ __device__ __forceinline__ int rank_below(const int32_t *v, int n4, int x) {
     return r;
 }
 
+// Bitonic sorting network over 32 J values held by a warp, element i = 32 j +
+// lane in v[j]: exchanges at distance d >= 32 stay within a lane, shorter
+// ones go through shuffles.  Ascending order.
+template <int J>
+__device__ __forceinline__ void warp_bitonic(int32_t (&v)[J], int lane) {
+    constexpr int kLog = J == 1 ? 5 : J == 2 ? 6 : J == 4 ? 7 : 8;
+#pragma unroll
+    for (int lk = 1; lk <= kLog; ++lk) {
+        const int k = 1 << lk;
+#pragma unroll
+        for (int ld = lk - 1; ld >= 0; --ld) {
+            const int d = 1 << ld;
+            if (d >= 32) {
+                const int dj = d >> 5;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    if ((j & dj) == 0) {
+                        const bool up = ((j * 32 + lane) & k) == 0;
+                        const int32_t a = v[j], b = v[j | dj];
+                        if ((a > b) == up) {
+                            v[j] = b;
+                            v[j | dj] = a;
+                        }
+                    }
+                }
+            } else {
+                const bool lower = (lane & d) == 0;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int32_t p = __shfl_xor_sync(0xffffffffu, v[j], d);
+                    const bool up = ((j * 32 + lane) & k) == 0;
+                    v[j] = (lower == up) ? min(v[j], p) : max(v[j], p);
+                }
+            }
+        }
+    }
+}
+
+// one run of n <= 32 J members, sorted by the warp in registers
+template <int J>
+__device__ __forceinline__ void warp_sort_run(int32_t *run, int n, int lane) {
+    int32_t v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int i = j * 32 + lane;
+        v[j] = i < n ? run[i] : INT_MAX;
+    }
+    warp_bitonic<J>(v, lane);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int i = j * 32 + lane;
+        if (i < n) run[i] = v[j];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_sort_cells(const int32_t *cstart, const int32_t *ccount,
                                                     int64_t nc, int32_t *perm) {
-    __shared__ __align__(16) int32_t v[kSortMax];  // one run, or one run per warp
+    __shared__ __align__(16) int32_t v[kSortMax];  // one longer run
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // runs of at most kWarpSortMax: a warp each, in its own part of v
-    int32_t *wv = v + warp * kWarpSortMax;
+    // runs of at most kWarpSortMax: a warp each, in registers
     for (int64_t c = (int64_t)blockIdx.x * 8 + warp; c < nc; c += (int64_t)gridDim.x * 8) {
         const int n = ccount[c];
         if (n < 2 || n > kWarpSortMax) continue;  // uniform in the warp
-        const int n4 = (n + 3) & ~3;
-        const int s = cstart[c];
-        for (int i = lane; i < n4; i += 32) wv[i] = i < n ? perm[s + i] : INT_MAX;
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const int x = wv[i];
-            perm[s + rank_below(wv, n4, x)] = x;
-        }
-        __syncwarp();
+        int32_t *run = perm + cstart[c];
+        if (n <= 32) warp_sort_run<1>(run, n, lane);
+        else if (n <= 64) warp_sort_run<2>(run, n, lane);
+        else if (n <= 128) warp_sort_run<4>(run, n, lane);
+        else warp_sort_run<8>(run, n, lane);
     }
     __syncthreads();
-    // longer runs: the whole CTA on one run
+    // longer runs: the whole CTA on one run, each member placed by the number
+    // of members below it
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
         const int n = ccount[c];
         if (n <= kWarpSortMax || n > kSortMax) continue;  // uniform in the CTA
