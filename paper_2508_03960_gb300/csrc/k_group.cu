@@ -495,7 +495,7 @@ __global__ void k_cell_threads(int64_t nc, const int64_t *off, const int32_t *st
 // members below it (they are distinct), counted over the run in shared
 // memory.  Runs longer than kSortMax keep the scatter order.
 constexpr int kSortMax = 4096;
-constexpr int kWarpSortMax = 256;  // runs up to this length: one warp each
+constexpr int kWarpSortMax = 1024;  // runs up to this length: one warp each
 
 __device__ __forceinline__ int rank_below(const int32_t *v, int n4, int x) {
     const int4 *v4 = reinterpret_cast<const int4 *>(v);
@@ -512,7 +512,8 @@ __device__ __forceinline__ int rank_below(const int32_t *v, int n4, int x) {
 // ones go through shuffles.  Ascending order.
 template <int J>
 __device__ __forceinline__ void warp_bitonic(int32_t (&v)[J], int lane) {
-    constexpr int kLog = J == 1 ? 5 : J == 2 ? 6 : J == 4 ? 7 : 8;
+    constexpr int kLog = J == 1 ? 5 : J == 2 ? 6 : J == 4 ? 7 : J == 8 ? 8 : J == 16 ? 9 : 10;
+    static_assert(J == 1 || J == 2 || J == 4 || J == 8 || J == 16 || J == 32, "J");
 #pragma unroll
     for (int lk = 1; lk <= kLog; ++lk) {
         const int k = 1 << lk;
@@ -574,7 +575,9 @@ __global__ void __launch_bounds__(256) k_sort_cells(const int32_t *cstart, const
         if (n <= 32) warp_sort_run<1>(run, n, lane);
         else if (n <= 64) warp_sort_run<2>(run, n, lane);
         else if (n <= 128) warp_sort_run<4>(run, n, lane);
-        else warp_sort_run<8>(run, n, lane);
+        else if (n <= 256) warp_sort_run<8>(run, n, lane);
+        else if (n <= 512) warp_sort_run<16>(run, n, lane);
+        else warp_sort_run<32>(run, n, lane);
     }
     __syncthreads();
     // longer runs: the whole CTA on one run, each member placed by the number

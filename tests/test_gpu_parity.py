@@ -173,6 +173,19 @@ def test_layout_dense_and_hashed_cells(mrsim, ctx, n_db0):
     ctx.free("ph", hp)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_long_cells_sorted_layout(mrsim, ctx, precision):
+    """A tall phantom (8 x 1000 x 2) whose layout cells hold up to 1,000
+    isochromats, so every branch of the cell sort runs: warp networks of 32
+    to 1,024 members.  A member lost or doubled by the sort would show in the
+    final magnetization, which comes back through the layout permutation."""
+    ph = configs.small_phantom(8, 1000, 2)
+    seq = fse_2d(n_ro=16, n_pe=16, etl=4, n_shots=1)
+    ref, Mref = oracle.simulate(ph, seq)
+    sig, M = run_both(mrsim, ctx, ph, seq, mrsim.GROUPED, precision)
+    check(sig, M, ref, Mref, precision)
+
+
 def test_group_ids_with_b1_and_negative_zero(mrsim, ctx):
     ph = configs.small_phantom(16, 16, 2)
     rng = np.random.default_rng(3)
