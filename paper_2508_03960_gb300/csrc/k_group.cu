@@ -605,17 +605,35 @@ struct GatherSet {
     int n;
 };
 
-__global__ void k_gather_set(int64_t K, const int32_t *perm, GatherSet g) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = perm[i];
-        uint32_t v[kGatherMax];  // every load issued before the first store
+// A CTA takes kGatherPer x 256 consecutive layout positions; each thread keeps
+// its positions' phantom indices in registers and walks the arrays one at a
+// time.  Consecutive phantom indices fall in neighbouring cells of the
+// layout, so a sector one load brings into L1 serves the tile's other cells
+// before it is evicted, instead of coming from L2 once per member.
+constexpr int kGatherPer = 8;
+constexpr int kGatherTile = 256 * kGatherPer;
+
+__global__ void __launch_bounds__(256) k_gather_set(int64_t K, const int32_t *perm, GatherSet g) {
+    for (int64_t base = blockIdx.x * (int64_t)kGatherTile; base < K;
+         base += (int64_t)gridDim.x * kGatherTile) {
+        int32_t p[kGatherPer];
 #pragma unroll
-        for (int a = 0; a < kGatherMax; ++a)
-            if (a < g.n) v[a] = __ldg(g.in[a] + p);
+        for (int r = 0; r < kGatherPer; ++r) {
+            const int64_t i = base + r * 256 + threadIdx.x;
+            p[r] = i < K ? perm[i] : 0;
+        }
+        for (int a = 0; a < g.n; ++a) {
+            const uint32_t *in = g.in[a];
+            uint32_t *out = g.out[a];
+            uint32_t v[kGatherPer];  // every load issued before the first store
 #pragma unroll
-        for (int a = 0; a < kGatherMax; ++a)
-            if (a < g.n) g.out[a][i] = v[a];
+            for (int r = 0; r < kGatherPer; ++r) v[r] = __ldg(in + p[r]);
+#pragma unroll
+            for (int r = 0; r < kGatherPer; ++r) {
+                const int64_t i = base + r * 256 + threadIdx.x;
+                if (i < K) out[i] = v[r];
+            }
+        }
     }
 }
 
@@ -965,7 +983,7 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
     static_assert(7 + 1 + kNTypes <= kGatherMax, "gather set too small");
     {
         KScope ks(c, "layout_gather");
-        k_gather_set<<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, gs);
+        k_gather_set<<<grid_for(c, K, kGatherTile), 256, 0, c->stream>>>(K, perm, gs);
     }
     g->has_M_init = ph->has_M_init;
     if (ph->has_M_init) {
@@ -977,7 +995,7 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
         }
         gm.n = 3;
         KScope ks(c, "layout_gather");
-        k_gather_set<<<grid_for(c, K), 256, 0, c->stream>>>(K, perm, gm);
+        k_gather_set<<<grid_for(c, K, kGatherTile), 256, 0, c->stream>>>(K, perm, gm);
     }
     sync(c);
 }
