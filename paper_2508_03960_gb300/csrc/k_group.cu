@@ -113,6 +113,44 @@ constexpr int kHashPer = 4;
 constexpr int kHashTile = kHashThreads * kHashPer;
 constexpr int kHashLocal = 2 * kHashTile;  // never more than half full
 
+// Global slot of the key of element k (bounded linear probing): claims an
+// empty slot (counting the distinct keys; past key_limit the table is
+// outgrown and the pass is redone) or finds the slot holding the same key;
+// the slot's minimum index then covers k.  0 after an error.
+template <class KF>
+__device__ int32_t global_probe(const KF &kf, int64_t k, int32_t *owner, int32_t *minidx,
+                                uint32_t mask, int key_limit, int *err, int *n_keys) {
+    uint32_t w[KF::W];
+    kf.words(k, w);
+    uint32_t s = (uint32_t)key_hash(w, KF::W) & mask;
+    for (uint32_t probes = 0;; ++probes) {
+        if (probes > mask) {
+            atomicOr(err, kErrTableFull);
+            return 0;
+        }
+        int32_t o = __ldcg(&owner[s]);
+        if (o < 0) {
+            const int32_t prev = atomicCAS(&owner[s], -1, (int32_t)k);
+            if (prev < 0) {
+                if (atomicAdd(n_keys, 1) >= key_limit) atomicOr(err, kErrGrow);
+                atomicMin(&minidx[s], (int32_t)k);
+                return (int32_t)s;
+            }
+            o = prev;
+        }
+        uint32_t w2[KF::W];
+        kf.words(o, w2);
+        bool eq = true;
+#pragma unroll
+        for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
+        if (eq) {
+            if ((int32_t)k < __ldcg(&minidx[s])) atomicMin(&minidx[s], (int32_t)k);
+            return (int32_t)s;
+        }
+        s = (s + 1) & mask;
+    }
+}
+
 template <class KF>
 __global__ void __launch_bounds__(kHashThreads)
     k_hash_insert(int64_t K, KF kf, int32_t *owner, int32_t *minidx, int32_t *slot_of,
@@ -185,38 +223,7 @@ __global__ void __launch_bounds__(kHashThreads)
                 l_slot[e] = found;
                 continue;
             }
-            const int64_t k = base + l_min[e];
-            uint32_t w[KF::W];
-            kf.words(k, w);
-            uint32_t s = (uint32_t)key_hash(w, KF::W) & mask;
-            for (uint32_t probes = 0;; ++probes) {
-                if (probes > mask) {
-                    atomicOr(err, kErrTableFull);
-                    break;
-                }
-                int32_t o = __ldcg(&owner[s]);
-                if (o < 0) {
-                    int32_t prev = atomicCAS(&owner[s], -1, (int32_t)k);
-                    if (prev < 0) {
-                        if (atomicAdd(n_keys, 1) >= key_limit) atomicOr(err, kErrGrow);
-                        atomicMin(&minidx[s], (int32_t)k);
-                        found = (int32_t)s;
-                        break;
-                    }
-                    o = prev;
-                }
-                uint32_t w2[KF::W];
-                kf.words(o, w2);
-                bool eq = true;
-#pragma unroll
-                for (int i = 0; i < KF::W; ++i) eq &= (w2[i] == w[i]);
-                if (eq) {
-                    if ((int32_t)k < __ldcg(&minidx[s])) atomicMin(&minidx[s], (int32_t)k);
-                    found = (int32_t)s;
-                    break;
-                }
-                s = (s + 1) & mask;
-            }
+            found = global_probe(kf, base + l_min[e], owner, minidx, mask, key_limit, err, n_keys);
             l_slot[e] = found;
         }
         __syncthreads();
@@ -233,6 +240,108 @@ __global__ void __launch_bounds__(kHashThreads)
             l_min[e] = INT_MAX;
         }
         if (threadIdx.x == 0) l_n = 0;
+        __syncthreads();
+    }
+}
+
+// One-word keys (the distinct positions of an axis: hundreds to thousands):
+// a CTA keeps a cache key -> global slot in shared memory across all its
+// tiles, so after its first tiles a lookup is a shared-memory probe.  Keys new
+// to the cache are probed in the global table once per tile, with the tile's
+// smallest index of the key (earlier tiles of a CTA hold smaller indices, so a
+// key already cached needs no minimum update).  The cache is cleared when more
+// than a quarter full at the end of a tile (a tile adds at most kHashTile).
+constexpr int kAxisCache = 2048;
+constexpr uint32_t kEmptyWord = 0xffffffffu;  // a NaN pattern: never a valid key
+
+template <class KF>
+__global__ void __launch_bounds__(kHashThreads)
+    k_hash_insert_1w(int64_t K, KF kf, int32_t *owner, int32_t *minidx, int32_t *slot_of,
+                     uint32_t mask, int key_limit, int *err, int *n_keys) {
+    static_assert(KF::W == 1, "one-word keys");
+    static_assert(kAxisCache / 4 + kHashTile <= kAxisCache, "cache room for a tile");
+    __shared__ uint32_t c_key[kAxisCache];
+    __shared__ int32_t c_slot[kAxisCache];  // global slot; -1 while new in this tile
+    __shared__ int32_t c_min[kAxisCache];   // smallest tile index of a key new in this tile
+    __shared__ int32_t l_used[kHashTile];   // entries new in this tile
+    __shared__ int l_n, c_fill;
+    for (int i = threadIdx.x; i < kAxisCache; i += kHashThreads) {
+        c_key[i] = kEmptyWord;
+        c_slot[i] = -1;
+        c_min[i] = INT_MAX;
+    }
+    if (threadIdx.x == 0) {
+        l_n = 0;
+        c_fill = 0;
+    }
+    __syncthreads();
+    for (int64_t base = blockIdx.x * (int64_t)kHashTile; base < K;
+         base += (int64_t)gridDim.x * kHashTile) {
+        int ent[kHashPer];
+#pragma unroll
+        for (int r = 0; r < kHashPer; ++r) {
+            const int t = r * kHashThreads + threadIdx.x;
+            const int64_t k = base + t;
+            ent[r] = -1;
+            if (k >= K) continue;
+            uint32_t w[1];
+            if (!kf.words(k, w)) {
+                atomicOr(err, kErrNaN);
+                continue;
+            }
+            uint32_t e = (w[0] * 0x9e3779b1u) >> 21;  // top 11 bits: [0, kAxisCache)
+            for (int probes = 0; probes < kAxisCache; ++probes) {
+                uint32_t kk = *(volatile uint32_t *)&c_key[e];
+                if (kk == kEmptyWord) {
+                    kk = atomicCAS(&c_key[e], kEmptyWord, w[0]);
+                    if (kk == kEmptyWord) {
+                        l_used[atomicAdd(&l_n, 1)] = (int32_t)e;
+                        ent[r] = (int)e;
+                        break;
+                    }
+                }
+                if (kk == w[0]) {
+                    ent[r] = (int)e;
+                    break;
+                }
+                e = (e + 1) & (kAxisCache - 1);
+            }
+            if (ent[r] < 0) {  // unreachable: the cache keeps room for a tile
+                atomicOr(err, kErrTableFull);
+                continue;
+            }
+            if (*(volatile int32_t *)&c_slot[ent[r]] < 0 && t < *(volatile int32_t *)&c_min[ent[r]])
+                atomicMin(&c_min[ent[r]], t);
+        }
+        __syncthreads();
+        const int nl = l_n;
+        for (int u = threadIdx.x; u < nl; u += kHashThreads) {
+            const int e = l_used[u];
+            c_slot[e] = (*(volatile int *)err & kErrGrow)
+                            ? 0
+                            : global_probe(kf, base + c_min[e], owner, minidx, mask, key_limit,
+                                           err, n_keys);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kHashPer; ++r) {
+            const int64_t k = base + r * kHashThreads + threadIdx.x;
+            if (k < K) slot_of[k] = ent[r] >= 0 ? c_slot[ent[r]] : 0;
+        }
+        __syncthreads();
+        const bool clear = c_fill + nl > kAxisCache / 4;  // uniform: read before the update
+        __syncthreads();
+        if (clear) {
+            for (int i = threadIdx.x; i < kAxisCache; i += kHashThreads) {
+                c_key[i] = kEmptyWord;
+                c_slot[i] = -1;
+                c_min[i] = INT_MAX;
+            }
+        }
+        if (threadIdx.x == 0) {
+            c_fill = clear ? 0 : c_fill + nl;
+            l_n = 0;
+        }
         __syncthreads();
     }
 }
@@ -681,8 +790,12 @@ int64_t hash_group(mrsim_ctx *c, int64_t K, const KF &kf, int32_t *gid, int32_t 
         }
         {
             KScope ks(c, "group_hash_insert");
-            k_hash_insert<<<grid_for(c, K, kHashTile), kHashThreads, 0, c->stream>>>(
-                K, kf, owner, minidx, slot_of, (uint32_t)(C - 1), (int)(C / 2), err, err + 1);
+            if constexpr (KF::W == 1)
+                k_hash_insert_1w<<<grid_for(c, K, kHashTile), kHashThreads, 0, c->stream>>>(
+                    K, kf, owner, minidx, slot_of, (uint32_t)(C - 1), (int)(C / 2), err, err + 1);
+            else
+                k_hash_insert<<<grid_for(c, K, kHashTile), kHashThreads, 0, c->stream>>>(
+                    K, kf, owner, minidx, slot_of, (uint32_t)(C - 1), (int)(C / 2), err, err + 1);
         }
         {
             KScope ks(c, "group_rep_flag");
