@@ -200,7 +200,9 @@ int mrsim_seq_info(const mrsim_seq *seq, int64_t *n_subseq, uint8_t *type, uint8
  * +0 compare equal; b1 joins the key when the phantom has one.  Groups are
  * numbered by first occurrence in isochromat index order.  Also lays the
  * isochromats out in device memory sorted by (with-ADC group, with-RF group).
- * Runs on the device; done once per (phantom, sequence shape).
+ * Runs on the device; done once per (phantom, sequence shape).  Layout-order
+ * copies that only some run forms read are filled by the first run that
+ * needs them, so a group set must not be used by two threads at once.
  * Errors: MRSIM_EINVAL, MRSIM_ENOMEM, MRSIM_ECUDA. */
 int mrsim_group(mrsim_ctx *ctx, const mrsim_phantom_t *ph, const mrsim_seq *seq,
                 mrsim_groups **out);

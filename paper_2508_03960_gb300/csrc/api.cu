@@ -999,6 +999,15 @@ void run_grouped(mrsim_ctx *c, const mrsim_phantom_t *ph, const mrsim_seq *s,
     using A = typename AdvOf<R>::T;
     GPlan<R> P;
     plan_grouped<R>(c, s, g, P, true);
+    // the FP32 cell form alone reads M0 and the axis index of the layout-order
+    // arrays; everything else (per-isochromat form, fallbacks, initial
+    // states, receive coils, windows and pulses of other group types) needs
+    // the rest of them
+    bool cell_only = sizeof(R) == 4 && P.cell && !g->has_M_init && ph->n_coils == 0 &&
+                     !g->built[G_NONE];
+    for (const auto &sp : P.spans) cell_only &= sp.fallback < 0;
+    for (const CellEv &e : P.cev) cell_only &= e.kind != CE_ADC_OTHER;
+    if (!cell_only) ensure_layout_arrays(c, g, ph);
     R *T_tab = (R *)scratch(c, 6, std::max<int64_t>(P.rows, 1) * 12 * sizeof(R));
     for (auto &t : P.tabs) {
         if constexpr (sizeof(R) == 4) {
@@ -1220,6 +1229,8 @@ std::map<const mrsim_ctx *, std::unique_ptr<BatchCache>> &batch_caches() {
 void run_batch(mrsim_ctx *c, int n, const mrsim_phantom_t *const *ph, const mrsim_seq *const *s,
                const mrsim_groups *const *g, double *const *signals) {
     using R = float;
+    // the batched kernels read every layout-order array of a job
+    for (int i = 0; i < n; ++i) ensure_layout_arrays(c, g[i], ph[i]);
     std::vector<uint64_t> key;
     for (int i = 0; i < n; ++i) {
         key.push_back(ph[i]->uid);

@@ -198,6 +198,9 @@ struct mrsim_groups {
     mrsim::DBuf gid_sorted[mrsim::kNTypes];  // int32 [K], layout order
     mrsim::GroupTable tab[mrsim::kNTypes];
     int primary = -1, secondary = -1;  // layout keys (gradient types)
+    // the layout-order copies of the primary axis position, T1, T2, dB0, b1 and
+    // the group ids are allocated but still to be gathered (ensure_layout_arrays)
+    mutable bool rest_pending = false;
     int64_t n_cells = 0;
     // distinct positions of the two axes other than the primary one, numbered
     // by first occurrence in layout order; ax_idx packs both indices per
@@ -315,6 +318,10 @@ bool sur_table(mrsim_ctx *c, const mrsim_seq *s, const mrsim_groups *g, int cid,
 void build_group_type(mrsim_ctx *c, const mrsim_phantom_t *ph, int gtype, DBuf &gid,
                       int64_t &n_groups, GroupTable &tab);
 void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g);
+// Gathers the layout-order arrays the group build left for later (the
+// per-isochromat form, fallbacks, initial states and gid-reading events need
+// them); ph is the phantom the groups were built from.  Queued on c's stream.
+void ensure_layout_arrays(mrsim_ctx *c, const mrsim_groups *g, const mrsim_phantom_t *ph);
 // Distinct keys (x[k], x[K + k], x[2K + k], bits of T1[k], bits of T2[k]) of K
 // elements: id[k] in [0, U) numbered by first occurrence, table [3][U] of the
 // integer words, tf [2][U] of T1 and T2, count [U] of occurrences.  Returns U.

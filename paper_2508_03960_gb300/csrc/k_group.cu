@@ -1074,7 +1074,11 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
                                                   g->perm.as<int32_t>());
     }
     const int32_t *perm = g->perm.as<int32_t>();
-    // every per-isochromat array in layout order, in one gather pass
+    // the per-isochromat arrays in layout order.  Gathered now: M0 and the
+    // positions the axis index is built from; the rest (the primary axis
+    // position, T1, T2, dB0, b1 and the layout-order group ids, which only the
+    // per-isochromat form and the fallbacks read) is allocated now and gathered
+    // by the first run that needs it (ensure_layout_arrays)
     GatherSet gs{};
     auto add = [&](DBuf &dst, const void *src) {
         dst = dalloc(K * sizeof(uint32_t));
@@ -1082,22 +1086,25 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
         gs.out[gs.n] = dst.as<uint32_t>();
         ++gs.n;
     };
-    add(g->x, ph->x.p);
-    add(g->y, ph->y.p);
-    add(g->z, ph->z.p);
-    add(g->T1, ph->T1.p);
-    add(g->T2, ph->T2.p);
-    add(g->dB0, ph->dB0.p);
+    const int pa = (g->primary >= G_X && g->primary <= G_Z) ? g->primary - 1 : -1;
+    DBuf *pos_dst[3] = {&g->x, &g->y, &g->z};
+    const DBuf *pos_src[3] = {&ph->x, &ph->y, &ph->z};
+    for (int a = 0; a < 3; ++a)
+        if (a != pa) add(*pos_dst[a], pos_src[a]->p);
     add(g->M0, ph->M0.p);
-    g->has_b1 = ph->has_b1;
-    if (ph->has_b1) add(g->b1, ph->b1.p);
-    for (int t = 0; t < kNTypes; ++t)
-        if (g->built[t]) add(g->gid_sorted[t], g->gid_orig[t].p);
-    static_assert(7 + 1 + kNTypes <= kGatherMax, "gather set too small");
     {
         KScope ks(c, "layout_gather");
         k_gather_set<<<grid_for(c, K, kGatherTile), 256, 0, c->stream>>>(K, perm, gs);
     }
+    if (pa >= 0) *pos_dst[pa] = dalloc(K * sizeof(float));
+    g->T1 = dalloc(K * sizeof(float));
+    g->T2 = dalloc(K * sizeof(float));
+    g->dB0 = dalloc(K * sizeof(float));
+    g->has_b1 = ph->has_b1;
+    if (ph->has_b1) g->b1 = dalloc(K * sizeof(float));
+    for (int t = 0; t < kNTypes; ++t)
+        if (g->built[t]) g->gid_sorted[t] = dalloc(K * sizeof(int32_t));
+    g->rest_pending = true;
     g->has_M_init = ph->has_M_init;
     if (ph->has_M_init) {
         g->M_init = dalloc(3 * K * sizeof(float));
@@ -1111,6 +1118,38 @@ void build_layout(mrsim_ctx *c, const mrsim_phantom_t *ph, mrsim_groups *g) {
         k_gather_set<<<grid_for(c, K, kGatherTile), 256, 0, c->stream>>>(K, perm, gm);
     }
     sync(c);
+}
+
+void ensure_layout_arrays(mrsim_ctx *c, const mrsim_groups *cg, const mrsim_phantom_t *ph) {
+    if (!cg->rest_pending) return;
+    // the arrays were allocated by the group build; only their contents are
+    // formed here (the group set is not shared between threads)
+    mrsim_groups *g = const_cast<mrsim_groups *>(cg);
+    const int64_t K = g->K;
+    GatherSet gs{};
+    auto add = [&](DBuf &dst, const void *src) {
+        gs.in[gs.n] = static_cast<const uint32_t *>(src);
+        gs.out[gs.n] = dst.as<uint32_t>();
+        ++gs.n;
+    };
+    const int pa = (g->primary >= G_X && g->primary <= G_Z) ? g->primary - 1 : -1;
+    if (pa == 0) add(g->x, ph->x.p);
+    if (pa == 1) add(g->y, ph->y.p);
+    if (pa == 2) add(g->z, ph->z.p);
+    add(g->T1, ph->T1.p);
+    add(g->T2, ph->T2.p);
+    add(g->dB0, ph->dB0.p);
+    if (g->has_b1) add(g->b1, ph->b1.p);
+    for (int t = 0; t < kNTypes; ++t)
+        if (g->built[t]) add(g->gid_sorted[t], g->gid_orig[t].p);
+    static_assert(1 + 4 + kNTypes <= kGatherMax, "gather set too small");
+    {
+        KScope ks(c, "layout_gather");
+        k_gather_set<<<grid_for(c, K, kGatherTile), 256, 0, c->stream>>>(
+            K, g->perm.as<int32_t>(), gs);
+    }
+    MRSIM_CUDA(cudaGetLastError());
+    g->rest_pending = false;
 }
 
 void build_cell_threads(mrsim_ctx *c, mrsim_groups *g, const std::vector<int32_t> &count) {
