@@ -55,3 +55,18 @@ def test_binding_refuses_a_missing_library(tmp_path):
     from paper_2508_03960_gb300 import mrsim
     with pytest.raises(ImportError):
         mrsim.load_library(str(tmp_path / "libmrsim.so"))
+
+
+def test_binding_constants_equal_the_header():
+    """Every integer the Python binding names (status codes, modes, flags,
+    types, tuning parameters) has the value of the header's #define."""
+    from paper_2508_03960_gb300 import mrsim
+    src = open(os.path.join(ROOT, "include", "mrsim.h")).read()
+    defines = {m.group(1): int(m.group(2))
+               for m in re.finditer(r"^#define MRSIM_([A-Z0-9_]+)\s+(\d+)u?\b", src, flags=re.M)}
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(mrsim, name):
+            assert getattr(mrsim, name) == value, name
+            checked += 1
+    assert checked >= 30
